@@ -1,0 +1,250 @@
+"""CPU oracle for the SMMO hot path -- TEST INFRASTRUCTURE ONLY.
+
+A plain, slow, single-threaded array-of-structs restatement (in C, see the
+``*.c`` files beside this one) of the thesis' SMMO workloads: object-based
+Game of Life (Sec. 7.9), Wa-Tor (Sec. 7.7), Nagel-Schreckenberg traffic
+(Sec. 7.6), n-body with collision merge (Sec. 7.1/7.2) and the n-body adjoint.
+It has its own Philox4x32-10 (Salmon et al., SC'11).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  It never imports the CUDA library and the CUDA
+library never imports it; both consume the same seeded inputs from
+``paper_1908_05845_gb300.inputs``.
+
+Pins (tests/test_oracle_*.py): Philox known-answer vectors; Life blinker /
+glider / block, all 512 3x3 neighbourhoods and dense B3/S23 on random tori,
+the candidate-set closed form; Wa-Tor bookkeeping, lone fish / lone shark
+histories, full grid without sharks; NaSch free-flow closed form, car
+conservation on a ring with p = 0, evenly spaced flow; n-body momentum
+conservation, two-body circular orbit, energy drift O(dt^2), merge mass
+conservation; adjoint against central finite differences and the pair
+kernel against finite differences of the acceleration.  Parity of every
+function here is pinned by at least one of those.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_SOURCES = ["philox.c", "gol.c", "wator.c", "nasch.c", "nbody.c"]
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, strict IEEE)."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    deps = srcs + [os.path.join(_HERE, "oracle.h")]
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(d) for d in deps)):
+        return _LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ------------------------------------------------------------------ Philox
+def philox4x32_10(ctr, key):
+    lib = _load()
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib.orc_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def draw(seed: int, tag: int, step: int, cells, inst: int = 0) -> np.ndarray:
+    lib = _load()
+    cells = np.ascontiguousarray(cells, dtype=np.uint32)
+    out = np.empty_like(cells)
+    lib.orc_draw_many(ctypes.c_uint64(seed), ctypes.c_uint32(tag), ctypes.c_uint32(step),
+                      _p(cells), ctypes.c_int64(cells.size), ctypes.c_uint32(inst), _p(out))
+    return out
+
+
+# -------------------------------------------------------------- Game of Life
+EMPTY, ALIVE, CANDIDATE = 0, 1, 2
+
+
+def gol_run(W: int, H: int, kind, state, T: int):
+    """Returns (kind, state, counters[T, 7]) after T generations."""
+    lib = _load()
+    kind = np.ascontiguousarray(kind, dtype=np.uint8).copy()
+    state = np.ascontiguousarray(state, dtype=np.uint8).copy()
+    cnt = np.zeros((max(T, 1), 7), dtype=np.int64)
+    rc = lib.orc_gol_run(W, H, _p(kind), _p(state), T, _p(cnt))
+    if rc != 0:
+        raise ValueError("orc_gol_run: bad arguments")
+    return kind, state, cnt[:T]
+
+
+# ------------------------------------------------------------------- Wa-Tor
+FISH, SHARK = 1, 2
+
+
+class _WatorParams(ctypes.Structure):
+    _fields_ = [("fish_breed", ctypes.c_int), ("shark_breed", ctypes.c_int),
+                ("starve", ctypes.c_int), ("breed_strict", ctypes.c_int)]
+
+
+def wator_run(W, H, seed, kind, age, energy, T, t0=0, inst=0, fish_breed=4,
+              shark_breed=12, starve=3, breed_strict=0):
+    """Returns (kind, age, energy, counters[T, 8])."""
+    lib = _load()
+    kind = np.ascontiguousarray(kind, dtype=np.int8).copy()
+    age = np.ascontiguousarray(age, dtype=np.int16).copy()
+    energy = np.ascontiguousarray(energy, dtype=np.int16).copy()
+    cnt = np.zeros((max(T, 1), 8), dtype=np.int64)
+    p = _WatorParams(fish_breed, shark_breed, starve, breed_strict)
+    rc = lib.orc_wator_run(W, H, ctypes.c_uint64(seed), ctypes.c_uint32(inst), ctypes.byref(p),
+                           _p(kind), _p(age), _p(energy), t0, T, _p(cnt))
+    if rc != 0:
+        raise ValueError("orc_wator_run: bad arguments")
+    return kind, age, energy, cnt[:T]
+
+
+# ------------------------------------------------------ Nagel-Schreckenberg
+class _NaschGraph(ctypes.Structure):
+    _fields_ = [("num_streets", ctypes.c_int), ("street_start", ctypes.c_void_p),
+                ("street_len", ctypes.c_void_p), ("out_deg", ctypes.c_void_p),
+                ("out_street", ctypes.c_void_p), ("is_source", ctypes.c_void_p),
+                ("num_cells", ctypes.c_int), ("v_max", ctypes.c_int),
+                ("brake_threshold", ctypes.c_uint32), ("sources_enabled", ctypes.c_int),
+                ("sinks_enabled", ctypes.c_int)]
+
+
+def nasch_run(graph: dict, seed: int, car_v, T: int, t0: int = 0):
+    """graph: dict from inputs.nasch_graph (or a hand-built one).
+    Returns (car_v, counters[T, 4])."""
+    lib = _load()
+    keep = {k: np.ascontiguousarray(graph[k], dtype=dt) for k, dt in
+            [("street_start", np.int32), ("street_len", np.int32), ("out_deg", np.int32),
+             ("out_street", np.int32), ("is_source", np.uint8)]}
+    g = _NaschGraph(int(graph["num_streets"]), _p(keep["street_start"]).value,
+                    _p(keep["street_len"]).value, _p(keep["out_deg"]).value,
+                    _p(keep["out_street"]).value, _p(keep["is_source"]).value,
+                    int(graph["num_cells"]), int(graph.get("v_max", 5)),
+                    int(graph["brake_threshold"]), int(graph.get("sources_enabled", 1)),
+                    int(graph.get("sinks_enabled", 1)))
+    car_v = np.ascontiguousarray(car_v, dtype=np.int8).copy()
+    cnt = np.zeros((max(T, 1), 4), dtype=np.int64)
+    rc = lib.orc_nasch_run(ctypes.byref(g), ctypes.c_uint64(seed), _p(car_v), t0, T, _p(cnt))
+    if rc != 0:
+        raise ValueError("orc_nasch_run: bad arguments")
+    return car_v, cnt[:T]
+
+
+# ------------------------------------------------------------------- N-body
+class _NBodyParams(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_float), ("eps", ctypes.c_float), ("dt", ctypes.c_float),
+                ("merge_r", ctypes.c_float), ("merge", ctypes.c_int)]
+
+
+def nbody_run_f32(state: dict, T: int, G=1.0, eps=1e-2, dt=1e-3, merge_r=5e-3, merge=True):
+    """state: dict of float32 arrays x, y, z, vx, vy, vz, m and uint8 live
+    (indexed by body id).  Returns (new_state, merges_per_step[T])."""
+    lib = _load()
+    st = {k: np.ascontiguousarray(state[k], dtype=np.float32).copy()
+          for k in ("x", "y", "z", "vx", "vy", "vz", "m")}
+    st["live"] = np.ascontiguousarray(state["live"], dtype=np.uint8).copy()
+    N = st["x"].size
+    cnt = np.zeros(max(T, 1), dtype=np.int64)
+    p = _NBodyParams(G, eps, dt, merge_r, 1 if merge else 0)
+    rc = lib.orc_nbody_run_f32(N, ctypes.byref(p), *[_p(st[k]) for k in
+                               ("x", "y", "z", "vx", "vy", "vz", "m", "live")], T, _p(cnt))
+    if rc != 0:
+        raise ValueError("orc_nbody_run_f32: bad arguments")
+    return st, cnt[:T]
+
+
+def nbody_accel_f32(state: dict, G=1.0, eps=1e-2):
+    lib = _load()
+    x, y, z, m = (np.ascontiguousarray(state[k], dtype=np.float32) for k in ("x", "y", "z", "m"))
+    live = np.ascontiguousarray(state["live"], dtype=np.uint8)
+    N = x.size
+    ax, ay, az = (np.zeros(N, np.float32) for _ in range(3))
+    lib.orc_nbody_accel_f32(N, ctypes.c_float(G), ctypes.c_float(eps), _p(x), _p(y), _p(z),
+                            _p(m), _p(live), _p(ax), _p(ay), _p(az))
+    return ax, ay, az
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def nbody_run_f64(pos, vel, m, T, G=1.0, eps=1e-2, dt=1e-3):
+    lib = _load()
+    pos, vel, m = _d(pos).copy(), _d(vel).copy(), _d(m)
+    lib.orc_nbody_run_f64(m.size, ctypes.c_double(G), ctypes.c_double(eps), ctypes.c_double(dt),
+                          _p(pos), _p(vel), _p(m), T)
+    return pos, vel
+
+
+def nbody_accel_f64(pos, m, G=1.0, eps=1e-2):
+    lib = _load()
+    pos, m = _d(pos), _d(m)
+    acc = np.zeros_like(pos)
+    lib.orc_nbody_accel_f64(m.size, ctypes.c_double(G), ctypes.c_double(eps), _p(pos), _p(m), _p(acc))
+    return acc
+
+
+def nbody_energy_f64(pos, vel, m, G=1.0, eps=1e-2):
+    lib = _load()
+    pos, vel, m = _d(pos), _d(vel), _d(m)
+    E = ctypes.c_double()
+    P = (ctypes.c_double * 3)()
+    lib.orc_nbody_energy_f64(m.size, ctypes.c_double(G), ctypes.c_double(eps), _p(pos), _p(vel),
+                             _p(m), ctypes.byref(E), P)
+    return E.value, np.array(list(P))
+
+
+def nbody_pair_adjoint_f64(pos, m, mu, G=1.0, eps=1e-2):
+    lib = _load()
+    pos, m, mu = _d(pos), _d(m), _d(mu)
+    g = np.zeros_like(pos)
+    lib.orc_nbody_pair_adjoint_f64(m.size, ctypes.c_double(G), ctypes.c_double(eps), _p(pos),
+                                   _p(m), _p(mu), _p(g))
+    return g
+
+
+def nbody_adjoint_f64(pos0, vel0, m, T, ckpt=10, G=1.0, eps=1e-2, dt=1e-3):
+    """Returns (grad wrt v0 [N,3], loss)."""
+    lib = _load()
+    pos0, vel0, m = _d(pos0), _d(vel0), _d(m)
+    grad = np.zeros_like(pos0)
+    loss = ctypes.c_double()
+    rc = lib.orc_nbody_adjoint_f64(m.size, ctypes.c_double(G), ctypes.c_double(eps),
+                                   ctypes.c_double(dt), _p(pos0), _p(vel0), _p(m), T, ckpt,
+                                   _p(grad), ctypes.byref(loss))
+    if rc != 0:
+        raise ValueError("orc_nbody_adjoint_f64: bad arguments")
+    return grad, loss.value
+
+
+def nbody_loss_f64(pos0, vel0, m, T, G=1.0, eps=1e-2, dt=1e-3):
+    _, v = nbody_run_f64(pos0, vel0, m, T, G, eps, dt)
+    m = _d(m)
+    return 0.5 * float(np.sum(m[:, None] * v * v))

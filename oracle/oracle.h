@@ -1,0 +1,123 @@
+/*
+ * oracle.h -- CPU oracle for the SMMO hot path (TEST INFRASTRUCTURE ONLY).
+ *
+ * This is a plain, slow, single-threaded array-of-structs restatement of the
+ * four SMMO workloads of the thesis (Springer, "Memory-Efficient
+ * Object-Oriented Programming on GPUs", Ch. 7) plus its own Philox4x32-10.
+ * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may
+ * load it.  It shares no code, header or constant generator with the CUDA
+ * library in paper_1908_05845_gb300/csrc; the only thing both sides consume
+ * in common are the seeded input arrays built by
+ * paper_1908_05845_gb300/inputs.py, which contain none of the method's
+ * arithmetic.
+ *
+ * Every entry point returns 0 on success and a negative value on bad
+ * arguments.  All arrays are caller-owned host memory.
+ */
+#ifndef SMMO_ORACLE_H
+#define SMMO_ORACLE_H
+#include <stdint.h>
+
+/* ---------------------------------------------------------------- Philox */
+/* Philox4x32-10 block function (Salmon et al., SC'11, Sec. 3.2 / Table 2). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                       uint32_t out[4]);
+/* draw(tag, step, cell, inst): word 0 of Philox4x32-10 with
+ * key = (seed mod 2^32, seed >> 32), counter = (step, cell, tag, inst). */
+uint32_t orc_draw(uint64_t seed, uint32_t tag, uint32_t step, uint32_t cell,
+                  uint32_t inst);
+void orc_draw_many(uint64_t seed, uint32_t tag, uint32_t step,
+                   const uint32_t* cells, int64_t n, uint32_t inst,
+                   uint32_t* out);
+
+/* Random-stream tags used inside the method (step draws). */
+enum {
+  ORC_TAG_INIT = 0, ORC_TAG_FISH = 1, ORC_TAG_SHARK = 2, ORC_TAG_LEN = 3,
+  ORC_TAG_PLACE = 4, ORC_TAG_ROUTE = 5, ORC_TAG_BRAKE = 6, ORC_TAG_KIND = 7,
+  ORC_TAG_SIDE = 8, ORC_TAG_OUTDEG = 9, ORC_TAG_OUT = 10
+};
+
+/* ------------------------------------------------------------ Game of Life */
+/* Cell kinds in the canonical per-cell output. */
+enum { ORC_EMPTY = 0, ORC_ALIVE = 1, ORC_CANDIDATE = 2 };
+/* Runs T generations of the object-based Life of Sec. 7.9 on a W x H torus.
+ * kind/state: per-cell in/out arrays (kind: EMPTY/ALIVE/CANDIDATE; state:
+ * is_new flag of an Alive object, 0 for candidates).  Per generation
+ * counters (7 x int64 per generation, may be NULL):
+ * [alive, candidates, births, deaths, candidates_created, candidates_deleted,
+ *  allocs+frees]. */
+int orc_gol_run(int W, int H, uint8_t* kind, uint8_t* state, int T,
+                int64_t* counters);
+
+/* ---------------------------------------------------------------- Wa-Tor */
+enum { ORC_FISH = 1, ORC_SHARK = 2 };
+typedef struct {
+  int fish_breed, shark_breed, starve;
+  int breed_strict; /* 0: breed when age >= breed (default); 1: age > breed */
+} orc_wator_params;
+/* Runs steps t0+1 .. t0+T of Wa-Tor (Sec. 7.7) on a W x H torus.
+ * kind/age/energy are per-cell in/out arrays.  seed/inst select the draws.
+ * counters (may be NULL): 8 x int64 per step:
+ * [fish, sharks, fish_births, fish_eaten, shark_births, sharks_starved,
+ *  fish_moves, shark_moves]. */
+int orc_wator_run(int W, int H, uint64_t seed, uint32_t inst,
+                  const orc_wator_params* p, int8_t* kind, int16_t* age,
+                  int16_t* energy, int t0, int T, int64_t* counters);
+
+/* ------------------------------------------------- Nagel-Schreckenberg */
+typedef struct {
+  int num_streets;
+  const int32_t* street_start; /* first cell of each street */
+  const int32_t* street_len;   /* length (cells) of each street */
+  const int32_t* out_deg;      /* number of outgoing streets (0 = sink) */
+  const int32_t* out_street;   /* num_streets x 3 outgoing street ids */
+  const uint8_t* is_source;    /* 1 = spawns cars at its first cell */
+  int num_cells;
+  int v_max;
+  uint32_t brake_threshold;    /* floor(p * 2^32) */
+  int sources_enabled;         /* 0 disables car creation */
+  int sinks_enabled;           /* 0 keeps cars on sink streets (blocked) */
+} orc_nasch_graph;
+/* car_v: per-cell in/out array, -1 = no car, else velocity.
+ * counters (may be NULL): 4 x int64 per step: [cars, spawned, sunk, moved]. */
+int orc_nasch_run(const orc_nasch_graph* g, uint64_t seed, int8_t* car_v,
+                  int t0, int T, int64_t* counters);
+
+/* ---------------------------------------------------------------- N-body */
+typedef struct {
+  float G, eps, dt, merge_r;
+  int merge; /* 1: collision merge after each step */
+} orc_nbody_params_f32;
+/* FP32 DKD leapfrog with fixed evaluation order.  Arrays are N-long, indexed
+ * by body id; live[i] = 0 marks a body freed by a merge.  counters: 1 x
+ * int64 per step (merges in that step).  */
+int orc_nbody_run_f32(int N, const orc_nbody_params_f32* p, float* x, float* y,
+                      float* z, float* vx, float* vy, float* vz, float* m,
+                      uint8_t* live, int T, int64_t* counters);
+/* Accelerations only (one force evaluation), FP32, same order as the run. */
+int orc_nbody_accel_f32(int N, float G, float eps, const float* x,
+                        const float* y, const float* z, const float* m,
+                        const uint8_t* live, float* ax, float* ay, float* az);
+
+/* FP64 variants (no merge).  pos/vel: N x 3 row-major. */
+int orc_nbody_run_f64(int N, double G, double eps, double dt, double* pos,
+                      double* vel, const double* m, int T);
+int orc_nbody_accel_f64(int N, double G, double eps, const double* pos,
+                        const double* m, double* acc);
+/* Energy E = KE - G sum_{i<j} m_i m_j / sqrt(r^2 + eps^2), momentum P. */
+int orc_nbody_energy_f64(int N, double G, double eps, const double* pos,
+                         const double* vel, const double* m, double* E,
+                         double* P3);
+/* Adjoint of the no-merge DKD run: gradient of L = 1/2 sum m |v_T|^2 with
+ * respect to the initial velocities, checkpointing (x, v) every `ckpt`
+ * steps and recomputing within each segment.  grad: N x 3.  loss: L. */
+int orc_nbody_adjoint_f64(int N, double G, double eps, double dt,
+                          const double* pos0, const double* vel0,
+                          const double* m, int T, int ckpt, double* grad,
+                          double* loss);
+/* One application of the pair kernel g_k = G sum_{j!=k} H(x_j - x_k)
+ * (m_k mu_j - m_j mu_k), H(r) = I/s^3 - 3 r r^T / s^5. */
+int orc_nbody_pair_adjoint_f64(int N, double G, double eps, const double* pos,
+                               const double* m, const double* mu, double* g);
+
+#endif

@@ -1,0 +1,173 @@
+"""Pins of the n-body oracle (thesis Sec. 7.1/7.2) and its adjoint.
+
+Momentum conservation, the softened two-body circular orbit and its O(dt^2)
+phase error, O(dt^2) energy drift, merge bookkeeping (mass and momentum
+conserved, midpoint position, lowest receiver wins, a merge into a body that
+is itself merged is skipped), FP32 against FP64, and the adjoint against
+central finite differences (both the pair kernel and the whole 50-step run).
+"""
+import numpy as np
+
+from paper_1908_05845_gb300 import inputs
+
+
+def as64(st):
+    pos = np.stack([st["x"], st["y"], st["z"]], 1).astype(np.float64)
+    vel = np.stack([st["vx"], st["vy"], st["vz"]], 1).astype(np.float64)
+    return pos, vel, st["m"].astype(np.float64)
+
+
+def test_momentum_conserved_f64(orc):
+    pos, vel, m = as64(inputs.nbody_initial(64, 1))
+    _, P0 = orc.nbody_energy_f64(pos, vel, m)
+    p2, v2 = orc.nbody_run_f64(pos, vel, m, 50)
+    _, P1 = orc.nbody_energy_f64(p2, v2, m)
+    scale = np.sum(m[:, None] * np.abs(v2))
+    assert np.max(np.abs(P1 - P0)) / scale < 1e-12
+
+
+def _orbit(orc, dt, m=1.0, d=0.5, eps=1e-2):
+    w = np.sqrt(2 * m / (d * d + eps * eps) ** 1.5)
+    vt = w * d / 2
+    pos = np.array([[-d / 2, 0, 0], [d / 2, 0, 0]])
+    vel = np.array([[0, -vt, 0], [0, vt, 0]])
+    T = 2 * np.pi / w
+    n = int(round(T / dt))
+    p, v = orc.nbody_run_f64(pos, vel, np.array([m, m]), n, dt=T / n)
+    return np.max(np.abs(p - pos))
+
+
+def test_two_body_circular_orbit(orc):
+    e1 = _orbit(orc, 1e-3)
+    e2 = _orbit(orc, 5e-4)
+    assert e1 < 1e-2
+    assert 3.0 < e1 / e2 < 5.0  # second-order integrator
+
+
+def test_energy_drift_second_order(orc):
+    pos, vel, m = as64(inputs.nbody_initial(32, 2))
+    m = m * 0.01
+    E0, _ = orc.nbody_energy_f64(pos, vel, m)
+    drift = []
+    for dt, n in ((2e-3, 100), (1e-3, 200)):
+        p, v = orc.nbody_run_f64(pos, vel, m, n, dt=dt)
+        E1, _ = orc.nbody_energy_f64(p, v, m)
+        drift.append(abs(E1 - E0) / abs(E0))
+    assert drift[0] < 1e-3
+    assert 2.5 < drift[0] / drift[1] < 6.0
+
+
+def test_f32_matches_f64_short(orc):
+    st = inputs.nbody_initial(256, 3)
+    s32, _ = orc.nbody_run_f32(st, 5, merge=False)
+    pos, vel, m = as64(st)
+    p64, _ = orc.nbody_run_f64(pos, vel, m, 5)
+    p32 = np.stack([s32["x"], s32["y"], s32["z"]], 1)
+    assert np.max(np.abs(p32 - p64)) < 1e-5
+    ax, ay, az = orc.nbody_accel_f32(st)
+    a64 = orc.nbody_accel_f64(pos, m)
+    a32 = np.stack([ax, ay, az], 1)
+    assert np.max(np.abs(a32 - a64)) / np.max(np.abs(a64)) < 1e-5
+
+
+def _bodies(rows):
+    st = {k: np.array([r[i] for r in rows], np.float32)
+          for i, k in enumerate(("x", "y", "z", "vx", "vy", "vz", "m"))}
+    st["live"] = np.ones(len(rows), np.uint8)
+    return st
+
+
+def test_merge_rules(orc):
+    # body 0 heavy receiver, body 1 light and within R; body 2 far away
+    st = _bodies([(0.5, 0.5, 0.5, 0, 0, 0, 2.0), (0.501, 0.5, 0.5, 1.0, 0, 0, 1.0),
+                  (0.9, 0.9, 0.9, 0, 0, 0, 1.0)])
+    out, k = orc.nbody_run_f32(st, 1, G=0.0, merge_r=5e-3)
+    assert k[0] == 1 and list(out["live"]) == [1, 0, 1]
+    assert out["m"][0] == np.float32(3.0)
+    assert abs(out["vx"][0] - 1.0 / 3.0) < 1e-7
+    assert abs(out["x"][0] - (0.5 + (0.501 + 1.0e-3)) / 2) < 1e-6  # drifted 1e-3 first
+    # two receivers pick the same light body: the lower id wins
+    st = _bodies([(0.5, 0.5, 0.5, 0, 0, 0, 3.0), (0.506, 0.5, 0.5, 0, 0, 0, 5.0),
+                  (0.503, 0.5, 0.5, 0, 0, 0, 1.0)])
+    out, k = orc.nbody_run_f32(st, 1, G=0.0, dt=0.0, merge_r=4e-3)
+    assert k[0] == 1 and list(out["live"]) == [1, 1, 0] and out["m"][0] == 4.0
+    # a receiver takes the first lighter body in id order, even if a later
+    # one is closer: 1 takes 0 (not 2); 0 takes 2 but is itself merged
+    st = _bodies([(0.5, 0.5, 0.5, 0, 0, 0, 3.0), (0.502, 0.5, 0.5, 0, 0, 0, 5.0),
+                  (0.501, 0.5, 0.5, 0, 0, 0, 1.0)])
+    out, k = orc.nbody_run_f32(st, 1, G=0.0, dt=0.0, merge_r=5e-3)
+    assert k[0] == 1 and list(out["live"]) == [0, 1, 1] and out["m"][1] == 8.0
+    # chain: 0 (m=1) -> picked by 1 (m=2), 1 picked by 2 (m=3): only 1 -> 2 merges
+    st = _bodies([(0.5, 0.5, 0.5, 0, 0, 0, 1.0), (0.5015, 0.5, 0.5, 0, 0, 0, 2.0),
+                  (0.503, 0.5, 0.5, 0, 0, 0, 3.0)])
+    out, k = orc.nbody_run_f32(st, 1, G=0.0, dt=0.0, merge_r=2e-3)
+    assert k[0] == 1 and list(out["live"]) == [1, 0, 1] and out["m"][2] == 5.0
+
+
+def test_merge_conserves_mass_and_momentum(orc):
+    st = inputs.nbody_initial(512, 1)
+    m0 = float(st["m"].astype(np.float64).sum())
+    out, k = orc.nbody_run_f32(st, 20, merge_r=2e-2)
+    assert k.sum() > 0
+    live = out["live"] == 1
+    assert (~live).sum() == k.sum()
+    assert abs(out["m"][live].astype(np.float64).sum() - m0) / m0 < 1e-5
+
+
+def test_pair_adjoint_vs_fd(orc):
+    rng = np.random.default_rng(0)
+    N = 12
+    pos = rng.random((N, 3))
+    m = np.exp(0.5 * rng.standard_normal(N))
+    mu = rng.standard_normal((N, 3))
+    g = orc.nbody_pair_adjoint_f64(pos, m, mu)
+
+    def phi(p):
+        return float(np.sum(orc.nbody_accel_f64(p, m) * mu))
+
+    fd = np.zeros_like(pos)
+    h = 1e-6
+    for k in range(N):
+        for c in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[k, c] += h
+            pm[k, c] -= h
+            fd[k, c] = (phi(pp) - phi(pm)) / (2 * h)
+    assert np.linalg.norm(g - fd) / np.linalg.norm(fd) < 1e-6
+
+
+def test_adjoint_vs_central_fd_n256(orc):
+    st = inputs.nbody_initial(256, 1)
+    pos, vel, m = as64(st)
+    T = 50
+    grad, L = orc.nbody_adjoint_f64(pos, vel, m, T, ckpt=10)
+    assert abs(L - orc.nbody_loss_f64(pos, vel, m, T)) <= 1e-12 * abs(L)
+    rng = np.random.default_rng(1)
+    comps = rng.choice(3 * 256, size=96, replace=False)
+    fd = np.zeros(comps.size)
+
+    def central(i, c, h):
+        vp, vm = vel.copy(), vel.copy()
+        vp[i, c] += h
+        vm[i, c] -= h
+        return (orc.nbody_loss_f64(pos, vp, m, T) - orc.nbody_loss_f64(pos, vm, m, T)) / (2 * h)
+
+    for n, k in enumerate(comps):
+        i, c = divmod(int(k), 3)
+        # This 50-step run has close encounters, so the central difference's
+        # truncation error at h = 1e-6 is ~2% on the most sensitive
+        # components.  Richardson extrapolation of two central differences
+        # (h and h/2, h = 1e-7 max(1, |v|)) removes the O(h^2) term.
+        h = 1e-7 * max(1.0, abs(vel[i, c]))
+        fd[n] = (4.0 * central(i, c, h / 2) - central(i, c, h)) / 3.0
+    g = grad.reshape(-1)[comps]
+    assert np.linalg.norm(g - fd) / np.linalg.norm(fd) < 1e-3
+
+
+def test_adjoint_checkpoint_invariance(orc):
+    st = inputs.nbody_initial(64, 2)
+    pos, vel, m = as64(st)
+    g1, _ = orc.nbody_adjoint_f64(pos, vel, m, 23, ckpt=1)
+    g2, _ = orc.nbody_adjoint_f64(pos, vel, m, 23, ckpt=10)
+    g3, _ = orc.nbody_adjoint_f64(pos, vel, m, 23, ckpt=23)
+    assert np.array_equal(g1, g2) and np.array_equal(g2, g3)
