@@ -1,0 +1,298 @@
+/*
+ * smmo.h -- C ABI of the GB300 SMMO heap ("Single-Method Multiple-Objects":
+ * run one method on every live object of a class, objects stored in a
+ * Structure-of-Arrays heap with a device-side allocator).
+ *
+ * Thesis: M. Springer, "Memory-Efficient Object-Oriented Programming on
+ * GPUs" (arXiv 1908.05845).  Citations below name its sections, equations
+ * and algorithms.
+ *
+ * General rules
+ *  - Every call returns an int status (SMMO_OK = 0 or a negative SMMO_E_*).
+ *  - Pointers documented as "device" must point to device memory of the
+ *    current CUDA device; "host" pointers to host memory.  The library never
+ *    frees memory it did not allocate; caller-owned buffers stay
+ *    caller-owned.
+ *  - `stream` arguments are cudaStream_t values passed as void* (0 = the
+ *    legacy default stream).  Calls documented as asynchronous only enqueue
+ *    work; device-side failures (heap exhausted during a device `new`, a
+ *    retry budget running out, a double free) are recorded in the heap's
+ *    device error word and reported by smmo_heap_sync().
+ *  - A heap must be used from one stream at a time (its enumeration scratch
+ *    is shared by consecutive parallel_do calls).
+ *  - Device loops never spin without bound: every retry loop has a budget
+ *    and sets SMMO_E_CONTENTION or SMMO_E_DEVICE_OOM when it runs out.
+ */
+#ifndef SMMO_H
+#define SMMO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- status */
+enum {
+  SMMO_OK = 0,
+  SMMO_E_INVALID_ARG = -1,  /* bad argument (null pointer, id out of range) */
+  SMMO_E_OOM = -2,          /* heap has too few free blocks (host check)    */
+  SMMO_E_DEVICE_OOM = -3,   /* a device `new` found no free block            */
+  SMMO_E_CONTENTION = -4,   /* a device retry budget ran out                 */
+  SMMO_E_CUDA = -5,         /* a CUDA runtime call failed; see last_cuda_error */
+  SMMO_E_TIMEOUT = -6,      /* host wait exceeded its limit                  */
+  SMMO_E_BAD_HANDLE = -7,   /* double free / foreign handle                  */
+  SMMO_E_BOUNDS = -8,       /* debug bounds check failed                     */
+  SMMO_E_UNSUPPORTED = -9,  /* operation not supported in this state         */
+  SMMO_E_FROZEN = -10       /* class registration after the first bulk_new   */
+};
+
+const char* smmo_status_string(int status);
+/* Last CUDA error code observed by the library (cudaError_t as int). */
+int smmo_last_cuda_error(void);
+
+/* -------------------------------------------------------------- types */
+typedef struct smmo_heap smmo_heap;
+
+/* Handle of an object: (block index << 6) | slot.  0xFFFFFFFF = null.
+ * Replaces the thesis' 64-bit "fake pointer" (Sec. 5.2.3: block address,
+ * slot in bits 0-5, capacity and type id in the high bits); the type id
+ * and capacity are looked up in per-block and per-class tables instead. */
+typedef uint32_t smmo_handle;
+#define SMMO_NULL_HANDLE 0xFFFFFFFFu
+
+enum {
+  SMMO_I8 = 1, SMMO_U8 = 2, SMMO_I16 = 3, SMMO_U16 = 4, SMMO_I32 = 5,
+  SMMO_U32 = 6, SMMO_F32 = 7, SMMO_I64 = 8, SMMO_U64 = 9, SMMO_F64 = 10,
+  SMMO_HANDLE = 11 /* a smmo_handle (4 bytes) */
+};
+
+#define SMMO_MAX_CLASSES 16
+#define SMMO_MAX_FIELDS 16
+
+/* One field of a class.  `count` > 1 declares a fixed-length inner array
+ * stored as `count` separate SOA columns ("SOA, full inlining", Sec. 4.3).
+ * `ref_class` names the class a SMMO_HANDLE field refers to (-1 = unknown);
+ * compaction of class T rewrites every HANDLE column whose ref_class is T
+ * or a superclass of T (Sec. 6.3.4, "limiting heap scans"). */
+typedef struct {
+  const char* name;
+  int elem_type;
+  int count;
+  int ref_class;
+} smmo_field_desc;
+
+typedef struct {
+  /* Bytes of a block's data segment.  0 = 64 * size of the smallest
+   * registered class (Sec. 5.2.2, block capacity
+   * N_T = floor(64 size(T_s) / size(T))). Rounded up to 128. */
+  uint32_t block_data_bytes;
+  /* Active-block lookups tried before a new block is initialised
+   * (Sec. 5.3.2, "lookup retry").  Default 5. */
+  int32_t lookup_retries;
+  /* Budget of a device `new` (rounds of warp-aggregated reservation) and
+   * of bitmap spin loops.  Defaults 4096 and 1 << 20. */
+  int32_t alloc_retries;
+  int32_t bitmap_spins;
+  /* parallel_do launch shape: threads per CTA (multiple of 64) and CTAs
+   * per SM of the persistent grid.  Defaults 256 and 8. */
+  int32_t threads_per_cta;
+  int32_t ctas_per_sm;
+  /* 1 = device code checks handles and indices and records the first
+   * violation as SMMO_E_BOUNDS instead of touching memory. */
+  int32_t debug_checks;
+} smmo_heap_config;
+
+/* Fills `cfg` with the defaults above. */
+void smmo_heap_config_default(smmo_heap_config* cfg);
+
+typedef struct {
+  int64_t live_objects[SMMO_MAX_CLASSES];  /* per class (not subclasses) */
+  int64_t blocks[SMMO_MAX_CLASSES];        /* allocated blocks per class  */
+  int64_t free_blocks;
+  int64_t num_blocks;                       /* M                          */
+  double fragmentation[SMMO_MAX_CLASSES];   /* F of Sec. 6.2.2, per class */
+  double fragmentation_all;                 /* F over all allocated blocks */
+  int64_t allocs[SMMO_MAX_CLASSES];         /* device news since create   */
+  int64_t frees[SMMO_MAX_CLASSES];          /* device deletes since create */
+  int64_t slow_paths;                       /* blocks initialised by news */
+  int32_t capacity[SMMO_MAX_CLASSES];       /* N_T per class              */
+  int32_t object_bytes[SMMO_MAX_CLASSES];
+  int32_t block_bytes;
+  int32_t num_classes;
+} smmo_heap_stats;
+
+typedef struct {
+  int32_t passes;             /* defragmentation passes run              */
+  int64_t blocks_freed;       /* source blocks eliminated                */
+  int64_t objects_moved;
+  int64_t pointers_rewritten;
+  int64_t candidates_left;    /* candidates after the last pass          */
+} smmo_compact_stats;
+
+/* ------------------------------------------------------------- heap */
+/* Creates a heap inside the caller's device buffer (Sec. 5.2: one heap of
+ * M equal-size blocks; Sec. 5.3.1 hierarchical bitmaps).  The heap borrows
+ * `dev_buf` (>= 1 MiB, 256-byte aligned) and never frees it; the buffer
+ * must outlive the heap.  `cfg` may be NULL (defaults).  The block geometry
+ * is fixed when the first object is created. */
+int smmo_heap_create(const smmo_heap_config* cfg, void* dev_buf,
+                     size_t buf_bytes, void* stream, smmo_heap** out);
+/* Releases the host-side heap object and the small device state the
+ * library allocated; does not touch `dev_buf`. */
+int smmo_heap_destroy(smmo_heap* heap);
+
+/* Registers a class (Sec. 5.1.1 "Data Layout DSL", "Class Inheritance").
+ * Inherited fields come first (field i of the parent is field i of the
+ * child).  Abstract classes own no objects; parallel_do on them runs every
+ * concrete subclass.  Must precede the first bulk_new (SMMO_E_FROZEN). */
+int smmo_class_register(smmo_heap* heap, const char* name,
+                        const smmo_field_desc* fields, int nfields,
+                        int parent_class, int is_abstract, int* class_id);
+int smmo_class_lookup(smmo_heap* heap, const char* name, int* class_id);
+/* Number of fields (including inherited) and capacity N_T of a class;
+ * valid after the geometry is fixed (first bulk_new or smmo_heap_freeze). */
+int smmo_class_info(smmo_heap* heap, int class_id, int* nfields,
+                    int* capacity, int* object_bytes);
+/* Fixes the block geometry now (otherwise done by the first bulk_new). */
+int smmo_heap_freeze(smmo_heap* heap);
+
+/* Methods are compiled into the library and looked up by name, e.g.
+ * "test.add_i32", "wator.fish_prepare" (see the workload sections). */
+int smmo_method_lookup(const char* name, int* method_id);
+
+/* Host-launched creation of n objects of a concrete class (the thesis'
+ * parallel_new, Sec. 5.1.1).  field_src[k] is a device array of n elements
+ * for SOA column k (columns are the fields in order, an inner array of
+ * `count` elements contributing `count` columns).  Objects fill whole free
+ * blocks in ascending block order; out_handles (device, nullable) receives
+ * their handles.  out_first_block (host, nullable) receives the first
+ * block index when the blocks used are consecutive, else -1 (objects i
+ * then sit at block first + i / N_T, slot i % N_T).  Synchronises
+ * `stream`.  SMMO_E_OOM if the heap has fewer than ceil(n / N_T) free
+ * blocks. */
+int smmo_bulk_new(smmo_heap* heap, int class_id, int64_t n,
+                  const void* const* field_src, smmo_handle* out_handles,
+                  int64_t* out_first_block, void* stream);
+
+/* parallel_do(class, method) (Sec. 5.2.7): for every concrete class C in
+ * the subtree of `class_id`, snapshot the allocated blocks of C with their
+ * allocation bitmaps, then run `method` once for every object of C that
+ * existed at that point, one thread per slot.  Objects created by the
+ * method are not visited; the method may delete only its own object of
+ * the visited class (and any object of another class).  `args` (host,
+ * args_bytes <= 1024) is copied by value into the kernel parameters.
+ * Asynchronous; capturable in a CUDA graph. */
+int smmo_parallel_do(smmo_heap* heap, int class_id, int method_id,
+                     const void* args, size_t args_bytes, void* stream);
+
+/* Handles of all live objects of class_id (and of its subclasses when
+ * include_subclasses != 0), in unspecified order, into out_handles
+ * (device, capacity `cap`).  *out_count (host) receives the full count,
+ * which may exceed cap (output truncated).  Synchronises `stream`.  The
+ * enumeration follows the thesis' indices() of the allocated-block bitmaps
+ * (Sec. 5.3.1, "enumerating set bit indices"). */
+int smmo_enumerate_live(smmo_heap* heap, int class_id, int include_subclasses,
+                        smmo_handle* out_handles, int64_t cap,
+                        int64_t* out_count, void* stream);
+
+/* Copies field columns of n objects into dense arrays: dst[k][i] = column
+ * `columns[k]` of object handles[i].  Column indices count inner-array
+ * columns (see bulk_new).  handles/dst are device pointers; `columns` and
+ * `dst` arrays are host arrays of length ncol.  Asynchronous. */
+int smmo_gather_fields(smmo_heap* heap, int class_id, const smmo_handle* handles,
+                       int64_t n, const int* columns, int ncol,
+                       void* const* dst, void* stream);
+
+/* Defragments class_id (CompactGpu, Ch. 6): passes of (1) candidate scan
+ * (blocks at most n/(n+1) full, Sec. 6.3.1), (2) source/target assignment
+ * (first B = floor(r/(n+1)) candidates are sources, Sec. 6.3.2), (3) object
+ * copy, (4) forwarding pointers in the source blocks, (5) rewrite of every
+ * HANDLE column referring to class_id or a superclass, (6) block-state
+ * update, until at most k1 candidates remain (Sec. 6.3.6).  Handles held
+ * outside the heap are invalidated.  Synchronises `stream`. */
+int smmo_compact(smmo_heap* heap, int class_id, int defrag_factor,
+                 int64_t k1, smmo_compact_stats* out, void* stream);
+
+/* Statistics (Sec. 6.2.2 fragmentation F; device counters).  Synchronises
+ * `stream`. */
+int smmo_heap_get_stats(smmo_heap* heap, smmo_heap_stats* out, void* stream);
+
+/* Checks the heap invariants after all kernels have finished (Sec. 5.4.6,
+ * consistency of hierarchical bitmaps; Sec. 6.2.2, block states):
+ * every higher-level bit equals the OR of its container; a block is either
+ * free or allocated to exactly one class, the one in its type id; a block
+ * is active iff it is allocated and not full; an allocated block holds at
+ * least one object; free blocks have no object.  *violations (host)
+ * receives the number of violated checks (0 = consistent).  Synchronises
+ * `stream`. */
+int smmo_heap_check(smmo_heap* heap, int64_t* violations, void* stream);
+
+/* Synchronises `stream` and returns the first device error recorded since
+ * the last sync (then clears it).  *detail (host, nullable) receives the
+ * error's detail word (e.g. the offending handle). */
+int smmo_heap_sync(smmo_heap* heap, void* stream, uint64_t* detail);
+
+/* Device pointer to the start of a block's data segment and the column
+ * offset table of a class, for callers writing their own kernels.
+ * col_off (host, SMMO_MAX_FIELDS*?) receives per-column byte offsets inside
+ * a block; *block_bytes the block stride. */
+int smmo_class_layout(smmo_heap* heap, int class_id, uint32_t* col_off,
+                      int* ncols, uint32_t* block_bytes, void** data_base);
+
+/* ===================================================== cellular workloads
+ * A "world" is a set of independent simulation instances of the thesis'
+ * cellular SMMO applications on one heap (Ch. 7): object-based Game of Life
+ * (Sec. 7.9; classes Cell, LAgent, Alive, Candidate) and Wa-Tor (Sec. 7.7;
+ * classes Cell, WAgent, Fish, Shark), each on its own W x H torus.  All
+ * instances' objects share the heap; one step runs every do-all of the
+ * step once per class over all instances (one Life generation and one
+ * Wa-Tor iteration).  With one instance this is the plain single
+ * simulation.  Randomness is Philox4x32-10 keyed by
+ * (seed; step, local cell, tag, instance); contested cells go to the agent
+ * on the lowest cell index. */
+typedef struct smmo_world smmo_world;
+enum { SMMO_WORLD_LIFE = 0, SMMO_WORLD_WATOR = 1 };
+
+typedef struct {
+  int fish_breed;   /* fish breed when age >= fish_breed (default 4)   */
+  int shark_breed;  /* sharks likewise (default 12)                    */
+  int starve;       /* shark energy after eating / at birth (3)        */
+  int breed_strict; /* 1: breed when age > breed instead of >=         */
+} smmo_wator_params;
+
+/* Registers the classes in a fresh heap (no class registered yet, else
+ * SMMO_E_FROZEN) and creates the instances.  kind/W/H: host arrays of
+ * n_inst entries (W, H >= 3).  Per-cell initial state: device arrays over
+ * the concatenation of all instances' cells in instance order, row-major
+ * (cell = y * W + x): init_kind (Life: 0 empty, 1 Alive, 2 Candidate;
+ * Wa-Tor: 0 empty, 1 Fish, 2 Shark), init_age / init_energy (Wa-Tor,
+ * nullable = 0), init_state (Life is_new flag, nullable = 0).  params may be
+ * NULL.  Synchronises `stream`.  The world allocates two small instance
+ * tables with cudaMalloc, freed by smmo_world_destroy. */
+int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind,
+                      const uint32_t* W, const uint32_t* H, uint64_t seed,
+                      const smmo_wator_params* params, const int8_t* init_kind,
+                      const int16_t* init_age, const int16_t* init_energy,
+                      const uint8_t* init_state, void* stream,
+                      smmo_world** out);
+/* Advances every instance by nsteps steps.  Asynchronous (host loop of
+ * parallel_do launches; capturable in a CUDA graph). */
+int smmo_world_step(smmo_world* w, int nsteps, void* stream);
+/* Writes the live objects into per-cell device arrays (same indexing as
+ * the initial state; kind, age, energy, state as above; empty cells 0) and
+ * counts consistency errors (two agents on a cell, a cell not pointing back
+ * at its agent) into *errors (host, nullable).  Synchronises `stream`. */
+int smmo_world_export(smmo_world* w, int8_t* kind, int16_t* age, int16_t* energy,
+                      uint8_t* state, int64_t* errors, void* stream);
+/* total_cells, class ids [Cell, WAgent, Fish, Shark, LAgent, Alive,
+ * Candidate] (-1 when absent; class_ids host array of 7), steps done. */
+int smmo_world_info(smmo_world* w, int64_t* total_cells, int* class_ids,
+                    uint32_t* steps_done);
+int smmo_world_destroy(smmo_world* w);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMMO_H */

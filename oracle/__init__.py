@@ -95,7 +95,7 @@ def gol_run(W: int, H: int, kind, state, T: int):
     kind = np.ascontiguousarray(kind, dtype=np.uint8).copy()
     state = np.ascontiguousarray(state, dtype=np.uint8).copy()
     cnt = np.zeros((max(T, 1), 7), dtype=np.int64)
-    rc = lib.orc_gol_run(W, H, _p(kind), _p(state), T, _p(cnt))
+    rc = lib.orc_gol_run(int(W), int(H), _p(kind), _p(state), int(T), _p(cnt))
     if rc != 0:
         raise ValueError("orc_gol_run: bad arguments")
     return kind, state, cnt[:T]
@@ -119,8 +119,8 @@ def wator_run(W, H, seed, kind, age, energy, T, t0=0, inst=0, fish_breed=4,
     energy = np.ascontiguousarray(energy, dtype=np.int16).copy()
     cnt = np.zeros((max(T, 1), 8), dtype=np.int64)
     p = _WatorParams(fish_breed, shark_breed, starve, breed_strict)
-    rc = lib.orc_wator_run(W, H, ctypes.c_uint64(seed), ctypes.c_uint32(inst), ctypes.byref(p),
-                           _p(kind), _p(age), _p(energy), t0, T, _p(cnt))
+    rc = lib.orc_wator_run(int(W), int(H), ctypes.c_uint64(int(seed)), ctypes.c_uint32(int(inst)),
+                           ctypes.byref(p), _p(kind), _p(age), _p(energy), int(t0), int(T), _p(cnt))
     if rc != 0:
         raise ValueError("orc_wator_run: bad arguments")
     return kind, age, energy, cnt[:T]
@@ -151,7 +151,7 @@ def nasch_run(graph: dict, seed: int, car_v, T: int, t0: int = 0):
                     int(graph.get("sinks_enabled", 1)))
     car_v = np.ascontiguousarray(car_v, dtype=np.int8).copy()
     cnt = np.zeros((max(T, 1), 4), dtype=np.int64)
-    rc = lib.orc_nasch_run(ctypes.byref(g), ctypes.c_uint64(seed), _p(car_v), t0, T, _p(cnt))
+    rc = lib.orc_nasch_run(ctypes.byref(g), ctypes.c_uint64(int(seed)), _p(car_v), int(t0), int(T), _p(cnt))
     if rc != 0:
         raise ValueError("orc_nasch_run: bad arguments")
     return car_v, cnt[:T]

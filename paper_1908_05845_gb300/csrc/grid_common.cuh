@@ -1,0 +1,79 @@
+// grid_common.cuh -- helpers shared by the cellular workloads (Life, Wa-Tor):
+// counter-based random draws, the instance table of a (batched) heap, and
+// addressing of the statically allocated Cell objects.
+#pragma once
+#include <cstdint>
+
+#include "smmo_core.cuh"
+
+namespace smmo {
+
+// Philox4x32-10 (Salmon et al., SC'11, Sec. 3.2 and Table 2): ten rounds of
+// two 32x32->64 multiplications, high halves xored with the other counter
+// words and the round key, Weyl-sequence key schedule.  draw() returns word
+// 0 for key (seed lo, seed hi) and counter (step, cell, tag, inst).
+__device__ __forceinline__ uint32_t philox_draw(uint64_t seed, uint32_t tag, uint32_t step,
+                                                uint32_t cell, uint32_t inst) {
+  uint32_t c0 = step, c1 = cell, c2 = tag, c3 = inst;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+  }
+  return c0;
+}
+
+// Random-stream tags of the step draws.
+enum : uint32_t { TAG_FISH = 1, TAG_SHARK = 2, TAG_ROUTE = 5, TAG_BRAKE = 6 };
+
+// One simulation instance of a (batched) heap: its cells occupy the global
+// cell range [cell_base, cell_base + W*H) of the dense Cell objects.
+struct Inst {
+  uint32_t cell_base;
+  uint32_t W;
+  uint32_t H;
+  uint32_t id;  // instance number used in the random counter
+};
+
+// Instance owning global cell g (instances sorted by cell_base).
+__device__ __forceinline__ const Inst* find_inst(const Inst* tab, uint32_t n, uint32_t g) {
+  uint32_t lo = 0, hi = n;  // invariant: tab[lo].cell_base <= g
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(&tab[mid].cell_base) <= g) lo = mid; else hi = mid;
+  }
+  return tab + lo;
+}
+
+// The Cell objects are created by one bulk_new into consecutive blocks of
+// capacity 64, so cell g is object slot g % 64 of block cell_b0 + g / 64.
+struct CellRef {
+  uint8_t* data;
+  uint32_t block_bytes;
+  uint32_t b0;
+  __device__ __forceinline__ uint8_t* blk(uint32_t g) const {
+    return data + (size_t)(b0 + (g >> 6)) * block_bytes;
+  }
+  template <class T>
+  __device__ __forceinline__ T* col(uint32_t g, uint32_t off) const {
+    return reinterpret_cast<T*>(blk(g) + off) + (g & 63);
+  }
+  __device__ __forceinline__ uint32_t handle(uint32_t g) const { return ((b0 + (g >> 6)) << 6) | (g & 63); }
+};
+
+// Torus neighbour of local cell (x, y) in direction d:
+// 0 = (0,-1), 1 = (+1,0), 2 = (0,+1), 3 = (-1,0).
+__device__ __forceinline__ uint32_t torus_nb4(uint32_t x, uint32_t y, uint32_t W, uint32_t H, int d) {
+  uint32_t nx = x, ny = y;
+  if (d == 0) ny = y == 0 ? H - 1 : y - 1;
+  else if (d == 1) nx = x + 1 == W ? 0 : x + 1;
+  else if (d == 2) ny = y + 1 == H ? 0 : y + 1;
+  else nx = x == 0 ? W - 1 : x - 1;
+  return ny * W + nx;
+}
+
+}  // namespace smmo

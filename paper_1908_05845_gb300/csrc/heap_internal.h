@@ -1,0 +1,81 @@
+// heap_internal.h -- host-side heap object shared by the library's .cu files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "smmo.h"
+#include "smmo_core.cuh"
+
+struct ClassInfo {
+  std::string name;
+  std::vector<smmo_field_desc> fields;   // including inherited (first)
+  std::vector<std::string> field_names;  // owned copies of the names
+  int parent = -1;
+  int abstract = 0;
+  std::vector<int> children;
+  // geometry (after freeze)
+  int ncols = 0;
+  int object_bytes = 0;
+  smmo::ClassLayout layout{};
+};
+
+struct smmo_heap {
+  smmo_heap_config cfg{};
+  uint8_t* buf = nullptr;
+  size_t buf_bytes = 0;
+  bool frozen = false;
+  int device = 0;
+  int num_sms = 0;
+  std::vector<ClassInfo> classes;
+  smmo::HeapView view{};
+  smmo::ClassLayout* d_layouts = nullptr;  // inside buf
+  uint32_t* d_scratch = nullptr;           // inside buf: num_blocks + 64 words
+};
+
+namespace smmo {
+// status helpers
+int cuda_status(cudaError_t e);
+int freeze(smmo_heap* h, cudaStream_t s);
+// concrete classes in the subtree of c (c itself first if concrete)
+void concrete_subtree(const smmo_heap* h, int c, std::vector<int>* out);
+// enumerate class c into h->view.R, count into st->rcount (asynchronous)
+int enumerate(smmo_heap* h, int c, cudaStream_t s);
+// grid for persistent kernels
+inline dim3 do_all_grid(const smmo_heap* h) {
+  return dim3((unsigned)(h->num_sms * h->cfg.ctas_per_sm));
+}
+
+// Method registry: methods are compiled-in do-all kernels.
+typedef int (*method_launch_fn)(smmo_heap*, int cls, const void* args, cudaStream_t);
+struct MethodEntry {
+  const char* name;
+  size_t args_size;
+  method_launch_fn launch;
+};
+const MethodEntry* method_by_id(int id);
+}  // namespace smmo
+
+// Per-workload method tables (external linkage: defined in the wl_*.cu files).
+extern const smmo::MethodEntry g_methods_test[];
+extern const int g_methods_test_n;
+extern const smmo::MethodEntry g_methods_wator[];
+extern const int g_methods_wator_n;
+extern const smmo::MethodEntry g_methods_gol[];
+extern const int g_methods_gol_n;
+extern const smmo::MethodEntry g_methods_nasch[];
+extern const int g_methods_nasch_n;
+extern const smmo::MethodEntry g_methods_nbody[];
+extern const int g_methods_nbody_n;
+
+#ifdef __CUDACC__
+// Instantiates the do-all kernel for method M (see smmo_core.cuh).
+template <class M>
+int launch_do_all(smmo_heap* h, int cls, const void* args, cudaStream_t s) {
+  const typename M::Args* a = static_cast<const typename M::Args*>(args);
+  smmo::do_all_kernel<M><<<smmo::do_all_grid(h), h->cfg.threads_per_cta, 0, s>>>(h->view, cls, *a);
+  return smmo::cuda_status(cudaGetLastError());
+}
+#define SMMO_METHOD(name, M) {name, sizeof(typename M::Args), &launch_do_all<M>}
+#endif

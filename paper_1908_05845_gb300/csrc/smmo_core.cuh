@@ -1,0 +1,409 @@
+// smmo_core.cuh -- device-side core of the SMMO heap (sm_103a).
+//
+// Heap layout (all inside the caller's buffer):
+//   * per block: a 64-bit object allocation bitmap (alloc_bm) and a type id
+//     (block_type); Sec. 5.2.1 "block structure".  The data segments of all
+//     blocks form one array of M equal-size blocks, each holding the SOA
+//     columns of up to N_T <= 64 objects of one class (Sec. 5.2, Fig. 5.4).
+//     Bitmaps and type ids live in their own arrays instead of a block
+//     header, so enumeration and statistics read 8 bytes per block.
+//   * hierarchical bitmaps (Sec. 5.3.1) of M bits: free, and per class
+//     allocated[T], active[T], defrag[T].  All of them share one geometry
+//     (levels of 64-bit containers until one container remains).
+//   * a device state word block: error word, enumeration counter and
+//     sharded event counters.
+//
+// Every loop that waits for another thread has a budget; on exhaustion it
+// records SMMO_E_CONTENTION / SMMO_E_DEVICE_OOM in the state and gives up
+// (the thesis' allocator loops forever on OOM, Alg. 5.1; that is not
+// acceptable on a shared GPU).
+#pragma once
+#include <cstdint>
+
+#include "smmo.h"
+
+#define SMMO_MAX_COLS 32
+#define SMMO_MAX_LEVELS 6
+#define SMMO_NSHARD 32
+#define SMMO_CTR_SLOW 0
+#define SMMO_CTR_RETRY 1
+#define SMMO_CTR_ALLOC(c) (2 + (c))
+#define SMMO_CTR_FREE(c) (2 + SMMO_MAX_CLASSES + (c))
+#define SMMO_NCTR (2 + 2 * SMMO_MAX_CLASSES)
+
+namespace smmo {
+
+constexpr uint32_t kNull = 0xFFFFFFFFu;
+constexpr unsigned long long kAll = ~0ull;
+
+struct ClassLayout {
+  uint32_t cap;                       // N_T
+  uint32_t ncols;
+  unsigned long long capmask;         // low N_T bits set
+  uint32_t col_off[SMMO_MAX_COLS];    // byte offset of each SOA column
+  uint32_t col_size[SMMO_MAX_COLS];   // element size of each column
+};
+
+struct DeviceState {
+  int err;
+  int pad0;
+  unsigned long long err_detail;
+  uint32_t rcount;                    // enumeration result count
+  uint32_t pad1;
+  unsigned long long aux[6];          // per-call scratch counters
+  unsigned long long stat_live[SMMO_MAX_CLASSES];
+  unsigned long long stat_blocks[SMMO_MAX_CLASSES];
+  unsigned long long stat_free_slots[SMMO_MAX_CLASSES];
+  unsigned long long stat_free_blocks;
+  unsigned long long pad2;
+  unsigned long long ctr[SMMO_NSHARD][SMMO_NCTR];
+};
+
+// An enumerated block: its index and the snapshot of its allocation bitmap
+// (the thesis' "iteration bitmap", Sec. 5.2.1, carried with the index).
+struct __align__(16) REntry {
+  uint32_t block;
+  uint32_t pad;
+  unsigned long long bits;
+};
+
+struct HeapView {
+  uint8_t* data;                      // block data segments
+  unsigned long long* alloc_bm;       // per-block allocation bitmaps
+  uint32_t* block_type;               // per-block class id
+  unsigned long long* bitmaps;        // all hierarchical bitmaps
+  DeviceState* st;
+  const ClassLayout* cls;             // per-class layouts (device)
+  REntry* R;                          // enumeration scratch
+  uint32_t block_bytes;
+  uint32_t num_blocks;
+  uint32_t bm_words;                  // words of one hierarchical bitmap
+  uint32_t nlevels;
+  uint32_t level_off[SMMO_MAX_LEVELS];
+  uint32_t level_words[SMMO_MAX_LEVELS];
+  int32_t num_classes;
+  int32_t lookup_retries;
+  int32_t alloc_retries;
+  int32_t bitmap_spins;
+  int32_t debug;
+};
+
+// bitmap ids
+__host__ __device__ __forceinline__ int bm_free() { return 0; }
+__host__ __device__ __forceinline__ int bm_alloc(const HeapView& h, int c) { return 1 + c; }
+__host__ __device__ __forceinline__ int bm_active(const HeapView& h, int c) {
+  return 1 + h.num_classes + c;
+}
+__host__ __device__ __forceinline__ int bm_defrag(const HeapView& h, int c) {
+  return 1 + 2 * h.num_classes + c;
+}
+
+#ifdef __CUDACC__
+
+__device__ __forceinline__ unsigned long long* bm_level(const HeapView& h, int k, int l) {
+  return h.bitmaps + (size_t)k * h.bm_words + h.level_off[l];
+}
+
+__device__ __forceinline__ unsigned long long ld_cg(const unsigned long long* p) {
+  return __ldcg(p);
+}
+
+__device__ __forceinline__ void set_error(const HeapView& h, int code,
+                                          unsigned long long detail) {
+  if (atomicCAS(&h.st->err, 0, code) == 0) h.st->err_detail = detail;
+}
+
+__device__ __forceinline__ void count(const HeapView& h, int ctr, unsigned long long v) {
+  atomicAdd(&h.st->ctr[blockIdx.x % SMMO_NSHARD][ctr], v);
+}
+
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+  // integer finaliser (murmur3 fmix32) for rotation seeds
+  x ^= x >> 16; x *= 0x85ebca6bu; x ^= x >> 13; x *= 0xc2b2ae35u; x ^= x >> 16;
+  return x;
+}
+
+// Position of the n-th (0-based) set bit of b (Alg. 5.10 "nth_set_bit":
+// clear the n lowest set bits, then find-first-set).  -1 if b has <= n bits.
+__device__ __forceinline__ int nth_set_bit(unsigned long long b, int n) {
+  for (int i = 0; i < n; ++i) b &= b - 1;
+  return b ? __ffsll((long long)b) - 1 : -1;
+}
+
+// ---------------------------------------------------- hierarchical bitmaps
+// Blocking set/clear of bit `pos` at level l >= 1 (higher levels are always
+// changed with the blocking form, Sec. 5.3.1 "set and clear with atomic
+// operations"), then propagation upwards while a container changes between
+// empty and non-empty.
+static __device__ __noinline__ void bm_propagate(const HeapView& h, int k, int l, uint32_t pos,
+                                          bool set) {
+  for (; l < (int)h.nlevels; ++l) {
+    unsigned long long* w = bm_level(h, k, l) + (pos >> 6);
+    const unsigned long long m = 1ull << (pos & 63);
+    unsigned long long prev = 0;
+    bool done = false;
+    for (int s = 0; s < h.bitmap_spins; ++s) {
+      prev = set ? atomicOr(w, m) : atomicAnd(w, ~m);
+      if (set ? !(prev & m) : (prev & m)) { done = true; break; }
+      __nanosleep(32);
+    }
+    if (!done) { set_error(h, SMMO_E_CONTENTION, ((unsigned long long)k << 32) | pos); return; }
+    // continue only on set-first / clear-last of this container
+    if (set ? (prev != 0) : (prev != m)) return;
+    pos >>= 6;
+  }
+}
+
+// try_set / try_clear of a level-0 bit (Alg. 5.3 try_clear; try_set is its
+// mirror).  Returns true iff this thread flipped the bit.
+__device__ __forceinline__ bool bm_try_set(const HeapView& h, int k, uint32_t pos) {
+  unsigned long long* w = bm_level(h, k, 0) + (pos >> 6);
+  const unsigned long long m = 1ull << (pos & 63);
+  const unsigned long long prev = atomicOr(w, m);
+  if (prev & m) return false;
+  if (prev == 0 && h.nlevels > 1) bm_propagate(h, k, 1, pos >> 6, true);
+  return true;
+}
+
+__device__ __forceinline__ bool bm_try_clear(const HeapView& h, int k, uint32_t pos) {
+  unsigned long long* w = bm_level(h, k, 0) + (pos >> 6);
+  const unsigned long long m = 1ull << (pos & 63);
+  const unsigned long long prev = atomicAnd(w, ~m);
+  if (!(prev & m)) return false;
+  if (prev == m && h.nlevels > 1) bm_propagate(h, k, 1, pos >> 6, false);
+  return true;
+}
+
+// Blocking forms (retry until this thread flipped the bit), bounded.
+__device__ __forceinline__ void bm_set(const HeapView& h, int k, uint32_t pos) {
+  for (int s = 0; s < h.bitmap_spins; ++s) {
+    if (bm_try_set(h, k, pos)) return;
+    __nanosleep(32);
+  }
+  set_error(h, SMMO_E_CONTENTION, ((unsigned long long)k << 32) | pos);
+}
+
+__device__ __forceinline__ void bm_clear(const HeapView& h, int k, uint32_t pos) {
+  for (int s = 0; s < h.bitmap_spins; ++s) {
+    if (bm_try_clear(h, k, pos)) return;
+    __nanosleep(32);
+  }
+  set_error(h, SMMO_E_CONTENTION, ((unsigned long long)k << 32) | pos);
+}
+
+__device__ __forceinline__ bool bm_get(const HeapView& h, int k, uint32_t pos) {
+  return (ld_cg(bm_level(h, k, 0) + (pos >> 6)) >> (pos & 63)) & 1;
+}
+
+// Top-down search for any set bit (Alg. 5.4 try_find_set), each container
+// rotated by a seed-dependent amount before find-first-set (Sec. 5.3.2,
+// "bitmap rotation").  Returns -1 (FAIL) on an empty or inconsistent path.
+__device__ __forceinline__ int bm_try_find_set(const HeapView& h, int k, uint32_t seed) {
+  uint32_t idx = 0;
+  for (int l = (int)h.nlevels - 1; l >= 0; --l) {
+    const unsigned long long w = ld_cg(bm_level(h, k, l) + idx);
+    if (w == 0) return -1;
+    const int rot = mix32(seed + 0x9E3779B9u * (uint32_t)(l + 1)) & 63;
+    const unsigned long long r = rot ? ((w >> rot) | (w << (64 - rot))) : w;
+    const int b = ((__ffsll((long long)r) - 1) + rot) & 63;
+    idx = idx * 64 + (uint32_t)b;
+  }
+  return idx < h.num_blocks ? (int)idx : -1;
+}
+
+// clear(): find a set bit and clear it atomically (Sec. 5.3.1), bounded.
+__device__ __forceinline__ int bm_clear_any(const HeapView& h, int k, uint32_t seed) {
+  for (int s = 0; s < h.bitmap_spins; ++s) {
+    const int i = bm_try_find_set(h, k, seed + 7919u * (uint32_t)s);
+    if (i < 0) {
+      // an empty top-level word means the bitmap is (momentarily) empty
+      if (ld_cg(bm_level(h, k, h.nlevels - 1)) == 0) return -1;
+      __nanosleep(64);
+      continue;
+    }
+    if (bm_try_clear(h, k, (uint32_t)i)) return i;
+  }
+  return -2;
+}
+
+// ----------------------------------------------------------- field access
+__device__ __forceinline__ uint8_t* block_data(const HeapView& h, uint32_t bid) {
+  return h.data + (size_t)bid * h.block_bytes;
+}
+
+template <class T>
+__device__ __forceinline__ T* field_ptr(const HeapView& h, uint32_t col_off, uint32_t handle) {
+  return reinterpret_cast<T*>(block_data(h, handle >> 6) + col_off) + (handle & 63);
+}
+
+__device__ __forceinline__ uint32_t type_of(const HeapView& h, uint32_t handle) {
+  return __ldcg(h.block_type + (handle >> 6));
+}
+
+// ------------------------------------------------------------- deallocation
+// Frees the slots `bits` of block `bid` of class t: the divergence-safe
+// deallocation of Alg. 5.12 with block invalidation (Alg. 5.11) folded in.
+// All block-state bitmap changes are collected as pending +1/-1 operations
+// first and then retried with try_ operations in one converged loop, so no
+// lane waits on a bit that another lane of its own warp has yet to flip.
+static __device__ __noinline__ void dealloc_bits(const HeapView& h, uint32_t bid, uint32_t t,
+                                          unsigned long long bits) {
+  const unsigned long long capmask = __ldg(&h.cls[t].capmask);
+  const unsigned long long empty = ~capmask;
+  const unsigned long long before = atomicAnd(h.alloc_bm + bid, ~bits);
+  if ((before & bits) != bits) {  // precondition of Alg. 5.9 violated
+    set_error(h, SMMO_E_BAD_HANDLE, ((unsigned long long)bid << 6) | (__ffsll((long long)bits) - 1));
+    return;
+  }
+  int act = 0, alc = 0, fre = 0;
+  if (before == kAll) act += 1;  // freed the first slot of a full block
+  if ((before & ~bits) == empty) {
+    // freed the last object: try to invalidate the block (Alg. 5.11)
+    for (int s = 0; s < h.bitmap_spins; ++s) {
+      const unsigned long long ib = atomicOr(h.alloc_bm + bid, kAll);
+      if (ib == kAll) break;                       // nothing invalidated
+      if (ib == empty) { act -= 1; alc -= 1; fre += 1; break; }  // success
+      const unsigned long long rb = atomicAnd(h.alloc_bm + bid, ib);  // rollback
+      if (rb != kAll) act -= 1;  // a concurrent free saw a full block
+      if ((rb & ib) != empty) break;               // not empty again
+    }
+  }
+  for (int s = 0; (act | alc | fre) && s < h.bitmap_spins; ++s) {
+    if (act > 0 && bm_try_set(h, bm_active(h, t), bid)) --act;
+    if (act < 0 && bm_try_clear(h, bm_active(h, t), bid)) ++act;
+    if (alc < 0 && bm_try_clear(h, bm_alloc(h, t), bid)) ++alc;
+    if (fre > 0 && act == 0 && alc == 0 && bm_try_set(h, bm_free(), bid)) --fre;
+    if (act | alc | fre) __nanosleep(32);
+  }
+  if (act | alc | fre) set_error(h, SMMO_E_CONTENTION, bid);
+}
+
+// destroy(ptr) for a single object (Alg. 5.2 / 5.12).
+__device__ __forceinline__ void smmo_delete(const HeapView& h, uint32_t handle) {
+  const uint32_t bid = handle >> 6;
+  if (handle == kNull || bid >= h.num_blocks) {  // never touch memory for a bad handle
+    set_error(h, SMMO_E_BOUNDS, handle);
+    return;
+  }
+  const uint32_t t = type_of(h, handle);
+  if (t >= (uint32_t)h.num_classes) { set_error(h, SMMO_E_BAD_HANDLE, handle); return; }
+  dealloc_bits(h, bid, t, 1ull << (handle & 63));
+  // warp-aggregated free counter
+  const unsigned m = __activemask();
+  const unsigned same = __match_any_sync(m, t);
+  if ((threadIdx.x & 31) == __ffs(same) - 1) count(h, SMMO_CTR_FREE(t), __popc(same));
+}
+
+// ---------------------------------------------------------------- allocation
+// Leader part of allocation with request coalescing (Alg. 5.8): find an
+// active block of class c (with lookup retry, Sec. 5.3.2), else initialise
+// a free block (slow path, Alg. 5.13), then reserve up to n slots in it.
+// Returns the reserved slot bits (possibly fewer than n, possibly 0) and the
+// block in *bid; *bid = kNull signals that no free block exists.
+static __device__ __noinline__ unsigned long long leader_reserve(const HeapView& h, uint32_t c, int n,
+                                                          uint32_t seed, uint32_t* bid_out) {
+  const unsigned long long capmask = __ldg(&h.cls[c].capmask);
+  int bid = -1;
+  for (int r = 0; r < h.lookup_retries && bid < 0; ++r)
+    bid = bm_try_find_set(h, bm_active(h, c), seed + 104729u * (uint32_t)r);
+  if (bid < 0) {
+    bid = bm_clear_any(h, bm_free(), seed ^ 0x5bd1e995u);
+    if (bid < 0) { *bid_out = kNull; return 0; }
+    // initialize_block (Alg. 5.13): type first, fence, then open the slots
+    atomicExch(h.block_type + bid, c);
+    __threadfence();
+    atomicExch(h.alloc_bm + bid, ~capmask);
+    bm_set(h, bm_alloc(h, c), (uint32_t)bid);
+    bm_set(h, bm_active(h, c), (uint32_t)bid);
+    count(h, SMMO_CTR_SLOW, 1);
+  }
+  *bid_out = (uint32_t)bid;
+  // reserve_multiple(n): Alg. 5.9 extended to several slots
+  for (int s = 0; s < h.bitmap_spins; ++s) {
+    const unsigned long long cur = ld_cg(h.alloc_bm + bid);
+    unsigned long long freeb = ~cur;
+    if (freeb == 0) return 0;  // full or invalidated: retry from the start
+    // rotate the choice of slots a little to spread concurrent leaders
+    unsigned long long pick = 0;
+    for (int i = 0; i < n && freeb; ++i) {
+      const unsigned long long low = freeb & (0ull - freeb);
+      pick |= low;
+      freeb ^= low;
+    }
+    const unsigned long long before = atomicOr(h.alloc_bm + bid, pick);
+    const unsigned long long got = pick & ~before;
+    if (!got) continue;
+    const uint32_t t = atomicAdd(h.block_type + bid, 0u);
+    if ((before | pick) == kAll) bm_clear(h, bm_active(h, t), (uint32_t)bid);  // filled it
+    if (t != c) {  // block was re-initialised to another class: roll back
+      dealloc_bits(h, (uint32_t)bid, t, got);
+      return 0;
+    }
+    return got;
+  }
+  return 0;
+}
+
+// new(d_allocator) T: warp-aggregated allocation of one object of class c
+// per calling lane (Alg. 5.8).  Lanes that call it together (the active
+// mask) are served by one leader per round; lanes left without a slot retry
+// with a new leader.  Returns kNull (and records SMMO_E_DEVICE_OOM or
+// SMMO_E_CONTENTION) if the heap is exhausted or the budget runs out.
+__device__ __forceinline__ uint32_t smmo_new(const HeapView& h, uint32_t c) {
+  if (c >= (uint32_t)h.num_classes) { set_error(h, SMMO_E_INVALID_ARG, c); return kNull; }
+  const unsigned active = __activemask();
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp_uid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  uint32_t result = kNull;
+  int round = 0;
+  for (; round < h.alloc_retries; ++round) {
+    const unsigned need = __ballot_sync(active, result == kNull);
+    if (need == 0) break;
+    const int leader = __ffs(need) - 1;
+    unsigned long long got = 0;
+    uint32_t bid = 0;
+    if (lane == leader) {
+      got = leader_reserve(h, c, __popc(need), mix32(warp_uid * 0x27d4eb2fu + (uint32_t)round), &bid);
+      if (got) count(h, SMMO_CTR_ALLOC(c), __popcll(got));
+      if (round) count(h, SMMO_CTR_RETRY, 1);
+    }
+    got = __shfl_sync(active, got, leader);
+    bid = __shfl_sync(active, bid, leader);
+    if (bid == kNull) {  // no free block anywhere
+      if (lane == leader) set_error(h, SMMO_E_DEVICE_OOM, c);
+      break;
+    }
+    if (result == kNull) {
+      const int rank = __popc(need & ((1u << lane) - 1));
+      const int slot = nth_set_bit(got, rank);
+      if (slot >= 0) result = (bid << 6) | (uint32_t)slot;
+    }
+  }
+  if (round == h.alloc_retries && result == kNull) set_error(h, SMMO_E_CONTENTION, c);
+  return result;
+}
+
+// ---------------------------------------------------------------- do-all
+// Persistent grid-stride do-all over the enumerated blocks (Sec. 5.2.7):
+// the slots of one block are handled by consecutive threads (one warp per
+// 32 slots), thread t of a block's group handles slot t, and a slot runs the
+// method iff its bit is set in the snapshot taken at enumeration time.
+template <class M>
+__global__ void __launch_bounds__(256) do_all_kernel(HeapView h, uint32_t c,
+                                                     typename M::Args args) {
+  const uint32_t n = __ldcg(&h.st->rcount);
+  const uint32_t cap = __ldg(&h.cls[c].cap);
+  const uint32_t halves = cap > 32 ? 2u : 1u;
+  const uint32_t units = n * halves;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units; u += nwarps) {
+    const uint32_t i = halves == 2 ? (u >> 1) : u;
+    const uint32_t slot = (halves == 2 ? (u & 1) * 32 : 0) + lane;
+    const REntry e = h.R[i];
+    if ((e.bits >> slot) & 1) M::run(h, args, c, (e.block << 6) | slot);
+  }
+}
+
+#endif  // __CUDACC__
+}  // namespace smmo

@@ -1,0 +1,76 @@
+// wl_test.cu -- small methods used by the allocator and enumeration tests
+// and by the allocation microbenchmark (the thesis' Linux-scalability
+// experiment, Sec. 5.6.4: many threads allocate objects, then free them).
+#include "heap_internal.h"
+#include "smmo_core.cuh"
+
+using namespace smmo;
+
+namespace {
+
+// field[col] += value  (int32 column)
+struct AddI32 {
+  struct Args { uint32_t col; int32_t value; };
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
+    int32_t* f = field_ptr<int32_t>(h, __ldg(&h.cls[c].col_off[a.col]), self);
+    *f += a.value;
+  }
+};
+
+// Each visited object allocates `k` objects of class `target` and writes
+// `marker` into their int32 column `col` and its own value of column
+// `src_col` into column `col2` (so the test can check who allocated what).
+struct AllocK {
+  struct Args { uint32_t target; uint32_t k; uint32_t col; uint32_t col2; uint32_t src_col; int32_t marker; };
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
+    const int32_t mine = *field_ptr<int32_t>(h, __ldg(&h.cls[c].col_off[a.src_col]), self);
+    for (uint32_t i = 0; i < a.k; ++i) {
+      const uint32_t o = smmo_new(h, a.target);
+      if (o == kNull) return;
+      *field_ptr<int32_t>(h, __ldg(&h.cls[a.target].col_off[a.col]), o) = a.marker;
+      *field_ptr<int32_t>(h, __ldg(&h.cls[a.target].col_off[a.col2]), o) = mine;
+    }
+  }
+};
+
+// Deletes itself when (column col) % mod == rem.
+struct FreeSelfIf {
+  struct Args { uint32_t col; int32_t mod; int32_t rem; };
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
+    const int32_t v = *field_ptr<int32_t>(h, __ldg(&h.cls[c].col_off[a.col]), self);
+    const int32_t m = a.mod > 0 ? ((v % a.mod) + a.mod) % a.mod : 0;
+    if (a.mod <= 0 || m == a.rem) smmo_delete(h, self);
+  }
+};
+
+// Deletes the object referenced by HANDLE column `col` (an object of
+// another class) and clears the reference.
+struct FreeRef {
+  struct Args { uint32_t col; };
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
+    uint32_t* r = field_ptr<uint32_t>(h, __ldg(&h.cls[c].col_off[a.col]), self);
+    if (*r != kNull) { smmo_delete(h, *r); *r = kNull; }
+  }
+};
+
+// Replaces itself by a new object of class `target` carrying column col.
+struct Replace {
+  struct Args { uint32_t target; uint32_t col; uint32_t tcol; };
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
+    const int32_t v = *field_ptr<int32_t>(h, __ldg(&h.cls[c].col_off[a.col]), self);
+    const uint32_t o = smmo_new(h, a.target);
+    if (o != kNull) *field_ptr<int32_t>(h, __ldg(&h.cls[a.target].col_off[a.tcol]), o) = v;
+    smmo_delete(h, self);
+  }
+};
+
+}  // namespace
+
+const smmo::MethodEntry g_methods_test[] = {
+    SMMO_METHOD("test.add_i32", AddI32),
+    SMMO_METHOD("test.alloc_k", AllocK),
+    SMMO_METHOD("test.free_self_if", FreeSelfIf),
+    SMMO_METHOD("test.free_ref", FreeRef),
+    SMMO_METHOD("test.replace", Replace),
+};
+const int g_methods_test_n = sizeof(g_methods_test) / sizeof(g_methods_test[0]);

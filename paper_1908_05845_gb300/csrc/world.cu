@@ -1,0 +1,652 @@
+// world.cu -- the cellular SMMO workloads of the thesis' Ch. 7 on one heap:
+// object-based Game of Life (Sec. 7.9) and Wa-Tor (Sec. 7.7), for one or
+// many independent instances ("batched heap": all instances' objects share
+// the heap and every step runs one parallel_do per class over all of them).
+//
+// Classes: Cell {occ: handle of the agent on the cell, req: u64 request
+// word}; WAgent (abstract) {cell, target} with Fish {age} and Shark {age,
+// energy}; LAgent (abstract) {cell, action} with Alive {is_new} and
+// Candidate {}.  Cells are created once by bulk_new in global cell order and
+// addressed densely; agents hold their global cell index.
+//
+// Conflict resolution and randomness are keyed by (seed, step, local cell,
+// tag, instance) and by lowest cell index, so a run is deterministic
+// whatever the enumeration order or slot placement.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+#include "grid_common.cuh"
+#include "heap_internal.h"
+#include "smmo.h"
+#include "smmo_core.cuh"
+
+using namespace smmo;
+
+namespace {
+
+struct WorldArgs {
+  const Inst* winst;
+  const Inst* linst;
+  uint32_t nwinst, nlinst;
+  CellRef cells;
+  uint32_t occ_off, req_off;
+  uint32_t fish, shark, alive, cand;
+  uint32_t f_cell, f_target, f_age;
+  uint32_t s_cell, s_target, s_age, s_energy;
+  uint32_t a_cell, a_action, a_isnew;
+  uint32_t c_cell, c_action;
+  uint64_t seed;
+  uint32_t t, key_hi;
+  int32_t fish_breed, shark_breed, starve, breed_strict;
+  int8_t* out_kind;
+  int16_t* out_age;
+  int16_t* out_energy;
+  uint8_t* out_state;
+  uint32_t* out_count;
+  unsigned long long* errors;
+};
+
+template <class T>
+__device__ __forceinline__ T* fld(const HeapView& h, uint32_t self, uint32_t off) {
+  return field_ptr<T>(h, off, self);
+}
+
+// ================================================================ Wa-Tor
+// One phase = prepare (choose a neighbour, post a request) + update (move if
+// granted).  The thesis' Cell::prepare / Cell::decide passes are folded into
+// the request word of the target cell: an agent on cell s posts
+// key = ((0xFFFFFFFF - phase) << 32) | s with atomicMin; the smallest key of
+// the current phase wins (lowest source cell), keys of older phases are
+// larger and never win, so no pass over all cells is needed to reset them.
+__device__ __forceinline__ unsigned long long req_key(uint32_t key_hi, uint32_t src) {
+  return ((unsigned long long)key_hi << 32) | src;
+}
+
+struct FishPrepare {
+  using Args = WorldArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+    const uint32_t g = *fld<int32_t>(h, self, a.f_cell);
+    int16_t* agep = fld<int16_t>(h, self, a.f_age);
+    *agep = (int16_t)(*agep + 1);
+    const Inst* in = find_inst(a.winst, a.nwinst, g);
+    const uint32_t lc = g - in->cell_base, W = in->W, H = in->H;
+    const uint32_t x = lc % W, y = lc / W;
+    uint32_t cand[4];
+    int nc = 0;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const uint32_t n = in->cell_base + torus_nb4(x, y, W, H, d);
+      if (*a.cells.col<uint32_t>(n, a.occ_off) == kNull) cand[nc++] = n;
+    }
+    uint32_t tgt = g;
+    if (nc) {
+      const uint32_t r = philox_draw(a.seed, TAG_FISH, a.t, lc, in->id);
+      tgt = cand[r % (uint32_t)nc];
+      atomicMin(a.cells.col<unsigned long long>(tgt, a.req_off), req_key(a.key_hi, g));
+    }
+    *fld<int32_t>(h, self, a.f_target) = (int32_t)tgt;
+  }
+};
+
+struct FishUpdate {
+  using Args = WorldArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+    int32_t* cellp = fld<int32_t>(h, self, a.f_cell);
+    const uint32_t g = *cellp;
+    const uint32_t tgt = *fld<int32_t>(h, self, a.f_target);
+    if (tgt == g) return;
+    if (*a.cells.col<unsigned long long>(tgt, a.req_off) != req_key(a.key_hi, g)) return;
+    *a.cells.col<uint32_t>(tgt, a.occ_off) = self;
+    *cellp = (int32_t)tgt;
+    int16_t* agep = fld<int16_t>(h, self, a.f_age);
+    const int age = *agep;
+    const bool ripe = a.breed_strict ? age > a.fish_breed : age >= a.fish_breed;
+    uint32_t child = kNull;
+    if (ripe) {
+      *agep = 0;
+      child = smmo_new(h, a.fish);
+      if (child != kNull) {
+        *fld<int32_t>(h, child, a.f_cell) = (int32_t)g;
+        *fld<int32_t>(h, child, a.f_target) = (int32_t)g;
+        *fld<int16_t>(h, child, a.f_age) = 0;
+      }
+    }
+    *a.cells.col<uint32_t>(g, a.occ_off) = child;
+  }
+};
+
+struct SharkPrepare {
+  using Args = WorldArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+    const uint32_t g = *fld<int32_t>(h, self, a.s_cell);
+    int16_t* agep = fld<int16_t>(h, self, a.s_age);
+    int16_t* enp = fld<int16_t>(h, self, a.s_energy);
+    *agep = (int16_t)(*agep + 1);
+    const int16_t en = (int16_t)(*enp - 1);
+    *enp = en;
+    uint32_t tgt = g;
+    if (en != 0) {
+      const Inst* in = find_inst(a.winst, a.nwinst, g);
+      const uint32_t lc = g - in->cell_base, W = in->W, H = in->H;
+      const uint32_t x = lc % W, y = lc / W;
+      uint32_t fishc[4], emptyc[4];
+      int nf = 0, ne = 0;
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        const uint32_t n = in->cell_base + torus_nb4(x, y, W, H, d);
+        const uint32_t o = *a.cells.col<uint32_t>(n, a.occ_off);
+        if (o == kNull) emptyc[ne++] = n;
+        else if (type_of(h, o) == a.fish) fishc[nf++] = n;
+      }
+      if (nf || ne) {
+        const uint32_t r = philox_draw(a.seed, TAG_SHARK, a.t, lc, in->id);
+        tgt = nf ? fishc[r % (uint32_t)nf] : emptyc[r % (uint32_t)ne];
+        atomicMin(a.cells.col<unsigned long long>(tgt, a.req_off), req_key(a.key_hi, g));
+      }
+    }
+    *fld<int32_t>(h, self, a.s_target) = (int32_t)tgt;
+  }
+};
+
+struct SharkUpdate {
+  using Args = WorldArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+    int32_t* cellp = fld<int32_t>(h, self, a.s_cell);
+    const uint32_t g = *cellp;
+    int16_t* enp = fld<int16_t>(h, self, a.s_energy);
+    if (*enp == 0) {  // starved: leave the cell and delete itself (last statement)
+      *a.cells.col<uint32_t>(g, a.occ_off) = kNull;
+      smmo_delete(h, self);
+      return;
+    }
+    const uint32_t tgt = *fld<int32_t>(h, self, a.s_target);
+    if (tgt == g) return;
+    if (*a.cells.col<unsigned long long>(tgt, a.req_off) != req_key(a.key_hi, g)) return;
+    uint32_t* tocc = a.cells.col<uint32_t>(tgt, a.occ_off);
+    const uint32_t prey = *tocc;
+    if (prey != kNull) {  // eat the fish (deleting an object of another class)
+      smmo_delete(h, prey);
+      *enp = (int16_t)a.starve;
+    }
+    *tocc = self;
+    *cellp = (int32_t)tgt;
+    int16_t* agep = fld<int16_t>(h, self, a.s_age);
+    const int age = *agep;
+    const bool ripe = a.breed_strict ? age > a.shark_breed : age >= a.shark_breed;
+    uint32_t child = kNull;
+    if (ripe) {
+      *agep = 0;
+      child = smmo_new(h, a.shark);
+      if (child != kNull) {
+        *fld<int32_t>(h, child, a.s_cell) = (int32_t)g;
+        *fld<int32_t>(h, child, a.s_target) = (int32_t)g;
+        *fld<int16_t>(h, child, a.s_age) = 0;
+        *fld<int16_t>(h, child, a.s_energy) = (int16_t)a.starve;
+      }
+    }
+    *a.cells.col<uint32_t>(g, a.occ_off) = child;
+  }
+};
+
+// ================================================================ Life
+enum : uint8_t { ACT_KEEP = 0, ACT_BORN = 1, ACT_DELETE = 2, ACT_DIE = 3 };
+
+__device__ __forceinline__ uint32_t torus8(uint32_t x, uint32_t y, int dx, int dy, uint32_t W,
+                                           uint32_t H) {
+  const uint32_t nx = dx < 0 ? (x == 0 ? W - 1 : x - 1) : (dx > 0 ? (x + 1 == W ? 0 : x + 1) : x);
+  const uint32_t ny = dy < 0 ? (y == 0 ? H - 1 : y - 1) : (dy > 0 ? (y + 1 == H ? 0 : y + 1) : y);
+  return ny * W + nx;
+}
+
+__device__ __forceinline__ int alive_neighbours(const HeapView& h, const WorldArgs& a,
+                                                const Inst* in, uint32_t x, uint32_t y) {
+  int n = 0;
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      if (!dx && !dy) continue;
+      const uint32_t o = *a.cells.col<uint32_t>(in->cell_base + torus8(x, y, dx, dy, in->W, in->H), a.occ_off);
+      if (o != kNull && type_of(h, o) == a.alive) ++n;
+    }
+  return n;
+}
+
+struct CandPrepare {
+  using Args = WorldArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+    const uint32_t g = *fld<int32_t>(h, self, a.c_cell);
+    const Inst* in = find_inst(a.linst, a.nlinst, g);
+    const uint32_t lc = g - in->cell_base;
+    const int n = alive_neighbours(h, a, in, lc % in->W, lc / in->W);
+    *fld<uint8_t>(h, self, a.c_action) = n == 3 ? ACT_BORN : (n == 0 ? ACT_DELETE : ACT_KEEP);
+  }
+};
+
+struct AlivePrepare {
+  using Args = WorldArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+    const uint32_t g = *fld<int32_t>(h, self, a.a_cell);
+    *fld<uint8_t>(h, self, a.a_isnew) = 0;
+    const Inst* in = find_inst(a.linst, a.nlinst, g);
+    const uint32_t lc = g - in->cell_base;
+    const int n = alive_neighbours(h, a, in, lc % in->W, lc / in->W);
+    *fld<uint8_t>(h, self, a.a_action) = (n == 2 || n == 3) ? ACT_KEEP : ACT_DIE;
+  }
+};
+
+struct CandUpdate {
+  using Args = WorldArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+    const uint8_t act = *fld<uint8_t>(h, self, a.c_action);
+    if (act == ACT_KEEP) return;
+    const uint32_t g = *fld<int32_t>(h, self, a.c_cell);
+    uint32_t repl = kNull;
+    if (act == ACT_BORN) {
+      repl = smmo_new(h, a.alive);
+      if (repl != kNull) {
+        *fld<int32_t>(h, repl, a.a_cell) = (int32_t)g;
+        *fld<uint8_t>(h, repl, a.a_action) = ACT_KEEP;
+        *fld<uint8_t>(h, repl, a.a_isnew) = 1;
+      }
+    }
+    *a.cells.col<uint32_t>(g, a.occ_off) = repl;
+    smmo_delete(h, self);
+  }
+};
+
+struct AliveUpdate {
+  using Args = WorldArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+    const uint32_t g = *fld<int32_t>(h, self, a.a_cell);
+    if (*fld<uint8_t>(h, self, a.a_isnew)) {
+      // create Candidates on empty surrounding cells; the creator of an empty
+      // cell e is the first new Alive of e's neighbourhood in scan order
+      const Inst* in = find_inst(a.linst, a.nlinst, g);
+      const uint32_t lc = g - in->cell_base, W = in->W, H = in->H;
+      const uint32_t x = lc % W, y = lc / W;
+      for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy) {
+          const uint32_t el = torus8(x, y, dx, dy, W, H);
+          const uint32_t e = in->cell_base + el;
+          uint32_t* eocc = a.cells.col<uint32_t>(e, a.occ_off);
+          if (*(volatile uint32_t*)eocc != kNull) continue;
+          const uint32_t ex = el % W, ey = el / W;
+          uint32_t first = kNull;
+          for (int ddx = -1; ddx <= 1 && first == kNull; ++ddx)
+            for (int ddy = -1; ddy <= 1; ++ddy) {
+              const uint32_t o = *(volatile uint32_t*)a.cells.col<uint32_t>(
+                  in->cell_base + torus8(ex, ey, ddx, ddy, W, H), a.occ_off);
+              if (o != kNull && type_of(h, o) == a.alive && *fld<uint8_t>(h, o, a.a_isnew)) {
+                first = o;
+                break;
+              }
+            }
+          if (first == self) {
+            const uint32_t cnd = smmo_new(h, a.cand);
+            if (cnd != kNull) {
+              *fld<int32_t>(h, cnd, a.c_cell) = (int32_t)e;
+              *fld<uint8_t>(h, cnd, a.c_action) = ACT_KEEP;
+            }
+            *eocc = cnd;
+          }
+        }
+    } else if (*fld<uint8_t>(h, self, a.a_action) == ACT_DIE) {
+      const uint32_t cnd = smmo_new(h, a.cand);
+      if (cnd != kNull) {
+        *fld<int32_t>(h, cnd, a.c_cell) = (int32_t)g;
+        *fld<uint8_t>(h, cnd, a.c_action) = ACT_KEEP;
+      }
+      *a.cells.col<uint32_t>(g, a.occ_off) = cnd;
+      smmo_delete(h, self);
+    }
+  }
+};
+
+// ================================================================ export
+// Writes every agent into dense per-cell arrays (kind/age/energy/state) and
+// counts agents per cell; an agent whose cell does not point back at it is
+// counted as an error.
+struct Export {
+  using Args = WorldArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
+    uint32_t off = c == a.fish ? a.f_cell : c == a.shark ? a.s_cell : c == a.alive ? a.a_cell : a.c_cell;
+    const uint32_t g = *fld<int32_t>(h, self, off);
+    atomicAdd(a.out_count + g, 1u);
+    if (*a.cells.col<uint32_t>(g, a.occ_off) != self) atomicAdd(a.errors, 1ull);
+    if (c == a.fish) {
+      a.out_kind[g] = 1;
+      a.out_age[g] = *fld<int16_t>(h, self, a.f_age);
+      a.out_energy[g] = 0;
+    } else if (c == a.shark) {
+      a.out_kind[g] = 2;
+      a.out_age[g] = *fld<int16_t>(h, self, a.s_age);
+      a.out_energy[g] = *fld<int16_t>(h, self, a.s_energy);
+    } else if (c == a.alive) {
+      a.out_kind[g] = 1;
+      a.out_state[g] = *fld<uint8_t>(h, self, a.a_isnew);
+    } else {
+      a.out_kind[g] = 2;
+      a.out_state[g] = 0;
+    }
+  }
+};
+
+// Initial back-references: every agent writes its handle into its cell.
+struct Link {
+  using Args = WorldArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
+    uint32_t off = c == a.fish ? a.f_cell : c == a.shark ? a.s_cell : c == a.alive ? a.a_cell : a.c_cell;
+    *a.cells.col<uint32_t>(*fld<int32_t>(h, self, off), a.occ_off) = self;
+  }
+};
+
+// Occupied cells whose agent does not live on them count as errors.
+struct CheckCells {
+  using Args = WorldArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+    const uint32_t g = ((self >> 6) - a.cells.b0) * 64 + (self & 63);
+    const uint32_t o = *a.cells.col<uint32_t>(g, a.occ_off);
+    if (o == kNull) return;
+    const uint32_t t = type_of(h, o);
+    uint32_t off = t == a.fish ? a.f_cell : t == a.shark ? a.s_cell : t == a.alive ? a.a_cell : a.c_cell;
+    if (t >= (uint32_t)h.num_classes || (uint32_t)*fld<int32_t>(h, o, off) != g) atomicAdd(a.errors, 1ull);
+  }
+};
+
+}  // namespace
+
+const smmo::MethodEntry g_methods_wator[] = {
+    SMMO_METHOD("wator.fish_prepare", FishPrepare), SMMO_METHOD("wator.fish_update", FishUpdate),
+    SMMO_METHOD("wator.shark_prepare", SharkPrepare), SMMO_METHOD("wator.shark_update", SharkUpdate),
+    SMMO_METHOD("world.export", Export), SMMO_METHOD("world.link", Link),
+    SMMO_METHOD("world.check_cells", CheckCells)};
+const int g_methods_wator_n = sizeof(g_methods_wator) / sizeof(g_methods_wator[0]);
+
+const smmo::MethodEntry g_methods_gol[] = {
+    SMMO_METHOD("gol.candidate_prepare", CandPrepare), SMMO_METHOD("gol.alive_prepare", AlivePrepare),
+    SMMO_METHOD("gol.candidate_update", CandUpdate), SMMO_METHOD("gol.alive_update", AliveUpdate)};
+const int g_methods_gol_n = sizeof(g_methods_gol) / sizeof(g_methods_gol[0]);
+
+// ================================================================ world API
+struct smmo_world {
+  smmo_heap* heap = nullptr;
+  int n_inst = 0;
+  std::vector<int> kind;
+  std::vector<uint32_t> W, H, base;
+  uint64_t total_cells = 0;
+  int cls_cell = -1, cls_wagent = -1, cls_fish = -1, cls_shark = -1;
+  int cls_lagent = -1, cls_alive = -1, cls_cand = -1;
+  Inst* d_winst = nullptr;
+  Inst* d_linst = nullptr;
+  uint32_t nw = 0, nl = 0;
+  uint32_t t = 0;  // steps done
+  WorldArgs args{};
+  smmo_wator_params p{};
+};
+
+namespace {
+int pdo(smmo_world* w, int cls, method_launch_fn fn, const WorldArgs& a, cudaStream_t s) {
+  std::vector<int> cl;
+  concrete_subtree(w->heap, cls, &cl);
+  for (int k : cl) {
+    int st = enumerate(w->heap, k, s);
+    if (st) return st;
+    st = fn(w->heap, k, &a, s);
+    if (st) return st;
+  }
+  return SMMO_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32_t* W,
+                      const uint32_t* H, uint64_t seed, const smmo_wator_params* params,
+                      const int8_t* init_kind, const int16_t* init_age, const int16_t* init_energy,
+                      const uint8_t* init_state, void* stream, smmo_world** out) {
+  if (!heap || n_inst < 1 || !kind || !W || !H || !init_kind || !out) return SMMO_E_INVALID_ARG;
+  if (!heap->classes.empty() || heap->frozen) return SMMO_E_FROZEN;
+  cudaStream_t s = (cudaStream_t)stream;
+  smmo_world* w = new smmo_world();
+  w->heap = heap;
+  w->n_inst = n_inst;
+  w->p.fish_breed = 4; w->p.shark_breed = 12; w->p.starve = 3; w->p.breed_strict = 0;
+  if (params) w->p = *params;
+  std::vector<Inst> wi, li;
+  for (int i = 0; i < n_inst; ++i) {
+    if ((kind[i] != SMMO_WORLD_LIFE && kind[i] != SMMO_WORLD_WATOR) || W[i] < 3 || H[i] < 3) {
+      delete w;
+      return SMMO_E_INVALID_ARG;
+    }
+    w->kind.push_back(kind[i]);
+    w->W.push_back(W[i]);
+    w->H.push_back(H[i]);
+    w->base.push_back((uint32_t)w->total_cells);
+    Inst in{(uint32_t)w->total_cells, W[i], H[i], (uint32_t)i};
+    (kind[i] == SMMO_WORLD_WATOR ? wi : li).push_back(in);
+    w->total_cells += (uint64_t)W[i] * H[i];
+  }
+  if (w->total_cells >= (1ull << 31)) { delete w; return SMMO_E_INVALID_ARG; }
+  // classes
+  smmo_field_desc cell_f[2] = {{"occ", SMMO_HANDLE, 1, -1}, {"req", SMMO_U64, 1, -1}};
+  int st = smmo_class_register(heap, "Cell", cell_f, 2, -1, 0, &w->cls_cell);
+  if (!st && !wi.empty()) {
+    smmo_field_desc ag[2] = {{"cell", SMMO_I32, 1, -1}, {"target", SMMO_I32, 1, -1}};
+    smmo_field_desc fi[1] = {{"age", SMMO_I16, 1, -1}};
+    smmo_field_desc sh[2] = {{"age", SMMO_I16, 1, -1}, {"energy", SMMO_I16, 1, -1}};
+    st = smmo_class_register(heap, "WAgent", ag, 2, -1, 1, &w->cls_wagent);
+    if (!st) st = smmo_class_register(heap, "Fish", fi, 1, w->cls_wagent, 0, &w->cls_fish);
+    if (!st) st = smmo_class_register(heap, "Shark", sh, 2, w->cls_wagent, 0, &w->cls_shark);
+  }
+  if (!st && !li.empty()) {
+    smmo_field_desc ag[2] = {{"cell", SMMO_I32, 1, -1}, {"action", SMMO_U8, 1, -1}};
+    smmo_field_desc al[1] = {{"is_new", SMMO_U8, 1, -1}};
+    st = smmo_class_register(heap, "LAgent", ag, 2, -1, 1, &w->cls_lagent);
+    if (!st) st = smmo_class_register(heap, "Alive", al, 1, w->cls_lagent, 0, &w->cls_alive);
+    if (!st) st = smmo_class_register(heap, "Candidate", nullptr, 0, w->cls_lagent, 0, &w->cls_cand);
+  }
+  if (heap->cfg.block_data_bytes == 0) heap->cfg.block_data_bytes = 768;  // every class gets N_T = 64
+  if (!st) st = freeze(heap, s);
+  if (!st && heap->classes[w->cls_cell].layout.cap != 64) st = SMMO_E_UNSUPPORTED;
+  if (st) { delete w; return st; }
+  // instance tables (device memory inside the heap's scratch tail is not
+  // reserved for this, so use a dedicated allocation owned by the world)
+  w->nw = (uint32_t)wi.size();
+  w->nl = (uint32_t)li.size();
+  cudaError_t e = cudaSuccess;
+  if (w->nw) e = cudaMalloc(&w->d_winst, sizeof(Inst) * w->nw);
+  if (e == cudaSuccess && w->nl) e = cudaMalloc(&w->d_linst, sizeof(Inst) * w->nl);
+  if (e == cudaSuccess && w->nw) e = cudaMemcpyAsync(w->d_winst, wi.data(), sizeof(Inst) * w->nw, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && w->nl) e = cudaMemcpyAsync(w->d_linst, li.data(), sizeof(Inst) * w->nl, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) { smmo_world_destroy(w); return cuda_status(e); }
+  // cells: occ = null, req = all ones
+  const uint64_t N = w->total_cells;
+  uint32_t* occ0 = nullptr;
+  unsigned long long* req0 = nullptr;
+  e = cudaMallocAsync(&occ0, N * 4, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&req0, N * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(occ0, 0xFF, N * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(req0, 0xFF, N * 8, s);
+  if (e != cudaSuccess) { smmo_world_destroy(w); return cuda_status(e); }
+  const void* csrc[2] = {occ0, req0};
+  int64_t first = -1;
+  st = smmo_bulk_new(heap, w->cls_cell, (int64_t)N, csrc, nullptr, &first, stream);
+  cudaFreeAsync(occ0, s);
+  cudaFreeAsync(req0, s);
+  if (!st && first < 0) st = SMMO_E_OOM;  // cells must be contiguous
+  if (st) { smmo_world_destroy(w); return st; }
+  // argument block
+  WorldArgs& a = w->args;
+  memset(&a, 0, sizeof(a));
+  a.winst = w->d_winst; a.linst = w->d_linst; a.nwinst = w->nw; a.nlinst = w->nl;
+  a.cells.data = heap->view.data;
+  a.cells.block_bytes = heap->view.block_bytes;
+  a.cells.b0 = (uint32_t)first;
+  const ClassLayout& CL = heap->classes[w->cls_cell].layout;
+  a.occ_off = CL.col_off[0];
+  a.req_off = CL.col_off[1];
+  a.fish = a.shark = a.alive = a.cand = kNull;
+  if (w->nw) {
+    const ClassLayout& F = heap->classes[w->cls_fish].layout;
+    const ClassLayout& S = heap->classes[w->cls_shark].layout;
+    a.fish = w->cls_fish; a.shark = w->cls_shark;
+    a.f_cell = F.col_off[0]; a.f_target = F.col_off[1]; a.f_age = F.col_off[2];
+    a.s_cell = S.col_off[0]; a.s_target = S.col_off[1]; a.s_age = S.col_off[2]; a.s_energy = S.col_off[3];
+  }
+  if (w->nl) {
+    const ClassLayout& A = heap->classes[w->cls_alive].layout;
+    const ClassLayout& C = heap->classes[w->cls_cand].layout;
+    a.alive = w->cls_alive; a.cand = w->cls_cand;
+    a.a_cell = A.col_off[0]; a.a_action = A.col_off[1]; a.a_isnew = A.col_off[2];
+    a.c_cell = C.col_off[0]; a.c_action = C.col_off[1];
+  }
+  a.seed = seed;
+  a.fish_breed = w->p.fish_breed; a.shark_breed = w->p.shark_breed; a.starve = w->p.starve;
+  a.breed_strict = w->p.breed_strict;
+  // agents: gather the per-kind cell lists on the host (setup only)
+  std::vector<int8_t> hk(N);
+  std::vector<int16_t> ha(N, 0), he(N, 0);
+  std::vector<uint8_t> hs(N, 0);
+  e = cudaMemcpyAsync(hk.data(), init_kind, N, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && init_age) e = cudaMemcpyAsync(ha.data(), init_age, N * 2, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && init_energy) e = cudaMemcpyAsync(he.data(), init_energy, N * 2, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && init_state) e = cudaMemcpyAsync(hs.data(), init_state, N, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { smmo_world_destroy(w); return cuda_status(e); }
+  struct Pop { std::vector<int32_t> cell, target; std::vector<int16_t> age, energy; std::vector<uint8_t> act, isnew; };
+  Pop fish, shark, alive, cand;
+  for (int i = 0; i < n_inst; ++i) {
+    const uint64_t b = w->base[i], n = (uint64_t)w->W[i] * w->H[i];
+    for (uint64_t g = b; g < b + n; ++g) {
+      const int k = hk[g];
+      if (k == 0) continue;
+      if (w->kind[i] == SMMO_WORLD_WATOR) {
+        Pop& P = k == 1 ? fish : shark;
+        P.cell.push_back((int32_t)g); P.target.push_back((int32_t)g);
+        P.age.push_back(ha[g]); P.energy.push_back(he[g]);
+      } else {
+        Pop& P = k == 1 ? alive : cand;
+        P.cell.push_back((int32_t)g); P.act.push_back(0); P.isnew.push_back(k == 1 ? hs[g] : 0);
+      }
+    }
+  }
+  auto upload = [&](int cls, std::vector<const void*> cols_h, std::vector<size_t> esz, size_t n) -> int {
+    if (n == 0) return SMMO_OK;
+    std::vector<void*> d(cols_h.size(), nullptr);
+    cudaError_t ee = cudaSuccess;
+    for (size_t k = 0; k < cols_h.size() && ee == cudaSuccess; ++k) {
+      ee = cudaMallocAsync(&d[k], n * esz[k], s);
+      if (ee == cudaSuccess) ee = cudaMemcpyAsync(d[k], cols_h[k], n * esz[k], cudaMemcpyHostToDevice, s);
+    }
+    int r = ee == cudaSuccess ? smmo_bulk_new(heap, cls, (int64_t)n, (const void* const*)d.data(), nullptr, nullptr, stream)
+                              : cuda_status(ee);
+    for (void* p : d) if (p) cudaFreeAsync(p, s);
+    return r;
+  };
+  if (!st && w->nw) {
+    st = upload(w->cls_fish, {fish.cell.data(), fish.target.data(), fish.age.data()}, {4, 4, 2}, fish.cell.size());
+    if (!st) st = upload(w->cls_shark, {shark.cell.data(), shark.target.data(), shark.age.data(), shark.energy.data()},
+                         {4, 4, 2, 2}, shark.cell.size());
+  }
+  if (!st && w->nl) {
+    st = upload(w->cls_alive, {alive.cell.data(), alive.act.data(), alive.isnew.data()}, {4, 1, 1}, alive.cell.size());
+    if (!st) st = upload(w->cls_cand, {cand.cell.data(), cand.act.data()}, {4, 1}, cand.cell.size());
+  }
+  if (!st && w->nw) st = pdo(w, w->cls_wagent, &launch_do_all<Link>, a, s);
+  if (!st && w->nl) st = pdo(w, w->cls_lagent, &launch_do_all<Link>, a, s);
+  if (!st) { e = cudaStreamSynchronize(s); if (e != cudaSuccess) st = cuda_status(e); }
+  if (st) { smmo_world_destroy(w); return st; }
+  *out = w;
+  return SMMO_OK;
+}
+
+int smmo_world_step(smmo_world* w, int nsteps, void* stream) {
+  if (!w || nsteps < 0) return SMMO_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  WorldArgs a = w->args;
+  for (int k = 0; k < nsteps; ++k) {
+    const uint32_t t = ++w->t;
+    a.t = t;
+    int st = SMMO_OK;
+    if (w->nl) {  // one Life generation (Sec. 7.9, four do-alls)
+      st = pdo(w, w->cls_cand, &launch_do_all<CandPrepare>, a, s);
+      if (!st) st = pdo(w, w->cls_alive, &launch_do_all<AlivePrepare>, a, s);
+      if (!st) st = pdo(w, w->cls_cand, &launch_do_all<CandUpdate>, a, s);
+      if (!st) st = pdo(w, w->cls_alive, &launch_do_all<AliveUpdate>, a, s);
+    }
+    if (!st && w->nw) {  // one Wa-Tor iteration (Sec. 7.7): fish phase, shark phase
+      a.key_hi = 0xFFFFFFFFu - 2u * t;
+      st = pdo(w, w->cls_fish, &launch_do_all<FishPrepare>, a, s);
+      if (!st) st = pdo(w, w->cls_fish, &launch_do_all<FishUpdate>, a, s);
+      a.key_hi = 0xFFFFFFFFu - (2u * t + 1u);
+      if (!st) st = pdo(w, w->cls_shark, &launch_do_all<SharkPrepare>, a, s);
+      if (!st) st = pdo(w, w->cls_shark, &launch_do_all<SharkUpdate>, a, s);
+    }
+    if (st) return st;
+  }
+  return SMMO_OK;
+}
+
+int smmo_world_export(smmo_world* w, int8_t* kind, int16_t* age, int16_t* energy, uint8_t* state,
+                      int64_t* errors, void* stream) {
+  if (!w || !kind || !age || !energy || !state) return SMMO_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint64_t N = w->total_cells;
+  WorldArgs a = w->args;
+  uint32_t* cnt = nullptr;
+  unsigned long long* err = nullptr;
+  cudaError_t e = cudaMallocAsync(&cnt, N * 4, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&err, 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, N * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(kind, 0, N, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(age, 0, N * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(energy, 0, N * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(state, 0, N, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  a.out_kind = kind; a.out_age = age; a.out_energy = energy; a.out_state = state;
+  a.out_count = cnt; a.errors = err;
+  int st = SMMO_OK;
+  if (w->nw) st = pdo(w, w->cls_wagent, &launch_do_all<Export>, a, s);
+  if (!st && w->nl) st = pdo(w, w->cls_lagent, &launch_do_all<Export>, a, s);
+  if (!st) st = pdo(w, w->cls_cell, &launch_do_all<CheckCells>, a, s);
+  // cells holding two agents
+  std::vector<uint32_t> hc(N);
+  unsigned long long herr = 0;
+  if (!st) {
+    e = cudaMemcpyAsync(hc.data(), cnt, N * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e);
+  }
+  cudaFreeAsync(cnt, s);
+  cudaFreeAsync(err, s);
+  if (st) return st;
+  for (uint64_t g = 0; g < N; ++g) if (hc[g] > 1) herr += hc[g] - 1;
+  if (errors) *errors = (int64_t)herr;
+  return SMMO_OK;
+}
+
+int smmo_world_info(smmo_world* w, int64_t* total_cells, int* class_ids, uint32_t* steps_done) {
+  if (!w) return SMMO_E_INVALID_ARG;
+  if (total_cells) *total_cells = (int64_t)w->total_cells;
+  if (class_ids) {
+    const int ids[7] = {w->cls_cell, w->cls_wagent, w->cls_fish, w->cls_shark, w->cls_lagent, w->cls_alive, w->cls_cand};
+    memcpy(class_ids, ids, sizeof(ids));
+  }
+  if (steps_done) *steps_done = w->t;
+  return SMMO_OK;
+}
+
+int smmo_world_destroy(smmo_world* w) {
+  if (!w) return SMMO_E_INVALID_ARG;
+  if (w->d_winst) cudaFree(w->d_winst);
+  if (w->d_linst) cudaFree(w->d_linst);
+  delete w;
+  return SMMO_OK;
+}
+
+}  // extern "C"

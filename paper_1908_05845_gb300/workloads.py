@@ -1,0 +1,136 @@
+"""Python side of the cellular workloads (smmo_world_* in include/smmo.h).
+
+Argument marshalling only; the simulation runs in libsmmo.so.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import smmo
+
+LIFE, WATOR = 0, 1
+
+
+class WatorParams(ctypes.Structure):
+    _fields_ = [("fish_breed", ctypes.c_int), ("shark_breed", ctypes.c_int),
+                ("starve", ctypes.c_int), ("breed_strict", ctypes.c_int)]
+
+
+def heap_bytes_for(total_cells: int, agent_fill: float = 1.0) -> int:
+    """Heap buffer size: the dense Cell blocks plus room for agents on up to
+    `agent_fill` of the cells at 50% block fill, plus metadata slack."""
+    blocks = total_cells / 64.0
+    return int((blocks * (1.0 + 2.0 * agent_fill) + 4096) * 800) + (32 << 20)
+
+
+class World:
+    """Independent Life / Wa-Tor instances sharing one SMMO heap."""
+
+    def __init__(self, kinds, widths, heights, seed: int, init_kind, init_age=None,
+                 init_energy=None, init_state=None, params: WatorParams | None = None,
+                 heap_bytes: int | None = None, config: smmo.HeapConfig | None = None,
+                 stream=None):
+        n = len(kinds)
+        self.kinds = [int(k) for k in kinds]
+        self.W = [int(w) for w in widths]
+        self.H = [int(h) for h in heights]
+        self.sizes = [w * h for w, h in zip(self.W, self.H)]
+        self.total = int(sum(self.sizes))
+        self.stream = stream
+        dev = torch.device("cuda")
+
+        def dt(a, dtype):
+            if a is None:
+                return None
+            return torch.as_tensor(np.ascontiguousarray(a)).to(dev, dtype).contiguous()
+
+        k = dt(init_kind, torch.int8)
+        a = dt(init_age, torch.int16)
+        e = dt(init_energy, torch.int16)
+        s = dt(init_state, torch.uint8)
+        self.heap = smmo.Heap(heap_bytes or heap_bytes_for(self.total), config, stream=stream)
+        self._w = ctypes.c_void_p()
+        ka = (ctypes.c_int * n)(*self.kinds)
+        wa = (ctypes.c_uint32 * n)(*self.W)
+        ha = (ctypes.c_uint32 * n)(*self.H)
+        p = ctypes.byref(params) if params is not None else None
+
+        def ptr(t):
+            return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+        smmo.check(smmo.lib().smmo_world_create(
+            self.heap.handle, n, ka, wa, ha, ctypes.c_uint64(seed), p, ptr(k), ptr(a), ptr(e),
+            ptr(s), smmo._stream(stream), ctypes.byref(self._w)), "world_create")
+        ids = (ctypes.c_int * 7)()
+        smmo.check(smmo.lib().smmo_world_info(self._w, None, ids, None), "world_info")
+        names = ["Cell", "WAgent", "Fish", "Shark", "LAgent", "Alive", "Candidate"]
+        self.class_ids = dict(zip(names, list(ids)))
+
+    def step(self, n: int = 1):
+        smmo.check(smmo.lib().smmo_world_step(self._w, n, smmo._stream(self.stream)), "world_step")
+
+    def export(self):
+        """Per-cell numpy arrays (kind, age, energy, state) and error count."""
+        N = self.total
+        dev = torch.device("cuda")
+        k = torch.empty(N, dtype=torch.int8, device=dev)
+        a = torch.empty(N, dtype=torch.int16, device=dev)
+        e = torch.empty(N, dtype=torch.int16, device=dev)
+        s = torch.empty(N, dtype=torch.uint8, device=dev)
+        err = ctypes.c_int64()
+        smmo.check(smmo.lib().smmo_world_export(
+            self._w, ctypes.c_void_p(k.data_ptr()), ctypes.c_void_p(a.data_ptr()),
+            ctypes.c_void_p(e.data_ptr()), ctypes.c_void_p(s.data_ptr()), ctypes.byref(err),
+            smmo._stream(self.stream)), "world_export")
+        return k.cpu().numpy(), a.cpu().numpy(), e.cpu().numpy(), s.cpu().numpy(), err.value
+
+    def split(self, arr):
+        out, o = [], 0
+        for n in self.sizes:
+            out.append(arr[o:o + n])
+            o += n
+        return out
+
+    def sync(self):
+        return self.heap.sync()
+
+    def close(self):
+        if self._w:
+            smmo.lib().smmo_world_destroy(self._w)
+            self._w = ctypes.c_void_p()
+        self.heap.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class WaTor(World):
+    """A single Wa-Tor instance (thesis Sec. 7.7)."""
+
+    def __init__(self, W, H, seed, kind, age, energy, **kw):
+        super().__init__([WATOR], [W], [H], seed, kind, age, energy, None, **kw)
+
+    def read(self):
+        k, a, e, _, err = self.export()
+        if err:
+            raise AssertionError("Wa-Tor heap inconsistent: %d errors" % err)
+        return k, a, e
+
+
+class Life(World):
+    """A single object-based Game of Life instance (thesis Sec. 7.9)."""
+
+    def __init__(self, W, H, kind, state, seed: int = 0, **kw):
+        super().__init__([LIFE], [W], [H], seed, kind, None, None, state, **kw)
+
+    def read(self):
+        k, _, _, s, err = self.export()
+        if err:
+            raise AssertionError("Life heap inconsistent: %d errors" % err)
+        return k.astype(np.uint8), s
