@@ -1,0 +1,366 @@
+#!/usr/bin/env python3
+"""Benchmark: SMMO parallel_do on Wa-Tor 2048x2048 (thesis Sec. 7.7).
+
+One bench step = one Wa-Tor iteration: the fish phase and the shark phase,
+each a parallel_do of prepare and of update over all live agents of the
+class (4 enumeration kernels + 4 method kernels, with device new/delete).
+The metric is object-updates/s: objects visited by the parallel_do launches
+of the timed steps divided by their device time.  Timed steps start from the
+seeded initial state (step 1, 2, ...); the L2 cache (129 MB) is flushed by a
+256 MiB write before every timed step, outside the timed interval, since the
+simulation's working set (~60-120 MB) would otherwise stay L2-resident.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl smmo|reference]
+
+--impl reference times the CPU oracle (plain single-threaded C) on the same
+workload and metric.  Under torchrun every rank runs an independent replica
+(the workload does not shard; see the design notes); value = objects of all
+ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W_SIDE = 2048
+SEED = 1
+CONFIG_STEPS = 500
+FLUSH_BYTES = 256 << 20
+# Algorithmic bytes per visited object for each method kernel (bytes the
+# method must read or write for that object: its own SOA fields plus the
+# cell words it touches; the request atomics count 8 read + 8 write).
+BYTES_PER_OBJECT = {
+    "fish_prepare": 4 + 2 + 2 + 4 + 4 * 4 + 16,      # cell, age r/w, target, 4 occ, req RMW
+    "fish_update": 4 + 4 + 8 + 4 + 4 + 2 + 4,        # cell, target, req, occ[tgt], cell w, age, occ[old]
+    "shark_prepare": 4 + 4 + 4 + 4 + 4 * 4 + 4 * 4 + 16,  # cell, age, energy r/w, target, occ, types, req
+    "shark_update": 4 + 2 + 4 + 8 + 4 + 4 + 4 + 2 + 4,
+}
+PHASES = ["life_cand_prepare", "life_alive_prepare", "life_cand_update", "life_alive_update",
+          "fish_prepare", "fish_update", "shark_prepare", "shark_update"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "wator_2048_traffic.json")
+KERNEL_SOURCES = ["paper_1908_05845_gb300/csrc/world.cu", "paper_1908_05845_gb300/csrc/smmo_core.cuh",
+                  "paper_1908_05845_gb300/csrc/grid_common.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the
+    timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------ reference arm
+def oracle_sample(steps: int, t0: int = 0, state=None):
+    """Times the oracle for `steps` Wa-Tor steps; returns (updates, seconds,
+    final state)."""
+    import oracle
+    from paper_1908_05845_gb300 import inputs
+    if state is None:
+        state = inputs.wator_initial(W_SIDE, W_SIDE, SEED)
+    k, a, e = state
+    F0, S0 = int((k == 1).sum()), int((k == 2).sum())
+    t = time.perf_counter()
+    k2, a2, e2, cnt = oracle.wator_run(W_SIDE, W_SIDE, SEED, k, a, e, steps, t0=t0)
+    dt = time.perf_counter() - t
+    F = np.concatenate([[F0], cnt[:-1, 0]])
+    S = np.concatenate([[S0], cnt[:-1, 1]])
+    return int(np.sum(2 * F + 2 * S)), dt, (k2, a2, e2)
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    state = None
+    t0 = 0
+    if args.warmup:
+        _, _, state = oracle_sample(args.warmup, 0, state)
+        t0 = args.warmup
+    # timed steps start again from the initial state so they cover the same
+    # iterations as the GPU arm
+    upd, dt, _ = oracle_sample(args.steps, 0, None)
+    value = upd / dt
+    line = {
+        "impl": "reference", "metric": "object-updates/s", "value": value, "unit": "object-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32/int16", "data": "synthetic (seeded Philox)",
+        "config": {"workload": "wator_2048x2048", "W": W_SIDE, "H": W_SIDE, "seed": SEED,
+                   "steps_in_config": CONFIG_STEPS, "instances": 1},
+        "cpu_baseline": {"value": value, "unit": "object-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": "Wa-Tor 2048x2048 steps 1..%d from the seeded initial state, "
+                                   "single-threaded C oracle" % args.steps},
+        "e2e": {"value": value, "unit": "object-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------ GPU arm
+def run_gpu(args, ws, rank, local):
+    import torch
+    from paper_1908_05845_gb300 import inputs, smmo
+    from paper_1908_05845_gb300.workloads import WaTor, heap_bytes_for
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    try:
+        smmo.lib()
+    except smmo.SmmoError:
+        from paper_1908_05845_gb300 import build
+        build.build()
+    seed = SEED + rank  # independent replicas
+    k0, a0, e0 = inputs.wator_initial(W_SIDE, W_SIDE, seed)
+    hb = heap_bytes_for(W_SIDE * W_SIDE, 1.0)
+    stream = torch.cuda.current_stream()
+    # warm-up on its own world (same seed)
+    warm = WaTor(W_SIDE, W_SIDE, seed, k0, a0, e0, heap_bytes=hb)
+    if args.warmup:
+        warm.step_profiled(args.warmup)
+    warm.sync()
+    warm.close()
+    del warm
+    sim = WaTor(W_SIDE, W_SIDE, seed, k0, a0, e0, heap_bytes=hb)
+    fish_cls, shark_cls = sim.class_ids["Fish"], sim.class_ids["Shark"]
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    phase_ms = np.zeros(16)
+    step_ms = 0.0
+    launches = 0
+    objs_phase = np.zeros(8)
+    F = int((k0 == 1).sum())
+    S = int((k0 == 2).sum())
+    enum0, alloc0, free0 = sim.heap.counters()
+    clocks = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        ph, sm, la = sim.step_profiled(1)
+        phase_ms += np.array(ph)
+        step_ms += sm
+        launches += la
+        objs_phase[4] += F
+        objs_phase[5] += F
+        objs_phase[6] += S
+        objs_phase[7] += S
+        st = sim.heap.stats()
+        F, S = st["live_objects"][fish_cls], st["live_objects"][shark_cls]
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+    enum1, alloc1, free1 = sim.heap.counters()
+    sim.sync()
+    objects = enum1 - enum0
+    assert objects == int(objs_phase.sum()), (objects, objs_phase.sum())
+    allocfree = (alloc1 - alloc0) + (free1 - free0)
+    t_local = step_ms / 1e3
+    t_max, objects_all, allocfree_all = t_local, objects, allocfree
+    if ws > 1:
+        import torch.distributed as dist
+        v = torch.tensor([t_local], dtype=torch.float64, device="cuda")
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        t_max = float(v.item())
+        o = torch.tensor([objects, allocfree], dtype=torch.float64, device="cuda")
+        dist.all_reduce(o)
+        objects_all, allocfree_all = int(o[0].item()), int(o[1].item())
+    value = objects_all / t_max
+
+    # roofline of the dominant kernel
+    meth = phase_ms[1::2]
+    dom = int(np.argmax(meth))
+    name = PHASES[dom]
+    peaks = load_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    bytes_dom = BYTES_PER_OBJECT.get(name, 0) * objs_phase[dom]
+    achieved = bytes_dom / (meth[dom] / 1e3) / 1e9 if meth[dom] > 0 else 0.0
+    n_launch_dom = args.steps
+    traffic = None
+    try:
+        tr = json.load(open(TRAFFIC_FILE))
+        if tr.get("kernel_hash") == kernel_hash() and tr.get("phase") == name:
+            # per launch at the captured case, scaled by objects per launch
+            traffic = tr["dram_bytes_per_object"] * objs_phase[dom] / n_launch_dom
+    except Exception:
+        pass
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic, "kernel": "do_all<%s>" % name,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
+                "bytes_per_object": BYTES_PER_OBJECT.get(name, 0),
+                "objects_per_launch": objs_phase[dom] / n_launch_dom,
+                "avg_launch_us": 1e3 * meth[dom] / n_launch_dom}
+
+    cpu = None
+    e2e = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        upd, dt, _ = oracle_sample(args.cpu_steps)
+        cpu = {"value": upd / dt, "unit": "object-updates/s", "cores": 1, "kind": "oracle",
+               "sample": "Wa-Tor 2048x2048 steps 1..%d (single-threaded C oracle, %.1f s)"
+                         % (args.cpu_steps, dt)}
+    if rank == 0 and not args.no_e2e:
+        e2e = run_e2e(args, seed, hb)
+    sim.close()
+
+    if rank == 0:
+        line = {
+            "metric": "object-updates/s", "value": value, "unit": "object-updates/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32/int16", "data": "synthetic (seeded Philox)",
+            "config": {"workload": "wator_2048x2048", "W": W_SIDE, "H": W_SIDE, "seed": SEED,
+                       "steps_in_config": CONFIG_STEPS, "instances_per_gpu": 1,
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "flushed (256 MiB write) before every timed step"},
+            "alloc_free_per_s": allocfree_all / t_max,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "phase_ms_per_step": {PHASES[p]: {"enumerate": phase_ms[2 * p] / args.steps,
+                                              "method": phase_ms[2 * p + 1] / args.steps}
+                                  for p in range(4, 8)},
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, seed, hb):
+    """Same metric through the public API from host memory: pinned initial
+    state copied in, world created, K steps each followed by a read-back of
+    the device counters, final per-cell state copied out."""
+    import torch
+    from paper_1908_05845_gb300 import inputs
+    from paper_1908_05845_gb300.workloads import WaTor
+    k0, a0, e0 = inputs.wator_initial(W_SIDE, W_SIDE, seed)
+    hk = torch.from_numpy(k0).pin_memory()
+    ha = torch.from_numpy(a0).pin_memory()
+    he = torch.from_numpy(e0).pin_memory()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    dk, da, de = (x.to("cuda", non_blocking=True) for x in (hk, ha, he))
+    sim = WaTor(W_SIDE, W_SIDE, seed, dk, da, de, heap_bytes=hb)
+    e_start, _, _ = sim.heap.counters()
+    for _ in range(args.steps):
+        sim.step(1)
+        sim.heap.counters()
+    k, a, e = sim.read()
+    e_end, _, _ = sim.heap.counters()
+    dt = time.perf_counter() - t
+    sim.close()
+    h2d = hk.numel() + 2 * ha.numel() + 2 * he.numel()
+    d2h = k.nbytes + a.nbytes + e.nbytes
+    ctr = 8 * 36 * 32
+    return {"value": (e_end - e_start) / dt, "unit": "object-updates/s",
+            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps + ctr,
+            "seconds": dt, "includes": "H2D of initial state, world setup, K steps with a "
+                                       "counter read-back each, D2H of final state"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=CONFIG_STEPS)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="smmo", choices=["smmo", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_gpu(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

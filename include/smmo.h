@@ -117,6 +117,8 @@ typedef struct {
   int64_t allocs[SMMO_MAX_CLASSES];         /* device news since create   */
   int64_t frees[SMMO_MAX_CLASSES];          /* device deletes since create */
   int64_t slow_paths;                       /* blocks initialised by news */
+  int64_t enumerated_objects;               /* objects visited by do-alls */
+  int64_t enumerated_blocks;
   int32_t capacity[SMMO_MAX_CLASSES];       /* N_T per class              */
   int32_t object_bytes[SMMO_MAX_CLASSES];
   int32_t block_bytes;
@@ -229,6 +231,12 @@ int smmo_heap_get_stats(smmo_heap* heap, smmo_heap_stats* out, void* stream);
  * `stream`. */
 int smmo_heap_check(smmo_heap* heap, int64_t* violations, void* stream);
 
+/* Cumulative device counters since create: objects visited by parallel_do
+ * launches, device news and device deletes (all classes).  Host outputs
+ * (nullable).  Synchronises `stream`; reads 9 KB. */
+int smmo_heap_counters(smmo_heap* heap, int64_t* enumerated_objects,
+                       int64_t* allocs, int64_t* frees, void* stream);
+
 /* Synchronises `stream` and returns the first device error recorded since
  * the last sync (then clears it).  *detail (host, nullable) receives the
  * error's detail word (e.g. the offending handle). */
@@ -286,6 +294,17 @@ int smmo_world_step(smmo_world* w, int nsteps, void* stream);
  * at its agent) into *errors (host, nullable).  Synchronises `stream`. */
 int smmo_world_export(smmo_world* w, int8_t* kind, int16_t* age, int16_t* energy,
                       uint8_t* state, int64_t* errors, void* stream);
+/* As smmo_world_step, and additionally records CUDA events on `stream`
+ * around every enumeration and do-all kernel and adds their durations (ms)
+ * to phase_ms (host, 16 doubles, accumulated): index 2*p is the
+ * enumeration and 2*p+1 the method kernel of phase p = Life candidate
+ * prepare, alive prepare, candidate update, alive update, fish prepare,
+ * fish update, shark prepare, shark update.  step_ms (host, nullable)
+ * accumulates the device time from the first to the last launch of each
+ * step; launches (host, nullable) is increased by the number of kernels
+ * launched.  Synchronises `stream` once, after the last step. */
+int smmo_world_step_profiled(smmo_world* w, int nsteps, double* phase_ms,
+                             double* step_ms, int64_t* launches, void* stream);
 /* total_cells, class ids [Cell, WAgent, Fish, Shark, LAgent, Alive,
  * Candidate] (-1 when absent; class_ids host array of 7), steps done. */
 int smmo_world_info(smmo_world* w, int64_t* total_cells, int* class_ids,

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256) k_enumerate(HeapView h, int c) {
     uint32_t base = 0;
     if (lane == 0) base = atomicAdd(&h.st->rcount, tot);
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    uint32_t off = 0;
+    uint32_t off = 0, objs = 0;
     for (int j = 0; j < 64; ++j) {
       const unsigned long long wj = __shfl_sync(0xFFFFFFFFu, w, j >> 1);
       const uint32_t half = (uint32_t)(wj >> ((j & 1) * 32));
@@ -96,8 +96,15 @@ __global__ void __launch_bounds__(256) k_enumerate(HeapView h, int c) {
         e.pad = 0;
         e.bits = __ldcg(h.alloc_bm + b) & capmask;
         h.R[base + off + rank] = e;
+        objs += __popcll(e.bits);
       }
       off += __popc(half);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) objs += __shfl_xor_sync(0xFFFFFFFFu, objs, o);
+    if (lane == 0) {
+      count(h, SMMO_CTR_ENUM_OBJ, objs);
+      count(h, SMMO_CTR_ENUM_BLK, tot);
     }
   }
 }
@@ -731,11 +738,38 @@ int smmo_heap_get_stats(smmo_heap* h, smmo_heap_stats* out, void* stream) {
       out->frees[c] += (int64_t)d->ctr[sh][SMMO_CTR_FREE(c)];
     }
   }
-  for (int sh = 0; sh < SMMO_NSHARD; ++sh) out->slow_paths += (int64_t)d->ctr[sh][SMMO_CTR_SLOW];
+  for (int sh = 0; sh < SMMO_NSHARD; ++sh) {
+    out->slow_paths += (int64_t)d->ctr[sh][SMMO_CTR_SLOW];
+    out->enumerated_objects += (int64_t)d->ctr[sh][SMMO_CTR_ENUM_OBJ];
+    out->enumerated_blocks += (int64_t)d->ctr[sh][SMMO_CTR_ENUM_BLK];
+  }
   out->fragmentation_all = fblk ? fsum / fblk : 0.0;
   out->free_blocks = (int64_t)d->stat_free_blocks;
   out->num_blocks = h->view.num_blocks;
   out->block_bytes = (int)h->view.block_bytes;
+  return SMMO_OK;
+}
+
+int smmo_heap_counters(smmo_heap* h, int64_t* enumerated_objects, int64_t* allocs, int64_t* frees,
+                       void* stream) {
+  if (!h) return SMMO_E_INVALID_ARG;
+  if (enumerated_objects) *enumerated_objects = 0;
+  if (allocs) *allocs = 0;
+  if (frees) *frees = 0;
+  if (!h->frozen) return SMMO_OK;
+  std::vector<unsigned long long> c(SMMO_NSHARD * SMMO_NCTR);
+  cudaError_t e = cudaMemcpyAsync(c.data(), h->view.st->ctr, sizeof(unsigned long long) * c.size(),
+                                  cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return smmo::cuda_status(e);
+  for (int sh = 0; sh < SMMO_NSHARD; ++sh) {
+    const unsigned long long* r = &c[(size_t)sh * SMMO_NCTR];
+    if (enumerated_objects) *enumerated_objects += (int64_t)r[SMMO_CTR_ENUM_OBJ];
+    for (int k = 0; k < SMMO_MAX_CLASSES; ++k) {
+      if (allocs) *allocs += (int64_t)r[SMMO_CTR_ALLOC(k)];
+      if (frees) *frees += (int64_t)r[SMMO_CTR_FREE(k)];
+    }
+  }
   return SMMO_OK;
 }
 

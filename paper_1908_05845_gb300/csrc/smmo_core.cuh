@@ -27,9 +27,11 @@
 #define SMMO_NSHARD 32
 #define SMMO_CTR_SLOW 0
 #define SMMO_CTR_RETRY 1
+#define SMMO_CTR_ENUM_OBJ 34
+#define SMMO_CTR_ENUM_BLK 35
 #define SMMO_CTR_ALLOC(c) (2 + (c))
 #define SMMO_CTR_FREE(c) (2 + SMMO_MAX_CLASSES + (c))
-#define SMMO_NCTR (2 + 2 * SMMO_MAX_CLASSES)
+#define SMMO_NCTR (4 + 2 * SMMO_MAX_CLASSES)
 
 namespace smmo {
 

@@ -388,13 +388,57 @@ struct smmo_world {
 };
 
 namespace {
-int pdo(smmo_world* w, int cls, method_launch_fn fn, const WorldArgs& a, cudaStream_t s) {
+// Optional per-phase timing: events recorded on the launching stream.
+struct PhaseTimer {
+  std::vector<cudaEvent_t> ev;  // 3 per pdo: before enum, between, after
+  std::vector<int> phase;
+  int64_t launches = 0;
+};
+
+int pdo(smmo_world* w, int cls, method_launch_fn fn, const WorldArgs& a, cudaStream_t s,
+        PhaseTimer* pt = nullptr, int phase = 0) {
   std::vector<int> cl;
   concrete_subtree(w->heap, cls, &cl);
   for (int k : cl) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    if (pt) {
+      cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
+      cudaEventRecord(e0, s);
+    }
     int st = enumerate(w->heap, k, s);
+    if (pt) cudaEventRecord(e1, s);
+    if (!st) st = fn(w->heap, k, &a, s);
+    if (pt) {
+      cudaEventRecord(e2, s);
+      pt->ev.push_back(e0); pt->ev.push_back(e1); pt->ev.push_back(e2);
+      pt->phase.push_back(phase);
+      pt->launches += 2;
+    }
     if (st) return st;
-    st = fn(w->heap, k, &a, s);
+  }
+  return SMMO_OK;
+}
+
+int world_steps(smmo_world* w, int nsteps, cudaStream_t s, PhaseTimer* pt) {
+  WorldArgs a = w->args;
+  for (int k = 0; k < nsteps; ++k) {
+    const uint32_t t = ++w->t;
+    a.t = t;
+    int st = SMMO_OK;
+    if (w->nl) {  // one Life generation (Sec. 7.9, four do-alls)
+      st = pdo(w, w->cls_cand, &launch_do_all<CandPrepare>, a, s, pt, 0);
+      if (!st) st = pdo(w, w->cls_alive, &launch_do_all<AlivePrepare>, a, s, pt, 1);
+      if (!st) st = pdo(w, w->cls_cand, &launch_do_all<CandUpdate>, a, s, pt, 2);
+      if (!st) st = pdo(w, w->cls_alive, &launch_do_all<AliveUpdate>, a, s, pt, 3);
+    }
+    if (!st && w->nw) {  // one Wa-Tor iteration (Sec. 7.7): fish phase, shark phase
+      a.key_hi = 0xFFFFFFFFu - 2u * t;
+      st = pdo(w, w->cls_fish, &launch_do_all<FishPrepare>, a, s, pt, 4);
+      if (!st) st = pdo(w, w->cls_fish, &launch_do_all<FishUpdate>, a, s, pt, 5);
+      a.key_hi = 0xFFFFFFFFu - (2u * t + 1u);
+      if (!st) st = pdo(w, w->cls_shark, &launch_do_all<SharkPrepare>, a, s, pt, 6);
+      if (!st) st = pdo(w, w->cls_shark, &launch_do_all<SharkUpdate>, a, s, pt, 7);
+    }
     if (st) return st;
   }
   return SMMO_OK;
@@ -565,29 +609,44 @@ int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32
 
 int smmo_world_step(smmo_world* w, int nsteps, void* stream) {
   if (!w || nsteps < 0) return SMMO_E_INVALID_ARG;
+  return world_steps(w, nsteps, (cudaStream_t)stream, nullptr);
+}
+
+int smmo_world_step_profiled(smmo_world* w, int nsteps, double* phase_ms, double* step_ms,
+                             int64_t* launches, void* stream) {
+  if (!w || nsteps < 0 || !phase_ms) return SMMO_E_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  WorldArgs a = w->args;
-  for (int k = 0; k < nsteps; ++k) {
-    const uint32_t t = ++w->t;
-    a.t = t;
-    int st = SMMO_OK;
-    if (w->nl) {  // one Life generation (Sec. 7.9, four do-alls)
-      st = pdo(w, w->cls_cand, &launch_do_all<CandPrepare>, a, s);
-      if (!st) st = pdo(w, w->cls_alive, &launch_do_all<AlivePrepare>, a, s);
-      if (!st) st = pdo(w, w->cls_cand, &launch_do_all<CandUpdate>, a, s);
-      if (!st) st = pdo(w, w->cls_alive, &launch_do_all<AliveUpdate>, a, s);
-    }
-    if (!st && w->nw) {  // one Wa-Tor iteration (Sec. 7.7): fish phase, shark phase
-      a.key_hi = 0xFFFFFFFFu - 2u * t;
-      st = pdo(w, w->cls_fish, &launch_do_all<FishPrepare>, a, s);
-      if (!st) st = pdo(w, w->cls_fish, &launch_do_all<FishUpdate>, a, s);
-      a.key_hi = 0xFFFFFFFFu - (2u * t + 1u);
-      if (!st) st = pdo(w, w->cls_shark, &launch_do_all<SharkPrepare>, a, s);
-      if (!st) st = pdo(w, w->cls_shark, &launch_do_all<SharkUpdate>, a, s);
-    }
-    if (st) return st;
+  PhaseTimer pt;
+  std::vector<cudaEvent_t> se;  // begin/end event of every step
+  int st = SMMO_OK;
+  for (int k = 0; k < nsteps && !st; ++k) {
+    cudaEvent_t b, e;
+    cudaEventCreate(&b);
+    cudaEventCreate(&e);
+    cudaEventRecord(b, s);
+    st = world_steps(w, 1, s, &pt);
+    cudaEventRecord(e, s);
+    se.push_back(b);
+    se.push_back(e);
   }
-  return SMMO_OK;
+  cudaError_t e = cudaStreamSynchronize(s);
+  for (size_t i = 0; i < pt.phase.size(); ++i) {
+    float m1 = 0, m2 = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&m1, pt.ev[3 * i], pt.ev[3 * i + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&m2, pt.ev[3 * i + 1], pt.ev[3 * i + 2]);
+    phase_ms[2 * pt.phase[i]] += m1;
+    phase_ms[2 * pt.phase[i] + 1] += m2;
+  }
+  for (size_t i = 0; i + 1 < se.size(); i += 2) {
+    float m = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&m, se[i], se[i + 1]);
+    if (step_ms) *step_ms += m;
+  }
+  for (cudaEvent_t ev : pt.ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : se) cudaEventDestroy(ev);
+  if (launches) *launches += pt.launches;
+  if (st) return st;
+  return cuda_status(e);
 }
 
 int smmo_world_export(smmo_world* w, int8_t* kind, int16_t* age, int16_t* energy, uint8_t* state,

@@ -82,7 +82,8 @@ class HeapStats(ctypes.Structure):
                 ("num_blocks", ctypes.c_int64), ("fragmentation", ctypes.c_double * MAX_CLASSES),
                 ("fragmentation_all", ctypes.c_double),
                 ("allocs", ctypes.c_int64 * MAX_CLASSES), ("frees", ctypes.c_int64 * MAX_CLASSES),
-                ("slow_paths", ctypes.c_int64), ("capacity", ctypes.c_int32 * MAX_CLASSES),
+                ("slow_paths", ctypes.c_int64), ("enumerated_objects", ctypes.c_int64),
+                ("enumerated_blocks", ctypes.c_int64), ("capacity", ctypes.c_int32 * MAX_CLASSES),
                 ("object_bytes", ctypes.c_int32 * MAX_CLASSES), ("block_bytes", ctypes.c_int32),
                 ("num_classes", ctypes.c_int32)]
 
@@ -263,6 +264,13 @@ class Heap:
             v = getattr(s, k)
             out[k] = list(v)[:nc] if hasattr(v, "__len__") else v
         return out
+
+    def counters(self):
+        """(enumerated objects, device news, device deletes), cumulative."""
+        e, a, f = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        check(lib().smmo_heap_counters(self._h, ctypes.byref(e), ctypes.byref(a), ctypes.byref(f),
+                                       _stream(self.stream)), "heap_counters")
+        return e.value, a.value, f.value
 
     def check(self) -> int:
         v = ctypes.c_int64()

@@ -45,6 +45,8 @@ class World:
         def dt(a, dtype):
             if a is None:
                 return None
+            if isinstance(a, torch.Tensor):
+                return a.to(dev, dtype).contiguous()
             return torch.as_tensor(np.ascontiguousarray(a)).to(dev, dtype).contiguous()
 
         k = dt(init_kind, torch.int8)
@@ -71,6 +73,17 @@ class World:
 
     def step(self, n: int = 1):
         smmo.check(smmo.lib().smmo_world_step(self._w, n, smmo._stream(self.stream)), "world_step")
+
+    def step_profiled(self, n: int = 1):
+        """Steps n times and returns (phase_ms[16], step_ms, launches): device
+        times from CUDA events on the launching stream (see the C header)."""
+        ph = (ctypes.c_double * 16)()
+        sm = ctypes.c_double()
+        la = ctypes.c_int64()
+        smmo.check(smmo.lib().smmo_world_step_profiled(self._w, n, ph, ctypes.byref(sm),
+                                                       ctypes.byref(la), smmo._stream(self.stream)),
+                   "world_step_profiled")
+        return list(ph), sm.value, la.value
 
     def export(self):
         """Per-cell numpy arrays (kind, age, energy, state) and error count."""
