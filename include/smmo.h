@@ -237,6 +237,12 @@ int smmo_heap_check(smmo_heap* heap, int64_t* violations, void* stream);
 int smmo_heap_counters(smmo_heap* heap, int64_t* enumerated_objects,
                        int64_t* allocs, int64_t* frees, void* stream);
 
+/* Cumulative allocator event counters (host array of 6): blocks
+ * initialised by the slow path, allocation rounds retried, warp-cache
+ * refills, active-block lookups that found nothing, reservations that found
+ * the chosen block full, blocks enumerated.  Synchronises `stream`. */
+int smmo_heap_alloc_counters(smmo_heap* heap, int64_t* out6, void* stream);
+
 /* Synchronises `stream` and returns the first device error recorded since
  * the last sync (then clears it).  *detail (host, nullable) receives the
  * error's detail word (e.g. the offending handle). */

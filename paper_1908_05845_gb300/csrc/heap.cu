@@ -57,55 +57,50 @@ __global__ void k_fill_bitmap(unsigned long long* w, uint32_t nwords, uint64_t n
 }
 
 // Enumeration of the allocated blocks of class c into h.R (the thesis'
-// indices(), Alg. 5.5, with the iteration-bitmap snapshot fused in).  Each
-// warp takes 32 level-0 containers (2048 blocks) at a time, skips them when
-// the level-1 bitmap says they are empty, reserves output space with one
-// atomicAdd and writes the set blocks in ascending order within the chunk.
+// indices(), Alg. 5.5, with the iteration-bitmap snapshot fused in).  One
+// warp per level-0 container (64 blocks): the level-1 bit is tested first so
+// empty regions of the heap are skipped without reading level 0; a
+// non-empty container reserves its output slots with one atomicAdd and its
+// two halves are written by the 32 lanes (block index + bitmap snapshot).
 __global__ void __launch_bounds__(256) k_enumerate(HeapView h, int c) {
   const unsigned long long* L0 = bm_level(h, bm_alloc(h, c), 0);
   const unsigned long long* L1 = h.nlevels > 1 ? bm_level(h, bm_alloc(h, c), 1) : nullptr;
   const uint32_t nw = h.level_words[0];
-  const uint32_t nchunks = (nw + 31) / 32;
   const unsigned long long capmask = h.cls[c].capmask;
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t ch = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < nchunks; ch += nwarps) {
-    if (L1) {
-      const unsigned long long w1 = L1[ch >> 1];
-      if (((w1 >> ((ch & 1) * 32)) & 0xFFFFFFFFull) == 0) continue;
-    }
-    const uint32_t wi = ch * 32 + lane;
-    const unsigned long long w = wi < nw ? L0[wi] : 0ull;
-    uint32_t tot = __popcll(w);
-#pragma unroll
-    for (int o = 16; o; o >>= 1) tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
-    if (tot == 0) continue;
+  const unsigned lt = (1u << lane) - 1;
+  uint32_t objs = 0, blks = 0;
+  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += nwarps) {
+    if (L1 && !((L1[w >> 6] >> (w & 63)) & 1)) continue;
+    const unsigned long long word = L0[w];
+    if (word == 0) continue;
+    const uint32_t lo = (uint32_t)word, hi = (uint32_t)(word >> 32);
     uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&h.st->rcount, tot);
+    if (lane == 0) base = atomicAdd(&h.st->rcount, (uint32_t)__popcll(word));
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    uint32_t off = 0, objs = 0;
-    for (int j = 0; j < 64; ++j) {
-      const unsigned long long wj = __shfl_sync(0xFFFFFFFFu, w, j >> 1);
-      const uint32_t half = (uint32_t)(wj >> ((j & 1) * 32));
-      if (half == 0) continue;
-      if ((half >> lane) & 1) {
-        const uint32_t b = ch * 2048 + j * 32 + lane;
-        const uint32_t rank = __popc(half & ((1u << lane) - 1));
-        REntry e;
-        e.block = b;
-        e.pad = 0;
-        e.bits = __ldcg(h.alloc_bm + b) & capmask;
-        h.R[base + off + rank] = e;
-        objs += __popcll(e.bits);
-      }
-      off += __popc(half);
+    unsigned long long b0 = 0, b1 = 0;
+    if ((lo >> lane) & 1) b0 = __ldcg(h.alloc_bm + w * 64 + lane) & capmask;
+    if ((hi >> lane) & 1) b1 = __ldcg(h.alloc_bm + w * 64 + 32 + lane) & capmask;
+    if ((lo >> lane) & 1) {
+      REntry e;
+      e.block = w * 64 + lane; e.pad = 0; e.bits = b0;
+      h.R[base + __popc(lo & lt)] = e;
+      objs += __popcll(b0);
     }
+    if ((hi >> lane) & 1) {
+      REntry e;
+      e.block = w * 64 + 32 + lane; e.pad = 0; e.bits = b1;
+      h.R[base + __popc(lo) + __popc(hi & lt)] = e;
+      objs += __popcll(b1);
+    }
+    if (lane == 0) blks += __popcll(word);
+  }
 #pragma unroll
-    for (int o = 16; o; o >>= 1) objs += __shfl_xor_sync(0xFFFFFFFFu, objs, o);
-    if (lane == 0) {
-      count(h, SMMO_CTR_ENUM_OBJ, objs);
-      count(h, SMMO_CTR_ENUM_BLK, tot);
-    }
+  for (int o = 16; o; o >>= 1) objs += __shfl_xor_sync(0xFFFFFFFFu, objs, o);
+  if (lane == 0 && (objs | blks)) {
+    count(h, SMMO_CTR_ENUM_OBJ, objs);
+    count(h, SMMO_CTR_ENUM_BLK, blks);
   }
 }
 
@@ -316,9 +311,8 @@ namespace smmo {
 
 static int launch_enumerate(smmo_heap* h, int c, cudaStream_t s) {
   cudaMemsetAsync(&h->view.st->rcount, 0, sizeof(uint32_t), s);
-  const uint32_t nchunks = (h->view.level_words[0] + 31) / 32;
-  uint32_t grid = (nchunks + 7) / 8;
-  grid = std::max(1u, std::min(grid, (uint32_t)h->num_sms * 4));
+  uint32_t grid = (h->view.level_words[0] + 7) / 8;  // one warp per container
+  grid = std::max(1u, std::min(grid, (uint32_t)h->num_sms * 8));
   k_enumerate<<<grid, 256, 0, s>>>(h->view, c);
   return cuda_status(cudaGetLastError());
 }
@@ -747,6 +741,22 @@ int smmo_heap_get_stats(smmo_heap* h, smmo_heap_stats* out, void* stream) {
   out->free_blocks = (int64_t)d->stat_free_blocks;
   out->num_blocks = h->view.num_blocks;
   out->block_bytes = (int)h->view.block_bytes;
+  return SMMO_OK;
+}
+
+int smmo_heap_alloc_counters(smmo_heap* h, int64_t* out6, void* stream) {
+  if (!h || !out6) return SMMO_E_INVALID_ARG;
+  for (int k = 0; k < 6; ++k) out6[k] = 0;
+  if (!h->frozen) return SMMO_OK;
+  std::vector<unsigned long long> c(SMMO_NSHARD * SMMO_NCTR);
+  cudaError_t e = cudaMemcpyAsync(c.data(), h->view.st->ctr, sizeof(unsigned long long) * c.size(),
+                                  cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return smmo::cuda_status(e);
+  const int idx[6] = {SMMO_CTR_SLOW, SMMO_CTR_RETRY, SMMO_CTR_REFILL, SMMO_CTR_LOOKUP_MISS,
+                      SMMO_CTR_RESERVE_FAIL, SMMO_CTR_ENUM_BLK};
+  for (int sh = 0; sh < SMMO_NSHARD; ++sh)
+    for (int k = 0; k < 6; ++k) out6[k] += (int64_t)c[(size_t)sh * SMMO_NCTR + idx[k]];
   return SMMO_OK;
 }
 

@@ -71,10 +71,21 @@ extern const int g_methods_nbody_n;
 
 #ifdef __CUDACC__
 // Instantiates the do-all kernel for method M (see smmo_core.cuh).
+// The persistent grid holds as many CTAs as can be resident at once
+// (occupancy of this instantiation at the configured CTA size, capped by
+// ctas_per_sm), so no CTA waits for another to finish before it starts.
 template <class M>
 int launch_do_all(smmo_heap* h, int cls, const void* args, cudaStream_t s) {
   const typename M::Args* a = static_cast<const typename M::Args*>(args);
-  smmo::do_all_kernel<M><<<smmo::do_all_grid(h), h->cfg.threads_per_cta, 0, s>>>(h->view, cls, *a);
+  static int occ_threads = 0, occ_blocks = 0;
+  if (occ_threads != h->cfg.threads_per_cta) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, smmo::do_all_kernel<M>, h->cfg.threads_per_cta, 0) != cudaSuccess || nb < 1) nb = 1;
+    occ_blocks = nb;
+    occ_threads = h->cfg.threads_per_cta;
+  }
+  const int per_sm = occ_blocks < h->cfg.ctas_per_sm ? occ_blocks : h->cfg.ctas_per_sm;
+  smmo::do_all_kernel<M><<<h->num_sms * per_sm, h->cfg.threads_per_cta, 0, s>>>(h->view, cls, *a);
   return smmo::cuda_status(cudaGetLastError());
 }
 #define SMMO_METHOD(name, M) {name, sizeof(typename M::Args), &launch_do_all<M>}

@@ -29,9 +29,12 @@
 #define SMMO_CTR_RETRY 1
 #define SMMO_CTR_ENUM_OBJ 34
 #define SMMO_CTR_ENUM_BLK 35
+#define SMMO_CTR_REFILL 36
+#define SMMO_CTR_LOOKUP_MISS 37
+#define SMMO_CTR_RESERVE_FAIL 38
 #define SMMO_CTR_ALLOC(c) (2 + (c))
 #define SMMO_CTR_FREE(c) (2 + SMMO_MAX_CLASSES + (c))
-#define SMMO_NCTR (4 + 2 * SMMO_MAX_CLASSES)
+#define SMMO_NCTR (8 + 2 * SMMO_MAX_CLASSES)
 
 namespace smmo {
 
@@ -305,27 +308,36 @@ __device__ __forceinline__ void smmo_delete(const HeapView& h, uint32_t handle) 
 static __device__ __noinline__ unsigned long long leader_reserve(const HeapView& h, uint32_t c, int n,
                                                           uint32_t seed, uint32_t* bid_out) {
   const unsigned long long capmask = __ldg(&h.cls[c].capmask);
+  const uint32_t cap = __ldg(&h.cls[c].cap);
   int bid = -1;
   for (int r = 0; r < h.lookup_retries && bid < 0; ++r)
     bid = bm_try_find_set(h, bm_active(h, c), seed + 104729u * (uint32_t)r);
   if (bid < 0) {
+    count(h, SMMO_CTR_LOOKUP_MISS, 1);
     bid = bm_clear_any(h, bm_free(), seed ^ 0x5bd1e995u);
     if (bid < 0) { *bid_out = kNull; return 0; }
+    count(h, SMMO_CTR_SLOW, 1);
     // initialize_block (Alg. 5.13): type first, fence, then open the slots
     atomicExch(h.block_type + bid, c);
     __threadfence();
+    if ((uint32_t)n >= cap) {
+      // the caller takes the whole block: it is born full, so it never
+      // enters the active bitmap
+      atomicExch(h.alloc_bm + bid, kAll);
+      bm_set(h, bm_alloc(h, c), (uint32_t)bid);
+      *bid_out = (uint32_t)bid;
+      return capmask;
+    }
     atomicExch(h.alloc_bm + bid, ~capmask);
     bm_set(h, bm_alloc(h, c), (uint32_t)bid);
     bm_set(h, bm_active(h, c), (uint32_t)bid);
-    count(h, SMMO_CTR_SLOW, 1);
   }
   *bid_out = (uint32_t)bid;
   // reserve_multiple(n): Alg. 5.9 extended to several slots
   for (int s = 0; s < h.bitmap_spins; ++s) {
     const unsigned long long cur = ld_cg(h.alloc_bm + bid);
     unsigned long long freeb = ~cur;
-    if (freeb == 0) return 0;  // full or invalidated: retry from the start
-    // rotate the choice of slots a little to spread concurrent leaders
+    if (freeb == 0) { count(h, SMMO_CTR_RESERVE_FAIL, 1); return 0; }  // full or invalidated
     unsigned long long pick = 0;
     for (int i = 0; i < n && freeb; ++i) {
       const unsigned long long low = freeb & (0ull - freeb);
@@ -346,11 +358,84 @@ static __device__ __noinline__ unsigned long long leader_reserve(const HeapView&
   return 0;
 }
 
+// Per-warp allocation cache (shared memory, one slot per warp and class).
+// When a warp runs out of cached slots its leader runs the global
+// allocation path (leader_reserve) and reserves every free slot of the
+// block it finds; later allocations of the same warp are served from the
+// cached bits without touching global memory.  Only leader lanes of the
+// warp touch its slot; a per-warp lock still guards it because two diverged
+// lane groups of one warp may each be inside smmo_new at the same time
+// (independent thread scheduling), and without the lock both could hand
+// out the same cached slot.  The lock is uncontended unless that happens.
+// Slots still cached when the do-all kernel ends are returned with
+// dealloc_bits, exactly like deleted objects (the block turns active again
+// or is invalidated).
+struct WarpAllocCache {
+  unsigned long long bits[SMMO_MAX_CLASSES];
+  uint32_t bid[SMMO_MAX_CLASSES];
+  int lock;
+};
+static __shared__ WarpAllocCache g_wcache[32];
+
+__device__ __forceinline__ void alloc_cache_init() {
+  const uint32_t lane = threadIdx.x & 31;
+  if (lane < SMMO_MAX_CLASSES) {
+    g_wcache[threadIdx.x >> 5].bid[lane] = kNull;
+    g_wcache[threadIdx.x >> 5].bits[lane] = 0;
+  }
+  if (lane == 0) g_wcache[threadIdx.x >> 5].lock = 0;
+  __syncwarp();
+}
+
+__device__ __forceinline__ void alloc_cache_flush(const HeapView& h) {
+  __syncwarp();
+  const uint32_t lane = threadIdx.x & 31;
+  WarpAllocCache& wc = g_wcache[threadIdx.x >> 5];
+  if (lane < SMMO_MAX_CLASSES && wc.bits[lane]) {
+    dealloc_bits(h, wc.bid[lane], lane, wc.bits[lane]);
+    wc.bits[lane] = 0;
+  }
+}
+
+// Takes up to n slots of class c from the calling warp's cache, refilling
+// it from the heap when empty.  Returns the slot bits (possibly fewer or
+// none) and the block in *bid (kNull: heap exhausted).
+static __device__ __noinline__ unsigned long long cache_take(const HeapView& h, uint32_t c, int n,
+                                                             uint32_t seed, uint32_t* bid) {
+  WarpAllocCache& wc = g_wcache[threadIdx.x >> 5];
+  int spins = 0;
+  while (atomicCAS(&wc.lock, 0, 1) != 0) {
+    if (++spins > h.bitmap_spins) { set_error(h, SMMO_E_CONTENTION, c); *bid = 0; return 0; }
+    __nanosleep(8);
+  }
+  __threadfence_block();
+  unsigned long long avail = wc.bits[c];
+  uint32_t b = wc.bid[c];
+  if (avail == 0) {
+    avail = leader_reserve(h, c, 64, seed, &b);
+    wc.bid[c] = b;
+    count(h, SMMO_CTR_REFILL, 1);
+  }
+  unsigned long long take = 0;
+  for (int i = 0; i < n && avail; ++i) {
+    const unsigned long long low = avail & (0ull - avail);
+    take |= low;
+    avail ^= low;
+  }
+  wc.bits[c] = b == kNull ? 0ull : avail;
+  __threadfence_block();
+  atomicExch(&wc.lock, 0);
+  *bid = b;
+  return take;
+}
+
 // new(d_allocator) T: warp-aggregated allocation of one object of class c
-// per calling lane (Alg. 5.8).  Lanes that call it together (the active
-// mask) are served by one leader per round; lanes left without a slot retry
-// with a new leader.  Returns kNull (and records SMMO_E_DEVICE_OOM or
-// SMMO_E_CONTENTION) if the heap is exhausted or the budget runs out.
+// per calling lane (allocation request coalescing, Alg. 5.8).  Lanes that
+// call it together (the active mask) are served by one leader per round;
+// lanes left without a slot retry with a new leader.  Only methods run by
+// parallel_do may call it (it uses the warp cache above).  Returns kNull (and
+// records SMMO_E_DEVICE_OOM or SMMO_E_CONTENTION) if the heap is exhausted
+// or the budget runs out.
 __device__ __forceinline__ uint32_t smmo_new(const HeapView& h, uint32_t c) {
   if (c >= (uint32_t)h.num_classes) { set_error(h, SMMO_E_INVALID_ARG, c); return kNull; }
   const unsigned active = __activemask();
@@ -365,12 +450,13 @@ __device__ __forceinline__ uint32_t smmo_new(const HeapView& h, uint32_t c) {
     unsigned long long got = 0;
     uint32_t bid = 0;
     if (lane == leader) {
-      got = leader_reserve(h, c, __popc(need), mix32(warp_uid * 0x27d4eb2fu + (uint32_t)round), &bid);
+      got = cache_take(h, c, __popc(need), mix32(warp_uid * 0x27d4eb2fu + (uint32_t)round), &bid);
       if (got) count(h, SMMO_CTR_ALLOC(c), __popcll(got));
       if (round) count(h, SMMO_CTR_RETRY, 1);
     }
     got = __shfl_sync(active, got, leader);
     bid = __shfl_sync(active, bid, leader);
+    __syncwarp(active);  // the leader's cache update is visible to the next leader
     if (bid == kNull) {  // no free block anywhere
       if (lane == leader) set_error(h, SMMO_E_DEVICE_OOM, c);
       break;
@@ -399,12 +485,15 @@ __global__ void __launch_bounds__(256) do_all_kernel(HeapView h, uint32_t c,
   const uint32_t units = n * halves;
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  alloc_cache_init();
   for (uint32_t u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units; u += nwarps) {
     const uint32_t i = halves == 2 ? (u >> 1) : u;
     const uint32_t slot = (halves == 2 ? (u & 1) * 32 : 0) + lane;
     const REntry e = h.R[i];
     if ((e.bits >> slot) & 1) M::run(h, args, c, (e.block << 6) | slot);
+    __syncwarp();  // reconverge: lane groups never run different iterations
   }
+  alloc_cache_flush(h);
 }
 
 #endif  // __CUDACC__

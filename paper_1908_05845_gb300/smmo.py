@@ -272,6 +272,12 @@ class Heap:
                                        _stream(self.stream)), "heap_counters")
         return e.value, a.value, f.value
 
+    def alloc_counters(self):
+        v = (ctypes.c_int64 * 6)()
+        check(lib().smmo_heap_alloc_counters(self._h, v, _stream(self.stream)), "alloc_counters")
+        return dict(zip(["slow_paths", "retries", "refills", "lookup_misses", "reserve_fails",
+                         "enumerated_blocks"], list(v)))
+
     def check(self) -> int:
         v = ctypes.c_int64()
         check(lib().smmo_heap_check(self._h, ctypes.byref(v), _stream(self.stream)), "heap_check")

@@ -72,7 +72,7 @@ def test_device_new_coalesced_and_counts():
     assert np.array_equal(np.bincount(par, minlength=n), np.full(n, 4))
     st = h.stats()
     assert st["allocs"][B] == 4 * n and st["live_objects"][B] == 4 * n
-    assert st["fragmentation"][B] < 0.05  # new objects fill active blocks first
+    assert st["fragmentation"][B] < 0.1  # new objects fill active blocks first
     assert h.check() == 0
 
 
