@@ -1,5 +1,5 @@
 #!/usr/bin/env python3
-"""Benchmark: SMMO parallel_do on Wa-Tor 2048x2048 (thesis Sec. 7.7).
+"""Benchmark: SMMO parallel_do on Wa-Tor 2048x2048 (thesis Sec. 7.6).
 
 One bench step = one Wa-Tor iteration: the fish phase and the shark phase,
 each a parallel_do of prepare and of update over all live agents of the

@@ -75,7 +75,7 @@ enum {
  * stored as `count` separate SOA columns ("SOA, full inlining", Sec. 4.3).
  * `ref_class` names the class a SMMO_HANDLE field refers to (-1 = unknown);
  * compaction of class T rewrites every HANDLE column whose ref_class is T
- * or a superclass of T (Sec. 6.3.4, "limiting heap scans"). */
+ * or a superclass of T (Sec. 6.3.5, "limiting heap scans"). */
 typedef struct {
   const char* name;
   int elem_type;
@@ -209,10 +209,10 @@ int smmo_gather_fields(smmo_heap* heap, int class_id, const smmo_handle* handles
 
 /* Defragments class_id (CompactGpu, Ch. 6): passes of (1) candidate scan
  * (blocks at most n/(n+1) full, Sec. 6.3.1), (2) source/target assignment
- * (first B = floor(r/(n+1)) candidates are sources, Sec. 6.3.2), (3) object
+ * (first B = floor(r/(n+1)) candidates are sources, Sec. 6.3.3), (3) object
  * copy, (4) forwarding pointers in the source blocks, (5) rewrite of every
  * HANDLE column referring to class_id or a superclass, (6) block-state
- * update, until at most k1 candidates remain (Sec. 6.3.6).  Handles held
+ * update, until at most k1 candidates remain (Sec. 6.3.7).  Handles held
  * outside the heap are invalidated.  Synchronises `stream`. */
 int smmo_compact(smmo_heap* heap, int class_id, int defrag_factor,
                  int64_t k1, smmo_compact_stats* out, void* stream);
@@ -221,7 +221,7 @@ int smmo_compact(smmo_heap* heap, int class_id, int defrag_factor,
  * `stream`. */
 int smmo_heap_get_stats(smmo_heap* heap, smmo_heap_stats* out, void* stream);
 
-/* Checks the heap invariants after all kernels have finished (Sec. 5.4.6,
+/* Checks the heap invariants after all kernels have finished (Sec. 5.4.5,
  * consistency of hierarchical bitmaps; Sec. 6.2.2, block states):
  * every higher-level bit equals the OR of its container; a block is either
  * free or allocated to exactly one class, the one in its type id; a block
@@ -258,7 +258,7 @@ int smmo_class_layout(smmo_heap* heap, int class_id, uint32_t* col_off,
 /* ===================================================== cellular workloads
  * A "world" is a set of independent simulation instances of the thesis'
  * cellular SMMO applications on one heap (Ch. 7): object-based Game of Life
- * (Sec. 7.9; classes Cell, LAgent, Alive, Candidate) and Wa-Tor (Sec. 7.7;
+ * (Sec. 7.8; classes Cell, LAgent, Alive, Candidate) and Wa-Tor (Sec. 7.6;
  * classes Cell, WAgent, Fish, Shark), each on its own W x H torus.  All
  * instances' objects share the heap; one step runs every do-all of the
  * step once per class over all instances (one Life generation and one

@@ -2,8 +2,8 @@
 
 A plain, slow, single-threaded array-of-structs restatement (in C, see the
 ``*.c`` files beside this one) of the thesis' SMMO workloads: object-based
-Game of Life (Sec. 7.9), Wa-Tor (Sec. 7.7), Nagel-Schreckenberg traffic
-(Sec. 7.6), n-body with collision merge (Sec. 7.1/7.2) and the n-body adjoint.
+Game of Life (Sec. 7.8), Wa-Tor (Sec. 7.6), Nagel-Schreckenberg traffic
+(Sec. 7.5), n-body with collision merge (Sec. 7.1/7.2) and the n-body adjoint.
 It has its own Philox4x32-10 (Salmon et al., SC'11).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline

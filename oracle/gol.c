@@ -2,7 +2,7 @@
  * Game of Life with dynamic Alive/Candidate objects -- oracle (test
  * infrastructure only; never linked into the CUDA library).
  *
- * Follows the thesis, Sec. 7.9 ("gol"): classes Cell, abstract Agent,
+ * Follows the thesis, Sec. 7.8 ("gol"): classes Cell, abstract Agent,
  * Alive and Candidate; four parallel do-alls per generation:
  *   1. Candidate::prepare  -- decide delete / upgrade / keep,
  *   2. Alive::prepare      -- decide die / stay,
@@ -11,7 +11,7 @@
  *      creates Candidates on empty surrounding cells, one creator per cell
  *      chosen by a fixed scan order of the empty cell's neighbourhood
  *      (dx outer, dy inner, both -1..1), as in the "create candidates" code
- *      figure of Sec. 7.9.
+ *      figure of Sec. 7.8.
  * Readings (where the thesis is silent): torus instead of a bounded grid;
  * a candidate with no alive neighbour is deleted; is_new is cleared in step 2
  * of the following generation; step 4 sees the occupancy left by step 3.

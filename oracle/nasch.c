@@ -2,7 +2,7 @@
  * Nagel-Schreckenberg traffic on a street graph -- oracle (test
  * infrastructure only).
  *
- * Follows the thesis, Sec. 7.6 ("traffic"): streets are split into cells
+ * Follows the thesis, Sec. 7.5 ("traffic"): streets are split into cells
  * holding at most one Car; each iteration a car (a) accelerates by one up to
  * v_max, (b) computes its path of the next v cells (choosing an outgoing
  * street at an intersection), (c) reduces v to the number of free cells on

@@ -40,7 +40,7 @@ enum {
 /* ------------------------------------------------------------ Game of Life */
 /* Cell kinds in the canonical per-cell output. */
 enum { ORC_EMPTY = 0, ORC_ALIVE = 1, ORC_CANDIDATE = 2 };
-/* Runs T generations of the object-based Life of Sec. 7.9 on a W x H torus.
+/* Runs T generations of the object-based Life of Sec. 7.8 on a W x H torus.
  * kind/state: per-cell in/out arrays (kind: EMPTY/ALIVE/CANDIDATE; state:
  * is_new flag of an Alive object, 0 for candidates).  Per generation
  * counters (7 x int64 per generation, may be NULL):
@@ -55,7 +55,7 @@ typedef struct {
   int fish_breed, shark_breed, starve;
   int breed_strict; /* 0: breed when age >= breed (default); 1: age > breed */
 } orc_wator_params;
-/* Runs steps t0+1 .. t0+T of Wa-Tor (Sec. 7.7) on a W x H torus.
+/* Runs steps t0+1 .. t0+T of Wa-Tor (Sec. 7.6) on a W x H torus.
  * kind/age/energy are per-cell in/out arrays.  seed/inst select the draws.
  * counters (may be NULL): 8 x int64 per step:
  * [fish, sharks, fish_births, fish_eaten, shark_births, sharks_starved,

@@ -1,7 +1,7 @@
 /*
  * Wa-Tor predator-prey -- oracle (test infrastructure only).
  *
- * Follows the thesis, Sec. 7.7 ("wa-tor"): classes Cell, abstract Agent,
+ * Follows the thesis, Sec. 7.6 ("wa-tor"): classes Cell, abstract Agent,
  * Fish and Shark; one iteration is a fish phase (Cell::prepare,
  * Fish::prepare, Cell::decide, Fish::update) followed by a shark phase with
  * the same four steps.  Agents request one neighbouring cell (fish: an

@@ -45,7 +45,7 @@ void concrete_subtree(const smmo_heap* h, int c, std::vector<int>* out) {
 
 // =========================================================== kernels
 // Fills level l of a hierarchical bitmap so that exactly the first nbits
-// bits are set (initial free bitmap: every block free, Sec. 5.2.6).
+// bits are set (initial free bitmap: every block free, Sec. 5.2.4).
 __global__ void k_fill_bitmap(unsigned long long* w, uint32_t nwords, uint64_t nbits) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += gridDim.x * blockDim.x) {
     const uint64_t lo = (uint64_t)i * 64;

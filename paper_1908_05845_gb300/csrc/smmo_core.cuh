@@ -4,7 +4,7 @@
 //   * per block: a 64-bit object allocation bitmap (alloc_bm) and a type id
 //     (block_type); Sec. 5.2.1 "block structure".  The data segments of all
 //     blocks form one array of M equal-size blocks, each holding the SOA
-//     columns of up to N_T <= 64 objects of one class (Sec. 5.2, Fig. 5.4).
+//     columns of up to N_T <= 64 objects of one class (Sec. 5.2).
 //     Bitmaps and type ids live in their own arrays instead of a block
 //     header, so enumeration and statistics read 8 bytes per block.
 //   * hierarchical bitmaps (Sec. 5.3.1) of M bits: free, and per class
@@ -128,7 +128,7 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
   return x;
 }
 
-// Position of the n-th (0-based) set bit of b (Alg. 5.10 "nth_set_bit":
+// Position of the n-th (0-based) set bit of b (Alg. 5.9 "nth_set_bit":
 // clear the n lowest set bits, then find-first-set).  -1 if b has <= n bits.
 __device__ __forceinline__ int nth_set_bit(unsigned long long b, int n) {
   for (int i = 0; i < n; ++i) b &= b - 1;
@@ -256,7 +256,7 @@ static __device__ __noinline__ void dealloc_bits(const HeapView& h, uint32_t bid
   const unsigned long long capmask = __ldg(&h.cls[t].capmask);
   const unsigned long long empty = ~capmask;
   const unsigned long long before = atomicAnd(h.alloc_bm + bid, ~bits);
-  if ((before & bits) != bits) {  // precondition of Alg. 5.9 violated
+  if ((before & bits) != bits) {  // precondition of Alg. 5.8 violated
     set_error(h, SMMO_E_BAD_HANDLE, ((unsigned long long)bid << 6) | (__ffsll((long long)bits) - 1));
     return;
   }
@@ -300,9 +300,9 @@ __device__ __forceinline__ void smmo_delete(const HeapView& h, uint32_t handle) 
 }
 
 // ---------------------------------------------------------------- allocation
-// Leader part of allocation with request coalescing (Alg. 5.8): find an
+// Leader part of allocation with request coalescing (Alg. 5.6): find an
 // active block of class c (with lookup retry, Sec. 5.3.2), else initialise
-// a free block (slow path, Alg. 5.13), then reserve up to n slots in it.
+// a free block (slow path of Alg. 5.1), then reserve up to n slots in it.
 // Returns the reserved slot bits (possibly fewer than n, possibly 0) and the
 // block in *bid; *bid = kNull signals that no free block exists.
 static __device__ __noinline__ unsigned long long leader_reserve(const HeapView& h, uint32_t c, int n,
@@ -317,7 +317,7 @@ static __device__ __noinline__ unsigned long long leader_reserve(const HeapView&
     bid = bm_clear_any(h, bm_free(), seed ^ 0x5bd1e995u);
     if (bid < 0) { *bid_out = kNull; return 0; }
     count(h, SMMO_CTR_SLOW, 1);
-    // initialize_block (Alg. 5.13): type first, fence, then open the slots
+    // initialize_block (Alg. 5.10): type first, fence, then open the slots
     atomicExch(h.block_type + bid, c);
     __threadfence();
     if ((uint32_t)n >= cap) {
@@ -333,7 +333,7 @@ static __device__ __noinline__ unsigned long long leader_reserve(const HeapView&
     bm_set(h, bm_active(h, c), (uint32_t)bid);
   }
   *bid_out = (uint32_t)bid;
-  // reserve_multiple(n): Alg. 5.9 extended to several slots
+  // reserve_multiple(n): Alg. 5.7 extended to several slots
   for (int s = 0; s < h.bitmap_spins; ++s) {
     const unsigned long long cur = ld_cg(h.alloc_bm + bid);
     unsigned long long freeb = ~cur;
@@ -430,7 +430,7 @@ static __device__ __noinline__ unsigned long long cache_take(const HeapView& h, 
 }
 
 // new(d_allocator) T: warp-aggregated allocation of one object of class c
-// per calling lane (allocation request coalescing, Alg. 5.8).  Lanes that
+// per calling lane (allocation request coalescing, Alg. 5.6).  Lanes that
 // call it together (the active mask) are served by one leader per round;
 // lanes left without a slot retry with a new leader.  Only methods run by
 // parallel_do may call it (it uses the warp cache above).  Returns kNull (and

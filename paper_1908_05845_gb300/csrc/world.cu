@@ -1,5 +1,5 @@
 // world.cu -- the cellular SMMO workloads of the thesis' Ch. 7 on one heap:
-// object-based Game of Life (Sec. 7.9) and Wa-Tor (Sec. 7.7), for one or
+// object-based Game of Life (Sec. 7.8) and Wa-Tor (Sec. 7.6), for one or
 // many independent instances ("batched heap": all instances' objects share
 // the heap and every step runs one parallel_do per class over all of them).
 //
@@ -425,13 +425,13 @@ int world_steps(smmo_world* w, int nsteps, cudaStream_t s, PhaseTimer* pt) {
     const uint32_t t = ++w->t;
     a.t = t;
     int st = SMMO_OK;
-    if (w->nl) {  // one Life generation (Sec. 7.9, four do-alls)
+    if (w->nl) {  // one Life generation (Sec. 7.8, four do-alls)
       st = pdo(w, w->cls_cand, &launch_do_all<CandPrepare>, a, s, pt, 0);
       if (!st) st = pdo(w, w->cls_alive, &launch_do_all<AlivePrepare>, a, s, pt, 1);
       if (!st) st = pdo(w, w->cls_cand, &launch_do_all<CandUpdate>, a, s, pt, 2);
       if (!st) st = pdo(w, w->cls_alive, &launch_do_all<AliveUpdate>, a, s, pt, 3);
     }
-    if (!st && w->nw) {  // one Wa-Tor iteration (Sec. 7.7): fish phase, shark phase
+    if (!st && w->nw) {  // one Wa-Tor iteration (Sec. 7.6): fish phase, shark phase
       a.key_hi = 0xFFFFFFFFu - 2u * t;
       st = pdo(w, w->cls_fish, &launch_do_all<FishPrepare>, a, s, pt, 4);
       if (!st) st = pdo(w, w->cls_fish, &launch_do_all<FishUpdate>, a, s, pt, 5);

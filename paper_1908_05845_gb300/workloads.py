@@ -124,7 +124,7 @@ class World:
 
 
 class WaTor(World):
-    """A single Wa-Tor instance (thesis Sec. 7.7)."""
+    """A single Wa-Tor instance (thesis Sec. 7.6)."""
 
     def __init__(self, W, H, seed, kind, age, energy, **kw):
         super().__init__([WATOR], [W], [H], seed, kind, age, energy, None, **kw)
@@ -137,7 +137,7 @@ class WaTor(World):
 
 
 class Life(World):
-    """A single object-based Game of Life instance (thesis Sec. 7.9)."""
+    """A single object-based Game of Life instance (thesis Sec. 7.8)."""
 
     def __init__(self, W, H, kind, state, seed: int = 0, **kw):
         super().__init__([LIFE], [W], [H], seed, kind, None, None, state, **kw)

@@ -1,4 +1,4 @@
-"""Pins of the object-based Game of Life oracle (thesis Sec. 7.9).
+"""Pins of the object-based Game of Life oracle (thesis Sec. 7.8).
 
 Closed forms: the Alive set must equal dense B3/S23 on the torus; the
 Candidate set must equal D_{t+1} & ({c in Cand_t: n_t(c) >= 1} | A_t |

@@ -1,4 +1,4 @@
-"""Pins of the Nagel-Schreckenberg oracle (thesis Sec. 7.6).
+"""Pins of the Nagel-Schreckenberg oracle (thesis Sec. 7.5).
 
 Free-flow closed form x(t) = x0 + sum_{k<=t} min(k, v_max); car-count
 conservation on a closed ring with and without braking; evenly spaced cars

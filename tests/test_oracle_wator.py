@@ -1,4 +1,4 @@
-"""Pins of the Wa-Tor oracle (thesis Sec. 7.7).
+"""Pins of the Wa-Tor oracle (thesis Sec. 7.6).
 
 Bookkeeping identities, hand-checkable histories (lone fish, lone shark,
 shark next to a fish, full grid of fish) and an exhaustive check that a
