@@ -311,6 +311,31 @@ int smmo_world_export(smmo_world* w, int8_t* kind, int16_t* age, int16_t* energy
  * launched.  Synchronises `stream` once, after the last step. */
 int smmo_world_step_profiled(smmo_world* w, int nsteps, double* phase_ms,
                              double* step_ms, int64_t* launches, void* stream);
+/* Allocation-free variant of smmo_world_export (the thesis has no
+ * counterpart; this is a library service).  Some callers cannot call
+ * cudaMalloc at the point where they want the state: programs that hand all
+ * device memory to their own pool or allocator up front, code that must not
+ * hit the device-wide synchronisation a cudaMalloc/cudaFree can cause in
+ * the middle of a time-stepped loop, or plugins hosted by a framework that
+ * forbids device allocations.  smmo_world_export takes its per-cell scratch
+ * with cudaMallocAsync; this entry point takes it from a fixed array inside
+ * the library instead and allocates nothing (no cudaMalloc, no cudaFree, no
+ * allocating library routine).
+ *   - Same arguments and outputs as smmo_world_export; errors (host) is
+ *     required.  Synchronises `stream`.
+ *   - Limit: at most SMMO_EXPORT_NOALLOC_MAX_CELLS cells in the world
+ *     (SMMO_E_UNSUPPORTED above that).  The fixed array (2 MiB + 256 bytes)
+ *     is held by every GPU that loads the library until the process exits.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call uses the same array and clears it at its start.  Calls
+ *     whose work overlaps on the GPU (other streams, other host threads on
+ *     the same device) race on it and must be serialised by the caller. */
+#define SMMO_EXPORT_NOALLOC_MAX_CELLS (1u << 24)
+int smmo_world_export_noalloc(smmo_world* w, int8_t* kind, int16_t* age,
+                              int16_t* energy, uint8_t* state, int64_t* errors,
+                              void* stream);
 /* total_cells, class ids [Cell, WAgent, Fish, Shark, LAgent, Alive,
  * Candidate] (-1 when absent; class_ids host array of 7), steps done. */
 int smmo_world_info(smmo_world* w, int64_t* total_cells, int* class_ids,

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "grid_common.cuh"
@@ -46,6 +47,7 @@ struct WorldArgs {
   uint8_t* out_state;
   uint32_t* out_count;
   unsigned long long* errors;
+  uint32_t* seen;  // one bit per cell (allocation-free export only)
 };
 
 template <class T>
@@ -315,6 +317,36 @@ struct Export {
     uint32_t off = c == a.fish ? a.f_cell : c == a.shark ? a.s_cell : c == a.alive ? a.a_cell : a.c_cell;
     const uint32_t g = *fld<int32_t>(h, self, off);
     atomicAdd(a.out_count + g, 1u);
+    if (*a.cells.col<uint32_t>(g, a.occ_off) != self) atomicAdd(a.errors, 1ull);
+    if (c == a.fish) {
+      a.out_kind[g] = 1;
+      a.out_age[g] = *fld<int16_t>(h, self, a.f_age);
+      a.out_energy[g] = 0;
+    } else if (c == a.shark) {
+      a.out_kind[g] = 2;
+      a.out_age[g] = *fld<int16_t>(h, self, a.s_age);
+      a.out_energy[g] = *fld<int16_t>(h, self, a.s_energy);
+    } else if (c == a.alive) {
+      a.out_kind[g] = 1;
+      a.out_state[g] = *fld<uint8_t>(h, self, a.a_isnew);
+    } else {
+      a.out_kind[g] = 2;
+      a.out_state[g] = 0;
+    }
+  }
+};
+
+// Export variant for smmo_world_export_noalloc: instead of a per-cell agent
+// count it sets one bit per cell in a fixed scratch bitmap; finding the bit
+// already set means a second agent on the cell (one error per extra agent,
+// the same total as the counting export).
+struct ExportBits {
+  using Args = WorldArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
+    uint32_t off = c == a.fish ? a.f_cell : c == a.shark ? a.s_cell : c == a.alive ? a.a_cell : a.c_cell;
+    const uint32_t g = *fld<int32_t>(h, self, off);
+    const uint32_t bit = 1u << (g & 31);
+    if (atomicOr(a.seen + (g >> 5), bit) & bit) atomicAdd(a.errors, 1ull);
     if (*a.cells.col<uint32_t>(g, a.occ_off) != self) atomicAdd(a.errors, 1ull);
     if (c == a.fish) {
       a.out_kind[g] = 1;
@@ -686,6 +718,79 @@ int smmo_world_export(smmo_world* w, int8_t* kind, int16_t* age, int16_t* energy
   if (st) return st;
   for (uint64_t g = 0; g < N; ++g) if (hc[g] > 1) herr += hc[g] - 1;
   if (errors) *errors = (int64_t)herr;
+  return SMMO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free export.  Its scratch is this fixed array, part of the
+// library image, so every GPU that loads the library holds it until exit:
+// 8 bytes of error counter (padded to 256) and one bit per cell for
+// SMMO_EXPORT_NOALLOC_MAX_CELLS cells (2 MiB).  Host code cannot use the
+// array's name as a device address; the address is looked up once per
+// device with cudaGetSymbolAddress (first call on that device).
+}  // extern "C"
+
+namespace {
+struct NoAllocScratch {
+  unsigned long long errors;
+  unsigned long long pad[31];
+  uint32_t seen[SMMO_EXPORT_NOALLOC_MAX_CELLS / 32];
+};
+static __device__ __align__(256) NoAllocScratch g_export_scratch;
+
+std::mutex g_scratch_mu;
+NoAllocScratch* g_scratch_addr[256];  // per device ordinal, set on first use
+
+int scratch_for_current_device(NoAllocScratch** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (dev < 0 || dev >= 256) return SMMO_E_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_export_scratch);
+    if (e != cudaSuccess) return cuda_status(e);
+    g_scratch_addr[dev] = (NoAllocScratch*)p;
+  }
+  *out = g_scratch_addr[dev];
+  return SMMO_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int smmo_world_export_noalloc(smmo_world* w, int8_t* kind, int16_t* age, int16_t* energy,
+                              uint8_t* state, int64_t* errors, void* stream) {
+  if (!w || !kind || !age || !energy || !state || !errors) return SMMO_E_INVALID_ARG;
+  const uint64_t N = w->total_cells;
+  if (N > SMMO_EXPORT_NOALLOC_MAX_CELLS) return SMMO_E_UNSUPPORTED;
+  NoAllocScratch* scr = nullptr;
+  int st = scratch_for_current_device(&scr);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the array keeps the previous call's contents: clear what must start at 0
+  cudaError_t e = cudaMemsetAsync(&scr->errors, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(scr->seen, 0, (N + 31) / 32 * sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(kind, 0, N, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(age, 0, N * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(energy, 0, N * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(state, 0, N, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  WorldArgs a = w->args;
+  a.out_kind = kind; a.out_age = age; a.out_energy = energy; a.out_state = state;
+  a.out_count = nullptr;
+  a.errors = &scr->errors;
+  a.seen = scr->seen;
+  if (w->nw) st = pdo(w, w->cls_wagent, &launch_do_all<ExportBits>, a, s);
+  if (!st && w->nl) st = pdo(w, w->cls_lagent, &launch_do_all<ExportBits>, a, s);
+  if (!st) st = pdo(w, w->cls_cell, &launch_do_all<CheckCells>, a, s);
+  if (st) return st;
+  unsigned long long herr = 0;
+  e = cudaMemcpyAsync(&herr, &scr->errors, sizeof(herr), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  *errors = (int64_t)herr;
   return SMMO_OK;
 }
 
