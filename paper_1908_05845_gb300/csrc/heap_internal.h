@@ -42,6 +42,10 @@ int freeze(smmo_heap* h, cudaStream_t s);
 void concrete_subtree(const smmo_heap* h, int c, std::vector<int>* out);
 // enumerate class c into h->view.R, count into st->rcount (asynchronous)
 int enumerate(smmo_heap* h, int c, cudaStream_t s);
+// level l of hierarchical bitmap k (device pointer computed on the host)
+inline unsigned long long* bm_level_host(const smmo_heap* h, int k, int l = 0) {
+  return h->view.bitmaps + (size_t)k * h->view.bm_words + h->view.level_off[l];
+}
 // grid for persistent kernels
 inline dim3 do_all_grid(const smmo_heap* h) {
   return dim3((unsigned)(h->num_sms * h->cfg.ctas_per_sm));

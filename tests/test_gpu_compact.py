@@ -1,0 +1,124 @@
+"""GPU tests of compact (CompactGpu, Ch. 6): the relocated multiset is
+unchanged, every HANDLE column referring to the class is rewritten, the
+fragmentation bound F < 1/(n+1) holds when all candidates are eliminated,
+the pass count respects the worst-case bound, and the thesis' worked
+examples of source/target assignment and relocation come out as printed."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1908_05845_gb300 import inputs, smmo  # noqa: E402
+from paper_1908_05845_gb300.workloads import WaTor  # noqa: E402
+
+
+def cuda_i32(a):
+    return torch.as_tensor(np.asarray(a, dtype=np.int32)).cuda()
+
+
+def test_compact_preserves_objects_and_rewrites_handles():
+    h = smmo.Heap(64 << 20)
+    A = h.register("A", [("v", smmo.I32), ("w", smmo.I32)])
+    Rf = h.register("Ref", [("ref", smmo.HANDLE, 1, A), ("val", smmo.I32)])
+    n = 64 * 50
+    v = np.arange(n)
+    hd, first = h.bulk_new(A, n, [cuda_i32(v), cuda_i32(7 * v)], want_handles=True)
+    h.parallel_do(A, "test.free_self_if", smmo.FreeSelfIfArgs(0, 3, 1))
+    h.parallel_do(A, "test.free_self_if", smmo.FreeSelfIfArgs(0, 3, 2))
+    keep = v % 3 == 0
+    h.bulk_new(Rf, int(keep.sum()), [hd[torch.as_tensor(keep).cuda()], cuda_i32(v[keep])])
+    h.sync()
+    d0 = 50  # every A block is ~1/3 full: all are candidates for n = 2
+    st = h.compact(A, n=2, k1=0)
+    h.sync()
+    assert h.check() == 0
+    assert st["blocks_freed"] > 0 and st["objects_moved"] > 0
+    assert st["pointers_rewritten"] > 0
+    assert st["passes"] <= math.ceil(math.log(d0) / math.log(1.5)) + 1
+    hd2 = h.enumerate_live(A)
+    vv, ww = (t.cpu().numpy() for t in h.gather(A, hd2, ["v", "w"]))
+    assert np.array_equal(np.sort(vv), v[keep]) and np.array_equal(ww[np.argsort(vv)], 7 * v[keep])
+    rh = h.enumerate_live(Rf)
+    ref, val = h.gather(Rf, rh, ["ref", "val"])
+    (tv,) = h.gather(A, ref, ["v"])
+    assert np.array_equal(tv.cpu().numpy(), val.cpu().numpy())
+    stt = h.stats()
+    assert stt["fragmentation"][A] < 1 / 3
+    assert stt["live_objects"][A] == keep.sum()
+
+
+def _kill_all_but(h, A, fill_per_block, nblocks, cap):
+    n = nblocks * cap
+    v = np.arange(n)
+    kill = np.zeros(n, np.int32)
+    for b, f in fill_per_block.items():
+        kill[b * cap + f:(b + 1) * cap] = 1
+    _, first = h.bulk_new(A, n, [cuda_i32(v), cuda_i32(kill)])
+    assert first == 0
+    h.parallel_do(A, "test.free_self_if", smmo.FreeSelfIfArgs(1, 2, 1))
+    h.sync()
+    return v, kill
+
+
+def where_now(h, A):
+    hd = h.enumerate_live(A)
+    (vv,) = h.gather(A, hd, ["v"])
+    blk = (hd.cpu().numpy().astype(np.int64) & 0xFFFFFFFF) >> 6
+    return dict(zip(vv.cpu().numpy().tolist(), blk.tolist()))
+
+
+def test_worked_example_assignment_n2():
+    """n = 2, seven candidates: B = 2 sources; source 5 moves into 14 and
+    19, source 9 into 16 and 22, block 30 is left over (Sec. 6.3.3)."""
+    h = smmo.Heap(32 << 20)
+    A = h.register("A", [("v", smmo.I32), ("kill", smmo.I32)])
+    fill = {5: 30, 9: 30, 14: 40, 16: 40, 19: 20, 22: 20, 30: 20}
+    v, kill = _kill_all_but(h, A, fill, 31, 64)
+    st = h.compact(A, n=2, k1=6)
+    h.sync()
+    assert st["passes"] == 1 and st["blocks_freed"] == 2 and st["objects_moved"] == 60
+    loc = where_now(h, A)
+    src5 = [x for x in range(5 * 64, 5 * 64 + 30)]
+    src9 = [x for x in range(9 * 64, 9 * 64 + 30)]
+    assert sorted(loc[x] for x in src5) == [14] * 24 + [19] * 6
+    assert sorted(loc[x] for x in src9) == [16] * 24 + [22] * 6
+    assert all(loc[x] == x // 64 for x in loc if x // 64 not in (5, 9))
+    assert h.check() == 0
+
+
+def test_worked_example_relocation_n3_capacity32():
+    """n = 3, block capacity 32, 18 objects: the first 12 fit into the first
+    target, the remaining 6 into the second (Sec. 6.3.3, Alg. 6.4)."""
+    h = smmo.Heap(32 << 20, smmo.default_config(block_data_bytes=256))
+    A = h.register("A", [("v", smmo.I32), ("kill", smmo.I32)])
+    h.freeze()
+    assert h.class_info(A)["capacity"] == 32
+    fill = {0: 18, 1: 20, 2: 10, 3: 24}
+    _kill_all_but(h, A, fill, 4, 32)
+    st = h.compact(A, n=3, k1=3)
+    h.sync()
+    loc = where_now(h, A)
+    assert st["passes"] == 1 and st["objects_moved"] == 18
+    assert sorted(loc[x] for x in range(18)) == [1] * 12 + [2] * 6
+    assert h.check() == 0
+
+
+def test_wator_with_periodic_compaction_matches_oracle(orc):
+    W = H = 256
+    k, a, e = inputs.wator_initial(W, H, 2)
+    sim = WaTor(W, H, 2, k, a, e)
+    F, S = sim.class_ids["Fish"], sim.class_ids["Shark"]
+    for _ in range(6):
+        sim.step(10)
+        for c in (F, S):
+            sim.heap.compact(c, n=2, k1=0)
+            assert sim.heap.stats()["fragmentation"][c] < 1 / 3
+    got = sim.read()
+    want = orc.wator_run(W, H, 2, k, a, e, 60)
+    for g, w in zip(got, want[:3]):
+        assert np.array_equal(g, w)
+    assert sim.heap.check() == 0
+    sim.sync()
