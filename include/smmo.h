@@ -342,6 +342,46 @@ int smmo_world_info(smmo_world* w, int64_t* total_cells, int* class_ids,
                     uint32_t* steps_done);
 int smmo_world_destroy(smmo_world* w);
 
+/* ========================================================= street traffic
+ * Nagel-Schreckenberg traffic on a street graph (Sec. 7.5): classes Cell
+ * {car}, Car {cell, street, v, route, cross}, Source {street}; one step =
+ * Car::prepare (accelerate, path, gap against the occupancy at step start,
+ * brake with probability p, claim the first cell of the street being
+ * entered), Car::move (claim losers stop at the end of their street, cars
+ * ending on or passing the last cell of a sink street delete themselves,
+ * the rest move), Source::spawn (a producer street with an empty first cell
+ * creates a car with v = 0).  The outgoing street at the end of street s in
+ * step t is out[s][draw(ROUTE, t, last cell of s) % out_deg[s]]; brake draws
+ * are keyed by the car's cell; the lowest cell wins a contested entry. */
+typedef struct smmo_traffic smmo_traffic;
+/* Registers the classes in a fresh heap and creates cells, cars and
+ * producers.  Host arrays of num_streets entries: street_start (cells are
+ * numbered street by street, street_start[0] = 0), street_len (>= 2),
+ * out_deg (0..3; 0 = sink), out_street (3 per street), is_source.  car_v:
+ * device array over all cells, -1 = no car, else the velocity.
+ * brake_threshold = floor(p 2^32).  sources_enabled = 0 creates no
+ * producers; sinks_enabled = 0 makes sink streets dead ends.  Allocates
+ * small street tables with cudaMalloc (freed by smmo_traffic_destroy).
+ * Synchronises `stream`. */
+int smmo_traffic_create(smmo_heap* heap, int num_streets,
+                        const int32_t* street_start, const int32_t* street_len,
+                        const int32_t* out_deg, const int32_t* out_street,
+                        const uint8_t* is_source, int v_max,
+                        uint32_t brake_threshold, int sources_enabled,
+                        int sinks_enabled, uint64_t seed, const int8_t* car_v,
+                        void* stream, smmo_traffic** out);
+/* nsteps steps; asynchronous. */
+int smmo_traffic_step(smmo_traffic* w, int nsteps, void* stream);
+/* car_v (device, per cell): -1 or the car's velocity; *errors (host,
+ * nullable): cells holding two cars + cars whose cell does not point back.
+ * Synchronises `stream`. */
+int smmo_traffic_export(smmo_traffic* w, int8_t* car_v, int64_t* errors,
+                        void* stream);
+/* num_cells, class ids [Cell, Car, Source] (host array of 3), steps done. */
+int smmo_traffic_info(smmo_traffic* w, int64_t* num_cells, int* class_ids,
+                      uint32_t* steps_done);
+int smmo_traffic_destroy(smmo_traffic* w);
+
 #ifdef __cplusplus
 }
 #endif

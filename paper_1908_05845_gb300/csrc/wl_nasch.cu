@@ -1,0 +1,362 @@
+// wl_nasch.cu -- Nagel-Schreckenberg traffic on a street graph as an SMMO
+// application (thesis Sec. 7.5).  Classes: Cell {car: handle}, Car {cell,
+// street, v, route, cross}, Source {street}.  One step is three do-alls:
+//   Car::prepare  accelerate, compute the path of the next v cells
+//                 (choosing the outgoing street at the end of the street),
+//                 cut v to the free cells on the path (occupancy at step
+//                 start), brake with probability p, and post a claim on the
+//                 first cell of the street the car would enter;
+//   Car::move     a car that lost its claim stops at the end of its street;
+//                 a car on a sink street that ends on or passes the last
+//                 cell deletes itself; the others move;
+//   Source::spawn a producer street whose first cell is empty creates a Car.
+// Claims are u64 words per street: ((2^32-1-t) << 32) | cell, atomicMin, so
+// the lowest cell wins and words of older steps never match (no reset).
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+#include "grid_common.cuh"
+#include "heap_internal.h"
+#include "smmo.h"
+#include "smmo_core.cuh"
+
+using namespace smmo;
+
+namespace {
+
+struct TrafficArgs {
+  const int32_t* start;   // per street
+  const int32_t* len;
+  const int32_t* deg;
+  const int32_t* out;     // 3 per street
+  unsigned long long* claim;  // per street
+  CellRef cells;
+  uint32_t occ_off;
+  uint32_t car_cls;
+  uint32_t c_cell, c_street, c_v, c_route, c_cross;
+  uint32_t s_street;      // Source.street column offset
+  uint64_t seed;
+  uint32_t t, key_hi;
+  int32_t v_max;
+  uint32_t brake_threshold;
+  int32_t sinks_enabled;
+  // export
+  int8_t* out_v;
+  uint32_t* out_count;
+  unsigned long long* errors;
+};
+
+template <class T>
+__device__ __forceinline__ T* fld(const HeapView& h, uint32_t self, uint32_t off) {
+  return field_ptr<T>(h, off, self);
+}
+
+struct CarPrepare {
+  using Args = TrafficArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+    const int32_t c = *fld<int32_t>(h, self, a.c_cell);
+    const int32_t s = *fld<int32_t>(h, self, a.c_street);
+    int8_t* vp = fld<int8_t>(h, self, a.c_v);
+    const int32_t st = __ldg(a.start + s), L = __ldg(a.len + s), dg = __ldg(a.deg + s);
+    const int32_t p = c - st;
+    int v = *vp + 1 < a.v_max ? *vp + 1 : a.v_max;
+    int32_t o = -1;
+    if (dg > 0) {
+      const uint32_t r = philox_draw(a.seed, TAG_ROUTE, a.t, (uint32_t)(st + L - 1), 0);
+      o = __ldg(a.out + 3 * s + (int)(r % (uint32_t)dg));
+    }
+    int free_run = 0;
+    for (int k = 1; k <= v; ++k) {
+      const int32_t q = p + k;
+      int32_t cell;
+      if (q < L) cell = st + q;
+      else if (o >= 0) cell = __ldg(a.start + o) + (q - L);
+      else if (a.sinks_enabled) { free_run = k; continue; }  // leaving the network
+      else break;                                               // dead end
+      if (*a.cells.col<uint32_t>((uint32_t)cell, a.occ_off) != kNull) break;
+      free_run = k;
+    }
+    v = free_run;
+    if (v > 0 && philox_draw(a.seed, TAG_BRAKE, a.t, (uint32_t)c, 0) < a.brake_threshold) --v;
+    const bool cross = o >= 0 && p + v >= L;
+    if (cross)
+      atomicMin(a.claim + o, ((unsigned long long)a.key_hi << 32) | (uint32_t)c);
+    *vp = (int8_t)v;
+    *fld<int32_t>(h, self, a.c_route) = o;
+    *fld<uint8_t>(h, self, a.c_cross) = cross ? 1 : 0;
+  }
+};
+
+struct CarMove {
+  using Args = TrafficArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+    int32_t* cp = fld<int32_t>(h, self, a.c_cell);
+    int32_t* sp = fld<int32_t>(h, self, a.c_street);
+    int8_t* vp = fld<int8_t>(h, self, a.c_v);
+    const int32_t c = *cp, s = *sp;
+    const int32_t st = __ldg(a.start + s), L = __ldg(a.len + s);
+    const int32_t p = c - st;
+    int v = *vp;
+    const int32_t o = *fld<int32_t>(h, self, a.c_route);
+    bool cross = *fld<uint8_t>(h, self, a.c_cross);
+    if (cross && a.claim[o] != (((unsigned long long)a.key_hi << 32) | (uint32_t)c)) {
+      v = L - 1 - p;  // lost the claim: stop on the last cell of the street
+      cross = false;
+      *vp = (int8_t)v;
+    }
+    if (__ldg(a.deg + s) == 0 && a.sinks_enabled && p + v >= L - 1) {
+      *a.cells.col<uint32_t>((uint32_t)c, a.occ_off) = kNull;
+      smmo_delete(h, self);
+      return;
+    }
+    if (v == 0) return;
+    const int32_t q = p + v;
+    const int32_t dst = q < L ? st + q : __ldg(a.start + o) + (q - L);
+    *a.cells.col<uint32_t>((uint32_t)c, a.occ_off) = kNull;
+    *a.cells.col<uint32_t>((uint32_t)dst, a.occ_off) = self;
+    *cp = dst;
+    if (q >= L) *sp = o;
+  }
+};
+
+struct SourceSpawn {
+  using Args = TrafficArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+    const int32_t s = *fld<int32_t>(h, self, a.s_street);
+    const uint32_t c = (uint32_t)__ldg(a.start + s);
+    uint32_t* occ = a.cells.col<uint32_t>(c, a.occ_off);
+    if (*occ != kNull) return;
+    const uint32_t car = smmo_new(h, a.car_cls);
+    if (car == kNull) return;
+    *fld<int32_t>(h, car, a.c_cell) = (int32_t)c;
+    *fld<int32_t>(h, car, a.c_street) = s;
+    *fld<int8_t>(h, car, a.c_v) = 0;
+    *fld<int32_t>(h, car, a.c_route) = -1;
+    *fld<uint8_t>(h, car, a.c_cross) = 0;
+    *occ = car;
+  }
+};
+
+struct CarLink {
+  using Args = TrafficArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+    *a.cells.col<uint32_t>((uint32_t)*fld<int32_t>(h, self, a.c_cell), a.occ_off) = self;
+  }
+};
+
+struct CarExport {
+  using Args = TrafficArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+    const uint32_t c = (uint32_t)*fld<int32_t>(h, self, a.c_cell);
+    if (atomicAdd(a.out_count + c, 1u)) atomicAdd(a.errors, 1ull);
+    if (*a.cells.col<uint32_t>(c, a.occ_off) != self) atomicAdd(a.errors, 1ull);
+    a.out_v[c] = *fld<int8_t>(h, self, a.c_v);
+  }
+};
+
+}  // namespace
+
+const smmo::MethodEntry g_methods_nasch[] = {
+    SMMO_METHOD("nasch.car_prepare", CarPrepare), SMMO_METHOD("nasch.car_move", CarMove),
+    SMMO_METHOD("nasch.source_spawn", SourceSpawn), SMMO_METHOD("nasch.car_link", CarLink),
+    SMMO_METHOD("nasch.car_export", CarExport)};
+const int g_methods_nasch_n = sizeof(g_methods_nasch) / sizeof(g_methods_nasch[0]);
+
+struct smmo_traffic {
+  smmo_heap* heap = nullptr;
+  int cls_cell = -1, cls_car = -1, cls_src = -1;
+  int num_streets = 0, num_cells = 0;
+  int32_t* d_tab = nullptr;  // start | len | deg | out[3]
+  unsigned long long* d_claim = nullptr;
+  uint32_t t = 0;
+  TrafficArgs args{};
+};
+
+namespace {
+int pdo(smmo_traffic* w, int cls, method_launch_fn fn, const TrafficArgs& a, cudaStream_t s) {
+  int st = enumerate(w->heap, cls, s);
+  if (!st) st = fn(w->heap, cls, &a, s);
+  return st;
+}
+}  // namespace
+
+extern "C" {
+
+int smmo_traffic_create(smmo_heap* heap, int num_streets, const int32_t* street_start,
+                        const int32_t* street_len, const int32_t* out_deg, const int32_t* out_street,
+                        const uint8_t* is_source, int v_max, uint32_t brake_threshold,
+                        int sources_enabled, int sinks_enabled, uint64_t seed, const int8_t* car_v,
+                        void* stream, smmo_traffic** out) {
+  if (!heap || num_streets < 1 || !street_start || !street_len || !out_deg || !out_street ||
+      !is_source || !car_v || !out || v_max < 1 || v_max > 100)
+    return SMMO_E_INVALID_ARG;
+  if (!heap->classes.empty() || heap->frozen) return SMMO_E_FROZEN;
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t cells = 0;
+  for (int i = 0; i < num_streets; ++i) {
+    if (street_len[i] < 2 || street_start[i] != cells || out_deg[i] < 0 || out_deg[i] > 3)
+      return SMMO_E_INVALID_ARG;
+    for (int k = 0; k < out_deg[i]; ++k)
+      if (out_street[3 * i + k] < 0 || out_street[3 * i + k] >= num_streets) return SMMO_E_INVALID_ARG;
+    cells += street_len[i];
+  }
+  if (cells >= (1ll << 31)) return SMMO_E_INVALID_ARG;
+  smmo_traffic* w = new smmo_traffic();
+  w->heap = heap;
+  w->num_streets = num_streets;
+  w->num_cells = (int)cells;
+  smmo_field_desc cf[1] = {{"car", SMMO_HANDLE, 1, -1}};
+  smmo_field_desc kf[5] = {{"cell", SMMO_I32, 1, -1}, {"street", SMMO_I32, 1, -1}, {"v", SMMO_I8, 1, -1},
+                           {"route", SMMO_I32, 1, -1}, {"cross", SMMO_U8, 1, -1}};
+  smmo_field_desc sf[1] = {{"street", SMMO_I32, 1, -1}};
+  int st = smmo_class_register(heap, "Car", kf, 5, -1, 0, &w->cls_car);
+  if (!st) st = smmo_class_register(heap, "Cell", cf, 1, -1, 0, &w->cls_cell);
+  if (!st) st = smmo_class_register(heap, "Source", sf, 1, -1, 0, &w->cls_src);
+  if (heap->cfg.block_data_bytes == 0) heap->cfg.block_data_bytes = 256 + 256 + 64 + 256 + 64;
+  if (!st) st = freeze(heap, s);
+  if (!st && heap->classes[w->cls_cell].layout.cap != 64) st = SMMO_E_UNSUPPORTED;
+  if (st) { delete w; return st; }
+  std::vector<int32_t> tab(6 * (size_t)num_streets, -1);
+  for (int i = 0; i < num_streets; ++i) {
+    tab[i] = street_start[i];
+    tab[num_streets + i] = street_len[i];
+    tab[2 * num_streets + i] = out_deg[i];
+    for (int k = 0; k < 3; ++k) tab[3 * num_streets + 3 * i + k] = k < out_deg[i] ? out_street[3 * i + k] : -1;
+  }
+  cudaError_t e = cudaMalloc(&w->d_tab, sizeof(int32_t) * tab.size());
+  if (e == cudaSuccess) e = cudaMalloc(&w->d_claim, sizeof(unsigned long long) * num_streets);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w->d_tab, tab.data(), sizeof(int32_t) * tab.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w->d_claim, 0xFF, sizeof(unsigned long long) * num_streets, s);
+  if (e != cudaSuccess) { smmo_traffic_destroy(w); return cuda_status(e); }
+  // cells (dense, in cell order), empty
+  uint32_t* occ0 = nullptr;
+  e = cudaMallocAsync(&occ0, (size_t)cells * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(occ0, 0xFF, (size_t)cells * 4, s);
+  if (e != cudaSuccess) { smmo_traffic_destroy(w); return cuda_status(e); }
+  const void* csrc[1] = {occ0};
+  int64_t first = -1;
+  st = smmo_bulk_new(heap, w->cls_cell, cells, csrc, nullptr, &first, stream);
+  cudaFreeAsync(occ0, s);
+  if (!st && first < 0) st = SMMO_E_OOM;
+  if (st) { smmo_traffic_destroy(w); return st; }
+  TrafficArgs& a = w->args;
+  memset(&a, 0, sizeof(a));
+  a.start = w->d_tab;
+  a.len = w->d_tab + num_streets;
+  a.deg = w->d_tab + 2 * num_streets;
+  a.out = w->d_tab + 3 * num_streets;
+  a.claim = w->d_claim;
+  a.cells.data = heap->view.data;
+  a.cells.block_bytes = heap->view.block_bytes;
+  a.cells.b0 = (uint32_t)first;
+  a.occ_off = heap->classes[w->cls_cell].layout.col_off[0];
+  const ClassLayout& K = heap->classes[w->cls_car].layout;
+  a.car_cls = w->cls_car;
+  a.c_cell = K.col_off[0]; a.c_street = K.col_off[1]; a.c_v = K.col_off[2];
+  a.c_route = K.col_off[3]; a.c_cross = K.col_off[4];
+  a.s_street = heap->classes[w->cls_src].layout.col_off[0];
+  a.seed = seed;
+  a.v_max = v_max;
+  a.brake_threshold = brake_threshold;
+  a.sinks_enabled = sinks_enabled;
+  // cars and sources from the host copies (setup only)
+  std::vector<int8_t> hv((size_t)cells);
+  e = cudaMemcpyAsync(hv.data(), car_v, (size_t)cells, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { smmo_traffic_destroy(w); return cuda_status(e); }
+  std::vector<int32_t> kc, ks, kr;
+  std::vector<int8_t> kv;
+  std::vector<uint8_t> kx;
+  int sidx = 0;
+  for (int64_t c = 0; c < cells; ++c) {
+    while (sidx + 1 < num_streets && street_start[sidx + 1] <= c) ++sidx;
+    if (hv[c] < 0) continue;
+    kc.push_back((int32_t)c); ks.push_back(sidx); kv.push_back(hv[c]); kr.push_back(-1); kx.push_back(0);
+  }
+  std::vector<int32_t> src;
+  if (sources_enabled)
+    for (int i = 0; i < num_streets; ++i) if (is_source[i]) src.push_back(i);
+  auto upload = [&](int cls, std::vector<const void*> cols, std::vector<size_t> esz, size_t n) -> int {
+    if (n == 0) return SMMO_OK;
+    std::vector<void*> d(cols.size(), nullptr);
+    cudaError_t ee = cudaSuccess;
+    for (size_t k = 0; k < cols.size() && ee == cudaSuccess; ++k) {
+      ee = cudaMallocAsync(&d[k], n * esz[k], s);
+      if (ee == cudaSuccess) ee = cudaMemcpyAsync(d[k], cols[k], n * esz[k], cudaMemcpyHostToDevice, s);
+    }
+    int r = ee == cudaSuccess ? smmo_bulk_new(heap, cls, (int64_t)n, (const void* const*)d.data(), nullptr, nullptr, stream)
+                              : cuda_status(ee);
+    for (void* p : d) if (p) cudaFreeAsync(p, s);
+    return r;
+  };
+  st = upload(w->cls_car, {kc.data(), ks.data(), kv.data(), kr.data(), kx.data()}, {4, 4, 1, 4, 1}, kc.size());
+  if (!st) st = upload(w->cls_src, {src.data()}, {4}, src.size());
+  if (!st) st = pdo(w, w->cls_car, &launch_do_all<CarLink>, a, s);
+  if (!st) { e = cudaStreamSynchronize(s); if (e != cudaSuccess) st = cuda_status(e); }
+  if (st) { smmo_traffic_destroy(w); return st; }
+  *out = w;
+  return SMMO_OK;
+}
+
+int smmo_traffic_step(smmo_traffic* w, int nsteps, void* stream) {
+  if (!w || nsteps < 0) return SMMO_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  TrafficArgs a = w->args;
+  for (int k = 0; k < nsteps; ++k) {
+    a.t = ++w->t;
+    a.key_hi = 0xFFFFFFFFu - a.t;
+    int st = pdo(w, w->cls_car, &launch_do_all<CarPrepare>, a, s);
+    if (!st) st = pdo(w, w->cls_car, &launch_do_all<CarMove>, a, s);
+    if (!st) st = pdo(w, w->cls_src, &launch_do_all<SourceSpawn>, a, s);
+    if (st) return st;
+  }
+  return SMMO_OK;
+}
+
+int smmo_traffic_export(smmo_traffic* w, int8_t* car_v, int64_t* errors, void* stream) {
+  if (!w || !car_v) return SMMO_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  TrafficArgs a = w->args;
+  uint32_t* cnt = nullptr;
+  unsigned long long* err = nullptr;
+  cudaError_t e = cudaMallocAsync(&cnt, (size_t)w->num_cells * 4, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&err, 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, (size_t)w->num_cells * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(car_v, 0xFF, (size_t)w->num_cells, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  a.out_v = car_v;
+  a.out_count = cnt;
+  a.errors = err;
+  int st = pdo(w, w->cls_car, &launch_do_all<CarExport>, a, s);
+  unsigned long long herr = 0;
+  if (!st) {
+    e = cudaMemcpyAsync(&herr, err, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e);
+  }
+  cudaFreeAsync(cnt, s);
+  cudaFreeAsync(err, s);
+  if (errors) *errors = (int64_t)herr;
+  return st;
+}
+
+int smmo_traffic_info(smmo_traffic* w, int64_t* num_cells, int* class_ids, uint32_t* steps_done) {
+  if (!w) return SMMO_E_INVALID_ARG;
+  if (num_cells) *num_cells = w->num_cells;
+  if (class_ids) { class_ids[0] = w->cls_cell; class_ids[1] = w->cls_car; class_ids[2] = w->cls_src; }
+  if (steps_done) *steps_done = w->t;
+  return SMMO_OK;
+}
+
+int smmo_traffic_destroy(smmo_traffic* w) {
+  if (!w) return SMMO_E_INVALID_ARG;
+  if (w->d_tab) cudaFree(w->d_tab);
+  if (w->d_claim) cudaFree(w->d_claim);
+  delete w;
+  return SMMO_OK;
+}
+
+}  // extern "C"

@@ -147,3 +147,62 @@ class Life(World):
         if err:
             raise AssertionError("Life heap inconsistent: %d errors" % err)
         return k.astype(np.uint8), s
+
+
+class Traffic:
+    """Nagel-Schreckenberg traffic on a street graph (thesis Sec. 7.5)."""
+
+    def __init__(self, graph: dict, seed: int, car_v, heap_bytes: int | None = None,
+                 config: smmo.HeapConfig | None = None, stream=None):
+        self.stream = stream
+        self.num_cells = int(graph["num_cells"])
+        S = int(graph["num_streets"])
+        nbytes = heap_bytes or int((self.num_cells / 64.0 * 3 + 4096) * 1000) + (32 << 20)
+        self.heap = smmo.Heap(nbytes, config, stream=stream)
+        self._w = ctypes.c_void_p()
+
+        def arr(name, ct, n):
+            a = np.ascontiguousarray(graph[name], dtype=np.int32 if ct is ctypes.c_int32 else np.uint8)
+            return (ct * n)(*a.tolist())
+
+        cv = torch.as_tensor(np.ascontiguousarray(car_v, dtype=np.int8)).cuda() \
+            if not isinstance(car_v, torch.Tensor) else car_v.to("cuda", torch.int8).contiguous()
+        smmo.check(smmo.lib().smmo_traffic_create(
+            self.heap.handle, S, arr("street_start", ctypes.c_int32, S),
+            arr("street_len", ctypes.c_int32, S), arr("out_deg", ctypes.c_int32, S),
+            arr("out_street", ctypes.c_int32, 3 * S), arr("is_source", ctypes.c_uint8, S),
+            int(graph.get("v_max", 5)), ctypes.c_uint32(int(graph["brake_threshold"])),
+            int(graph.get("sources_enabled", 1)), int(graph.get("sinks_enabled", 1)),
+            ctypes.c_uint64(seed), ctypes.c_void_p(cv.data_ptr()), smmo._stream(stream),
+            ctypes.byref(self._w)), "traffic_create")
+        ids = (ctypes.c_int * 3)()
+        smmo.check(smmo.lib().smmo_traffic_info(self._w, None, ids, None), "traffic_info")
+        self.class_ids = dict(zip(["Cell", "Car", "Source"], list(ids)))
+
+    def step(self, n: int = 1):
+        smmo.check(smmo.lib().smmo_traffic_step(self._w, n, smmo._stream(self.stream)), "traffic_step")
+
+    def read(self):
+        v = torch.empty(self.num_cells, dtype=torch.int8, device="cuda")
+        err = ctypes.c_int64()
+        smmo.check(smmo.lib().smmo_traffic_export(self._w, ctypes.c_void_p(v.data_ptr()),
+                                                  ctypes.byref(err), smmo._stream(self.stream)),
+                   "traffic_export")
+        if err.value:
+            raise AssertionError("traffic heap inconsistent: %d errors" % err.value)
+        return v.cpu().numpy()
+
+    def sync(self):
+        return self.heap.sync()
+
+    def close(self):
+        if self._w:
+            smmo.lib().smmo_traffic_destroy(self._w)
+            self._w = ctypes.c_void_p()
+        self.heap.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
