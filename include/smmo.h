@@ -382,6 +382,50 @@ int smmo_traffic_info(smmo_traffic* w, int64_t* num_cells, int* class_ids,
                       uint32_t* steps_done);
 int smmo_traffic_destroy(smmo_traffic* w);
 
+/* ================================================================ n-body
+ * Direct n-body with collision merge (Sec. 7.1, 7.2) and its adjoint.  One
+ * class Body {x, y, z, vx, vy, vz, m, id, lx, ly, lz, lvx, lvy, lvz}
+ * (the last six: adjoint state).  A step is drift-kick-drift: x += v dt/2,
+ * a = G sum_j m_j r_ij / (|r_ij|^2 + eps^2)^{3/2} summed over body ids in
+ * increasing order with a fixed FP32 evaluation order and IEEE division and
+ * square root, v += a dt, x += v dt/2; then, if merge != 0, a receiver takes
+ * the first lighter body ((m, id) lexicographic) within merge_r in id order,
+ * a body picked by several receivers goes to the lowest receiver id, and it
+ * merges (v = (v1 m1 + v2 m2)/(m1 + m2), x = midpoint, m = m1 + m2) unless
+ * its receiver is itself picked; merged bodies delete themselves. */
+typedef struct {
+  float G, eps, dt, merge_r;
+  int merge;
+} smmo_nbody_params;
+typedef struct smmo_nbody smmo_nbody;
+/* Registers class Body in a fresh heap and creates n bodies with ids
+ * 0..n-1.  cols: host array of 7 device pointers (x, y, z, vx, vy, vz, m;
+ * n floats each).  Allocates its id-indexed staging arrays with cudaMalloc
+ * (freed by smmo_nbody_destroy).  Synchronises `stream`. */
+int smmo_nbody_create(smmo_heap* heap, int64_t n, const float* const* cols,
+                      const smmo_nbody_params* p, void* stream, smmo_nbody** out);
+/* nsteps steps; asynchronous. */
+int smmo_nbody_step(smmo_nbody* w, int nsteps, void* stream);
+/* out7 (device, 7 x n floats, id-indexed: x, y, z, vx, vy, vz, m), live
+ * (device, n bytes), *merges (host, nullable) = merges so far.
+ * Synchronises `stream`. */
+int smmo_nbody_export(smmo_nbody* w, float* out7, uint8_t* live,
+                      int64_t* merges, void* stream);
+/* Adjoint of the no-merge run (merge must be 0): runs nsteps steps from the
+ * current state keeping (x, v) every ckpt steps, returns the loss
+ * L = 1/2 sum m |v|^2 at the end in *loss (host) and initialises the
+ * adjoint state (lambda_x = 0, lambda_v = m v).  Synchronises `stream`. */
+int smmo_nbody_forward_ckpt(smmo_nbody* w, int nsteps, int ckpt, double* loss,
+                            void* stream);
+/* Reverse sweep after smmo_nbody_forward_ckpt: every segment is recomputed
+ * from its checkpoint, then reversed step by step with the pair kernel
+ * g_k = G sum_j H(x_j - x_k)(m_k mu_j - m_j mu_k),
+ * H(r) = I/s^3 - 3 r r^T/s^5, mu = dt (lambda_v + dt/2 lambda_x).
+ * grad_v0 (device, n x 3 floats, id-indexed) receives dL/dv_0.  The body
+ * state afterwards is that of the end of the first segment.  Asynchronous. */
+int smmo_nbody_backward(smmo_nbody* w, float* grad_v0, void* stream);
+int smmo_nbody_destroy(smmo_nbody* w);
+
 #ifdef __cplusplus
 }
 #endif

@@ -191,6 +191,20 @@ def nbody_accel_f32(state: dict, G=1.0, eps=1e-2):
     return ax, ay, az
 
 
+def nbody_step_sample_f32(state: dict, idx, G=1.0, eps=1e-2, dt=1e-3):
+    """One no-merge FP32 step for the receivers in idx: [len(idx), 6]
+    (x, y, z, vx, vy, vz)."""
+    lib = _load()
+    cols = [np.ascontiguousarray(state[k], dtype=np.float32) for k in ("x", "y", "z", "vx", "vy", "vz", "m")]
+    live = np.ascontiguousarray(state["live"], dtype=np.uint8)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    out = np.zeros((idx.size, 6), np.float32)
+    lib.orc_nbody_step_sample_f32(cols[0].size, ctypes.c_float(G), ctypes.c_float(eps),
+                                  ctypes.c_float(dt), *[_p(c) for c in cols], _p(live), _p(idx),
+                                  int(idx.size), _p(out))
+    return out
+
+
 def _d(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
@@ -241,6 +255,20 @@ def nbody_adjoint_f64(pos0, vel0, m, T, ckpt=10, G=1.0, eps=1e-2, dt=1e-3):
                                    _p(grad), ctypes.byref(loss))
     if rc != 0:
         raise ValueError("orc_nbody_adjoint_f64: bad arguments")
+    return grad, loss.value
+
+
+def nbody_adjoint_f32traj(state: dict, T, G=1.0, eps=1e-2, dt=1e-3):
+    """FP64 reverse sweep along the FP32 trajectory: (grad [N,3], loss)."""
+    lib = _load()
+    cols = [np.ascontiguousarray(state[k], dtype=np.float32) for k in ("x", "y", "z", "vx", "vy", "vz", "m")]
+    N = cols[0].size
+    grad = np.zeros((N, 3), np.float64)
+    loss = ctypes.c_double()
+    rc = lib.orc_nbody_adjoint_f32traj(N, ctypes.c_float(G), ctypes.c_float(eps), ctypes.c_float(dt),
+                                       *[_p(c) for c in cols], int(T), _p(grad), ctypes.byref(loss))
+    if rc != 0:
+        raise ValueError("orc_nbody_adjoint_f32traj: bad arguments")
     return grad, loss.value
 
 

@@ -154,6 +154,55 @@ int orc_nbody_run_f32(int N, const orc_nbody_params_f32* p, float* x, float* y,
   return 0;
 }
 
+/* One no-merge FP32 step evaluated only for the listed receivers (same
+ * order of operations as orc_nbody_run_f32): out = 6 floats per listed
+ * body (x, y, z, vx, vy, vz after the step). */
+int orc_nbody_step_sample_f32(int N, float G, float eps, float dt, const float* x,
+                              const float* y, const float* z, const float* vx,
+                              const float* vy, const float* vz, const float* m,
+                              const uint8_t* live, const int32_t* idx, int nidx,
+                              float* out) {
+  if (N < 0 || nidx < 0) return -1;
+  const float h = 0.5f * dt, eps2 = eps * eps;
+  float* x1 = (float*)malloc(sizeof(float) * (size_t)(3 * N + 3));
+  float* y1 = x1 + N + 1;
+  float* z1 = y1 + N + 1;
+  for (int j = 0; j < N; ++j) {
+    x1[j] = x[j] + vx[j] * h;
+    y1[j] = y[j] + vy[j] * h;
+    z1[j] = z[j] + vz[j] * h;
+  }
+  for (int q = 0; q < nidx; ++q) {
+    const int i = idx[q];
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+    for (int j = 0; j < N; ++j) {
+      if (j == i || !live[j]) continue;
+      float dx = x1[j] - x1[i];
+      float dy = y1[j] - y1[i];
+      float dz = z1[j] - z1[i];
+      float s2 = dx * dx;
+      s2 = s2 + dy * dy;
+      s2 = s2 + dz * dz;
+      s2 = s2 + eps2;
+      float inv = 1.0f / (s2 * sqrtf(s2));
+      float f = m[j] * inv;
+      sx = sx + f * dx;
+      sy = sy + f * dy;
+      sz = sz + f * dz;
+    }
+    float ax = G * sx, ay = G * sy, az = G * sz;
+    float nvx = vx[i] + ax * dt, nvy = vy[i] + ay * dt, nvz = vz[i] + az * dt;
+    out[6 * q + 0] = x1[i] + nvx * h;
+    out[6 * q + 1] = y1[i] + nvy * h;
+    out[6 * q + 2] = z1[i] + nvz * h;
+    out[6 * q + 3] = nvx;
+    out[6 * q + 4] = nvy;
+    out[6 * q + 5] = nvz;
+  }
+  free(x1);
+  return 0;
+}
+
 /* ---------------------------------------------------------------- FP64 */
 int orc_nbody_accel_f64(int N, double G, double eps, const double* pos,
                         const double* m, double* acc) {
@@ -230,6 +279,74 @@ int orc_nbody_pair_adjoint_f64(int N, double G, double eps, const double* pos,
     }
     for (int c = 0; c < 3; ++c) g[3 * k + c] = G * acc[c];
   }
+  return 0;
+}
+
+/* Reverse sweep shared by both adjoints: from lambda_x = 0, lambda_v = m v_T,
+ * step s = T-1 .. 0 with the mid-step positions x1[s] (N x 3 each). */
+static void reverse_sweep(int N, double G, double eps, double dt, const double* m,
+                          const double* x1, int T, const double* vT, double* grad) {
+  const size_t n3 = 3 * (size_t)N;
+  const double h = 0.5 * dt;
+  double* lx = (double*)calloc(n3, sizeof(double));
+  double* lv = (double*)malloc(sizeof(double) * n3);
+  double* w = (double*)malloc(sizeof(double) * n3);
+  double* mu = (double*)malloc(sizeof(double) * n3);
+  double* g = (double*)malloc(sizeof(double) * n3);
+  for (int i = 0; i < N; ++i)
+    for (int c = 0; c < 3; ++c) lv[3 * i + c] = m[i] * vT[3 * i + c];
+  for (int s = T - 1; s >= 0; --s) {
+    for (size_t k = 0; k < n3; ++k) { w[k] = lv[k] + h * lx[k]; mu[k] = dt * w[k]; }
+    orc_nbody_pair_adjoint_f64(N, G, eps, x1 + n3 * (size_t)s, m, mu, g);
+    for (size_t k = 0; k < n3; ++k) { lx[k] += g[k]; lv[k] = w[k] + h * lx[k]; }
+  }
+  memcpy(grad, lv, sizeof(double) * n3);
+  free(lx); free(lv); free(w); free(mu); free(g);
+}
+
+/* FP64 reverse sweep along the FP32 trajectory: the forward pass is the
+ * FP32 no-merge step of orc_nbody_run_f32 (same operations), its mid-step
+ * positions and final velocities are widened to double, and the reverse
+ * sweep runs in FP64.  Isolates the accuracy of an FP32 reverse sweep from
+ * the divergence of FP32 and FP64 forward trajectories. */
+int orc_nbody_adjoint_f32traj(int N, float G, float eps, float dt, const float* x0,
+                              const float* y0, const float* z0, const float* vx0,
+                              const float* vy0, const float* vz0, const float* m32,
+                              int T, double* grad, double* loss) {
+  if (N < 1 || T < 0) return -1;
+  const size_t n3 = 3 * (size_t)N;
+  float* st = (float*)malloc(sizeof(float) * 6 * (size_t)N);
+  float *x = st, *y = st + N, *z = st + 2 * N, *vx = st + 3 * N, *vy = st + 4 * N, *vz = st + 5 * N;
+  memcpy(x, x0, sizeof(float) * N); memcpy(y, y0, sizeof(float) * N); memcpy(z, z0, sizeof(float) * N);
+  memcpy(vx, vx0, sizeof(float) * N); memcpy(vy, vy0, sizeof(float) * N); memcpy(vz, vz0, sizeof(float) * N);
+  float* ax = (float*)malloc(sizeof(float) * 3 * (size_t)N);
+  float *ay = ax + N, *az = ax + 2 * N;
+  uint8_t* live = (uint8_t*)malloc((size_t)N);
+  memset(live, 1, (size_t)N);
+  double* x1 = (double*)malloc(sizeof(double) * n3 * (size_t)(T > 0 ? T : 1));
+  double* m = (double*)malloc(sizeof(double) * N);
+  double* vT = (double*)malloc(sizeof(double) * n3);
+  for (int i = 0; i < N; ++i) m[i] = m32[i];
+  const float h = 0.5f * dt;
+  for (int s = 0; s < T; ++s) {
+    for (int i = 0; i < N; ++i) {
+      x[i] = x[i] + vx[i] * h; y[i] = y[i] + vy[i] * h; z[i] = z[i] + vz[i] * h;
+      x1[n3 * s + 3 * i] = x[i]; x1[n3 * s + 3 * i + 1] = y[i]; x1[n3 * s + 3 * i + 2] = z[i];
+    }
+    orc_nbody_accel_f32(N, G, eps, x, y, z, m32, live, ax, ay, az);
+    for (int i = 0; i < N; ++i) {
+      vx[i] = vx[i] + ax[i] * dt; vy[i] = vy[i] + ay[i] * dt; vz[i] = vz[i] + az[i] * dt;
+      x[i] = x[i] + vx[i] * h; y[i] = y[i] + vy[i] * h; z[i] = z[i] + vz[i] * h;
+    }
+  }
+  double L = 0;
+  for (int i = 0; i < N; ++i) {
+    vT[3 * i] = vx[i]; vT[3 * i + 1] = vy[i]; vT[3 * i + 2] = vz[i];
+    for (int c = 0; c < 3; ++c) L += 0.5 * m[i] * vT[3 * i + c] * vT[3 * i + c];
+  }
+  reverse_sweep(N, G, eps, dt, m, x1, T, vT, grad);
+  if (loss) *loss = L;
+  free(st); free(ax); free(live); free(x1); free(m); free(vT);
   return 0;
 }
 

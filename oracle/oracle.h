@@ -99,6 +99,14 @@ int orc_nbody_accel_f32(int N, float G, float eps, const float* x,
                         const float* y, const float* z, const float* m,
                         const uint8_t* live, float* ax, float* ay, float* az);
 
+/* One no-merge FP32 step for the listed receivers only (out: 6 floats per
+ * listed body: x, y, z, vx, vy, vz after the step), same arithmetic. */
+int orc_nbody_step_sample_f32(int N, float G, float eps, float dt, const float* x,
+                              const float* y, const float* z, const float* vx,
+                              const float* vy, const float* vz, const float* m,
+                              const uint8_t* live, const int32_t* idx, int nidx,
+                              float* out);
+
 /* FP64 variants (no merge).  pos/vel: N x 3 row-major. */
 int orc_nbody_run_f64(int N, double G, double eps, double dt, double* pos,
                       double* vel, const double* m, int T);
@@ -115,6 +123,13 @@ int orc_nbody_adjoint_f64(int N, double G, double eps, double dt,
                           const double* pos0, const double* vel0,
                           const double* m, int T, int ckpt, double* grad,
                           double* loss);
+/* FP64 reverse sweep along the FP32 no-merge trajectory (forward pass as in
+ * orc_nbody_run_f32, mid-step positions and final velocities widened to
+ * double).  grad: N x 3. */
+int orc_nbody_adjoint_f32traj(int N, float G, float eps, float dt, const float* x0,
+                              const float* y0, const float* z0, const float* vx0,
+                              const float* vy0, const float* vz0, const float* m32,
+                              int T, double* grad, double* loss);
 /* One application of the pair kernel g_k = G sum_{j!=k} H(x_j - x_k)
  * (m_k mu_j - m_j mu_k), H(r) = I/s^3 - 3 r r^T / s^5. */
 int orc_nbody_pair_adjoint_f64(int N, double G, double eps, const double* pos,

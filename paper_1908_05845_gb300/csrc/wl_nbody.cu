@@ -1,0 +1,605 @@
+// wl_nbody.cu -- direct n-body with collision merge and its adjoint as an
+// SMMO application (thesis Sec. 7.1 "nbody", Sec. 7.2 "collision").
+//
+// Class Body {x, y, z, vx, vy, vz, m, id, lx, ly, lz, lvx, lvy, lvz}; the
+// last six fields hold the adjoint state.  One step (drift-kick-drift):
+//   Body::drift_stage  x += v dt/2 and publish (x, m) into an id-ordered
+//                      staging array (the sequential device_do of the thesis
+//                      iterates over objects; here it iterates over this
+//                      array in id order, which fixes the summation order);
+//   force              a_i = G sum_j m_j r_ij / (|r_ij|^2 + eps^2)^{3/2}
+//                      over j in id order, read tile by tile through shared
+//                      memory, then v += a dt and x += v dt/2;
+// and with merging (Sec. 7.2, made deterministic): restage, merge_prepare
+// (a receiver takes the first lighter body within R in id order and posts
+// its id with atomicMin, so the lowest receiver wins), merge_perform (a
+// picked body merges into its receiver unless the receiver is itself picked,
+// then deletes itself).
+//
+// FP32 arithmetic uses explicit round-to-nearest intrinsics in the order
+//   s2 = ((dx*dx + dy*dy) + dz*dz) + eps^2; inv = 1/(s2*sqrt(s2));
+//   f = m_j*inv; a += f*d;
+// with IEEE division and square root, so results equal a sequential FP32
+// evaluation in the same order bit for bit.  The self pair and freed ids
+// (mass 0 in the staging array) add exactly +0 and need no branch.
+//
+// Adjoint (no merge, loss L = 1/2 sum m |v_T|^2, gradient w.r.t. v_0):
+// checkpoints of (x, v) every `ckpt` steps; each segment is recomputed
+// forward keeping the mid-step positions x1, then reversed step by step:
+//   w = lambda_v + dt/2 lambda_x;  mu = dt w;
+//   g_k = G sum_j H(x1_j - x1_k)(m_k mu_j - m_j mu_k),
+//   H(r) = I/s^3 - 3 r r^T / s^5,  s^2 = |r|^2 + eps^2;
+//   lambda_x += g;  lambda_v = w + dt/2 lambda_x.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+#include "heap_internal.h"
+#include "smmo.h"
+#include "smmo_core.cuh"
+
+using namespace smmo;
+
+namespace {
+
+enum { CX, CY, CZ, CVX, CVY, CVZ, CM, CID, CLX, CLY, CLZ, CLVX, CLVY, CLVZ, NCOL };
+
+struct NBodyArgs {
+  float4* S;            // (x, y, z, m) by id
+  float4* A;            // (mu_x, mu_y, mu_z, 0) by id (adjoint)
+  const float4* X1;     // mid-step (x, y, z, m) by id for the step being reversed
+  uint32_t* hmap;       // handle by id
+  uint32_t* tgt;        // merge receiver by id
+  float* buf;           // per-id scratch (checkpoints, export)
+  double* ke;           // per-id kinetic energy
+  uint32_t n0;
+  float G, eps2, dt, h, R2;
+  uint32_t off[NCOL];
+  unsigned long long* merges;
+};
+
+template <class T>
+__device__ __forceinline__ T& F(const HeapView& h, uint32_t self, uint32_t off) {
+  return *field_ptr<T>(h, off, self);
+}
+
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+
+struct DriftStage {
+  using Args = NBodyArgs;
+  __device__ static void run(const HeapView& hv, const Args& a, uint32_t, uint32_t self) {
+    float& x = F<float>(hv, self, a.off[CX]);
+    float& y = F<float>(hv, self, a.off[CY]);
+    float& z = F<float>(hv, self, a.off[CZ]);
+    x = fa(x, fm(F<float>(hv, self, a.off[CVX]), a.h));
+    y = fa(y, fm(F<float>(hv, self, a.off[CVY]), a.h));
+    z = fa(z, fm(F<float>(hv, self, a.off[CVZ]), a.h));
+    const uint32_t id = F<int32_t>(hv, self, a.off[CID]);
+    a.S[id] = make_float4(x, y, z, F<float>(hv, self, a.off[CM]));
+    a.hmap[id] = self;
+  }
+};
+
+struct Stage {
+  using Args = NBodyArgs;
+  __device__ static void run(const HeapView& hv, const Args& a, uint32_t, uint32_t self) {
+    const uint32_t id = F<int32_t>(hv, self, a.off[CID]);
+    a.S[id] = make_float4(F<float>(hv, self, a.off[CX]), F<float>(hv, self, a.off[CY]),
+                          F<float>(hv, self, a.off[CZ]), F<float>(hv, self, a.off[CM]));
+    a.hmap[id] = self;
+    a.tgt[id] = kNull;
+  }
+};
+
+// Tiled pass over all ids for the objects of class c enumerated in h.R:
+// the CTA walks groups of 8 warp units (32 slots each); every thread of the
+// CTA loads the shared tiles, only threads on live slots accumulate.
+#define NB_TILE 256
+
+__global__ void __launch_bounds__(256) k_force(HeapView hv, uint32_t c, NBodyArgs a) {
+  __shared__ float4 tile[NB_TILE];
+  const uint32_t n = __ldcg(&hv.st->rcount);
+  const uint32_t cap = hv.cls[c].cap;
+  const uint32_t halves = cap > 32 ? 2u : 1u;
+  const uint32_t units = n * halves, groups = (units + 7) / 8;
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (uint32_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const uint32_t u = g * 8 + warp;
+    bool live = false;
+    uint32_t self = 0;
+    if (u < units) {
+      const REntry e = hv.R[halves == 2 ? (u >> 1) : u];
+      const uint32_t slot = (halves == 2 ? (u & 1) * 32 : 0) + lane;
+      live = (e.bits >> slot) & 1;
+      self = (e.block << 6) | slot;
+    }
+    float xi = 0, yi = 0, zi = 0, ax = 0.0f, ay = 0.0f, az = 0.0f;
+    if (live) {
+      xi = F<float>(hv, self, a.off[CX]);
+      yi = F<float>(hv, self, a.off[CY]);
+      zi = F<float>(hv, self, a.off[CZ]);
+    }
+    for (uint32_t base = 0; base < a.n0; base += NB_TILE) {
+      __syncthreads();
+      if (base + threadIdx.x < a.n0) tile[threadIdx.x] = a.S[base + threadIdx.x];
+      __syncthreads();
+      const uint32_t cnt = a.n0 - base < NB_TILE ? a.n0 - base : NB_TILE;
+      if (live) {
+        for (uint32_t k = 0; k < cnt; ++k) {
+          const float4 p = tile[k];
+          const float dx = fs(p.x, xi), dy = fs(p.y, yi), dz = fs(p.z, zi);
+          float s2 = fm(dx, dx);
+          s2 = fa(s2, fm(dy, dy));
+          s2 = fa(s2, fm(dz, dz));
+          s2 = fa(s2, a.eps2);
+          const float inv = __fdiv_rn(1.0f, fm(s2, __fsqrt_rn(s2)));
+          const float f = fm(p.w, inv);
+          ax = fa(ax, fm(f, dx));
+          ay = fa(ay, fm(f, dy));
+          az = fa(az, fm(f, dz));
+        }
+      }
+    }
+    if (live) {
+      ax = fm(a.G, ax); ay = fm(a.G, ay); az = fm(a.G, az);
+      float& vx = F<float>(hv, self, a.off[CVX]);
+      float& vy = F<float>(hv, self, a.off[CVY]);
+      float& vz = F<float>(hv, self, a.off[CVZ]);
+      vx = fa(vx, fm(ax, a.dt));
+      vy = fa(vy, fm(ay, a.dt));
+      vz = fa(vz, fm(az, a.dt));
+      F<float>(hv, self, a.off[CX]) = fa(xi, fm(vx, a.h));
+      F<float>(hv, self, a.off[CY]) = fa(yi, fm(vy, a.h));
+      F<float>(hv, self, a.off[CZ]) = fa(zi, fm(vz, a.h));
+    }
+  }
+}
+
+// Receiver i takes the first body j in id order with (m_j, j) < (m_i, i)
+// and |x_j - x_i|^2 < R^2; the lowest receiver id wins j.
+__global__ void __launch_bounds__(256) k_merge_prepare(HeapView hv, uint32_t c, NBodyArgs a) {
+  __shared__ float4 tile[NB_TILE];
+  const uint32_t n = __ldcg(&hv.st->rcount);
+  const uint32_t cap = hv.cls[c].cap;
+  const uint32_t halves = cap > 32 ? 2u : 1u;
+  const uint32_t units = n * halves, groups = (units + 7) / 8;
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (uint32_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const uint32_t u = g * 8 + warp;
+    bool searching = false;
+    uint32_t self = 0, id = 0;
+    if (u < units) {
+      const REntry e = hv.R[halves == 2 ? (u >> 1) : u];
+      const uint32_t slot = (halves == 2 ? (u & 1) * 32 : 0) + lane;
+      searching = (e.bits >> slot) & 1;
+      self = (e.block << 6) | slot;
+    }
+    float xi = 0, yi = 0, zi = 0, mi = 0;
+    if (searching) {
+      xi = F<float>(hv, self, a.off[CX]);
+      yi = F<float>(hv, self, a.off[CY]);
+      zi = F<float>(hv, self, a.off[CZ]);
+      mi = F<float>(hv, self, a.off[CM]);
+      id = F<int32_t>(hv, self, a.off[CID]);
+    }
+    uint32_t pick = kNull;
+    for (uint32_t base = 0; base < a.n0; base += NB_TILE) {
+      if (!__syncthreads_or(searching)) break;
+      if (base + threadIdx.x < a.n0) tile[threadIdx.x] = a.S[base + threadIdx.x];
+      __syncthreads();
+      const uint32_t cnt = a.n0 - base < NB_TILE ? a.n0 - base : NB_TILE;
+      if (searching) {
+        for (uint32_t k = 0; k < cnt; ++k) {
+          const float4 p = tile[k];
+          const uint32_t j = base + k;
+          if (!(p.w > 0.0f) || !(p.w < mi || (p.w == mi && j < id))) continue;
+          const float dx = fs(p.x, xi), dy = fs(p.y, yi), dz = fs(p.z, zi);
+          float d2 = fm(dx, dx);
+          d2 = fa(d2, fm(dy, dy));
+          d2 = fa(d2, fm(dz, dz));
+          if (d2 < a.R2) { pick = j; searching = false; break; }
+        }
+      }
+    }
+    if (pick != kNull) atomicMin(a.tgt + pick, id);
+  }
+}
+
+struct MergePerform {
+  using Args = NBodyArgs;
+  __device__ static void run(const HeapView& hv, const Args& a, uint32_t, uint32_t self) {
+    const uint32_t id = F<int32_t>(hv, self, a.off[CID]);
+    const uint32_t t = a.tgt[id];
+    if (t == kNull || a.tgt[t] != kNull) return;
+    const uint32_t th = a.hmap[t];
+    const float my = F<float>(hv, self, a.off[CM]);
+    float& mt = F<float>(hv, th, a.off[CM]);
+    const float nm = fa(my, mt);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float& vt = F<float>(hv, th, a.off[CVX + d]);
+      const float vy = F<float>(hv, self, a.off[CVX + d]);
+      vt = __fdiv_rn(fa(fm(vy, my), fm(vt, mt)), nm);
+      float& xt = F<float>(hv, th, a.off[CX + d]);
+      xt = __fdiv_rn(fa(F<float>(hv, self, a.off[CX + d]), xt), 2.0f);
+    }
+    mt = nm;
+    atomicAdd(a.merges, 1ull);
+    smmo_delete(hv, self);
+  }
+};
+
+// id-indexed export of (x, y, z, vx, vy, vz, m) into buf (7 arrays of n0)
+// and live flags into the byte array after them.
+struct Export {
+  using Args = NBodyArgs;
+  __device__ static void run(const HeapView& hv, const Args& a, uint32_t, uint32_t self) {
+    const uint32_t id = F<int32_t>(hv, self, a.off[CID]);
+    for (int k = 0; k < 7; ++k) a.buf[(size_t)k * a.n0 + id] = F<float>(hv, self, a.off[k]);
+    reinterpret_cast<uint8_t*>(a.buf + (size_t)7 * a.n0)[id] = 1;
+  }
+};
+
+// Checkpoint save / restore of (x, v) by id into buf (6 arrays of n0).
+struct SaveState {
+  using Args = NBodyArgs;
+  __device__ static void run(const HeapView& hv, const Args& a, uint32_t, uint32_t self) {
+    const uint32_t id = F<int32_t>(hv, self, a.off[CID]);
+    for (int k = 0; k < 6; ++k) a.buf[(size_t)k * a.n0 + id] = F<float>(hv, self, a.off[k]);
+  }
+};
+
+struct LoadState {
+  using Args = NBodyArgs;
+  __device__ static void run(const HeapView& hv, const Args& a, uint32_t, uint32_t self) {
+    const uint32_t id = F<int32_t>(hv, self, a.off[CID]);
+    for (int k = 0; k < 6; ++k) F<float>(hv, self, a.off[k]) = a.buf[(size_t)k * a.n0 + id];
+  }
+};
+
+// Loss term and adjoint initialisation at the final state:
+// ke = 1/2 m |v|^2 (double), lambda_x = 0, lambda_v = m v.
+struct AdjInit {
+  using Args = NBodyArgs;
+  __device__ static void run(const HeapView& hv, const Args& a, uint32_t, uint32_t self) {
+    const uint32_t id = F<int32_t>(hv, self, a.off[CID]);
+    const float m = F<float>(hv, self, a.off[CM]);
+    double ke = 0;
+    for (int d = 0; d < 3; ++d) {
+      const float v = F<float>(hv, self, a.off[CVX + d]);
+      ke += (double)v * (double)v;
+      F<float>(hv, self, a.off[CLX + d]) = 0.0f;
+      F<float>(hv, self, a.off[CLVX + d]) = m * v;
+    }
+    a.ke[id] = 0.5 * (double)m * ke;
+  }
+};
+
+// First half of a reverse step: w = lambda_v + h lambda_x (kept in the
+// lambda_v fields), mu = dt w published by id.
+struct AdjW {
+  using Args = NBodyArgs;
+  __device__ static void run(const HeapView& hv, const Args& a, uint32_t, uint32_t self) {
+    const uint32_t id = F<int32_t>(hv, self, a.off[CID]);
+    float mu[3];
+    for (int d = 0; d < 3; ++d) {
+      float& lv = F<float>(hv, self, a.off[CLVX + d]);
+      lv = fmaf(a.h, F<float>(hv, self, a.off[CLX + d]), lv);
+      mu[d] = a.dt * lv;
+    }
+    a.A[id] = make_float4(mu[0], mu[1], mu[2], 0.0f);
+  }
+};
+
+// Pair kernel of the reverse step (tiled like the force), then
+// lambda_x += g and lambda_v = w + h lambda_x.
+__global__ void __launch_bounds__(256) k_adjoint_pair(HeapView hv, uint32_t c, NBodyArgs a) {
+  __shared__ float4 tx[NB_TILE];
+  __shared__ float4 tm[NB_TILE];
+  const uint32_t n = __ldcg(&hv.st->rcount);
+  const uint32_t cap = hv.cls[c].cap;
+  const uint32_t halves = cap > 32 ? 2u : 1u;
+  const uint32_t units = n * halves, groups = (units + 7) / 8;
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (uint32_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const uint32_t u = g * 8 + warp;
+    bool live = false;
+    uint32_t self = 0;
+    if (u < units) {
+      const REntry e = hv.R[halves == 2 ? (u >> 1) : u];
+      const uint32_t slot = (halves == 2 ? (u & 1) * 32 : 0) + lane;
+      live = (e.bits >> slot) & 1;
+      self = (e.block << 6) | slot;
+    }
+    float4 xk = make_float4(0, 0, 0, 0), mk = make_float4(0, 0, 0, 0);
+    if (live) {
+      const uint32_t id = F<int32_t>(hv, self, a.off[CID]);
+      xk = a.X1[id];
+      mk = a.A[id];
+    }
+    float gx = 0, gy = 0, gz = 0;
+    for (uint32_t base = 0; base < a.n0; base += NB_TILE) {
+      __syncthreads();
+      if (base + threadIdx.x < a.n0) {
+        tx[threadIdx.x] = a.X1[base + threadIdx.x];
+        tm[threadIdx.x] = a.A[base + threadIdx.x];
+      }
+      __syncthreads();
+      const uint32_t cnt = a.n0 - base < NB_TILE ? a.n0 - base : NB_TILE;
+      if (live) {
+        for (uint32_t k = 0; k < cnt; ++k) {
+          const float4 p = tx[k], q = tm[k];
+          const float rx = p.x - xk.x, ry = p.y - xk.y, rz = p.z - xk.z;
+          const float s2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, a.eps2)));
+          const float is = rsqrtf(s2);
+          const float is3 = is * is * is;
+          const float ux = xk.w * q.x - p.w * mk.x;
+          const float uy = xk.w * q.y - p.w * mk.y;
+          const float uz = xk.w * q.z - p.w * mk.z;
+          const float ru = fmaf(rx, ux, fmaf(ry, uy, rz * uz));
+          const float c3 = 3.0f * ru * is3 * is * is;
+          gx += ux * is3 - c3 * rx;
+          gy += uy * is3 - c3 * ry;
+          gz += uz * is3 - c3 * rz;
+        }
+      }
+    }
+    if (live) {
+      const float gg[3] = {a.G * gx, a.G * gy, a.G * gz};
+      for (int d = 0; d < 3; ++d) {
+        float& lx = F<float>(hv, self, a.off[CLX + d]);
+        lx += gg[d];
+        float& lv = F<float>(hv, self, a.off[CLVX + d]);
+        lv = fmaf(a.h, lx, lv);
+      }
+    }
+  }
+}
+
+struct GradOut {
+  using Args = NBodyArgs;
+  __device__ static void run(const HeapView& hv, const Args& a, uint32_t, uint32_t self) {
+    const uint32_t id = F<int32_t>(hv, self, a.off[CID]);
+    for (int d = 0; d < 3; ++d) a.buf[(size_t)id * 3 + d] = F<float>(hv, self, a.off[CLVX + d]);
+  }
+};
+
+}  // namespace
+
+const smmo::MethodEntry g_methods_nbody[] = {
+    SMMO_METHOD("nbody.drift_stage", DriftStage), SMMO_METHOD("nbody.stage", Stage),
+    SMMO_METHOD("nbody.merge_perform", MergePerform), SMMO_METHOD("nbody.export", Export)};
+const int g_methods_nbody_n = sizeof(g_methods_nbody) / sizeof(g_methods_nbody[0]);
+
+struct smmo_nbody {
+  smmo_heap* heap = nullptr;
+  int cls = -1;
+  uint32_t n0 = 0;
+  smmo_nbody_params p{};
+  NBodyArgs args{};
+  float4* d_S = nullptr;
+  float4* d_A = nullptr;
+  uint32_t* d_hmap = nullptr;
+  uint32_t* d_tgt = nullptr;
+  double* d_ke = nullptr;
+  unsigned long long* d_merges = nullptr;
+  float* d_ckpt = nullptr;   // nseg x 6 x n0
+  float4* d_x1 = nullptr;    // ckpt x n0
+  int fw_steps = 0, fw_ckpt = 0;
+  uint64_t steps_done = 0;
+};
+
+namespace {
+int pdo(smmo_nbody* w, method_launch_fn fn, const NBodyArgs& a, cudaStream_t s) {
+  int st = enumerate(w->heap, w->cls, s);
+  if (!st) st = fn(w->heap, w->cls, &a, s);
+  return st;
+}
+
+int tiled_grid(const smmo_heap* h) { return h->num_sms * 4; }
+
+// one drift-kick-drift step (no merge); x1 (nullable) receives the mid-step
+// staging array
+int dkd_step(smmo_nbody* w, cudaStream_t s, float4* x1) {
+  NBodyArgs a = w->args;
+  cudaError_t e = cudaMemsetAsync(w->d_S, 0, sizeof(float4) * w->n0, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = pdo(w, &launch_do_all<DriftStage>, a, s);
+  if (st) return st;
+  if (x1) {
+    e = cudaMemcpyAsync(x1, w->d_S, sizeof(float4) * w->n0, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  k_force<<<tiled_grid(w->heap), 256, 0, s>>>(w->heap->view, w->cls, a);
+  return cuda_status(cudaGetLastError());
+}
+}  // namespace
+
+extern "C" {
+
+int smmo_nbody_create(smmo_heap* heap, int64_t n, const float* const* cols,
+                      const smmo_nbody_params* p, void* stream, smmo_nbody** out) {
+  if (!heap || n < 1 || n > (1 << 26) || !cols || !p || !out) return SMMO_E_INVALID_ARG;
+  for (int k = 0; k < 7; ++k) if (!cols[k]) return SMMO_E_INVALID_ARG;
+  if (!heap->classes.empty() || heap->frozen) return SMMO_E_FROZEN;
+  cudaStream_t s = (cudaStream_t)stream;
+  smmo_nbody* w = new smmo_nbody();
+  w->heap = heap;
+  w->n0 = (uint32_t)n;
+  w->p = *p;
+  const char* names[NCOL] = {"x", "y", "z", "vx", "vy", "vz", "m", "id", "lx", "ly", "lz", "lvx", "lvy", "lvz"};
+  smmo_field_desc f[NCOL];
+  for (int k = 0; k < NCOL; ++k) f[k] = {names[k], k == CID ? SMMO_I32 : SMMO_F32, 1, -1};
+  int st = smmo_class_register(heap, "Body", f, NCOL, -1, 0, &w->cls);
+  if (!st) st = freeze(heap, s);
+  if (st) { delete w; return st; }
+  cudaError_t e = cudaMalloc(&w->d_S, sizeof(float4) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w->d_A, sizeof(float4) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w->d_hmap, sizeof(uint32_t) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w->d_tgt, sizeof(uint32_t) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w->d_ke, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w->d_merges, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(w->d_merges, 0, sizeof(unsigned long long), s);
+  int32_t* ids = nullptr;
+  if (e == cudaSuccess) e = cudaMallocAsync(&ids, sizeof(int32_t) * n, s);
+  if (e != cudaSuccess) { smmo_nbody_destroy(w); return cuda_status(e); }
+  std::vector<int32_t> hid((size_t)n);
+  for (int64_t i = 0; i < n; ++i) hid[i] = (int32_t)i;
+  e = cudaMemcpyAsync(ids, hid.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
+  float* zeros = nullptr;
+  if (e == cudaSuccess) e = cudaMallocAsync(&zeros, sizeof(float) * n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(zeros, 0, sizeof(float) * n, s);
+  if (e != cudaSuccess) { smmo_nbody_destroy(w); return cuda_status(e); }
+  const void* src[NCOL] = {cols[0], cols[1], cols[2], cols[3], cols[4], cols[5], cols[6], ids,
+                           zeros, zeros, zeros, zeros, zeros, zeros};
+  st = smmo_bulk_new(heap, w->cls, n, src, nullptr, nullptr, stream);
+  cudaFreeAsync(ids, s);
+  cudaFreeAsync(zeros, s);
+  if (st) { smmo_nbody_destroy(w); return st; }
+  NBodyArgs& a = w->args;
+  memset(&a, 0, sizeof(a));
+  a.S = w->d_S; a.A = w->d_A; a.hmap = w->d_hmap; a.tgt = w->d_tgt; a.ke = w->d_ke;
+  a.merges = w->d_merges;
+  a.n0 = (uint32_t)n;
+  a.G = p->G;
+  a.eps2 = p->eps * p->eps;
+  a.dt = p->dt;
+  a.h = 0.5f * p->dt;
+  a.R2 = p->merge_r * p->merge_r;
+  for (int k = 0; k < NCOL; ++k) a.off[k] = heap->classes[w->cls].layout.col_off[k];
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { smmo_nbody_destroy(w); return cuda_status(e); }
+  *out = w;
+  return SMMO_OK;
+}
+
+int smmo_nbody_step(smmo_nbody* w, int nsteps, void* stream) {
+  if (!w || nsteps < 0) return SMMO_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int k = 0; k < nsteps; ++k) {
+    int st = dkd_step(w, s, nullptr);
+    if (st) return st;
+    if (w->p.merge) {
+      NBodyArgs a = w->args;
+      cudaError_t e = cudaMemsetAsync(w->d_S, 0, sizeof(float4) * w->n0, s);
+      if (e != cudaSuccess) return cuda_status(e);
+      st = pdo(w, &launch_do_all<Stage>, a, s);
+      if (st) return st;
+      k_merge_prepare<<<tiled_grid(w->heap), 256, 0, s>>>(w->heap->view, w->cls, a);
+      st = cuda_status(cudaGetLastError());
+      if (!st) st = pdo(w, &launch_do_all<MergePerform>, a, s);
+      if (st) return st;
+    }
+    ++w->steps_done;
+  }
+  return SMMO_OK;
+}
+
+int smmo_nbody_export(smmo_nbody* w, float* out7, uint8_t* live, int64_t* merges, void* stream) {
+  if (!w || !out7 || !live) return SMMO_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n0 = w->n0;
+  float* buf = nullptr;
+  cudaError_t e = cudaMallocAsync(&buf, sizeof(float) * 7 * n0 + n0, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, sizeof(float) * 7 * n0 + n0, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  NBodyArgs a = w->args;
+  a.buf = buf;
+  int st = pdo(w, &launch_do_all<Export>, a, s);
+  if (!st) {
+    e = cudaMemcpyAsync(out7, buf, sizeof(float) * 7 * n0, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(live, buf + 7 * n0, n0, cudaMemcpyDeviceToDevice, s);
+    unsigned long long m = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&m, w->d_merges, sizeof(m), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e);
+    if (merges) *merges = (int64_t)m;
+  }
+  cudaFreeAsync(buf, s);
+  return st;
+}
+
+int smmo_nbody_forward_ckpt(smmo_nbody* w, int nsteps, int ckpt, double* loss, void* stream) {
+  if (!w || nsteps < 1 || ckpt < 1 || !loss || w->p.merge) return SMMO_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nseg = (nsteps + ckpt - 1) / ckpt;
+  const size_t n0 = w->n0;
+  if (w->d_ckpt) cudaFreeAsync(w->d_ckpt, s);
+  if (w->d_x1) cudaFreeAsync(w->d_x1, s);
+  w->d_ckpt = nullptr;
+  w->d_x1 = nullptr;
+  cudaError_t e = cudaMallocAsync(&w->d_ckpt, sizeof(float) * 6 * n0 * nseg, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&w->d_x1, sizeof(float4) * n0 * ckpt, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  w->fw_steps = nsteps;
+  w->fw_ckpt = ckpt;
+  NBodyArgs a = w->args;
+  for (int k = 0; k < nsteps; ++k) {
+    if (k % ckpt == 0) {
+      a.buf = w->d_ckpt + (size_t)(k / ckpt) * 6 * n0;
+      int st = pdo(w, &launch_do_all<SaveState>, a, s);
+      if (st) return st;
+    }
+    int st = dkd_step(w, s, nullptr);
+    if (st) return st;
+  }
+  e = cudaMemsetAsync(w->d_ke, 0, sizeof(double) * n0, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = pdo(w, &launch_do_all<AdjInit>, a, s);
+  if (st) return st;
+  std::vector<double> ke(n0);
+  e = cudaMemcpyAsync(ke.data(), w->d_ke, sizeof(double) * n0, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  double L = 0;
+  for (double v : ke) L += v;  // fixed (id) order
+  *loss = L;
+  return SMMO_OK;
+}
+
+int smmo_nbody_backward(smmo_nbody* w, float* grad_v0, void* stream) {
+  if (!w || !grad_v0 || !w->d_ckpt) return SMMO_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n0 = w->n0;
+  const int T = w->fw_steps, ck = w->fw_ckpt, nseg = (T + ck - 1) / ck;
+  NBodyArgs a = w->args;
+  // adjoint fields survive LoadState (which restores x and v only)
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int s0 = seg * ck, s1 = s0 + ck < T ? s0 + ck : T;
+    a.buf = w->d_ckpt + (size_t)seg * 6 * n0;
+    int st = pdo(w, &launch_do_all<LoadState>, a, s);
+    if (st) return st;
+    for (int k = s0; k < s1; ++k) {
+      st = dkd_step(w, s, w->d_x1 + (size_t)(k - s0) * n0);
+      if (st) return st;
+    }
+    for (int k = s1 - 1; k >= s0; --k) {
+      NBodyArgs b = a;
+      b.X1 = w->d_x1 + (size_t)(k - s0) * n0;
+      st = pdo(w, &launch_do_all<AdjW>, b, s);
+      if (st) return st;
+      k_adjoint_pair<<<tiled_grid(w->heap), 256, 0, s>>>(w->heap->view, w->cls, b);
+      st = cuda_status(cudaGetLastError());
+      if (st) return st;
+    }
+  }
+  a.buf = grad_v0;
+  cudaError_t e = cudaMemsetAsync(grad_v0, 0, sizeof(float) * 3 * n0, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  return pdo(w, &launch_do_all<GradOut>, a, s);
+}
+
+int smmo_nbody_destroy(smmo_nbody* w) {
+  if (!w) return SMMO_E_INVALID_ARG;
+  cudaFree(w->d_S); cudaFree(w->d_A); cudaFree(w->d_hmap); cudaFree(w->d_tgt);
+  cudaFree(w->d_ke); cudaFree(w->d_merges);
+  if (w->d_ckpt) cudaFree(w->d_ckpt);
+  if (w->d_x1) cudaFree(w->d_x1);
+  delete w;
+  return SMMO_OK;
+}
+
+}  // extern "C"

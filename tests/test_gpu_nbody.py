@@ -1,0 +1,124 @@
+"""Parity of the GPU n-body (forces, drift-kick-drift, merge) with the FP32
+oracle -- bit-exact, since both evaluate the same FP32 operations in the
+same order -- and of the GPU FP32 adjoint with the oracle's FP64 adjoint
+and with finite differences."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1908_05845_gb300 import inputs  # noqa: E402
+from paper_1908_05845_gb300.nbody import KineticEnergyAfterSteps, NBody  # noqa: E402
+
+KEYS = ("x", "y", "z", "vx", "vy", "vz", "m", "live")
+
+
+def check_equal(got, want):
+    for k in KEYS:
+        g, w = np.asarray(got[k]), np.asarray(want[k])
+        live = np.asarray(want["live"]) == 1
+        assert np.array_equal(g[live], w[live]), k
+    assert np.array_equal(np.asarray(got["live"]), np.asarray(want["live"]))
+
+
+@pytest.mark.parametrize("N,T,R", [(512, 20, 2e-2), (1000, 30, 2e-2), (2049, 10, 1e-2)])
+def test_nbody_bit_exact_with_merges(orc, N, T, R):
+    st = inputs.nbody_initial(N, 3)
+    sim = NBody(st, merge_r=R)
+    sim.step(T)
+    got, merges = sim.read()
+    want, k = orc.nbody_run_f32(st, T, merge_r=R)
+    assert merges == k.sum() and merges > 0
+    check_equal(got, want)
+    assert sim.heap.check() == 0
+    sim.sync()
+
+
+def test_nbody_full_size_sampled_step(orc):
+    N = 65536
+    st = inputs.nbody_initial(N, 1)
+    sim = NBody(st, merge=False)
+    sim.step(1)
+    got, _ = sim.read()
+    idx = np.random.default_rng(0).choice(N, 192, replace=False)
+    want = orc.nbody_step_sample_f32(st, idx)
+    for c, k in enumerate(("x", "y", "z", "vx", "vy", "vz")):
+        assert np.array_equal(got[k][idx], want[:, c]), k
+
+
+def test_nbody_full_size_merge_bookkeeping():
+    N = 65536
+    st = inputs.nbody_initial(N, 1)
+    sim = NBody(st)
+    sim.step(10)
+    got, merges = sim.read()
+    live = got["live"] == 1
+    assert (~live).sum() == merges
+    m0 = st["m"].astype(np.float64).sum()
+    assert abs(got["m"][live].astype(np.float64).sum() - m0) / m0 < 1e-5
+    assert sim.heap.stats()["live_objects"][0] == N - merges
+    sim.sync()
+
+
+def _pos(st):
+    return np.stack([st["x"], st["y"], st["z"]], 1).astype(np.float64)
+
+
+def _vel(st):
+    return np.stack([st["vx"], st["vy"], st["vz"]], 1).astype(np.float64)
+
+
+@pytest.mark.parametrize("N", [256, 4096])
+def test_adjoint_vs_fp64_sweep_on_the_same_trajectory(orc, N):
+    """50 steps: the GPU FP32 adjoint against the oracle's FP64 reverse
+    sweep along the (bit-identical) FP32 forward trajectory."""
+    st = inputs.nbody_initial(N, 1)
+    sim = NBody(st, merge=False)
+    L = sim.forward_ckpt(50, 10)
+    g = sim.backward().cpu().numpy().astype(np.float64)
+    sim.sync()
+    gref, Lref = orc.nbody_adjoint_f32traj(st, 50)
+    assert abs(L - Lref) / abs(Lref) < 1e-6
+    assert np.linalg.norm(g - gref) / np.linalg.norm(gref) < 1e-3
+
+
+def test_adjoint_vs_fp64_adjoint_short_horizon(orc):
+    """10 steps, where FP32 and FP64 trajectories still agree: the GPU FP32
+    adjoint against the FP64 adjoint of the FP64 trajectory."""
+    N = 4096
+    st = inputs.nbody_initial(N, 1)
+    sim = NBody(st, merge=False)
+    sim.forward_ckpt(10, 10)
+    g = sim.backward().cpu().numpy().astype(np.float64)
+    gref, _ = orc.nbody_adjoint_f64(_pos(st), _vel(st), st["m"].astype(np.float64), 10, ckpt=10)
+    assert np.linalg.norm(g - gref) / np.linalg.norm(gref) < 1e-3
+
+
+def test_autograd_function(orc):
+    N = 256
+    st = inputs.nbody_initial(N, 2)
+    x0 = torch.tensor(_pos(st), dtype=torch.float32, device="cuda")
+    v0 = torch.tensor(_vel(st), dtype=torch.float32, device="cuda", requires_grad=True)
+    m = torch.tensor(st["m"], dtype=torch.float32, device="cuda")
+    loss = KineticEnergyAfterSteps.apply(v0, x0, m, 10, 5)
+    loss.backward()
+    g = v0.grad.cpu().numpy().astype(np.float64)
+    # central differences of the FP64 loss (Richardson-extrapolated)
+    pos, vel, mm = _pos(st), _vel(st), st["m"].astype(np.float64)
+    rng = np.random.default_rng(3)
+    comps = rng.choice(3 * N, size=48, replace=False)
+    fd = np.zeros(comps.size)
+    for n, kk in enumerate(comps):
+        i, c = divmod(int(kk), 3)
+        hh = 1e-7 * max(1.0, abs(vel[i, c]))
+
+        def central(step):
+            vp, vm = vel.copy(), vel.copy()
+            vp[i, c] += step
+            vm[i, c] -= step
+            return (orc.nbody_loss_f64(pos, vp, mm, 10) - orc.nbody_loss_f64(pos, vm, mm, 10)) / (2 * step)
+
+        fd[n] = (4 * central(hh / 2) - central(hh)) / 3
+    gs = g.reshape(-1)[comps]
+    assert np.linalg.norm(gs - fd) / np.linalg.norm(fd) < 1e-3

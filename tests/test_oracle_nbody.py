@@ -171,3 +171,26 @@ def test_adjoint_checkpoint_invariance(orc):
     g2, _ = orc.nbody_adjoint_f64(pos, vel, m, 23, ckpt=10)
     g3, _ = orc.nbody_adjoint_f64(pos, vel, m, 23, ckpt=23)
     assert np.array_equal(g1, g2) and np.array_equal(g2, g3)
+
+
+def test_sampled_step_equals_full_step(orc):
+    st = inputs.nbody_initial(300, 4)
+    full, _ = orc.nbody_run_f32(st, 1, merge=False)
+    idx = np.array([0, 7, 123, 299])
+    samp = orc.nbody_step_sample_f32(st, idx)
+    for q, i in enumerate(idx):
+        want = [full[k][i] for k in ("x", "y", "z", "vx", "vy", "vz")]
+        assert np.array_equal(samp[q], np.array(want, np.float32))
+
+
+def test_f32_trajectory_sweep_agrees_with_f64_adjoint_on_short_horizon(orc):
+    """Over a few steps the FP32 and FP64 trajectories agree closely, so the
+    FP64 sweep along the FP32 trajectory must equal the FP64 adjoint up to
+    that divergence (measured: 5e-6 after 2 steps, 2e-4 after 10)."""
+    st = inputs.nbody_initial(128, 5)
+    pos, vel, m = as64(st)
+    for T, tol in ((2, 2e-5), (10, 1e-3)):
+        g64, L64 = orc.nbody_adjoint_f64(pos, vel, m, T, ckpt=5)
+        g32, L32 = orc.nbody_adjoint_f32traj(st, T)
+        assert abs(L32 - L64) / L64 < 1e-5
+        assert np.linalg.norm(g32 - g64) / np.linalg.norm(g64) < tol
