@@ -346,6 +346,233 @@ def run_e2e(args, seed, hb):
                                        "counter read-back each, D2H of final state"}
 
 
+# ------------------------------------------------------------ other workloads
+def _events(stream):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    return a, b
+
+
+def batched_init(seed, n):
+    from paper_1908_05845_gb300 import inputs
+    from paper_1908_05845_gb300.workloads import LIFE
+    kinds, sides = inputs.batched_instances(seed, n)
+    ks, ags, ens, sts = [], [], [], []
+    for i, (kd, sd) in enumerate(zip(kinds, sides)):
+        if kd == LIFE:
+            k, s = inputs.gol_initial(sd, sd, seed, inst=i)
+            a = np.zeros(sd * sd, np.int16)
+            e = np.zeros(sd * sd, np.int16)
+        else:
+            k, a, e = inputs.wator_initial(sd, sd, seed, inst=i)
+            s = np.zeros(sd * sd, np.uint8)
+        ks.append(k.astype(np.int8)); ags.append(a); ens.append(e); sts.append(s)
+    return kinds, sides, (np.concatenate(ks), np.concatenate(ags), np.concatenate(ens), np.concatenate(sts))
+
+
+def run_batched(args):
+    """256 Life/Wa-Tor instances (sides log-uniform 64..1024) on one heap,
+    one step = one captured CUDA graph (one parallel_do per class per phase
+    over all instances), against the same instances on separate heaps stepped
+    one instance at a time (plain launches, and one graph per instance)."""
+    import torch
+    from paper_1908_05845_gb300 import autotune, smmo
+    from paper_1908_05845_gb300.workloads import World, heap_bytes_for
+    n_inst = args.instances
+    kinds, sides, init = batched_init(SEED, n_inst)
+    total = int(np.sum(sides.astype(np.int64) ** 2))
+    sample = np.arange(0, n_inst, 8)
+    sk, ss = kinds[sample], sides[sample]
+    offs = np.concatenate([[0], np.cumsum(sides.astype(np.int64) ** 2)])
+    samp_init = tuple(np.concatenate([x[offs[i]:offs[i + 1]] for i in sample]) for x in init)
+    cfg, _ = autotune.tune("batched_life_wator", sk, ss, SEED, samp_init, use_cache=not args.retune)
+    stream = torch.cuda.Stream()
+    res = {}
+    with torch.cuda.stream(stream):
+        # batched: one heap, one graph per step
+        w = World(kinds, sides, sides, SEED, *init, config=smmo.default_config(**cfg),
+                  heap_bytes=heap_bytes_for(total), stream=stream)
+        w.step(args.warmup)
+        w.capture(1)
+        e0 = w.heap.counters()[0]
+        a, b = _events(stream)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.steps):
+            w.replay()
+        b.record(stream)
+        b.synchronize()
+        t_b = a.elapsed_time(b) / 1e3
+        objs = w.heap.counters()[0] - e0
+        w.sync()
+        k_gpu, a_gpu, e_gpu, s_gpu, err = w.export()
+        res["batched"] = objs / t_b
+        steps_done = args.warmup + args.steps
+        w.close()
+        # per-instance heaps
+        worlds = []
+        for i in range(n_inst):
+            sl = slice(offs[i], offs[i + 1])
+            worlds.append(World([kinds[i]], [sides[i]], [sides[i]], SEED, *(x[sl] for x in init),
+                                config=smmo.default_config(**cfg),
+                                heap_bytes=heap_bytes_for(int(sides[i]) ** 2), stream=stream))
+        # instance ids: every per-instance world draws with instance 0; the
+        # batched one with the instance index, so only timing is compared
+        for x in worlds:
+            x.step(args.warmup)
+        e0 = sum(x.heap.counters()[0] for x in worlds)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.steps):
+            for x in worlds:
+                x.step(1)
+        b.record(stream)
+        b.synchronize()
+        t_p = a.elapsed_time(b) / 1e3
+        objs_p = sum(x.heap.counters()[0] for x in worlds) - e0
+        res["per_instance_launches"] = objs_p / t_p
+        for x in worlds:
+            x.capture(1)
+        e0 = sum(x.heap.counters()[0] for x in worlds)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.steps):
+            for x in worlds:
+                x.replay()
+        b.record(stream)
+        b.synchronize()
+        t_g = a.elapsed_time(b) / 1e3
+        objs_g = sum(x.heap.counters()[0] for x in worlds) - e0
+        res["per_instance_graphs"] = objs_g / t_g
+        for x in worlds:
+            x.close()
+    # parity of a sample of instances against the oracle
+    import oracle
+    from paper_1908_05845_gb300.workloads import LIFE
+    checked = []
+    for i in [int(j) for j in np.argsort(sides)[:3]]:
+        sl = slice(offs[i], offs[i + 1])
+        sd = int(sides[i])
+        if kinds[i] == LIFE:
+            wk, ws, _ = oracle.gol_run(sd, sd, init[0][sl].astype(np.uint8), init[3][sl], steps_done)
+            ok = np.array_equal(k_gpu[sl].astype(np.uint8), wk) and np.array_equal(s_gpu[sl], ws)
+        else:
+            wk, wa, we, _ = oracle.wator_run(sd, sd, SEED, init[0][sl], init[1][sl], init[2][sl], steps_done, inst=i)
+            ok = np.array_equal(k_gpu[sl], wk) and np.array_equal(a_gpu[sl], wa) and np.array_equal(e_gpu[sl], we)
+        checked.append({"instance": i, "side": sd, "kind": "life" if kinds[i] == LIFE else "wator", "bit_exact": bool(ok)})
+    line = {"metric": "object-updates/s", "value": res["batched"], "unit": "object-updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_b / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/int16",
+            "data": "synthetic (seeded Philox)",
+            "config": {"workload": "batched_%d_instances" % n_inst, "cells": total,
+                       "life_instances": int((kinds == LIFE).sum()), "tuned": cfg,
+                       "l2": "working set larger than L2"},
+            "per_instance_launches": res["per_instance_launches"],
+            "per_instance_graphs": res["per_instance_graphs"],
+            "speedup_vs_per_instance_launches": res["batched"] / res["per_instance_launches"],
+            "speedup_vs_per_instance_graphs": res["batched"] / res["per_instance_graphs"],
+            "export_errors": int(err), "parity_sample": checked}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gol(args):
+    import torch
+    from paper_1908_05845_gb300 import inputs
+    from paper_1908_05845_gb300.workloads import Life
+    k, s = inputs.gol_initial(256, 256, SEED)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        w = Life(256, 256, k, s, stream=stream)
+        w.capture(1)
+        e0 = w.heap.counters()[0]
+        a, b = _events(stream)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.steps):
+            w.replay()
+        b.record(stream)
+        b.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        objs = w.heap.counters()[0] - e0
+        w.sync()
+    print(json.dumps({"metric": "object-updates/s", "value": objs / t, "unit": "object-updates/s",
+                      "ms_per_step": 1e3 * t / args.steps, "steps": args.steps,
+                      "config": {"workload": "life_256x256", "graph": "one CUDA graph per generation"}}),
+          flush=True)
+    return 0
+
+
+def run_nasch(args):
+    import torch
+    from paper_1908_05845_gb300 import inputs
+    from paper_1908_05845_gb300.workloads import Traffic
+    g = inputs.nasch_graph(SEED)
+    v = inputs.nasch_cars(g, SEED)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        w = Traffic(g, SEED, v, stream=stream)
+        w.step(args.warmup)
+        e0, a0, f0 = w.heap.counters()
+        a, b = _events(stream)
+        torch.cuda.synchronize()
+        a.record(stream)
+        w.step(args.steps)
+        b.record(stream)
+        b.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        e1, a1, f1 = w.heap.counters()
+        w.sync()
+    print(json.dumps({"metric": "object-updates/s", "value": (e1 - e0) / t, "unit": "object-updates/s",
+                      "alloc_free_per_s": ((a1 - a0) + (f1 - f0)) / t, "ms_per_step": 1e3 * t / args.steps,
+                      "steps": args.steps, "config": {"workload": "nasch_2000_streets", "cells": g["num_cells"],
+                                                      "cars": int((v >= 0).sum())}}), flush=True)
+    return 0
+
+
+def run_nbody(args):
+    import torch
+    from paper_1908_05845_gb300 import inputs
+    from paper_1908_05845_gb300.nbody import NBody
+    N = 65536
+    st = inputs.nbody_initial(N, SEED)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        w = NBody(st, stream=stream)
+        w.step(args.warmup)
+        a, b = _events(stream)
+        torch.cuda.synchronize()
+        a.record(stream)
+        w.step(args.steps)
+        b.record(stream)
+        b.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        got, merges = w.read()
+        live = int(got["live"].sum())
+        w.close()
+        # adjoint cost: forward with checkpoints vs reverse sweep (50 steps)
+        w = NBody(st, merge=False, stream=stream)
+        a.record(stream)
+        w.forward_ckpt(50, 10)
+        b.record(stream)
+        b.synchronize()
+        t_f = a.elapsed_time(b) / 1e3
+        a.record(stream)
+        w.backward()
+        b.record(stream)
+        b.synchronize()
+        t_b = a.elapsed_time(b) / 1e3
+        w.close()
+    pairs = float(N) * N * args.steps
+    print(json.dumps({"metric": "pair-interactions/s", "value": pairs / t, "unit": "pairs/s",
+                      "ms_per_step": 1e3 * t / args.steps, "steps": args.steps, "merges": merges,
+                      "live_after": live, "adjoint_backward_over_forward": t_b / t_f,
+                      "forward_ckpt_ms_per_step": 1e3 * t_f / 50, "backward_ms_per_step": 1e3 * t_b / 50,
+                      "config": {"workload": "nbody_65536_merge", "note": "force + merge search are both O(N^2)"}}),
+          flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -355,10 +582,19 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="wator", choices=["wator", "batched", "gol", "nasch", "nbody"])
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--retune", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.workload != "wator":
+        import torch
+        torch.cuda.set_device(local)
+        from paper_1908_05845_gb300 import smmo
+        smmo.lib()
+        return {"batched": run_batched, "gol": run_gol, "nasch": run_nasch, "nbody": run_nbody}[args.workload](args)
     return run_gpu(args, ws, rank, local)
 
 

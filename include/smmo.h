@@ -95,8 +95,8 @@ typedef struct {
    * of bitmap spin loops.  Defaults 4096 and 1 << 20. */
   int32_t alloc_retries;
   int32_t bitmap_spins;
-  /* parallel_do launch shape: threads per CTA (multiple of 64) and CTAs
-   * per SM of the persistent grid.  Defaults 256 and 8. */
+  /* parallel_do launch shape: threads per CTA (multiple of 64, at most
+   * 512) and CTAs per SM of the persistent grid.  Defaults 256 and 8. */
   int32_t threads_per_cta;
   int32_t ctas_per_sm;
   /* 1 = device code checks handles and indices and records the first
@@ -300,6 +300,13 @@ int smmo_world_step(smmo_world* w, int nsteps, void* stream);
  * at its agent) into *errors (host, nullable).  Synchronises `stream`. */
 int smmo_world_export(smmo_world* w, int8_t* kind, int16_t* age, int16_t* energy,
                       uint8_t* state, int64_t* errors, void* stream);
+/* Captures nsteps steps of the world into a CUDA graph (the step counter
+ * lives in device memory, so every replay advances the simulation by
+ * nsteps steps).  `stream` must be a non-default stream; nothing runs
+ * during the capture.  smmo_world_replay launches the graph on `stream`
+ * (asynchronous). */
+int smmo_world_capture(smmo_world* w, int nsteps, void* stream);
+int smmo_world_replay(smmo_world* w, void* stream);
 /* As smmo_world_step, and additionally records CUDA events on `stream`
  * around every enumeration and do-all kernel and adds their durations (ms)
  * to phase_ms (host, 16 doubles, accumulated): index 2*p is the

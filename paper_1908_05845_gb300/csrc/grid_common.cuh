@@ -50,20 +50,31 @@ __device__ __forceinline__ const Inst* find_inst(const Inst* tab, uint32_t n, ui
 }
 
 // The Cell objects are created by one bulk_new into consecutive blocks of
-// capacity 64, so cell g is object slot g % 64 of block cell_b0 + g / 64.
+// capacity N = 2^shift (32 or 64), so cell g is object slot g % N of block
+// b0 + g / N.
 struct CellRef {
   uint8_t* data;
   uint32_t block_bytes;
   uint32_t b0;
+  uint32_t shift;
   __device__ __forceinline__ uint8_t* blk(uint32_t g) const {
-    return data + (size_t)(b0 + (g >> 6)) * block_bytes;
+    return data + (size_t)(b0 + (g >> shift)) * block_bytes;
   }
   template <class T>
   __device__ __forceinline__ T* col(uint32_t g, uint32_t off) const {
-    return reinterpret_cast<T*>(blk(g) + off) + (g & 63);
+    return reinterpret_cast<T*>(blk(g) + off) + (g & ((1u << shift) - 1));
   }
-  __device__ __forceinline__ uint32_t handle(uint32_t g) const { return ((b0 + (g >> 6)) << 6) | (g & 63); }
+  __device__ __forceinline__ uint32_t handle(uint32_t g) const {
+    return ((b0 + (g >> shift)) << 6) | (g & ((1u << shift) - 1));
+  }
+  __device__ __forceinline__ uint32_t cell_of(uint32_t handle) const {
+    return (((handle >> 6) - b0) << shift) | (handle & 63);
+  }
 };
+
+// The step counter lives in device memory so that a captured step graph
+// advances it on every replay; this kernel opens a step (t <- t + 1).
+static __global__ void k_step_begin(uint32_t* t) { *t += 1; }
 
 // Torus neighbour of local cell (x, y) in direction d:
 // 0 = (0,-1), 1 = (+1,0), 2 = (0,+1), 3 = (-1,0).

@@ -503,7 +503,7 @@ int smmo_heap_create(const smmo_heap_config* cfg, void* dev_buf, size_t buf_byte
   smmo_heap_config c;
   smmo_heap_config_default(&c);
   if (cfg) c = *cfg;
-  if (c.threads_per_cta <= 0 || c.threads_per_cta % 64 || c.threads_per_cta > 1024 ||
+  if (c.threads_per_cta <= 0 || c.threads_per_cta % 64 || c.threads_per_cta > 512 ||
       c.ctas_per_sm <= 0 || c.lookup_retries < 1 || c.alloc_retries < 1 || c.bitmap_spins < 1)
     return SMMO_E_INVALID_ARG;
   smmo_heap* h = new smmo_heap();

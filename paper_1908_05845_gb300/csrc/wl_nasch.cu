@@ -38,7 +38,7 @@ struct TrafficArgs {
   uint32_t c_cell, c_street, c_v, c_route, c_cross;
   uint32_t s_street;      // Source.street column offset
   uint64_t seed;
-  uint32_t t, key_hi;
+  const uint32_t* tp;  // device step counter
   int32_t v_max;
   uint32_t brake_threshold;
   int32_t sinks_enabled;
@@ -63,8 +63,9 @@ struct CarPrepare {
     const int32_t p = c - st;
     int v = *vp + 1 < a.v_max ? *vp + 1 : a.v_max;
     int32_t o = -1;
+    const uint32_t t = *a.tp;
     if (dg > 0) {
-      const uint32_t r = philox_draw(a.seed, TAG_ROUTE, a.t, (uint32_t)(st + L - 1), 0);
+      const uint32_t r = philox_draw(a.seed, TAG_ROUTE, t, (uint32_t)(st + L - 1), 0);
       o = __ldg(a.out + 3 * s + (int)(r % (uint32_t)dg));
     }
     int free_run = 0;
@@ -79,10 +80,10 @@ struct CarPrepare {
       free_run = k;
     }
     v = free_run;
-    if (v > 0 && philox_draw(a.seed, TAG_BRAKE, a.t, (uint32_t)c, 0) < a.brake_threshold) --v;
+    if (v > 0 && philox_draw(a.seed, TAG_BRAKE, t, (uint32_t)c, 0) < a.brake_threshold) --v;
     const bool cross = o >= 0 && p + v >= L;
     if (cross)
-      atomicMin(a.claim + o, ((unsigned long long)a.key_hi << 32) | (uint32_t)c);
+      atomicMin(a.claim + o, ((unsigned long long)(0xFFFFFFFFu - t) << 32) | (uint32_t)c);
     *vp = (int8_t)v;
     *fld<int32_t>(h, self, a.c_route) = o;
     *fld<uint8_t>(h, self, a.c_cross) = cross ? 1 : 0;
@@ -101,7 +102,7 @@ struct CarMove {
     int v = *vp;
     const int32_t o = *fld<int32_t>(h, self, a.c_route);
     bool cross = *fld<uint8_t>(h, self, a.c_cross);
-    if (cross && a.claim[o] != (((unsigned long long)a.key_hi << 32) | (uint32_t)c)) {
+    if (cross && a.claim[o] != (((unsigned long long)(0xFFFFFFFFu - *a.tp) << 32) | (uint32_t)c)) {
       v = L - 1 - p;  // lost the claim: stop on the last cell of the street
       cross = false;
       *vp = (int8_t)v;
@@ -171,6 +172,7 @@ struct smmo_traffic {
   int32_t* d_tab = nullptr;  // start | len | deg | out[3]
   unsigned long long* d_claim = nullptr;
   uint32_t t = 0;
+  uint32_t* d_t = nullptr;
   TrafficArgs args{};
 };
 
@@ -227,6 +229,8 @@ int smmo_traffic_create(smmo_heap* heap, int num_streets, const int32_t* street_
   }
   cudaError_t e = cudaMalloc(&w->d_tab, sizeof(int32_t) * tab.size());
   if (e == cudaSuccess) e = cudaMalloc(&w->d_claim, sizeof(unsigned long long) * num_streets);
+  if (e == cudaSuccess) e = cudaMalloc(&w->d_t, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(w->d_t, 0, sizeof(uint32_t), s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(w->d_tab, tab.data(), sizeof(int32_t) * tab.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(w->d_claim, 0xFF, sizeof(unsigned long long) * num_streets, s);
   if (e != cudaSuccess) { smmo_traffic_destroy(w); return cuda_status(e); }
@@ -251,6 +255,8 @@ int smmo_traffic_create(smmo_heap* heap, int num_streets, const int32_t* street_
   a.cells.data = heap->view.data;
   a.cells.block_bytes = heap->view.block_bytes;
   a.cells.b0 = (uint32_t)first;
+  a.cells.shift = 6;
+  a.tp = w->d_t;
   a.occ_off = heap->classes[w->cls_cell].layout.col_off[0];
   const ClassLayout& K = heap->classes[w->cls_car].layout;
   a.car_cls = w->cls_car;
@@ -305,9 +311,10 @@ int smmo_traffic_step(smmo_traffic* w, int nsteps, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   TrafficArgs a = w->args;
   for (int k = 0; k < nsteps; ++k) {
-    a.t = ++w->t;
-    a.key_hi = 0xFFFFFFFFu - a.t;
-    int st = pdo(w, w->cls_car, &launch_do_all<CarPrepare>, a, s);
+    ++w->t;
+    k_step_begin<<<1, 1, 0, s>>>(w->d_t);
+    int st = cuda_status(cudaGetLastError());
+    if (!st) st = pdo(w, w->cls_car, &launch_do_all<CarPrepare>, a, s);
     if (!st) st = pdo(w, w->cls_car, &launch_do_all<CarMove>, a, s);
     if (!st) st = pdo(w, w->cls_src, &launch_do_all<SourceSpawn>, a, s);
     if (st) return st;
@@ -355,6 +362,7 @@ int smmo_traffic_destroy(smmo_traffic* w) {
   if (!w) return SMMO_E_INVALID_ARG;
   if (w->d_tab) cudaFree(w->d_tab);
   if (w->d_claim) cudaFree(w->d_claim);
+  if (w->d_t) cudaFree(w->d_t);
   delete w;
   return SMMO_OK;
 }

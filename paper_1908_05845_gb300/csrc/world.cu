@@ -39,7 +39,8 @@ struct WorldArgs {
   uint32_t a_cell, a_action, a_isnew;
   uint32_t c_cell, c_action;
   uint64_t seed;
-  uint32_t t, key_hi;
+  const uint32_t* tp;  // device step counter (1-based during a step)
+  uint32_t phase;      // 0 fish, 1 shark
   int32_t fish_breed, shark_breed, starve, breed_strict;
   int8_t* out_kind;
   int16_t* out_age;
@@ -62,8 +63,8 @@ __device__ __forceinline__ T* fld(const HeapView& h, uint32_t self, uint32_t off
 // key = ((0xFFFFFFFF - phase) << 32) | s with atomicMin; the smallest key of
 // the current phase wins (lowest source cell), keys of older phases are
 // larger and never win, so no pass over all cells is needed to reset them.
-__device__ __forceinline__ unsigned long long req_key(uint32_t key_hi, uint32_t src) {
-  return ((unsigned long long)key_hi << 32) | src;
+__device__ __forceinline__ unsigned long long req_key(uint32_t t, uint32_t phase, uint32_t src) {
+  return ((unsigned long long)(0xFFFFFFFFu - (2u * t + phase)) << 32) | src;
 }
 
 struct FishPrepare {
@@ -84,9 +85,10 @@ struct FishPrepare {
     }
     uint32_t tgt = g;
     if (nc) {
-      const uint32_t r = philox_draw(a.seed, TAG_FISH, a.t, lc, in->id);
+      const uint32_t t = *a.tp;
+      const uint32_t r = philox_draw(a.seed, TAG_FISH, t, lc, in->id);
       tgt = cand[r % (uint32_t)nc];
-      atomicMin(a.cells.col<unsigned long long>(tgt, a.req_off), req_key(a.key_hi, g));
+      atomicMin(a.cells.col<unsigned long long>(tgt, a.req_off), req_key(t, a.phase, g));
     }
     *fld<int32_t>(h, self, a.f_target) = (int32_t)tgt;
   }
@@ -99,7 +101,7 @@ struct FishUpdate {
     const uint32_t g = *cellp;
     const uint32_t tgt = *fld<int32_t>(h, self, a.f_target);
     if (tgt == g) return;
-    if (*a.cells.col<unsigned long long>(tgt, a.req_off) != req_key(a.key_hi, g)) return;
+    if (*a.cells.col<unsigned long long>(tgt, a.req_off) != req_key(*a.tp, a.phase, g)) return;
     *a.cells.col<uint32_t>(tgt, a.occ_off) = self;
     *cellp = (int32_t)tgt;
     int16_t* agep = fld<int16_t>(h, self, a.f_age);
@@ -143,9 +145,10 @@ struct SharkPrepare {
         else if (type_of(h, o) == a.fish) fishc[nf++] = n;
       }
       if (nf || ne) {
-        const uint32_t r = philox_draw(a.seed, TAG_SHARK, a.t, lc, in->id);
+        const uint32_t t = *a.tp;
+        const uint32_t r = philox_draw(a.seed, TAG_SHARK, t, lc, in->id);
         tgt = nf ? fishc[r % (uint32_t)nf] : emptyc[r % (uint32_t)ne];
-        atomicMin(a.cells.col<unsigned long long>(tgt, a.req_off), req_key(a.key_hi, g));
+        atomicMin(a.cells.col<unsigned long long>(tgt, a.req_off), req_key(t, a.phase, g));
       }
     }
     *fld<int32_t>(h, self, a.s_target) = (int32_t)tgt;
@@ -165,7 +168,7 @@ struct SharkUpdate {
     }
     const uint32_t tgt = *fld<int32_t>(h, self, a.s_target);
     if (tgt == g) return;
-    if (*a.cells.col<unsigned long long>(tgt, a.req_off) != req_key(a.key_hi, g)) return;
+    if (*a.cells.col<unsigned long long>(tgt, a.req_off) != req_key(*a.tp, a.phase, g)) return;
     uint32_t* tocc = a.cells.col<uint32_t>(tgt, a.occ_off);
     const uint32_t prey = *tocc;
     if (prey != kNull) {  // eat the fish (deleting an object of another class)
@@ -379,7 +382,7 @@ struct Link {
 struct CheckCells {
   using Args = WorldArgs;
   __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
-    const uint32_t g = ((self >> 6) - a.cells.b0) * 64 + (self & 63);
+    const uint32_t g = a.cells.cell_of(self);
     const uint32_t o = *a.cells.col<uint32_t>(g, a.occ_off);
     if (o == kNull) return;
     const uint32_t t = type_of(h, o);
@@ -415,6 +418,9 @@ struct smmo_world {
   Inst* d_linst = nullptr;
   uint32_t nw = 0, nl = 0;
   uint32_t t = 0;  // steps done
+  uint32_t* d_t = nullptr;  // device step counter
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
   WorldArgs args{};
   smmo_wator_params p{};
 };
@@ -454,9 +460,9 @@ int pdo(smmo_world* w, int cls, method_launch_fn fn, const WorldArgs& a, cudaStr
 int world_steps(smmo_world* w, int nsteps, cudaStream_t s, PhaseTimer* pt) {
   WorldArgs a = w->args;
   for (int k = 0; k < nsteps; ++k) {
-    const uint32_t t = ++w->t;
-    a.t = t;
-    int st = SMMO_OK;
+    ++w->t;
+    k_step_begin<<<1, 1, 0, s>>>(w->d_t);
+    int st = cuda_status(cudaGetLastError());
     if (w->nl) {  // one Life generation (Sec. 7.8, four do-alls)
       st = pdo(w, w->cls_cand, &launch_do_all<CandPrepare>, a, s, pt, 0);
       if (!st) st = pdo(w, w->cls_alive, &launch_do_all<AlivePrepare>, a, s, pt, 1);
@@ -464,10 +470,10 @@ int world_steps(smmo_world* w, int nsteps, cudaStream_t s, PhaseTimer* pt) {
       if (!st) st = pdo(w, w->cls_alive, &launch_do_all<AliveUpdate>, a, s, pt, 3);
     }
     if (!st && w->nw) {  // one Wa-Tor iteration (Sec. 7.6): fish phase, shark phase
-      a.key_hi = 0xFFFFFFFFu - 2u * t;
+      a.phase = 0;
       st = pdo(w, w->cls_fish, &launch_do_all<FishPrepare>, a, s, pt, 4);
       if (!st) st = pdo(w, w->cls_fish, &launch_do_all<FishUpdate>, a, s, pt, 5);
-      a.key_hi = 0xFFFFFFFFu - (2u * t + 1u);
+      a.phase = 1;
       if (!st) st = pdo(w, w->cls_shark, &launch_do_all<SharkPrepare>, a, s, pt, 6);
       if (!st) st = pdo(w, w->cls_shark, &launch_do_all<SharkUpdate>, a, s, pt, 7);
     }
@@ -526,14 +532,17 @@ int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32
   }
   if (heap->cfg.block_data_bytes == 0) heap->cfg.block_data_bytes = 768;  // every class gets N_T = 64
   if (!st) st = freeze(heap, s);
-  if (!st && heap->classes[w->cls_cell].layout.cap != 64) st = SMMO_E_UNSUPPORTED;
+  if (!st && heap->classes[w->cls_cell].layout.cap != 64 && heap->classes[w->cls_cell].layout.cap != 32)
+    st = SMMO_E_UNSUPPORTED;  // dense cell addressing needs N = 32 or 64
   if (st) { delete w; return st; }
   // instance tables (device memory inside the heap's scratch tail is not
   // reserved for this, so use a dedicated allocation owned by the world)
   w->nw = (uint32_t)wi.size();
   w->nl = (uint32_t)li.size();
   cudaError_t e = cudaSuccess;
-  if (w->nw) e = cudaMalloc(&w->d_winst, sizeof(Inst) * w->nw);
+  e = cudaMalloc(&w->d_t, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(w->d_t, 0, sizeof(uint32_t), s);
+  if (e == cudaSuccess && w->nw) e = cudaMalloc(&w->d_winst, sizeof(Inst) * w->nw);
   if (e == cudaSuccess && w->nl) e = cudaMalloc(&w->d_linst, sizeof(Inst) * w->nl);
   if (e == cudaSuccess && w->nw) e = cudaMemcpyAsync(w->d_winst, wi.data(), sizeof(Inst) * w->nw, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && w->nl) e = cudaMemcpyAsync(w->d_linst, li.data(), sizeof(Inst) * w->nl, cudaMemcpyHostToDevice, s);
@@ -561,6 +570,8 @@ int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32
   a.cells.data = heap->view.data;
   a.cells.block_bytes = heap->view.block_bytes;
   a.cells.b0 = (uint32_t)first;
+  a.cells.shift = heap->classes[w->cls_cell].layout.cap == 64 ? 6 : 5;
+  a.tp = w->d_t;
   const ClassLayout& CL = heap->classes[w->cls_cell].layout;
   a.occ_off = CL.col_off[0];
   a.req_off = CL.col_off[1];
@@ -642,6 +653,34 @@ int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32
 int smmo_world_step(smmo_world* w, int nsteps, void* stream) {
   if (!w || nsteps < 0) return SMMO_E_INVALID_ARG;
   return world_steps(w, nsteps, (cudaStream_t)stream, nullptr);
+}
+
+int smmo_world_capture(smmo_world* w, int nsteps, void* stream) {
+  if (!w || nsteps < 1 || !stream) return SMMO_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (w->graph) { cudaGraphExecDestroy(w->graph); w->graph = nullptr; }
+  const uint32_t t_save = w->t;
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = world_steps(w, nsteps, s, nullptr);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(s, &g);
+  w->t = t_save;  // capturing does not run the steps
+  if (st) { if (g) cudaGraphDestroy(g); return st; }
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaGraphInstantiate(&w->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { w->graph = nullptr; return cuda_status(e); }
+  w->graph_steps = nsteps;
+  return SMMO_OK;
+}
+
+int smmo_world_replay(smmo_world* w, void* stream) {
+  if (!w || !w->graph) return SMMO_E_INVALID_ARG;
+  cudaError_t e = cudaGraphLaunch(w->graph, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  w->t += (uint32_t)w->graph_steps;
+  return SMMO_OK;
 }
 
 int smmo_world_step_profiled(smmo_world* w, int nsteps, double* phase_ms, double* step_ms,
@@ -807,6 +846,8 @@ int smmo_world_info(smmo_world* w, int64_t* total_cells, int* class_ids, uint32_
 
 int smmo_world_destroy(smmo_world* w) {
   if (!w) return SMMO_E_INVALID_ARG;
+  if (w->graph) cudaGraphExecDestroy(w->graph);
+  if (w->d_t) cudaFree(w->d_t);
   if (w->d_winst) cudaFree(w->d_winst);
   if (w->d_linst) cudaFree(w->d_linst);
   delete w;

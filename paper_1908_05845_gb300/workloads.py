@@ -74,6 +74,13 @@ class World:
     def step(self, n: int = 1):
         smmo.check(smmo.lib().smmo_world_step(self._w, n, smmo._stream(self.stream)), "world_step")
 
+    def capture(self, n: int):
+        """Captures n steps into a CUDA graph (needs a non-default stream)."""
+        smmo.check(smmo.lib().smmo_world_capture(self._w, n, smmo._stream(self.stream)), "world_capture")
+
+    def replay(self):
+        smmo.check(smmo.lib().smmo_world_replay(self._w, smmo._stream(self.stream)), "world_replay")
+
     def step_profiled(self, n: int = 1):
         """Steps n times and returns (phase_ms[16], step_ms, launches): device
         times from CUDA events on the launching stream (see the C header)."""

@@ -131,3 +131,49 @@ def test_batched_mixed_instances(orc):
             assert np.array_equal(gk, wk) and np.array_equal(ga, wa) and np.array_equal(ge, we), i
     assert w.heap.check() == 0
     w.sync()
+
+
+def test_graph_replay_matches_plain_steps(orc):
+    """A captured step replayed k times advances the simulation exactly like
+    k plain steps (the step counter lives in device memory)."""
+    import torch
+    k, a, e = inputs.wator_initial(64, 64, 9)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = WaTor(64, 64, 9, k, a, e, stream=stream)
+        sim.step(2)
+        sim.capture(3)
+        for _ in range(4):
+            sim.replay()
+        got = sim.read()
+    want = orc.wator_run(64, 64, 9, k, a, e, 14)
+    for g, w in zip(got, want[:3]):
+        assert np.array_equal(g, w)
+
+
+def test_results_identical_for_every_tuning_choice(orc):
+    from paper_1908_05845_gb300 import smmo
+    kinds, sides = inputs.batched_instances(4, n=6, side_min=8, ratio=8.0)
+    seed = 4
+    ks, ags, ens, sts = [], [], [], []
+    for i, (kd, sd) in enumerate(zip(kinds, sides)):
+        if kd == LIFE:
+            kk, s = inputs.gol_initial(sd, sd, seed, inst=i)
+            aa, ee = np.zeros(sd * sd, np.int16), np.zeros(sd * sd, np.int16)
+        else:
+            kk, aa, ee = inputs.wator_initial(sd, sd, seed, inst=i)
+            s = np.zeros(sd * sd, np.uint8)
+        ks.append(kk.astype(np.int8)); ags.append(aa); ens.append(ee); sts.append(s)
+    init = [np.concatenate(x) for x in (ks, ags, ens, sts)]
+    outs = []
+    for cfg in ({"block_data_bytes": 384, "threads_per_cta": 128, "ctas_per_sm": 4},
+                {"block_data_bytes": 768, "threads_per_cta": 512, "ctas_per_sm": 16},
+                {"block_data_bytes": 768, "threads_per_cta": 256, "ctas_per_sm": 8}):
+        w = World(kinds, sides, sides, seed, *init, config=smmo.default_config(**cfg))
+        w.step(20)
+        outs.append(w.export())
+        w.close()
+    for o in outs[1:]:
+        for x, y in zip(o, outs[0]):
+            assert np.array_equal(x, y)
+    assert outs[0][4] == 0
