@@ -339,7 +339,7 @@ def run_e2e(args, seed, hb):
     sim.close()
     h2d = hk.numel() + 2 * ha.numel() + 2 * he.numel()
     d2h = k.nbytes + a.nbytes + e.nbytes
-    ctr = 8 * 36 * 32
+    ctr = 8 * 40 * 32
     return {"value": (e_end - e_start) / dt, "unit": "object-updates/s",
             "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps + ctr,
             "seconds": dt, "includes": "H2D of initial state, world setup, K steps with a "

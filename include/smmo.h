@@ -102,6 +102,11 @@ typedef struct {
   /* 1 = device code checks handles and indices and records the first
    * violation as SMMO_E_BOUNDS instead of touching memory. */
   int32_t debug_checks;
+  /* n of the defragmentation-candidate state kept by new and delete
+   * (Sec. 6.3.1): a block is a candidate iff it holds at most
+   * floor(N_T n / (n + 1)) objects.  Warp caches refill from candidates
+   * first.  Default 1 (at most half full). */
+  int32_t defrag_factor;
 } smmo_heap_config;
 
 /* Fills `cfg` with the defaults above. */
@@ -231,9 +236,10 @@ int smmo_heap_get_stats(smmo_heap* heap, smmo_heap_stats* out, void* stream);
  * `stream`. */
 int smmo_heap_check(smmo_heap* heap, int64_t* violations, void* stream);
 
-/* Cumulative device counters since create: objects visited by parallel_do
- * launches, device news and device deletes (all classes).  Host outputs
- * (nullable).  Synchronises `stream`; reads 9 KB. */
+/* Cumulative device counters since create: objects visited by do-all
+ * kernels (every object a method ran on, counted per launch), device news
+ * and device deletes (all classes).  Host outputs (nullable).  Synchronises
+ * `stream`; reads the 10 KB counter array. */
 int smmo_heap_counters(smmo_heap* heap, int64_t* enumerated_objects,
                        int64_t* allocs, int64_t* frees, void* stream);
 

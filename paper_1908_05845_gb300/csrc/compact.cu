@@ -211,8 +211,37 @@ struct Rewrite {
   }
 };
 
-__global__ void k_zero(unsigned long long* p, uint32_t n) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = 0;
+// Rebuilds the candidate bitmap defrag[c] that new and delete maintain
+// (fill <= dlimit) after a compaction used its level 0 as scratch: level 0
+// from the allocation bitmaps, every higher level as the OR of its
+// container below.
+__global__ void k_rebuild_defrag_l0(HeapView h, uint32_t c) {
+  const unsigned long long* A = bm_level(h, bm_alloc(h, c), 0);
+  unsigned long long* D = bm_level(h, bm_defrag(h, c), 0);
+  const unsigned long long capmask = h.cls[c].capmask;
+  const uint32_t lim = h.cls[c].dlimit;
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < h.level_words[0]; w += gridDim.x * blockDim.x) {
+    unsigned long long a = A[w], d = 0;
+    while (a) {
+      const int b = __ffsll((long long)a) - 1;
+      a &= a - 1;
+      if ((uint32_t)__popcll(h.alloc_bm[w * 64 + b] & capmask) <= lim) d |= 1ull << b;
+    }
+    D[w] = d;
+  }
+}
+
+__global__ void k_rebuild_level(HeapView h, int k, uint32_t l) {
+  const unsigned long long* lo = bm_level(h, k, l - 1);
+  unsigned long long* hi = bm_level(h, k, l);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < h.level_words[l]; i += gridDim.x * blockDim.x) {
+    unsigned long long v = 0;
+    for (uint32_t j = 0; j < 64; ++j) {
+      const uint64_t q = (uint64_t)i * 64 + j;
+      if (q < h.level_words[l - 1] && lo[q]) v |= 1ull << j;
+    }
+    hi[i] = v;
+  }
 }
 
 bool is_ancestor_or_self(const smmo_heap* h, int anc, int c) {
@@ -295,8 +324,12 @@ extern "C" int smmo_compact(smmo_heap* h, int c, int n, int64_t k1, smmo_compact
     st.objects_moved += (int64_t)mv[0];
     st.pointers_rewritten += (int64_t)mv[1];
   }
-  // defrag[c] is only meaningful during a pass: leave it empty
-  k_zero<<<g, 256, 0, s>>>(D0, nw);
+  // the pass used defrag[c] level 0 as scratch: restore the candidate state
+  // that new and delete maintain
+  k_rebuild_defrag_l0<<<g, 256, 0, s>>>(h->view, c);
+  for (uint32_t l = 1; l < h->view.nlevels; ++l)
+    k_rebuild_level<<<std::max(1u, std::min((h->view.level_words[l] + 255) / 256, 1024u)), 256, 0, s>>>(
+        h->view, bm_defrag(h->view, c), l);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (out) *out = st;
   return cuda_status(e);

@@ -155,6 +155,7 @@ __global__ void k_bulk_claim(HeapView h, uint32_t c, const uint32_t* list, uint3
     h.alloc_bm[bid] = ~capmask | used;
     bm_set(h, bm_alloc(h, c), bid);
     if (fill < cap) bm_set(h, bm_active(h, c), bid);
+    if (fill <= h.cls[c].dlimit) bm_set(h, bm_defrag(h, c), bid);
   }
 }
 
@@ -301,6 +302,11 @@ __global__ void k_check_blocks(HeapView h) {
       if ((bm & L.capmask) == 0) ++bad;                     // empty but allocated
       const bool full = bm == kAll;
       if (bm_get(h, bm_active(h, owner), b) == full) ++bad;  // active iff not full
+      const bool cand = (uint32_t)__popcll(bm & L.capmask) <= L.dlimit;
+      if (bm_get(h, bm_defrag(h, owner), b) != cand) ++bad;  // candidate iff fill <= dlimit
+    } else {
+      for (int c = 0; c < h.num_classes; ++c)
+        if (bm_get(h, bm_defrag(h, c), b)) ++bad;
     }
   }
   if (bad) atomicAdd(&h.st->aux[2], bad);
@@ -351,6 +357,7 @@ int freeze(smmo_heap* h, cudaStream_t s) {
     L.cap = (uint32_t)cap;
     L.ncols = (uint32_t)ci.ncols;
     L.capmask = cap >= 64 ? kAll : ((1ull << cap) - 1);
+    L.dlimit = (uint32_t)((uint64_t)cap * (uint64_t)h->cfg.defrag_factor / (uint64_t)(h->cfg.defrag_factor + 1));
     size_t off = 0;
     int col = 0;
     for (auto& f : ci.fields)
@@ -494,6 +501,7 @@ void smmo_heap_config_default(smmo_heap_config* c) {
   c->threads_per_cta = 256;
   c->ctas_per_sm = 8;
   c->debug_checks = 0;
+  c->defrag_factor = 1;
 }
 
 int smmo_heap_create(const smmo_heap_config* cfg, void* dev_buf, size_t buf_bytes, void* stream,
@@ -504,7 +512,8 @@ int smmo_heap_create(const smmo_heap_config* cfg, void* dev_buf, size_t buf_byte
   smmo_heap_config_default(&c);
   if (cfg) c = *cfg;
   if (c.threads_per_cta <= 0 || c.threads_per_cta % 64 || c.threads_per_cta > 512 ||
-      c.ctas_per_sm <= 0 || c.lookup_retries < 1 || c.alloc_retries < 1 || c.bitmap_spins < 1)
+      c.ctas_per_sm <= 0 || c.lookup_retries < 1 || c.alloc_retries < 1 || c.bitmap_spins < 1 ||
+      c.defrag_factor < 1 || c.defrag_factor > 63)
     return SMMO_E_INVALID_ARG;
   smmo_heap* h = new smmo_heap();
   h->cfg = c;
@@ -774,7 +783,7 @@ int smmo_heap_counters(smmo_heap* h, int64_t* enumerated_objects, int64_t* alloc
   if (e != cudaSuccess) return smmo::cuda_status(e);
   for (int sh = 0; sh < SMMO_NSHARD; ++sh) {
     const unsigned long long* r = &c[(size_t)sh * SMMO_NCTR];
-    if (enumerated_objects) *enumerated_objects += (int64_t)r[SMMO_CTR_ENUM_OBJ];
+    if (enumerated_objects) *enumerated_objects += (int64_t)r[SMMO_CTR_VISIT];
     for (int k = 0; k < SMMO_MAX_CLASSES; ++k) {
       if (allocs) *allocs += (int64_t)r[SMMO_CTR_ALLOC(k)];
       if (frees) *frees += (int64_t)r[SMMO_CTR_FREE(k)];

@@ -32,6 +32,7 @@
 #define SMMO_CTR_REFILL 36
 #define SMMO_CTR_LOOKUP_MISS 37
 #define SMMO_CTR_RESERVE_FAIL 38
+#define SMMO_CTR_VISIT 39
 #define SMMO_CTR_ALLOC(c) (2 + (c))
 #define SMMO_CTR_FREE(c) (2 + SMMO_MAX_CLASSES + (c))
 #define SMMO_NCTR (8 + 2 * SMMO_MAX_CLASSES)
@@ -45,6 +46,8 @@ struct ClassLayout {
   uint32_t cap;                       // N_T
   uint32_t ncols;
   unsigned long long capmask;         // low N_T bits set
+  uint32_t dlimit;                    // defrag candidate iff fill <= dlimit
+  uint32_t pad;
   uint32_t col_off[SMMO_MAX_COLS];    // byte offset of each SOA column
   uint32_t col_size[SMMO_MAX_COLS];   // element size of each column
 };
@@ -247,40 +250,47 @@ __device__ __forceinline__ uint32_t type_of(const HeapView& h, uint32_t handle) 
 
 // ------------------------------------------------------------- deallocation
 // Frees the slots `bits` of block `bid` of class t: the divergence-safe
-// deallocation of Alg. 5.12 with block invalidation (Alg. 5.11) folded in.
-// All block-state bitmap changes are collected as pending +1/-1 operations
-// first and then retried with try_ operations in one converged loop, so no
-// lane waits on a bit that another lane of its own warp has yet to flip.
+// deallocation of Alg. 5.12 with block invalidation (Alg. 5.11) folded in,
+// extended with the defragmentation-candidate state of Alg. 6.3 (a block is
+// a candidate iff it is allocated and holds at most dlimit objects).  All
+// block-state bitmap changes are collected as pending +1/-1 operations first
+// and then retried with try_ operations in one converged loop, so no lane
+// waits on a bit that another lane of its own warp has yet to flip.
 static __device__ __noinline__ void dealloc_bits(const HeapView& h, uint32_t bid, uint32_t t,
-                                          unsigned long long bits) {
+                                                 unsigned long long bits) {
   const unsigned long long capmask = __ldg(&h.cls[t].capmask);
+  const uint32_t dlim = __ldg(&h.cls[t].dlimit);
   const unsigned long long empty = ~capmask;
   const unsigned long long before = atomicAnd(h.alloc_bm + bid, ~bits);
   if ((before & bits) != bits) {  // precondition of Alg. 5.8 violated
     set_error(h, SMMO_E_BAD_HANDLE, ((unsigned long long)bid << 6) | (__ffsll((long long)bits) - 1));
     return;
   }
-  int act = 0, alc = 0, fre = 0;
+  int act = 0, alc = 0, fre = 0, dfr = 0;
   if (before == kAll) act += 1;  // freed the first slot of a full block
+  const uint32_t fb = __popcll(before & capmask), fa = fb - __popcll(bits);
+  if (fb > dlim && fa <= dlim) dfr += 1;  // became a defragmentation candidate
   if ((before & ~bits) == empty) {
     // freed the last object: try to invalidate the block (Alg. 5.11)
     for (int s = 0; s < h.bitmap_spins; ++s) {
       const unsigned long long ib = atomicOr(h.alloc_bm + bid, kAll);
       if (ib == kAll) break;                       // nothing invalidated
-      if (ib == empty) { act -= 1; alc -= 1; fre += 1; break; }  // success
+      if (ib == empty) { act -= 1; alc -= 1; fre += 1; dfr -= 1; break; }  // success
       const unsigned long long rb = atomicAnd(h.alloc_bm + bid, ib);  // rollback
       if (rb != kAll) act -= 1;  // a concurrent free saw a full block
       if ((rb & ib) != empty) break;               // not empty again
     }
   }
-  for (int s = 0; (act | alc | fre) && s < h.bitmap_spins; ++s) {
+  for (int s = 0; (act | alc | fre | dfr) && s < h.bitmap_spins; ++s) {
     if (act > 0 && bm_try_set(h, bm_active(h, t), bid)) --act;
     if (act < 0 && bm_try_clear(h, bm_active(h, t), bid)) ++act;
+    if (dfr > 0 && bm_try_set(h, bm_defrag(h, t), bid)) --dfr;
+    if (dfr < 0 && bm_try_clear(h, bm_defrag(h, t), bid)) ++dfr;
     if (alc < 0 && bm_try_clear(h, bm_alloc(h, t), bid)) ++alc;
-    if (fre > 0 && act == 0 && alc == 0 && bm_try_set(h, bm_free(), bid)) --fre;
-    if (act | alc | fre) __nanosleep(32);
+    if (fre > 0 && act == 0 && alc == 0 && dfr == 0 && bm_try_set(h, bm_free(), bid)) --fre;
+    if (act | alc | fre | dfr) __nanosleep(32);
   }
-  if (act | alc | fre) set_error(h, SMMO_E_CONTENTION, bid);
+  if (act | alc | fre | dfr) set_error(h, SMMO_E_CONTENTION, bid);
 }
 
 // destroy(ptr) for a single object (Alg. 5.2 / 5.12).
@@ -300,40 +310,13 @@ __device__ __forceinline__ void smmo_delete(const HeapView& h, uint32_t handle) 
 }
 
 // ---------------------------------------------------------------- allocation
-// Leader part of allocation with request coalescing (Alg. 5.6): find an
-// active block of class c (with lookup retry, Sec. 5.3.2), else initialise
-// a free block (slow path of Alg. 5.1), then reserve up to n slots in it.
-// Returns the reserved slot bits (possibly fewer than n, possibly 0) and the
-// block in *bid; *bid = kNull signals that no free block exists.
-static __device__ __noinline__ unsigned long long leader_reserve(const HeapView& h, uint32_t c, int n,
-                                                          uint32_t seed, uint32_t* bid_out) {
-  const unsigned long long capmask = __ldg(&h.cls[c].capmask);
-  const uint32_t cap = __ldg(&h.cls[c].cap);
-  int bid = -1;
-  for (int r = 0; r < h.lookup_retries && bid < 0; ++r)
-    bid = bm_try_find_set(h, bm_active(h, c), seed + 104729u * (uint32_t)r);
-  if (bid < 0) {
-    count(h, SMMO_CTR_LOOKUP_MISS, 1);
-    bid = bm_clear_any(h, bm_free(), seed ^ 0x5bd1e995u);
-    if (bid < 0) { *bid_out = kNull; return 0; }
-    count(h, SMMO_CTR_SLOW, 1);
-    // initialize_block (Alg. 5.10): type first, fence, then open the slots
-    atomicExch(h.block_type + bid, c);
-    __threadfence();
-    if ((uint32_t)n >= cap) {
-      // the caller takes the whole block: it is born full, so it never
-      // enters the active bitmap
-      atomicExch(h.alloc_bm + bid, kAll);
-      bm_set(h, bm_alloc(h, c), (uint32_t)bid);
-      *bid_out = (uint32_t)bid;
-      return capmask;
-    }
-    atomicExch(h.alloc_bm + bid, ~capmask);
-    bm_set(h, bm_alloc(h, c), (uint32_t)bid);
-    bm_set(h, bm_active(h, c), (uint32_t)bid);
-  }
-  *bid_out = (uint32_t)bid;
-  // reserve_multiple(n): Alg. 5.7 extended to several slots
+// Reserves up to n free slots of block bid for class c (Block::reserve of
+// Alg. 5.7, extended to several slots, with the state changes of Alg. 6.2:
+// the thread that fills the block removes it from active, the one that
+// takes it above dlimit removes it from the candidates).  If the block was
+// re-initialised to another class the reservation is rolled back (Alg. 5.1).
+static __device__ __noinline__ unsigned long long reserve_in(const HeapView& h, uint32_t c, uint32_t bid,
+                                                             int n) {
   for (int s = 0; s < h.bitmap_spins; ++s) {
     const unsigned long long cur = ld_cg(h.alloc_bm + bid);
     unsigned long long freeb = ~cur;
@@ -348,9 +331,15 @@ static __device__ __noinline__ unsigned long long leader_reserve(const HeapView&
     const unsigned long long got = pick & ~before;
     if (!got) continue;
     const uint32_t t = atomicAdd(h.block_type + bid, 0u);
-    if ((before | pick) == kAll) bm_clear(h, bm_active(h, t), (uint32_t)bid);  // filled it
+    if (t < (uint32_t)h.num_classes) {
+      const unsigned long long tcap = __ldg(&h.cls[t].capmask);
+      const uint32_t dlim = __ldg(&h.cls[t].dlimit);
+      const uint32_t fb = __popcll(before & tcap), fa = fb + __popcll(got);
+      if ((before | pick) == kAll) bm_clear(h, bm_active(h, t), bid);       // filled it
+      if (fb <= dlim && fa > dlim) bm_clear(h, bm_defrag(h, t), bid);       // no candidate now
+    }
     if (t != c) {  // block was re-initialised to another class: roll back
-      dealloc_bits(h, (uint32_t)bid, t, got);
+      dealloc_bits(h, bid, t, got);
       return 0;
     }
     return got;
@@ -358,18 +347,58 @@ static __device__ __noinline__ unsigned long long leader_reserve(const HeapView&
   return 0;
 }
 
+// Finds room for a warp's cache: (1) a defragmentation candidate, i.e. a
+// block at most dlimit full, so one reservation yields many slots; (2) a
+// fresh block from the free bitmap, initialised full for the caller
+// (initialize_block, Alg. 5.10, opening no slot to others); (3) when no block
+// is free, any active block with room.  Lookups retry with rotation
+// (Sec. 5.3.2).  Returns the reserved slot bits and the block in *bid_out
+// (kNull: the heap is exhausted).
+static __device__ __noinline__ unsigned long long refill_reserve(const HeapView& h, uint32_t c,
+                                                                 uint32_t seed, uint32_t* bid_out) {
+  for (int r = 0; r < h.lookup_retries; ++r) {
+    const int b = bm_try_find_set(h, bm_defrag(h, c), seed + 104729u * (uint32_t)r);
+    if (b < 0) {
+      if (ld_cg(bm_level(h, bm_defrag(h, c), h.nlevels - 1)) == 0) break;
+      continue;
+    }
+    const unsigned long long got = reserve_in(h, c, (uint32_t)b, 64);
+    if (got) { *bid_out = (uint32_t)b; return got; }
+  }
+  count(h, SMMO_CTR_LOOKUP_MISS, 1);
+  const int fb = bm_clear_any(h, bm_free(), seed ^ 0x5bd1e995u);
+  if (fb >= 0) {
+    atomicExch(h.block_type + fb, c);
+    __threadfence();
+    atomicExch(h.alloc_bm + fb, kAll);
+    bm_set(h, bm_alloc(h, c), (uint32_t)fb);
+    count(h, SMMO_CTR_SLOW, 1);
+    *bid_out = (uint32_t)fb;
+    return __ldg(&h.cls[c].capmask);
+  }
+  for (int r = 0; r < h.lookup_retries; ++r) {
+    const int b = bm_try_find_set(h, bm_active(h, c), seed + 7u + 104729u * (uint32_t)r);
+    if (b < 0) {
+      if (ld_cg(bm_level(h, bm_active(h, c), h.nlevels - 1)) == 0) break;
+      continue;
+    }
+    const unsigned long long got = reserve_in(h, c, (uint32_t)b, 64);
+    if (got) { *bid_out = (uint32_t)b; return got; }
+  }
+  *bid_out = kNull;
+  return 0;
+}
+
 // Per-warp allocation cache (shared memory, one slot per warp and class).
-// When a warp runs out of cached slots its leader runs the global
-// allocation path (leader_reserve) and reserves every free slot of the
-// block it finds; later allocations of the same warp are served from the
-// cached bits without touching global memory.  Only leader lanes of the
-// warp touch its slot; a per-warp lock still guards it because two diverged
-// lane groups of one warp may each be inside smmo_new at the same time
-// (independent thread scheduling), and without the lock both could hand
-// out the same cached slot.  The lock is uncontended unless that happens.
-// Slots still cached when the do-all kernel ends are returned with
-// dealloc_bits, exactly like deleted objects (the block turns active again
-// or is invalidated).
+// When a warp runs out of cached slots its leader refills the cache with
+// every free slot of the block refill_reserve finds; later allocations of
+// the same warp are served from the cached bits without touching global
+// memory.  Only leader lanes of the warp touch its slot; a per-warp lock
+// still guards it because two diverged lane groups of one warp may each be
+// inside smmo_new at the same time (independent thread scheduling), and
+// without the lock both could hand out the same cached slot.  The lock is
+// uncontended unless that happens.  Slots still cached when the do-all
+// kernel ends are returned with dealloc_bits, exactly like deleted objects.
 struct WarpAllocCache {
   unsigned long long bits[SMMO_MAX_CLASSES];
   uint32_t bid[SMMO_MAX_CLASSES];
@@ -398,8 +427,8 @@ __device__ __forceinline__ void alloc_cache_flush(const HeapView& h) {
 }
 
 // Takes up to n slots of class c from the calling warp's cache, refilling
-// it from the heap when empty.  Returns the slot bits (possibly fewer or
-// none) and the block in *bid (kNull: heap exhausted).
+// it when empty.  Returns the slot bits (possibly fewer or none) and the
+// block in *bid (kNull: heap exhausted).
 static __device__ __noinline__ unsigned long long cache_take(const HeapView& h, uint32_t c, int n,
                                                              uint32_t seed, uint32_t* bid) {
   WarpAllocCache& wc = g_wcache[threadIdx.x >> 5];
@@ -412,7 +441,7 @@ static __device__ __noinline__ unsigned long long cache_take(const HeapView& h, 
   unsigned long long avail = wc.bits[c];
   uint32_t b = wc.bid[c];
   if (avail == 0) {
-    avail = leader_reserve(h, c, 64, seed, &b);
+    avail = refill_reserve(h, c, seed, &b);
     wc.bid[c] = b;
     count(h, SMMO_CTR_REFILL, 1);
   }
@@ -431,11 +460,11 @@ static __device__ __noinline__ unsigned long long cache_take(const HeapView& h, 
 
 // new(d_allocator) T: warp-aggregated allocation of one object of class c
 // per calling lane (allocation request coalescing, Alg. 5.6).  Lanes that
-// call it together (the active mask) are served by one leader per round;
-// lanes left without a slot retry with a new leader.  Only methods run by
-// parallel_do may call it (it uses the warp cache above).  Returns kNull (and
-// records SMMO_E_DEVICE_OOM or SMMO_E_CONTENTION) if the heap is exhausted
-// or the budget runs out.
+// call it together (the active mask) are served by one leader per round from
+// the warp cache; lanes left without a slot retry with a new leader.  Only
+// methods run by parallel_do may call it (it uses the warp cache above).
+// Returns kNull (and records SMMO_E_DEVICE_OOM or SMMO_E_CONTENTION) if the
+// heap is exhausted or the budget runs out.
 __device__ __forceinline__ uint32_t smmo_new(const HeapView& h, uint32_t c) {
   if (c >= (uint32_t)h.num_classes) { set_error(h, SMMO_E_INVALID_ARG, c); return kNull; }
   const unsigned active = __activemask();
@@ -486,13 +515,16 @@ __global__ void __launch_bounds__(512) do_all_kernel(HeapView h, uint32_t c,
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   alloc_cache_init();
+  uint32_t visited = 0;
   for (uint32_t u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units; u += nwarps) {
     const uint32_t i = halves == 2 ? (u >> 1) : u;
     const uint32_t slot = (halves == 2 ? (u & 1) * 32 : 0) + lane;
     const REntry e = h.R[i];
+    if (lane == 0) visited += __popcll(halves == 2 ? (e.bits >> ((u & 1) * 32)) & 0xFFFFFFFFull : e.bits);
     if ((e.bits >> slot) & 1) M::run(h, args, c, (e.block << 6) | slot);
     __syncwarp();  // reconverge: lane groups never run different iterations
   }
+  if (lane == 0 && visited) count(h, SMMO_CTR_VISIT, visited);
   alloc_cache_flush(h);
 }
 

@@ -177,8 +177,9 @@ struct smmo_traffic {
 };
 
 namespace {
-int pdo(smmo_traffic* w, int cls, method_launch_fn fn, const TrafficArgs& a, cudaStream_t s) {
-  int st = enumerate(w->heap, cls, s);
+int pdo(smmo_traffic* w, int cls, method_launch_fn fn, const TrafficArgs& a, cudaStream_t s,
+        bool reuse = false) {
+  int st = reuse ? SMMO_OK : enumerate(w->heap, cls, s);
   if (!st) st = fn(w->heap, cls, &a, s);
   return st;
 }
@@ -315,7 +316,7 @@ int smmo_traffic_step(smmo_traffic* w, int nsteps, void* stream) {
     k_step_begin<<<1, 1, 0, s>>>(w->d_t);
     int st = cuda_status(cudaGetLastError());
     if (!st) st = pdo(w, w->cls_car, &launch_do_all<CarPrepare>, a, s);
-    if (!st) st = pdo(w, w->cls_car, &launch_do_all<CarMove>, a, s);
+    if (!st) st = pdo(w, w->cls_car, &launch_do_all<CarMove>, a, s, true);  // prepare keeps the cars
     if (!st) st = pdo(w, w->cls_src, &launch_do_all<SourceSpawn>, a, s);
     if (st) return st;
   }

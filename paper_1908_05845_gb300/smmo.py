@@ -73,7 +73,7 @@ class HeapConfig(ctypes.Structure):
     _fields_ = [("block_data_bytes", ctypes.c_uint32), ("lookup_retries", ctypes.c_int32),
                 ("alloc_retries", ctypes.c_int32), ("bitmap_spins", ctypes.c_int32),
                 ("threads_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("debug_checks", ctypes.c_int32)]
+                ("debug_checks", ctypes.c_int32), ("defrag_factor", ctypes.c_int32)]
 
 
 class HeapStats(ctypes.Structure):
@@ -266,7 +266,8 @@ class Heap:
         return out
 
     def counters(self):
-        """(enumerated objects, device news, device deletes), cumulative."""
+        """(objects visited by do-all kernels, device news, device deletes),
+        cumulative."""
         e, a, f = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         check(lib().smmo_heap_counters(self._h, ctypes.byref(e), ctypes.byref(a), ctypes.byref(f),
                                        _stream(self.stream)), "heap_counters")
