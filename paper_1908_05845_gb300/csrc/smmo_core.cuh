@@ -506,7 +506,7 @@ __device__ __forceinline__ uint32_t smmo_new(const HeapView& h, uint32_t c) {
 // 32 slots), thread t of a block's group handles slot t, and a slot runs the
 // method iff its bit is set in the snapshot taken at enumeration time.
 template <class M>
-__global__ void __launch_bounds__(512) do_all_kernel(HeapView h, uint32_t c,
+__global__ void __launch_bounds__(512, 3) do_all_kernel(HeapView h, uint32_t c,
                                                      typename M::Args args) {
   const uint32_t n = __ldcg(&h.st->rcount);
   const uint32_t cap = __ldg(&h.cls[c].cap);
