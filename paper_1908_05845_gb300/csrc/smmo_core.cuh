@@ -426,11 +426,18 @@ __device__ __forceinline__ void alloc_cache_flush(const HeapView& h) {
   }
 }
 
+// Refills an empty warp-cache entry (out of line: the global path is long).
+static __device__ __noinline__ unsigned long long cache_refill(const HeapView& h, uint32_t c,
+                                                               uint32_t seed, uint32_t* bid) {
+  count(h, SMMO_CTR_REFILL, 1);
+  return refill_reserve(h, c, seed, bid);
+}
+
 // Takes up to n slots of class c from the calling warp's cache, refilling
 // it when empty.  Returns the slot bits (possibly fewer or none) and the
-// block in *bid (kNull: heap exhausted).
-static __device__ __noinline__ unsigned long long cache_take(const HeapView& h, uint32_t c, int n,
-                                                             uint32_t seed, uint32_t* bid) {
+// block in *bid (kNull: heap exhausted).  The cache-hit path is inline.
+__device__ __forceinline__ unsigned long long cache_take(const HeapView& h, uint32_t c, int n,
+                                                         uint32_t seed, uint32_t* bid) {
   WarpAllocCache& wc = g_wcache[threadIdx.x >> 5];
   int spins = 0;
   while (atomicCAS(&wc.lock, 0, 1) != 0) {
@@ -441,15 +448,19 @@ static __device__ __noinline__ unsigned long long cache_take(const HeapView& h, 
   unsigned long long avail = wc.bits[c];
   uint32_t b = wc.bid[c];
   if (avail == 0) {
-    avail = refill_reserve(h, c, seed, &b);
+    avail = cache_refill(h, c, seed, &b);
     wc.bid[c] = b;
-    count(h, SMMO_CTR_REFILL, 1);
   }
-  unsigned long long take = 0;
-  for (int i = 0; i < n && avail; ++i) {
-    const unsigned long long low = avail & (0ull - avail);
-    take |= low;
-    avail ^= low;
+  unsigned long long take = avail;
+  if (__popcll(avail) > n) {  // keep the highest bits, hand out the n lowest
+    take = 0;
+    for (int i = 0; i < n; ++i) {
+      const unsigned long long low = avail & (0ull - avail);
+      take |= low;
+      avail ^= low;
+    }
+  } else {
+    avail = 0;
   }
   wc.bits[c] = b == kNull ? 0ull : avail;
   __threadfence_block();
