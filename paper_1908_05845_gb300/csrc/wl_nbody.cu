@@ -128,6 +128,9 @@ __global__ void __launch_bounds__(256) k_force(HeapView hv, uint32_t c, NBodyArg
       __syncthreads();
       const uint32_t cnt = a.n0 - base < NB_TILE ? a.n0 - base : NB_TILE;
       if (live) {
+        // unrolled so that the pair terms of consecutive j (independent)
+        // overlap; the accumulation stays in increasing j
+#pragma unroll 8
         for (uint32_t k = 0; k < cnt; ++k) {
           const float4 p = tile[k];
           const float dx = fs(p.x, xi), dy = fs(p.y, yi), dz = fs(p.z, zi);
@@ -158,53 +161,122 @@ __global__ void __launch_bounds__(256) k_force(HeapView hv, uint32_t c, NBodyArg
   }
 }
 
-// Receiver i takes the first body j in id order with (m_j, j) < (m_i, i)
-// and |x_j - x_i|^2 < R^2; the lowest receiver id wins j.
-__global__ void __launch_bounds__(256) k_merge_prepare(HeapView hv, uint32_t c, NBodyArgs a) {
-  __shared__ float4 tile[NB_TILE];
-  const uint32_t n = __ldcg(&hv.st->rcount);
-  const uint32_t cap = hv.cls[c].cap;
-  const uint32_t halves = cap > 32 ? 2u : 1u;
-  const uint32_t units = n * halves, groups = (units + 7) / 8;
-  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (uint32_t g = blockIdx.x; g < groups; g += gridDim.x) {
-    const uint32_t u = g * 8 + warp;
-    bool searching = false;
-    uint32_t self = 0, id = 0;
-    if (u < units) {
-      const REntry e = hv.R[halves == 2 ? (u >> 1) : u];
-      const uint32_t slot = (halves == 2 ? (u & 1) * 32 : 0) + lane;
-      searching = (e.bits >> slot) & 1;
-      self = (e.block << 6) | slot;
-    }
-    float xi = 0, yi = 0, zi = 0, mi = 0;
-    if (searching) {
-      xi = F<float>(hv, self, a.off[CX]);
-      yi = F<float>(hv, self, a.off[CY]);
-      zi = F<float>(hv, self, a.off[CZ]);
-      mi = F<float>(hv, self, a.off[CM]);
-      id = F<int32_t>(hv, self, a.off[CID]);
-    }
+// ---- merge search on a hashed uniform grid (cell edge >= R) -------------
+// Receiver i takes the first body j in id order with (m_j, j) < (m_i, i) and
+// |x_j - x_i|^2 < R^2; the lowest receiver id wins j.  Every body j with
+// |x_j - x_i| < R lies in one of the 27 cells around i's cell, so the
+// smallest qualifying id over those cells is that first body.  The
+// edge is R (1 + 1e-4) and cell coordinates are taken in double, so that
+// neither the float distance test (which may accept |x_j - x_i| up to
+// R (1 + 2^-22)) nor the rounding of x / edge can split such a pair across
+// two cells apart.  Colliding hashes only add candidates, which the exact
+// test rejects.
+#define NB_HASH_BITS 20
+#define NB_HASH (1u << NB_HASH_BITS)
+
+__device__ __forceinline__ uint32_t cell_coord(float v, double inv_edge) {
+  return (uint32_t)__double2ll_rd((double)v * inv_edge);
+}
+
+__device__ __forceinline__ uint32_t cell_hash(uint32_t cx, uint32_t cy, uint32_t cz) {
+  const uint32_t h = cx * 73856093u ^ cy * 19349663u ^ cz * 83492791u;
+  return (h ^ (h >> 16)) & (NB_HASH - 1);
+}
+
+struct GridArgs {
+  const float4* S;
+  uint32_t* cnt;    // NB_HASH counts, then fill cursors
+  uint32_t* start;  // NB_HASH + 1 exclusive offsets
+  uint32_t* part;   // per-CTA partial sums of the scan
+  uint32_t* ids;    // n0 ids sorted by bucket
+  uint32_t* tgt;
+  uint32_t n0;
+  float R2;
+  double inv_edge;
+};
+
+__global__ void k_grid_count(GridArgs g) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n0; i += gridDim.x * blockDim.x) {
+    const float4 p = g.S[i];
+    if (!(p.w > 0.0f)) continue;
+    atomicAdd(g.cnt + cell_hash(cell_coord(p.x, g.inv_edge), cell_coord(p.y, g.inv_edge),
+                                cell_coord(p.z, g.inv_edge)), 1u);
+  }
+}
+
+// exclusive scan of cnt into start: per CTA 1024 x 4 buckets
+__global__ void __launch_bounds__(1024) k_grid_scan_local(GridArgs g) {
+  __shared__ uint32_t sh[1024];
+  const uint32_t base = blockIdx.x * 4096 + threadIdx.x * 4;
+  uint32_t v[4], t = 0;
+  for (int k = 0; k < 4; ++k) { v[k] = g.cnt[base + k]; t += v[k]; }
+  sh[threadIdx.x] = t;
+  __syncthreads();
+  for (uint32_t o = 1; o < 1024; o <<= 1) {
+    const uint32_t x = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += x;
+    __syncthreads();
+  }
+  uint32_t run = sh[threadIdx.x] - t;
+  for (int k = 0; k < 4; ++k) { g.start[base + k] = run; run += v[k]; }
+  if (threadIdx.x == 1023) g.part[blockIdx.x] = sh[1023];
+}
+
+__global__ void __launch_bounds__(256) k_grid_scan_top(GridArgs g, uint32_t nparts) {
+  __shared__ uint32_t sh[256];
+  const uint32_t v = threadIdx.x < nparts ? g.part[threadIdx.x] : 0;
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (uint32_t o = 1; o < 256; o <<= 1) {
+    const uint32_t x = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += x;
+    __syncthreads();
+  }
+  if (threadIdx.x < nparts) g.part[threadIdx.x] = sh[threadIdx.x] - v;
+  if (threadIdx.x == 0) g.start[NB_HASH] = sh[255];
+}
+
+__global__ void k_grid_scatter(GridArgs g) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n0; i += gridDim.x * blockDim.x) {
+    const float4 p = g.S[i];
+    if (!(p.w > 0.0f)) continue;
+    const uint32_t hb = cell_hash(cell_coord(p.x, g.inv_edge), cell_coord(p.y, g.inv_edge),
+                                  cell_coord(p.z, g.inv_edge));
+    const uint32_t pos = g.start[hb] + g.part[hb >> 12] + atomicAdd(g.cnt + hb, 1u);
+    g.ids[pos] = i;
+  }
+}
+
+// receiver i: smallest j in the 27 cells with (m_j, j) < (m_i, i) and
+// |x_j - x_i|^2 < R^2, then atomicMin(tgt[j], i)
+__global__ void k_grid_merge_prepare(GridArgs g) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n0; i += gridDim.x * blockDim.x) {
+    const float4 pi = g.S[i];
+    if (!(pi.w > 0.0f)) continue;
+    const uint32_t cx = cell_coord(pi.x, g.inv_edge), cy = cell_coord(pi.y, g.inv_edge),
+                   cz = cell_coord(pi.z, g.inv_edge);
     uint32_t pick = kNull;
-    for (uint32_t base = 0; base < a.n0; base += NB_TILE) {
-      if (!__syncthreads_or(searching)) break;
-      if (base + threadIdx.x < a.n0) tile[threadIdx.x] = a.S[base + threadIdx.x];
-      __syncthreads();
-      const uint32_t cnt = a.n0 - base < NB_TILE ? a.n0 - base : NB_TILE;
-      if (searching) {
-        for (uint32_t k = 0; k < cnt; ++k) {
-          const float4 p = tile[k];
-          const uint32_t j = base + k;
-          if (!(p.w > 0.0f) || !(p.w < mi || (p.w == mi && j < id))) continue;
-          const float dx = fs(p.x, xi), dy = fs(p.y, yi), dz = fs(p.z, zi);
-          float d2 = fm(dx, dx);
-          d2 = fa(d2, fm(dy, dy));
-          d2 = fa(d2, fm(dz, dz));
-          if (d2 < a.R2) { pick = j; searching = false; break; }
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const uint32_t hb = cell_hash(cx + (uint32_t)dx, cy + (uint32_t)dy, cz + (uint32_t)dz);
+          const uint32_t b0 = g.start[hb] + g.part[hb >> 12];
+          const uint32_t b1 = hb + 1 < NB_HASH ? g.start[hb + 1] + g.part[(hb + 1) >> 12] : g.start[NB_HASH];
+          for (uint32_t q = b0; q < b1; ++q) {
+            const uint32_t j = g.ids[q];
+            if (j >= pick) continue;
+            const float4 p = g.S[j];
+            if (!(p.w < pi.w || (p.w == pi.w && j < i))) continue;
+            const float ddx = fs(p.x, pi.x), ddy = fs(p.y, pi.y), ddz = fs(p.z, pi.z);
+            float d2 = fm(ddx, ddx);
+            d2 = fa(d2, fm(ddy, ddy));
+            d2 = fa(d2, fm(ddz, ddz));
+            if (d2 < g.R2) pick = j;
+          }
         }
-      }
-    }
-    if (pick != kNull) atomicMin(a.tgt + pick, id);
+    if (pick != kNull) atomicMin(g.tgt + pick, i);
   }
 }
 
@@ -386,6 +458,7 @@ struct smmo_nbody {
   uint32_t* d_tgt = nullptr;
   double* d_ke = nullptr;
   unsigned long long* d_merges = nullptr;
+  uint32_t* d_grid = nullptr;  // counts | start | parts | ids
   float* d_ckpt = nullptr;   // nseg x 6 x n0
   float4* d_x1 = nullptr;    // ckpt x n0
   int fw_steps = 0, fw_ckpt = 0;
@@ -442,6 +515,7 @@ int smmo_nbody_create(smmo_heap* heap, int64_t n, const float* const* cols,
   if (e == cudaSuccess) e = cudaMalloc(&w->d_tgt, sizeof(uint32_t) * n);
   if (e == cudaSuccess) e = cudaMalloc(&w->d_ke, sizeof(double) * n);
   if (e == cudaSuccess) e = cudaMalloc(&w->d_merges, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&w->d_grid, sizeof(uint32_t) * (2 * (size_t)NB_HASH + 1 + 256 + (size_t)n));
   if (e == cudaSuccess) e = cudaMemsetAsync(w->d_merges, 0, sizeof(unsigned long long), s);
   int32_t* ids = nullptr;
   if (e == cudaSuccess) e = cudaMallocAsync(&ids, sizeof(int32_t) * n, s);
@@ -488,7 +562,26 @@ int smmo_nbody_step(smmo_nbody* w, int nsteps, void* stream) {
       if (e != cudaSuccess) return cuda_status(e);
       st = pdo(w, &launch_do_all<Stage>, a, s);
       if (st) return st;
-      k_merge_prepare<<<tiled_grid(w->heap), 256, 0, s>>>(w->heap->view, w->cls, a);
+      GridArgs g;
+      g.S = w->d_S;
+      g.cnt = w->d_grid;
+      g.start = w->d_grid + NB_HASH;
+      g.part = w->d_grid + 2 * NB_HASH + 1;
+      g.ids = w->d_grid + 2 * NB_HASH + 1 + 256;
+      g.tgt = w->d_tgt;
+      g.n0 = w->n0;
+      g.inv_edge = 1.0 / ((double)w->p.merge_r * 1.0001);
+      g.R2 = a.R2;
+      const unsigned gb = (unsigned)((w->n0 + 255) / 256);
+      e = cudaMemsetAsync(g.cnt, 0, sizeof(uint32_t) * NB_HASH, s);
+      if (e != cudaSuccess) return cuda_status(e);
+      k_grid_count<<<gb, 256, 0, s>>>(g);
+      k_grid_scan_local<<<NB_HASH / 4096, 1024, 0, s>>>(g);
+      k_grid_scan_top<<<1, 256, 0, s>>>(g, NB_HASH / 4096);
+      e = cudaMemsetAsync(g.cnt, 0, sizeof(uint32_t) * NB_HASH, s);
+      if (e != cudaSuccess) return cuda_status(e);
+      k_grid_scatter<<<gb, 256, 0, s>>>(g);
+      k_grid_merge_prepare<<<gb, 256, 0, s>>>(g);
       st = cuda_status(cudaGetLastError());
       if (!st) st = pdo(w, &launch_do_all<MergePerform>, a, s);
       if (st) return st;
@@ -596,6 +689,7 @@ int smmo_nbody_destroy(smmo_nbody* w) {
   if (!w) return SMMO_E_INVALID_ARG;
   cudaFree(w->d_S); cudaFree(w->d_A); cudaFree(w->d_hmap); cudaFree(w->d_tgt);
   cudaFree(w->d_ke); cudaFree(w->d_merges);
+  if (w->d_grid) cudaFree(w->d_grid);
   if (w->d_ckpt) cudaFree(w->d_ckpt);
   if (w->d_x1) cudaFree(w->d_x1);
   delete w;
