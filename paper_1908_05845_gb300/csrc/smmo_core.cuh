@@ -138,12 +138,24 @@ __device__ __forceinline__ int nth_set_bit(unsigned long long b, int n) {
   return b ? __ffsll((long long)b) - 1 : -1;
 }
 
+// Position of set bit number n (0-based, n < popcount(b)) of b, by binary
+// search on population counts of halves.
+__device__ __forceinline__ int nth_set_bit64(unsigned long long b, uint32_t n) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 32; w >= 1; w >>= 1) {
+    const uint32_t c = __popcll(b & ((1ull << w) - 1));
+    if (n >= c) { n -= c; b >>= w; pos += w; }
+  }
+  return pos;
+}
+
 // ---------------------------------------------------- hierarchical bitmaps
 // Blocking set/clear of bit `pos` at level l >= 1 (higher levels are always
 // changed with the blocking form, Sec. 5.3.1 "set and clear with atomic
 // operations"), then propagation upwards while a container changes between
 // empty and non-empty.
-static __device__ __noinline__ void bm_propagate(const HeapView& h, int k, int l, uint32_t pos,
+static __device__ __forceinline__ void bm_propagate(const HeapView& h, int k, int l, uint32_t pos,
                                           bool set) {
   for (; l < (int)h.nlevels; ++l) {
     unsigned long long* w = bm_level(h, k, l) + (pos >> 6);
@@ -203,18 +215,19 @@ __device__ __forceinline__ bool bm_get(const HeapView& h, int k, uint32_t pos) {
   return (ld_cg(bm_level(h, k, 0) + (pos >> 6)) >> (pos & 63)) & 1;
 }
 
-// Top-down search for any set bit (Alg. 5.4 try_find_set), each container
-// rotated by a seed-dependent amount before find-first-set (Sec. 5.3.2,
-// "bitmap rotation").  Returns -1 (FAIL) on an empty or inconsistent path.
+// Top-down search for any set bit (Alg. 5.4 try_find_set).  Against
+// contention (the purpose of the bitmap rotation of Sec. 5.3.2) each level
+// picks a seed-dependent set bit uniformly among the set bits of the
+// container: rotation followed by find-first-set favours the first set bit
+// after a gap, so when the set bits are clustered most threads would land on
+// the same container.  Returns -1 (FAIL) on an empty or inconsistent path.
 __device__ __forceinline__ int bm_try_find_set(const HeapView& h, int k, uint32_t seed) {
   uint32_t idx = 0;
   for (int l = (int)h.nlevels - 1; l >= 0; --l) {
     const unsigned long long w = ld_cg(bm_level(h, k, l) + idx);
     if (w == 0) return -1;
-    const int rot = mix32(seed + 0x9E3779B9u * (uint32_t)(l + 1)) & 63;
-    const unsigned long long r = rot ? ((w >> rot) | (w << (64 - rot))) : w;
-    const int b = ((__ffsll((long long)r) - 1) + rot) & 63;
-    idx = idx * 64 + (uint32_t)b;
+    const uint32_t pick = mix32(seed + 0x9E3779B9u * (uint32_t)(l + 1)) % (uint32_t)__popcll(w);
+    idx = idx * 64 + (uint32_t)nth_set_bit64(w, pick);
   }
   return idx < h.num_blocks ? (int)idx : -1;
 }
@@ -256,7 +269,7 @@ __device__ __forceinline__ uint32_t type_of(const HeapView& h, uint32_t handle) 
 // block-state bitmap changes are collected as pending +1/-1 operations first
 // and then retried with try_ operations in one converged loop, so no lane
 // waits on a bit that another lane of its own warp has yet to flip.
-static __device__ __noinline__ void dealloc_bits(const HeapView& h, uint32_t bid, uint32_t t,
+static __device__ __forceinline__ void dealloc_bits(const HeapView& h, uint32_t bid, uint32_t t,
                                                  unsigned long long bits) {
   const unsigned long long capmask = __ldg(&h.cls[t].capmask);
   const uint32_t dlim = __ldg(&h.cls[t].dlimit);
@@ -315,7 +328,7 @@ __device__ __forceinline__ void smmo_delete(const HeapView& h, uint32_t handle) 
 // the thread that fills the block removes it from active, the one that
 // takes it above dlimit removes it from the candidates).  If the block was
 // re-initialised to another class the reservation is rolled back (Alg. 5.1).
-static __device__ __noinline__ unsigned long long reserve_in(const HeapView& h, uint32_t c, uint32_t bid,
+static __device__ __forceinline__ unsigned long long reserve_in(const HeapView& h, uint32_t c, uint32_t bid,
                                                              int n) {
   for (int s = 0; s < h.bitmap_spins; ++s) {
     const unsigned long long cur = ld_cg(h.alloc_bm + bid);
@@ -354,7 +367,7 @@ static __device__ __noinline__ unsigned long long reserve_in(const HeapView& h, 
 // is free, any active block with room.  Lookups retry with rotation
 // (Sec. 5.3.2).  Returns the reserved slot bits and the block in *bid_out
 // (kNull: the heap is exhausted).
-static __device__ __noinline__ unsigned long long refill_reserve(const HeapView& h, uint32_t c,
+static __device__ __forceinline__ unsigned long long refill_reserve(const HeapView& h, uint32_t c,
                                                                  uint32_t seed, uint32_t* bid_out) {
   for (int r = 0; r < h.lookup_retries; ++r) {
     const int b = bm_try_find_set(h, bm_defrag(h, c), seed + 104729u * (uint32_t)r);
@@ -426,8 +439,8 @@ __device__ __forceinline__ void alloc_cache_flush(const HeapView& h) {
   }
 }
 
-// Refills an empty warp-cache entry (out of line: the global path is long).
-static __device__ __noinline__ unsigned long long cache_refill(const HeapView& h, uint32_t c,
+// Refills an empty warp-cache entry.
+static __device__ __forceinline__ unsigned long long cache_refill(const HeapView& h, uint32_t c,
                                                                uint32_t seed, uint32_t* bid) {
   count(h, SMMO_CTR_REFILL, 1);
   return refill_reserve(h, c, seed, bid);
@@ -435,7 +448,7 @@ static __device__ __noinline__ unsigned long long cache_refill(const HeapView& h
 
 // Takes up to n slots of class c from the calling warp's cache, refilling
 // it when empty.  Returns the slot bits (possibly fewer or none) and the
-// block in *bid (kNull: heap exhausted).  The cache-hit path is inline.
+// block in *bid (kNull: heap exhausted).
 __device__ __forceinline__ unsigned long long cache_take(const HeapView& h, uint32_t c, int n,
                                                          uint32_t seed, uint32_t* bid) {
   WarpAllocCache& wc = g_wcache[threadIdx.x >> 5];
