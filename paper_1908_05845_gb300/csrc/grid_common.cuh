@@ -36,8 +36,22 @@ struct Inst {
   uint32_t cell_base;
   uint32_t W;
   uint32_t H;
-  uint32_t id;  // instance number used in the random counter
+  uint32_t id;    // instance number used in the random counter
+  uint64_t wdiv;  // div_magic(W)
 };
+
+// Division by the invariant width W as a multiply-high (Granlund and
+// Montgomery, PLDI 1994): with M = floor((2^64 - 1) / W) + 1 the product
+// lc M / 2^64 exceeds lc / W by less than lc / 2^64 < 1 / W for lc < 2^32,
+// too little to reach the next integer, so its floor is floor(lc / W).
+__host__ __device__ inline uint64_t div_magic(uint32_t W) { return ~0ull / W + 1; }
+
+// (x, y) of local cell lc of instance in (row-major, width W).
+__device__ __forceinline__ void cell_xy(const Inst* in, uint32_t lc, uint32_t* x, uint32_t* y) {
+  const uint32_t q = (uint32_t)__umul64hi((unsigned long long)lc, in->wdiv);
+  *y = q;
+  *x = lc - q * in->W;
+}
 
 // Instance owning global cell g (instances sorted by cell_base).
 __device__ __forceinline__ const Inst* find_inst(const Inst* tab, uint32_t n, uint32_t g) {

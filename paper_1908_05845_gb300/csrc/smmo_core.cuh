@@ -360,15 +360,33 @@ static __device__ __forceinline__ unsigned long long reserve_in(const HeapView& 
   return 0;
 }
 
-// Finds room for a warp's cache: (1) a defragmentation candidate, i.e. a
-// block at most dlimit full, so one reservation yields many slots; (2) a
-// fresh block from the free bitmap, initialised full for the caller
-// (initialize_block, Alg. 5.10, opening no slot to others); (3) when no block
-// is free, any active block with room.  Lookups retry with rotation
-// (Sec. 5.3.2).  Returns the reserved slot bits and the block in *bid_out
-// (kNull: the heap is exhausted).
+// Finds room for a warp's cache: (0) near the hint (the block whose objects
+// the warp is running a method on): the hint block itself if it is of class
+// c and has a free slot, else a defragmentation candidate among the 64
+// blocks of the hint's level-0 bitmap word, so that new objects land next to
+// the objects that created them (in the cellular workloads, next to them in
+// space, which keeps neighbour accesses of later do-alls coalesced); (1) any
+// defragmentation candidate, i.e. a block at most dlimit full, so one
+// reservation yields many slots; (2) a fresh block from the free bitmap,
+// initialised full for the caller (initialize_block, Alg. 5.10, opening no
+// slot to others); (3) when no block is free, any active block with room.
+// Lookups retry with a new random choice (Sec. 5.3.2).  Returns the reserved
+// slot bits and the block in *bid_out (kNull: the heap is exhausted).
 static __device__ __forceinline__ unsigned long long refill_reserve(const HeapView& h, uint32_t c,
-                                                                 uint32_t seed, uint32_t* bid_out) {
+                                                                 uint32_t seed, uint32_t hint,
+                                                                 uint32_t* bid_out) {
+  if (hint < h.num_blocks) {
+    if (__ldcg(h.block_type + hint) == c && ~ld_cg(h.alloc_bm + hint) != 0) {
+      const unsigned long long got = reserve_in(h, c, hint, 64);
+      if (got) { *bid_out = hint; return got; }
+    }
+    const unsigned long long w = ld_cg(bm_level(h, bm_defrag(h, c), 0) + (hint >> 6));
+    if (w) {
+      const uint32_t b = (hint & ~63u) + (uint32_t)nth_set_bit64(w, mix32(seed) % (uint32_t)__popcll(w));
+      const unsigned long long got = b < h.num_blocks ? reserve_in(h, c, b, 64) : 0ull;
+      if (got) { *bid_out = b; return got; }
+    }
+  }
   for (int r = 0; r < h.lookup_retries; ++r) {
     const int b = bm_try_find_set(h, bm_defrag(h, c), seed + 104729u * (uint32_t)r);
     if (b < 0) {
@@ -402,7 +420,8 @@ static __device__ __forceinline__ unsigned long long refill_reserve(const HeapVi
   return 0;
 }
 
-// Per-warp allocation cache (shared memory, one slot per warp and class).
+// Per-warp allocation cache (shared memory, one slot per warp and class,
+// plus the block the warp is working on as a placement hint).
 // When a warp runs out of cached slots its leader refills the cache with
 // every free slot of the block refill_reserve finds; later allocations of
 // the same warp are served from the cached bits without touching global
@@ -415,6 +434,7 @@ static __device__ __forceinline__ unsigned long long refill_reserve(const HeapVi
 struct WarpAllocCache {
   unsigned long long bits[SMMO_MAX_CLASSES];
   uint32_t bid[SMMO_MAX_CLASSES];
+  uint32_t hint;
   int lock;
 };
 static __shared__ WarpAllocCache g_wcache[32];
@@ -425,7 +445,7 @@ __device__ __forceinline__ void alloc_cache_init() {
     g_wcache[threadIdx.x >> 5].bid[lane] = kNull;
     g_wcache[threadIdx.x >> 5].bits[lane] = 0;
   }
-  if (lane == 0) g_wcache[threadIdx.x >> 5].lock = 0;
+  if (lane == 0) { g_wcache[threadIdx.x >> 5].lock = 0; g_wcache[threadIdx.x >> 5].hint = kNull; }
   __syncwarp();
 }
 
@@ -443,7 +463,7 @@ __device__ __forceinline__ void alloc_cache_flush(const HeapView& h) {
 static __device__ __forceinline__ unsigned long long cache_refill(const HeapView& h, uint32_t c,
                                                                uint32_t seed, uint32_t* bid) {
   count(h, SMMO_CTR_REFILL, 1);
-  return refill_reserve(h, c, seed, bid);
+  return refill_reserve(h, c, seed, g_wcache[threadIdx.x >> 5].hint, bid);
 }
 
 // Takes up to n slots of class c from the calling warp's cache, refilling
@@ -525,10 +545,14 @@ __device__ __forceinline__ uint32_t smmo_new(const HeapView& h, uint32_t c) {
 }
 
 // ---------------------------------------------------------------- do-all
-// Persistent grid-stride do-all over the enumerated blocks (Sec. 5.2.7):
-// the slots of one block are handled by consecutive threads (one warp per
-// 32 slots), thread t of a block's group handles slot t, and a slot runs the
-// method iff its bit is set in the snapshot taken at enumeration time.
+// Persistent do-all over the enumerated blocks (Sec. 5.2.7): the slots of
+// one block are handled by consecutive threads (one warp per 32 slots, a
+// "unit"), thread t of a block's group handles slot t, and a slot runs the
+// method iff its bit is set in the snapshot taken at enumeration time.  Each
+// warp takes one contiguous run of units (rather than every nwarps-th), so
+// that consecutive units of a warp are neighbouring blocks and the warp's
+// allocation cache, refilled near the current block, keeps new objects close
+// to their creators.
 template <class M>
 __global__ void __launch_bounds__(512, 3) do_all_kernel(HeapView h, uint32_t c,
                                                      typename M::Args args) {
@@ -540,10 +564,14 @@ __global__ void __launch_bounds__(512, 3) do_all_kernel(HeapView h, uint32_t c,
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   alloc_cache_init();
   uint32_t visited = 0;
-  for (uint32_t u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units; u += nwarps) {
+  const uint32_t per = (units + nwarps - 1) / nwarps;
+  const uint32_t ub = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * per;
+  const uint32_t ue = ub + per < units ? ub + per : units;
+  for (uint32_t u = ub; u < ue; ++u) {
     const uint32_t i = halves == 2 ? (u >> 1) : u;
     const uint32_t slot = (halves == 2 ? (u & 1) * 32 : 0) + lane;
     const REntry e = h.R[i];
+    g_wcache[threadIdx.x >> 5].hint = e.block;
     if (lane == 0) visited += __popcll(halves == 2 ? (e.bits >> ((u & 1) * 32)) & 0xFFFFFFFFull : e.bits);
     if ((e.bits >> slot) & 1) M::run(h, args, c, (e.block << 6) | slot);
     __syncwarp();  // reconverge: lane groups never run different iterations

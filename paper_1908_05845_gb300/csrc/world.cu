@@ -67,6 +67,16 @@ __device__ __forceinline__ unsigned long long req_key(uint32_t t, uint32_t phase
   return ((unsigned long long)(0xFFFFFFFFu - (2u * t + phase)) << 32) | src;
 }
 
+// The (r mod k)-th of the k directions set in mask (in direction order 0..3),
+// as the neighbour cell nb[d]; every index is a constant, so nb stays in
+// registers.
+__device__ __forceinline__ uint32_t pick_dir(const uint32_t (&nb)[4], uint32_t mask, uint32_t r) {
+  uint32_t k = r % (uint32_t)__popc(mask);
+  while (k--) mask &= mask - 1;
+  const int d = __ffs(mask) - 1;
+  return d == 0 ? nb[0] : d == 1 ? nb[1] : d == 2 ? nb[2] : nb[3];
+}
+
 struct FishPrepare {
   using Args = WorldArgs;
   __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
@@ -75,19 +85,19 @@ struct FishPrepare {
     *agep = (int16_t)(*agep + 1);
     const Inst* in = find_inst(a.winst, a.nwinst, g);
     const uint32_t lc = g - in->cell_base, W = in->W, H = in->H;
-    const uint32_t x = lc % W, y = lc / W;
-    uint32_t cand[4];
-    int nc = 0;
+    uint32_t x, y;
+    cell_xy(in, lc, &x, &y);
+    uint32_t nb[4], empty = 0;
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
-      const uint32_t n = in->cell_base + torus_nb4(x, y, W, H, d);
-      if (*a.cells.col<uint32_t>(n, a.occ_off) == kNull) cand[nc++] = n;
+      nb[d] = in->cell_base + torus_nb4(x, y, W, H, d);
+      if (*a.cells.col<uint32_t>(nb[d], a.occ_off) == kNull) empty |= 1u << d;
     }
     uint32_t tgt = g;
-    if (nc) {
+    if (empty) {
       const uint32_t t = *a.tp;
       const uint32_t r = philox_draw(a.seed, TAG_FISH, t, lc, in->id);
-      tgt = cand[r % (uint32_t)nc];
+      tgt = pick_dir(nb, empty, r);
       atomicMin(a.cells.col<unsigned long long>(tgt, a.req_off), req_key(t, a.phase, g));
     }
     *fld<int32_t>(h, self, a.f_target) = (int32_t)tgt;
@@ -134,20 +144,20 @@ struct SharkPrepare {
     if (en != 0) {
       const Inst* in = find_inst(a.winst, a.nwinst, g);
       const uint32_t lc = g - in->cell_base, W = in->W, H = in->H;
-      const uint32_t x = lc % W, y = lc / W;
-      uint32_t fishc[4], emptyc[4];
-      int nf = 0, ne = 0;
+      uint32_t x, y;
+      cell_xy(in, lc, &x, &y);
+      uint32_t nb[4], fish = 0, empty = 0;
 #pragma unroll
       for (int d = 0; d < 4; ++d) {
-        const uint32_t n = in->cell_base + torus_nb4(x, y, W, H, d);
-        const uint32_t o = *a.cells.col<uint32_t>(n, a.occ_off);
-        if (o == kNull) emptyc[ne++] = n;
-        else if (type_of(h, o) == a.fish) fishc[nf++] = n;
+        nb[d] = in->cell_base + torus_nb4(x, y, W, H, d);
+        const uint32_t o = *a.cells.col<uint32_t>(nb[d], a.occ_off);
+        if (o == kNull) empty |= 1u << d;
+        else if (type_of(h, o) == a.fish) fish |= 1u << d;
       }
-      if (nf || ne) {
+      if (fish | empty) {
         const uint32_t t = *a.tp;
         const uint32_t r = philox_draw(a.seed, TAG_SHARK, t, lc, in->id);
-        tgt = nf ? fishc[r % (uint32_t)nf] : emptyc[r % (uint32_t)ne];
+        tgt = pick_dir(nb, fish ? fish : empty, r);
         atomicMin(a.cells.col<unsigned long long>(tgt, a.req_off), req_key(t, a.phase, g));
       }
     }
@@ -225,7 +235,9 @@ struct CandPrepare {
     const uint32_t g = *fld<int32_t>(h, self, a.c_cell);
     const Inst* in = find_inst(a.linst, a.nlinst, g);
     const uint32_t lc = g - in->cell_base;
-    const int n = alive_neighbours(h, a, in, lc % in->W, lc / in->W);
+    uint32_t x, y;
+    cell_xy(in, lc, &x, &y);
+    const int n = alive_neighbours(h, a, in, x, y);
     *fld<uint8_t>(h, self, a.c_action) = n == 3 ? ACT_BORN : (n == 0 ? ACT_DELETE : ACT_KEEP);
   }
 };
@@ -237,7 +249,9 @@ struct AlivePrepare {
     *fld<uint8_t>(h, self, a.a_isnew) = 0;
     const Inst* in = find_inst(a.linst, a.nlinst, g);
     const uint32_t lc = g - in->cell_base;
-    const int n = alive_neighbours(h, a, in, lc % in->W, lc / in->W);
+    uint32_t x, y;
+    cell_xy(in, lc, &x, &y);
+    const int n = alive_neighbours(h, a, in, x, y);
     *fld<uint8_t>(h, self, a.a_action) = (n == 2 || n == 3) ? ACT_KEEP : ACT_DIE;
   }
 };
@@ -271,14 +285,16 @@ struct AliveUpdate {
       // cell e is the first new Alive of e's neighbourhood in scan order
       const Inst* in = find_inst(a.linst, a.nlinst, g);
       const uint32_t lc = g - in->cell_base, W = in->W, H = in->H;
-      const uint32_t x = lc % W, y = lc / W;
+      uint32_t x, y;
+      cell_xy(in, lc, &x, &y);
       for (int dx = -1; dx <= 1; ++dx)
         for (int dy = -1; dy <= 1; ++dy) {
           const uint32_t el = torus8(x, y, dx, dy, W, H);
           const uint32_t e = in->cell_base + el;
           uint32_t* eocc = a.cells.col<uint32_t>(e, a.occ_off);
           if (*(volatile uint32_t*)eocc != kNull) continue;
-          const uint32_t ex = el % W, ey = el / W;
+          uint32_t ex, ey;
+          cell_xy(in, el, &ex, &ey);
           uint32_t first = kNull;
           for (int ddx = -1; ddx <= 1 && first == kNull; ++ddx)
             for (int ddy = -1; ddy <= 1; ++ddy) {
@@ -509,7 +525,7 @@ int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32
     w->W.push_back(W[i]);
     w->H.push_back(H[i]);
     w->base.push_back((uint32_t)w->total_cells);
-    Inst in{(uint32_t)w->total_cells, W[i], H[i], (uint32_t)i};
+    Inst in{(uint32_t)w->total_cells, W[i], H[i], (uint32_t)i, div_magic(W[i])};
     (kind[i] == SMMO_WORLD_WATOR ? wi : li).push_back(in);
     w->total_cells += (uint64_t)W[i] * H[i];
   }
