@@ -136,6 +136,13 @@ typedef struct {
   int64_t objects_moved;
   int64_t pointers_rewritten;
   int64_t candidates_left;    /* candidates after the last pass          */
+  /* device time of the phases, summed over passes (CUDA events on the
+   * stream): candidate scan and sorted list; object copy and forwarding
+   * pointers; block-state update; pointer rewrite (with its enumeration) */
+  double scan_ms;
+  double copy_ms;
+  double state_ms;
+  double rewrite_ms;
 } smmo_compact_stats;
 
 /* ------------------------------------------------------------- heap */

@@ -325,6 +325,15 @@ static int launch_enumerate(smmo_heap* h, int c, cudaStream_t s) {
 
 int enumerate(smmo_heap* h, int c, cudaStream_t s) { return launch_enumerate(h, c, s); }
 
+// Enumeration scratch: one REntry per block, and at least room for the
+// compaction scan's per-word offsets and per-chunk totals (level-0 words
+// rounded up to 1024, plus 1024), which reuse it.
+static uint64_t rscratch_bytes(uint64_t M) {
+  const uint64_t words = (M + 63) / 64;
+  const uint64_t scan = ((words + 1023) / 1024 * 1024 + 1024) * 4;
+  return std::max<uint64_t>(M * 16, scan);
+}
+
 int freeze(smmo_heap* h, cudaStream_t s) {
   if (h->frozen) return SMMO_OK;
   const int nc = (int)h->classes.size();
@@ -392,7 +401,7 @@ int freeze(smmo_heap* h, cudaStream_t s) {
   auto need_bytes = [&](uint64_t M) {
     uint32_t lw[SMMO_MAX_LEVELS], lo[SMMO_MAX_LEVELS], nl;
     const uint64_t bw = bm_geom(M, lw, lo, &nl);
-    return fixed + align_up(M * 8, 256) + align_up(M * 4, 256) + align_up(M * 16, 256) +
+    return fixed + align_up(M * 8, 256) + align_up(M * 4, 256) + align_up(rscratch_bytes(M), 256) +
            align_up(M * 4 + 1024, 256) + align_up(bw * 8 * nbm, 256) + M * block_bytes;
   };
   uint64_t M = h->buf_bytes / (block_bytes + 40);
@@ -410,7 +419,7 @@ int freeze(smmo_heap* h, cudaStream_t s) {
   v.cls = h->d_layouts;
   v.alloc_bm = (unsigned long long*)take(M * 8);
   v.block_type = (uint32_t*)take(M * 4);
-  v.R = (REntry*)take(M * 16);
+  v.R = (REntry*)take(rscratch_bytes(M));
   h->d_scratch = (uint32_t*)take(M * 4 + 1024);
   v.bitmaps = (unsigned long long*)take(bw * 8 * nbm);
   v.data = p;

@@ -64,6 +64,16 @@ struct Replace {
   }
 };
 
+// HANDLE column col_ref = table[int32 column col_idx] (wiring references
+// between classes after both were created).
+struct SetRefFrom {
+  struct Args { uint32_t col_ref; uint32_t col_idx; const uint32_t* table; };
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
+    const int32_t i = *field_ptr<int32_t>(h, __ldg(&h.cls[c].col_off[a.col_idx]), self);
+    *field_ptr<uint32_t>(h, __ldg(&h.cls[c].col_off[a.col_ref]), self) = a.table[i];
+  }
+};
+
 }  // namespace
 
 const smmo::MethodEntry g_methods_test[] = {
@@ -72,5 +82,6 @@ const smmo::MethodEntry g_methods_test[] = {
     SMMO_METHOD("test.free_self_if", FreeSelfIf),
     SMMO_METHOD("test.free_ref", FreeRef),
     SMMO_METHOD("test.replace", Replace),
+    SMMO_METHOD("test.set_ref_from", SetRefFrom),
 };
 const int g_methods_test_n = sizeof(g_methods_test) / sizeof(g_methods_test[0]);

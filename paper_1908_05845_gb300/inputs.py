@@ -25,6 +25,12 @@ OpenStreetMap street networks -- are not available, these stand in for them):
   from Box-Muller on u_3..u_10 in float64, rounded to float32 once.
 * Batched: instance i is Life if draw(KIND, 0, i) & 1 else Wa-Tor, side
   floor(64 * 16^u) with u = draw(SIDE, 0, i) / 2^32 (log-uniform 64..1024).
+* Compaction (the thesis' synthetic defragmentation benchmark, Sec. 6.4):
+  two classes of n objects each that point at each other at random; object
+  i of the first class dies iff draw(KILL, 0, i) < floor(0.6 * 2^32), refers
+  to object draw(AREF, 0, i) % n of the second class, and object j of the
+  second class refers to object draw(BREF, 0, j) % n of the first class
+  (null when that one dies).
 """
 from __future__ import annotations
 
@@ -32,6 +38,7 @@ import numpy as np
 
 TAG_INIT, TAG_FISH, TAG_SHARK, TAG_LEN, TAG_PLACE, TAG_ROUTE, TAG_BRAKE = 0, 1, 2, 3, 4, 5, 6
 TAG_KIND, TAG_SIDE, TAG_OUTDEG, TAG_OUT, TAG_NBODY = 7, 8, 9, 10, 11
+TAG_KILL, TAG_AREF, TAG_BREF = 12, 13, 14
 
 _M0, _M1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
 _W0, _W1 = np.uint32(0x9E3779B9), np.uint32(0xBB67AE85)
@@ -166,3 +173,14 @@ def batched_instances(seed: int, n: int = 256, side_min: int = 64, ratio: float 
     u = draw(seed, TAG_SIDE, 0, i).astype(np.float64) / 2.0 ** 32
     side = np.floor(side_min * ratio ** u).astype(np.int32)
     return kind, side
+
+
+# -------------------------------------------------------------- compaction
+def compact_synthetic(n: int, seed: int, kill=(3, 5)):
+    """(kill mask of the first class, its references into the second class,
+    the second class's references into the first) as index arrays."""
+    i = np.arange(n, dtype=np.uint32)
+    dead = (draw(seed, TAG_KILL, 0, i) < np.uint32(threshold(*kill))).astype(np.int32)
+    a_ref = (draw(seed, TAG_AREF, 0, i) % np.uint32(n)).astype(np.int64)
+    b_ref = (draw(seed, TAG_BREF, 0, i) % np.uint32(n)).astype(np.int64)
+    return dead, a_ref, b_ref

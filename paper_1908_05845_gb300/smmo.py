@@ -91,7 +91,8 @@ class HeapStats(ctypes.Structure):
 class CompactStats(ctypes.Structure):
     _fields_ = [("passes", ctypes.c_int32), ("blocks_freed", ctypes.c_int64),
                 ("objects_moved", ctypes.c_int64), ("pointers_rewritten", ctypes.c_int64),
-                ("candidates_left", ctypes.c_int64)]
+                ("candidates_left", ctypes.c_int64), ("scan_ms", ctypes.c_double),
+                ("copy_ms", ctypes.c_double), ("state_ms", ctypes.c_double), ("rewrite_ms", ctypes.c_double)]
 
 
 def default_config(**kw) -> HeapConfig:
@@ -312,3 +313,7 @@ class FreeRefArgs(ctypes.Structure):
 
 class ReplaceArgs(ctypes.Structure):
     _fields_ = [("target", ctypes.c_uint32), ("col", ctypes.c_uint32), ("tcol", ctypes.c_uint32)]
+
+
+class SetRefFromArgs(ctypes.Structure):
+    _fields_ = [("col_ref", ctypes.c_uint32), ("col_idx", ctypes.c_uint32), ("table", ctypes.c_void_p)]

@@ -213,3 +213,63 @@ class Traffic:
             self.close()
         except Exception:
             pass
+
+
+class CompactSynthetic:
+    """The thesis' synthetic defragmentation benchmark (Sec. 6.4): classes A
+    and B of n objects each (32 bytes: a reference to the other class, an
+    index and padding), A objects referring to random B objects and B
+    objects to random A objects; 60 % of the A objects are deleted (B
+    references to them are null), leaving every A block about 40 % full.
+    ``verify()`` checks, after a compaction of A, that every object and
+    every reference survived the relocation."""
+
+    def __init__(self, n: int, seed: int = 1, block_data_bytes: int = 64 * 32, stream=None):
+        from . import inputs
+        dev = "cuda"
+        dead, a_ref, b_ref = inputs.compact_synthetic(n, seed)
+        self.n = n
+        self.dead = torch.as_tensor(dead, device=dev)
+        self.a_ref = torch.as_tensor(a_ref, device=dev)
+        self.b_ref = torch.as_tensor(b_ref, device=dev)
+        nbytes = int(2 * n * 32 * 1.12) + (64 << 20)
+        h = self.heap = smmo.Heap(nbytes, smmo.default_config(block_data_bytes=block_data_bytes), stream=stream)
+        # B first, so that A's reference column can name B as its target
+        # class (compacting A then scans B's references only)
+        self.B = h.register("B", [("ref", smmo.HANDLE), ("idx", smmo.I32), ("pad", smmo.I32, 6)])
+        self.A = h.register("A", [("ref", smmo.HANDLE, 1, self.B), ("idx", smmo.I32), ("dead", smmo.I32),
+                                  ("pad", smmo.I32, 5)])
+        idx = torch.arange(n, dtype=torch.int32, device=dev)
+        nul = torch.full((n,), -1, dtype=torch.int32, device=dev)
+        pad = torch.zeros(n, dtype=torch.int32, device=dev)
+        hb, _ = h.bulk_new(self.B, n, [nul, idx] + [pad] * 6, want_handles=True)
+        self.hb = hb
+        ha, _ = h.bulk_new(self.A, n, [hb[self.a_ref], idx, self.dead] + [pad] * 5, want_handles=True)
+        table = torch.where(self.dead[self.b_ref] == 1, nul, ha[self.b_ref]).contiguous()
+        h.parallel_do(self.B, "test.set_ref_from", smmo.SetRefFromArgs(0, 1, table.data_ptr()))
+        h.parallel_do(self.A, "test.free_self_if", smmo.FreeSelfIfArgs(2, 2, 1))
+        h.sync()
+        del table, ha, nul, pad, idx
+        self.survivors = int(n - int(self.dead.sum()))
+
+    def verify(self) -> dict:
+        """Relocation checks after compact(A): A keeps exactly the survivors
+        with their fields; every B reference leads to the A object it led to
+        before (same index), or stays null."""
+        h = self.heap
+        ha = h.enumerate_live(self.A)
+        ai, aref, adead = h.gather(self.A, ha, ["idx", "ref", "dead"])
+        ok_a = (ha.numel() == self.survivors and bool((adead == 0).all())
+                and bool((aref == self.hb[self.a_ref[ai.long()]]).all())
+                and int(torch.unique(ai).numel()) == self.survivors)
+        hbl = h.enumerate_live(self.B)
+        bi, bref = h.gather(self.B, hbl, ["idx", "ref"])
+        want_null = self.dead[self.b_ref[bi.long()]] == 1
+        null_ok = bool((bref[want_null] == -1).all())
+        live_refs = bref[~want_null]
+        (ti,) = h.gather(self.A, live_refs, ["idx"])
+        ok_b = null_ok and bool((ti.long() == self.b_ref[bi.long()][~want_null]).all())
+        return {"a_objects_ok": ok_a, "b_references_ok": ok_b, "heap_violations": h.check()}
+
+    def close(self):
+        self.heap.close()

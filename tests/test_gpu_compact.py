@@ -122,3 +122,26 @@ def test_wator_with_periodic_compaction_matches_oracle(orc):
         assert np.array_equal(g, w)
     assert sim.heap.check() == 0
     sim.sync()
+
+
+def test_synthetic_two_class_benchmark_small():
+    """The synthetic defragmentation benchmark (Sec. 6.4) at 64 x 1000
+    objects per class: after compact(A, n=3) every A object survives with
+    its fields, every B reference leads to the same A object as before, no
+    A candidate (fill <= 48 of 64) is left, and the phases were timed."""
+    from paper_1908_05845_gb300.workloads import CompactSynthetic
+    w = CompactSynthetic(64 * 1000, seed=2)
+    h = w.heap
+    st0 = h.stats()
+    assert st0["live_objects"][w.A] == w.survivors
+    assert 0.55 < 1 - w.survivors / w.n < 0.65
+    st = h.compact(w.A, n=3, k1=0)
+    v = w.verify()
+    assert v == {"a_objects_ok": True, "b_references_ok": True, "heap_violations": 0}
+    assert st["candidates_left"] < 4 and st["passes"] >= 2
+    assert st["objects_moved"] > 0 and st["pointers_rewritten"] > 0
+    assert min(st["scan_ms"], st["copy_ms"], st["state_ms"], st["rewrite_ms"]) > 0
+    st1 = h.stats()
+    assert st1["blocks"][w.A] < st0["blocks"][w.A] * 0.6
+    assert st1["fragmentation"][w.A] < 0.25 + 1.0 / 64
+    w.close()
