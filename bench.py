@@ -645,10 +645,10 @@ def run_compact(args):
     obj = 32
     moved, rew, passes = st["objects_moved"], st["pointers_rewritten"], st["passes"]
     # algorithmic bytes: copy = read + write of each moved object and its
-    # forwarding handle; rewrite = every B reference read once per pass plus
-    # a read of the forwarding handle and a write per rewritten reference
+    # forwarding handle; rewrite (once, after all passes) = every B
+    # reference read plus a forwarding read and a write per rewritten one
     copy_bytes = moved * (2 * obj + 4)
-    rewrite_bytes = passes * n * 4 + rew * 8
+    rewrite_bytes = n * 4 + rew * 8
     hbm = (load_peaks() or {}).get("hbm_gbs")
     copy_gbs = copy_bytes / (st["copy_ms"] * 1e6) if st["copy_ms"] else None
     rew_gbs = rewrite_bytes / (st["rewrite_ms"] * 1e6) if st["rewrite_ms"] else None

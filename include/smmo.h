@@ -136,9 +136,10 @@ typedef struct {
   int64_t objects_moved;
   int64_t pointers_rewritten;
   int64_t candidates_left;    /* candidates after the last pass          */
-  /* device time of the phases, summed over passes (CUDA events on the
-   * stream): candidate scan and sorted list; object copy and forwarding
-   * pointers; block-state update; pointer rewrite (with its enumeration) */
+  /* device time of the phases (CUDA events on the stream), summed over
+   * passes: candidate scan and sorted list; object copy and forwarding
+   * pointers; block-state update; and the final pointer rewrite (with its
+   * enumeration of each referring class) */
   double scan_ms;
   double copy_ms;
   double state_ms;
@@ -222,10 +223,14 @@ int smmo_gather_fields(smmo_heap* heap, int class_id, const smmo_handle* handles
 /* Defragments class_id (CompactGpu, Ch. 6): passes of (1) candidate scan
  * (blocks at most n/(n+1) full, Sec. 6.3.1), (2) source/target assignment
  * (first B = floor(r/(n+1)) candidates are sources, Sec. 6.3.3), (3) object
- * copy, (4) forwarding pointers in the source blocks, (5) rewrite of every
- * HANDLE column referring to class_id or a superclass, (6) block-state
- * update, until at most k1 candidates remain (Sec. 6.3.7).  Handles held
- * outside the heap are invalidated.  Synchronises `stream`. */
+ * copy, (4) forwarding pointers in the source blocks, (5) block-state
+ * update, until at most k1 candidates remain (Sec. 6.3.7); then (6) one
+ * rewrite of every HANDLE column that may refer to class_id (ref_class
+ * class_id, a superclass of it, or -1), following forwarding pointers
+ * through all passes (Alg. 6.6; the thesis rewrites after each pass, with
+ * the same result).  n in 1..63, k1 >= 0.  Handles held outside the heap
+ * are invalidated.  Allocates nothing (its scratch is part of the heap
+ * buffer).  Synchronises `stream`. */
 int smmo_compact(smmo_heap* heap, int class_id, int defrag_factor,
                  int64_t k1, smmo_compact_stats* out, void* stream);
 

@@ -6,18 +6,22 @@
 //      their sorted index list R (order matters, Sec. 6.3.3);
 //   2. with B = floor(r/(n+1)), R[0..B-1] are sources and source s moves
 //      its objects into targets R[s + i B], i = 1..n (Sec. 6.3.3);
-//   3. move_objects: 64 threads per source, thread l copies the l-th object
-//      of the source into the l-th free slot across its targets (Alg. 6.4);
-//   4. place_forwarding_ptrs: a second kernel writes the new handle into the
-//      source slot (Alg. 6.5; separate so no copy reads an overwritten slot);
-//   5. block states: targets get their first m free slots marked, sources
-//      become free (Sec. 6.3.6);
-//   6. rewrite every HANDLE column that can refer to the class: a handle is
-//      forwarded iff its block is a candidate with index < R[B] (Alg. 6.6),
-//      so the forwarding slot is read only for real sources (Sec. 6.3.5).
-//      The rewrite runs after the state update so that a class referring to
-//      itself is rewritten in the moved copies, never in the dead sources.
-// Passes repeat until at most k1 candidates remain (Sec. 6.3.7).
+//   3. relocate: 64 threads per source, thread l copies the l-th object of
+//      the source into the l-th free slot across its targets (Alg. 6.4),
+//      then, after a CTA barrier (a source's 64 threads share a CTA, so no
+//      copy still reads the slot), writes the new handle into the source
+//      slot as its forwarding pointer (Alg. 6.5);
+//   4. block states: targets get their first m free slots marked, sources
+//      become free and are marked in a "moved from" bitmap (Sec. 6.3.6).
+// Passes repeat until at most k1 candidates remain (Sec. 6.3.7).  Then
+//   5. one rewrite of every HANDLE column that can refer to the class: a
+//      handle into a block that was a source in some pass is replaced by
+//      its forwarding pointer, repeatedly while the result lies in a later
+//      source (Alg. 6.6 applied to the chain of passes).
+// The thesis rewrites after every pass (Sec. 6.3.5); forwarding slots of a
+// freed source are never overwritten during the compaction (a free block is
+// no candidate), so one rewrite that follows the chain gives the same
+// handles and reads every HANDLE column once instead of once per pass.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -53,9 +57,17 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_1024(uint32_t v, uint32
   return incl - v;
 }
 
+// Pass control in device memory, so that passes run without a host round
+// trip: ctl[0] done flag, ctl[1] passes run, ctl[2] sources freed, ctl[3]
+// r of the latest scan.  Every kernel of a pass returns at once when done.
+enum { CTL_DONE = 0, CTL_PASSES = 1, CTL_FREED = 2, CTL_R = 3 };
+
+// (part and ctl may be null: the restore of the maintained candidate bitmap
+// after the compaction uses this kernel with limit = dlimit.)
 __global__ void __launch_bounds__(1024) k_cand_scan1(HeapView h, uint32_t c, uint32_t limit,
-                                                     uint32_t* part) {
+                                                     uint32_t* part, const unsigned long long* ctl) {
   __shared__ uint32_t wsum[32];
+  if (ctl && ctl[CTL_DONE]) return;
   const uint32_t blk = blockIdx.x * 1024 + threadIdx.x;  // grid covers every level-0 bit
   bool cand = false;
   if (blk < h.num_blocks) {
@@ -68,6 +80,7 @@ __global__ void __launch_bounds__(1024) k_cand_scan1(HeapView h, uint32_t c, uin
     D32[blk >> 5] = bal;  // little-endian halves of the 64-bit words
     wsum[threadIdx.x >> 5] = __popc(bal);
   }
+  if (!part) return;
   __syncthreads();
   if (threadIdx.x < 32) {
     const uint32_t t = __reduce_add_sync(0xFFFFFFFFu, wsum[threadIdx.x]);
@@ -75,9 +88,12 @@ __global__ void __launch_bounds__(1024) k_cand_scan1(HeapView h, uint32_t c, uin
   }
 }
 
-__global__ void __launch_bounds__(1024) k_cand_scan2(uint32_t* part, uint32_t nparts,
-                                                     unsigned long long* r) {
+// (2) also decides the pass: r <= k1 or fewer than n + 1 candidates ends
+// the compaction (Sec. 6.3.7).
+__global__ void __launch_bounds__(1024) k_cand_scan2(uint32_t* part, uint32_t nparts, uint32_t n,
+                                                     unsigned long long k1, unsigned long long* ctl) {
   __shared__ uint32_t sh[1024];
+  if (ctl[CTL_DONE]) return;
   uint32_t run = 0;
   for (uint32_t base = 0; base < nparts; base += 1024) {
     const uint32_t i = base + threadIdx.x;
@@ -87,12 +103,22 @@ __global__ void __launch_bounds__(1024) k_cand_scan2(uint32_t* part, uint32_t np
     if (i < nparts) part[i] = run + ex;
     run += tot;
   }
-  if (threadIdx.x == 0) *r = run;
+  if (threadIdx.x == 0) {
+    const unsigned long long B = run / (n + 1);
+    ctl[CTL_R] = run;
+    if (run <= k1 || B == 0) {
+      ctl[CTL_DONE] = 1;
+    } else {
+      ctl[CTL_PASSES] += 1;
+      ctl[CTL_FREED] += B;
+    }
+  }
 }
 
 __global__ void __launch_bounds__(1024) k_cand_scan3(HeapView h, uint32_t c, const uint32_t* part,
-                                                     uint32_t* R) {
+                                                     uint32_t* R, const unsigned long long* ctl) {
   __shared__ uint32_t wsum[32];
+  if (ctl[CTL_DONE]) return;
   const uint32_t blk = blockIdx.x * 1024 + threadIdx.x;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t bal = reinterpret_cast<const uint32_t*>(bm_level(h, bm_defrag(h, c), 0))[blk >> 5];
@@ -112,8 +138,8 @@ __global__ void __launch_bounds__(1024) k_cand_scan3(HeapView h, uint32_t c, con
   if ((bal >> lane) & 1) R[part[blockIdx.x] + wsum[warp] + __popc(bal & ((1u << lane) - 1))] = blk;
 }
 
-// Target slot of the l-th object of source s (shared by the copy and the
-// forwarding kernels): walks the n targets' free slots in order (Alg. 6.4).
+// Target slot of the l-th object of source s: walks the n targets' free
+// slots in order (Alg. 6.4).
 __device__ __forceinline__ bool target_slot(const HeapView& h, const uint32_t* R, uint32_t B,
                                             uint32_t n, uint32_t s, uint32_t l, uint32_t* t_bid,
                                             uint32_t* t_oid) {
@@ -124,7 +150,7 @@ __device__ __forceinline__ bool target_slot(const HeapView& h, const uint32_t* R
     const uint32_t nf = __popcll(tfree);
     if (t_loc < nf) {
       *t_bid = tb;
-      *t_oid = (uint32_t)nth_set_bit(tfree, (int)t_loc);
+      *t_oid = (uint32_t)nth_set_bit64(tfree, t_loc);
       return true;
     }
     t_loc -= nf;
@@ -132,62 +158,64 @@ __device__ __forceinline__ bool target_slot(const HeapView& h, const uint32_t* R
   return false;
 }
 
-__global__ void k_move_objects(HeapView h, uint32_t c, const uint32_t* R, uint32_t B, uint32_t n) {
+// Copy and forwarding pointers of one pass.  The loop runs over CTA-sized
+// chunks of (source, l) pairs so that every thread of a CTA meets the
+// barrier equally often; 256 threads hold four whole sources.
+__global__ void __launch_bounds__(256) k_relocate(HeapView h, uint32_t c, const uint32_t* R, uint32_t n,
+                                                  const unsigned long long* ctl, unsigned long long* moved) {
+  if (ctl[CTL_DONE]) return;
+  const uint32_t B = (uint32_t)(ctl[CTL_R] / (n + 1));
   const ClassLayout& L = h.cls[c];
   const uint64_t total = (uint64_t)B * 64;
-  for (uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; tid < total;
-       tid += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t s = (uint32_t)(tid / 64), l = (uint32_t)(tid % 64);
-    const uint32_t sb = R[s];
-    const unsigned long long sbits = h.alloc_bm[sb] & L.capmask;
-    if (l >= (uint32_t)__popcll(sbits)) continue;
-    uint32_t tb, to;
-    if (!target_slot(h, R, B, n, s, l, &tb, &to)) { set_error(h, SMMO_E_CONTENTION, sb); continue; }
-    const uint32_t so = (uint32_t)nth_set_bit(sbits, (int)l);
-    const uint8_t* src = block_data(h, sb);
-    uint8_t* dst = block_data(h, tb);
-    for (uint32_t k = 0; k < L.ncols; ++k) {
-      const uint32_t sz = L.col_size[k];
-      const uint8_t* p = src + L.col_off[k] + (size_t)so * sz;
-      uint8_t* q = dst + L.col_off[k] + (size_t)to * sz;
-      switch (sz) {
-        case 1: *q = *p; break;
-        case 2: *(uint16_t*)q = *(const uint16_t*)p; break;
-        case 4: *(uint32_t*)q = *(const uint32_t*)p; break;
-        default: *(uint64_t*)q = *(const uint64_t*)p; break;
+  uint32_t cnt = 0;
+  for (uint64_t base = (uint64_t)blockIdx.x * 256; base < total; base += (uint64_t)gridDim.x * 256) {
+    const uint64_t tid = base + threadIdx.x;
+    bool go = false;
+    uint32_t sb = 0, so = 0, tb = 0, to = 0;
+    if (tid < total) {
+      const uint32_t s = (uint32_t)(tid >> 6), l = (uint32_t)(tid & 63);
+      sb = R[s];
+      const unsigned long long sbits = h.alloc_bm[sb] & L.capmask;
+      if (l < (uint32_t)__popcll(sbits)) {
+        go = target_slot(h, R, B, n, s, l, &tb, &to);
+        if (!go) set_error(h, SMMO_E_CONTENTION, sb);
+        so = (uint32_t)nth_set_bit64(sbits, l);
       }
     }
-  }
-}
-
-// Forwarding handle of source slot so: a u32 at offset 4*so of the dead
-// source block's data segment.
-__global__ void k_place_forwarding(HeapView h, uint32_t c, const uint32_t* R, uint32_t B, uint32_t n,
-                                   unsigned long long* moved) {
-  const ClassLayout& L = h.cls[c];
-  const uint64_t total = (uint64_t)B * 64;
-  unsigned long long cnt = 0;
-  for (uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; tid < total;
-       tid += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t s = (uint32_t)(tid / 64), l = (uint32_t)(tid % 64);
-    const uint32_t sb = R[s];
-    const unsigned long long sbits = h.alloc_bm[sb] & L.capmask;
-    if (l >= (uint32_t)__popcll(sbits)) continue;
-    uint32_t tb, to;
-    if (!target_slot(h, R, B, n, s, l, &tb, &to)) continue;
-    const uint32_t so = (uint32_t)nth_set_bit(sbits, (int)l);
-    reinterpret_cast<uint32_t*>(block_data(h, sb))[so] = (tb << 6) | to;
-    ++cnt;
+    if (go) {
+      const uint8_t* src = block_data(h, sb);
+      uint8_t* dst = block_data(h, tb);
+      for (uint32_t k = 0; k < L.ncols; ++k) {
+        const uint32_t sz = L.col_size[k];
+        const uint8_t* p = src + L.col_off[k] + (size_t)so * sz;
+        uint8_t* q = dst + L.col_off[k] + (size_t)to * sz;
+        switch (sz) {
+          case 1: *q = *p; break;
+          case 2: *(uint16_t*)q = *(const uint16_t*)p; break;
+          case 4: *(uint32_t*)q = *(const uint32_t*)p; break;
+          default: *(uint64_t*)q = *(const uint64_t*)p; break;
+        }
+      }
+    }
+    __syncthreads();  // every copy out of these sources is done
+    if (go) {
+      reinterpret_cast<uint32_t*>(block_data(h, sb))[so] = (tb << 6) | to;
+      ++cnt;
+    }
+    // the next chunk's sources are other blocks: no second barrier needed
   }
   // one atomic per warp: a counter hit by every thread serialises in L2
-  cnt = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)cnt);
-  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(moved, cnt);
+  cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(moved, (unsigned long long)cnt);
 }
 
 // Block states after a pass: each target gets its first m free slots marked
 // (m = objects it received), a target that filled up leaves the active
 // bitmap; each source block is invalidated and becomes free.
-__global__ void k_update_states(HeapView h, uint32_t c, const uint32_t* R, uint32_t B, uint32_t n) {
+__global__ void k_update_states(HeapView h, uint32_t c, const uint32_t* R, uint32_t n,
+                                const unsigned long long* ctl, unsigned long long* moved_from) {
+  if (ctl[CTL_DONE]) return;
+  const uint32_t B = (uint32_t)(ctl[CTL_R] / (n + 1));
   const ClassLayout& L = h.cls[c];
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < B; s += gridDim.x * blockDim.x) {
     const uint32_t sb = R[s];
@@ -205,6 +233,7 @@ __global__ void k_update_states(HeapView h, uint32_t c, const uint32_t* R, uint3
       h.alloc_bm[tb] = bm | add;
       if ((bm | add) == kAll) bm_clear(h, bm_active(h, c), tb);
     }
+    atomicOr(moved_from + (sb >> 6), 1ull << (sb & 63));
     h.alloc_bm[sb] = kAll;  // invalidated
     bm_clear(h, bm_active(h, c), sb);
     bm_clear(h, bm_alloc(h, c), sb);
@@ -212,21 +241,27 @@ __global__ void k_update_states(HeapView h, uint32_t c, const uint32_t* R, uint3
   }
 }
 
-// Pointer rewrite over the enumerated objects of a referring class (Alg.
-// 6.6): a handle whose block is a source of this pass (a candidate with
-// index below R[B]) is replaced by the forwarding handle in its source
-// slot, so the forwarding slot is read only for real sources (Sec. 6.3.5).
-// Like a do-all, one thread per slot of each enumerated block; each warp
-// takes four units (32 slots each) at a time so that their column loads,
-// bitmap tests and forwarding loads are in flight together.
+// Pointer rewrite over the enumerated objects of a referring class, once
+// after all passes (Alg. 6.6 along the chain of passes): a handle whose
+// block was a source is replaced by the forwarding pointer in its source
+// slot, again while the result lies in a block that was a source of a later
+// pass (at most one hop per pass), so the forwarding slot is read only for
+// real sources (Sec. 6.3.5).  Like a do-all, one thread per slot of each
+// enumerated block; each warp takes four units (32 slots each) at a time so
+// that their column loads, bitmap tests and forwarding loads are in flight
+// together.
 struct RewriteArgs {
-  const uint32_t* R;  // sorted candidates of this pass
-  uint32_t B;         // number of sources
-  const unsigned long long* defrag_l0;
+  const unsigned long long* moved_from;  // level-0 bitmap of the passes' sources
+  uint32_t max_hops;                     // passes run
   uint32_t ncols;
   uint32_t col_off[8];  // HANDLE columns of the referring class
   unsigned long long* rewritten;
 };
+
+__device__ __forceinline__ bool was_source(const HeapView& h, const unsigned long long* mf, uint32_t v) {
+  const uint32_t b = v >> 6;
+  return v != kNull && b < h.num_blocks && ((__ldg(mf + (b >> 6)) >> (b & 63)) & 1);
+}
 
 __global__ void __launch_bounds__(256) k_rewrite(HeapView h, uint32_t u_cls, RewriteArgs a) {
   const uint32_t n = __ldcg(&h.st->rcount);
@@ -235,7 +270,6 @@ __global__ void __launch_bounds__(256) k_rewrite(HeapView h, uint32_t u_cls, Rew
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  const uint32_t first_target = a.R[a.B];
   uint32_t cnt = 0;
   for (uint32_t u0 = warp * 4; u0 < units; u0 += nwarps * 4) {
     uint32_t hd[4];
@@ -256,21 +290,25 @@ __global__ void __launch_bounds__(256) k_rewrite(HeapView h, uint32_t u_cls, Rew
     for (uint32_t col = 0; col < 8; ++col) {  // constant indices into the parameter block
       if (col >= a.ncols) break;
       const uint32_t off = a.col_off[col];
-      uint32_t v[4], nv[4];
-      bool fwd[4];
+      uint32_t v[4];
+      bool fwd[4], moved[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) v[k] = live[k] ? *field_ptr<uint32_t>(h, off, hd[k]) : kNull;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const uint32_t b = v[k] >> 6;
-        fwd[k] = v[k] != kNull && b < first_target && ((__ldg(a.defrag_l0 + (b >> 6)) >> (b & 63)) & 1);
+        fwd[k] = was_source(h, a.moved_from, v[k]);
+        moved[k] = fwd[k];
+      }
+      for (uint32_t hop = 0; hop < a.max_hops && (fwd[0] | fwd[1] | fwd[2] | fwd[3]); ++hop) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (fwd[k]) v[k] = reinterpret_cast<const uint32_t*>(block_data(h, v[k] >> 6))[v[k] & 63];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) fwd[k] = fwd[k] && was_source(h, a.moved_from, v[k]);
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k)
-        nv[k] = fwd[k] ? reinterpret_cast<const uint32_t*>(block_data(h, v[k] >> 6))[v[k] & 63] : 0u;
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (fwd[k]) { *field_ptr<uint32_t>(h, off, hd[k]) = nv[k]; ++cnt; }
+        if (moved[k]) { *field_ptr<uint32_t>(h, off, hd[k]) = v[k]; ++cnt; }
     }
   }
   // one atomic per warp: a counter hit by every thread serialises in L2
@@ -278,26 +316,8 @@ __global__ void __launch_bounds__(256) k_rewrite(HeapView h, uint32_t u_cls, Rew
   if (lane == 0 && cnt) atomicAdd(a.rewritten, (unsigned long long)cnt);
 }
 
-// Rebuilds the candidate bitmap defrag[c] that new and delete maintain
-// (fill <= dlimit) after a compaction used its level 0 as scratch: level 0
-// from the allocation bitmaps, every higher level as the OR of its
-// container below.
-__global__ void k_rebuild_defrag_l0(HeapView h, uint32_t c) {
-  const unsigned long long* A = bm_level(h, bm_alloc(h, c), 0);
-  unsigned long long* D = bm_level(h, bm_defrag(h, c), 0);
-  const unsigned long long capmask = h.cls[c].capmask;
-  const uint32_t lim = h.cls[c].dlimit;
-  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < h.level_words[0]; w += gridDim.x * blockDim.x) {
-    unsigned long long a = A[w], d = 0;
-    while (a) {
-      const int b = __ffsll((long long)a) - 1;
-      a &= a - 1;
-      if ((uint32_t)__popcll(h.alloc_bm[w * 64 + b] & capmask) <= lim) d |= 1ull << b;
-    }
-    D[w] = d;
-  }
-}
-
+// Level l of a hierarchical bitmap as the OR of the containers below (the
+// restore of defrag[c] after a compaction used its level 0 as scratch).
 __global__ void k_rebuild_level(HeapView h, int k, uint32_t l) {
   const unsigned long long* lo = bm_level(h, k, l - 1);
   unsigned long long* hi = bm_level(h, k, l);
@@ -331,13 +351,11 @@ extern "C" int smmo_compact(smmo_heap* h, int c, int n, int64_t k1, smmo_compact
   const uint32_t limit = (uint32_t)((uint64_t)L.cap * n / (n + 1));
   uint32_t* R = h->d_scratch;
   unsigned long long* aux = h->view.st->aux;  // [3] r, [4] moved, [5] rewritten
-  unsigned long long* D0 = bm_level_host(h, bm_defrag(h->view, c));  // level 0 only
   const uint32_t nw = h->view.level_words[0];
   const uint32_t nchunks = (nw * 64 + 1023) / 1024;  // CTAs of the scan, 1024 blocks each
-  // the scan's per-CTA counts live in the enumeration scratch, which no
-  // kernel of the scan's own pass uses before the rewrite re-enumerates
+  // the scan's per-CTA counts live in the enumeration scratch, which is
+  // unused during the passes (the rewrite enumerates after the last pass)
   uint32_t* part = reinterpret_cast<uint32_t*>(h->view.R);
-  const uint32_t g = std::max(1u, std::min((nw + 255) / 256, (uint32_t)h->num_sms * 4));
   // referring (class, HANDLE columns) pairs: columns whose ref_class is c or
   // an ancestor of c, or unknown (-1)
   std::vector<std::pair<int, std::vector<uint32_t>>> refs;
@@ -353,42 +371,52 @@ extern "C" int smmo_compact(smmo_heap* h, int c, int n, int64_t k1, smmo_compact
     for (size_t k = 0; k < offs.size(); k += 8)
       refs.push_back({u, std::vector<uint32_t>(offs.begin() + k, offs.begin() + std::min(offs.size(), k + 8))});
   }
-  cudaError_t e = cudaMemsetAsync(aux + 4, 0, 2 * sizeof(unsigned long long), s);
+  cudaError_t e = cudaMemsetAsync(aux, 0, 6 * sizeof(unsigned long long), s);
+  unsigned long long* moved_from = h->d_moved;  // sources of all passes, one bit per block
+  if (e == cudaSuccess) e = cudaMemsetAsync(moved_from, 0, (size_t)nw * 8, s);
   // phase timing: per pass, events at the pass start, after the scan, after
-  // copy and forwarding, after the state update and after the rewrite
+  // copy and forwarding and after the state update
   std::vector<cudaEvent_t> ev;
   auto mark = [&]() {
     cudaEvent_t x = nullptr;
     if (cudaEventCreate(&x) == cudaSuccess) { cudaEventRecord(x, s); ev.push_back(x); }
     else ev.push_back(nullptr);
   };
-  std::vector<int> full_pass;  // 1 if the pass recorded all five events
+  // passes are queued in groups of kGroup; the host looks at the control
+  // block once per group (passes after the last real one return at once)
+  const int kGroup = 4;
+  const unsigned grel = (unsigned)h->num_sms * 8, gupd = (unsigned)h->num_sms * 4;
   int status = SMMO_OK;
-  for (int pass = 0; pass < 1000 && e == cudaSuccess; ++pass) {
-    mark();
-    k_cand_scan1<<<nchunks, 1024, 0, s>>>(h->view, c, limit, part);
-    k_cand_scan2<<<1, 1024, 0, s>>>(part, nchunks, aux + 3);
-    k_cand_scan3<<<nchunks, 1024, 0, s>>>(h->view, c, part, R);
-    mark();
-    unsigned long long r = 0;
-    e = cudaMemcpyAsync(&r, aux + 3, sizeof(r), cudaMemcpyDeviceToHost, s);
+  unsigned long long ctl[4] = {0, 0, 0, 0};
+  for (int queued = 0; queued < 1000 && e == cudaSuccess;) {
+    for (int k = 0; k < kGroup; ++k, ++queued) {
+      mark();
+      k_cand_scan1<<<nchunks, 1024, 0, s>>>(h->view, c, limit, part, aux);
+      k_cand_scan2<<<1, 1024, 0, s>>>(part, nchunks, (uint32_t)n, (unsigned long long)k1, aux);
+      k_cand_scan3<<<nchunks, 1024, 0, s>>>(h->view, c, part, R, aux);
+      mark();
+      k_relocate<<<grel, 256, 0, s>>>(h->view, c, R, (uint32_t)n, aux, aux + 4);
+      mark();
+      k_update_states<<<gupd, 256, 0, s>>>(h->view, c, R, (uint32_t)n, aux, moved_from);
+      mark();
+    }
+    e = cudaMemcpyAsync(ctl, aux, sizeof(ctl), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) break;
-    st.candidates_left = (int64_t)r;
-    const uint64_t B = r / (uint64_t)(n + 1);
-    if ((int64_t)r <= k1 || B == 0) { full_pass.push_back(0); break; }
-    const unsigned gm = (unsigned)std::min<uint64_t>((B * 64 + 255) / 256, 65535);
-    k_move_objects<<<gm, 256, 0, s>>>(h->view, c, R, (uint32_t)B, (uint32_t)n);
-    k_place_forwarding<<<gm, 256, 0, s>>>(h->view, c, R, (uint32_t)B, (uint32_t)n, aux + 4);
-    mark();
-    k_update_states<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>((B + 255) / 256, 4096)), 256, 0, s>>>(
-        h->view, c, R, (uint32_t)B, (uint32_t)n);
-    mark();
+    if (e != cudaSuccess || ctl[0]) break;
+  }
+  st.passes = (int32_t)ctl[1];
+  st.blocks_freed = (int64_t)ctl[2];
+  st.candidates_left = (int64_t)ctl[3];
+  // one rewrite along the chain of passes
+  cudaEvent_t rw0 = nullptr, rw1 = nullptr;
+  if (e == cudaSuccess && st.passes > 0) {
+    cudaEventCreate(&rw0);
+    cudaEventCreate(&rw1);
+    cudaEventRecord(rw0, s);
     for (auto& rc : refs) {
       RewriteArgs ra{};
-      ra.R = R;
-      ra.B = (uint32_t)B;
-      ra.defrag_l0 = D0;
+      ra.moved_from = moved_from;
+      ra.max_hops = (uint32_t)st.passes;
       ra.ncols = (uint32_t)rc.second.size();
       for (uint32_t k = 0; k < ra.ncols; ++k) ra.col_off[k] = rc.second[k];
       ra.rewritten = aux + 5;
@@ -396,17 +424,13 @@ extern "C" int smmo_compact(smmo_heap* h, int c, int n, int64_t k1, smmo_compact
       if (status) break;
       k_rewrite<<<h->num_sms * 4, 256, 0, s>>>(h->view, (uint32_t)rc.first, ra);
     }
-    mark();
-    full_pass.push_back(1);
-    if (status) break;
+    cudaEventRecord(rw1, s);
     e = cudaGetLastError();
-    st.passes += 1;
-    st.blocks_freed += (int64_t)B;
   }
   // the pass used defrag[c] level 0 as scratch: restore the candidate state
   // that new and delete maintain
   if (e == cudaSuccess && !status) {
-    k_rebuild_defrag_l0<<<g, 256, 0, s>>>(h->view, c);
+    k_cand_scan1<<<nchunks, 1024, 0, s>>>(h->view, c, L.dlimit, nullptr, nullptr);
     for (uint32_t l = 1; l < h->view.nlevels; ++l)
       k_rebuild_level<<<std::max(1u, std::min((h->view.level_words[l] + 255) / 256, 1024u)), 256, 0, s>>>(
           h->view, bm_defrag(h->view, c), l);
@@ -422,18 +446,17 @@ extern "C" int smmo_compact(smmo_heap* h, int c, int n, int64_t k1, smmo_compact
     if (j >= ev.size() || !ev[i] || !ev[j]) return 0.0;
     return cudaEventElapsedTime(&ms, ev[i], ev[j]) == cudaSuccess ? (double)ms : 0.0;
   };
-  size_t k = 0;
-  for (int f : full_pass) {
+  for (size_t k = 0; k + 3 < ev.size(); k += 4) {
     st.scan_ms += el(k, k + 1);
-    if (f) {
-      st.copy_ms += el(k + 1, k + 2);
-      st.state_ms += el(k + 2, k + 3);
-      st.rewrite_ms += el(k + 3, k + 4);
-      k += 5;
-    } else {
-      k += 2;
-    }
+    st.copy_ms += el(k + 1, k + 2);
+    st.state_ms += el(k + 2, k + 3);
   }
+  if (rw0 && rw1) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, rw0, rw1) == cudaSuccess) st.rewrite_ms = ms;
+  }
+  if (rw0) cudaEventDestroy(rw0);
+  if (rw1) cudaEventDestroy(rw1);
   for (cudaEvent_t x : ev)
     if (x) cudaEventDestroy(x);
   if (out) *out = st;

@@ -402,7 +402,8 @@ int freeze(smmo_heap* h, cudaStream_t s) {
     uint32_t lw[SMMO_MAX_LEVELS], lo[SMMO_MAX_LEVELS], nl;
     const uint64_t bw = bm_geom(M, lw, lo, &nl);
     return fixed + align_up(M * 8, 256) + align_up(M * 4, 256) + align_up(rscratch_bytes(M), 256) +
-           align_up(M * 4 + 1024, 256) + align_up(bw * 8 * nbm, 256) + M * block_bytes;
+           align_up(M * 4 + 1024, 256) + align_up((M + 63) / 64 * 8, 256) + align_up(bw * 8 * nbm, 256) +
+           M * block_bytes;
   };
   uint64_t M = h->buf_bytes / (block_bytes + 40);
   M = std::min<uint64_t>(M, (1ull << 26) - 1);
@@ -421,6 +422,7 @@ int freeze(smmo_heap* h, cudaStream_t s) {
   v.block_type = (uint32_t*)take(M * 4);
   v.R = (REntry*)take(rscratch_bytes(M));
   h->d_scratch = (uint32_t*)take(M * 4 + 1024);
+  h->d_moved = (unsigned long long*)take((M + 63) / 64 * 8);
   v.bitmaps = (unsigned long long*)take(bw * 8 * nbm);
   v.data = p;
   v.block_bytes = (uint32_t)block_bytes;

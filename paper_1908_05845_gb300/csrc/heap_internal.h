@@ -32,6 +32,7 @@ struct smmo_heap {
   smmo::HeapView view{};
   smmo::ClassLayout* d_layouts = nullptr;  // inside buf
   uint32_t* d_scratch = nullptr;           // inside buf: num_blocks + 64 words
+  unsigned long long* d_moved = nullptr;   // inside buf: one bit per block (compaction)
 };
 
 namespace smmo {

@@ -145,3 +145,35 @@ def test_synthetic_two_class_benchmark_small():
     assert st1["blocks"][w.A] < st0["blocks"][w.A] * 0.6
     assert st1["fragmentation"][w.A] < 0.25 + 1.0 / 64
     w.close()
+
+
+def test_self_referencing_ring_survives_multi_pass_compaction():
+    """A class referring to itself (a ring through the survivors) keeps
+    every link through several passes, so objects that move twice are
+    reached by following forwarding pointers across passes."""
+    h = smmo.Heap(64 << 20)
+    N = h.register("Node", [("next", smmo.HANDLE), ("v", smmo.I32), ("kill", smmo.I32)])
+    n = 64 * 300
+    rng = np.random.default_rng(5)
+    kill = (rng.random(n) < 0.7).astype(np.int32)
+    v = np.arange(n)
+    nul = np.full(n, -1, np.int32)
+    hd, _ = h.bulk_new(N, n, [cuda_i32(nul), cuda_i32(v), cuda_i32(kill)], want_handles=True)
+    alive = np.flatnonzero(kill == 0)
+    nxt = np.full(n, -1, np.int64)
+    nxt[alive] = np.roll(alive, -1)
+    hd_np = hd.cpu().numpy()
+    table = np.where(nxt >= 0, hd_np[np.maximum(nxt, 0)], -1).astype(np.int32)
+    tt = cuda_i32(table)
+    h.parallel_do(N, "test.set_ref_from", smmo.SetRefFromArgs(0, 1, tt.data_ptr()))
+    h.parallel_do(N, "test.free_self_if", smmo.FreeSelfIfArgs(2, 2, 1))
+    h.sync()
+    st = h.compact(N, n=3, k1=0)
+    assert st["passes"] >= 3 and st["objects_moved"] > len(alive) // 2
+    assert h.check() == 0
+    hh = h.enumerate_live(N)
+    nv, vv = h.gather(N, hh, ["next", "v"])
+    (tv,) = h.gather(N, nv, ["v"])
+    got = dict(zip(vv.cpu().numpy().tolist(), tv.cpu().numpy().tolist()))
+    assert sorted(got) == alive.tolist()
+    assert all(got[a] == b for a, b in zip(alive.tolist(), np.roll(alive, -1).tolist()))
