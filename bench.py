@@ -49,7 +49,7 @@ BYTES_PER_OBJECT = {
 }
 PHASES = ["life_cand_prepare", "life_alive_prepare", "life_cand_update", "life_alive_update",
           "fish_prepare", "fish_update", "shark_prepare", "shark_update"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "wator_2048_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "wator_2048_fish_update_traffic.txt")  # JSON
 KERNEL_SOURCES = ["paper_1908_05845_gb300/csrc/world.cu", "paper_1908_05845_gb300/csrc/smmo_core.cuh",
                   "paper_1908_05845_gb300/csrc/grid_common.cuh"]
 
@@ -564,11 +564,27 @@ def run_nbody(args):
         t_b = a.elapsed_time(b) / 1e3
         w.close()
     pairs = float(N) * N * args.steps
+    # ALU roofline of the force pass (no-merge forward with checkpoints,
+    # which is the force kernel plus an O(N) drift): 19 FP32 operations per
+    # pair (3 sub, 7 mul, 7 add, 1 sqrt, 1 div, each counted once; the
+    # fixed evaluation order forbids contraction into FMA) against one FP32
+    # operation per lane per clock: SMs x 128 lanes x max SM clock
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    mhz = (load_peaks() or {}).get("sm_max_mhz", 2070.0)
+    peak_tops = props.multi_processor_count * 128 * mhz * 1e6 / 1e12
+    fwd_pairs_per_s = float(N) * N * 50 / t_f
+    ach_tops = fwd_pairs_per_s * 19 / 1e12
     print(json.dumps({"metric": "pair-interactions/s", "value": pairs / t, "unit": "pairs/s",
                       "ms_per_step": 1e3 * t / args.steps, "steps": args.steps, "merges": merges,
                       "live_after": live, "adjoint_backward_over_forward": t_b / t_f,
                       "forward_ckpt_ms_per_step": 1e3 * t_f / 50, "backward_ms_per_step": 1e3 * t_b / 50,
-                      "config": {"workload": "nbody_65536_merge", "note": "force + merge search are both O(N^2)"}}),
+                      "dtype": "f32",
+                      "roofline": {"bound": "alu", "achieved": ach_tops, "peak": peak_tops, "unit": "TFLOP/s",
+                                   "frac": ach_tops / peak_tops, "traffic": None, "kernel": "k_force",
+                                   "peak_source": "derived: %d SMs x 128 FP32 lanes x %.0f MHz"
+                                                  % (props.multi_processor_count, mhz)},
+                      "config": {"workload": "nbody_65536_merge",
+                                 "note": "force O(N^2), merge search on a uniform grid"}}),
           flush=True)
     return 0
 
