@@ -451,6 +451,18 @@ int smmo_nbody_forward_ckpt(smmo_nbody* w, int nsteps, int ckpt, double* loss,
 int smmo_nbody_backward(smmo_nbody* w, float* grad_v0, void* stream);
 int smmo_nbody_destroy(smmo_nbody* w);
 
+/* Self-test of the branch-free, correctly rounded FP32 square root and
+ * reciprocal that the force kernel uses when every coordinate is within
+ * 2^18 and eps^2 is in [2^-40, 2^38] (otherwise it uses the IEEE-rounded
+ * intrinsics): compares both with __fsqrt_rn / __frcp_rn on every positive
+ * float whose bit pattern lies in [lo_bits, hi_bits] (hi_bits < 0x7F800000).
+ * out4 (host): mismatches of the square root, of the reciprocal, and the
+ * smallest mismatching bit pattern of each (0xFFFFFFFF if none).  The force
+ * kernel relies on no mismatch of the square root in [2^-40, 2^40] and of
+ * the reciprocal in [2^-60, 2^60].  Allocates 24 bytes with cudaMallocAsync
+ * on `stream`; synchronises `stream`. */
+int smmo_selftest_fp32_rn(uint32_t lo_bits, uint32_t hi_bits, uint64_t* out4, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,9 +32,11 @@
 //   lambda_x += g;  lambda_v = w + dt/2 lambda_x.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
+#include "fp32_rn.cuh"
 #include "heap_internal.h"
 #include "smmo.h"
 #include "smmo_core.cuh"
@@ -99,13 +101,47 @@ struct Stage {
 // CTA loads the shared tiles, only threads on live slots accumulate.
 #define NB_TILE 256
 
+// Coordinates bound for the branch-free square root and reciprocal: with
+// |x| <= 2^18 for both bodies and eps^2 in [2^-40, 2^38], s2 lies in
+// [2^-40, 2^40] and s2 sqrt(s2) in [2^-60, 2^60], the ranges on which those
+// functions equal the IEEE-rounded ones.
+constexpr unsigned kCoordMaxBits = 0x48800000u;  // 2^18
+
+// Sum of the pair terms of one tile into (ax, ay, az), j in increasing order.
+template <bool FAST>
+__device__ __forceinline__ void force_tile(const float4* tile, uint32_t cnt, float xi, float yi, float zi,
+                                           float eps2, float& ax, float& ay, float& az) {
+  // unrolled so that the pair terms of consecutive j (independent) overlap;
+  // the accumulation stays in increasing j
+#pragma unroll 8
+  for (uint32_t k = 0; k < cnt; ++k) {
+    const float4 p = tile[k];
+    const float dx = fs(p.x, xi), dy = fs(p.y, yi), dz = fs(p.z, zi);
+    float s2 = fm(dx, dx);
+    s2 = fa(s2, fm(dy, dy));
+    s2 = fa(s2, fm(dz, dz));
+    s2 = fa(s2, eps2);
+    const float inv = FAST ? rcp_rn_fast(fm(s2, sqrt_rn_fast(s2))) : __fdiv_rn(1.0f, fm(s2, __fsqrt_rn(s2)));
+    const float f = fm(p.w, inv);
+    ax = fa(ax, fm(f, dx));
+    ay = fa(ay, fm(f, dy));
+    az = fa(az, fm(f, dz));
+  }
+}
+
+__device__ __forceinline__ unsigned abs_max_bits(float x, float y, float z) {
+  return max(__float_as_uint(fabsf(x)), max(__float_as_uint(fabsf(y)), __float_as_uint(fabsf(z))));
+}
+
 __global__ void __launch_bounds__(256) k_force(HeapView hv, uint32_t c, NBodyArgs a) {
   __shared__ float4 tile[NB_TILE];
+  __shared__ unsigned tile_max[NB_TILE / 32];
   const uint32_t n = __ldcg(&hv.st->rcount);
   const uint32_t cap = hv.cls[c].cap;
   const uint32_t halves = cap > 32 ? 2u : 1u;
   const uint32_t units = n * halves, groups = (units + 7) / 8;
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool eps_ok = a.eps2 >= 0x1p-40f && a.eps2 <= 0x1p38f;
   for (uint32_t g = blockIdx.x; g < groups; g += gridDim.x) {
     const uint32_t u = g * 8 + warp;
     bool live = false;
@@ -122,28 +158,22 @@ __global__ void __launch_bounds__(256) k_force(HeapView hv, uint32_t c, NBodyArg
       yi = F<float>(hv, self, a.off[CY]);
       zi = F<float>(hv, self, a.off[CZ]);
     }
+    const bool own_ok = eps_ok && abs_max_bits(xi, yi, zi) <= kCoordMaxBits;
     for (uint32_t base = 0; base < a.n0; base += NB_TILE) {
       __syncthreads();
-      if (base + threadIdx.x < a.n0) tile[threadIdx.x] = a.S[base + threadIdx.x];
+      float4 q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (base + threadIdx.x < a.n0) q = a.S[base + threadIdx.x];
+      tile[threadIdx.x] = q;
+      const unsigned wm = __reduce_max_sync(0xFFFFFFFFu, abs_max_bits(q.x, q.y, q.z));
+      if (lane == 0) tile_max[warp] = wm;
       __syncthreads();
+      unsigned tm = 0;
+#pragma unroll
+      for (int w = 0; w < NB_TILE / 32; ++w) tm = max(tm, tile_max[w]);
       const uint32_t cnt = a.n0 - base < NB_TILE ? a.n0 - base : NB_TILE;
       if (live) {
-        // unrolled so that the pair terms of consecutive j (independent)
-        // overlap; the accumulation stays in increasing j
-#pragma unroll 8
-        for (uint32_t k = 0; k < cnt; ++k) {
-          const float4 p = tile[k];
-          const float dx = fs(p.x, xi), dy = fs(p.y, yi), dz = fs(p.z, zi);
-          float s2 = fm(dx, dx);
-          s2 = fa(s2, fm(dy, dy));
-          s2 = fa(s2, fm(dz, dz));
-          s2 = fa(s2, a.eps2);
-          const float inv = __fdiv_rn(1.0f, fm(s2, __fsqrt_rn(s2)));
-          const float f = fm(p.w, inv);
-          ax = fa(ax, fm(f, dx));
-          ay = fa(ay, fm(f, dy));
-          az = fa(az, fm(f, dz));
-        }
+        if (own_ok && tm <= kCoordMaxBits) force_tile<true>(tile, cnt, xi, yi, zi, a.eps2, ax, ay, az);
+        else force_tile<false>(tile, cnt, xi, yi, zi, a.eps2, ax, ay, az);
       }
     }
     if (live) {
@@ -368,21 +398,27 @@ struct AdjW {
 
 // Pair kernel of the reverse step (tiled like the force), then
 // lambda_x += g and lambda_v = w + h lambda_x.
-__global__ void __launch_bounds__(256) k_adjoint_pair(HeapView hv, uint32_t c, NBodyArgs a) {
+// Reverse-step pair sum g_k.  The sum is not bound to an evaluation order
+// (its tolerance is 1e-3 against the FP64 sweep), so four lanes share one
+// body, each summing every fourth id of every tile, and the four partial sums are
+// combined by shuffles: 65,536 bodies then occupy four times the warps one
+// lane per body would.  A CTA (8 warps) covers 64 slots (two units).
+__global__ void __launch_bounds__(256, 7) k_adjoint_pair(HeapView hv, uint32_t c, NBodyArgs a) {
   __shared__ float4 tx[NB_TILE];
   __shared__ float4 tm[NB_TILE];
   const uint32_t n = __ldcg(&hv.st->rcount);
   const uint32_t cap = hv.cls[c].cap;
   const uint32_t halves = cap > 32 ? 2u : 1u;
-  const uint32_t units = n * halves, groups = (units + 7) / 8;
+  const uint32_t units = n * halves, pairs = (units + 1) / 2;
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (uint32_t g = blockIdx.x; g < groups; g += gridDim.x) {
-    const uint32_t u = g * 8 + warp;
+  const uint32_t part = lane & 3, q = warp * 8 + (lane >> 2);  // q: slot of the CTA's 64
+  for (uint32_t g = blockIdx.x; g < pairs; g += gridDim.x) {
+    const uint32_t u = g * 2 + (q >> 5);
     bool live = false;
     uint32_t self = 0;
     if (u < units) {
       const REntry e = hv.R[halves == 2 ? (u >> 1) : u];
-      const uint32_t slot = (halves == 2 ? (u & 1) * 32 : 0) + lane;
+      const uint32_t slot = (halves == 2 ? (u & 1) * 32 : 0) + (q & 31);
       live = (e.bits >> slot) & 1;
       self = (e.block << 6) | slot;
     }
@@ -402,15 +438,18 @@ __global__ void __launch_bounds__(256) k_adjoint_pair(HeapView hv, uint32_t c, N
       __syncthreads();
       const uint32_t cnt = a.n0 - base < NB_TILE ? a.n0 - base : NB_TILE;
       if (live) {
-        for (uint32_t k = 0; k < cnt; ++k) {
-          const float4 p = tx[k], q = tm[k];
+        // lane part takes every fourth j of the tile: the four lanes of a
+        // body read neighbouring float4s (distinct banks, no conflict)
+#pragma unroll 4
+        for (uint32_t k = part; k < cnt; k += 4) {
+          const float4 p = tx[k], w = tm[k];
           const float rx = p.x - xk.x, ry = p.y - xk.y, rz = p.z - xk.z;
           const float s2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, a.eps2)));
           const float is = rsqrtf(s2);
           const float is3 = is * is * is;
-          const float ux = xk.w * q.x - p.w * mk.x;
-          const float uy = xk.w * q.y - p.w * mk.y;
-          const float uz = xk.w * q.z - p.w * mk.z;
+          const float ux = xk.w * w.x - p.w * mk.x;
+          const float uy = xk.w * w.y - p.w * mk.y;
+          const float uz = xk.w * w.z - p.w * mk.z;
           const float ru = fmaf(rx, ux, fmaf(ry, uy, rz * uz));
           const float c3 = 3.0f * ru * is3 * is * is;
           gx += ux * is3 - c3 * rx;
@@ -419,7 +458,14 @@ __global__ void __launch_bounds__(256) k_adjoint_pair(HeapView hv, uint32_t c, N
         }
       }
     }
-    if (live) {
+    // combine the four lanes of a body (every lane takes part)
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+      gx += __shfl_xor_sync(0xFFFFFFFFu, gx, o);
+      gy += __shfl_xor_sync(0xFFFFFFFFu, gy, o);
+      gz += __shfl_xor_sync(0xFFFFFFFFu, gz, o);
+    }
+    if (live && part == 0) {
       const float gg[3] = {a.G * gx, a.G * gy, a.G * gz};
       for (int d = 0; d < 3; ++d) {
         float& lx = F<float>(hv, self, a.off[CLX + d]);
@@ -674,7 +720,9 @@ int smmo_nbody_backward(smmo_nbody* w, float* grad_v0, void* stream) {
       b.X1 = w->d_x1 + (size_t)(k - s0) * n0;
       st = pdo(w, &launch_do_all<AdjW>, b, s);
       if (st) return st;
-      k_adjoint_pair<<<tiled_grid(w->heap), 256, 0, s>>>(w->heap->view, w->cls, b);
+      // one CTA per 64 ids: 1,024 CTAs at N = 65,536, all resident at once
+      // on 152 SMs (at least 7 CTAs of 256 threads per SM)
+      k_adjoint_pair<<<std::max<uint32_t>(1, (w->n0 + 63) / 64), 256, 0, s>>>(w->heap->view, w->cls, b);
       st = cuda_status(cudaGetLastError());
       if (st) return st;
     }
@@ -693,6 +741,56 @@ int smmo_nbody_destroy(smmo_nbody* w) {
   if (w->d_ckpt) cudaFree(w->d_ckpt);
   if (w->d_x1) cudaFree(w->d_x1);
   delete w;
+  return SMMO_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// Self-test of the branch-free square root and reciprocal against the
+// IEEE-rounded intrinsics on every float with bit pattern in [lo, hi].
+__global__ void k_selftest_fp32_rn(uint32_t lo, uint32_t hi, unsigned long long* cnt, unsigned* first) {
+  for (uint64_t u = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= hi;
+       u += (uint64_t)gridDim.x * blockDim.x) {
+    const float x = __uint_as_float((uint32_t)u);
+    const bool bs = __float_as_uint(sqrt_rn_fast(x)) != __float_as_uint(__fsqrt_rn(x));
+    const bool br = __float_as_uint(rcp_rn_fast(x)) != __float_as_uint(__frcp_rn(x));
+    if (bs) { atomicAdd(cnt + 0, 1ull); atomicMin(first + 0, (unsigned)u); }
+    if (br) { atomicAdd(cnt + 1, 1ull); atomicMin(first + 1, (unsigned)u); }
+  }
+}
+}  // namespace
+
+extern "C" {
+
+int smmo_selftest_fp32_rn(uint32_t lo_bits, uint32_t hi_bits, uint64_t* out4, void* stream) {
+  if (!out4 || lo_bits > hi_bits || hi_bits >= 0x7F800000u) return SMMO_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* cnt = nullptr;
+  unsigned* first = nullptr;
+  cudaError_t e = cudaMallocAsync(&cnt, 2 * sizeof(unsigned long long) + 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return cuda_status(e);
+  first = reinterpret_cast<unsigned*>(cnt + 2);
+  e = cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(first, 0xFF, 2 * sizeof(unsigned), s);
+  int dev = 0, sms = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) {
+    k_selftest_fp32_rn<<<sms * 16, 256, 0, s>>>(lo_bits, hi_bits, cnt, first);
+    e = cudaGetLastError();
+  }
+  unsigned long long hc[2] = {0, 0};
+  unsigned hf[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hf, first, sizeof(hf), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFreeAsync(cnt, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  out4[0] = hc[0];
+  out4[1] = hc[1];
+  out4[2] = hf[0];
+  out4[3] = hf[1];
   return SMMO_OK;
 }
 

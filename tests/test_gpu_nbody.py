@@ -122,3 +122,23 @@ def test_autograd_function(orc):
         fd[n] = (4 * central(hh / 2) - central(hh)) / 3
     gs = g.reshape(-1)[comps]
     assert np.linalg.norm(gs - fd) / np.linalg.norm(fd) < 1e-3
+
+
+def test_branch_free_sqrt_and_reciprocal_are_correctly_rounded_on_their_ranges():
+    """The force kernel's branch-free square root and reciprocal (used when
+    every coordinate is within 2^18 and eps^2 in [2^-40, 2^38]) equal the
+    IEEE-rounded intrinsics on every float of the ranges it relies on:
+    square root on [2^-40, 2^40], reciprocal on [2^-60, 2^60]."""
+    import ctypes
+    from paper_1908_05845_gb300 import smmo
+    lib = smmo.lib()
+    out = (ctypes.c_uint64 * 4)()
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.smmo_selftest_fp32_rn(ctypes.c_uint32(0x2B800000), ctypes.c_uint32(0x53800000), out, s) == 0
+    assert out[0] == 0, "sqrt mismatches %d, first %08x" % (out[0], out[2])
+    assert lib.smmo_selftest_fp32_rn(ctypes.c_uint32(0x21800000), ctypes.c_uint32(0x5D800000), out, s) == 0
+    assert out[1] == 0, "reciprocal mismatches %d, first %08x" % (out[1], out[3])
+    # outside: the square root fails next to the smallest normals, the
+    # reciprocal where its result is subnormal, so the ranges are needed
+    assert lib.smmo_selftest_fp32_rn(ctypes.c_uint32(0x00800000), ctypes.c_uint32(0x7F7FFFFF), out, s) == 0
+    assert out[0] > 0 and out[1] > 0
