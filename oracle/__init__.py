@@ -33,7 +33,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["philox.c", "gol.c", "wator.c", "nasch.c", "nbody.c"]
+_SOURCES = ["philox.c", "gol.c", "generation.c", "wator.c", "nasch.c", "nbody.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -99,6 +99,27 @@ def gol_run(W: int, H: int, kind, state, T: int):
     if rc != 0:
         raise ValueError("orc_gol_run: bad arguments")
     return kind, state, cnt[:T]
+
+
+# ----------------------------------------------------- generational automaton
+BURST = (0b111101101, 0b101011000, 255)  # survive {0,2,3,5,6,7,8}, born {3,4,6,8}, block 255
+LIFE_RULE = (0b1100, 0b1000, 0)
+
+
+def gen_run(W: int, H: int, kind, state, blocked, T: int, rule=BURST):
+    """Returns (kind, state, blocked, counters[T, 8]) after T generations of
+    the generational automaton with rule (survive mask, born mask, block)."""
+    lib = _load()
+    kind = np.ascontiguousarray(kind, dtype=np.uint8).copy()
+    state = np.ascontiguousarray(state, dtype=np.uint8).copy()
+    blocked = np.ascontiguousarray(blocked, dtype=np.uint16).copy()
+    cnt = np.zeros((max(T, 1), 8), dtype=np.int64)
+    s, b, blk = rule
+    rc = lib.orc_gen_run(int(W), int(H), ctypes.c_uint32(s), ctypes.c_uint32(b), int(blk), _p(kind),
+                         _p(state), _p(blocked), int(T), _p(cnt))
+    if rc != 0:
+        raise ValueError("orc_gen_run: bad arguments")
+    return kind, state, blocked, cnt[:T]
 
 
 # ------------------------------------------------------------------- Wa-Tor

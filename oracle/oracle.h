@@ -49,6 +49,19 @@ enum { ORC_EMPTY = 0, ORC_ALIVE = 1, ORC_CANDIDATE = 2 };
 int orc_gol_run(int W, int H, uint8_t* kind, uint8_t* state, int T,
                 int64_t* counters);
 
+/* ------------------------------------------- generational automaton */
+/* Runs T generations of the "generation" extension of Life (Sec. 7.8):
+ * survive/born are masks over the number of alive neighbours (bit n set =
+ * survive / born with n), a dead Alive blocks its cell for `block`
+ * generations before a Candidate replaces it (block 0 = Life semantics).
+ * kind/state/blocked: per-cell in/out arrays (state: is_new of an Alive;
+ * blocked: generations an Alive has blocked, 0 = alive).  counters (may be
+ * NULL): 8 x int64 per generation: [alive, blocking, candidates, births,
+ * deaths, expired, candidates_created, candidates_deleted]. */
+int orc_gen_run(int W, int H, uint32_t survive, uint32_t born, int block,
+                uint8_t* kind, uint8_t* state, uint16_t* blocked, int T,
+                int64_t* counters);
+
 /* ---------------------------------------------------------------- Wa-Tor */
 enum { ORC_FISH = 1, ORC_SHARK = 2 };
 typedef struct {
