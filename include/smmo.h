@@ -299,10 +299,13 @@ typedef struct {
  * n_inst entries (W, H >= 3).  Per-cell initial state: device arrays over
  * the concatenation of all instances' cells in instance order, row-major
  * (cell = y * W + x): init_kind (Life: 0 empty, 1 Alive, 2 Candidate;
- * Wa-Tor: 0 empty, 1 Fish, 2 Shark), init_age / init_energy (Wa-Tor,
- * nullable = 0), init_state (Life is_new flag, nullable = 0).  params may be
- * NULL.  Synchronises `stream`.  The world allocates two small instance
- * tables with cudaMalloc, freed by smmo_world_destroy. */
+ * Wa-Tor: 0 empty, 1 Fish, 2 Shark), init_age (Wa-Tor: age; Life: the
+ * generations an Alive has blocked its cell, 0 = alive; nullable = 0),
+ * init_energy (Wa-Tor, nullable = 0), init_state (Life is_new flag,
+ * nullable = 0).  params may be NULL.  Life-kind instances start with the
+ * Life rule (see smmo_world_set_life_rule).  Synchronises `stream`.  The
+ * world allocates two small instance tables with cudaMalloc, freed by
+ * smmo_world_destroy. */
 int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind,
                       const uint32_t* W, const uint32_t* H, uint64_t seed,
                       const smmo_wator_params* params, const int8_t* init_kind,
@@ -312,8 +315,20 @@ int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind,
 /* Advances every instance by nsteps steps.  Asynchronous (host loop of
  * parallel_do launches; capturable in a CUDA graph). */
 int smmo_world_step(smmo_world* w, int nsteps, void* stream);
+/* Rule of the Life-kind instances (Sec. 7.8, "gol" and its "generation"
+ * extension): with n = alive Alive objects among the 8 neighbours (a dead
+ * Alive that blocks its cell does not count), an Alive survives iff bit n
+ * of `survive` is set, a Candidate becomes a new Alive iff bit n of `born`
+ * is set; a dead Alive keeps its cell blocked for `block` generations and
+ * is then replaced by a Candidate (block 0: replaced at once).  Life:
+ * survive 0x00C, born 0x008, block 0 (the default); Burst: survive 0x1ED,
+ * born 0x158, block 255.  survive, born < 2^9 (born bit 0 is invalid: a
+ * Candidate without alive neighbour is deleted), block <= 65535.  Takes
+ * effect at the next step; drops a captured graph. */
+int smmo_world_set_life_rule(smmo_world* w, uint32_t survive, uint32_t born, uint32_t block);
 /* Writes the live objects into per-cell device arrays (same indexing as
- * the initial state; kind, age, energy, state as above; empty cells 0) and
+ * the initial state; kind, age, energy, state as above, age of an Alive =
+ * its blocked count; empty cells 0) and
  * counts consistency errors (two agents on a cell, a cell not pointing back
  * at its agent) into *errors (host, nullable).  Synchronises `stream`. */
 int smmo_world_export(smmo_world* w, int8_t* kind, int16_t* age, int16_t* energy,

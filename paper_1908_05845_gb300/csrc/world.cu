@@ -1,13 +1,23 @@
 // world.cu -- the cellular SMMO workloads of the thesis' Ch. 7 on one heap:
-// object-based Game of Life (Sec. 7.8) and Wa-Tor (Sec. 7.6), for one or
-// many independent instances ("batched heap": all instances' objects share
-// the heap and every step runs one parallel_do per class over all of them).
+// object-based Game of Life and its generational extension (Sec. 7.8,
+// "gol" and "generation") and Wa-Tor (Sec. 7.6), for one or many
+// independent instances ("batched heap": all instances' objects share the
+// heap and every step runs one parallel_do per class over all of them).
 //
 // Classes: Cell {occ: handle of the agent on the cell, req: u64 request
 // word}; WAgent (abstract) {cell, target} with Fish {age} and Shark {age,
-// energy}; LAgent (abstract) {cell, action} with Alive {is_new} and
-// Candidate {}.  Cells are created once by bulk_new in global cell order and
-// addressed densely; agents hold their global cell index.
+// energy}; LAgent (abstract) {cell, action} with Alive {is_new, blocked}
+// and Candidate {}.  Cells are created once by bulk_new in global cell order
+// and addressed densely; agents hold their global cell index.
+//
+// The Life-kind instances follow one rule: an alive object survives iff bit
+// n of `survive` is set (n = alive, i.e. not blocking, Alive objects among
+// the 8 neighbours), a Candidate becomes alive iff bit n of `born` is set,
+// and a dead Alive blocks its cell for `block` generations (field blocked
+// counts them) before a Candidate replaces it.  Life is survive {2,3},
+// born {3}, block 0 (a dead Alive is replaced at once); the generation
+// application's Burst rule is survive {0,2,3,5,6,7,8}, born {3,4,6,8},
+// block 255.
 //
 // Conflict resolution and randomness are keyed by (seed, step, local cell,
 // tag, instance) and by lowest cell index, so a run is deterministic
@@ -36,8 +46,9 @@ struct WorldArgs {
   uint32_t fish, shark, alive, cand;
   uint32_t f_cell, f_target, f_age;
   uint32_t s_cell, s_target, s_age, s_energy;
-  uint32_t a_cell, a_action, a_isnew;
+  uint32_t a_cell, a_action, a_isnew, a_blocked;
   uint32_t c_cell, c_action;
+  uint32_t survive, born, block;  // rule of the Life-kind instances
   uint64_t seed;
   const uint32_t* tp;  // device step counter (1-based during a step)
   uint32_t phase;      // 0 fish, 1 shark
@@ -206,7 +217,7 @@ struct SharkUpdate {
 };
 
 // ================================================================ Life
-enum : uint8_t { ACT_KEEP = 0, ACT_BORN = 1, ACT_DELETE = 2, ACT_DIE = 3 };
+enum : uint8_t { ACT_KEEP = 0, ACT_BORN = 1, ACT_DELETE = 2, ACT_DIE = 3, ACT_AGE = 4, ACT_EXPIRE = 5 };
 
 __device__ __forceinline__ uint32_t torus8(uint32_t x, uint32_t y, int dx, int dy, uint32_t W,
                                            uint32_t H) {
@@ -224,7 +235,8 @@ __device__ __forceinline__ int alive_neighbours(const HeapView& h, const WorldAr
     for (int dx = -1; dx <= 1; ++dx) {
       if (!dx && !dy) continue;
       const uint32_t o = *a.cells.col<uint32_t>(in->cell_base + torus8(x, y, dx, dy, in->W, in->H), a.occ_off);
-      if (o != kNull && type_of(h, o) == a.alive) ++n;
+      if (o != kNull && type_of(h, o) == a.alive && (a.block == 0 || *fld<uint16_t>(h, o, a.a_blocked) == 0))
+        ++n;
     }
   return n;
 }
@@ -238,7 +250,7 @@ struct CandPrepare {
     uint32_t x, y;
     cell_xy(in, lc, &x, &y);
     const int n = alive_neighbours(h, a, in, x, y);
-    *fld<uint8_t>(h, self, a.c_action) = n == 3 ? ACT_BORN : (n == 0 ? ACT_DELETE : ACT_KEEP);
+    *fld<uint8_t>(h, self, a.c_action) = ((a.born >> n) & 1) ? ACT_BORN : (n == 0 ? ACT_DELETE : ACT_KEEP);
   }
 };
 
@@ -247,12 +259,17 @@ struct AlivePrepare {
   __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
     const uint32_t g = *fld<int32_t>(h, self, a.a_cell);
     *fld<uint8_t>(h, self, a.a_isnew) = 0;
+    const uint32_t blocked = a.block ? *fld<uint16_t>(h, self, a.a_blocked) : 0u;
+    if (blocked) {  // dead and blocking its cell
+      *fld<uint8_t>(h, self, a.a_action) = blocked >= a.block ? ACT_EXPIRE : ACT_AGE;
+      return;
+    }
     const Inst* in = find_inst(a.linst, a.nlinst, g);
     const uint32_t lc = g - in->cell_base;
     uint32_t x, y;
     cell_xy(in, lc, &x, &y);
     const int n = alive_neighbours(h, a, in, x, y);
-    *fld<uint8_t>(h, self, a.a_action) = (n == 2 || n == 3) ? ACT_KEEP : ACT_DIE;
+    *fld<uint8_t>(h, self, a.a_action) = ((a.survive >> n) & 1) ? ACT_KEEP : ACT_DIE;
   }
 };
 
@@ -269,6 +286,7 @@ struct CandUpdate {
         *fld<int32_t>(h, repl, a.a_cell) = (int32_t)g;
         *fld<uint8_t>(h, repl, a.a_action) = ACT_KEEP;
         *fld<uint8_t>(h, repl, a.a_isnew) = 1;
+        *fld<uint16_t>(h, repl, a.a_blocked) = 0;
       }
     }
     *a.cells.col<uint32_t>(g, a.occ_off) = repl;
@@ -314,14 +332,22 @@ struct AliveUpdate {
             *eocc = cnd;
           }
         }
-    } else if (*fld<uint8_t>(h, self, a.a_action) == ACT_DIE) {
-      const uint32_t cnd = smmo_new(h, a.cand);
-      if (cnd != kNull) {
-        *fld<int32_t>(h, cnd, a.c_cell) = (int32_t)g;
-        *fld<uint8_t>(h, cnd, a.c_action) = ACT_KEEP;
+    } else {
+      const uint8_t act = *fld<uint8_t>(h, self, a.a_action);
+      if (act == ACT_DIE && a.block) {
+        *fld<uint16_t>(h, self, a.a_blocked) = 1;  // dead: blocks its cell
+      } else if (act == ACT_AGE) {
+        uint16_t* b = fld<uint16_t>(h, self, a.a_blocked);
+        *b = (uint16_t)(*b + 1);
+      } else if (act == ACT_DIE || act == ACT_EXPIRE) {  // replaced by a Candidate
+        const uint32_t cnd = smmo_new(h, a.cand);
+        if (cnd != kNull) {
+          *fld<int32_t>(h, cnd, a.c_cell) = (int32_t)g;
+          *fld<uint8_t>(h, cnd, a.c_action) = ACT_KEEP;
+        }
+        *a.cells.col<uint32_t>(g, a.occ_off) = cnd;
+        smmo_delete(h, self);
       }
-      *a.cells.col<uint32_t>(g, a.occ_off) = cnd;
-      smmo_delete(h, self);
     }
   }
 };
@@ -347,6 +373,7 @@ struct Export {
       a.out_energy[g] = *fld<int16_t>(h, self, a.s_energy);
     } else if (c == a.alive) {
       a.out_kind[g] = 1;
+      a.out_age[g] = (int16_t)*fld<uint16_t>(h, self, a.a_blocked);
       a.out_state[g] = *fld<uint8_t>(h, self, a.a_isnew);
     } else {
       a.out_kind[g] = 2;
@@ -377,6 +404,7 @@ struct ExportBits {
       a.out_energy[g] = *fld<int16_t>(h, self, a.s_energy);
     } else if (c == a.alive) {
       a.out_kind[g] = 1;
+      a.out_age[g] = (int16_t)*fld<uint16_t>(h, self, a.a_blocked);
       a.out_state[g] = *fld<uint8_t>(h, self, a.a_isnew);
     } else {
       a.out_kind[g] = 2;
@@ -543,9 +571,9 @@ int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32
   }
   if (!st && !li.empty()) {
     smmo_field_desc ag[2] = {{"cell", SMMO_I32, 1, -1}, {"action", SMMO_U8, 1, -1}};
-    smmo_field_desc al[1] = {{"is_new", SMMO_U8, 1, -1}};
+    smmo_field_desc al[2] = {{"is_new", SMMO_U8, 1, -1}, {"blocked", SMMO_U16, 1, -1}};
     st = smmo_class_register(heap, "LAgent", ag, 2, -1, 1, &w->cls_lagent);
-    if (!st) st = smmo_class_register(heap, "Alive", al, 1, w->cls_lagent, 0, &w->cls_alive);
+    if (!st) st = smmo_class_register(heap, "Alive", al, 2, w->cls_lagent, 0, &w->cls_alive);
     if (!st) st = smmo_class_register(heap, "Candidate", nullptr, 0, w->cls_lagent, 0, &w->cls_cand);
   }
   if (heap->cfg.block_data_bytes == 0) heap->cfg.block_data_bytes = 768;  // every class gets N_T = 64
@@ -606,9 +634,13 @@ int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32
     const ClassLayout& C = heap->classes[w->cls_cand].layout;
     a.alive = w->cls_alive; a.cand = w->cls_cand;
     a.a_cell = A.col_off[0]; a.a_action = A.col_off[1]; a.a_isnew = A.col_off[2];
+    a.a_blocked = A.col_off[3];
     a.c_cell = C.col_off[0]; a.c_action = C.col_off[1];
   }
   a.seed = seed;
+  a.survive = (1u << 2) | (1u << 3);  // Life until smmo_world_set_life_rule
+  a.born = 1u << 3;
+  a.block = 0;
   a.fish_breed = w->p.fish_breed; a.shark_breed = w->p.shark_breed; a.starve = w->p.starve;
   a.breed_strict = w->p.breed_strict;
   // agents: gather the per-kind cell lists on the host (setup only)
@@ -621,7 +653,12 @@ int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32
   if (e == cudaSuccess && init_state) e = cudaMemcpyAsync(hs.data(), init_state, N, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { smmo_world_destroy(w); return cuda_status(e); }
-  struct Pop { std::vector<int32_t> cell, target; std::vector<int16_t> age, energy; std::vector<uint8_t> act, isnew; };
+  struct Pop {
+    std::vector<int32_t> cell, target;
+    std::vector<int16_t> age, energy;
+    std::vector<uint8_t> act, isnew;
+    std::vector<uint16_t> blocked;
+  };
   Pop fish, shark, alive, cand;
   for (int i = 0; i < n_inst; ++i) {
     const uint64_t b = w->base[i], n = (uint64_t)w->W[i] * w->H[i];
@@ -635,6 +672,7 @@ int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32
       } else {
         Pop& P = k == 1 ? alive : cand;
         P.cell.push_back((int32_t)g); P.act.push_back(0); P.isnew.push_back(k == 1 ? hs[g] : 0);
+        P.blocked.push_back(k == 1 ? (uint16_t)ha[g] : 0);
       }
     }
   }
@@ -657,7 +695,8 @@ int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32
                          {4, 4, 2, 2}, shark.cell.size());
   }
   if (!st && w->nl) {
-    st = upload(w->cls_alive, {alive.cell.data(), alive.act.data(), alive.isnew.data()}, {4, 1, 1}, alive.cell.size());
+    st = upload(w->cls_alive, {alive.cell.data(), alive.act.data(), alive.isnew.data(), alive.blocked.data()},
+                {4, 1, 1, 2}, alive.cell.size());
     if (!st) st = upload(w->cls_cand, {cand.cell.data(), cand.act.data()}, {4, 1}, cand.cell.size());
   }
   if (!st && w->nw) st = pdo(w, w->cls_wagent, &launch_do_all<Link>, a, s);
@@ -671,6 +710,16 @@ int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32
 int smmo_world_step(smmo_world* w, int nsteps, void* stream) {
   if (!w || nsteps < 0) return SMMO_E_INVALID_ARG;
   return world_steps(w, nsteps, (cudaStream_t)stream, nullptr);
+}
+
+int smmo_world_set_life_rule(smmo_world* w, uint32_t survive, uint32_t born, uint32_t block) {
+  if (!w || survive >= (1u << 9) || born >= (1u << 9) || block > 65535u) return SMMO_E_INVALID_ARG;
+  if ((born & 1u) != 0) return SMMO_E_INVALID_ARG;  // birth with no alive neighbour: candidates would be deleted
+  w->args.survive = survive;
+  w->args.born = born;
+  w->args.block = block;
+  if (w->graph) { cudaGraphExecDestroy(w->graph); w->graph = nullptr; }  // captured with the old rule
+  return SMMO_OK;
 }
 
 int smmo_world_capture(smmo_world* w, int nsteps, void* stream) {

@@ -74,6 +74,11 @@ class World:
     def step(self, n: int = 1):
         smmo.check(smmo.lib().smmo_world_step(self._w, n, smmo._stream(self.stream)), "world_step")
 
+    def set_life_rule(self, survive: int, born: int, block: int):
+        """Rule of the Life-kind instances (see smmo_world_set_life_rule)."""
+        smmo.check(smmo.lib().smmo_world_set_life_rule(self._w, ctypes.c_uint32(survive), ctypes.c_uint32(born),
+                                                       ctypes.c_uint32(block)), "world_set_life_rule")
+
     def capture(self, n: int):
         """Captures n steps into a CUDA graph (needs a non-default stream)."""
         smmo.check(smmo.lib().smmo_world_capture(self._w, n, smmo._stream(self.stream)), "world_capture")
@@ -154,6 +159,29 @@ class Life(World):
         if err:
             raise AssertionError("Life heap inconsistent: %d errors" % err)
         return k.astype(np.uint8), s
+
+
+# Burst (0235678/3468) with a dead cell blocked for 255 generations: the
+# generation application's rule as masks over the alive-neighbour count
+BURST = (0b111101101, 0b101011000, 255)
+
+
+class Generation(World):
+    """A single instance of the generational automaton (thesis Sec. 7.8,
+    "generation"): the object-based Life in which a dead Alive blocks its
+    cell for `block` generations; rule = (survive mask, born mask, block)."""
+
+    def __init__(self, W, H, kind, state, blocked=None, rule=BURST, seed: int = 0, **kw):
+        b = None if blocked is None else np.asarray(blocked).astype(np.int16)
+        super().__init__([LIFE], [W], [H], seed, kind, b, None, state, **kw)
+        self.set_life_rule(*rule)
+
+    def read(self):
+        """(kind, is_new, blocked) per cell."""
+        k, a, _, s, err = self.export()
+        if err:
+            raise AssertionError("generation heap inconsistent: %d errors" % err)
+        return k.astype(np.uint8), s, a.astype(np.uint16)
 
 
 class Traffic:

@@ -177,3 +177,46 @@ def test_results_identical_for_every_tuning_choice(orc):
         for x, y in zip(o, outs[0]):
             assert np.array_equal(x, y)
     assert outs[0][4] == 0
+
+
+@pytest.mark.parametrize("W,H,seed", [(96, 80, 1), (67, 45, 2), (130, 33, 3)])
+def test_generation_burst_matches_oracle(orc, W, H, seed):
+    """The generation application (Burst rule, dead cells blocked for 255
+    generations) equals the oracle cell for cell (kind, is_new, blocked)
+    after 300 generations, so blocked cells have expired into Candidates."""
+    from paper_1908_05845_gb300.workloads import Generation
+    k0, s0 = inputs.gol_initial(W, H, seed, p=(3, 10))
+    g = Generation(W, H, k0, s0, seed=seed)
+    g.step(300)
+    k, s, b = g.read()
+    assert g.heap.check() == 0
+    g.close()
+    ok, os_, ob, cnt = orc.gen_run(W, H, k0, s0, np.zeros(W * H, np.uint16), 300, orc.BURST)
+    assert cnt[:, 5].sum() > 0 and cnt[:, 3].sum() > 0
+    assert np.array_equal(k, ok) and np.array_equal(s, os_) and np.array_equal(b, ob)
+
+
+def test_generation_graph_replay_and_rule_switch(orc):
+    """Graph replay of the generation world matches plain steps; switching
+    the rule back to Life gives Life."""
+    import torch
+    from paper_1908_05845_gb300.workloads import Generation
+    W, H = 64, 48
+    k0, s0 = inputs.gol_initial(W, H, 5, p=(3, 10))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g = Generation(W, H, k0, s0, stream=stream)
+        g.step(5)
+        g.capture(1)
+        for _ in range(20):
+            g.replay()
+        k, s, b = g.read()
+        g.close()
+    ok, os_, ob, _ = orc.gen_run(W, H, k0, s0, np.zeros(W * H, np.uint16), 25, orc.BURST)
+    assert np.array_equal(k, ok) and np.array_equal(b, ob)
+    g = Generation(W, H, k0, s0, rule=orc.LIFE_RULE)
+    g.step(30)
+    k, s, b = g.read()
+    g.close()
+    lk, ls, _ = orc.gol_run(W, H, k0, s0, 30)
+    assert np.array_equal(k, lk) and np.array_equal(s, ls) and not b.any()
