@@ -503,6 +503,76 @@ def run_gol(args):
     return 0
 
 
+def run_generation(args):
+    """The generation application (Sec. 7.8: Life objects with the Burst
+    rule, a dead cell blocked for 255 generations) on a 1024 x 1024 torus
+    from 30 % alive, 500 generations as one captured graph per generation;
+    once plain and once with compact(n = 2) of Alive and Candidate every 50
+    generations (the thesis' defragmentation experiment for this
+    application).  Both runs are checked cell for cell against the oracle."""
+    import torch
+    import oracle
+    from paper_1908_05845_gb300 import inputs
+    from paper_1908_05845_gb300.workloads import Generation
+    W = H = 1024
+    T = args.gen_steps
+    k0, s0 = inputs.gol_initial(W, H, SEED, p=(3, 10))
+    t0 = time.time()
+    ok_, os_, ob, cnt = oracle.gen_run(W, H, k0, s0, np.zeros(W * H, np.uint16), T, oracle.BURST)
+    cpu_s = time.time() - t0
+    out = {}
+    stream = torch.cuda.Stream()
+    for label, every in (("plain", 0), ("compact_every_50", 50)):
+        with torch.cuda.stream(stream):
+            g = Generation(W, H, k0, s0, stream=stream)
+            A, C = g.class_ids["Alive"], g.class_ids["Candidate"]
+            g.capture(1)
+            a, b = _events(stream)
+            c0, c1 = _events(stream)
+            e0 = g.heap.counters()[0]
+            t_compact = 0.0
+            peak_blocks = 0
+            torch.cuda.synchronize()
+            a.record(stream)
+            for t in range(T):
+                g.replay()
+                if every and (t + 1) % every == 0:
+                    c0.record(stream)
+                    g.heap.compact(A, n=2, k1=0)
+                    g.heap.compact(C, n=2, k1=0)
+                    c1.record(stream)
+                    c1.synchronize()
+                    t_compact += c0.elapsed_time(c1)
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b)
+            objs = g.heap.counters()[0] - e0
+            st = g.heap.stats()
+            k, s_, bl = g.read()
+            g.close()
+        out[label] = {"ms_per_generation": ms / T, "object_updates_per_s": objs / (ms / 1e3),
+                      "compaction_ms_total": t_compact,
+                      "alive_blocks_end": st["blocks"][A], "candidate_blocks_end": st["blocks"][C],
+                      "fragmentation_alive_end": st["fragmentation"][A],
+                      "fragmentation_candidate_end": st["fragmentation"][C],
+                      "bit_exact": bool(np.array_equal(k, ok_) and np.array_equal(s_, os_)
+                                        and np.array_equal(bl, ob))}
+    p, c = out["plain"], out["compact_every_50"]
+    line = {"metric": "object-updates/s", "value": p["object_updates_per_s"], "unit": "object-updates/s",
+            "ms_per_step": p["ms_per_generation"], "steps": T, "higher_is_better": True,
+            "dtype": "int32/u16", "data": "synthetic (seeded Philox)",
+            "config": {"workload": "generation_burst_1024x1024", "rule": "0235678/3468, blocked 255",
+                       "initial_alive": 0.3},
+            "runs": out,
+            "compaction_speedup": p["ms_per_generation"] / c["ms_per_generation"],
+            # every object is visited by two of the four do-alls per generation
+            "cpu_baseline": {"value": 2.0 * float(np.sum(cnt[:, :3])) / cpu_s, "unit": "object-updates/s",
+                             "cores": 1, "kind": "oracle",
+                             "sample": "all %d generations (%.1f s)" % (T, cpu_s)}}
+    print(json.dumps(line), flush=True)
+    return 0 if (p["bit_exact"] and c["bit_exact"]) else 1
+
+
 def run_nasch(args):
     import torch
     from paper_1908_05845_gb300 import inputs
@@ -697,7 +767,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="wator",
-                    choices=["wator", "batched", "gol", "nasch", "nbody", "alloc", "compact"])
+                    choices=["wator", "batched", "gol", "generation", "nasch", "nbody", "alloc", "compact"])
+    ap.add_argument("--gen-steps", type=int, default=500)
     ap.add_argument("--compact-objects", type=int, default=32_768_000)
     ap.add_argument("--alloc-n", default="1,4,16,64,256")
     ap.add_argument("--reps", type=int, default=3)
@@ -712,7 +783,8 @@ def main():
         torch.cuda.set_device(local)
         from paper_1908_05845_gb300 import smmo
         smmo.lib()
-        return {"batched": run_batched, "gol": run_gol, "nasch": run_nasch, "nbody": run_nbody,
+        return {"batched": run_batched, "gol": run_gol, "generation": run_generation, "nasch": run_nasch,
+                "nbody": run_nbody,
                 "alloc": run_alloc, "compact": run_compact}[args.workload](args)
     return run_gpu(args, ws, rank, local)
 
