@@ -50,14 +50,22 @@ BYTES_PER_OBJECT = {
 PHASES = ["life_cand_prepare", "life_alive_prepare", "life_cand_update", "life_alive_update",
           "fish_prepare", "fish_update", "shark_prepare", "shark_update"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "wator_2048_fish_update_traffic.txt")  # JSON
-KERNEL_SOURCES = ["paper_1908_05845_gb300/csrc/world.cu", "paper_1908_05845_gb300/csrc/smmo_core.cuh",
-                  "paper_1908_05845_gb300/csrc/grid_common.cuh"]
+# Sources of the Wa-Tor do-all kernels: the allocator and do-all core, the
+# cellular helpers, and the Wa-Tor section of world.cu (between its Wa-Tor
+# and Life banners), so that changes elsewhere keep a traffic capture valid.
+KERNEL_SOURCES = ["paper_1908_05845_gb300/csrc/smmo_core.cuh", "paper_1908_05845_gb300/csrc/grid_common.cuh"]
+WATOR_SECTION = ("paper_1908_05845_gb300/csrc/world.cu",
+                 "// ================================================================ Wa-Tor",
+                 "// ================================================================ Life")
 
 
-def kernel_hash() -> str:
+def kernel_hash(read=lambda f: open(os.path.join(ROOT, f), "rb").read()) -> str:
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        h.update(read(f))
+    src = read(WATOR_SECTION[0]).decode()
+    a, b = src.index(WATOR_SECTION[1]), src.index(WATOR_SECTION[2])
+    h.update(src[a:b].encode())
     return h.hexdigest()[:16]
 
 
