@@ -508,6 +508,7 @@ int world_steps(smmo_world* w, int nsteps, cudaStream_t s, PhaseTimer* pt) {
   for (int k = 0; k < nsteps; ++k) {
     ++w->t;
     k_step_begin<<<1, 1, 0, s>>>(w->d_t);
+    if (pt) pt->launches += 1;
     int st = cuda_status(cudaGetLastError());
     if (w->nl) {  // one Life generation (Sec. 7.8, four do-alls)
       st = pdo(w, w->cls_cand, &launch_do_all<CandPrepare>, a, s, pt, 0);
