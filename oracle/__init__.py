@@ -33,7 +33,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["philox.c", "gol.c", "generation.c", "wator.c", "nasch.c", "nbody.c"]
+_SOURCES = ["philox.c", "gol.c", "generation.c", "wator.c", "nasch.c", "nasch_ctrl.c", "nbody.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -176,6 +176,38 @@ def nasch_run(graph: dict, seed: int, car_v, T: int, t0: int = 0):
     if rc != 0:
         raise ValueError("orc_nasch_run: bad arguments")
     return car_v, cnt[:T]
+
+
+class _NaschCtrl(ctypes.Structure):
+    _fields_ = [("ctrl_kind", ctypes.c_void_p), ("phase_len", ctypes.c_int), ("lookahead", ctypes.c_int)]
+
+
+def nasch_ctrl_run(graph: dict, seed: int, car_v, T: int, ctrl_kind, phase_len: int = 8,
+                   lookahead: int = 5, green=None, timer=None, t0: int = 0):
+    """Traffic with controllers (ctrl_kind per street: -1 none, 0 light,
+    1 smart light, 2 yield).  Returns (car_v, green, timer, counters[T, 6])."""
+    lib = _load()
+    keep = {k: np.ascontiguousarray(graph[k], dtype=dt) for k, dt in
+            [("street_start", np.int32), ("street_len", np.int32), ("out_deg", np.int32),
+             ("out_street", np.int32), ("is_source", np.uint8)]}
+    g = _NaschGraph(int(graph["num_streets"]), _p(keep["street_start"]).value,
+                    _p(keep["street_len"]).value, _p(keep["out_deg"]).value,
+                    _p(keep["out_street"]).value, _p(keep["is_source"]).value,
+                    int(graph["num_cells"]), int(graph.get("v_max", 5)),
+                    int(graph["brake_threshold"]), int(graph.get("sources_enabled", 1)),
+                    int(graph.get("sinks_enabled", 1)))
+    S = int(graph["num_streets"])
+    kind = np.ascontiguousarray(ctrl_kind, dtype=np.int8)
+    c = _NaschCtrl(_p(kind).value, int(phase_len), int(lookahead))
+    car_v = np.ascontiguousarray(car_v, dtype=np.int8).copy()
+    green = np.zeros(S, np.int16) if green is None else np.ascontiguousarray(green, np.int16).copy()
+    timer = np.zeros(S, np.int16) if timer is None else np.ascontiguousarray(timer, np.int16).copy()
+    cnt = np.zeros((max(T, 1), 6), dtype=np.int64)
+    rc = lib.orc_nasch_ctrl_run(ctypes.byref(g), ctypes.byref(c), ctypes.c_uint64(int(seed)), _p(car_v),
+                                _p(green), _p(timer), int(t0), int(T), _p(cnt))
+    if rc != 0:
+        raise ValueError("orc_nasch_ctrl_run: bad arguments")
+    return car_v, green, timer, cnt[:T]
 
 
 # ------------------------------------------------------------------- N-body

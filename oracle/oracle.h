@@ -96,6 +96,23 @@ typedef struct {
 int orc_nasch_run(const orc_nasch_graph* g, uint64_t seed, int8_t* car_v,
                   int t0, int T, int64_t* counters);
 
+/* Traffic controllers (Sec. 7.5): per street o, ctrl_kind[o] = -1 (none),
+ * 0 traffic light, 1 smart traffic light, 2 yield controller; a controller
+ * acts only when o has two or more incoming streets. */
+enum { ORC_CTRL_LIGHT = 0, ORC_CTRL_SMART = 1, ORC_CTRL_YIELD = 2 };
+typedef struct {
+  const int8_t* ctrl_kind;
+  int phase_len;  /* green phase of a traffic light, steps (>= 1) */
+  int lookahead;  /* cells before a crossing checked for a waiting car */
+} orc_nasch_ctrl;
+/* Runs steps t0+1 .. t0+T of traffic with controllers.  car_v as in
+ * orc_nasch_run; green/timer: per-street in/out controller state (index of
+ * the green incoming street, phase timer).  counters (may be NULL): 6 x
+ * int64 per step: [cars, spawned, sunk, moved, claims_lost, switches]. */
+int orc_nasch_ctrl_run(const orc_nasch_graph* g, const orc_nasch_ctrl* ctl,
+                       uint64_t seed, int8_t* car_v, int16_t* green,
+                       int16_t* timer, int t0, int T, int64_t* counters);
+
 /* ---------------------------------------------------------------- N-body */
 typedef struct {
   float G, eps, dt, merge_r;

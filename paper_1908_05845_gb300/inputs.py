@@ -19,7 +19,9 @@ OpenStreetMap street networks -- are not available, these stand in for them):
   street ends in an intersection with 1 + draw(OUTDEG, 0, s) % 3 distinct
   outgoing non-producer streets other than s, picked by successive draws
   draw(OUT, i, s); 200,000 cars (v = 0) on the cells with the smallest
-  draw(PLACE, 0, c) (ties by c).
+  draw(PLACE, 0, c) (ties by c); a street with two or more incoming streets
+  gets controller kind draw(CTRL, 0, s) % 3 (traffic light, smart traffic
+  light, yield).
 * N-body: per body i uniforms u_k = (draw(NBODY, k, i) + 0.5) / 2^32,
   positions u_0..u_2 in [0,1)^3, masses exp(0.5 z) and velocities N(0, 0.01)
   from Box-Muller on u_3..u_10 in float64, rounded to float32 once.
@@ -38,7 +40,7 @@ import numpy as np
 
 TAG_INIT, TAG_FISH, TAG_SHARK, TAG_LEN, TAG_PLACE, TAG_ROUTE, TAG_BRAKE = 0, 1, 2, 3, 4, 5, 6
 TAG_KIND, TAG_SIDE, TAG_OUTDEG, TAG_OUT, TAG_NBODY = 7, 8, 9, 10, 11
-TAG_KILL, TAG_AREF, TAG_BREF = 12, 13, 14
+TAG_KILL, TAG_AREF, TAG_BREF, TAG_CTRL = 12, 13, 14, 15
 
 _M0, _M1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
 _W0, _W1 = np.uint32(0x9E3779B9), np.uint32(0xBB67AE85)
@@ -133,6 +135,21 @@ def nasch_graph(seed: int, num_streets: int = 2000, n_sources: int = 64, n_sinks
                 out_deg=out_deg, out_street=out.reshape(-1), is_source=is_source,
                 num_cells=int(length.sum()), v_max=5, brake_threshold=threshold(*p_brake),
                 sources_enabled=1, sinks_enabled=1)
+
+
+def nasch_controllers(graph: dict, seed: int):
+    """Controller kind per street: -1 for streets with fewer than two
+    incoming streets, else draw(CTRL, 0, street) % 3 (0 traffic light,
+    1 smart traffic light, 2 yield controller)."""
+    S = int(graph["num_streets"])
+    indeg = np.zeros(S, np.int64)
+    out = np.asarray(graph["out_street"]).reshape(S, 3)
+    for s in range(S):
+        for k in range(int(graph["out_deg"][s])):
+            indeg[out[s, k]] += 1
+    kind = (draw(seed, TAG_CTRL, 0, np.arange(S, dtype=np.uint32)) % np.uint32(3)).astype(np.int8)
+    kind[indeg < 2] = -1
+    return kind
 
 
 def nasch_cars(graph: dict, seed: int, n_cars: int = 200_000):
