@@ -417,7 +417,27 @@ int smmo_traffic_step(smmo_traffic* w, int nsteps, void* stream);
  * Synchronises `stream`. */
 int smmo_traffic_export(smmo_traffic* w, int8_t* car_v, int64_t* errors,
                         void* stream);
-/* num_cells, class ids [Cell, Car, Source] (host array of 3), steps done. */
+/* Incoming streets a controller can guard (its inlined inner array). */
+#define SMMO_TRAFFIC_MAX_IN 12
+/* Adds traffic controllers (Sec. 7.5): ctrl_kind (host, one per street):
+ * -1 none, 0 traffic light, 1 smart traffic light, 2 yield controller; a
+ * street with fewer than two incoming streets gets none.  phase_len
+ * (>= 1): green phase of a light in steps; lookahead (>= 0): cells before
+ * the end of an incoming street searched for a waiting car.  Incoming
+ * streets are listed in increasing street id (the yield priority); every
+ * controller starts green on the first of them, timer 0.  From the next
+ * step on, controllers run first and a car from a red street cannot enter
+ * the guarded street (speed limit 0 on its first cell).  Once per traffic
+ * object; SMMO_E_UNSUPPORTED if a guarded street has more than
+ * SMMO_TRAFFIC_MAX_IN incoming streets.  Synchronises `stream`. */
+int smmo_traffic_set_controllers(smmo_traffic* w, const int8_t* ctrl_kind, int phase_len,
+                                 int lookahead, void* stream);
+/* Controller state per street (host arrays of num_streets): index of the
+ * green incoming street and phase timer; 0 for unguarded streets.
+ * Synchronises `stream`. */
+int smmo_traffic_controller_state(smmo_traffic* w, int16_t* green, int16_t* timer, void* stream);
+/* num_cells, class ids [Cell, Car, Source, Controller] (host array of 4),
+ * steps done; each output nullable. */
 int smmo_traffic_info(smmo_traffic* w, int64_t* num_cells, int* class_ids,
                       uint32_t* steps_done);
 int smmo_traffic_destroy(smmo_traffic* w);

@@ -12,6 +12,19 @@
 //   Source::spawn a producer street whose first cell is empty creates a Car.
 // Claims are u64 words per street: ((2^32-1-t) << 32) | cell, atomicMin, so
 // the lowest cell wins and words of older steps never match (no reset).
+//
+// Traffic controllers (Sec. 7.5, optional): a Controller object guards the
+// entry of a street o with two or more incoming streets (listed in an
+// inlined inner array, increasing street id) and runs first in every step,
+// Controller::step, reading the occupancy at step start: a traffic light
+// moves its green on after `phase_len` steps (round robin), a smart traffic
+// light turns green at once for the only incoming street with a waiting
+// car, a yield controller gives green to the first incoming street with a
+// waiting car (a car within `lookahead` cells of the end of a street whose
+// route in this step leads to o).  It publishes the green street per street
+// o; Car::prepare then follows the thesis' adjust-velocity rule with speed
+// limits: the first cell of o has limit 0 for cars from a red street, every
+// other cell v_max (with no controller this is the plain free-cell count).
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -37,6 +50,11 @@ struct TrafficArgs {
   uint32_t car_cls;
   uint32_t c_cell, c_street, c_v, c_route, c_cross;
   uint32_t s_street;      // Source.street column offset
+  int32_t* green_street;  // per street: green incoming street, -1 = no controller
+  // Controller column offsets; k_in is the column index of the first of the
+  // SMMO_TRAFFIC_MAX_IN inlined incoming-street columns
+  uint32_t k_street, k_kind, k_nin, k_green, k_timer, k_in;
+  int32_t phase_len, lookahead;
   uint64_t seed;
   const uint32_t* tp;  // device step counter
   int32_t v_max;
@@ -68,18 +86,30 @@ struct CarPrepare {
       const uint32_t r = philox_draw(a.seed, TAG_ROUTE, t, (uint32_t)(st + L - 1), 0);
       o = __ldg(a.out + 3 * s + (int)(r % (uint32_t)dg));
     }
-    int free_run = 0;
-    for (int k = 1; k <= v; ++k) {
-      const int32_t q = p + k;
-      int32_t cell;
-      if (q < L) cell = st + q;
-      else if (o >= 0) cell = __ldg(a.start + o) + (q - L);
-      else if (a.sinks_enabled) { free_run = k; continue; }  // leaving the network
-      else break;                                               // dead end
-      if (*a.cells.col<uint32_t>((uint32_t)cell, a.occ_off) != kNull) break;
-      free_run = k;
+    // adjust velocity along the path: an occupied cell stops the car before
+    // it; a cell whose limit is below v lowers v to the limit if that still
+    // reaches the cell, else the car stops before it
+    const int32_t gs = o >= 0 ? a.green_street[o] : -1;
+    for (int d = 1; d <= v; ++d) {
+      const int32_t q = p + d;
+      int32_t cell, limit = a.v_max;
+      if (q < L) {
+        cell = st + q;
+      } else if (o >= 0) {
+        cell = __ldg(a.start + o) + (q - L);
+        if (q == L && gs >= 0 && gs != s) limit = 0;  // red at the crossing
+      } else if (a.sinks_enabled) {
+        continue;  // leaving the network: free, no limit
+      } else {
+        v = d - 1;  // dead end
+        break;
+      }
+      if (*a.cells.col<uint32_t>((uint32_t)cell, a.occ_off) != kNull) { v = d - 1; break; }
+      if (v > limit) {
+        if (limit > d - 1) v = limit;
+        else { v = d - 1; break; }
+      }
     }
-    v = free_run;
     if (v > 0 && philox_draw(a.seed, TAG_BRAKE, t, (uint32_t)c, 0) < a.brake_threshold) --v;
     const bool cross = o >= 0 && p + v >= L;
     if (cross)
@@ -140,6 +170,53 @@ struct SourceSpawn {
   }
 };
 
+enum { CTRL_LIGHT = 0, CTRL_SMART = 1, CTRL_YIELD = 2 };
+
+struct CtrlStep {
+  using Args = TrafficArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
+    const int32_t o = *fld<int32_t>(h, self, a.k_street);
+    const int kind = *fld<int8_t>(h, self, a.k_kind);
+    const int n = *fld<int8_t>(h, self, a.k_nin);
+    int16_t* gp = fld<int16_t>(h, self, a.k_green);
+    int16_t* tp = fld<int16_t>(h, self, a.k_timer);
+    const uint32_t t = *a.tp;
+    uint32_t wait = 0;  // bit i: incoming street i has a car waiting for o
+    for (int i = 0; i < n; ++i) {
+      const int32_t s = *fld<int32_t>(h, self, __ldg(&h.cls[c].col_off[a.k_in + i]));
+      const int32_t st = __ldg(a.start + s), L = __ldg(a.len + s), dg = __ldg(a.deg + s);
+      if (dg <= 0) continue;
+      const uint32_t r = philox_draw(a.seed, TAG_ROUTE, t, (uint32_t)(st + L - 1), 0);
+      if (__ldg(a.out + 3 * s + (int)(r % (uint32_t)dg)) != o) continue;
+      for (int k = 0; k < a.lookahead && k < L; ++k)
+        if (*a.cells.col<uint32_t>((uint32_t)(st + L - 1 - k), a.occ_off) != kNull) { wait |= 1u << i; break; }
+    }
+    int gi = *gp, tm = *tp;
+    if (kind == CTRL_YIELD) {
+      if (wait) gi = __ffs(wait) - 1;
+    } else if (kind == CTRL_SMART && __popc(wait) == 1 && !((wait >> gi) & 1)) {
+      gi = __ffs(wait) - 1;
+      tm = 0;
+    } else if (++tm >= a.phase_len) {
+      gi = gi + 1 == n ? 0 : gi + 1;
+      tm = 0;
+    }
+    *gp = (int16_t)gi;
+    *tp = (int16_t)tm;
+    a.green_street[o] = *fld<int32_t>(h, self, __ldg(&h.cls[c].col_off[a.k_in + gi]));
+  }
+};
+
+struct CtrlExport {
+  using Args = TrafficArgs;
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+    const int32_t o = *fld<int32_t>(h, self, a.k_street);
+    // green and timer of street o, packed into the export's 32-bit array
+    reinterpret_cast<int32_t*>(a.out_count)[o] =
+        ((int32_t)*fld<int16_t>(h, self, a.k_green) << 16) | (uint16_t)*fld<int16_t>(h, self, a.k_timer);
+  }
+};
+
 struct CarLink {
   using Args = TrafficArgs;
   __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
@@ -162,14 +239,17 @@ struct CarExport {
 const smmo::MethodEntry g_methods_nasch[] = {
     SMMO_METHOD("nasch.car_prepare", CarPrepare), SMMO_METHOD("nasch.car_move", CarMove),
     SMMO_METHOD("nasch.source_spawn", SourceSpawn), SMMO_METHOD("nasch.car_link", CarLink),
-    SMMO_METHOD("nasch.car_export", CarExport)};
+    SMMO_METHOD("nasch.car_export", CarExport), SMMO_METHOD("nasch.controller_step", CtrlStep),
+    SMMO_METHOD("nasch.controller_export", CtrlExport)};
 const int g_methods_nasch_n = sizeof(g_methods_nasch) / sizeof(g_methods_nasch[0]);
 
 struct smmo_traffic {
   smmo_heap* heap = nullptr;
-  int cls_cell = -1, cls_car = -1, cls_src = -1;
+  int cls_cell = -1, cls_car = -1, cls_src = -1, cls_ctrl = -1;
   int num_streets = 0, num_cells = 0;
+  bool controllers = false;
   int32_t* d_tab = nullptr;  // start | len | deg | out[3]
+  int32_t* d_green = nullptr;  // per street green incoming street (-1: none)
   unsigned long long* d_claim = nullptr;
   uint32_t t = 0;
   uint32_t* d_t = nullptr;
@@ -214,9 +294,13 @@ int smmo_traffic_create(smmo_heap* heap, int num_streets, const int32_t* street_
   smmo_field_desc kf[5] = {{"cell", SMMO_I32, 1, -1}, {"street", SMMO_I32, 1, -1}, {"v", SMMO_I8, 1, -1},
                            {"route", SMMO_I32, 1, -1}, {"cross", SMMO_U8, 1, -1}};
   smmo_field_desc sf[1] = {{"street", SMMO_I32, 1, -1}};
+  smmo_field_desc tf[6] = {{"street", SMMO_I32, 1, -1}, {"kind", SMMO_I8, 1, -1}, {"n_in", SMMO_I8, 1, -1},
+                           {"green", SMMO_I16, 1, -1}, {"timer", SMMO_I16, 1, -1},
+                           {"in", SMMO_I32, SMMO_TRAFFIC_MAX_IN, -1}};
   int st = smmo_class_register(heap, "Car", kf, 5, -1, 0, &w->cls_car);
   if (!st) st = smmo_class_register(heap, "Cell", cf, 1, -1, 0, &w->cls_cell);
   if (!st) st = smmo_class_register(heap, "Source", sf, 1, -1, 0, &w->cls_src);
+  if (!st) st = smmo_class_register(heap, "Controller", tf, 6, -1, 0, &w->cls_ctrl);
   if (heap->cfg.block_data_bytes == 0) heap->cfg.block_data_bytes = 256 + 256 + 64 + 256 + 64;
   if (!st) st = freeze(heap, s);
   if (!st && heap->classes[w->cls_cell].layout.cap != 64) st = SMMO_E_UNSUPPORTED;
@@ -231,6 +315,8 @@ int smmo_traffic_create(smmo_heap* heap, int num_streets, const int32_t* street_
   cudaError_t e = cudaMalloc(&w->d_tab, sizeof(int32_t) * tab.size());
   if (e == cudaSuccess) e = cudaMalloc(&w->d_claim, sizeof(unsigned long long) * num_streets);
   if (e == cudaSuccess) e = cudaMalloc(&w->d_t, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&w->d_green, sizeof(int32_t) * num_streets);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w->d_green, 0xFF, sizeof(int32_t) * num_streets, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(w->d_t, 0, sizeof(uint32_t), s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(w->d_tab, tab.data(), sizeof(int32_t) * tab.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(w->d_claim, 0xFF, sizeof(unsigned long long) * num_streets, s);
@@ -264,6 +350,15 @@ int smmo_traffic_create(smmo_heap* heap, int num_streets, const int32_t* street_
   a.c_cell = K.col_off[0]; a.c_street = K.col_off[1]; a.c_v = K.col_off[2];
   a.c_route = K.col_off[3]; a.c_cross = K.col_off[4];
   a.s_street = heap->classes[w->cls_src].layout.col_off[0];
+  a.green_street = w->d_green;
+  {
+    const ClassLayout& T = heap->classes[w->cls_ctrl].layout;
+    a.k_street = T.col_off[0]; a.k_kind = T.col_off[1]; a.k_nin = T.col_off[2];
+    a.k_green = T.col_off[3]; a.k_timer = T.col_off[4];
+    a.k_in = 5;  // first column index of the inlined incoming-street array
+  }
+  a.phase_len = 8;
+  a.lookahead = v_max;
   a.seed = seed;
   a.v_max = v_max;
   a.brake_threshold = brake_threshold;
@@ -315,6 +410,7 @@ int smmo_traffic_step(smmo_traffic* w, int nsteps, void* stream) {
     ++w->t;
     k_step_begin<<<1, 1, 0, s>>>(w->d_t);
     int st = cuda_status(cudaGetLastError());
+    if (!st && w->controllers) st = pdo(w, w->cls_ctrl, &launch_do_all<CtrlStep>, a, s);
     if (!st) st = pdo(w, w->cls_car, &launch_do_all<CarPrepare>, a, s);
     if (!st) st = pdo(w, w->cls_car, &launch_do_all<CarMove>, a, s, true);  // prepare keeps the cars
     if (!st) st = pdo(w, w->cls_src, &launch_do_all<SourceSpawn>, a, s);
@@ -351,10 +447,87 @@ int smmo_traffic_export(smmo_traffic* w, int8_t* car_v, int64_t* errors, void* s
   return st;
 }
 
+int smmo_traffic_set_controllers(smmo_traffic* w, const int8_t* ctrl_kind, int phase_len, int lookahead,
+                                 void* stream) {
+  if (!w || !ctrl_kind || phase_len < 1 || phase_len > 32767 || lookahead < 0) return SMMO_E_INVALID_ARG;
+  if (w->controllers) return SMMO_E_INVALID_ARG;  // once per traffic object
+  cudaStream_t s = (cudaStream_t)stream;
+  const int S = w->num_streets;
+  // incoming lists in increasing street id, from the host copy of the table
+  std::vector<int32_t> tab(6 * (size_t)S);
+  cudaError_t e = cudaMemcpyAsync(tab.data(), w->d_tab, sizeof(int32_t) * tab.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  std::vector<std::vector<int32_t>> in((size_t)S);
+  for (int i = 0; i < S; ++i)
+    for (int k = 0; k < tab[2 * S + i]; ++k) in[(size_t)tab[3 * S + 3 * i + k]].push_back(i);
+  std::vector<int32_t> street, ins;
+  std::vector<int8_t> kind, nin;
+  std::vector<int16_t> zero;
+  for (int o = 0; o < S; ++o) {
+    if (ctrl_kind[o] < 0 || in[o].size() < 2) continue;
+    if (ctrl_kind[o] > 2 || in[o].size() > SMMO_TRAFFIC_MAX_IN) return SMMO_E_UNSUPPORTED;
+    street.push_back(o);
+    kind.push_back(ctrl_kind[o]);
+    nin.push_back((int8_t)in[o].size());
+    zero.push_back(0);
+  }
+  const size_t n = street.size();
+  w->args.phase_len = phase_len;
+  w->args.lookahead = lookahead;
+  w->controllers = true;
+  if (n == 0) return SMMO_OK;
+  // the inlined array: column k holds the k-th incoming street (-1 past n_in)
+  ins.assign(n * SMMO_TRAFFIC_MAX_IN, -1);
+  for (size_t j = 0; j < n; ++j)
+    for (size_t k = 0; k < in[(size_t)street[j]].size(); ++k) ins[k * n + j] = in[(size_t)street[j]][k];
+  std::vector<const void*> cols = {street.data(), kind.data(), nin.data(), zero.data(), zero.data()};
+  std::vector<size_t> esz = {4, 1, 1, 2, 2};
+  for (int k = 0; k < SMMO_TRAFFIC_MAX_IN; ++k) { cols.push_back(ins.data() + (size_t)k * n); esz.push_back(4); }
+  std::vector<void*> d(cols.size(), nullptr);
+  for (size_t k = 0; k < cols.size() && e == cudaSuccess; ++k) {
+    e = cudaMallocAsync(&d[k], n * esz[k], s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d[k], cols[k], n * esz[k], cudaMemcpyHostToDevice, s);
+  }
+  int st = e == cudaSuccess ? smmo_bulk_new(w->heap, w->cls_ctrl, (int64_t)n, (const void* const*)d.data(), nullptr,
+                                            nullptr, stream)
+                            : cuda_status(e);
+  for (void* p : d) if (p) cudaFreeAsync(p, s);
+  if (!st) { e = cudaStreamSynchronize(s); if (e != cudaSuccess) st = cuda_status(e); }
+  return st;
+}
+
+int smmo_traffic_controller_state(smmo_traffic* w, int16_t* green, int16_t* timer, void* stream) {
+  if (!w || !green || !timer) return SMMO_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int S = w->num_streets;
+  for (int i = 0; i < S; ++i) { green[i] = 0; timer[i] = 0; }
+  if (!w->controllers) return SMMO_OK;
+  int32_t* packed = nullptr;
+  cudaError_t e = cudaMallocAsync(&packed, sizeof(int32_t) * S, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(packed, 0, sizeof(int32_t) * S, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  TrafficArgs a = w->args;
+  a.out_count = reinterpret_cast<uint32_t*>(packed);
+  int st = pdo(w, w->cls_ctrl, &launch_do_all<CtrlExport>, a, s);
+  std::vector<int32_t> h((size_t)S);
+  if (!st) {
+    e = cudaMemcpyAsync(h.data(), packed, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e);
+  }
+  cudaFreeAsync(packed, s);
+  if (st) return st;
+  for (int i = 0; i < S; ++i) { green[i] = (int16_t)(h[(size_t)i] >> 16); timer[i] = (int16_t)(h[(size_t)i] & 0xFFFF); }
+  return SMMO_OK;
+}
+
 int smmo_traffic_info(smmo_traffic* w, int64_t* num_cells, int* class_ids, uint32_t* steps_done) {
   if (!w) return SMMO_E_INVALID_ARG;
   if (num_cells) *num_cells = w->num_cells;
-  if (class_ids) { class_ids[0] = w->cls_cell; class_ids[1] = w->cls_car; class_ids[2] = w->cls_src; }
+  if (class_ids) {
+    class_ids[0] = w->cls_cell; class_ids[1] = w->cls_car; class_ids[2] = w->cls_src; class_ids[3] = w->cls_ctrl;
+  }
   if (steps_done) *steps_done = w->t;
   return SMMO_OK;
 }
@@ -364,6 +537,7 @@ int smmo_traffic_destroy(smmo_traffic* w) {
   if (w->d_tab) cudaFree(w->d_tab);
   if (w->d_claim) cudaFree(w->d_claim);
   if (w->d_t) cudaFree(w->d_t);
+  if (w->d_green) cudaFree(w->d_green);
   delete w;
   return SMMO_OK;
 }

@@ -210,12 +210,29 @@ class Traffic:
             int(graph.get("sources_enabled", 1)), int(graph.get("sinks_enabled", 1)),
             ctypes.c_uint64(seed), ctypes.c_void_p(cv.data_ptr()), smmo._stream(stream),
             ctypes.byref(self._w)), "traffic_create")
-        ids = (ctypes.c_int * 3)()
+        ids = (ctypes.c_int * 4)()
         smmo.check(smmo.lib().smmo_traffic_info(self._w, None, ids, None), "traffic_info")
-        self.class_ids = dict(zip(["Cell", "Car", "Source"], list(ids)))
+        self.class_ids = dict(zip(["Cell", "Car", "Source", "Controller"], list(ids)))
+        self.num_streets = S
 
     def step(self, n: int = 1):
         smmo.check(smmo.lib().smmo_traffic_step(self._w, n, smmo._stream(self.stream)), "traffic_step")
+
+    def set_controllers(self, ctrl_kind, phase_len: int = 8, lookahead: int = 5):
+        """Traffic controllers (smmo_traffic_set_controllers); ctrl_kind per
+        street: -1 none, 0 traffic light, 1 smart traffic light, 2 yield."""
+        k = np.ascontiguousarray(ctrl_kind, dtype=np.int8)
+        arr = (ctypes.c_int8 * len(k))(*k.tolist())
+        smmo.check(smmo.lib().smmo_traffic_set_controllers(self._w, arr, int(phase_len), int(lookahead),
+                                                           smmo._stream(self.stream)), "traffic_set_controllers")
+
+    def controller_state(self):
+        """(green index, timer) per street."""
+        S = self.num_streets
+        g, t = (ctypes.c_int16 * S)(), (ctypes.c_int16 * S)()
+        smmo.check(smmo.lib().smmo_traffic_controller_state(self._w, g, t, smmo._stream(self.stream)),
+                   "traffic_controller_state")
+        return np.array(g, np.int16), np.array(t, np.int16)
 
     def read(self):
         v = torch.empty(self.num_cells, dtype=torch.int8, device="cuda")

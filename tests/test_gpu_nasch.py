@@ -67,3 +67,40 @@ def test_free_flow_and_conservation_on_gpu():
     sim = Traffic(g, 3, v)
     sim.step(200)
     assert (sim.read() >= 0).sum() == (v >= 0).sum()
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_controllers_full_graph_parity(orc, seed):
+    """Traffic with controllers (traffic lights, smart lights, yield) on the
+    2000-street graph: car velocities per cell and every controller's green
+    index and timer equal the oracle's after 200 steps."""
+    g = inputs.nasch_graph(seed)
+    v = inputs.nasch_cars(g, seed)
+    kind = inputs.nasch_controllers(g, seed)
+    sim = Traffic(g, seed, v)
+    sim.set_controllers(kind, phase_len=8, lookahead=5)
+    sim.step(200)
+    got = sim.read()
+    green, timer = sim.controller_state()
+    sim.sync()
+    sim.close()
+    want, wg, wt, cnt = orc.nasch_ctrl_run(g, seed, v, 200, kind, phase_len=8, lookahead=5)
+    assert (cnt[:, 4] == 0).all() and cnt[:, 5].sum() > 0
+    assert np.array_equal(got, want)
+    assert np.array_equal(green, wg) and np.array_equal(timer, wt)
+
+
+def test_controllers_small_graphs_many_seeds(orc):
+    for seed in range(1, 21):
+        g = inputs.nasch_graph(seed, num_streets=10, n_sources=2, n_sinks=2, len_min=6, len_span=10)
+        v = inputs.nasch_cars(g, seed, n_cars=g["num_cells"] // 3)
+        kind = inputs.nasch_controllers(g, seed)
+        sim = Traffic(g, seed, v)
+        sim.set_controllers(kind, phase_len=3, lookahead=4)
+        sim.step(50)
+        got = sim.read()
+        green, timer = sim.controller_state()
+        sim.close()
+        want, wg, wt, _ = orc.nasch_ctrl_run(g, seed, v, 50, kind, phase_len=3, lookahead=4)
+        assert np.array_equal(got, want), seed
+        assert np.array_equal(green, wg) and np.array_equal(timer, wt), seed
