@@ -601,10 +601,29 @@ def run_nasch(args):
         t = a.elapsed_time(b) / 1e3
         e1, a1, f1 = w.heap.counters()
         w.sync()
+    # the same graph with traffic controllers (lights, smart lights, yield)
+    kind = inputs.nasch_controllers(g, SEED)
+    with torch.cuda.stream(stream):
+        w = Traffic(g, SEED, v, stream=stream)
+        w.set_controllers(kind, phase_len=8, lookahead=5)
+        w.step(args.warmup)
+        ce0 = w.heap.counters()[0]
+        torch.cuda.synchronize()
+        a.record(stream)
+        w.step(args.steps)
+        b.record(stream)
+        b.synchronize()
+        tc = a.elapsed_time(b) / 1e3
+        ce1 = w.heap.counters()[0]
+        w.sync()
     print(json.dumps({"metric": "object-updates/s", "value": (e1 - e0) / t, "unit": "object-updates/s",
                       "alloc_free_per_s": ((a1 - a0) + (f1 - f0)) / t, "ms_per_step": 1e3 * t / args.steps,
                       "steps": args.steps, "config": {"workload": "nasch_2000_streets", "cells": g["num_cells"],
-                                                      "cars": int((v >= 0).sum())}}), flush=True)
+                                                      "cars": int((v >= 0).sum())},
+                      "controllers": {"ms_per_step": 1e3 * tc / args.steps, "object_updates_per_s": (ce1 - ce0) / tc,
+                                      "guarded_streets": int((kind >= 0).sum()),
+                                      "kinds": {"light": int((kind == 0).sum()), "smart": int((kind == 1).sum()),
+                                                "yield": int((kind == 2).sum())}}}), flush=True)
     return 0
 
 
