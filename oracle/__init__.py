@@ -33,7 +33,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["philox.c", "gol.c", "generation.c", "wator.c", "nasch.c", "nasch_ctrl.c", "nbody.c"]
+_SOURCES = ["philox.c", "gol.c", "generation.c", "wator.c", "nasch.c", "nasch_ctrl.c", "barnes_hut.c", "nbody.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -208,6 +208,45 @@ def nasch_ctrl_run(graph: dict, seed: int, car_v, T: int, ctrl_kind, phase_len: 
     if rc != 0:
         raise ValueError("orc_nasch_ctrl_run: bad arguments")
     return car_v, green, timer, cnt[:T]
+
+
+# --------------------------------------------------------------- Barnes-Hut
+class _BHParams(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_float), ("eps", ctypes.c_float), ("dt", ctypes.c_float),
+                ("theta", ctypes.c_float)]
+
+
+def bh_run(state: dict, T: int, G=1.0, eps=1e-2, dt=1e-4, theta=0.5):
+    """state: float32 arrays x, y, vx, vy, m.  Returns (new_state, counters[T, 2])."""
+    lib = _load()
+    st = {k: np.ascontiguousarray(state[k], dtype=np.float32).copy() for k in ("x", "y", "vx", "vy", "m")}
+    p = _BHParams(G, eps, dt, theta)
+    cnt = np.zeros((max(T, 1), 2), np.int64)
+    rc = lib.orc_bh_run(len(st["x"]), ctypes.byref(p), _p(st["x"]), _p(st["y"]), _p(st["vx"]), _p(st["vy"]),
+                        _p(st["m"]), int(T), _p(cnt))
+    if rc != 0:
+        raise ValueError("orc_bh_run: bad arguments or coincident bodies")
+    return st, cnt[:T]
+
+
+def bh_accel(x, y, m, eps=1e-2, theta=0.5):
+    lib = _load()
+    x, y, m = (np.ascontiguousarray(a, dtype=np.float32) for a in (x, y, m))
+    ax, ay = np.zeros_like(x), np.zeros_like(x)
+    rc = lib.orc_bh_accel(len(x), ctypes.c_float(eps), ctypes.c_float(theta), _p(x), _p(y), _p(m), _p(ax), _p(ay))
+    if rc != 0:
+        raise ValueError("orc_bh_accel: bad arguments")
+    return ax, ay
+
+
+def bh_build(x, y):
+    lib = _load()
+    x, y = (np.ascontiguousarray(a, dtype=np.float32) for a in (x, y))
+    n, d = ctypes.c_int(), ctypes.c_int()
+    rc = lib.orc_bh_build(len(x), _p(x), _p(y), ctypes.byref(n), ctypes.byref(d))
+    if rc != 0:
+        raise ValueError("orc_bh_build: coincident bodies")
+    return n.value, d.value
 
 
 # ------------------------------------------------------------------- N-body

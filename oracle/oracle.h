@@ -113,6 +113,22 @@ int orc_nasch_ctrl_run(const orc_nasch_graph* g, const orc_nasch_ctrl* ctl,
                        uint64_t seed, int8_t* car_v, int16_t* green,
                        int16_t* timer, int t0, int T, int64_t* counters);
 
+/* ---------------------------------------------------------- Barnes-Hut */
+typedef struct {
+  float G, eps, dt, theta;
+} orc_bh_params;
+/* 2-D Barnes-Hut (Sec. 7.3) on the unit square, FP32 with the fixed order
+ * given in barnes_hut.c.  x, y, vx, vy: N-long in/out; m: masses.
+ * counters (may be NULL): 2 x int64 per step: [tree nodes, node visits].
+ * Returns -1 on bad arguments or two bodies at the same position. */
+int orc_bh_run(int N, const orc_bh_params* p, float* x, float* y, float* vx,
+               float* vy, const float* m, int T, int64_t* counters);
+/* Accelerations (without G) of one tree build, same arithmetic. */
+int orc_bh_accel(int N, float eps, float theta, const float* x, const float* y,
+                 const float* m, float* ax, float* ay);
+/* Tree-node count and depth of the region quad tree of the positions. */
+int orc_bh_build(int N, const float* x, const float* y, int* nodes, int* depth);
+
 /* ---------------------------------------------------------------- N-body */
 typedef struct {
   float G, eps, dt, merge_r;

@@ -25,6 +25,7 @@ OpenStreetMap street networks -- are not available, these stand in for them):
 * N-body: per body i uniforms u_k = (draw(NBODY, k, i) + 0.5) / 2^32,
   positions u_0..u_2 in [0,1)^3, masses exp(0.5 z) and velocities N(0, 0.01)
   from Box-Muller on u_3..u_10 in float64, rounded to float32 once.
+* Barnes-Hut (2-D): the x, y, vx, vy, m of the n-body recipe.
 * Batched: instance i is Life if draw(KIND, 0, i) & 1 else Wa-Tor, side
   floor(64 * 16^u) with u = draw(SIDE, 0, i) / 2^32 (log-uniform 64..1024).
 * Compaction (the thesis' synthetic defragmentation benchmark, Sec. 6.4):
@@ -178,6 +179,12 @@ def nbody_initial(N: int, seed: int, sigma_m: float = 0.5, sigma_v: float = 0.01
               vz=(sigma_v * normal(u[9], u[10])).astype(np.float32),
               live=np.ones(N, np.uint8))
     return st
+
+
+def bh_initial(N: int, seed: int):
+    """2-D Barnes-Hut bodies: the x, y, vx, vy and m of the n-body recipe."""
+    st = nbody_initial(N, seed)
+    return {k: st[k] for k in ("x", "y", "vx", "vy", "m")}
 
 
 # -------------------------------------------------------------- batched
