@@ -486,6 +486,38 @@ int smmo_nbody_forward_ckpt(smmo_nbody* w, int nsteps, int ckpt, double* loss,
 int smmo_nbody_backward(smmo_nbody* w, float* grad_v0, void* stream);
 int smmo_nbody_destroy(smmo_nbody* w);
 
+/* ============================================================ Barnes-Hut
+ * 2-D Barnes-Hut with a dynamic quad tree (Sec. 7.3).  Classes NodeBase
+ * (abstract) {parent, child_idx, px, py, m}, BodyNode {vx, vy, ax, ay, id},
+ * TreeNode {children[4], p1x, p1y, w, frontier, done}; bodies live in the
+ * unit square (reflected at its walls).  A step: tree summaries (bottom-up
+ * frontier traversal), forces (preorder traversal; a tree node acts as one
+ * body when the body is outside its square and w^2 < theta^2 d^2), update,
+ * removal of bodies that left their quadrant, reinsertion (compare-and-swap
+ * descent, device new of tree nodes), collapse (bottom-up; empty tree nodes
+ * deleted, single-body ones replaced by the body).  FP32 in a fixed order,
+ * equal to the CPU oracle bit for bit. */
+typedef struct {
+  float G, eps, dt, theta;  /* eps > 0, theta >= 0 */
+} smmo_bh_params;
+typedef struct smmo_bh smmo_bh;
+/* Registers the classes in a fresh heap (else SMMO_E_FROZEN) and inserts n
+ * bodies (body i has id i).  cols: 5 device arrays of n floats: x, y (in
+ * [0,1), pairwise distinct), vx, vy, m.  Coincident bodies make device
+ * insertion report SMMO_E_BOUNDS (read by smmo_heap_sync).  Synchronises
+ * `stream`. */
+int smmo_bh_create(smmo_heap* heap, int64_t n, const float* const* cols,
+                   const smmo_bh_params* p, void* stream, smmo_bh** out);
+/* nsteps steps; each step reads back one flag per 8 tree levels. */
+int smmo_bh_step(smmo_bh* w, int nsteps, void* stream);
+/* out5: device, 5 x n floats (x, y, vx, vy, m by id); *tree_nodes (host,
+ * nullable) = live TreeNodes.  Synchronises `stream`. */
+int smmo_bh_export(smmo_bh* w, float* out5, int64_t* tree_nodes, void* stream);
+/* class ids [NodeBase, BodyNode, TreeNode] (host array of 3, nullable) and
+ * tree levels processed so far (nullable). */
+int smmo_bh_info(smmo_bh* w, int* class_ids, int64_t* levels);
+int smmo_bh_destroy(smmo_bh* w);
+
 /* Self-test of the branch-free, correctly rounded FP32 square root and
  * reciprocal that the force kernel uses when every coordinate is within
  * 2^18 and eps^2 is in [2^-40, 2^38] (otherwise it uses the IEEE-rounded

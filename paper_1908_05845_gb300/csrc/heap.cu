@@ -468,7 +468,8 @@ const Table kTables[] = {{g_methods_test, &g_methods_test_n},
                          {g_methods_wator, &g_methods_wator_n},
                          {g_methods_gol, &g_methods_gol_n},
                          {g_methods_nasch, &g_methods_nasch_n},
-                         {g_methods_nbody, &g_methods_nbody_n}};
+                         {g_methods_nbody, &g_methods_nbody_n},
+                         {g_methods_bh, &g_methods_bh_n}};
 }  // namespace
 
 const smmo::MethodEntry* smmo::method_by_id(int id) {

@@ -73,6 +73,8 @@ extern const smmo::MethodEntry g_methods_nasch[];
 extern const int g_methods_nasch_n;
 extern const smmo::MethodEntry g_methods_nbody[];
 extern const int g_methods_nbody_n;
+extern const smmo::MethodEntry g_methods_bh[];
+extern const int g_methods_bh_n;
 
 #ifdef __CUDACC__
 // Instantiates the do-all kernel for method M (see smmo_core.cuh).

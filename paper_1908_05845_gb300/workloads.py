@@ -318,3 +318,63 @@ class CompactSynthetic:
 
     def close(self):
         self.heap.close()
+
+
+class BHParams(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_float), ("eps", ctypes.c_float), ("dt", ctypes.c_float),
+                ("theta", ctypes.c_float)]
+
+
+class BarnesHut:
+    """2-D Barnes-Hut with a dynamic quad tree (thesis Sec. 7.3) on one heap.
+    state: float32 arrays x, y (in [0,1), pairwise distinct), vx, vy, m."""
+
+    def __init__(self, state: dict, G: float = 1e-5, eps: float = 1e-2, dt: float = 1e-3,
+                 theta: float = 0.5, heap_bytes: int | None = None, config: smmo.HeapConfig | None = None,
+                 stream=None):
+        self.stream = stream
+        n = len(state["x"])
+        self.n = n
+        cols = [torch.as_tensor(np.ascontiguousarray(state[k], dtype=np.float32)).cuda()
+                for k in ("x", "y", "vx", "vy", "m")]
+        self.heap = smmo.Heap(heap_bytes or int(n * 3.2 * 3200 / 64 * 1.25) + (64 << 20), config, stream=stream)
+        arr = (ctypes.c_void_p * 5)(*[c.data_ptr() for c in cols])
+        self._w = ctypes.c_void_p()
+        smmo.check(smmo.lib().smmo_bh_create(self.heap.handle, ctypes.c_int64(n), arr,
+                                             ctypes.byref(BHParams(G, eps, dt, theta)), smmo._stream(stream),
+                                             ctypes.byref(self._w)), "bh_create")
+        ids = (ctypes.c_int * 3)()
+        smmo.check(smmo.lib().smmo_bh_info(self._w, ids, None), "bh_info")
+        self.class_ids = dict(zip(["NodeBase", "BodyNode", "TreeNode"], list(ids)))
+
+    def step(self, n: int = 1):
+        smmo.check(smmo.lib().smmo_bh_step(self._w, n, smmo._stream(self.stream)), "bh_step")
+
+    def read(self):
+        """(state dict by id, live TreeNodes)."""
+        out = torch.empty(5 * self.n, dtype=torch.float32, device="cuda")
+        tn = ctypes.c_int64()
+        smmo.check(smmo.lib().smmo_bh_export(self._w, ctypes.c_void_p(out.data_ptr()), ctypes.byref(tn),
+                                             smmo._stream(self.stream)), "bh_export")
+        o = out.cpu().numpy().reshape(5, self.n)
+        return dict(zip(("x", "y", "vx", "vy", "m"), o)), tn.value
+
+    def levels(self) -> int:
+        lv = ctypes.c_int64()
+        smmo.check(smmo.lib().smmo_bh_info(self._w, None, ctypes.byref(lv)), "bh_info")
+        return lv.value
+
+    def sync(self):
+        return self.heap.sync()
+
+    def close(self):
+        if self._w:
+            smmo.lib().smmo_bh_destroy(self._w)
+            self._w = ctypes.c_void_p()
+        self.heap.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
