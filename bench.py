@@ -581,6 +581,58 @@ def run_generation(args):
     return 0 if (p["bit_exact"] and c["bit_exact"]) else 1
 
 
+def run_bh(args):
+    """2-D Barnes-Hut with a dynamic quad tree (Sec. 7.3): 65,536 bodies,
+    100 steps (tree summaries, forces, update, removal, reinsertion with
+    device new of tree nodes, collapse with device delete).  Parity: a
+    separate 10-step run against the oracle at full size."""
+    import torch
+    import oracle
+    from paper_1908_05845_gb300 import inputs
+    from paper_1908_05845_gb300.workloads import BarnesHut
+    N = args.bh_bodies
+    P = dict(G=1e-5, eps=1e-2, dt=1e-3, theta=0.5)
+    st = inputs.bh_initial(N, SEED)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = BarnesHut(st, stream=stream, **P)
+        sim.step(args.warmup)
+        e0, a0, f0 = sim.heap.counters()
+        l0 = sim.levels()
+        a, b = _events(stream)
+        torch.cuda.synchronize()
+        a.record(stream)
+        sim.step(args.steps)
+        b.record(stream)
+        b.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        e1, a1, f1 = sim.heap.counters()
+        l1 = sim.levels()
+        _, nodes = sim.read()
+        sim.sync()
+        sim.close()
+        chk = BarnesHut(st, stream=stream, **P)
+        chk.step(10)
+        got, _ = chk.read()
+        chk.close()
+    t0 = time.time()
+    want, _ = oracle.bh_run(st, 10, **P)
+    cpu_s = time.time() - t0
+    exact = all(np.array_equal(got[k], want[k]) for k in ("x", "y", "vx", "vy"))
+    print(json.dumps({"metric": "bodies/s", "value": N * args.steps / t, "unit": "body-steps/s",
+                      "ms_per_step": 1e3 * t / args.steps, "steps": args.steps, "dtype": "f32",
+                      "higher_is_better": True, "data": "synthetic (seeded Philox)",
+                      "config": {"workload": "barnes_hut_2d_%d" % N, **P},
+                      "object_updates_per_s": (e1 - e0) / t,
+                      "tree_node_news_per_step": (a1 - a0) / args.steps,
+                      "tree_node_deletes_per_step": (f1 - f0) / args.steps,
+                      "tree_levels_per_step": (l1 - l0) / args.steps, "tree_nodes_end": nodes,
+                      "parity_10_steps_bit_exact": bool(exact),
+                      "cpu_baseline": {"value": N * 10 / cpu_s, "unit": "body-steps/s", "cores": 1,
+                                       "kind": "oracle", "sample": "10 steps (%.1f s)" % cpu_s}}), flush=True)
+    return 0 if exact else 1
+
+
 def run_nasch(args):
     import torch
     from paper_1908_05845_gb300 import inputs
@@ -794,7 +846,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="wator",
-                    choices=["wator", "batched", "gol", "generation", "nasch", "nbody", "alloc", "compact"])
+                    choices=["wator", "batched", "gol", "generation", "nasch", "nbody", "bh", "alloc", "compact"])
+    ap.add_argument("--bh-bodies", type=int, default=65536)
     ap.add_argument("--gen-steps", type=int, default=500)
     ap.add_argument("--compact-objects", type=int, default=32_768_000)
     ap.add_argument("--alloc-n", default="1,4,16,64,256")
@@ -811,7 +864,7 @@ def main():
         from paper_1908_05845_gb300 import smmo
         smmo.lib()
         return {"batched": run_batched, "gol": run_gol, "generation": run_generation, "nasch": run_nasch,
-                "nbody": run_nbody,
+                "nbody": run_nbody, "bh": run_bh,
                 "alloc": run_alloc, "compact": run_compact}[args.workload](args)
     return run_gpu(args, ws, rank, local)
 

@@ -314,15 +314,19 @@ struct BodyInsert {
       __threadfence();  // the new node is complete before it becomes visible
       if (atomicCAS(slot, child, nn) == child) {
         // the moved body may still be finishing its own insertion: wait
-        // until its parent is cur, then point it at the new node
+        // until its parent is cur (only this thread may change it from cur
+        // now), then write its child index and only then its new parent,
+        // which the next thread to move it waits for (a later child-index
+        // write can then not be overtaken by this one)
         uint32_t* op = F<uint32_t>(h, B, child, C_PARENT);
         int spins = 0;
-        while (atomicCAS(op, cur, nn) != cur) {
+        while (__ldcg(op) != cur) {
           if (++spins > h.bitmap_spins) { set_error(h, SMMO_E_CONTENTION, child); return; }
           __nanosleep(32);
         }
         *F<int8_t>(h, B, child, C_CIDX) = (int8_t)oidx;
         __threadfence();
+        atomicExch(op, nn);
         cur = nn;
         ++depth;
       } else {

@@ -46,3 +46,25 @@ def test_theta_zero_and_fast_moving_bodies(orc):
     for k in ("x", "y", "vx", "vy"):
         assert np.array_equal(got[k], want[k]), k
     assert nodes == orc.bh_build(want["x"], want["y"])[0]
+
+
+def test_clustered_bodies_contended_insertion(orc):
+    """20,000 bodies in a 2^-6-wide square: every insertion descends the
+    same six levels and competes for the same slots; the tree and the
+    trajectory still equal the oracle's.  (Positions are distinct: the
+    square holds 2^36 representable points.)"""
+    st = inputs.bh_initial(20000, 6)
+    st["x"] = (0.5 + st["x"] * 2.0 ** -6).astype(np.float32)
+    st["y"] = (0.25 + st["y"] * 2.0 ** -6).astype(np.float32)
+    assert len(set(zip(st["x"].tolist(), st["y"].tolist()))) == 20000
+    p = dict(P, G=1e-9, dt=1e-4)
+    sim = BarnesHut(st, **p)
+    sim.step(4)
+    got, nodes = sim.read()
+    assert sim.heap.check() == 0
+    sim.sync()
+    sim.close()
+    want, _ = orc.bh_run(st, 4, **p)
+    for k in ("x", "y", "vx", "vy"):
+        assert np.array_equal(got[k], want[k]), k
+    assert nodes == orc.bh_build(want["x"], want["y"])[0]
