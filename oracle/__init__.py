@@ -33,7 +33,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["philox.c", "gol.c", "generation.c", "wator.c", "nasch.c", "nasch_ctrl.c", "barnes_hut.c", "nbody.c"]
+_SOURCES = ["philox.c", "gol.c", "generation.c", "wator.c", "nasch.c", "nasch_ctrl.c", "barnes_hut.c", "bfs.c", "nbody.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -208,6 +208,20 @@ def nasch_ctrl_run(graph: dict, seed: int, car_v, T: int, ctrl_kind, phase_len: 
     if rc != 0:
         raise ValueError("orc_nasch_ctrl_run: bad arguments")
     return car_v, green, timer, cnt[:T]
+
+
+# ---------------------------------------------------------------------- BFS
+def bfs(row_ptr, col, source: int):
+    """(distances int32 with 2^31-1 for unreachable, levels)."""
+    lib = _load()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    d = np.empty(len(rp) - 1, np.int32)
+    lv = ctypes.c_int()
+    rc = lib.orc_bfs(len(rp) - 1, _p(rp), _p(cl), int(source), _p(d), ctypes.byref(lv))
+    if rc != 0:
+        raise ValueError("orc_bfs: bad arguments")
+    return d, lv.value
 
 
 # --------------------------------------------------------------- Barnes-Hut

@@ -113,6 +113,12 @@ int orc_nasch_ctrl_run(const orc_nasch_graph* g, const orc_nasch_ctrl* ctl,
                        uint64_t seed, int8_t* car_v, int16_t* green,
                        int16_t* timer, int t0, int T, int64_t* counters);
 
+/* ----------------------------------------------------------------- BFS */
+/* Distances from `source` on a CSR graph (row_ptr: n + 1 offsets, col:
+ * neighbours); INT32_MAX = unreachable; *levels = largest distance + 1. */
+int orc_bfs(int n, const int32_t* row_ptr, const int32_t* col, int source,
+            int32_t* dist, int* levels);
+
 /* ---------------------------------------------------------- Barnes-Hut */
 typedef struct {
   float G, eps, dt, theta;

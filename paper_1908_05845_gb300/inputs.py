@@ -26,6 +26,8 @@ OpenStreetMap street networks -- are not available, these stand in for them):
   positions u_0..u_2 in [0,1)^3, masses exp(0.5 z) and velocities N(0, 0.01)
   from Box-Muller on u_3..u_10 in float64, rounded to float32 once.
 * Barnes-Hut (2-D): the x, y, vx, vy, m of the n-body recipe.
+* BFS: a grid of side x side vertices whose edges are kept with
+  probability 0.71 each (draw(EDGE, 0, e)), both directions.
 * Batched: instance i is Life if draw(KIND, 0, i) & 1 else Wa-Tor, side
   floor(64 * 16^u) with u = draw(SIDE, 0, i) / 2^32 (log-uniform 64..1024).
 * Compaction (the thesis' synthetic defragmentation benchmark, Sec. 6.4):
@@ -41,7 +43,7 @@ import numpy as np
 
 TAG_INIT, TAG_FISH, TAG_SHARK, TAG_LEN, TAG_PLACE, TAG_ROUTE, TAG_BRAKE = 0, 1, 2, 3, 4, 5, 6
 TAG_KIND, TAG_SIDE, TAG_OUTDEG, TAG_OUT, TAG_NBODY = 7, 8, 9, 10, 11
-TAG_KILL, TAG_AREF, TAG_BREF, TAG_CTRL = 12, 13, 14, 15
+TAG_KILL, TAG_AREF, TAG_BREF, TAG_CTRL, TAG_EDGE = 12, 13, 14, 15, 16
 
 _M0, _M1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
 _W0, _W1 = np.uint32(0x9E3779B9), np.uint32(0xBB67AE85)
@@ -185,6 +187,27 @@ def bh_initial(N: int, seed: int):
     """2-D Barnes-Hut bodies: the x, y, vx, vy and m of the n-body recipe."""
     st = nbody_initial(N, seed)
     return {k: st[k] for k in ("x", "y", "vx", "vy", "m")}
+
+
+def road_grid(side: int, seed: int, keep=(71, 100)):
+    """A road-network-like graph (stand-in for the thesis' Pennsylvania road
+    network, avg. degree 2.83): side x side grid vertices, each grid edge
+    kept iff draw(EDGE, 0, e) < floor(keep * 2^32) (edge e = 2 v for the
+    edge to the right of v, 2 v + 1 for the one below), both directions.
+    Returns CSR (row_ptr, col) with neighbours in increasing id."""
+    n = side * side
+    v = np.arange(n, dtype=np.int64)
+    x, y = v % side, v // side
+    thr = np.uint64(threshold(*keep))  # up to 2^32 (keep every edge)
+    right = (x + 1 < side) & (draw(seed, TAG_EDGE, 0, (2 * v).astype(np.uint32)).astype(np.uint64) < thr)
+    down = (y + 1 < side) & (draw(seed, TAG_EDGE, 0, (2 * v + 1).astype(np.uint32)).astype(np.uint64) < thr)
+    src = np.concatenate([v[right], v[right] + 1, v[down], v[down] + side])
+    dst = np.concatenate([v[right] + 1, v[right], v[down] + side, v[down]])
+    order = np.lexsort((dst, src))
+    src, dst = src[order], dst[order]
+    row_ptr = np.zeros(n + 1, np.int64)
+    np.add.at(row_ptr, src + 1, 1)
+    return np.cumsum(row_ptr).astype(np.int32), dst.astype(np.int32)
 
 
 # -------------------------------------------------------------- batched
