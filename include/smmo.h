@@ -202,6 +202,27 @@ int smmo_bulk_new(smmo_heap* heap, int class_id, int64_t n,
 int smmo_parallel_do(smmo_heap* heap, int class_id, int method_id,
                      const void* args, size_t args_bytes, void* stream);
 
+/* Reducers of smmo_parallel_do_and_reduce (64-bit signed integers; sum
+ * wraps). */
+enum {
+  SMMO_REDUCE_SUM = 0,
+  SMMO_REDUCE_MIN = 1,
+  SMMO_REDUCE_MAX = 2,
+  SMMO_REDUCE_OR = 3,
+  SMMO_REDUCE_AND = 4
+};
+/* parallel_do_and_reduce (Sec. 3.2.2): runs reducing method method_id (one
+ * whose per-object result is an int64) on every object of class_id and its
+ * concrete subclasses that exists at invocation, and combines the results
+ * with reducer `op` into *dev_result (a device int64 owned by the caller;
+ * it is set to the reducer's identity first, so no object gives the
+ * identity).  Same object semantics and argument rules as
+ * smmo_parallel_do; SMMO_E_INVALID_ARG if the method does not reduce.
+ * Asynchronous (capturable in a CUDA graph). */
+int smmo_parallel_do_and_reduce(smmo_heap* heap, int class_id, int method_id,
+                                const void* args, size_t args_bytes, int op,
+                                int64_t* dev_result, void* stream);
+
 /* Handles of all live objects of class_id (and of its subclasses when
  * include_subclasses != 0), in unspecified order, into out_handles
  * (device, capacity `cap`).  *out_count (host) receives the full count,
@@ -517,6 +538,29 @@ int smmo_bh_export(smmo_bh* w, float* out5, int64_t* tree_nodes, void* stream);
  * tree levels processed so far (nullable). */
 int smmo_bh_info(smmo_bh* w, int* class_ids, int64_t* levels);
 int smmo_bh_destroy(smmo_bh* w);
+
+/* ================================================================= BFS
+ * Frontier-based breadth-first search (Sec. 4.3) over Vertex objects
+ * {distance, degree, id, nbr[SMMO_BFS_MAX_DEGREE]} (neighbour handles as an
+ * inlined inner array), one parallel_do_and_reduce (OR) per level. */
+#define SMMO_BFS_MAX_DEGREE 8
+typedef struct smmo_bfs smmo_bfs;
+/* Creates n vertices in a fresh heap (else SMMO_E_FROZEN) from a host CSR
+ * graph (row_ptr: n + 1 offsets starting at 0, col: neighbour ids);
+ * SMMO_E_UNSUPPORTED if a vertex has more than SMMO_BFS_MAX_DEGREE
+ * neighbours.  Synchronises `stream`. */
+int smmo_bfs_create(smmo_heap* heap, int64_t n, const int32_t* row_ptr,
+                    const int32_t* col, void* stream, smmo_bfs** out);
+/* Distances from `source`: resets every vertex, then runs levels in
+ * batches of check_every (1..4096) and reads the batch's OR results back;
+ * levels after the last one change nothing.  *levels (host, nullable) =
+ * largest distance + 1.  Synchronises `stream` once per batch. */
+int smmo_bfs_run(smmo_bfs* w, int32_t source, int check_every, int32_t* levels,
+                 void* stream);
+/* dist: device array of n int32 (distance by vertex id, 2^31 - 1 =
+ * unreachable).  Synchronises `stream`. */
+int smmo_bfs_export(smmo_bfs* w, int32_t* dist, void* stream);
+int smmo_bfs_destroy(smmo_bfs* w);
 
 /* Self-test of the branch-free, correctly rounded FP32 square root and
  * reciprocal that the force kernel uses when every coordinate is within

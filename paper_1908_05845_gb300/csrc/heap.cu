@@ -469,7 +469,8 @@ const Table kTables[] = {{g_methods_test, &g_methods_test_n},
                          {g_methods_gol, &g_methods_gol_n},
                          {g_methods_nasch, &g_methods_nasch_n},
                          {g_methods_nbody, &g_methods_nbody_n},
-                         {g_methods_bh, &g_methods_bh_n}};
+                         {g_methods_bh, &g_methods_bh_n},
+                         {g_methods_bfs, &g_methods_bfs_n}};
 }  // namespace
 
 const smmo::MethodEntry* smmo::method_by_id(int id) {
@@ -663,7 +664,8 @@ int smmo_parallel_do(smmo_heap* h, int c, int method_id, const void* args, size_
                      void* stream) {
   if (!h || c < 0 || c >= (int)h->classes.size()) return SMMO_E_INVALID_ARG;
   const smmo::MethodEntry* m = smmo::method_by_id(method_id);
-  if (!m || args_bytes != m->args_size || (args_bytes && !args) || args_bytes > 1024) return SMMO_E_INVALID_ARG;
+  if (!m || !m->launch || args_bytes != m->args_size || (args_bytes && !args) || args_bytes > 1024)
+    return SMMO_E_INVALID_ARG;
   if (!h->frozen) return SMMO_OK;  // no object exists yet
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<int> cls;
@@ -672,6 +674,41 @@ int smmo_parallel_do(smmo_heap* h, int c, int method_id, const void* args, size_
     int st = smmo::enumerate(h, k, s);
     if (st) return st;
     st = m->launch(h, k, args, s);
+    if (st) return st;
+  }
+  return SMMO_OK;
+}
+
+namespace {
+__global__ void k_set_i64(long long* p, long long v) { *p = v; }
+long long host_identity(int op) {
+  switch (op) {
+    case SMMO_REDUCE_MIN: return 0x7FFFFFFFFFFFFFFFll;
+    case SMMO_REDUCE_MAX: return (long long)0x8000000000000000ull;
+    case SMMO_REDUCE_AND: return -1ll;
+    default: return 0ll;
+  }
+}
+}  // namespace
+
+int smmo_parallel_do_and_reduce(smmo_heap* h, int c, int method_id, const void* args, size_t args_bytes, int op,
+                                int64_t* dev_result, void* stream) {
+  if (!h || c < 0 || c >= (int)h->classes.size() || !dev_result || op < SMMO_REDUCE_SUM || op > SMMO_REDUCE_AND)
+    return SMMO_E_INVALID_ARG;
+  const smmo::MethodEntry* m = smmo::method_by_id(method_id);
+  if (!m || !m->reduce || args_bytes != m->args_size || (args_bytes && !args) || args_bytes > 1024)
+    return SMMO_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  long long* out = reinterpret_cast<long long*>(dev_result);
+  k_set_i64<<<1, 1, 0, s>>>(out, host_identity(op));
+  int st = smmo::cuda_status(cudaGetLastError());
+  if (st || !h->frozen) return st;
+  std::vector<int> cls;
+  smmo::concrete_subtree(h, c, &cls);
+  for (int k : cls) {
+    st = smmo::enumerate(h, k, s);
+    if (st) return st;
+    st = m->reduce(h, k, args, op, out, s);
     if (st) return st;
   }
   return SMMO_OK;

@@ -54,10 +54,13 @@ inline dim3 do_all_grid(const smmo_heap* h) {
 
 // Method registry: methods are compiled-in do-all kernels.
 typedef int (*method_launch_fn)(smmo_heap*, int cls, const void* args, cudaStream_t);
+// reducing methods (parallel_do_and_reduce): fold into *out (device)
+typedef int (*method_reduce_fn)(smmo_heap*, int cls, const void* args, int op, long long* out, cudaStream_t);
 struct MethodEntry {
   const char* name;
   size_t args_size;
-  method_launch_fn launch;
+  method_launch_fn launch;  // null for reducing methods
+  method_reduce_fn reduce;  // null for plain methods
 };
 const MethodEntry* method_by_id(int id);
 }  // namespace smmo
@@ -75,6 +78,8 @@ extern const smmo::MethodEntry g_methods_nbody[];
 extern const int g_methods_nbody_n;
 extern const smmo::MethodEntry g_methods_bh[];
 extern const int g_methods_bh_n;
+extern const smmo::MethodEntry g_methods_bfs[];
+extern const int g_methods_bfs_n;
 
 #ifdef __CUDACC__
 // Instantiates the do-all kernel for method M (see smmo_core.cuh).
@@ -95,5 +100,23 @@ int launch_do_all(smmo_heap* h, int cls, const void* args, cudaStream_t s) {
   smmo::do_all_kernel<M><<<h->num_sms * per_sm, h->cfg.threads_per_cta, 0, s>>>(h->view, cls, *a);
   return smmo::cuda_status(cudaGetLastError());
 }
-#define SMMO_METHOD(name, M) {name, sizeof(typename M::Args), &launch_do_all<M>}
+#define SMMO_METHOD(name, M) {name, sizeof(typename M::Args), &launch_do_all<M>, nullptr}
+
+template <class M>
+int launch_do_all_reduce(smmo_heap* h, int cls, const void* args, int op, long long* out, cudaStream_t s) {
+  const typename M::Args* a = static_cast<const typename M::Args*>(args);
+  static int occ_threads = 0, occ_blocks = 0;
+  if (occ_threads != h->cfg.threads_per_cta) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, smmo::do_all_reduce_kernel<M>, h->cfg.threads_per_cta, 0) !=
+            cudaSuccess || nb < 1)
+      nb = 1;
+    occ_blocks = nb;
+    occ_threads = h->cfg.threads_per_cta;
+  }
+  const int per_sm = occ_blocks < h->cfg.ctas_per_sm ? occ_blocks : h->cfg.ctas_per_sm;
+  smmo::do_all_reduce_kernel<M><<<h->num_sms * per_sm, h->cfg.threads_per_cta, 0, s>>>(h->view, cls, *a, op, out);
+  return smmo::cuda_status(cudaGetLastError());
+}
+#define SMMO_METHOD_REDUCE(name, M) {name, sizeof(typename M::Args), nullptr, &launch_do_all_reduce<M>}
 #endif

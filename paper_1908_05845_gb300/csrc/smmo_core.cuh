@@ -580,5 +580,76 @@ __global__ void __launch_bounds__(512, 3) do_all_kernel(HeapView h, uint32_t c,
   alloc_cache_flush(h);
 }
 
+// ------------------------------------------------------- do-all with reduce
+// parallel_do_and_reduce (Sec. 3.2.2, the SMMO programming interface: the
+// method's return values are combined with a binary reducer, e.g. for the
+// termination test of an iterative algorithm): M::run returns a long long;
+// each thread folds its values, then the warp (shuffles), the CTA (shared
+// memory) and the grid (one 64-bit atomic per CTA on *out, which holds the
+// identity before the launch).  Integer reducers only, so the result does
+// not depend on the order of the objects.
+__device__ __forceinline__ long long reduce_identity(int op) {
+  switch (op) {
+    case SMMO_REDUCE_MIN: return 0x7FFFFFFFFFFFFFFFll;
+    case SMMO_REDUCE_MAX: return (long long)0x8000000000000000ull;
+    case SMMO_REDUCE_AND: return -1ll;
+    default: return 0ll;  // sum, or
+  }
+}
+
+__device__ __forceinline__ long long reduce2(int op, long long x, long long y) {
+  switch (op) {
+    case SMMO_REDUCE_MIN: return x < y ? x : y;
+    case SMMO_REDUCE_MAX: return x > y ? x : y;
+    case SMMO_REDUCE_OR: return x | y;
+    case SMMO_REDUCE_AND: return x & y;
+    default: return (long long)((unsigned long long)x + (unsigned long long)y);  // wrapping sum
+  }
+}
+
+template <class M>
+__global__ void __launch_bounds__(512, 3) do_all_reduce_kernel(HeapView h, uint32_t c, typename M::Args args,
+                                                               int op, long long* out) {
+  __shared__ long long part[16];
+  const uint32_t n = __ldcg(&h.st->rcount);
+  const uint32_t cap = __ldg(&h.cls[c].cap);
+  const uint32_t halves = cap > 32 ? 2u : 1u;
+  const uint32_t units = n * halves;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  alloc_cache_init();
+  uint32_t visited = 0;
+  long long acc = reduce_identity(op);
+  const uint32_t per = (units + nwarps - 1) / nwarps;
+  const uint32_t ub = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * per;
+  const uint32_t ue = ub + per < units ? ub + per : units;
+  for (uint32_t u = ub; u < ue; ++u) {
+    const uint32_t i = halves == 2 ? (u >> 1) : u;
+    const uint32_t slot = (halves == 2 ? (u & 1) * 32 : 0) + lane;
+    const REntry e = h.R[i];
+    g_wcache[threadIdx.x >> 5].hint = e.block;
+    if (lane == 0) visited += __popcll(halves == 2 ? (e.bits >> ((u & 1) * 32)) & 0xFFFFFFFFull : e.bits);
+    if ((e.bits >> slot) & 1) acc = reduce2(op, acc, M::run(h, args, c, (e.block << 6) | slot));
+    __syncwarp();
+  }
+  if (lane == 0 && visited) count(h, SMMO_CTR_VISIT, visited);
+  alloc_cache_flush(h);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) acc = reduce2(op, acc, __shfl_xor_sync(0xFFFFFFFFu, acc, o));
+  if (lane == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long v = part[0];
+    for (uint32_t w = 1; w < (blockDim.x >> 5); ++w) v = reduce2(op, v, part[w]);
+    switch (op) {
+      case SMMO_REDUCE_MIN: atomicMin(out, v); break;
+      case SMMO_REDUCE_MAX: atomicMax(out, v); break;
+      case SMMO_REDUCE_OR: atomicOr((unsigned long long*)out, (unsigned long long)v); break;
+      case SMMO_REDUCE_AND: atomicAnd((unsigned long long*)out, (unsigned long long)v); break;
+      default: atomicAdd((unsigned long long*)out, (unsigned long long)v); break;
+    }
+  }
+}
+
 #endif  // __CUDACC__
 }  // namespace smmo

@@ -74,6 +74,15 @@ struct SetRefFrom {
   }
 };
 
+// Reducing method: the value of int32 column col (or 1 if count is set).
+struct ValueI32 {
+  struct Args { uint32_t col; uint32_t count; };
+  __device__ static long long run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
+    if (a.count) return 1;
+    return *field_ptr<int32_t>(h, __ldg(&h.cls[c].col_off[a.col]), self);
+  }
+};
+
 }  // namespace
 
 const smmo::MethodEntry g_methods_test[] = {
@@ -83,5 +92,6 @@ const smmo::MethodEntry g_methods_test[] = {
     SMMO_METHOD("test.free_ref", FreeRef),
     SMMO_METHOD("test.replace", Replace),
     SMMO_METHOD("test.set_ref_from", SetRefFrom),
+    SMMO_METHOD_REDUCE("test.value_i32", ValueI32),
 };
 const int g_methods_test_n = sizeof(g_methods_test) / sizeof(g_methods_test[0]);

@@ -223,6 +223,17 @@ class Heap:
         check(lib().smmo_parallel_do(self._h, cls, mid, ap, ctypes.c_size_t(n),
                                      _stream(self.stream)), "parallel_do")
 
+    def parallel_do_and_reduce(self, cls: int, method, args=None, op: int = 0, out: torch.Tensor | None = None):
+        """Runs a reducing method and returns the combined int64 (reads it
+        back) or, with `out` (a one-element int64 CUDA tensor), leaves it
+        there without synchronising."""
+        mid = method_id(method) if isinstance(method, str) else int(method)
+        ap, n = (None, 0) if args is None else (ctypes.byref(args), ctypes.sizeof(args))
+        dst = out if out is not None else torch.empty(1, dtype=torch.int64, device=self.buf.device)
+        check(lib().smmo_parallel_do_and_reduce(self._h, cls, mid, ap, ctypes.c_size_t(n), int(op), _ptr(dst),
+                                                _stream(self.stream)), "parallel_do_and_reduce")
+        return None if out is not None else int(dst.item())
+
     def enumerate_live(self, cls: int, include_subclasses: bool = True, cap: int | None = None):
         if cap is None:
             st = self.stats()
@@ -313,6 +324,13 @@ class FreeRefArgs(ctypes.Structure):
 
 class ReplaceArgs(ctypes.Structure):
     _fields_ = [("target", ctypes.c_uint32), ("col", ctypes.c_uint32), ("tcol", ctypes.c_uint32)]
+
+
+REDUCE_SUM, REDUCE_MIN, REDUCE_MAX, REDUCE_OR, REDUCE_AND = range(5)
+
+
+class ValueI32Args(ctypes.Structure):
+    _fields_ = [("col", ctypes.c_uint32), ("count", ctypes.c_uint32)]
 
 
 class SetRefFromArgs(ctypes.Structure):

@@ -378,3 +378,47 @@ class BarnesHut:
             self.close()
         except Exception:
             pass
+
+
+class Bfs:
+    """Frontier-based BFS over Vertex objects (thesis Sec. 4.3), terminated
+    with parallel_do_and_reduce.  row_ptr/col: CSR graph (host arrays)."""
+
+    def __init__(self, row_ptr, col, heap_bytes: int | None = None, config: smmo.HeapConfig | None = None,
+                 stream=None):
+        self.stream = stream
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        cl = np.ascontiguousarray(col, dtype=np.int32)
+        self.n = len(rp) - 1
+        self.heap = smmo.Heap(heap_bytes or int(self.n * 44 * 1.3) + (64 << 20), config, stream=stream)
+        self._w = ctypes.c_void_p()
+        smmo.check(smmo.lib().smmo_bfs_create(self.heap.handle, ctypes.c_int64(self.n),
+                                              rp.ctypes.data_as(ctypes.c_void_p), cl.ctypes.data_as(ctypes.c_void_p),
+                                              smmo._stream(stream), ctypes.byref(self._w)), "bfs_create")
+
+    def run(self, source: int, check_every: int = 16) -> int:
+        lv = ctypes.c_int32()
+        smmo.check(smmo.lib().smmo_bfs_run(self._w, int(source), int(check_every), ctypes.byref(lv),
+                                           smmo._stream(self.stream)), "bfs_run")
+        return lv.value
+
+    def distances(self):
+        d = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        smmo.check(smmo.lib().smmo_bfs_export(self._w, ctypes.c_void_p(d.data_ptr()), smmo._stream(self.stream)),
+                   "bfs_export")
+        return d.cpu().numpy()
+
+    def sync(self):
+        return self.heap.sync()
+
+    def close(self):
+        if self._w:
+            smmo.lib().smmo_bfs_destroy(self._w)
+            self._w = ctypes.c_void_p()
+        self.heap.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

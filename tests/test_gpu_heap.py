@@ -159,3 +159,43 @@ def test_double_free_detected():
     st, detail = h.sync(raise_on_error=False)
     assert st == -7 and detail == int(hb[0].item()) & 0xFFFFFFFF
     assert h.check() == 0
+
+
+def test_parallel_do_and_reduce_all_reducers():
+    """parallel_do_and_reduce over a class with holes and a subclass: sum,
+    min, max, or, and and a count equal numpy over the live objects; an
+    empty class gives the reducers' identities; a plain method is refused."""
+    h = smmo.Heap(64 << 20)
+    A = h.register("A", [("v", smmo.I32)])
+    B = h.register("B", [("w", smmo.I32)], parent=A)
+    rng = np.random.default_rng(3)
+    va = rng.integers(-10**6, 10**6, 5000).astype(np.int32)
+    vb = rng.integers(0, 1 << 20, 3000).astype(np.int32)
+    h.bulk_new(A, len(va), [torch.as_tensor(va).cuda()])
+    h.bulk_new(B, len(vb), [torch.as_tensor(vb).cuda(), torch.zeros(len(vb), dtype=torch.int32).cuda()])
+    h.parallel_do(A, "test.free_self_if", smmo.FreeSelfIfArgs(0, 7, 3))  # holes in A and B
+    keep = np.concatenate([va, vb])
+    keep = keep[((keep % 7) + 7) % 7 != 3].astype(np.int64)
+    arg = smmo.ValueI32Args(0, 0)
+    assert h.parallel_do_and_reduce(A, "test.value_i32", arg, smmo.REDUCE_SUM) == keep.sum()
+    assert h.parallel_do_and_reduce(A, "test.value_i32", arg, smmo.REDUCE_MIN) == keep.min()
+    assert h.parallel_do_and_reduce(A, "test.value_i32", arg, smmo.REDUCE_MAX) == keep.max()
+    orv = 0
+    andv = -1
+    for x in keep.tolist():
+        orv |= x
+        andv &= x
+    assert h.parallel_do_and_reduce(A, "test.value_i32", arg, smmo.REDUCE_OR) == orv
+    assert h.parallel_do_and_reduce(A, "test.value_i32", arg, smmo.REDUCE_AND) == andv
+    assert h.parallel_do_and_reduce(A, "test.value_i32", smmo.ValueI32Args(0, 1), smmo.REDUCE_SUM) == len(keep)
+    C = smmo.Heap(8 << 20)
+    E = C.register("E", [("v", smmo.I32)])
+    C.bulk_new(E, 1, [torch.zeros(1, dtype=torch.int32).cuda()])
+    C.parallel_do(E, "test.free_self_if", smmo.FreeSelfIfArgs(0, 0, 0))
+    assert C.parallel_do_and_reduce(E, "test.value_i32", arg, smmo.REDUCE_MIN) == 2**63 - 1
+    assert C.parallel_do_and_reduce(E, "test.value_i32", arg, smmo.REDUCE_SUM) == 0
+    with pytest.raises(smmo.SmmoError):
+        h.parallel_do_and_reduce(A, "test.add_i32", smmo.AddI32Args(0, 1), smmo.REDUCE_SUM)
+    with pytest.raises(smmo.SmmoError):
+        h.parallel_do(A, "test.value_i32", arg)
+    h.sync()
