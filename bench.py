@@ -633,6 +633,53 @@ def run_bh(args):
     return 0 if exact else 1
 
 
+def run_bfs(args):
+    """Frontier BFS (Sec. 4.3) on a 1043 x 1043 road grid (1,087,849
+    vertices, about 3.08 M directed edges: the size of the thesis'
+    Pennsylvania road network), one parallel_do_and_reduce per level.
+    Timed: the whole search from vertex 0 (best of `reps`); checked against
+    the oracle."""
+    import torch
+    import oracle
+    from paper_1908_05845_gb300 import inputs
+    from paper_1908_05845_gb300.workloads import Bfs
+    side = 1043
+    rp, col = inputs.road_grid(side, SEED)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g = Bfs(rp, col, stream=stream)
+        g.run(0, check_every=args.bfs_check)  # warm-up
+        a, b = _events(stream)
+        best = None
+        for _ in range(args.reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            a.record(stream)
+            lv = g.run(0, check_every=args.bfs_check)
+            b.record(stream)
+            b.synchronize()
+            wall = time.perf_counter() - t0
+            ms = a.elapsed_time(b)
+            best = (ms, wall, lv) if best is None or ms < best[0] else best
+        d = g.distances()
+        g.close()
+    t0 = time.time()
+    want, wl = oracle.bfs(rp, col, 0)
+    cpu_s = time.time() - t0
+    ms, wall, lv = best
+    edges = int(len(col))
+    print(json.dumps({"metric": "traversed edges/s", "value": edges / (ms / 1e3), "unit": "edges/s",
+                      "ms_per_search": ms, "wall_ms_per_search": 1e3 * wall, "levels": lv,
+                      "ms_per_level": ms / lv, "higher_is_better": True, "dtype": "int32",
+                      "data": "synthetic (seeded Philox)",
+                      "config": {"workload": "bfs_road_grid_%dx%d" % (side, side), "vertices": side * side,
+                                 "directed_edges": edges, "check_every": args.bfs_check},
+                      "bit_exact": bool(np.array_equal(d, want) and lv == wl),
+                      "cpu_baseline": {"value": edges / cpu_s, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                                       "sample": "one full search (%.3f s)" % cpu_s}}), flush=True)
+    return 0 if np.array_equal(d, want) else 1
+
+
 def run_nasch(args):
     import torch
     from paper_1908_05845_gb300 import inputs
@@ -846,7 +893,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="wator",
-                    choices=["wator", "batched", "gol", "generation", "nasch", "nbody", "bh", "alloc", "compact"])
+                    choices=["wator", "batched", "gol", "generation", "nasch", "nbody", "bh", "bfs", "alloc",
+                             "compact"])
+    ap.add_argument("--bfs-check", type=int, default=32)
     ap.add_argument("--bh-bodies", type=int, default=65536)
     ap.add_argument("--gen-steps", type=int, default=500)
     ap.add_argument("--compact-objects", type=int, default=32_768_000)
@@ -864,7 +913,7 @@ def main():
         from paper_1908_05845_gb300 import smmo
         smmo.lib()
         return {"batched": run_batched, "gol": run_gol, "generation": run_generation, "nasch": run_nasch,
-                "nbody": run_nbody, "bh": run_bh,
+                "nbody": run_nbody, "bh": run_bh, "bfs": run_bfs,
                 "alloc": run_alloc, "compact": run_compact}[args.workload](args)
     return run_gpu(args, ws, rank, local)
 

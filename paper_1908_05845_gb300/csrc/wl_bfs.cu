@@ -175,17 +175,19 @@ int smmo_bfs_run(smmo_bfs* w, int32_t source, int check_every, int32_t* levels, 
   }
   BfsArgs a = w->args;
   a.source = source;
+  // the vertex set does not change during the search, so one enumeration
+  // serves every level (each level is parallel_do_and_reduce's reducing
+  // do-all over that snapshot, the OR folded into a zeroed flag)
   int st = enumerate(w->heap, w->cls, s);
   if (!st) st = launch_do_all<VertexReset>(w->heap, w->cls, &a, s);
-  int method = -1;
-  if (!st) st = smmo_method_lookup("bfs.vertex_visit", &method);
   std::vector<long long> hf((size_t)check_every);
   for (int32_t base = 0; !st; base += check_every) {
     if (base > (int32_t)w->n0) return SMMO_E_TIMEOUT;  // more levels than vertices: impossible
+    cudaError_t e0 = cudaMemsetAsync(w->d_flags, 0, sizeof(long long) * check_every, s);
+    if (e0 != cudaSuccess) return cuda_status(e0);
     for (int k = 0; k < check_every && !st; ++k) {
       a.frontier = base + k;
-      st = smmo_parallel_do_and_reduce(w->heap, w->cls, method, &a, sizeof(a), SMMO_REDUCE_OR,
-                                       reinterpret_cast<int64_t*>(w->d_flags + k), stream);
+      st = launch_do_all_reduce<VertexVisit>(w->heap, w->cls, &a, SMMO_REDUCE_OR, w->d_flags + k, s);
     }
     if (st) break;
     cudaError_t e = cudaMemcpyAsync(hf.data(), w->d_flags, sizeof(long long) * check_every, cudaMemcpyDeviceToHost, s);
