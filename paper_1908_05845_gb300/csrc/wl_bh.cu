@@ -44,6 +44,9 @@ enum { B_VX = 5, B_VY = 6, B_AX = 7, B_AY = 8, B_ID = 9 };
 enum { T_CH = 5, T_P1X = 9, T_P1Y = 10, T_W = 11, T_FRONT = 12, T_DONE = 13 };
 
 constexpr int kMaxDepth = 60;      // squares down to 2^-60
+// error details: the handle, tagged with the place that gave up
+constexpr unsigned long long kTagWaitParent = 1ull << 40, kTagBudget = 2ull << 40, kTagDepth = 3ull << 40,
+                             kTagStack = 4ull << 40;
 constexpr int kStack = 3 * kMaxDepth + 4;
 constexpr int kInsertBudget = 1 << 14;
 
@@ -187,7 +190,7 @@ __device__ void body_force(const HeapView& h, const BHArgs& a, uint32_t self) {
   // the budget only guards against a damaged tree
   uint64_t budget = (uint64_t)a.n0 * kMaxDepth + 64;
   while (sp > 0) {
-    if (budget-- == 0) { set_error(h, SMMO_E_BOUNDS, self); break; }
+    if (budget-- == 0) { set_error(h, SMMO_E_BOUNDS, kTagStack | self); break; }
     const uint32_t nd = stack[--sp];
     if (type_of(h, nd) == B) {
       if (nd != self) pair_acc<FAST>(xs, ys, *F<float>(h, B, nd, C_PX), *F<float>(h, B, nd, C_PY),
@@ -200,7 +203,7 @@ __device__ void body_force(const HeapView& h, const BHArgs& a, uint32_t self) {
     const float dx = fs(cx, xs), dy = fs(cy, ys);
     const float d2 = fa(fm(dx, dx), fm(dy, dy));
     if (inside || fm(w, w) >= fm(a.theta2, d2)) {
-      if (sp + 4 > kStack) { set_error(h, SMMO_E_BOUNDS, nd); break; }
+      if (sp + 4 > kStack) { set_error(h, SMMO_E_BOUNDS, kTagStack | nd); break; }
       for (int i = 3; i >= 0; --i) {
         const uint32_t ch = *F<uint32_t>(h, T, nd, T_CH + i);
         if (ch != kNull) stack[sp++] = ch;
@@ -289,11 +292,11 @@ struct BodyInsert {
       }
       if (type_of(h, child) == T) {
         cur = child;
-        if (++depth > kMaxDepth) { set_error(h, SMMO_E_BOUNDS, self); return; }
+        if (++depth > kMaxDepth) { set_error(h, SMMO_E_BOUNDS, kTagDepth | self); return; }
         continue;
       }
       // the slot holds a body: put both under a new tree node
-      if (depth + 1 > kMaxDepth) { set_error(h, SMMO_E_BOUNDS, self); return; }  // coincident bodies
+      if (depth + 1 > kMaxDepth) { set_error(h, SMMO_E_BOUNDS, kTagDepth | self); return; }  // coincident bodies
       const uint32_t nn = smmo_new(h, T);
       if (nn == kNull) return;  // out of memory, recorded by new
       const float hw = fm(w, 0.5f);
@@ -321,7 +324,7 @@ struct BodyInsert {
         uint32_t* op = F<uint32_t>(h, B, child, C_PARENT);
         int spins = 0;
         while (__ldcg(op) != cur) {
-          if (++spins > h.bitmap_spins) { set_error(h, SMMO_E_CONTENTION, child); return; }
+          if (++spins > h.bitmap_spins) { set_error(h, SMMO_E_CONTENTION, kTagWaitParent | child); return; }
           __nanosleep(32);
         }
         *F<int8_t>(h, B, child, C_CIDX) = (int8_t)oidx;
@@ -333,7 +336,7 @@ struct BodyInsert {
         smmo_delete(h, nn);  // another thread changed the slot first
       }
     }
-    set_error(h, SMMO_E_CONTENTION, self);
+    set_error(h, SMMO_E_CONTENTION, kTagBudget | self);
   }
 };
 
@@ -370,21 +373,23 @@ struct smmo_bh {
 };
 
 namespace {
-int pdo(smmo_bh* w, int cls, method_launch_fn fn, const BHArgs& a, cudaStream_t s) {
-  int st = enumerate(w->heap, cls, s);
+int pdo(smmo_bh* w, int cls, method_launch_fn fn, const BHArgs& a, cudaStream_t s, bool reuse = false) {
+  int st = reuse ? SMMO_OK : enumerate(w->heap, cls, s);
   if (!st) st = fn(w->heap, cls, &a, s);
   return st;
 }
 
 // Bottom-up traversal: init, then groups of 8 (process, advance) levels
-// until the root is done (extra levels after that change nothing).
-int bottom_up(smmo_bh* w, method_launch_fn process, cudaStream_t s) {
+// until the root is done (extra levels after that change nothing).  With
+// `fixed` (the process step creates and deletes no tree node, as for the
+// summaries) one enumeration serves the whole traversal.
+int bottom_up(smmo_bh* w, method_launch_fn process, cudaStream_t s, bool fixed) {
   const BHArgs& a = w->args;
   int st = pdo(w, w->cls_tree, &launch_do_all<TreeInitFrontier>, a, s);
   for (int group = 0; group < 64 && !st; ++group) {
     for (int k = 0; k < 8 && !st; ++k) {
-      st = pdo(w, w->cls_tree, process, a, s);
-      if (!st) st = pdo(w, w->cls_tree, &launch_do_all<TreeAdvance>, a, s);
+      st = pdo(w, w->cls_tree, process, a, s, fixed);
+      if (!st) st = pdo(w, w->cls_tree, &launch_do_all<TreeAdvance>, a, s, fixed);
       ++w->levels;
     }
     if (st) break;
@@ -497,12 +502,14 @@ int smmo_bh_step(smmo_bh* w, int nsteps, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const BHArgs& a = w->args;
   for (int k = 0; k < nsteps; ++k) {
-    int st = bottom_up(w, &launch_do_all<TreeSummary>, s);
+    int st = bottom_up(w, &launch_do_all<TreeSummary>, s, true);
+    // no body is created or deleted in a step: one enumeration of the
+    // bodies serves the four body do-alls
     if (!st) st = pdo(w, w->cls_body, &launch_do_all<BodyForce>, a, s);
-    if (!st) st = pdo(w, w->cls_body, &launch_do_all<BodyUpdate>, a, s);
-    if (!st) st = pdo(w, w->cls_body, &launch_do_all<BodyRemove>, a, s);
-    if (!st) st = pdo(w, w->cls_body, &launch_do_all<BodyInsert>, a, s);
-    if (!st) st = bottom_up(w, &launch_do_all<TreeCollapse>, s);
+    if (!st) st = pdo(w, w->cls_body, &launch_do_all<BodyUpdate>, a, s, true);
+    if (!st) st = pdo(w, w->cls_body, &launch_do_all<BodyRemove>, a, s, true);
+    if (!st) st = pdo(w, w->cls_body, &launch_do_all<BodyInsert>, a, s, true);
+    if (!st) st = bottom_up(w, &launch_do_all<TreeCollapse>, s, false);
     if (st) return st;
   }
   return SMMO_OK;
