@@ -33,7 +33,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["philox.c", "gol.c", "generation.c", "wator.c", "nasch.c", "nasch_ctrl.c", "barnes_hut.c", "bfs.c", "nbody.c"]
+_SOURCES = ["philox.c", "gol.c", "generation.c", "wator.c", "nasch.c", "nasch_ctrl.c", "barnes_hut.c", "bfs.c", "structure.c", "nbody.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -382,3 +382,44 @@ def nbody_loss_f64(pos0, vel0, m, T, G=1.0, eps=1e-2, dt=1e-3):
     _, v = nbody_run_f64(pos0, vel0, m, T, G, eps, dt)
     m = _d(m)
     return 0.5 * float(np.sum(m[:, None] * v * v))
+
+
+# ---------------------------------------------------------------- structure
+STRUCT_ANCHOR, STRUCT_PULL, STRUCT_NODE = 0, 1, 2
+PHASE_PULL, PHASE_COMPUTE, PHASE_REMOVE = 1, 2, 4
+INF_DIST = 0x7FFFFFFF
+
+
+class _StructParams(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_float), ("damping", ctypes.c_float), ("substeps", ctypes.c_int32)]
+
+
+def structure_run(mesh: dict, T: int, dt=0.05, damping=0.01, substeps=40, phases=7):
+    """mesh: the dict of ``inputs.structure_mesh`` (or any dict with its
+    keys).  Returns (state, counters[T, 5]); state holds the updated node
+    arrays x, y, vx, vy, slot, nspr, nalive, dist and spring arrays fx, fy,
+    salive (the constant arrays are not copied)."""
+    lib = _load()
+    N, S = len(mesh["kind"]), len(mesh["p1"])
+    f32 = lambda k: np.ascontiguousarray(mesh[k], dtype=np.float32).copy()
+    st = {k: f32(k) for k in ("x", "y", "vx", "vy")}
+    st["slot"] = np.ascontiguousarray(mesh["slot"], dtype=np.int32).reshape(N, 3).copy()
+    st["nspr"] = np.ascontiguousarray(mesh["nspr"], dtype=np.int32).copy()
+    st["nalive"] = np.ascontiguousarray(mesh.get("nalive", np.ones(N, np.uint8)), dtype=np.uint8).copy()
+    st["fx"] = np.ascontiguousarray(mesh.get("fx", np.zeros(S, np.float32)), dtype=np.float32).copy()
+    st["fy"] = np.ascontiguousarray(mesh.get("fy", np.zeros(S, np.float32)), dtype=np.float32).copy()
+    st["salive"] = np.ascontiguousarray(mesh.get("salive", np.ones(S, np.uint8)), dtype=np.uint8).copy()
+    st["dist"] = np.zeros(N, np.int32)
+    const = {k: np.ascontiguousarray(mesh[k], dtype=t) for k, t in
+             (("kind", np.int8), ("m", np.float32), ("p1", np.int32), ("p2", np.int32), ("k", np.float32),
+              ("L0", np.float32), ("fmax", np.float32))}
+    cnt = np.zeros((max(T, 1), 5), np.int64)
+    p = _StructParams(dt, damping, substeps)
+    rc = lib.orc_structure_run(N, S, ctypes.byref(p), _p(const["kind"]), _p(st["x"]), _p(st["y"]), _p(st["vx"]),
+                               _p(st["vy"]), _p(const["m"]), _p(st["slot"]), _p(st["nspr"]), _p(st["nalive"]),
+                               _p(const["p1"]), _p(const["p2"]), _p(const["k"]), _p(const["L0"]),
+                               _p(const["fmax"]), _p(st["fx"]), _p(st["fy"]), _p(st["salive"]), _p(st["dist"]),
+                               int(T), int(phases), _p(cnt))
+    if rc != 0:
+        raise ValueError("orc_structure_run: bad arguments")
+    return st, cnt[:T]

@@ -187,4 +187,33 @@ int orc_nbody_adjoint_f32traj(int N, float G, float eps, float dt, const float* 
 int orc_nbody_pair_adjoint_f64(int N, double G, double eps, const double* pos,
                                const double* m, const double* mu, double* g);
 
+/* ------------------------------------------------------------ structure */
+/* Spring mesh with cracks (Sec. 7.4); the arithmetic and order are given
+ * in structure.c.  Node kinds: */
+#define ORC_STRUCT_ANCHOR 0
+#define ORC_STRUCT_PULL 1
+#define ORC_STRUCT_NODE 2
+/* phases of one iteration (bit mask; 7 = all) */
+#define ORC_STRUCT_PHASE_PULL 1
+#define ORC_STRUCT_PHASE_COMPUTE 2
+#define ORC_STRUCT_PHASE_REMOVE 4
+typedef struct {
+  float dt, damping;
+  int32_t substeps;
+} orc_structure_params;
+/* Nodes 0..N-1: kind, position x/y, velocity vx/vy (constant for pull
+ * nodes), mass m, slot (3 N spring ids, -1 empty), nspr (springs held),
+ * nalive.  Springs 0..S-1: endpoints p1/p2, stiffness k, rest length L0,
+ * break limit fmax, force on p1 fx/fy, salive.  dist: distances of the
+ * last removal phase (INT32_MAX unreached).  Arrays are updated in place.
+ * counters (may be NULL): 5 x int64 per iteration: springs broken, nodes
+ * deleted by breaks, springs deleted by the removal, nodes deleted by the
+ * removal, BFS levels run. */
+int orc_structure_run(int N, int S, const orc_structure_params* p, const int8_t* kind,
+                      float* x, float* y, float* vx, float* vy, const float* m,
+                      int32_t* slot, int32_t* nspr, uint8_t* nalive, const int32_t* p1,
+                      const int32_t* p2, const float* k, const float* L0,
+                      const float* fmax, float* fx, float* fy, uint8_t* salive,
+                      int32_t* dist, int T, int phases, int64_t* counters);
+
 #endif

@@ -28,6 +28,17 @@ OpenStreetMap street networks -- are not available, these stand in for them):
 * Barnes-Hut (2-D): the x, y, vx, vy, m of the n-body recipe.
 * BFS: a grid of side x side vertices whose edges are kept with
   probability 0.71 each (draw(EDGE, 0, e)), both directions.
+* Structure (stand-in for the thesis' generated random mesh): a brick-wall
+  (hexagonal) lattice of rows x cols nodes, node v = r cols + c at
+  (c + jx, r + jy) with jitter (u - 0.5) 0.3 from draw(MESH, 0 / 1, v); a
+  spring to the right neighbour (candidate 2 v) and, when r + c is even, to
+  the node above (candidate 2 v + 1), each kept iff draw(MESH, 4, e) <
+  floor(keep 2^32) (a node that would keep none keeps its first
+  candidate); row 0 anchor nodes, the top row pull nodes moving up with
+  v_pull, ordinary nodes elsewhere (mass 1); per spring stiffness
+  0.5 + u and break limit f_lo + (f_hi - f_lo) u (draw(MESH, 2 / 3, e)),
+  times `grip` for a spring at an anchor or pull node (the clamps of a
+  tensile test), rest length the initial distance (float64, rounded once).
 * Batched: instance i is Life if draw(KIND, 0, i) & 1 else Wa-Tor, side
   floor(64 * 16^u) with u = draw(SIDE, 0, i) / 2^32 (log-uniform 64..1024).
 * Compaction (the thesis' synthetic defragmentation benchmark, Sec. 6.4):
@@ -43,7 +54,7 @@ import numpy as np
 
 TAG_INIT, TAG_FISH, TAG_SHARK, TAG_LEN, TAG_PLACE, TAG_ROUTE, TAG_BRAKE = 0, 1, 2, 3, 4, 5, 6
 TAG_KIND, TAG_SIDE, TAG_OUTDEG, TAG_OUT, TAG_NBODY = 7, 8, 9, 10, 11
-TAG_KILL, TAG_AREF, TAG_BREF, TAG_CTRL, TAG_EDGE = 12, 13, 14, 15, 16
+TAG_KILL, TAG_AREF, TAG_BREF, TAG_CTRL, TAG_EDGE, TAG_MESH = 12, 13, 14, 15, 16, 17
 
 _M0, _M1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
 _W0, _W1 = np.uint32(0x9E3779B9), np.uint32(0xBB67AE85)
@@ -231,3 +242,64 @@ def compact_synthetic(n: int, seed: int, kill=(3, 5)):
     a_ref = (draw(seed, TAG_AREF, 0, i) % np.uint32(n)).astype(np.int64)
     b_ref = (draw(seed, TAG_BREF, 0, i) % np.uint32(n)).astype(np.int64)
     return dead, a_ref, b_ref
+
+
+# -------------------------------------------------------------- structure
+MESH_ANCHOR, MESH_PULL, MESH_NODE = 0, 1, 2
+
+
+def structure_mesh(rows: int, cols: int, seed: int, keep=(9, 10), v_pull: float = 0.5,
+                   f_lo: float = 0.005, f_hi: float = 0.05, grip: float = 10.0):
+    """Node arrays (kind, x, y, vx, vy, m, slot[N, 3], nspr) and spring
+    arrays (p1, p2, k, L0, fmax) of the brick-wall mesh; spring ids follow
+    the candidate order, a node's slots hold its springs in increasing id."""
+    N = rows * cols
+    v = np.arange(N, dtype=np.int64)
+    r, c = v // cols, v % cols
+    u = lambda step, idx: draw(seed, TAG_MESH, step, idx.astype(np.uint32)).astype(np.float64) / 2.0 ** 32
+    x = (c + (u(0, v) - 0.5) * 0.3).astype(np.float32)
+    y = (r + (u(1, v) - 0.5) * 0.3).astype(np.float32)
+    kind = np.full(N, MESH_NODE, np.int8)
+    kind[r == 0] = MESH_ANCHOR
+    kind[(r == rows - 1) & (rows > 1)] = MESH_PULL
+    vx = np.zeros(N, np.float32)
+    vy = np.where(kind == MESH_PULL, np.float32(v_pull), np.float32(0)).astype(np.float32)
+    # candidates: e = 2 v (right), 2 v + 1 (up, when r + c is even)
+    e = np.arange(2 * N, dtype=np.int64)
+    a = e // 2
+    ra, ca = a // cols, a % cols
+    up = (e & 1) == 1
+    exists = np.where(up, (ra + 1 < rows) & ((ra + ca) % 2 == 0), ca + 1 < cols)
+    b = np.where(up, a + cols, a + 1)
+    kept = exists & (draw(seed, TAG_MESH, 4, e.astype(np.uint32)).astype(np.uint64) < np.uint64(threshold(*keep)))
+    # a node left without springs keeps its first existing candidate
+    deg = np.zeros(N, np.int64)
+    np.add.at(deg, a[kept], 1)
+    np.add.at(deg, b[kept], 1)
+    for node in np.nonzero(deg == 0)[0]:
+        inc = np.nonzero(exists & ((a == node) | (b == node)))[0]
+        if len(inc):
+            kept[inc[0]] = True
+    ids = np.nonzero(kept)[0]
+    p1, p2 = a[ids].astype(np.int32), b[ids].astype(np.int32)
+    S = len(ids)
+    dx = x[p2].astype(np.float64) - x[p1].astype(np.float64)
+    dy = y[p2].astype(np.float64) - y[p1].astype(np.float64)
+    L0 = np.hypot(dx, dy).astype(np.float32)
+    k = (0.5 + u(2, ids)).astype(np.float32)
+    fmax = f_lo + (f_hi - f_lo) * u(3, ids)
+    fmax = np.where((kind[p1] != MESH_NODE) | (kind[p2] != MESH_NODE), fmax * grip, fmax).astype(np.float32)
+    # slots: springs of each node in increasing id
+    ends = np.concatenate([p1, p2]).astype(np.int64)
+    sid = np.concatenate([np.arange(S), np.arange(S)]).astype(np.int64)
+    order = np.lexsort((sid, ends))
+    ends, sid = ends[order], sid[order]
+    nspr = np.bincount(ends, minlength=N).astype(np.int32)
+    if nspr.max(initial=0) > 3:
+        raise AssertionError("mesh degree above 3")
+    start = np.concatenate([[0], np.cumsum(nspr)[:-1]])
+    pos = np.arange(len(ends)) - start[ends]
+    slot = np.full((N, 3), -1, np.int32)
+    slot[ends, pos] = sid
+    return dict(kind=kind, x=x, y=y, vx=vx, vy=vy, m=np.ones(N, np.float32), slot=slot, nspr=nspr,
+                p1=p1, p2=p2, k=k, L0=L0, fmax=fmax, rows=rows, cols=cols)
