@@ -680,6 +680,99 @@ def run_bfs(args):
     return 0 if np.array_equal(d, want) else 1
 
 
+def run_structure(args):
+    """The spring mesh of Sec. 7.4 (a tensile test of a composite: anchor
+    nodes along the bottom row, pull nodes along the top row) on a
+    256 x 8192 brick-wall mesh (2,097,152 nodes, about 2.8 M springs):
+    iterations of pull, 40 compute steps (Spring::compute_force with
+    breaking, Node::update) and the BFS removal of parts cut off from the
+    anchors.  Timed: `struct_iters` iterations, plain and with compaction of
+    Spring and Node (n = 10) every 50 iterations (the thesis' CompactGpu
+    setting for this application); the removal alone on the final state.
+    Parity: 3 iterations against the oracle at full size."""
+    import torch
+    import oracle
+    from paper_1908_05845_gb300 import inputs
+    from paper_1908_05845_gb300.workloads import Structure
+    rows, cols, T = 256, 8192, args.struct_iters
+    g = inputs.structure_mesh(rows, cols, SEED)
+    stream = torch.cuda.Stream()
+    a, b = _events(stream)
+    out = {}
+    for label, every in (("plain", 0), ("compact_every_50", 50)):
+        with torch.cuda.stream(stream):
+            sim = Structure(g, stream=stream)
+            sim.step(args.warmup)
+            e0, a0, f0 = sim.heap.counters()
+            c0 = sim.counters()
+            ids = sim.class_ids
+            t_compact, done = 0.0, 0
+            torch.cuda.synchronize()
+            a.record(stream)
+            while done < T:
+                k = min(T - done, every) if every else T
+                sim.step(k)
+                done += k
+                if every and done % every == 0 and done < T:
+                    for cname in ("Spring", "Node"):
+                        cs = sim.heap.compact(ids[cname], 10, 0)
+                        t_compact += cs["scan_ms"] + cs["copy_ms"] + cs["state_ms"] + cs["rewrite_ms"]
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b)
+            e1, a1, f1 = sim.heap.counters()
+            c1 = sim.counters()
+            st = sim.heap.stats()
+            # the removal phase alone on the final state
+            torch.cuda.synchronize()
+            a.record(stream)
+            sim.step(5, 4)
+            b.record(stream)
+            b.synchronize()
+            ms_remove = a.elapsed_time(b) / 5
+            assert sim.heap.check() == 0
+            sim.sync()
+            sim.close()
+        out[label] = {"ms_per_iteration": ms / T, "object_updates_per_s": (e1 - e0) / (ms / 1e3),
+                      "removal_ms_per_iteration": ms_remove, "compaction_ms_total": t_compact,
+                      "springs_broken": c1["broken"] - c0["broken"],
+                      "nodes_deleted": c1["nodes_deleted"] - c0["nodes_deleted"],
+                      "frees_per_s": (f1 - f0) / (ms / 1e3),
+                      "bfs_levels_per_iteration": (c1["bfs_levels"] - c0["bfs_levels"]) / T,
+                      "node_blocks_end": st["blocks"][ids["Node"]],
+                      "spring_blocks_end": st["blocks"][ids["Spring"]],
+                      "fragmentation_node_end": st["fragmentation"][ids["Node"]],
+                      "fragmentation_spring_end": st["fragmentation"][ids["Spring"]]}
+    # parity at full size: 3 iterations
+    with torch.cuda.stream(stream):
+        chk = Structure(g, stream=stream)
+        chk.step(3)
+        got = chk.read()
+        chk.close()
+    t0 = time.time()
+    want, oc = oracle.structure_run(g, 3)
+    cpu_s = time.time() - t0
+    alive = want["nalive"].astype(bool)
+    exact = bool(np.array_equal(got["nalive"].astype(bool), alive)
+                 and np.array_equal(got["salive"].astype(bool), want["salive"].astype(bool))
+                 and all(np.array_equal(got[k][alive], want[k][alive]) for k in ("x", "y", "nspr", "dist", "slot")))
+    n_obj = len(g["kind"]) + len(g["p1"])
+    p, c = out["plain"], out["compact_every_50"]
+    # oracle object-updates: per iteration every spring and node twice per
+    # compute step plus one node visit per BFS level
+    ou = 3 * (2 * 40 * n_obj) + int(oc[:, 4].sum()) * len(g["kind"])
+    print(json.dumps({"metric": "object-updates/s", "value": p["object_updates_per_s"], "unit": "object-updates/s",
+                      "ms_per_step": p["ms_per_iteration"], "steps": T, "higher_is_better": True, "dtype": "f32",
+                      "data": "synthetic (seeded Philox)",
+                      "config": {"workload": "structure_%dx%d" % (rows, cols), "nodes": len(g["kind"]),
+                                 "springs": len(g["p1"]), "substeps": 40, "dt": 0.05, "damping": 0.01},
+                      "runs": out, "compaction_speedup": p["ms_per_iteration"] / c["ms_per_iteration"],
+                      "parity_3_iterations_bit_exact": exact,
+                      "cpu_baseline": {"value": ou / cpu_s, "unit": "object-updates/s", "cores": 1,
+                                       "kind": "oracle", "sample": "3 iterations (%.1f s)" % cpu_s}}), flush=True)
+    return 0 if exact else 1
+
+
 def run_nasch(args):
     import torch
     from paper_1908_05845_gb300 import inputs
@@ -894,8 +987,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="wator",
                     choices=["wator", "batched", "gol", "generation", "nasch", "nbody", "bh", "bfs", "alloc",
-                             "compact"])
+                             "compact", "structure"])
     ap.add_argument("--bfs-check", type=int, default=32)
+    ap.add_argument("--struct-iters", type=int, default=100)
     ap.add_argument("--bh-bodies", type=int, default=65536)
     ap.add_argument("--gen-steps", type=int, default=500)
     ap.add_argument("--compact-objects", type=int, default=32_768_000)
@@ -913,7 +1007,7 @@ def main():
         from paper_1908_05845_gb300 import smmo
         smmo.lib()
         return {"batched": run_batched, "gol": run_gol, "generation": run_generation, "nasch": run_nasch,
-                "nbody": run_nbody, "bh": run_bh, "bfs": run_bfs,
+                "nbody": run_nbody, "bh": run_bh, "bfs": run_bfs, "structure": run_structure,
                 "alloc": run_alloc, "compact": run_compact}[args.workload](args)
     return run_gpu(args, ws, rank, local)
 

@@ -562,6 +562,71 @@ int smmo_bfs_run(smmo_bfs* w, int32_t source, int check_every, int32_t* levels,
 int smmo_bfs_export(smmo_bfs* w, int32_t* dist, void* stream);
 int smmo_bfs_destroy(smmo_bfs* w);
 
+/* ============================================================= structure
+ * A spring mesh that cracks under load (the finite-element application of
+ * Sec. 7.4).  Classes NodeBase (abstract) {x, y, springs[3] (an inlined
+ * inner array of Spring handles), num_springs, distance, id}, AnchorNode
+ * (fixed), AnchorPullNode {vx, vy} (constant velocity), Node {vx, vy, m},
+ * Spring {p1, p2, k, L0, fmax, fx, fy, flag, id}.  One iteration: pull
+ * (x += v dt for every AnchorPullNode); `substeps` times
+ * Spring::compute_force (d = p2 - p1, F = k (|d| - L0) when |d| > L0 else
+ * 0; F > fmax breaks the spring: it leaves both endpoints, a node left
+ * without springs is deleted, and it deletes itself; otherwise f = F d/|d|
+ * acts on p1 and -f on p2) and Node::update (v = (v + (sum of f in slot
+ * order) / m dt)(1 - damping), x += v dt); then the removal of every node
+ * that no longer reaches an AnchorNode through springs: a frontier BFS from
+ * the AnchorNodes (one parallel_do_and_reduce per level over all node
+ * classes in one launch), then the springs of unreached nodes are removed
+ * as above.  FP32 in that order, equal to the CPU oracle bit for bit. */
+#define SMMO_STRUCT_ANCHOR 0
+#define SMMO_STRUCT_PULL 1
+#define SMMO_STRUCT_NODE 2
+#define SMMO_STRUCT_PHASE_PULL 1
+#define SMMO_STRUCT_PHASE_COMPUTE 2
+#define SMMO_STRUCT_PHASE_REMOVE 4
+typedef struct {
+  float dt, damping;
+  int32_t substeps;         /* compute steps per iteration (>= 0)      */
+  int32_t bfs_check_every;  /* BFS levels per read-back (1..4096)      */
+} smmo_structure_params;
+typedef struct smmo_structure smmo_structure;
+/* Creates the mesh in a fresh heap (else SMMO_E_FROZEN).  Host arrays.
+ * Nodes (n): kind (SMMO_STRUCT_*), node_cols = {x, y, vx, vy, m} (vx, vy
+ * of anchor nodes and m of non-Node kinds are ignored), slot (3 n spring
+ * ids, -1 = empty).  Springs (ns): p1, p2 (node ids), spring_cols = {k,
+ * L0, fmax}.  Node i gets id i, spring j id j.  SMMO_E_INVALID_ARG unless
+ * every node's slots list exactly the springs that name it.  Synchronises
+ * `stream`. */
+int smmo_structure_create(smmo_heap* heap, int64_t n, const int8_t* kind,
+                          const float* const* node_cols, const int32_t* slot,
+                          int64_t ns, const int32_t* p1, const int32_t* p2,
+                          const float* const* spring_cols,
+                          const smmo_structure_params* p, void* stream,
+                          smmo_structure** out);
+/* `iterations` iterations of the phases in the bit mask `phases`
+ * (SMMO_STRUCT_PHASE_*; 7 = all, in the order pull, compute, remove).  The
+ * removal reads back one flag batch per bfs_check_every levels. */
+int smmo_structure_step(smmo_structure* w, int iterations, int phases, void* stream);
+/* Device output arrays by id (each nullable): nodes (n) node_alive (0/1),
+ * x, y, vx, vy (0 for anchors), num_springs, distance (of the last
+ * removal; 2^31 - 1 = unreached), slot (3 n spring ids, -1 = empty);
+ * springs (ns) spring_alive, fx, fy.  Values of deleted objects are left
+ * untouched.  Synchronises `stream`. */
+typedef struct {
+  uint8_t* node_alive;
+  float *x, *y, *vx, *vy;
+  int32_t *num_springs, *distance, *slot;
+  uint8_t* spring_alive;
+  float *fx, *fy;
+} smmo_structure_out;
+int smmo_structure_export(smmo_structure* w, const smmo_structure_out* out, void* stream);
+/* class ids [NodeBase, AnchorNode, AnchorPullNode, Node, Spring] (host, 5,
+ * nullable); counters (host, 5, nullable): springs broken, nodes deleted
+ * (by breaks and removals), springs removed by the removal phase, BFS
+ * levels run, BFS level launches.  Synchronises `stream` if counters. */
+int smmo_structure_info(smmo_structure* w, int* class_ids, int64_t* counters, void* stream);
+int smmo_structure_destroy(smmo_structure* w);
+
 /* Self-test of the branch-free, correctly rounded FP32 square root and
  * reciprocal that the force kernel uses when every coordinate is within
  * 2^18 and eps^2 is in [2^-40, 2^38] (otherwise it uses the IEEE-rounded

@@ -264,7 +264,7 @@ __device__ __forceinline__ bool was_source(const HeapView& h, const unsigned lon
 }
 
 __global__ void __launch_bounds__(256) k_rewrite(HeapView h, uint32_t u_cls, RewriteArgs a) {
-  const uint32_t n = __ldcg(&h.st->rcount);
+  const uint32_t n = __ldcg(h.rcnt);
   const uint32_t cap = h.cls[u_cls].cap;
   const uint32_t halves = cap > 32 ? 2u : 1u, units = n * halves;
   const uint32_t lane = threadIdx.x & 31;

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) k_enumerate(HeapView h, int c) {
     if (word == 0) continue;
     const uint32_t lo = (uint32_t)word, hi = (uint32_t)(word >> 32);
     uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&h.st->rcount, (uint32_t)__popcll(word));
+    if (lane == 0) base = atomicAdd(h.rcnt, (uint32_t)__popcll(word));
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
     unsigned long long b0 = 0, b1 = 0;
     if ((lo >> lane) & 1) b0 = __ldcg(h.alloc_bm + w * 64 + lane) & capmask;
@@ -192,7 +192,7 @@ __global__ void k_bulk_copy(HeapView h, uint32_t c, const uint32_t* list, uint64
 
 // Expands the enumerated blocks into object handles.
 __global__ void k_expand(HeapView h, uint32_t* out, uint64_t cap_out, unsigned long long* total) {
-  const uint32_t n = h.st->rcount;
+  const uint32_t n = *h.rcnt;
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps) {
@@ -315,15 +315,60 @@ __global__ void k_check_blocks(HeapView h) {
 // =========================================================== host helpers
 namespace smmo {
 
-static int launch_enumerate(smmo_heap* h, int c, cudaStream_t s) {
-  cudaMemsetAsync(&h->view.st->rcount, 0, sizeof(uint32_t), s);
-  uint32_t grid = (h->view.level_words[0] + 7) / 8;  // one warp per container
+static int launch_enumerate(smmo_heap* h, const HeapView& v, int c, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(v.rcnt, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return cuda_status(e);
+  uint32_t grid = (v.level_words[0] + 7) / 8;  // one warp per container
   grid = std::max(1u, std::min(grid, (uint32_t)h->num_sms * 8));
-  k_enumerate<<<grid, 256, 0, s>>>(h->view, c);
+  k_enumerate<<<grid, 256, 0, s>>>(v, c);
   return cuda_status(cudaGetLastError());
 }
 
-int enumerate(smmo_heap* h, int c, cudaStream_t s) { return launch_enumerate(h, c, s); }
+int enumerate(smmo_heap* h, int c, cudaStream_t s) { return launch_enumerate(h, h->view, c, s); }
+
+static int snapshot_alloc(smmo_heap* h, Snapshot* sn) {
+  if (sn->buf) return SMMO_OK;
+  // M entries and the count, in one allocation
+  const size_t bytes = (size_t)h->view.num_blocks * sizeof(REntry) + 16;
+  cudaError_t e = cudaMalloc(&sn->buf, bytes);
+  if (e != cudaSuccess) { sn->buf = nullptr; return cuda_status(e); }
+  sn->view = h->view;
+  sn->view.R = reinterpret_cast<REntry*>(sn->buf);
+  sn->view.rcnt = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(sn->buf) +
+                                              (size_t)h->view.num_blocks * sizeof(REntry));
+  return SMMO_OK;
+}
+
+int Snapshot::take_subtree(smmo_heap* h, int c, cudaStream_t s) {
+  if (!h->frozen) return SMMO_E_FROZEN;
+  int st = snapshot_alloc(h, this);
+  if (st) return st;
+  cls = c;
+  std::vector<int> cs;
+  concrete_subtree(h, c, &cs);
+  for (int k : cs)
+    if (h->classes[k].layout.cap > 64) return SMMO_E_UNSUPPORTED;
+  // the count is reset once: each class's blocks are appended
+  cudaError_t e = cudaMemsetAsync(view.rcnt, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return cuda_status(e);
+  uint32_t grid = (view.level_words[0] + 7) / 8;
+  grid = std::max(1u, std::min(grid, (uint32_t)h->num_sms * 8));
+  for (int k : cs) k_enumerate<<<grid, 256, 0, s>>>(view, k);
+  return cuda_status(cudaGetLastError());
+}
+
+int Snapshot::take(smmo_heap* h, int c, cudaStream_t s) {
+  if (!h->frozen) return SMMO_E_FROZEN;
+  int st = snapshot_alloc(h, this);
+  if (st) return st;
+  cls = c;
+  return launch_enumerate(h, view, c, s);
+}
+
+void Snapshot::release() {
+  if (buf) cudaFree(buf);
+  buf = nullptr;
+}
 
 // Enumeration scratch: one REntry per block, and at least room for the
 // compaction scan's per-word offsets and per-chunk totals (level-0 words
@@ -421,6 +466,7 @@ int freeze(smmo_heap* h, cudaStream_t s) {
   v.alloc_bm = (unsigned long long*)take(M * 8);
   v.block_type = (uint32_t*)take(M * 4);
   v.R = (REntry*)take(rscratch_bytes(M));
+  v.rcnt = &v.st->rcount;
   h->d_scratch = (uint32_t*)take(M * 4 + 1024);
   h->d_moved = (unsigned long long*)take((M + 63) / 64 * 8);
   v.bitmaps = (unsigned long long*)take(bw * 8 * nbm);
@@ -470,7 +516,8 @@ const Table kTables[] = {{g_methods_test, &g_methods_test_n},
                          {g_methods_nasch, &g_methods_nasch_n},
                          {g_methods_nbody, &g_methods_nbody_n},
                          {g_methods_bh, &g_methods_bh_n},
-                         {g_methods_bfs, &g_methods_bfs_n}};
+                         {g_methods_bfs, &g_methods_bfs_n},
+                         {g_methods_structure, &g_methods_structure_n}};
 }  // namespace
 
 const smmo::MethodEntry* smmo::method_by_id(int id) {

@@ -43,6 +43,20 @@ int freeze(smmo_heap* h, cudaStream_t s);
 void concrete_subtree(const smmo_heap* h, int c, std::vector<int>* out);
 // enumerate class c into h->view.R, count into st->rcount (asynchronous)
 int enumerate(smmo_heap* h, int c, cudaStream_t s);
+// A saved enumeration of one class with its own entry buffer and count, so
+// that several classes' snapshots can be reused by later do-alls (valid
+// while no object of the class is created or deleted).  `view` is the
+// heap's view with R and rcnt pointing at the snapshot.
+struct Snapshot {
+  void* buf = nullptr;  // M entries + the count (device)
+  HeapView view{};
+  int cls = -1;
+  int take(smmo_heap* h, int c, cudaStream_t s);  // (re-)enumerate class c
+  // the concrete classes of c's subtree one after the other (for a POLY
+  // do-all: each unit takes its class from the block's type id)
+  int take_subtree(smmo_heap* h, int c, cudaStream_t s);
+  void release();
+};
 // level l of hierarchical bitmap k (device pointer computed on the host)
 inline unsigned long long* bm_level_host(const smmo_heap* h, int k, int l = 0) {
   return h->view.bitmaps + (size_t)k * h->view.bm_words + h->view.level_off[l];
@@ -80,43 +94,54 @@ extern const smmo::MethodEntry g_methods_bh[];
 extern const int g_methods_bh_n;
 extern const smmo::MethodEntry g_methods_bfs[];
 extern const int g_methods_bfs_n;
+extern const smmo::MethodEntry g_methods_structure[];
+extern const int g_methods_structure_n;
 
 #ifdef __CUDACC__
 // Instantiates the do-all kernel for method M (see smmo_core.cuh).
 // The persistent grid holds as many CTAs as can be resident at once
 // (occupancy of this instantiation at the configured CTA size, capped by
 // ctas_per_sm), so no CTA waits for another to finish before it starts.
-template <class M>
-int launch_do_all(smmo_heap* h, int cls, const void* args, cudaStream_t s) {
+template <class M, bool POLY = false>
+int launch_do_all_view(smmo_heap* h, int cls, const void* args, cudaStream_t s, const smmo::HeapView* v) {
   const typename M::Args* a = static_cast<const typename M::Args*>(args);
   static int occ_threads = 0, occ_blocks = 0;
   if (occ_threads != h->cfg.threads_per_cta) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, smmo::do_all_kernel<M>, h->cfg.threads_per_cta, 0) != cudaSuccess || nb < 1) nb = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, smmo::do_all_kernel<M, POLY>, h->cfg.threads_per_cta, 0) != cudaSuccess || nb < 1) nb = 1;
     occ_blocks = nb;
     occ_threads = h->cfg.threads_per_cta;
   }
   const int per_sm = occ_blocks < h->cfg.ctas_per_sm ? occ_blocks : h->cfg.ctas_per_sm;
-  smmo::do_all_kernel<M><<<h->num_sms * per_sm, h->cfg.threads_per_cta, 0, s>>>(h->view, cls, *a);
+  smmo::do_all_kernel<M, POLY><<<h->num_sms * per_sm, h->cfg.threads_per_cta, 0, s>>>(v ? *v : h->view, cls, *a);
   return smmo::cuda_status(cudaGetLastError());
+}
+template <class M>
+int launch_do_all(smmo_heap* h, int cls, const void* args, cudaStream_t s) {
+  return launch_do_all_view<M>(h, cls, args, s, nullptr);
 }
 #define SMMO_METHOD(name, M) {name, sizeof(typename M::Args), &launch_do_all<M>, nullptr}
 
-template <class M>
-int launch_do_all_reduce(smmo_heap* h, int cls, const void* args, int op, long long* out, cudaStream_t s) {
+template <class M, bool POLY = false>
+int launch_do_all_reduce_view(smmo_heap* h, int cls, const void* args, int op, long long* out, cudaStream_t s,
+                              const smmo::HeapView* v) {
   const typename M::Args* a = static_cast<const typename M::Args*>(args);
   static int occ_threads = 0, occ_blocks = 0;
   if (occ_threads != h->cfg.threads_per_cta) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, smmo::do_all_reduce_kernel<M>, h->cfg.threads_per_cta, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, smmo::do_all_reduce_kernel<M, POLY>, h->cfg.threads_per_cta, 0) !=
             cudaSuccess || nb < 1)
       nb = 1;
     occ_blocks = nb;
     occ_threads = h->cfg.threads_per_cta;
   }
   const int per_sm = occ_blocks < h->cfg.ctas_per_sm ? occ_blocks : h->cfg.ctas_per_sm;
-  smmo::do_all_reduce_kernel<M><<<h->num_sms * per_sm, h->cfg.threads_per_cta, 0, s>>>(h->view, cls, *a, op, out);
+  smmo::do_all_reduce_kernel<M, POLY><<<h->num_sms * per_sm, h->cfg.threads_per_cta, 0, s>>>(v ? *v : h->view, cls, *a, op, out);
   return smmo::cuda_status(cudaGetLastError());
+}
+template <class M>
+int launch_do_all_reduce(smmo_heap* h, int cls, const void* args, int op, long long* out, cudaStream_t s) {
+  return launch_do_all_reduce_view<M>(h, cls, args, op, out, s, nullptr);
 }
 #define SMMO_METHOD_REDUCE(name, M) {name, sizeof(typename M::Args), nullptr, &launch_do_all_reduce<M>}
 #endif

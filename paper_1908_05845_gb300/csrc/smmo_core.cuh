@@ -83,6 +83,7 @@ struct HeapView {
   DeviceState* st;
   const ClassLayout* cls;             // per-class layouts (device)
   REntry* R;                          // enumeration scratch
+  uint32_t* rcnt;                     // its entry count (the heap's, or a saved snapshot's)
   uint32_t block_bytes;
   uint32_t num_blocks;
   uint32_t bm_words;                  // words of one hierarchical bitmap
@@ -552,12 +553,15 @@ __device__ __forceinline__ uint32_t smmo_new(const HeapView& h, uint32_t c) {
 // warp takes one contiguous run of units (rather than every nwarps-th), so
 // that consecutive units of a warp are neighbouring blocks and the warp's
 // allocation cache, refilled near the current block, keeps new objects close
-// to their creators.
-template <class M>
+// to their creators.  With POLY the enumeration holds blocks of several
+// classes (the concrete subclasses of one class, enumerated one after the
+// other into one snapshot): every unit reads its block's class from the
+// type id and passes it to the method, and every block counts as two units.
+template <class M, bool POLY = false>
 __global__ void __launch_bounds__(512, 3) do_all_kernel(HeapView h, uint32_t c,
                                                      typename M::Args args) {
-  const uint32_t n = __ldcg(&h.st->rcount);
-  const uint32_t cap = __ldg(&h.cls[c].cap);
+  const uint32_t n = __ldcg(h.rcnt);
+  const uint32_t cap = POLY ? 64u : __ldg(&h.cls[c].cap);
   const uint32_t halves = cap > 32 ? 2u : 1u;
   const uint32_t units = n * halves;
   const uint32_t lane = threadIdx.x & 31;
@@ -573,7 +577,7 @@ __global__ void __launch_bounds__(512, 3) do_all_kernel(HeapView h, uint32_t c,
     const REntry e = h.R[i];
     g_wcache[threadIdx.x >> 5].hint = e.block;
     if (lane == 0) visited += __popcll(halves == 2 ? (e.bits >> ((u & 1) * 32)) & 0xFFFFFFFFull : e.bits);
-    if ((e.bits >> slot) & 1) M::run(h, args, c, (e.block << 6) | slot);
+    if ((e.bits >> slot) & 1) M::run(h, args, POLY ? __ldg(&h.block_type[e.block]) : c, (e.block << 6) | slot);
     __syncwarp();  // reconverge: lane groups never run different iterations
   }
   if (lane == 0 && visited) count(h, SMMO_CTR_VISIT, visited);
@@ -607,12 +611,12 @@ __device__ __forceinline__ long long reduce2(int op, long long x, long long y) {
   }
 }
 
-template <class M>
+template <class M, bool POLY = false>
 __global__ void __launch_bounds__(512, 3) do_all_reduce_kernel(HeapView h, uint32_t c, typename M::Args args,
                                                                int op, long long* out) {
   __shared__ long long part[16];
-  const uint32_t n = __ldcg(&h.st->rcount);
-  const uint32_t cap = __ldg(&h.cls[c].cap);
+  const uint32_t n = __ldcg(h.rcnt);
+  const uint32_t cap = POLY ? 64u : __ldg(&h.cls[c].cap);
   const uint32_t halves = cap > 32 ? 2u : 1u;
   const uint32_t units = n * halves;
   const uint32_t lane = threadIdx.x & 31;
@@ -629,7 +633,8 @@ __global__ void __launch_bounds__(512, 3) do_all_reduce_kernel(HeapView h, uint3
     const REntry e = h.R[i];
     g_wcache[threadIdx.x >> 5].hint = e.block;
     if (lane == 0) visited += __popcll(halves == 2 ? (e.bits >> ((u & 1) * 32)) & 0xFFFFFFFFull : e.bits);
-    if ((e.bits >> slot) & 1) acc = reduce2(op, acc, M::run(h, args, c, (e.block << 6) | slot));
+    if ((e.bits >> slot) & 1)
+      acc = reduce2(op, acc, M::run(h, args, POLY ? __ldg(&h.block_type[e.block]) : c, (e.block << 6) | slot));
     __syncwarp();
   }
   if (lane == 0 && visited) count(h, SMMO_CTR_VISIT, visited);

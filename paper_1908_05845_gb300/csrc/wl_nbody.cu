@@ -136,7 +136,7 @@ __device__ __forceinline__ unsigned abs_max_bits(float x, float y, float z) {
 __global__ void __launch_bounds__(256) k_force(HeapView hv, uint32_t c, NBodyArgs a) {
   __shared__ float4 tile[NB_TILE];
   __shared__ unsigned tile_max[NB_TILE / 32];
-  const uint32_t n = __ldcg(&hv.st->rcount);
+  const uint32_t n = __ldcg(hv.rcnt);
   const uint32_t cap = hv.cls[c].cap;
   const uint32_t halves = cap > 32 ? 2u : 1u;
   const uint32_t units = n * halves, groups = (units + 7) / 8;
@@ -406,7 +406,7 @@ struct AdjW {
 __global__ void __launch_bounds__(256, 7) k_adjoint_pair(HeapView hv, uint32_t c, NBodyArgs a) {
   __shared__ float4 tx[NB_TILE];
   __shared__ float4 tm[NB_TILE];
-  const uint32_t n = __ldcg(&hv.st->rcount);
+  const uint32_t n = __ldcg(hv.rcnt);
   const uint32_t cap = hv.cls[c].cap;
   const uint32_t halves = cap > 32 ? 2u : 1u;
   const uint32_t units = n * halves, pairs = (units + 1) / 2;

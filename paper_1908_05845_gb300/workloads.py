@@ -422,3 +422,98 @@ class Bfs:
             self.close()
         except Exception:
             pass
+
+
+class StructureParams(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_float), ("damping", ctypes.c_float), ("substeps", ctypes.c_int32),
+                ("bfs_check_every", ctypes.c_int32)]
+
+
+class _StructureOut(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("node_alive", "x", "y", "vx", "vy", "num_springs", "distance",
+                                               "slot", "spring_alive", "fx", "fy")]
+
+
+STRUCT_PHASE_PULL, STRUCT_PHASE_COMPUTE, STRUCT_PHASE_REMOVE = 1, 2, 4
+
+
+class Structure:
+    """The spring mesh that cracks under load (thesis Sec. 7.4) on one heap.
+    mesh: the dict of ``inputs.structure_mesh`` (host arrays kind, x, y, vx,
+    vy, m, slot[N, 3], p1, p2, k, L0, fmax)."""
+
+    NAMES = ["NodeBase", "AnchorNode", "AnchorPullNode", "Node", "Spring"]
+
+    def __init__(self, mesh: dict, dt: float = 0.05, damping: float = 0.01, substeps: int = 40,
+                 bfs_check_every: int = 32, heap_bytes: int | None = None,
+                 config: smmo.HeapConfig | None = None, stream=None):
+        self.stream = stream
+        self.n, self.ns = len(mesh["kind"]), len(mesh["p1"])
+        host = lambda k, t: np.ascontiguousarray(mesh[k], dtype=t)
+        self._keep = [host("kind", np.int8), host("slot", np.int32).reshape(-1), host("p1", np.int32),
+                      host("p2", np.int32)]
+        ncols = [host(k, np.float32) for k in ("x", "y", "vx", "vy", "m")]
+        scols = [host(k, np.float32) for k in ("k", "L0", "fmax")]
+        nptr = (ctypes.c_void_p * 5)(*[c.ctypes.data for c in ncols])
+        sptr = (ctypes.c_void_p * 3)(*[c.ctypes.data for c in scols])
+        # 64-slot blocks of 2,816 data bytes, for nodes and springs
+        self.heap = smmo.Heap(heap_bytes or int((self.n + self.ns) * 48 * 1.25) + (64 << 20), config,
+                              stream=stream)
+        self._w = ctypes.c_void_p()
+        p = StructureParams(dt, damping, substeps, bfs_check_every)
+        kind, slot, p1, p2 = self._keep
+        smmo.check(smmo.lib().smmo_structure_create(
+            self.heap.handle, ctypes.c_int64(self.n), ctypes.c_void_p(kind.ctypes.data), nptr,
+            ctypes.c_void_p(slot.ctypes.data), ctypes.c_int64(self.ns), ctypes.c_void_p(p1.ctypes.data),
+            ctypes.c_void_p(p2.ctypes.data), sptr, ctypes.byref(p), smmo._stream(stream),
+            ctypes.byref(self._w)), "structure_create")
+        ids = (ctypes.c_int * 5)()
+        smmo.check(smmo.lib().smmo_structure_info(self._w, ids, None, None), "structure_info")
+        self.class_ids = dict(zip(self.NAMES, list(ids)))
+
+    def step(self, iterations: int = 1, phases: int = 7):
+        smmo.check(smmo.lib().smmo_structure_step(self._w, int(iterations), int(phases),
+                                                  smmo._stream(self.stream)), "structure_step")
+
+    def read(self) -> dict:
+        """Node and spring arrays by id (host): nalive, x, y, vx, vy, nspr,
+        dist, slot[N, 3]; salive, fx, fy.  Deleted objects read 0."""
+        dev = dict(nalive=torch.zeros(self.n, dtype=torch.uint8, device="cuda"),
+                   **{k: torch.zeros(self.n, dtype=torch.float32, device="cuda") for k in ("x", "y", "vx", "vy")},
+                   nspr=torch.zeros(self.n, dtype=torch.int32, device="cuda"),
+                   dist=torch.zeros(self.n, dtype=torch.int32, device="cuda"),
+                   slot=torch.full((self.n, 3), -1, dtype=torch.int32, device="cuda"),
+                   salive=torch.zeros(max(self.ns, 1), dtype=torch.uint8, device="cuda"),
+                   fx=torch.zeros(max(self.ns, 1), dtype=torch.float32, device="cuda"),
+                   fy=torch.zeros(max(self.ns, 1), dtype=torch.float32, device="cuda"))
+        ptr = lambda k: dev[k].data_ptr()
+        o = _StructureOut(ptr("nalive"), ptr("x"), ptr("y"), ptr("vx"), ptr("vy"), ptr("nspr"), ptr("dist"),
+                          ptr("slot"), ptr("salive"), ptr("fx"), ptr("fy"))
+        smmo.check(smmo.lib().smmo_structure_export(self._w, ctypes.byref(o), smmo._stream(self.stream)),
+                   "structure_export")
+        out = {k: v.cpu().numpy() for k, v in dev.items()}
+        for k in ("salive", "fx", "fy"):
+            out[k] = out[k][:self.ns]
+        return out
+
+    def counters(self) -> dict:
+        """springs broken, nodes deleted, springs removed by the removal
+        phase, BFS levels run, BFS level launches (cumulative)."""
+        c = (ctypes.c_int64 * 5)()
+        smmo.check(smmo.lib().smmo_structure_info(self._w, None, c, smmo._stream(self.stream)), "structure_info")
+        return dict(zip(("broken", "nodes_deleted", "springs_removed", "bfs_levels", "bfs_launches"), list(c)))
+
+    def sync(self):
+        return self.heap.sync()
+
+    def close(self):
+        if self._w:
+            smmo.lib().smmo_structure_destroy(self._w)
+            self._w = ctypes.c_void_p()
+        self.heap.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
