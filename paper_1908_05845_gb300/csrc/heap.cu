@@ -84,13 +84,13 @@ __global__ void __launch_bounds__(256) k_enumerate(HeapView h, int c) {
     if ((hi >> lane) & 1) b1 = __ldcg(h.alloc_bm + w * 64 + 32 + lane) & capmask;
     if ((lo >> lane) & 1) {
       REntry e;
-      e.block = w * 64 + lane; e.pad = 0; e.bits = b0;
+      e.block = w * 64 + lane; e.cls = (uint32_t)c; e.bits = b0;
       h.R[base + __popc(lo & lt)] = e;
       objs += __popcll(b0);
     }
     if ((hi >> lane) & 1) {
       REntry e;
-      e.block = w * 64 + 32 + lane; e.pad = 0; e.bits = b1;
+      e.block = w * 64 + 32 + lane; e.cls = (uint32_t)c; e.bits = b1;
       h.R[base + __popc(lo) + __popc(hi & lt)] = e;
       objs += __popcll(b1);
     }

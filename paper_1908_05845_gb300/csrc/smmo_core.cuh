@@ -67,11 +67,12 @@ struct DeviceState {
   unsigned long long ctr[SMMO_NSHARD][SMMO_NCTR];
 };
 
-// An enumerated block: its index and the snapshot of its allocation bitmap
-// (the thesis' "iteration bitmap", Sec. 5.2.1, carried with the index).
+// An enumerated block: its index, its class and the snapshot of its
+// allocation bitmap (the thesis' "iteration bitmap", Sec. 5.2.1, carried
+// with the index).
 struct __align__(16) REntry {
   uint32_t block;
-  uint32_t pad;
+  uint32_t cls;
   unsigned long long bits;
 };
 
@@ -555,8 +556,9 @@ __device__ __forceinline__ uint32_t smmo_new(const HeapView& h, uint32_t c) {
 // allocation cache, refilled near the current block, keeps new objects close
 // to their creators.  With POLY the enumeration holds blocks of several
 // classes (the concrete subclasses of one class, enumerated one after the
-// other into one snapshot): every unit reads its block's class from the
-// type id and passes it to the method, and every block counts as two units.
+// other into one snapshot): every unit takes its block's class from the
+// enumeration entry and passes it to the method, and every block counts as
+// two units.
 template <class M, bool POLY = false>
 __global__ void __launch_bounds__(512, 3) do_all_kernel(HeapView h, uint32_t c,
                                                      typename M::Args args) {
@@ -572,12 +574,11 @@ __global__ void __launch_bounds__(512, 3) do_all_kernel(HeapView h, uint32_t c,
   const uint32_t ub = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * per;
   const uint32_t ue = ub + per < units ? ub + per : units;
   for (uint32_t u = ub; u < ue; ++u) {
-    const uint32_t i = halves == 2 ? (u >> 1) : u;
     const uint32_t slot = (halves == 2 ? (u & 1) * 32 : 0) + lane;
-    const REntry e = h.R[i];
+    const REntry e = h.R[halves == 2 ? (u >> 1) : u];
     g_wcache[threadIdx.x >> 5].hint = e.block;
     if (lane == 0) visited += __popcll(halves == 2 ? (e.bits >> ((u & 1) * 32)) & 0xFFFFFFFFull : e.bits);
-    if ((e.bits >> slot) & 1) M::run(h, args, POLY ? __ldg(&h.block_type[e.block]) : c, (e.block << 6) | slot);
+    if ((e.bits >> slot) & 1) M::run(h, args, POLY ? e.cls : c, (e.block << 6) | slot);
     __syncwarp();  // reconverge: lane groups never run different iterations
   }
   if (lane == 0 && visited) count(h, SMMO_CTR_VISIT, visited);
@@ -628,13 +629,11 @@ __global__ void __launch_bounds__(512, 3) do_all_reduce_kernel(HeapView h, uint3
   const uint32_t ub = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * per;
   const uint32_t ue = ub + per < units ? ub + per : units;
   for (uint32_t u = ub; u < ue; ++u) {
-    const uint32_t i = halves == 2 ? (u >> 1) : u;
     const uint32_t slot = (halves == 2 ? (u & 1) * 32 : 0) + lane;
-    const REntry e = h.R[i];
+    const REntry e = h.R[halves == 2 ? (u >> 1) : u];
     g_wcache[threadIdx.x >> 5].hint = e.block;
     if (lane == 0) visited += __popcll(halves == 2 ? (e.bits >> ((u & 1) * 32)) & 0xFFFFFFFFull : e.bits);
-    if ((e.bits >> slot) & 1)
-      acc = reduce2(op, acc, M::run(h, args, POLY ? __ldg(&h.block_type[e.block]) : c, (e.block << 6) | slot));
+    if ((e.bits >> slot) & 1) acc = reduce2(op, acc, M::run(h, args, POLY ? e.cls : c, (e.block << 6) | slot));
     __syncwarp();
   }
   if (lane == 0 && visited) count(h, SMMO_CTR_VISIT, visited);

@@ -59,21 +59,27 @@ struct VertexReset {
   }
 };
 
-// Vertex::visit(frontier), reducing with OR: 1 if a neighbour was lowered
+// Vertex::visit(frontier), reducing with OR: 1 if a neighbour was lowered.
+// The frontier vertices are a level's critical path: the neighbour handles,
+// then all neighbour distances, are loaded before any store.
 struct VertexVisit {
   using Args = BfsArgs;
   __device__ static long long run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
     if (*V<int32_t>(h, c, self, V_DIST) != a.frontier) return 0;
     const int deg = *V<int32_t>(h, c, self, V_DEG);
+    uint32_t nb[SMMO_BFS_MAX_DEGREE];
+    int32_t dv[SMMO_BFS_MAX_DEGREE];
+#pragma unroll
+    for (int k = 0; k < SMMO_BFS_MAX_DEGREE; ++k) nb[k] = k < deg ? *V<uint32_t>(h, c, self, V_NBR + k) : kNull;
+#pragma unroll
+    for (int k = 0; k < SMMO_BFS_MAX_DEGREE; ++k) dv[k] = nb[k] != kNull ? *V<int32_t>(h, c, nb[k], V_DIST) : 0;
     long long changed = 0;
-    for (int k = 0; k < deg; ++k) {
-      const uint32_t nb = *V<uint32_t>(h, c, self, V_NBR + k);
-      int32_t* d = V<int32_t>(h, c, nb, V_DIST);
-      if (*d > a.frontier + 1) {
-        *d = a.frontier + 1;
+#pragma unroll
+    for (int k = 0; k < SMMO_BFS_MAX_DEGREE; ++k)
+      if (nb[k] != kNull && dv[k] > a.frontier + 1) {
+        *V<int32_t>(h, c, nb[k], V_DIST) = a.frontier + 1;
         changed = 1;
       }
-    }
     return changed;
   }
 };

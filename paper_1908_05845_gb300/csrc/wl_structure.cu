@@ -57,6 +57,10 @@ struct StructArgs {
   float *o_fx, *o_fy;
   uint32_t n0, s0;
   const uint32_t* handles;  // creation: node id -> handle
+  // byte offsets of the NodeBase columns when every node class has them at
+  // the same place (equal capacities), else base_uniform = 0
+  int32_t base_uniform;
+  uint32_t base_off[N_ID + 1];
 };
 
 __device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
@@ -68,14 +72,20 @@ __device__ __forceinline__ T* F(const HeapView& h, uint32_t cls, uint32_t self, 
   return field_ptr<T>(h, __ldg(&h.cls[cls].col_off[col]), self);
 }
 
+// A NodeBase column of a node whose class is not known: without the type
+// id when every node class keeps the column at the same offset.
+template <class T>
+__device__ __forceinline__ T* NB(const HeapView& h, const StructArgs& a, uint32_t v, int col) {
+  return a.base_uniform ? field_ptr<T>(h, a.base_off[col], v) : F<T>(h, type_of(h, v), v, col);
+}
+
 // Spring s leaves node v's array; the node is deleted when it held only s.
 __device__ __forceinline__ void unlink_end(const HeapView& h, const StructArgs& a, uint32_t v, uint32_t s) {
-  const uint32_t t = type_of(h, v);
   for (int i = 0; i < 3; ++i) {
-    uint32_t* sl = F<uint32_t>(h, t, v, N_SPR + i);
+    uint32_t* sl = NB<uint32_t>(h, a, v, N_SPR + i);
     if (*sl == s) {
       *sl = kNull;
-      if (atomicSub(F<int32_t>(h, t, v, N_NSPR), 1) == 1) {
+      if (atomicSub(NB<int32_t>(h, a, v, N_NSPR), 1) == 1) {
         smmo_delete(h, v);
         atomicAdd(&a.ctr[CTR_NODES_DELETED], 1ull);
       }
@@ -105,9 +115,8 @@ struct SpringForce {
   using Args = StructArgs;
   __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
     const uint32_t p1 = *F<uint32_t>(h, c, self, S_P1), p2 = *F<uint32_t>(h, c, self, S_P2);
-    const uint32_t t1 = type_of(h, p1), t2 = type_of(h, p2);
-    const float dx = fs(*F<float>(h, t2, p2, N_X), *F<float>(h, t1, p1, N_X));
-    const float dy = fs(*F<float>(h, t2, p2, N_Y), *F<float>(h, t1, p1, N_Y));
+    const float dx = fs(*NB<float>(h, a, p2, N_X), *NB<float>(h, a, p1, N_X));
+    const float dy = fs(*NB<float>(h, a, p2, N_Y), *NB<float>(h, a, p1, N_Y));
     const float len = __fsqrt_rn(fa(fm(dx, dx), fm(dy, dy)));
     const float stretch = fs(len, *F<float>(h, c, self, S_L0));
     const float f = stretch > 0.0f ? fm(*F<float>(h, c, self, S_K), stretch) : 0.0f;
@@ -165,19 +174,33 @@ struct NodeInitFrontier {
 };
 
 // NodeBase::visit(frontier), reducing with OR: 1 iff the node is in the
-// frontier (the thesis' continue flag)
+// frontier (the thesis' continue flag).  The few frontier nodes of a level
+// are its critical path, so each stage's loads are issued for all three
+// springs before the next stage (slots, endpoints, neighbour classes,
+// distances), and the stores come last.
 struct NodeVisit {
   using Args = StructArgs;
   __device__ static long long run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
     if (*F<int32_t>(h, c, self, N_DIST) != a.frontier) return 0;
+    uint32_t s[3], u[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) s[i] = *F<uint32_t>(h, c, self, N_SPR + i);
+#pragma unroll
     for (int i = 0; i < 3; ++i) {
-      const uint32_t s = *F<uint32_t>(h, c, self, N_SPR + i);
-      if (s == kNull) continue;
-      const uint32_t p1 = *F<uint32_t>(h, a.spring_cls, s, S_P1);
-      const uint32_t u = p1 == self ? *F<uint32_t>(h, a.spring_cls, s, S_P2) : p1;
-      int32_t* d = F<int32_t>(h, type_of(h, u), u, N_DIST);
-      if (*d == kInf) *d = a.frontier + 1;
+      u[i] = kNull;
+      if (s[i] == kNull) continue;
+      const uint32_t p1 = *F<uint32_t>(h, a.spring_cls, s[i], S_P1), p2 = *F<uint32_t>(h, a.spring_cls, s[i], S_P2);
+      u[i] = p1 == self ? p2 : p1;
     }
+    int32_t* d[3];
+    int32_t dv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[i] = u[i] == kNull ? nullptr : NB<int32_t>(h, a, u[i], N_DIST);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dv[i] = d[i] ? *d[i] : 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      if (d[i] && dv[i] == kInf) *d[i] = a.frontier + 1;
     return 1;
   }
 };
@@ -426,6 +449,14 @@ int smmo_structure_create(smmo_heap* heap, int64_t n, const int8_t* kind, const 
   a.keep = 1.0f - p->damping;
   a.n0 = (uint32_t)n;
   a.s0 = (uint32_t)ns;
+  {
+    const ClassLayout& L0 = heap->classes[w->cls_anchor].layout;
+    a.base_uniform = 1;
+    for (int cls : {w->cls_pull, w->cls_node})
+      for (int k = 0; k <= N_ID; ++k)
+        if (heap->classes[cls].layout.col_off[k] != L0.col_off[k]) a.base_uniform = 0;
+    for (int k = 0; k <= N_ID; ++k) a.base_off[k] = L0.col_off[k];
+  }
   cudaError_t e = cudaMalloc(&w->d_ctr, sizeof(unsigned long long) * CTR_N);
   if (e == cudaSuccess) e = cudaMemsetAsync(w->d_ctr, 0, sizeof(unsigned long long) * CTR_N, st_);
   if (e != cudaSuccess) { smmo_structure_destroy(w); return cuda_status(e); }
