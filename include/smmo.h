@@ -255,6 +255,23 @@ int smmo_gather_fields(smmo_heap* heap, int class_id, const smmo_handle* handles
 int smmo_compact(smmo_heap* heap, int class_id, int defrag_factor,
                  int64_t k1, smmo_compact_stats* out, void* stream);
 
+/* Number of defragmentation candidates of class_id for factor n (allocated
+ * blocks holding at most floor(N_T n / (n + 1)) objects, Sec. 6.3.1) into
+ * *count (host).  Synchronises `stream`. */
+int smmo_defrag_candidates(smmo_heap* heap, int class_id, int defrag_factor,
+                           int64_t* count, void* stream);
+
+/* The "after massive deallocations" policy of Sec. 6.3.8: compacts class_id
+ * (as smmo_compact with n = defrag_factor and k1) iff its candidate count
+ * is at least k2 n / (n + 1), where k2 = max(k2_blocks, k2_fraction x the
+ * heap's block count M) (k2_fraction in [0, 1]).  *ran (host, nullable) =
+ * 1 if it compacted; when it did not, *out holds zeros except
+ * candidates_left = the count.  Synchronises `stream`.  (The other policy,
+ * every m iterations, is a loop in the caller.) */
+int smmo_compact_if(smmo_heap* heap, int class_id, int defrag_factor, int64_t k1,
+                    int64_t k2_blocks, double k2_fraction, smmo_compact_stats* out,
+                    int* ran, void* stream);
+
 /* Statistics (Sec. 6.2.2 fragmentation F; device counters).  Synchronises
  * `stream`. */
 int smmo_heap_get_stats(smmo_heap* heap, smmo_heap_stats* out, void* stream);

@@ -463,3 +463,62 @@ extern "C" int smmo_compact(smmo_heap* h, int c, int n, int64_t k1, smmo_compact
   if (status) return status;
   return cuda_status(e);
 }
+
+namespace {
+// Defragmentation candidates of class c for factor n: allocated blocks at
+// most `limit` full (Sec. 6.3.1), one thread per block, warp-aggregated.
+__global__ void __launch_bounds__(256) k_count_candidates(HeapView h, uint32_t c, uint32_t limit,
+                                                          unsigned long long* out) {
+  uint32_t cnt = 0;
+  for (uint32_t blk = blockIdx.x * blockDim.x + threadIdx.x; blk < h.num_blocks; blk += gridDim.x * blockDim.x) {
+    const unsigned long long A = bm_level(h, bm_alloc(h, c), 0)[blk >> 6];
+    if ((A >> (blk & 63)) & 1) cnt += (uint32_t)__popcll(h.alloc_bm[blk] & h.cls[c].capmask) <= limit ? 1u : 0u;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, (unsigned long long)cnt);
+}
+}  // namespace
+
+extern "C" int smmo_defrag_candidates(smmo_heap* h, int c, int n, int64_t* count, void* stream) {
+  if (!h || c < 0 || c >= (int)h->classes.size() || n < 1 || n > 63 || !count) return SMMO_E_INVALID_ARG;
+  if (h->classes[c].abstract) return SMMO_E_INVALID_ARG;
+  *count = 0;
+  if (!h->frozen) return SMMO_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const ClassLayout& L = h->classes[c].layout;
+  const uint32_t limit = (uint32_t)((uint64_t)L.cap * n / (n + 1));
+  unsigned long long* d = &h->view.st->aux[0];
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(*d), s);
+  if (e != cudaSuccess) return cuda_status(e);
+  const uint32_t grid = std::max(1u, std::min((h->view.num_blocks + 255) / 256, (uint32_t)h->num_sms * 8));
+  k_count_candidates<<<grid, 256, 0, s>>>(h->view, (uint32_t)c, limit, d);
+  unsigned long long v = 0;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, d, sizeof(v), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  *count = (int64_t)v;
+  return SMMO_OK;
+}
+
+extern "C" int smmo_compact_if(smmo_heap* h, int c, int n, int64_t k1, int64_t k2_blocks, double k2_fraction,
+                               smmo_compact_stats* out, int* ran, void* stream) {
+  if (ran) *ran = 0;
+  if (!h || k2_blocks < 0 || !(k2_fraction >= 0.0) || k2_fraction > 1.0) return SMMO_E_INVALID_ARG;
+  int64_t cand = 0;
+  int st = smmo_defrag_candidates(h, c, n, &cand, stream);
+  if (st) return st;
+  // k2 as a block count or a fraction of the heap's blocks, scaled by
+  // n / (n + 1): a larger n makes more blocks candidates
+  const double k2 = std::max((double)k2_blocks, k2_fraction * (double)h->view.num_blocks);
+  if ((double)cand < k2 * n / (n + 1)) {
+    if (out) {
+      *out = smmo_compact_stats{};
+      out->candidates_left = cand;
+    }
+    return SMMO_OK;
+  }
+  if (ran) *ran = 1;
+  return smmo_compact(h, c, n, k1, out, stream);
+}

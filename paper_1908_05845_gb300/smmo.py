@@ -266,6 +266,22 @@ class Heap:
                                  _stream(self.stream)), "compact")
         return {k: getattr(cs, k) for k, _ in CompactStats._fields_}
 
+    def defrag_candidates(self, cls: int, n: int = 1) -> int:
+        """Blocks of class cls at most n/(n+1) full."""
+        v = ctypes.c_int64()
+        check(lib().smmo_defrag_candidates(self._h, cls, n, ctypes.byref(v), _stream(self.stream)),
+              "defrag_candidates")
+        return v.value
+
+    def compact_if(self, cls: int, n: int = 1, k1: int = 0, k2_blocks: int = 0, k2_fraction: float = 0.0):
+        """The 'after massive deallocations' policy: (ran, stats)."""
+        cs = CompactStats()
+        ran = ctypes.c_int()
+        check(lib().smmo_compact_if(self._h, cls, n, ctypes.c_int64(k1), ctypes.c_int64(k2_blocks),
+                                    ctypes.c_double(k2_fraction), ctypes.byref(cs), ctypes.byref(ran),
+                                    _stream(self.stream)), "compact_if")
+        return bool(ran.value), {k: getattr(cs, k) for k, _ in CompactStats._fields_}
+
     # ---------------------------------------------------------- status
     def stats(self):
         s = HeapStats()

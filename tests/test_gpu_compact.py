@@ -177,3 +177,33 @@ def test_self_referencing_ring_survives_multi_pass_compaction():
     got = dict(zip(vv.cpu().numpy().tolist(), tv.cpu().numpy().tolist()))
     assert sorted(got) == alive.tolist()
     assert all(got[a] == b for a, b in zip(alive.tolist(), np.roll(alive, -1).tolist()))
+
+
+def test_candidate_count_and_massive_deallocation_policy():
+    """Sec. 6.3.8: candidates counted for several n against the fills set
+    by hand; the policy compacts only once the count reaches k2 n / (n + 1)
+    (k2 absolute or as a fraction of the heap's blocks)."""
+    h = smmo.Heap(32 << 20)
+    A = h.register("A", [("v", smmo.I32), ("kill", smmo.I32)])
+    h.freeze()
+    cap = h.stats()["capacity"][A]
+    fills = {b: f for b, f in enumerate([1, 5, cap // 2, cap // 2 + 1, cap - 1, cap, 3, cap // 3] * 5)}
+    _kill_all_but(h, A, fills, len(fills), cap)
+    h.sync()
+    for n in (1, 2, 5, 63):
+        limit = cap * n // (n + 1)
+        assert h.defrag_candidates(A, n) == sum(1 for f in fills.values() if f <= limit), n
+    n = 2
+    cand = h.defrag_candidates(A, n)
+    M = h.stats()["num_blocks"]
+    thr_blocks = (cand * (n + 1)) // n  # the largest k2 with k2 n / (n + 1) <= cand
+    ran, st = h.compact_if(A, n, k2_blocks=thr_blocks + 1)
+    assert not ran and st["candidates_left"] == cand and st["passes"] == 0
+    ran, st = h.compact_if(A, n, k2_fraction=min(1.0, (thr_blocks + 1.5) / M))
+    assert not ran
+    live = h.stats()["live_objects"][A]
+    ran, st = h.compact_if(A, n, k2_blocks=thr_blocks)
+    assert ran and st["passes"] >= 1 and st["blocks_freed"] > 0
+    h.sync()
+    assert h.check() == 0 and h.stats()["live_objects"][A] == live
+    assert h.defrag_candidates(A, n) < cand
