@@ -988,7 +988,7 @@ def main():
     ap.add_argument("--workload", default="wator",
                     choices=["wator", "batched", "gol", "generation", "nasch", "nbody", "bh", "bfs", "alloc",
                              "compact", "structure"])
-    ap.add_argument("--bfs-check", type=int, default=32)
+    ap.add_argument("--bfs-check", type=int, default=1024)
     ap.add_argument("--struct-iters", type=int, default=100)
     ap.add_argument("--bh-bodies", type=int, default=65536)
     ap.add_argument("--gen-steps", type=int, default=500)

@@ -568,10 +568,12 @@ typedef struct smmo_bfs smmo_bfs;
  * neighbours.  Synchronises `stream`. */
 int smmo_bfs_create(smmo_heap* heap, int64_t n, const int32_t* row_ptr,
                     const int32_t* col, void* stream, smmo_bfs** out);
-/* Distances from `source`: resets every vertex, then runs levels in
- * batches of check_every (1..4096) and reads the batch's OR results back;
- * levels after the last one change nothing.  *levels (host, nullable) =
- * largest distance + 1.  Synchronises `stream` once per batch. */
+/* Distances from `source`: resets every vertex, then runs up to
+ * check_every (1..4096) levels per cooperative launch (a grid barrier
+ * between levels; the launch ends after the first level that lowers no
+ * distance) and reads the launch's OR results back.  *levels (host,
+ * nullable) = largest distance + 1.  Synchronises `stream` once per
+ * launch.  A barrier wait that gives up returns SMMO_E_TIMEOUT. */
 int smmo_bfs_run(smmo_bfs* w, int32_t source, int check_every, int32_t* levels,
                  void* stream);
 /* dist: device array of n int32 (distance by vertex id, 2^31 - 1 =
@@ -604,7 +606,7 @@ int smmo_bfs_destroy(smmo_bfs* w);
 typedef struct {
   float dt, damping;
   int32_t substeps;         /* compute steps per iteration (>= 0)      */
-  int32_t bfs_check_every;  /* BFS levels per read-back (1..4096)      */
+  int32_t bfs_check_every;  /* BFS levels per cooperative launch and read-back (1..4096) */
 } smmo_structure_params;
 typedef struct smmo_structure smmo_structure;
 /* Creates the mesh in a fresh heap (else SMMO_E_FROZEN).  Host arrays.
@@ -622,7 +624,9 @@ int smmo_structure_create(smmo_heap* heap, int64_t n, const int8_t* kind,
                           smmo_structure** out);
 /* `iterations` iterations of the phases in the bit mask `phases`
  * (SMMO_STRUCT_PHASE_*; 7 = all, in the order pull, compute, remove).  The
- * removal reads back one flag batch per bfs_check_every levels. */
+ * removal runs up to bfs_check_every BFS levels per cooperative launch (it
+ * ends after the first level without frontier) and reads the flags back
+ * after each; a barrier wait that gives up returns SMMO_E_TIMEOUT. */
 int smmo_structure_step(smmo_structure* w, int iterations, int phases, void* stream);
 /* Device output arrays by id (each nullable): nodes (n) node_alive (0/1),
  * x, y, vx, vy (0 for anchors), num_springs, distance (of the last
@@ -640,7 +644,8 @@ int smmo_structure_export(smmo_structure* w, const smmo_structure_out* out, void
 /* class ids [NodeBase, AnchorNode, AnchorPullNode, Node, Spring] (host, 5,
  * nullable); counters (host, 5, nullable): springs broken, nodes deleted
  * (by breaks and removals), springs removed by the removal phase, BFS
- * levels run, BFS level launches.  Synchronises `stream` if counters. */
+ * levels run, BFS launches (each up to
+ * bfs_check_every levels).  Synchronises `stream` if counters. */
 int smmo_structure_info(smmo_structure* w, int* class_ids, int64_t* counters, void* stream);
 int smmo_structure_destroy(smmo_structure* w);
 

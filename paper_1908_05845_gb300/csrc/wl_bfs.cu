@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "heap_internal.h"
+#include "levels.cuh"
 #include "smmo.h"
 #include "smmo_core.cuh"
 
@@ -61,18 +62,22 @@ struct VertexReset {
 
 // Vertex::visit(frontier), reducing with OR: 1 if a neighbour was lowered.
 // The frontier vertices are a level's critical path: the neighbour handles,
-// then all neighbour distances, are loaded before any store.
+// then all neighbour distances, are loaded before any store.  Distances,
+// which other CTAs write between levels of one launch, are read through L2.
 struct VertexVisit {
   using Args = BfsArgs;
+  __device__ static bool active(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
+    return __ldcg(V<int32_t>(h, c, self, V_DIST)) == a.frontier;
+  }
   __device__ static long long run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
-    if (*V<int32_t>(h, c, self, V_DIST) != a.frontier) return 0;
+    if (!active(h, a, c, self)) return 0;
     const int deg = *V<int32_t>(h, c, self, V_DEG);
     uint32_t nb[SMMO_BFS_MAX_DEGREE];
     int32_t dv[SMMO_BFS_MAX_DEGREE];
 #pragma unroll
     for (int k = 0; k < SMMO_BFS_MAX_DEGREE; ++k) nb[k] = k < deg ? *V<uint32_t>(h, c, self, V_NBR + k) : kNull;
 #pragma unroll
-    for (int k = 0; k < SMMO_BFS_MAX_DEGREE; ++k) dv[k] = nb[k] != kNull ? *V<int32_t>(h, c, nb[k], V_DIST) : 0;
+    for (int k = 0; k < SMMO_BFS_MAX_DEGREE; ++k) dv[k] = nb[k] != kNull ? __ldcg(V<int32_t>(h, c, nb[k], V_DIST)) : 0;
     long long changed = 0;
 #pragma unroll
     for (int k = 0; k < SMMO_BFS_MAX_DEGREE; ++k)
@@ -103,9 +108,11 @@ struct smmo_bfs {
   smmo_heap* heap = nullptr;
   int cls = -1;
   uint32_t n0 = 0;
-  long long* d_flags = nullptr;  // one OR result per level of a batch
+  unsigned long long* d_flags = nullptr;  // one OR result per level of a launch
+  unsigned int* d_arrive = nullptr;       // grid barrier counter
   int flags_cap = 0;
   BfsArgs args{};
+  smmo::Snapshot snap;                    // the vertices (fixed during a search)
 };
 
 extern "C" {
@@ -172,33 +179,37 @@ int smmo_bfs_run(smmo_bfs* w, int32_t source, int check_every, int32_t* levels, 
   if (!w || source < 0 || (uint32_t)source >= w->n0 || check_every < 1 || check_every > 4096)
     return SMMO_E_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  if (!w->d_arrive) {
+    cudaError_t e = cudaMalloc(&w->d_arrive, sizeof(unsigned int) * kBarrierWords);
+    if (e != cudaSuccess) { w->d_arrive = nullptr; return cuda_status(e); }
+  }
   if (w->flags_cap < check_every) {
     if (w->d_flags) cudaFree(w->d_flags);
     w->d_flags = nullptr;
-    cudaError_t e = cudaMalloc(&w->d_flags, sizeof(long long) * check_every);
+    cudaError_t e = cudaMalloc(&w->d_flags, sizeof(unsigned long long) * check_every);
     if (e != cudaSuccess) { w->flags_cap = 0; return cuda_status(e); }
     w->flags_cap = check_every;
   }
   BfsArgs a = w->args;
   a.source = source;
   // the vertex set does not change during the search, so one enumeration
-  // serves every level (each level is parallel_do_and_reduce's reducing
-  // do-all over that snapshot, the OR folded into a zeroed flag)
-  int st = enumerate(w->heap, w->cls, s);
-  if (!st) st = launch_do_all<VertexReset>(w->heap, w->cls, &a, s);
-  std::vector<long long> hf((size_t)check_every);
+  // serves every level; check_every levels run per cooperative launch
+  // (parallel_do_and_reduce with OR per level, a grid barrier between)
+  int st = w->snap.take(w->heap, w->cls, s);
+  if (!st) st = launch_do_all_view<VertexReset>(w->heap, w->cls, &a, s, &w->snap.view);
+  std::vector<unsigned long long> hf((size_t)check_every);
   for (int32_t base = 0; !st; base += check_every) {
     if (base > (int32_t)w->n0) return SMMO_E_TIMEOUT;  // more levels than vertices: impossible
-    cudaError_t e0 = cudaMemsetAsync(w->d_flags, 0, sizeof(long long) * check_every, s);
-    if (e0 != cudaSuccess) return cuda_status(e0);
-    for (int k = 0; k < check_every && !st; ++k) {
-      a.frontier = base + k;
-      st = launch_do_all_reduce<VertexVisit>(w->heap, w->cls, &a, SMMO_REDUCE_OR, w->d_flags + k, s);
-    }
+    st = launch_levels<VertexVisit, false>(w->heap, w->snap.view, w->cls, a, base, check_every, w->d_flags,
+                                           w->d_arrive, s);
     if (st) break;
-    cudaError_t e = cudaMemcpyAsync(hf.data(), w->d_flags, sizeof(long long) * check_every, cudaMemcpyDeviceToHost, s);
+    int err = 0;
+    cudaError_t e = cudaMemcpyAsync(hf.data(), w->d_flags, sizeof(unsigned long long) * check_every,
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &w->heap->view.st->err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_status(e);
+    if (err) return err;  // a barrier gave up
     for (int k = 0; k < check_every; ++k)
       if (hf[(size_t)k] == 0) {  // level base + k found nothing new
         if (levels) *levels = base + k + 1;
@@ -222,6 +233,8 @@ int smmo_bfs_export(smmo_bfs* w, int32_t* dist, void* stream) {
 int smmo_bfs_destroy(smmo_bfs* w) {
   if (!w) return SMMO_E_INVALID_ARG;
   if (w->d_flags) cudaFree(w->d_flags);
+  if (w->d_arrive) cudaFree(w->d_arrive);
+  w->snap.release();
   delete w;
   return SMMO_OK;
 }

@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "heap_internal.h"
+#include "levels.cuh"
 #include "smmo.h"
 #include "smmo_core.cuh"
 
@@ -177,11 +178,15 @@ struct NodeInitFrontier {
 // frontier (the thesis' continue flag).  The few frontier nodes of a level
 // are its critical path, so each stage's loads are issued for all three
 // springs before the next stage (slots, endpoints, neighbour classes,
-// distances), and the stores come last.
+// distances), and the stores come last.  Distances, which other CTAs write
+// between levels of one launch, are read through L2.
 struct NodeVisit {
   using Args = StructArgs;
+  __device__ static bool active(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
+    return __ldcg(F<int32_t>(h, c, self, N_DIST)) == a.frontier;
+  }
   __device__ static long long run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
-    if (*F<int32_t>(h, c, self, N_DIST) != a.frontier) return 0;
+    if (!active(h, a, c, self)) return 0;
     uint32_t s[3], u[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) s[i] = *F<uint32_t>(h, c, self, N_SPR + i);
@@ -197,7 +202,7 @@ struct NodeVisit {
 #pragma unroll
     for (int i = 0; i < 3; ++i) d[i] = u[i] == kNull ? nullptr : NB<int32_t>(h, a, u[i], N_DIST);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) dv[i] = d[i] ? *d[i] : 0;
+    for (int i = 0; i < 3; ++i) dv[i] = d[i] ? __ldcg(d[i]) : 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
       if (d[i] && dv[i] == kInf) *d[i] = a.frontier + 1;
@@ -307,7 +312,8 @@ struct smmo_structure {
   int32_t substeps = 0, check_every = 16;
   StructArgs args{};
   unsigned long long* d_ctr = nullptr;  // CTR_N counters
-  long long* d_flags = nullptr;         // one OR result per level of a batch
+  unsigned long long* d_flags = nullptr;  // one OR result per level of a launch
+  unsigned int* d_arrive = nullptr;       // grid barrier counter
   int flags_cap = 0;
   smmo::Snapshot nodes;                 // all node classes (one POLY snapshot)
   int64_t bfs_levels = 0;               // levels run (statistics)
@@ -326,9 +332,9 @@ int pdo(smmo_structure* w, int cls, method_launch_fn fn, const StructArgs& a, cu
   return st;
 }
 
-// the removal phase: BFS levels in batches of check_every over one
-// snapshot of all node classes (no node is created or deleted during the
-// search), then flags and deletions
+// the removal phase: BFS levels, check_every per cooperative launch, over
+// one snapshot of all node classes (no node is created or deleted during
+// the search), then flags and deletions
 int remove_disconnected(smmo_structure* w, cudaStream_t s) {
   StructArgs a = w->args;
   smmo_heap* h = w->heap;
@@ -339,26 +345,23 @@ int remove_disconnected(smmo_structure* w, cudaStream_t s) {
   if (w->flags_cap < ce) {
     if (w->d_flags) cudaFree(w->d_flags);
     w->d_flags = nullptr;
-    cudaError_t e = cudaMalloc(&w->d_flags, sizeof(long long) * ce);
+    cudaError_t e = cudaMalloc(&w->d_flags, sizeof(unsigned long long) * ce);
     if (e != cudaSuccess) { w->flags_cap = 0; return cuda_status(e); }
     w->flags_cap = ce;
   }
-  std::vector<long long> hf((size_t)ce);
+  std::vector<unsigned long long> hf((size_t)ce);
   bool done = false;
   for (int32_t base = 0; !done; base += ce) {
     if (base > (int32_t)w->n0 + 1) return SMMO_E_TIMEOUT;  // more levels than nodes: impossible
-    cudaError_t e = cudaMemsetAsync(w->d_flags, 0, sizeof(long long) * ce, s);
-    if (e != cudaSuccess) return cuda_status(e);
-    for (int k = 0; k < ce && !st; ++k) {
-      a.frontier = base + k;
-      st = launch_do_all_reduce_view<NodeVisit, true>(h, w->cls_base, &a, SMMO_REDUCE_OR, w->d_flags + k, s,
-                                                       &w->nodes.view);
-      ++w->bfs_launches;
-    }
+    st = launch_levels<NodeVisit, true>(h, w->nodes.view, w->cls_base, a, base, ce, w->d_flags, w->d_arrive, s);
+    ++w->bfs_launches;
     if (st) return st;
-    e = cudaMemcpyAsync(hf.data(), w->d_flags, sizeof(long long) * ce, cudaMemcpyDeviceToHost, s);
+    int err = 0;
+    cudaError_t e = cudaMemcpyAsync(hf.data(), w->d_flags, sizeof(unsigned long long) * ce, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &h->view.st->err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_status(e);
+    if (err) return err;  // a barrier gave up (left for smmo_heap_sync to report too)
     for (int k = 0; k < ce; ++k)
       if (hf[(size_t)k] == 0) {  // level base + k had no frontier: the search is over
         w->bfs_levels += base + k + 1;
@@ -459,6 +462,7 @@ int smmo_structure_create(smmo_heap* heap, int64_t n, const int8_t* kind, const 
   }
   cudaError_t e = cudaMalloc(&w->d_ctr, sizeof(unsigned long long) * CTR_N);
   if (e == cudaSuccess) e = cudaMemsetAsync(w->d_ctr, 0, sizeof(unsigned long long) * CTR_N, st_);
+  if (e == cudaSuccess) e = cudaMalloc(&w->d_arrive, sizeof(unsigned int) * kBarrierWords);
   if (e != cudaSuccess) { smmo_structure_destroy(w); return cuda_status(e); }
   a.ctr = w->d_ctr;
   // handle table: nodes by id, then springs by id
@@ -622,6 +626,7 @@ int smmo_structure_destroy(smmo_structure* w) {
   if (!w) return SMMO_E_INVALID_ARG;
   if (w->d_ctr) cudaFree(w->d_ctr);
   if (w->d_flags) cudaFree(w->d_flags);
+  if (w->d_arrive) cudaFree(w->d_arrive);
   w->nodes.release();
   delete w;
   return SMMO_OK;

@@ -445,7 +445,7 @@ class Structure:
     NAMES = ["NodeBase", "AnchorNode", "AnchorPullNode", "Node", "Spring"]
 
     def __init__(self, mesh: dict, dt: float = 0.05, damping: float = 0.01, substeps: int = 40,
-                 bfs_check_every: int = 32, heap_bytes: int | None = None,
+                 bfs_check_every: int = 1024, heap_bytes: int | None = None,
                  config: smmo.HeapConfig | None = None, stream=None):
         self.stream = stream
         self.n, self.ns = len(mesh["kind"]), len(mesh["p1"])
@@ -498,7 +498,7 @@ class Structure:
 
     def counters(self) -> dict:
         """springs broken, nodes deleted, springs removed by the removal
-        phase, BFS levels run, BFS level launches (cumulative)."""
+        phase, BFS levels run, BFS launches (cumulative)."""
         c = (ctypes.c_int64 * 5)()
         smmo.check(smmo.lib().smmo_structure_info(self._w, None, c, smmo._stream(self.stream)), "structure_info")
         return dict(zip(("broken", "nodes_deleted", "springs_removed", "bfs_levels", "bfs_launches"), list(c)))
