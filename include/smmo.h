@@ -649,6 +649,12 @@ int smmo_structure_export(smmo_structure* w, const smmo_structure_out* out, void
 int smmo_structure_info(smmo_structure* w, int* class_ids, int64_t* counters, void* stream);
 int smmo_structure_destroy(smmo_structure* w);
 
+/* Self-test of a bounded wait: one CTA waits at a grid barrier that nothing
+ * releases, for `spins` polls of about 100 ns (1..2^20), then records
+ * SMMO_E_TIMEOUT (detail 2) in the heap's error word and returns; the
+ * caller reads it with smmo_heap_sync.  Synchronises `stream`. */
+int smmo_selftest_barrier_timeout(smmo_heap* heap, uint32_t spins, void* stream);
+
 /* Self-test of the branch-free, correctly rounded FP32 square root and
  * reciprocal that the force kernel uses when every coordinate is within
  * 2^18 and eps^2 is in [2^-40, 2^38] (otherwise it uses the IEEE-rounded

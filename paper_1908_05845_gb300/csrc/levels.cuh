@@ -30,7 +30,8 @@ constexpr int kBarrierWords = 64;                  // arrive[0] counter, arrive[
 // the count k x gridDim.x) writes k to arrive[32], on which the others wait
 // (the count and the word are in different cache lines, so the waiting
 // reads do not slow the arrivals).
-__device__ __forceinline__ bool grid_barrier(const HeapView& h, unsigned int* arrive, unsigned int k) {
+__device__ __forceinline__ bool grid_barrier(const HeapView& h, unsigned int* arrive, unsigned int k,
+                                             unsigned spin_limit = kLevelBarrierSpins) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -43,7 +44,7 @@ __device__ __forceinline__ bool grid_barrier(const HeapView& h, unsigned int* ar
     }
     unsigned spins = 0;
     while (*(volatile unsigned int*)(arrive + 32) < k) {
-      if (++spins > kLevelBarrierSpins) {
+      if (++spins > spin_limit) {
         ok = 0;
         set_error(h, SMMO_E_TIMEOUT, target);
         break;

@@ -1,6 +1,8 @@
 """GPU tests of the heap core: bulk creation, parallel_do, device new /
 delete (warp-aggregated allocation, block invalidation), enumeration,
 inheritance, statistics and the post-kernel invariants (Sec. 5.4)."""
+import time
+
 import numpy as np
 import pytest
 
@@ -199,3 +201,23 @@ def test_parallel_do_and_reduce_all_reducers():
     with pytest.raises(smmo.SmmoError):
         h.parallel_do(A, "test.value_i32", arg)
     h.sync()
+
+
+def test_bounded_wait_runs_out_and_context_stays_usable():
+    """A grid-barrier wait that nothing releases gives up after its poll
+    limit with SMMO_E_TIMEOUT (read on the host); the next kernels run."""
+    h = smmo.Heap(8 << 20)
+    A = h.register("A", [("v", smmo.I32)])
+    h.freeze()
+    t0 = time.perf_counter()
+    smmo.check(smmo.lib().smmo_selftest_barrier_timeout(h.handle, 4096, smmo._stream(None)), "selftest")
+    assert time.perf_counter() - t0 < 5.0
+    with pytest.raises(smmo.SmmoError) as ei:
+        h.sync()
+    assert ei.value.status == -6  # SMMO_E_TIMEOUT
+    h.sync()  # the error was cleared
+    v = torch.arange(640, dtype=torch.int32, device="cuda")
+    h.bulk_new(A, 640, [v])
+    h.parallel_do(A, "test.add_i32", smmo.AddI32Args(0, 5))
+    (got,) = h.gather(A, h.enumerate_live(A), ["v"])
+    assert np.array_equal(np.sort(got.cpu().numpy()), np.arange(640) + 5)
