@@ -2,9 +2,12 @@
 
 A plain, slow, single-threaded array-of-structs restatement (in C, see the
 ``*.c`` files beside this one) of the thesis' SMMO workloads: object-based
-Game of Life (Sec. 7.8), Wa-Tor (Sec. 7.6), Nagel-Schreckenberg traffic
-(Sec. 7.5), n-body with collision merge (Sec. 7.1/7.2) and the n-body adjoint.
-It has its own Philox4x32-10 (Salmon et al., SC'11).
+Game of Life and the generational automaton (Sec. 7.8), Wa-Tor (Sec. 7.6),
+Nagel-Schreckenberg traffic with and without traffic controllers
+(Sec. 7.5), n-body with collision merge (Sec. 7.1/7.2) and the n-body
+adjoint, Barnes-Hut (Sec. 7.3), the spring mesh "structure" (Sec. 7.4) and
+frontier BFS (Sec. 4.3).  It has its own Philox4x32-10 (Salmon et al.,
+SC'11).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
 leg may import this package.  It never imports the CUDA library and the CUDA
@@ -18,7 +21,12 @@ histories, full grid without sharks; NaSch free-flow closed form, car
 conservation on a ring with p = 0, evenly spaced flow; n-body momentum
 conservation, two-body circular orbit, energy drift O(dt^2), merge mass
 conservation; adjoint against central finite differences and the pair
-kernel against finite differences of the acceleration.  Parity of every
+kernel against finite differences of the acceleration; generation rules
+against dense reference automata; traffic-light phases and yield
+priorities; Barnes-Hut against direct summation at theta 0 and the region
+tree's node count; spring mesh against one-spring and oscillator closed
+forms, momentum and energy conservation and connected components; BFS
+against Manhattan distances and scipy shortest paths.  Parity of every
 function here is pinned by at least one of those.
 """
 from __future__ import annotations
