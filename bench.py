@@ -773,6 +773,80 @@ def run_structure(args):
     return 0 if exact else 1
 
 
+def run_wator_compact(args):
+    """CompactGpu on Wa-Tor (Sec. 6.4's wa-tor experiment): the 2048 x 2048
+    world for 500 steps, plain, with compact(n = 10, k1 = 16) of Fish and
+    Shark every 50 steps (and with n = 2), and with the "after massive
+    deallocations" policy (Sec. 6.3.8: n = 10, checked every 10 steps, k2 =
+    5 % of the heap's blocks).  L2 is not flushed between steps here: the
+    runs are compared with each other.
+    Reported per run: ms per step (compaction included), compaction time,
+    the largest and the final number of allocated Fish + Shark blocks (the
+    memory footprint; sampled every 10 steps outside the timed intervals),
+    and whether the final world equals the plain run's (placement does not
+    change the results)."""
+    import torch
+    from paper_1908_05845_gb300 import inputs
+    from paper_1908_05845_gb300.workloads import WaTor, heap_bytes_for
+    W = W_SIDE
+    T = 500
+    k0, a0, e0 = inputs.wator_initial(W, W, SEED)
+    stream = torch.cuda.Stream()
+    a, b = _events(stream)
+    out, ref = {}, None
+    for label, n in (("plain", 0), ("compact_every_50", 10), ("compact_every_50_n2", 2),
+                     ("compact_after_massive_deallocations", 10)):
+        with torch.cuda.stream(stream):
+            sim = WaTor(W, W, SEED, k0, a0, e0, heap_bytes=heap_bytes_for(W * W, 1.0), stream=stream)
+            F, S = sim.class_ids["Fish"], sim.class_ids["Shark"]
+            ms, t_compact, runs, passes, peak, blocks = 0.0, 0.0, 0, 0, 0, []
+            for t0 in range(0, T, 10):
+                torch.cuda.synchronize()
+                a.record(stream)
+                sim.step(10)
+                done = t0 + 10
+                for cls in (F, S):
+                    cs = None
+                    if label.startswith("compact_every_50") and done % 50 == 0:
+                        cs = sim.heap.compact(cls, n=n, k1=16)
+                    elif label == "compact_after_massive_deallocations":
+                        ran, cs = sim.heap.compact_if(cls, n=n, k1=16, k2_fraction=0.05)
+                        cs = cs if ran else None
+                    if cs is not None:
+                        runs += 1
+                        passes += cs["passes"]
+                        t_compact += cs["scan_ms"] + cs["copy_ms"] + cs["state_ms"] + cs["rewrite_ms"]
+                b.record(stream)
+                b.synchronize()
+                ms += a.elapsed_time(b)
+                st = sim.heap.stats()
+                nb = st["blocks"][F] + st["blocks"][S]
+                blocks.append(nb)
+                peak = max(peak, nb)
+            world = sim.read()
+            sim.sync()
+            sim.close()
+        same = True
+        if ref is None:
+            ref = world
+        else:
+            same = all(np.array_equal(x, y) for x, y in zip(world, ref))
+        out[label] = {"n": n, "ms_per_step": ms / T, "compactions": runs, "passes": passes,
+                      "compaction_ms_total": t_compact,
+                      "peak_blocks": peak, "final_blocks": blocks[-1],
+                      "mean_blocks": float(np.mean(blocks)), "world_equals_plain": bool(same)}
+    p = out["plain"]
+    for k, v in out.items():
+        v["slowdown_vs_plain"] = v["ms_per_step"] / p["ms_per_step"]
+        v["peak_memory_vs_plain"] = v["peak_blocks"] / p["peak_blocks"]
+    print(json.dumps({"metric": "ms/step", "value": p["ms_per_step"], "unit": "ms", "higher_is_better": False,
+                      "steps": T, "dtype": "int32/int16", "data": "synthetic (seeded Philox)",
+                      "config": {"workload": "wator_%dx%d_compaction" % (W, W), "n": 10, "k1": 16,
+                                 "k2_fraction": 0.05},
+                      "runs": out}), flush=True)
+    return 0 if all(v["world_equals_plain"] for v in out.values()) else 1
+
+
 def run_nasch(args):
     import torch
     from paper_1908_05845_gb300 import inputs
@@ -987,7 +1061,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="wator",
                     choices=["wator", "batched", "gol", "generation", "nasch", "nbody", "bh", "bfs", "alloc",
-                             "compact", "structure"])
+                             "compact", "structure", "wator_compact"])
     ap.add_argument("--bfs-check", type=int, default=1024)
     ap.add_argument("--struct-iters", type=int, default=100)
     ap.add_argument("--bh-bodies", type=int, default=65536)
@@ -1008,6 +1082,7 @@ def main():
         smmo.lib()
         return {"batched": run_batched, "gol": run_gol, "generation": run_generation, "nasch": run_nasch,
                 "nbody": run_nbody, "bh": run_bh, "bfs": run_bfs, "structure": run_structure,
+                "wator_compact": run_wator_compact,
                 "alloc": run_alloc, "compact": run_compact}[args.workload](args)
     return run_gpu(args, ws, rank, local)
 
