@@ -255,6 +255,15 @@ int smmo_gather_fields(smmo_heap* heap, int class_id, const smmo_handle* handles
 int smmo_compact(smmo_heap* heap, int class_id, int defrag_factor,
                  int64_t k1, smmo_compact_stats* out, void* stream);
 
+/* Rewrites n caller-held handles (device array) to where the last
+ * smmo_compact moved their objects (following its forwarding slots, as the
+ * rewrite of the heap's own HANDLE columns does; handles of objects that
+ * did not move are unchanged).  Valid until the next allocation: returns
+ * SMMO_E_UNSUPPORTED once a device new or bulk_new has run since that
+ * compaction (the freed source blocks may hold new objects).  Synchronises
+ * `stream`. */
+int smmo_remap_handles(smmo_heap* heap, smmo_handle* handles, int64_t n, void* stream);
+
 /* Number of defragmentation candidates of class_id for factor n (allocated
  * blocks holding at most floor(N_T n / (n + 1)) objects, Sec. 6.3.1) into
  * *count (host).  Synchronises `stream`. */
@@ -298,6 +307,11 @@ int smmo_heap_counters(smmo_heap* heap, int64_t* enumerated_objects,
  * refills, active-block lookups that found nothing, reservations that found
  * the chosen block full, blocks enumerated.  Synchronises `stream`. */
 int smmo_heap_alloc_counters(smmo_heap* heap, int64_t* out6, void* stream);
+
+/* Synchronises `stream` and reads the first device error recorded since the
+ * last smmo_heap_sync without clearing it: *code (host) = the status (0 =
+ * none), *detail (host, nullable) = its detail word. */
+int smmo_heap_last_device_error(smmo_heap* heap, int* code, uint64_t* detail, void* stream);
 
 /* Synchronises `stream` and returns the first device error recorded since
  * the last sync (then clears it).  *detail (host, nullable) receives the

@@ -461,6 +461,16 @@ extern "C" int smmo_compact(smmo_heap* h, int c, int n, int64_t k1, smmo_compact
     if (x) cudaEventDestroy(x);
   if (out) *out = st;
   if (status) return status;
+  if (e == cudaSuccess) {
+    // forwarding slots of this compaction stay readable until the next
+    // allocation: remember where the allocation counters stand
+    int64_t news = 0;
+    const int cst = smmo_heap_counters(h, nullptr, &news, nullptr, stream);
+    if (cst) return cst;
+    h->compact_passes = (uint32_t)st.passes;
+    h->compact_news = news;
+    h->compact_bulks = h->bulk_calls;
+  }
   return cuda_status(e);
 }
 
@@ -521,4 +531,33 @@ extern "C" int smmo_compact_if(smmo_heap* h, int c, int n, int64_t k1, int64_t k
   }
   if (ran) *ran = 1;
   return smmo_compact(h, c, n, k1, out, stream);
+}
+
+namespace {
+// Caller-held handles through the forwarding slots of the last compaction
+// (the same chain the rewrite follows, at most one hop per pass).
+__global__ void __launch_bounds__(256) k_remap(HeapView h, const unsigned long long* mf, uint32_t* hd, uint64_t n,
+                                               uint32_t max_hops) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t v = hd[i];
+    for (uint32_t hop = 0; hop < max_hops && was_source(h, mf, v); ++hop)
+      v = reinterpret_cast<const uint32_t*>(block_data(h, v >> 6))[v & 63];
+    hd[i] = v;
+  }
+}
+}  // namespace
+
+extern "C" int smmo_remap_handles(smmo_heap* h, uint32_t* handles, int64_t n, void* stream) {
+  if (!h || n < 0 || (n > 0 && !handles)) return SMMO_E_INVALID_ARG;
+  if (!h->frozen || h->compact_news < 0 || n == 0) return SMMO_OK;  // nothing was moved
+  int64_t news = 0;
+  int st = smmo_heap_counters(h, nullptr, &news, nullptr, stream);
+  if (st) return st;
+  if (news != h->compact_news || h->bulk_calls != h->compact_bulks) return SMMO_E_UNSUPPORTED;  // slots reused
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint32_t grid = (uint32_t)std::min<int64_t>((n + 255) / 256, (int64_t)h->num_sms * 8);
+  k_remap<<<grid, 256, 0, s>>>(h->view, h->d_moved, handles, (uint64_t)n, h->compact_passes);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return cuda_status(e);
 }

@@ -676,6 +676,7 @@ int smmo_bulk_new(smmo_heap* h, int c, int64_t n, const void* const* field_src,
   cudaStream_t s = (cudaStream_t)stream;
   int st = smmo::freeze(h, s);
   if (st) return st;
+  if (n > 0) ++h->bulk_calls;
   if (out_first_block) *out_first_block = -1;
   if (n == 0) return SMMO_OK;
   const ClassInfo& ci = h->classes[c];
@@ -905,6 +906,22 @@ int smmo_heap_check(smmo_heap* h, int64_t* violations, void* stream) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return smmo::cuda_status(e);
   *violations = (int64_t)v;
+  return SMMO_OK;
+}
+
+int smmo_heap_last_device_error(smmo_heap* h, int* code, uint64_t* detail, void* stream) {
+  if (!h || !code) return SMMO_E_INVALID_ARG;
+  *code = 0;
+  if (detail) *detail = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return smmo::cuda_status(e);
+  if (!h->frozen) return SMMO_OK;
+  struct { int err; int pad; unsigned long long detail; } hd;
+  e = cudaMemcpy(&hd, h->view.st, sizeof(hd), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return smmo::cuda_status(e);
+  *code = hd.err;
+  if (detail) *detail = hd.detail;
   return SMMO_OK;
 }
 

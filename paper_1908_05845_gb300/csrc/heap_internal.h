@@ -33,6 +33,11 @@ struct smmo_heap {
   smmo::ClassLayout* d_layouts = nullptr;  // inside buf
   uint32_t* d_scratch = nullptr;           // inside buf: num_blocks + 64 words
   unsigned long long* d_moved = nullptr;   // inside buf: one bit per block (compaction)
+  // the last compaction, for smmo_remap_handles: passes run, and the device
+  // news and bulk creations counted at its end (-1: no compaction yet)
+  uint32_t compact_passes = 0;
+  int64_t compact_news = -1, compact_bulks = -1;
+  int64_t bulk_calls = 0;                  // bulk_new calls that created objects
 };
 
 namespace smmo {

@@ -266,6 +266,21 @@ class Heap:
                                  _stream(self.stream)), "compact")
         return {k: getattr(cs, k) for k, _ in CompactStats._fields_}
 
+    def remap_handles(self, handles):
+        """Caller-held handles (int32/uint32 CUDA tensor, rewritten in place)
+        to where the last compact moved their objects."""
+        check(lib().smmo_remap_handles(self._h, ctypes.c_void_p(handles.data_ptr()), ctypes.c_int64(handles.numel()),
+                                       _stream(self.stream)), "remap_handles")
+        return handles
+
+    def last_device_error(self):
+        """(status, detail) of the first device error since the last sync,
+        without clearing it."""
+        code, detail = ctypes.c_int(), ctypes.c_uint64()
+        check(lib().smmo_heap_last_device_error(self._h, ctypes.byref(code), ctypes.byref(detail),
+                                                _stream(self.stream)), "last_device_error")
+        return code.value, detail.value
+
     def defrag_candidates(self, cls: int, n: int = 1) -> int:
         """Blocks of class cls at most n/(n+1) full."""
         v = ctypes.c_int64()

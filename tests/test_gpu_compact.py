@@ -207,3 +207,32 @@ def test_candidate_count_and_massive_deallocation_policy():
     h.sync()
     assert h.check() == 0 and h.stats()["live_objects"][A] == live
     assert h.defrag_candidates(A, n) < cand
+
+
+def test_remap_caller_handles_after_compaction():
+    """Handles held outside the heap follow the objects through a
+    multi-pass compaction (smmo_remap_handles); once an object is allocated
+    afterwards the forwarding slots may be gone and remap refuses."""
+    h = smmo.Heap(64 << 20)
+    A = h.register("A", [("v", smmo.I32), ("w", smmo.I32)])
+    n = 64 * 80
+    v = np.arange(n)
+    hd, _ = h.bulk_new(A, n, [cuda_i32(v), cuda_i32(np.zeros(n))], want_handles=True)
+    h.parallel_do(A, "test.free_self_if", smmo.FreeSelfIfArgs(0, 4, 1))
+    h.parallel_do(A, "test.free_self_if", smmo.FreeSelfIfArgs(0, 4, 2))
+    h.parallel_do(A, "test.free_self_if", smmo.FreeSelfIfArgs(0, 4, 3))
+    keep = v % 4 == 0
+    held = hd[torch.as_tensor(keep).cuda()].clone()
+    st = h.compact(A, n=3, k1=0)
+    h.sync()
+    assert st["passes"] >= 2 and st["objects_moved"] > 0
+    (before,) = h.gather(A, held, ["v"])  # stale handles: not all still name their object
+    assert not np.array_equal(before.cpu().numpy(), v[keep])
+    h.remap_handles(held)
+    (after,) = h.gather(A, held, ["v"])
+    assert np.array_equal(after.cpu().numpy(), v[keep])
+    code, _ = h.last_device_error()
+    assert code == 0
+    h.bulk_new(A, 64, [cuda_i32(np.arange(64)), cuda_i32(np.zeros(64))])
+    with pytest.raises(smmo.SmmoError):
+        h.remap_handles(held)
