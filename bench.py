@@ -87,15 +87,23 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.first = 0
 
     def start(self):
+        """Starts sampling every 50 ms and returns once the first sample is
+        in (nvidia-smi takes a while to start), so that the samples kept,
+        those after this call, lie inside the timed region."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.first = len(self.lines)
         except Exception:
             self.proc = None
 
@@ -113,7 +121,10 @@ class ClockSampler:
             self.proc.kill()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        # samples taken during the timed region; the one just before it if
+        # the region was shorter than the sampling interval
+        kept = self.lines[self.first:] or self.lines[max(0, self.first - 1):self.first]
+        for ln in kept:
             p = [x.strip() for x in ln.split(",")]
             if len(p) < 9:
                 continue
@@ -128,6 +139,23 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def reduce_over_ranks(t_local: float, objects: int, allocfree: int, device):
+    """Whole-job figures of the replicas: the largest timed interval over
+    the ranks and the objects (and allocations + frees) of all ranks."""
+    import torch
+    import torch.distributed as dist
+    v = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    o = torch.tensor([objects, allocfree], dtype=torch.float64, device=device)
+    dist.all_reduce(o)
+    return float(v.item()), int(o[0].item()), int(o[1].item())
+
+
+def replica_seed(rank: int) -> int:
+    """Seed of rank `rank`'s independent replica."""
+    return SEED + rank
 
 
 def dist_setup():
@@ -201,7 +229,7 @@ def run_gpu(args, ws, rank, local):
     except smmo.SmmoError:
         from paper_1908_05845_gb300 import build
         build.build()
-    seed = SEED + rank  # independent replicas
+    seed = replica_seed(rank)  # independent replicas
     k0, a0, e0 = inputs.wator_initial(W_SIDE, W_SIDE, seed)
     hb = heap_bytes_for(W_SIDE * W_SIDE, 1.0)
     stream = torch.cuda.current_stream()
@@ -251,13 +279,7 @@ def run_gpu(args, ws, rank, local):
     t_local = step_ms / 1e3
     t_max, objects_all, allocfree_all = t_local, objects, allocfree
     if ws > 1:
-        import torch.distributed as dist
-        v = torch.tensor([t_local], dtype=torch.float64, device="cuda")
-        dist.all_reduce(v, op=dist.ReduceOp.MAX)
-        t_max = float(v.item())
-        o = torch.tensor([objects, allocfree], dtype=torch.float64, device="cuda")
-        dist.all_reduce(o)
-        objects_all, allocfree_all = int(o[0].item()), int(o[1].item())
+        t_max, objects_all, allocfree_all = reduce_over_ranks(t_local, objects, allocfree, "cuda")
     value = objects_all / t_max
 
     # roofline of the dominant kernel
