@@ -663,6 +663,14 @@ int smmo_structure_export(smmo_structure* w, const smmo_structure_out* out, void
 int smmo_structure_info(smmo_structure* w, int* class_ids, int64_t* counters, void* stream);
 int smmo_structure_destroy(smmo_structure* w);
 
+/* FP32 add/multiply throughput of this GPU (the peak of the n-body
+ * force's roofline, whose fixed evaluation order uses no FMA): every SM
+ * full of threads running eight independent multiply-then-add chains for
+ * `iters` (1..2^20) iterations, timed with CUDA events.  *ops_per_s (host)
+ * = FP32 operations (one per multiply, one per add) per second.
+ * Synchronises `stream`. */
+int smmo_measure_fp32_peak(int iters, double* ops_per_s, void* stream);
+
 /* Self-test of a bounded wait: one CTA waits at a grid barrier that nothing
  * releases, for `spins` polls of about 100 ns (1..2^20), then records
  * SMMO_E_TIMEOUT (detail 2) in the heap's error word and returns; the

@@ -761,6 +761,27 @@ __global__ void k_selftest_fp32_rn(uint32_t lo, uint32_t hi, unsigned long long*
 }
 }  // namespace
 
+namespace {
+// FP32 add/multiply throughput: eight independent chains per thread of
+// x = x * m + c as a round-to-nearest multiply then add (two instructions,
+// never fused), enough warps to fill every SM.  The chains stay bounded
+// (m < 1) and the result is stored so that nothing is eliminated.
+__global__ void __launch_bounds__(256) k_fp32_peak(float* out, int iters) {
+  float x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = 1.0f + (float)(threadIdx.x + k) * 1e-3f;
+  const float m = 0.999999f, c = 1e-6f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = __fadd_rn(__fmul_rn(x[k], m), c);
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+}  // namespace
+
 extern "C" {
 
 int smmo_selftest_fp32_rn(uint32_t lo_bits, uint32_t hi_bits, uint64_t* out4, void* stream) {
@@ -791,6 +812,38 @@ int smmo_selftest_fp32_rn(uint32_t lo_bits, uint32_t hi_bits, uint64_t* out4, vo
   out4[1] = hc[1];
   out4[2] = hf[0];
   out4[3] = hf[1];
+  return SMMO_OK;
+}
+
+int smmo_measure_fp32_peak(int iters, double* ops_per_s, void* stream) {
+  if (!ops_per_s || iters < 1 || iters > (1 << 20)) return SMMO_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fp32_peak, 256, 0);
+  if (e != cudaSuccess) return cuda_status(e);
+  const int grid = sms * (per_sm > 0 ? per_sm : 1);
+  float* out = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  e = cudaMallocAsync(&out, sizeof(float) * (size_t)grid * 256, s);
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  float ms = 0.0f;
+  if (e == cudaSuccess) {
+    k_fp32_peak<<<grid, 256, 0, s>>>(out, iters < 64 ? iters : 64);  // warm-up
+    cudaEventRecord(a, s);
+    k_fp32_peak<<<grid, 256, 0, s>>>(out, iters);
+    cudaEventRecord(b, s);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (out) cudaFreeAsync(out, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  *ops_per_s = ms > 0.0f ? (double)grid * 256.0 * iters * 16.0 / (ms * 1e-3) : 0.0;
   return SMMO_OK;
 }
 

@@ -142,3 +142,15 @@ def test_branch_free_sqrt_and_reciprocal_are_correctly_rounded_on_their_ranges()
     # reciprocal where its result is subnormal, so the ranges are needed
     assert lib.smmo_selftest_fp32_rn(ctypes.c_uint32(0x00800000), ctypes.c_uint32(0x7F7FFFFF), out, s) == 0
     assert out[0] > 0 and out[1] > 0
+
+
+def test_measured_fp32_peak_is_near_the_unit_count():
+    """The FP32 microbenchmark behind the force kernel's roofline measures
+    between half and all of SMs x 128 lanes x the maximum SM clock."""
+    import ctypes
+    from paper_1908_05845_gb300 import smmo
+    ops = ctypes.c_double()
+    assert smmo.lib().smmo_measure_fp32_peak(4096, ctypes.byref(ops), None) == 0
+    props = torch.cuda.get_device_properties(0)
+    nominal = props.multi_processor_count * 128 * 2.07e9
+    assert 0.5 * nominal < ops.value < 1.05 * nominal, (ops.value, nominal)
