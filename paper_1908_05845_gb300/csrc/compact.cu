@@ -374,35 +374,43 @@ extern "C" int smmo_compact(smmo_heap* h, int c, int n, int64_t k1, smmo_compact
   cudaError_t e = cudaMemsetAsync(aux, 0, 6 * sizeof(unsigned long long), s);
   unsigned long long* moved_from = h->d_moved;  // sources of all passes, one bit per block
   if (e == cudaSuccess) e = cudaMemsetAsync(moved_from, 0, (size_t)nw * 8, s);
-  // phase timing: per pass, events at the pass start, after the scan, after
-  // copy and forwarding and after the state update
-  std::vector<cudaEvent_t> ev;
-  auto mark = [&]() {
-    cudaEvent_t x = nullptr;
-    if (cudaEventCreate(&x) == cudaSuccess) { cudaEventRecord(x, s); ev.push_back(x); }
-    else ev.push_back(nullptr);
-  };
   // passes are queued in groups of kGroup; the host looks at the control
   // block once per group (passes after the last real one return at once)
   const int kGroup = 4;
   const unsigned grel = (unsigned)h->num_sms * 8, gupd = (unsigned)h->num_sms * 4;
   int status = SMMO_OK;
   unsigned long long ctl[4] = {0, 0, 0, 0};
+  // phase timing: per pass, events at the pass start, after the scan, after
+  // copy and forwarding and after the state update; one set of events for a
+  // group, read after the group's synchronisation and reused
+  cudaEvent_t ev[4 * kGroup] = {};
+  for (auto& x : ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&x);
+  auto el = [&](int i, int j) -> double {
+    float ms = 0.0f;
+    return cudaEventElapsedTime(&ms, ev[i], ev[j]) == cudaSuccess ? (double)ms : 0.0;
+  };
   for (int queued = 0; queued < 1000 && e == cudaSuccess;) {
     for (int k = 0; k < kGroup; ++k, ++queued) {
-      mark();
+      cudaEventRecord(ev[4 * k], s);
       k_cand_scan1<<<nchunks, 1024, 0, s>>>(h->view, c, limit, part, aux);
       k_cand_scan2<<<1, 1024, 0, s>>>(part, nchunks, (uint32_t)n, (unsigned long long)k1, aux);
       k_cand_scan3<<<nchunks, 1024, 0, s>>>(h->view, c, part, R, aux);
-      mark();
+      cudaEventRecord(ev[4 * k + 1], s);
       k_relocate<<<grel, 256, 0, s>>>(h->view, c, R, (uint32_t)n, aux, aux + 4);
-      mark();
+      cudaEventRecord(ev[4 * k + 2], s);
       k_update_states<<<gupd, 256, 0, s>>>(h->view, c, R, (uint32_t)n, aux, moved_from);
-      mark();
+      cudaEventRecord(ev[4 * k + 3], s);
     }
     e = cudaMemcpyAsync(ctl, aux, sizeof(ctl), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess || ctl[0]) break;
+    if (e != cudaSuccess) break;
+    for (int k = 0; k < kGroup; ++k) {
+      st.scan_ms += el(4 * k, 4 * k + 1);
+      st.copy_ms += el(4 * k + 1, 4 * k + 2);
+      st.state_ms += el(4 * k + 2, 4 * k + 3);
+    }
+    if (ctl[0]) break;
   }
   st.passes = (int32_t)ctl[1];
   st.blocks_freed = (int64_t)ctl[2];
@@ -439,17 +447,6 @@ extern "C" int smmo_compact(smmo_heap* h, int c, int n, int64_t k1, smmo_compact
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     st.objects_moved = (int64_t)mv[0];
     st.pointers_rewritten = (int64_t)mv[1];
-  }
-  // phase times from the events (all complete after the synchronisation)
-  auto el = [&](size_t i, size_t j) -> double {
-    float ms = 0.0f;
-    if (j >= ev.size() || !ev[i] || !ev[j]) return 0.0;
-    return cudaEventElapsedTime(&ms, ev[i], ev[j]) == cudaSuccess ? (double)ms : 0.0;
-  };
-  for (size_t k = 0; k + 3 < ev.size(); k += 4) {
-    st.scan_ms += el(k, k + 1);
-    st.copy_ms += el(k + 1, k + 2);
-    st.state_ms += el(k + 2, k + 3);
   }
   if (rw0 && rw1) {
     float ms = 0.0f;
