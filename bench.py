@@ -998,10 +998,10 @@ def run_alloc(args):
     rows = []
     for n in [int(x) for x in args.alloc_n.split(",")]:
         nbytes = int(threads * n * 64 * 1.3) + (64 << 20)
-        # blocks sized for 64 objects of the 64-byte class (the driver class
-        # is smaller and would otherwise set the block size, Sec. 5.2.2)
+        # blocks sized for 64 objects of the 64-byte class (the spawning
+        # class is smaller and would otherwise set the block size, Sec. 5.2.2)
         h = smmo.Heap(nbytes, smmo.default_config(block_data_bytes=64 * 64))
-        D = h.register("Driver", [("v", smmo.I32)])
+        D = h.register("Spawner", [("v", smmo.I32)])
         O = h.register("Obj", [("w", smmo.I32, 16)])
         h.bulk_new(D, threads, [torch.arange(threads, dtype=torch.int32, device="cuda")])
         a, b = _events(None)
