@@ -874,6 +874,66 @@ def run_wator_compact(args):
     return 0 if all(v["world_equals_plain"] for v in out.values()) else 1
 
 
+def run_nbody_compact(args):
+    """CompactGpu on the n-body simulation with collisions (the thesis'
+    "collision" benchmark, Sec. 6.4): 65,536 bodies, 600 steps of force,
+    update and merge (merged bodies are deleted, so the body blocks empty
+    out), plain and with compact of the Body class every 50 steps at n = 10
+    and n = 36.  Reported per run: ms per step (compaction included), the
+    force pass of the last 50 steps, live bodies and Body blocks at the end;
+    the final state must equal the plain run's (forces are summed in id
+    order, so placement never changes a result)."""
+    import torch
+    from paper_1908_05845_gb300 import inputs
+    from paper_1908_05845_gb300.nbody import NBody
+    N, T = 65536, 600
+    st = inputs.nbody_initial(N, SEED)
+    stream = torch.cuda.Stream()
+    a, b = _events(stream)
+    out, ref = {}, None
+    for label, n in (("plain", 0), ("compact_every_50_n10", 10), ("compact_every_50_n36", 36)):
+        with torch.cuda.stream(stream):
+            w = NBody(st, merge_r=1e-2, stream=stream)
+            body = w.heap.class_id("Body")
+            ms, ms_last, t_compact, runs = 0.0, 0.0, 0.0, 0
+            for t0 in range(0, T, 50):
+                torch.cuda.synchronize()
+                a.record(stream)
+                w.step(50)
+                if n and t0 + 50 < T:
+                    cs = w.heap.compact(body, n=n, k1=0)
+                    t_compact += cs["scan_ms"] + cs["copy_ms"] + cs["state_ms"] + cs["rewrite_ms"]
+                    runs += 1
+                b.record(stream)
+                b.synchronize()
+                dt = a.elapsed_time(b)
+                ms += dt
+                if t0 + 50 == T:
+                    ms_last = dt / 50
+            hs = w.heap.stats()
+            got, merges = w.read()
+            w.close()
+        live = got["live"].astype(bool)
+        same = True
+        if ref is None:
+            ref = got
+        else:
+            same = bool(np.array_equal(live, ref["live"].astype(bool))
+                        and all(np.array_equal(got[k][live], ref[k][live]) for k in ("x", "y", "z", "vx", "vy", "vz", "m")))
+        out[label] = {"n": n, "ms_per_step": ms / T, "ms_per_step_last_50": ms_last, "compactions": runs,
+                      "compaction_ms_total": t_compact, "merges": int(merges), "live_end": int(live.sum()),
+                      "body_blocks_end": hs["blocks"][body], "fragmentation_end": hs["fragmentation"][body],
+                      "state_equals_plain": same}
+    p = out["plain"]
+    for v in out.values():
+        v["speedup_vs_plain"] = p["ms_per_step"] / v["ms_per_step"]
+    print(json.dumps({"metric": "ms/step", "value": p["ms_per_step"], "unit": "ms", "higher_is_better": False,
+                      "steps": T, "dtype": "f32", "data": "synthetic (seeded Philox)",
+                      "config": {"workload": "nbody_65536_collision_compaction", "merge_r": 1e-2},
+                      "runs": out}), flush=True)
+    return 0 if all(v["state_equals_plain"] for v in out.values()) else 1
+
+
 def run_nasch(args):
     import torch
     from paper_1908_05845_gb300 import inputs
@@ -930,6 +990,7 @@ def run_nbody(args):
     with torch.cuda.stream(stream):
         w = NBody(st, stream=stream)
         w.step(args.warmup)
+        p0 = w.pairs()
         a, b = _events(stream)
         torch.cuda.synchronize()
         a.record(stream)
@@ -937,6 +998,7 @@ def run_nbody(args):
         b.record(stream)
         b.synchronize()
         t = a.elapsed_time(b) / 1e3
+        pairs = float(w.pairs() - p0)  # live x live per step: merged bodies drop out
         got, merges = w.read()
         live = int(got["live"].sum())
         w.close()
@@ -953,7 +1015,6 @@ def run_nbody(args):
         b.synchronize()
         t_b = a.elapsed_time(b) / 1e3
         w.close()
-    pairs = float(N) * N * args.steps
     # ALU roofline of the force pass (no-merge forward with checkpoints,
     # which is the force kernel plus an O(N) drift): 19 FP32 operations per
     # pair (3 sub, 7 mul, 7 add, 1 sqrt, 1 div, each counted once; the
@@ -1095,7 +1156,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="wator",
                     choices=["wator", "batched", "gol", "generation", "nasch", "nbody", "bh", "bfs", "alloc",
-                             "compact", "structure", "wator_compact"])
+                             "compact", "structure", "wator_compact", "nbody_compact"])
     ap.add_argument("--bfs-check", type=int, default=1024)
     ap.add_argument("--struct-iters", type=int, default=100)
     ap.add_argument("--struct-cols", type=int, default=8192)
@@ -1118,7 +1179,7 @@ def main():
         smmo.lib()
         return {"batched": run_batched, "gol": run_gol, "generation": run_generation, "nasch": run_nasch,
                 "nbody": run_nbody, "bh": run_bh, "bfs": run_bfs, "structure": run_structure,
-                "wator_compact": run_wator_compact,
+                "wator_compact": run_wator_compact, "nbody_compact": run_nbody_compact,
                 "alloc": run_alloc, "compact": run_compact}[args.workload](args)
     return run_gpu(args, ws, rank, local)
 

@@ -536,6 +536,10 @@ int smmo_nbody_forward_ckpt(smmo_nbody* w, int nsteps, int ckpt, double* loss,
  * grad_v0 (device, n x 3 floats, id-indexed) receives dL/dv_0.  The body
  * state afterwards is that of the end of the first segment.  Asynchronous. */
 int smmo_nbody_backward(smmo_nbody* w, float* grad_v0, void* stream);
+/* Pair terms computed by all force passes so far (live bodies squared per
+ * pass: the force sums over the live bodies only) into *pairs (host).
+ * Synchronises `stream`. */
+int smmo_nbody_pairs(smmo_nbody* w, int64_t* pairs, void* stream);
 int smmo_nbody_destroy(smmo_nbody* w);
 
 /* ============================================================ Barnes-Hut

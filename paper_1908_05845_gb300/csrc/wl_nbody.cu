@@ -49,6 +49,8 @@ enum { CX, CY, CZ, CVX, CVY, CVZ, CM, CID, CLX, CLY, CLZ, CLVX, CLVY, CLVZ, NCOL
 
 struct NBodyArgs {
   float4* S;            // (x, y, z, m) by id
+  float4* Sd;           // the live entries of S in id order (force partners)
+  uint32_t* live;       // [0] live count; [1..] per-chunk offsets
   float4* A;            // (mu_x, mu_y, mu_z, 0) by id (adjoint)
   const float4* X1;     // mid-step (x, y, z, m) by id for the step being reversed
   uint32_t* hmap;       // handle by id
@@ -189,10 +191,11 @@ __global__ void __launch_bounds__(256) k_force(HeapView hv, uint32_t c, NBodyArg
       zi = F<float>(hv, self, a.off[CZ]);
     }
     const bool own_ok = eps_ok && abs_max_bits(xi, yi, zi) <= kCoordMaxBits;
-    for (uint32_t base = 0; base < a.n0; base += NB_TILE) {
+    const uint32_t nl = __ldcg(a.live);  // partners: the live bodies in id order
+    for (uint32_t base = 0; base < nl; base += NB_TILE) {
       __syncthreads();
       float4 q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      if (base + threadIdx.x < a.n0) q = a.S[base + threadIdx.x];
+      if (base + threadIdx.x < nl) q = a.Sd[base + threadIdx.x];
       tile[threadIdx.x] = q;
       const unsigned wm = __reduce_max_sync(0xFFFFFFFFu, abs_max_bits(q.x, q.y, q.z));
       if (lane == 0) tile_max[warp] = wm;
@@ -200,7 +203,7 @@ __global__ void __launch_bounds__(256) k_force(HeapView hv, uint32_t c, NBodyArg
       unsigned tm = 0;
 #pragma unroll
       for (int w = 0; w < NB_TILE / 32; ++w) tm = max(tm, tile_max[w]);
-      const uint32_t cnt = a.n0 - base < NB_TILE ? a.n0 - base : NB_TILE;
+      const uint32_t cnt = nl - base < NB_TILE ? nl - base : NB_TILE;
       if (live) {
         if (own_ok && tm <= kCoordMaxBits) force_tile<true>(tile, cnt, xi, yi, zi, a.eps2, ax, ay, az);
         else force_tile<false>(tile, cnt, xi, yi, zi, a.eps2, ax, ay, az);
@@ -219,6 +222,76 @@ __global__ void __launch_bounds__(256) k_force(HeapView hv, uint32_t c, NBodyArg
       F<float>(hv, self, a.off[CZ]) = fa(zi, fm(vz, a.h));
     }
   }
+}
+
+// ---- force partners: the live bodies in id order -------------------------
+// The force sums over live bodies in increasing id; dead ids hold zeros in
+// S (mass 0, an exact zero term).  These kernels pack the live entries of
+// S, in id order, into Sd: (1) live count per chunk of 1024 ids, (2) the
+// exclusive prefix over the chunks and the total, (3) every live entry to
+// its place.  The sum over Sd is the sum over S without its zero terms,
+// bit for bit (an accumulator that starts at +0 never becomes -0).
+__global__ void __launch_bounds__(1024) k_live_count(const float4* S, uint32_t n0, uint32_t* part) {
+  __shared__ uint32_t wsum[32];
+  const uint32_t i = blockIdx.x * 1024 + threadIdx.x;
+  const bool lv = i < n0 && S[i].w > 0.0f;
+  const unsigned bal = __ballot_sync(0xFFFFFFFFu, lv);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const uint32_t t = __reduce_add_sync(0xFFFFFFFFu, wsum[threadIdx.x]);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_live_scan(uint32_t* part, uint32_t nparts, uint32_t* total,
+                                                    unsigned long long* pairs) {
+  __shared__ uint32_t sh[1024];
+  uint32_t run = 0;
+  for (uint32_t base = 0; base < nparts; base += 1024) {
+    const uint32_t i = base + threadIdx.x;
+    const uint32_t v = i < nparts ? part[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (uint32_t o = 1; o < 1024; o <<= 1) {
+      const uint32_t x = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += x;
+      __syncthreads();
+    }
+    if (i < nparts) part[i] = run + sh[threadIdx.x] - v;
+    run += sh[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *total = run;
+    *pairs += (unsigned long long)run * run;  // pair terms of this force pass
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_live_scatter(const float4* S, uint32_t n0, const uint32_t* part,
+                                                       float4* Sd) {
+  __shared__ uint32_t wsum[32];
+  const uint32_t i = blockIdx.x * 1024 + threadIdx.x;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  if (i < n0) v = S[i];
+  const bool lv = i < n0 && v.w > 0.0f;
+  const unsigned bal = __ballot_sync(0xFFFFFFFFu, lv);
+  if (lane == 0) wsum[warp] = __popc(bal);
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t c = wsum[lane];
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= (uint32_t)o) incl += x;
+    }
+    wsum[lane] = incl - c;
+  }
+  __syncthreads();
+  if (lv) Sd[part[blockIdx.x] + wsum[warp] + __popc(bal & ((1u << lane) - 1))] = v;
 }
 
 // ---- merge search on a hashed uniform grid (cell edge >= R) -------------
@@ -552,6 +625,9 @@ struct smmo_nbody {
   smmo_nbody_params p{};
   NBodyArgs args{};
   float4* d_S = nullptr;
+  float4* d_Sd = nullptr;      // live entries of d_S in id order
+  uint32_t* d_live = nullptr;  // count | per-chunk offsets
+  unsigned long long* d_pairs = nullptr;  // pair terms computed by the force passes
   float4* d_A = nullptr;
   uint32_t* d_hmap = nullptr;
   uint32_t* d_tgt = nullptr;
@@ -585,6 +661,10 @@ int dkd_step(smmo_nbody* w, cudaStream_t s, float4* x1) {
     e = cudaMemcpyAsync(x1, w->d_S, sizeof(float4) * w->n0, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_status(e);
   }
+  const uint32_t nch = (w->n0 + 1023) / 1024;
+  k_live_count<<<nch, 1024, 0, s>>>(w->d_S, w->n0, w->d_live + 1);
+  k_live_scan<<<1, 1024, 0, s>>>(w->d_live + 1, nch, w->d_live, w->d_pairs);
+  k_live_scatter<<<nch, 1024, 0, s>>>(w->d_S, w->n0, w->d_live + 1, w->d_Sd);
   k_force<<<tiled_grid(w->heap), 256, 0, s>>>(w->heap->view, w->cls, a);
   return cuda_status(cudaGetLastError());
 }
@@ -609,6 +689,10 @@ int smmo_nbody_create(smmo_heap* heap, int64_t n, const float* const* cols,
   if (!st) st = freeze(heap, s);
   if (st) { delete w; return st; }
   cudaError_t e = cudaMalloc(&w->d_S, sizeof(float4) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w->d_Sd, sizeof(float4) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w->d_live, sizeof(uint32_t) * (1 + ((size_t)n + 1023) / 1024));
+  if (e == cudaSuccess) e = cudaMalloc(&w->d_pairs, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(w->d_pairs, 0, sizeof(unsigned long long), s);
   if (e == cudaSuccess) e = cudaMalloc(&w->d_A, sizeof(float4) * n);
   if (e == cudaSuccess) e = cudaMalloc(&w->d_hmap, sizeof(uint32_t) * n);
   if (e == cudaSuccess) e = cudaMalloc(&w->d_tgt, sizeof(uint32_t) * n);
@@ -634,7 +718,7 @@ int smmo_nbody_create(smmo_heap* heap, int64_t n, const float* const* cols,
   if (st) { smmo_nbody_destroy(w); return st; }
   NBodyArgs& a = w->args;
   memset(&a, 0, sizeof(a));
-  a.S = w->d_S; a.A = w->d_A; a.hmap = w->d_hmap; a.tgt = w->d_tgt; a.ke = w->d_ke;
+  a.S = w->d_S; a.Sd = w->d_Sd; a.live = w->d_live; a.A = w->d_A; a.hmap = w->d_hmap; a.tgt = w->d_tgt; a.ke = w->d_ke;
   a.merges = w->d_merges;
   a.n0 = (uint32_t)n;
   a.G = p->G;
@@ -788,7 +872,7 @@ int smmo_nbody_backward(smmo_nbody* w, float* grad_v0, void* stream) {
 
 int smmo_nbody_destroy(smmo_nbody* w) {
   if (!w) return SMMO_E_INVALID_ARG;
-  cudaFree(w->d_S); cudaFree(w->d_A); cudaFree(w->d_hmap); cudaFree(w->d_tgt);
+  cudaFree(w->d_S); cudaFree(w->d_Sd); cudaFree(w->d_live); cudaFree(w->d_pairs); cudaFree(w->d_A); cudaFree(w->d_hmap); cudaFree(w->d_tgt);
   cudaFree(w->d_ke); cudaFree(w->d_merges);
   if (w->d_grid) cudaFree(w->d_grid);
   if (w->d_ckpt) cudaFree(w->d_ckpt);
@@ -897,6 +981,17 @@ int smmo_measure_fp32_peak(int iters, double* ops_per_s, void* stream) {
   if (out) cudaFreeAsync(out, s);
   if (e != cudaSuccess) return cuda_status(e);
   *ops_per_s = ms > 0.0f ? (double)grid * 256.0 * iters * 16.0 / (ms * 1e-3) : 0.0;
+  return SMMO_OK;
+}
+
+int smmo_nbody_pairs(smmo_nbody* w, int64_t* pairs, void* stream) {
+  if (!w || !pairs) return SMMO_E_INVALID_ARG;
+  unsigned long long v = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(&v, w->d_pairs, sizeof(v), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  *pairs = (int64_t)v;
   return SMMO_OK;
 }
 

@@ -37,6 +37,12 @@ class NBody:
                                                 ctypes.byref(self.params), smmo._stream(stream),
                                                 ctypes.byref(self._w)), "nbody_create")
 
+    def pairs(self) -> int:
+        """Pair terms computed by the force passes so far."""
+        v = ctypes.c_int64()
+        smmo.check(smmo.lib().smmo_nbody_pairs(self._w, ctypes.byref(v), smmo._stream(self.stream)), "nbody_pairs")
+        return v.value
+
     def step(self, n: int = 1):
         smmo.check(smmo.lib().smmo_nbody_step(self._w, n, smmo._stream(self.stream)), "nbody_step")
 

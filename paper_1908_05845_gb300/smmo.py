@@ -177,6 +177,11 @@ class Heap:
     def column_index(self, cls: int, name: str) -> int:
         return [c[0] for c in self.columns(cls)].index(name)
 
+    def class_id(self, name: str) -> int:
+        c = ctypes.c_int()
+        check(lib().smmo_class_lookup(self._h, name.encode(), ctypes.byref(c)), "class_lookup")
+        return c.value
+
     def freeze(self):
         check(lib().smmo_heap_freeze(self._h), "heap_freeze")
 
