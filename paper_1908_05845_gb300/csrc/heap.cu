@@ -58,27 +58,38 @@ __global__ void k_fill_bitmap(unsigned long long* w, uint32_t nwords, uint64_t n
 
 // Enumeration of the allocated blocks of class c into h.R (the thesis'
 // indices(), Alg. 5.5, with the iteration-bitmap snapshot fused in).  One
-// warp per level-0 container (64 blocks): the level-1 bit is tested first so
-// empty regions of the heap are skipped without reading level 0; a
-// non-empty container reserves its output slots with one atomicAdd and its
-// two halves are written by the 32 lanes (block index + bitmap snapshot).
+// warp per level-0 container (64 blocks) per round: the level-1 bit is
+// tested first so empty regions of the heap are skipped without reading
+// level 0; the CTA sums its eight containers' blocks and reserves their
+// output slots with one atomicAdd (one per container would serialise on the
+// counter), and the two halves of a container are written by the 32 lanes
+// (block index, class, bitmap snapshot).
 __global__ void __launch_bounds__(256) k_enumerate(HeapView h, int c) {
+  __shared__ uint32_t wcnt[8], wbase[8], cbase;
   const unsigned long long* L0 = bm_level(h, bm_alloc(h, c), 0);
   const unsigned long long* L1 = h.nlevels > 1 ? bm_level(h, bm_alloc(h, c), 1) : nullptr;
   const uint32_t nw = h.level_words[0];
   const unsigned long long capmask = h.cls[c].capmask;
-  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t rounds = (nw + nwarps - 1) / nwarps;  // the same in every CTA
   const unsigned lt = (1u << lane) - 1;
   uint32_t objs = 0, blks = 0;
-  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += nwarps) {
-    if (L1 && !((L1[w >> 6] >> (w & 63)) & 1)) continue;
-    const unsigned long long word = L0[w];
+  for (uint32_t r = 0; r < rounds; ++r) {
+    const uint32_t w = r * nwarps + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    unsigned long long word = 0;
+    if (w < nw && (!L1 || ((L1[w >> 6] >> (w & 63)) & 1))) word = L0[w];
+    if (lane == 0) wcnt[warp] = (uint32_t)__popcll(word);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t tot = 0;
+      for (int i = 0; i < 8; ++i) { wbase[i] = tot; tot += wcnt[i]; }
+      cbase = tot ? atomicAdd(h.rcnt, tot) : 0u;
+    }
+    __syncthreads();
     if (word == 0) continue;
     const uint32_t lo = (uint32_t)word, hi = (uint32_t)(word >> 32);
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(h.rcnt, (uint32_t)__popcll(word));
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    const uint32_t base = cbase + wbase[warp];
     unsigned long long b0 = 0, b1 = 0;
     if ((lo >> lane) & 1) b0 = __ldcg(h.alloc_bm + w * 64 + lane) & capmask;
     if ((hi >> lane) & 1) b1 = __ldcg(h.alloc_bm + w * 64 + 32 + lane) & capmask;
