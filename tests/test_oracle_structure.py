@@ -280,3 +280,34 @@ def test_mesh_run_bookkeeping(orc, seed):
     anc = g["kind"] == A
     assert np.array_equal(st["x"][anc], g["x"][anc]) and np.array_equal(st["y"][anc], g["y"][anc])
     assert (st["dist"][live] != 0x7FFFFFFF).all()
+
+
+@pytest.mark.parametrize("rows,cols,seed", [(8, 12, 1), (33, 65, 2)])
+def test_mesh_recipe(rows, cols, seed):
+    """The brick-wall input: degree at most 3 (exactly the lattice links
+    that were kept), right links everywhere but the last column, up links
+    where r + c is even, every node keeps a spring, kinds by row, slots in
+    increasing spring id naming exactly the node's springs, rest lengths the
+    float distance, about 90 % of the candidate links kept."""
+    g = inputs.structure_mesh(rows, cols, seed)
+    n, S = rows * cols, len(g["p1"])
+    p1, p2 = g["p1"].astype(np.int64), g["p2"].astype(np.int64)
+    r1, c1 = p1 // cols, p1 % cols
+    right = (p2 == p1 + 1) & (c1 + 1 < cols)
+    up = (p2 == p1 + cols) & ((r1 + c1) % 2 == 0)
+    assert (right | up).all()
+    assert np.array_equal(np.argsort(p1 * 2 + up, kind="stable"), np.arange(S))  # candidate order
+    deg = np.bincount(np.concatenate([p1, p2]), minlength=n)
+    assert deg.max() <= 3 and deg.min() >= 1 and np.array_equal(deg, g["nspr"])
+    for v in range(n):
+        mine = np.nonzero((p1 == v) | (p2 == v))[0]
+        sl = g["slot"][v]
+        assert np.array_equal(sl[:len(mine)], mine) and (sl[len(mine):] == -1).all()
+    r = np.arange(n) // cols
+    assert (g["kind"][r == 0] == A).all() and (g["kind"][r == rows - 1] == P).all()
+    assert (g["kind"][(r > 0) & (r < rows - 1)] == N_).all()
+    d = np.hypot(g["x"][p2].astype(np.float64) - g["x"][p1], g["y"][p2].astype(np.float64) - g["y"][p1])
+    assert np.array_equal(g["L0"], d.astype(np.float32))
+    cand = rows * (cols - 1) + sum(1 for rr in range(rows - 1) for cc in range(cols) if (rr + cc) % 2 == 0)
+    assert 0.8 < S / cand < 0.97
+    assert (g["vy"][g["kind"] == P] > 0).all() and (g["vy"][g["kind"] != P] == 0).all()
