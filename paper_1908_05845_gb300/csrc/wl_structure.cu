@@ -112,9 +112,21 @@ struct PullMove {
   }
 };
 
+// The compute phase runs over one snapshot per class per iteration (no
+// object is created during it): an object deleted since the snapshot (a
+// broken spring, a node left without springs) is skipped by this test.  A
+// block whose last object was freed keeps an all-ones slot bitmap (it is
+// invalidated) but has left the class's allocated bitmap, hence both tests;
+// every deletion it could see finished in an earlier do-all (a spring
+// deletes only itself, nodes are deleted in the spring pass).
+__device__ __forceinline__ bool still_allocated(const HeapView& h, uint32_t c, uint32_t self) {
+  return bm_get(h, bm_alloc(h, c), self >> 6) && ((ld_cg(h.alloc_bm + (self >> 6)) >> (self & 63)) & 1);
+}
+
 struct SpringForce {
   using Args = StructArgs;
   __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
+    if (!still_allocated(h, c, self)) return;
     const uint32_t p1 = *F<uint32_t>(h, c, self, S_P1), p2 = *F<uint32_t>(h, c, self, S_P2);
     const float dx = fs(*NB<float>(h, a, p2, N_X), *NB<float>(h, a, p1, N_X));
     const float dy = fs(*NB<float>(h, a, p2, N_Y), *NB<float>(h, a, p1, N_Y));
@@ -139,6 +151,7 @@ struct SpringForce {
 struct NodeMove {
   using Args = StructArgs;
   __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
+    if (!still_allocated(h, c, self)) return;
     float sx = 0.0f, sy = 0.0f;
     for (int i = 0; i < 3; ++i) {
       const uint32_t s = *F<uint32_t>(h, c, self, N_SPR + i);
@@ -316,6 +329,7 @@ struct smmo_structure {
   unsigned int* d_arrive = nullptr;       // grid barrier counter
   int flags_cap = 0;
   smmo::Snapshot nodes;                 // all node classes (one POLY snapshot)
+  smmo::Snapshot springs, free_nodes;   // the compute phase's snapshots
   int64_t bfs_levels = 0;               // levels run (statistics)
   int64_t bfs_launches = 0;
 };
@@ -560,11 +574,16 @@ int smmo_structure_step(smmo_structure* w, int iterations, int phases, void* str
   for (int it = 0; it < iterations; ++it) {
     int st = SMMO_OK;
     if (phases & SMMO_STRUCT_PHASE_PULL) st = pdo(w, w->cls_pull, &launch_do_all<PullMove>, a, s);
-    if (phases & SMMO_STRUCT_PHASE_COMPUTE)
+    if ((phases & SMMO_STRUCT_PHASE_COMPUTE) && w->substeps > 0 && !st) {
+      // one snapshot of each class for all compute steps: breaks only
+      // delete, and the methods skip what was deleted since
+      st = w->springs.take(w->heap, w->cls_spring, s);
+      if (!st) st = w->free_nodes.take(w->heap, w->cls_node, s);
       for (int k = 0; k < w->substeps && !st; ++k) {
-        st = pdo(w, w->cls_spring, &launch_do_all<SpringForce>, a, s);
-        if (!st) st = pdo(w, w->cls_node, &launch_do_all<NodeMove>, a, s);
+        st = launch_do_all_view<SpringForce>(w->heap, w->cls_spring, &a, s, &w->springs.view);
+        if (!st) st = launch_do_all_view<NodeMove>(w->heap, w->cls_node, &a, s, &w->free_nodes.view);
       }
+    }
     if (!st && (phases & SMMO_STRUCT_PHASE_REMOVE)) st = remove_disconnected(w, s);
     if (st) return st;
   }
@@ -628,6 +647,8 @@ int smmo_structure_destroy(smmo_structure* w) {
   if (w->d_flags) cudaFree(w->d_flags);
   if (w->d_arrive) cudaFree(w->d_arrive);
   w->nodes.release();
+  w->springs.release();
+  w->free_nodes.release();
   delete w;
   return SMMO_OK;
 }
