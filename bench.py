@@ -1030,6 +1030,8 @@ def run_nbody(args):
     ops = ctypes.c_double()
     smmo.check(smmo.lib().smmo_measure_fp32_peak(8192, ctypes.byref(ops), smmo._stream(None)), "fp32_peak")
     peak_tops = ops.value / 1e12
+    mufu = ctypes.c_double()
+    smmo.check(smmo.lib().smmo_measure_mufu_peak(4096, ctypes.byref(mufu), smmo._stream(None)), "mufu_peak")
     fwd_pairs_per_s = float(N) * N * 50 / t_f
     ach_tops = fwd_pairs_per_s * 19 / 1e12
     print(json.dumps({"metric": "pair-interactions/s", "value": pairs / t, "unit": "pairs/s",
@@ -1042,6 +1044,10 @@ def run_nbody(args):
                                    "peak_source": "measured: FP32 multiply-then-add chains on every SM "
                                                   "(smmo_measure_fp32_peak)",
                                    "peak_derived": derived_tops,
+                                   # the two hardware approximations per pair against the
+                                   # special-function pipe's measured rate
+                                   "mufu_peak_per_s": mufu.value,
+                                   "mufu_frac": fwd_pairs_per_s * 2 / mufu.value if mufu.value else None,
                                    "peak_derived_source": "%d SMs x 128 FP32 lanes x %.0f MHz"
                                                           % (props.multi_processor_count, mhz)},
                       "config": {"workload": "nbody_65536_merge",

@@ -674,6 +674,11 @@ int smmo_structure_destroy(smmo_structure* w);
  * = FP32 operations (one per multiply, one per add) per second.
  * Synchronises `stream`. */
 int smmo_measure_fp32_peak(int iters, double* ops_per_s, void* stream);
+/* Special-function (reciprocal square root) throughput, measured the same
+ * way with eight independent chains of the hardware approximation per
+ * thread: *ops_per_s (host) = approximations per second.  The force kernel
+ * issues two per pair (square root and reciprocal). */
+int smmo_measure_mufu_peak(int iters, double* ops_per_s, void* stream);
 
 /* Self-test of a bounded wait: one CTA waits at a grid barrier that nothing
  * releases, for `spins` polls of about 100 ns (1..2^20), then records

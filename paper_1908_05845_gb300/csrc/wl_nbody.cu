@@ -917,6 +917,52 @@ __global__ void __launch_bounds__(256) k_fp32_peak(float* out, int iters) {
   for (int k = 0; k < 8; ++k) s += x[k];
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
+// Special-function throughput: eight independent chains per thread of the
+// hardware reciprocal square root (x -> rsqrt(x) stays near 1).
+__global__ void __launch_bounds__(256) k_mufu_peak(float* out, int iters) {
+  float x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = 1.5f + (float)(threadIdx.x + k) * 1e-3f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) asm volatile("rsqrt.approx.f32 %0, %0;" : "+f"(x[k]));
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <class K>
+int time_peak(K kernel, int iters, double ops_per_thread_iter, double* ops_per_s, cudaStream_t s) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0);
+  if (e != cudaSuccess) return cuda_status(e);
+  const int grid = sms * (per_sm > 0 ? per_sm : 1);
+  float* out = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  e = cudaMallocAsync(&out, sizeof(float) * (size_t)grid * 256, s);
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  float ms = 0.0f;
+  if (e == cudaSuccess) {
+    kernel<<<grid, 256, 0, s>>>(out, iters < 64 ? iters : 64);  // warm-up
+    cudaEventRecord(a, s);
+    kernel<<<grid, 256, 0, s>>>(out, iters);
+    cudaEventRecord(b, s);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (out) cudaFreeAsync(out, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  *ops_per_s = ms > 0.0f ? (double)grid * 256.0 * iters * ops_per_thread_iter / (ms * 1e-3) : 0.0;
+  return SMMO_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -954,34 +1000,12 @@ int smmo_selftest_fp32_rn(uint32_t lo_bits, uint32_t hi_bits, uint64_t* out4, vo
 
 int smmo_measure_fp32_peak(int iters, double* ops_per_s, void* stream) {
   if (!ops_per_s || iters < 1 || iters > (1 << 20)) return SMMO_E_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fp32_peak, 256, 0);
-  if (e != cudaSuccess) return cuda_status(e);
-  const int grid = sms * (per_sm > 0 ? per_sm : 1);
-  float* out = nullptr;
-  cudaEvent_t a = nullptr, b = nullptr;
-  e = cudaMallocAsync(&out, sizeof(float) * (size_t)grid * 256, s);
-  if (e == cudaSuccess) e = cudaEventCreate(&a);
-  if (e == cudaSuccess) e = cudaEventCreate(&b);
-  float ms = 0.0f;
-  if (e == cudaSuccess) {
-    k_fp32_peak<<<grid, 256, 0, s>>>(out, iters < 64 ? iters : 64);  // warm-up
-    cudaEventRecord(a, s);
-    k_fp32_peak<<<grid, 256, 0, s>>>(out, iters);
-    cudaEventRecord(b, s);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = cudaEventSynchronize(b);
-  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-  if (a) cudaEventDestroy(a);
-  if (b) cudaEventDestroy(b);
-  if (out) cudaFreeAsync(out, s);
-  if (e != cudaSuccess) return cuda_status(e);
-  *ops_per_s = ms > 0.0f ? (double)grid * 256.0 * iters * 16.0 / (ms * 1e-3) : 0.0;
-  return SMMO_OK;
+  return time_peak(k_fp32_peak, iters, 16.0, ops_per_s, (cudaStream_t)stream);
+}
+
+int smmo_measure_mufu_peak(int iters, double* ops_per_s, void* stream) {
+  if (!ops_per_s || iters < 1 || iters > (1 << 20)) return SMMO_E_INVALID_ARG;
+  return time_peak(k_mufu_peak, iters, 8.0, ops_per_s, (cudaStream_t)stream);
 }
 
 int smmo_nbody_pairs(smmo_nbody* w, int64_t* pairs, void* stream) {

@@ -154,3 +154,15 @@ def test_measured_fp32_peak_is_near_the_unit_count():
     props = torch.cuda.get_device_properties(0)
     nominal = props.multi_processor_count * 128 * 2.07e9
     assert 0.5 * nominal < ops.value < 1.05 * nominal, (ops.value, nominal)
+
+
+def test_measured_special_function_peak_is_below_the_fp32_rate():
+    """The special-function pipe (one reciprocal square root per lane and
+    instruction) is a fraction of the FP32 rate: between 1 T/s and half of
+    the FP32 add/multiply rate."""
+    import ctypes
+    from paper_1908_05845_gb300 import smmo
+    mufu, fp32 = ctypes.c_double(), ctypes.c_double()
+    assert smmo.lib().smmo_measure_mufu_peak(2048, ctypes.byref(mufu), None) == 0
+    assert smmo.lib().smmo_measure_fp32_peak(2048, ctypes.byref(fp32), None) == 0
+    assert 1e12 < mufu.value < 0.5 * fp32.value, (mufu.value, fp32.value)
