@@ -220,3 +220,40 @@ def test_generation_graph_replay_and_rule_switch(orc):
     g.close()
     lk, ls, _ = orc.gol_run(W, H, k0, s0, 30)
     assert np.array_equal(k, lk) and np.array_equal(s, ls) and not b.any()
+
+
+@pytest.mark.parametrize("kind", [WATOR, LIFE])
+def test_thousand_small_tori_in_one_batched_world(orc, kind):
+    """1,000 independent 8 x 8 and 16 x 16 tori (500 each, instance i draws
+    with instance id i) stepped together in one batched heap; every one
+    equals the oracle's run of that instance alone."""
+    sides = np.array([8] * 500 + [16] * 500, np.int32)
+    n = len(sides)
+    seed = 11
+    ks, ags, ens, sts = [], [], [], []
+    for i, sd in enumerate(sides):
+        if kind == LIFE:
+            k, s = inputs.gol_initial(int(sd), int(sd), seed, inst=i, p=(3, 10))
+            a, e = np.zeros(sd * sd, np.int16), np.zeros(sd * sd, np.int16)
+        else:
+            k, a, e = inputs.wator_initial(int(sd), int(sd), seed, inst=i)
+            s = np.zeros(sd * sd, np.uint8)
+        ks.append(k.astype(np.int8)); ags.append(a); ens.append(e); sts.append(s)
+    w = World([kind] * n, sides, sides, seed, np.concatenate(ks), np.concatenate(ags), np.concatenate(ens),
+              np.concatenate(sts))
+    T = 30
+    w.step(T)
+    k, a, e, s, err = w.export()
+    assert err == 0
+    assert w.heap.check() == 0
+    w.sync()
+    w.close()
+    for i, sd in enumerate(sides):
+        gk, ga, ge, gs = (w.split(x)[i] for x in (k, a, e, s))
+        sd = int(sd)
+        if kind == LIFE:
+            wk, ws, _ = orc.gol_run(sd, sd, ks[i].astype(np.uint8), sts[i], T)
+            assert np.array_equal(gk.astype(np.uint8), wk) and np.array_equal(gs, ws), i
+        else:
+            wk, wa, we, _ = orc.wator_run(sd, sd, seed, ks[i], ags[i], ens[i], T, inst=i)
+            assert np.array_equal(gk, wk) and np.array_equal(ga, wa) and np.array_equal(ge, we), i
