@@ -54,3 +54,36 @@ def test_create_rejects_bad_args(libsmmo):
     # misaligned buffer pointer is rejected before any CUDA call
     assert libsmmo.smmo_heap_create(None, ctypes.c_void_p(0x1001), ctypes.c_size_t(1 << 20), None,
                                     ctypes.byref(h)) == -1
+
+
+def test_every_workload_method_is_registered(libsmmo):
+    """Each workload's compiled-in methods are found by name (the method
+    table is host data: no GPU needed)."""
+    mid = ctypes.c_int()
+    for name in (b"wator.fish_update", b"gol.candidate_prepare", b"bh.body_insert",
+                 b"bfs.vertex_visit", b"structure.spring_compute_force", b"structure.node_visit",
+                 b"structure.spring_delete", b"test.value_i32"):
+        assert libsmmo.smmo_method_lookup(name, ctypes.byref(mid)) == 0, name
+
+
+def test_entry_points_reject_null_objects(libsmmo):
+    """Argument checks that run on the host before any CUDA call."""
+    c = ctypes.c_int64()
+    d = ctypes.c_double()
+    ran = ctypes.c_int()
+    assert libsmmo.smmo_compact(None, 0, 1, ctypes.c_int64(0), None, None) == -1
+    assert libsmmo.smmo_compact_if(None, 0, 1, ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_double(0.0), None,
+                                   ctypes.byref(ran), None) == -1
+    assert ran.value == 0
+    assert libsmmo.smmo_defrag_candidates(None, 0, 1, ctypes.byref(c), None) == -1
+    assert libsmmo.smmo_remap_handles(None, None, ctypes.c_int64(0), None) == -1
+    assert libsmmo.smmo_heap_last_device_error(None, None, None, None) == -1
+    assert libsmmo.smmo_parallel_do_and_reduce(None, 0, 0, None, ctypes.c_size_t(0), 0, None, None) == -1
+    assert libsmmo.smmo_bfs_run(None, 0, 16, None, None) == -1
+    assert libsmmo.smmo_structure_step(None, 1, 7, None) == -1
+    assert libsmmo.smmo_structure_create(None, ctypes.c_int64(1), None, None, None, ctypes.c_int64(0), None, None,
+                                         None, None, None, None) == -1
+    assert libsmmo.smmo_bh_step(None, 1, None) == -1
+    assert libsmmo.smmo_measure_fp32_peak(0, ctypes.byref(d), None) == -1
+    assert libsmmo.smmo_measure_mufu_peak(1, None, None) == -1
+    assert libsmmo.smmo_selftest_barrier_timeout(None, 16, None) == -1
