@@ -8,7 +8,9 @@
 // vertex at distance f lowers every neighbour whose distance exceeds f + 1
 // to f + 1 and returns whether it changed one; the OR of the results tells
 // whether level f + 1 is non-empty.  Racing writers of a neighbour write
-// the same value, so distances do not depend on timing.
+// the same value, so distances do not depend on timing.  The vertex set is
+// fixed during a search: one snapshot serves every level, and the levels
+// run check_every at a time in one cooperative launch (levels.cuh).
 #include <cuda_runtime.h>
 
 #include <cstring>

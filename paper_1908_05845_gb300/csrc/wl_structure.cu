@@ -17,11 +17,15 @@
 //               Node::update: the sum of its springs' forces in slot order
 //                 (+f as p1, -f as p2), v = (v + F/m dt) (1 - damping),
 //                 x += v dt;
-//   remove    distance 0 at AnchorNodes, infinity elsewhere; one
-//             parallel_do_and_reduce (OR of "was in the frontier") per BFS
-//             level over all node classes; NodeBase::delete_node flags the
+//   remove    distance 0 at AnchorNodes, infinity elsewhere; BFS level l
+//             is parallel_do_and_reduce of NodeBase::visit(l) (OR of "was
+//             in the frontier") over all node classes, the levels of a
+//             search run in one cooperative launch (levels.cuh) over one
+//             snapshot of the node classes; NodeBase::delete_node flags the
 //             springs of unreached nodes; Spring::delete_spring removes the
 //             flagged springs from their endpoints and deletes them.
+// The compute phase, which deletes but never creates, runs over one
+// snapshot per class per iteration; its methods skip objects deleted since.
 // FP32 with round-to-nearest intrinsics in the order above: results equal
 // the CPU oracle bit for bit.  A node is deleted only after every spring
 // that names it is gone, so no thread reads a deleted node.
