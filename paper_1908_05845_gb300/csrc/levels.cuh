@@ -22,7 +22,7 @@ namespace smmo {
 constexpr unsigned kLevelBarrierSpins = 1u << 23;  // x ~100 ns: about a second
 constexpr int kLevelChunk = 4;                     // units tested at once per warp
 
-constexpr int kLevelThreads = 768;                 // CTA size: 2 CTAs of 24 warps per SM
+constexpr int kLevelThreads = 1024;                // CTA size: one CTA of 32 warps per SM (fewest arrivals)
 constexpr int kBarrierWords = 64;                  // arrive[0] counter, arrive[32] release word
 
 // Barrier across the grid's CTAs: arrive[0] counts arrivals (zeroed before
@@ -66,7 +66,7 @@ __device__ __forceinline__ bool grid_barrier(const HeapView& h, unsigned int* ar
 // so the locality of contiguous runs does not matter).  flags[k] (zeroed before the launch) receives the OR of level
 // base + k.
 template <class M, bool POLY>
-__global__ void __launch_bounds__(kLevelThreads, 2) levels_kernel(HeapView h, uint32_t c, typename M::Args args, int32_t base,
+__global__ void __launch_bounds__(kLevelThreads, 1) levels_kernel(HeapView h, uint32_t c, typename M::Args args, int32_t base,
                                                      int K, unsigned long long* flags, unsigned int* arrive) {
   __shared__ int any;
   const uint32_t n = __ldcg(h.rcnt);
