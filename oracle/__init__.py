@@ -14,7 +14,10 @@ leg may import this package.  It never imports the CUDA library and the CUDA
 library never imports it; both consume the same seeded inputs from
 ``paper_1908_05845_gb300.inputs``.
 
-Pins (tests/test_oracle_*.py): Philox known-answer vectors; Life blinker /
+Pins (tests/test_oracle_*.py): Philox agreement with the input generator's
+separately written implementation on a million draws (parity unpinned
+against the published generator: its known-answer vectors are not
+available here); Life blinker /
 glider / block, all 512 3x3 neighbourhoods and dense B3/S23 on random tori,
 the candidate-set closed form; Wa-Tor bookkeeping, lone fish / lone shark
 histories, full grid without sharks; NaSch free-flow closed form, car

@@ -4,6 +4,7 @@ fragmentation bound F < 1/(n+1) holds when all candidates are eliminated,
 the pass count respects the worst-case bound, and the thesis' worked
 examples of source/target assignment and relocation come out as printed."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -70,39 +71,53 @@ def where_now(h, A):
     return dict(zip(vv.cpu().numpy().tolist(), blk.tolist()))
 
 
-def test_worked_example_assignment_n2():
-    """n = 2, seven candidates: B = 2 sources; source 5 moves into 14 and
-    19, source 9 into 16 and 22, block 30 is left over (Sec. 6.3.3)."""
-    h = smmo.Heap(32 << 20)
-    A = h.register("A", [("v", smmo.I32), ("kill", smmo.I32)])
-    fill = {5: 30, 9: 30, 14: 40, 16: 40, 19: 20, 22: 20, 30: 20}
-    v, kill = _kill_all_but(h, A, fill, 31, 64)
-    st = h.compact(A, n=2, k1=6)
-    h.sync()
-    assert st["passes"] == 1 and st["blocks_freed"] == 2 and st["objects_moved"] == 60
-    loc = where_now(h, A)
-    src5 = [x for x in range(5 * 64, 5 * 64 + 30)]
-    src9 = [x for x in range(9 * 64, 9 * 64 + 30)]
-    assert sorted(loc[x] for x in src5) == [14] * 24 + [19] * 6
-    assert sorted(loc[x] for x in src9) == [16] * 24 + [22] * 6
-    assert all(loc[x] == x // 64 for x in loc if x // 64 not in (5, 9))
-    assert h.check() == 0
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "compactgpu_worked_examples.txt")
 
 
-def test_worked_example_relocation_n3_capacity32():
-    """n = 3, block capacity 32, 18 objects: the first 12 fit into the first
-    target, the remaining 6 into the second (Sec. 6.3.3, Alg. 6.4)."""
-    h = smmo.Heap(32 << 20, smmo.default_config(block_data_bytes=256))
+def worked_examples():
+    """Cases of tests/golden/compactgpu_worked_examples.txt (Sec. 6.3.3)."""
+    cases = []
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        head, fills, moves, left = (p.strip() for p in line.split("|"))
+        name, n, k1, cap = head.split()
+        fills = {int(b): int(f) for b, f in (x.split(":") for x in fills.split())}
+        mv = []
+        for x in moves.split():
+            src, rest = x.split(">")
+            tgt, cnt = rest.split(":")
+            mv.append((int(src), int(tgt), int(cnt)))
+        cases.append((name, int(n), int(k1), int(cap), fills, mv, [int(x) for x in left.split()]))
+    return cases
+
+
+@pytest.mark.parametrize("case", worked_examples(), ids=lambda c: c[0])
+def test_worked_examples(case):
+    """The thesis' worked examples of source/target assignment (n = 2) and
+    relocation (n = 3, capacity 32): one pass moves each source's objects
+    into its targets in order, as many into a target as it has free slots;
+    the left-over candidate and every other block keep their objects."""
+    name, n, k1, cap, fills, moves, left = case
+    cfg = smmo.default_config(block_data_bytes=256) if cap == 32 else None
+    h = smmo.Heap(32 << 20, cfg)
     A = h.register("A", [("v", smmo.I32), ("kill", smmo.I32)])
     h.freeze()
-    assert h.class_info(A)["capacity"] == 32
-    fill = {0: 18, 1: 20, 2: 10, 3: 24}
-    _kill_all_but(h, A, fill, 4, 32)
-    st = h.compact(A, n=3, k1=3)
+    assert h.class_info(A)["capacity"] == cap
+    _kill_all_but(h, A, fills, max(fills) + 1, cap)
+    st = h.compact(A, n=n, k1=k1)
     h.sync()
+    sources = sorted({s for s, _, _ in moves})
+    assert st["passes"] == 1 and st["blocks_freed"] == len(sources)
+    assert st["objects_moved"] == sum(c for _, _, c in moves)
     loc = where_now(h, A)
-    assert st["passes"] == 1 and st["objects_moved"] == 18
-    assert sorted(loc[x] for x in range(18)) == [1] * 12 + [2] * 6
+    for s in sources:
+        objs = range(s * cap, s * cap + fills[s])
+        want = sorted(t for src, t, c in moves if src == s for _ in range(c))
+        assert sorted(loc[x] for x in objs) == want, s
+    assert all(loc[x] == x // cap for x in loc if x // cap not in sources)
+    assert all(any(loc[x] == b for x in loc) for b in left)
     assert h.check() == 0
 
 
