@@ -680,9 +680,10 @@ int smmo_measure_fp32_peak(int iters, double* ops_per_s, void* stream);
  * issues two per pair (square root and reciprocal). */
 int smmo_measure_mufu_peak(int iters, double* ops_per_s, void* stream);
 
-/* Self-test of a bounded wait: one CTA waits at a grid barrier that nothing
- * releases, for `spins` polls of about 100 ns (1..2^20), then records
- * SMMO_E_TIMEOUT (detail 2) in the heap's error word and returns; the
+/* Self-test of a bounded wait: one CTA waits at the BFS level barrier for a
+ * second CTA that never arrives, for `spins` polls of about 100 ns
+ * (1..2^20), then records SMMO_E_TIMEOUT (detail 1) in the heap's error
+ * word and returns; the
  * caller reads it with smmo_heap_sync.  Synchronises `stream`. */
 int smmo_selftest_barrier_timeout(smmo_heap* heap, uint32_t spins, void* stream);
 

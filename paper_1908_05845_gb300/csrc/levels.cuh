@@ -23,37 +23,48 @@ constexpr unsigned kLevelBarrierSpins = 1u << 23;  // x ~100 ns: about a second
 constexpr int kLevelChunk = 4;                     // units tested at once per warp
 
 constexpr int kLevelThreads = 1024;                // CTA size: one CTA of 32 warps per SM (fewest arrivals)
-constexpr int kBarrierWords = 64;                  // arrive[0] counter, arrive[32] release word
+constexpr int kBarrierWords = 64;                  // 64-bit words: [0], [16] counters, [32] release
 
-// Barrier across the grid's CTAs: arrive[0] counts arrivals (zeroed before
-// the launch); the CTA that completes the k-th barrier (its arrival makes
-// the count k x gridDim.x) writes k to arrive[32], on which the others wait
-// (the count and the word are in different cache lines, so the waiting
-// reads do not slow the arrivals).
-__device__ __forceinline__ bool grid_barrier(const HeapView& h, unsigned int* arrive, unsigned int k,
-                                             unsigned spin_limit = kLevelBarrierSpins) {
-  __shared__ int ok;
+// Barrier across the grid's CTAs that also combines one bit per CTA (did
+// it find a frontier object).  Level k (counted from 0 in the launch) adds
+// 1 + (bit << 32) to the counter ctl[16 (k mod 2)]; the CTA whose addition
+// completes the count of `ncta` CTAs sees the OR of all bits in the high
+// half of the result, resets the other counter (the next level's: all CTAs
+// are past the level before), and publishes ((k + 1) << 1) | OR in the
+// release word ctl[32], on which the others wait.  Counters and release
+// word lie in different cache lines, so the waiting reads do not slow the
+// arrivals.  Returns 0 on timeout (recorded as SMMO_E_TIMEOUT), else 1,
+// with the level's OR in *any_out.  ctl is zeroed before the launch.
+__device__ __forceinline__ bool level_barrier(const HeapView& h, unsigned long long* ctl, unsigned int k, bool bit,
+                                              unsigned int ncta, int* any_out,
+                                              unsigned spin_limit = kLevelBarrierSpins) {
+  __shared__ int ok, any;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
     __threadfence();
-    const unsigned int target = k * gridDim.x;
-    if (atomicAdd(arrive, 1u) + 1 == target) {
+    const unsigned long long add = 1ull + (bit ? (1ull << 32) : 0ull);
+    const unsigned long long now = atomicAdd(ctl + 16 * (k & 1), add) + add;
+    if ((now & 0xFFFFFFFFull) == ncta) {
+      ctl[16 * ((k + 1) & 1)] = 0ull;
       __threadfence();
-      atomicExch(arrive + 32, k);
+      atomicExch(ctl + 32, ((unsigned long long)(k + 1) << 1) | ((now >> 32) ? 1ull : 0ull));
     }
     unsigned spins = 0;
-    while (*(volatile unsigned int*)(arrive + 32) < k) {
+    unsigned long long r;
+    while (((r = *(volatile unsigned long long*)(ctl + 32)) >> 1) < k + 1) {
       if (++spins > spin_limit) {
         ok = 0;
-        set_error(h, SMMO_E_TIMEOUT, target);
+        set_error(h, SMMO_E_TIMEOUT, k + 1);
         break;
       }
       __nanosleep(100);
     }
     __threadfence();
+    any = (int)(r & 1);
   }
   __syncthreads();
+  *any_out = any;
   return ok != 0;
 }
 
@@ -67,7 +78,7 @@ __device__ __forceinline__ bool grid_barrier(const HeapView& h, unsigned int* ar
 // base + k.
 template <class M, bool POLY>
 __global__ void __launch_bounds__(kLevelThreads, 1) levels_kernel(HeapView h, uint32_t c, typename M::Args args, int32_t base,
-                                                     int K, unsigned long long* flags, unsigned int* arrive) {
+                                                     int K, unsigned long long* flags, unsigned long long* ctl) {
   __shared__ int any;
   const uint32_t n = __ldcg(h.rcnt);
   const uint32_t cap = POLY ? 64u : __ldg(&h.cls[c].cap);
@@ -117,9 +128,10 @@ __global__ void __launch_bounds__(kLevelThreads, 1) levels_kernel(HeapView h, ui
     }
     if (__any_sync(0xFFFFFFFFu, mine) && lane == 0) any = 1;
     __syncthreads();
-    if (threadIdx.x == 0 && any) atomicOr(&flags[k], 1ull);
-    if (!grid_barrier(h, arrive, (unsigned)(k + 1))) break;
-    if (__ldcg(&flags[k]) == 0) break;  // no frontier at this level: the search is over
+    int level_or = 0;
+    if (!level_barrier(h, ctl, (unsigned)k, any != 0, gridDim.x, &level_or)) break;
+    if (threadIdx.x == 0 && blockIdx.x == 0 && level_or) flags[k] = 1ull;  // for the host
+    if (!level_or) break;  // no frontier at this level: the search is over
   }
   if (lane == 0 && visited) count(h, SMMO_CTR_VISIT, visited);
 }
@@ -128,7 +140,7 @@ __global__ void __launch_bounds__(kLevelThreads, 1) levels_kernel(HeapView h, ui
 // view `v` (class c, or with POLY the classes enumerated into it).
 template <class M, bool POLY>
 int launch_levels(smmo_heap* hp, const HeapView& v, int c, const typename M::Args& a, int32_t base, int K,
-                  unsigned long long* flags, unsigned int* arrive, cudaStream_t s) {
+                  unsigned long long* flags, unsigned long long* ctl, cudaStream_t s) {
   static int occ = 0;
   if (occ == 0) {
     int nb = 0;
@@ -138,7 +150,7 @@ int launch_levels(smmo_heap* hp, const HeapView& v, int c, const typename M::Arg
     occ = nb;
   }
   const int per_sm = occ;
-  cudaError_t e = cudaMemsetAsync(arrive, 0, sizeof(unsigned int) * kBarrierWords, s);
+  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(unsigned long long) * kBarrierWords, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, sizeof(unsigned long long) * (size_t)K, s);
   if (e != cudaSuccess) return cuda_status(e);
   HeapView hv = v;
@@ -146,7 +158,7 @@ int launch_levels(smmo_heap* hp, const HeapView& v, int c, const typename M::Arg
   typename M::Args args = a;
   int32_t b = base;
   int kk = K;
-  void* params[] = {&hv, &cc, &args, &b, &kk, &flags, &arrive};
+  void* params[] = {&hv, &cc, &args, &b, &kk, &flags, &ctl};
   e = cudaLaunchCooperativeKernel((const void*)levels_kernel<M, POLY>, dim3((unsigned)(hp->num_sms * per_sm)),
                                   dim3(kLevelThreads), params, 0, s);
   return cuda_status(e);

@@ -111,7 +111,7 @@ struct smmo_bfs {
   int cls = -1;
   uint32_t n0 = 0;
   unsigned long long* d_flags = nullptr;  // one OR result per level of a launch
-  unsigned int* d_arrive = nullptr;       // grid barrier counter
+  unsigned long long* d_arrive = nullptr;  // level barrier words
   int flags_cap = 0;
   BfsArgs args{};
   smmo::Snapshot snap;                    // the vertices (fixed during a search)
@@ -182,7 +182,7 @@ int smmo_bfs_run(smmo_bfs* w, int32_t source, int check_every, int32_t* levels, 
     return SMMO_E_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (!w->d_arrive) {
-    cudaError_t e = cudaMalloc(&w->d_arrive, sizeof(unsigned int) * kBarrierWords);
+    cudaError_t e = cudaMalloc(&w->d_arrive, sizeof(unsigned long long) * kBarrierWords);
     if (e != cudaSuccess) { w->d_arrive = nullptr; return cuda_status(e); }
   }
   if (w->flags_cap < check_every) {

@@ -330,7 +330,7 @@ struct smmo_structure {
   StructArgs args{};
   unsigned long long* d_ctr = nullptr;  // CTR_N counters
   unsigned long long* d_flags = nullptr;  // one OR result per level of a launch
-  unsigned int* d_arrive = nullptr;       // grid barrier counter
+  unsigned long long* d_arrive = nullptr;  // level barrier words
   int flags_cap = 0;
   smmo::Snapshot nodes;                 // all node classes (one POLY snapshot)
   smmo::Snapshot springs, free_nodes;   // the compute phase's snapshots
@@ -480,7 +480,7 @@ int smmo_structure_create(smmo_heap* heap, int64_t n, const int8_t* kind, const 
   }
   cudaError_t e = cudaMalloc(&w->d_ctr, sizeof(unsigned long long) * CTR_N);
   if (e == cudaSuccess) e = cudaMemsetAsync(w->d_ctr, 0, sizeof(unsigned long long) * CTR_N, st_);
-  if (e == cudaSuccess) e = cudaMalloc(&w->d_arrive, sizeof(unsigned int) * kBarrierWords);
+  if (e == cudaSuccess) e = cudaMalloc(&w->d_arrive, sizeof(unsigned long long) * kBarrierWords);
   if (e != cudaSuccess) { smmo_structure_destroy(w); return cuda_status(e); }
   a.ctr = w->d_ctr;
   // handle table: nodes by id, then springs by id

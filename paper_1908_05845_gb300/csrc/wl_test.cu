@@ -99,20 +99,21 @@ const int g_methods_test_n = sizeof(g_methods_test) / sizeof(g_methods_test[0]);
 
 // ------------------------------------------------ bounded barrier self-test
 namespace {
-// One CTA waits at the second barrier of a grid of one: its own arrival is
-// the only one, so nothing releases it and the wait runs out after
-// `spins` polls, recording SMMO_E_TIMEOUT (detail 2, the barrier).
-__global__ void k_barrier_nobody_comes(HeapView h, unsigned int* arrive, unsigned spins) {
-  smmo::grid_barrier(h, arrive, 2u, spins);
+// One CTA waits at a level barrier that expects two CTAs: its own arrival
+// is the only one, so nothing releases it and the wait runs out after
+// `spins` polls, recording SMMO_E_TIMEOUT (detail 1, the first level).
+__global__ void k_barrier_nobody_comes(HeapView h, unsigned long long* ctl, unsigned spins) {
+  int any = 0;
+  smmo::level_barrier(h, ctl, 0u, false, 2u, &any, spins);
 }
 }  // namespace
 
 extern "C" int smmo_selftest_barrier_timeout(smmo_heap* h, uint32_t spins, void* stream) {
   if (!h || !h->frozen || spins < 1 || spins > (1u << 20)) return SMMO_E_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  unsigned int* arrive = nullptr;
-  cudaError_t e = cudaMallocAsync(&arrive, sizeof(unsigned int) * smmo::kBarrierWords, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(arrive, 0, sizeof(unsigned int) * smmo::kBarrierWords, s);
+  unsigned long long* arrive = nullptr;
+  cudaError_t e = cudaMallocAsync(&arrive, sizeof(unsigned long long) * smmo::kBarrierWords, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(arrive, 0, sizeof(unsigned long long) * smmo::kBarrierWords, s);
   if (e == cudaSuccess) {
     k_barrier_nobody_comes<<<1, 64, 0, s>>>(h->view, arrive, spins);
     e = cudaGetLastError();
