@@ -3,7 +3,8 @@
 Closed forms: the Alive set must equal dense B3/S23 on the torus; the
 Candidate set must equal D_{t+1} & ({c in Cand_t: n_t(c) >= 1} | A_t |
 N8(Births_{t+1})); every dead cell with an alive neighbour holds a
-Candidate; is_new marks exactly this generation's births.
+Candidate; is_new marks exactly this generation's births; the created,
+deleted and allocator-operation counts follow from the dense boards.
 """
 import numpy as np
 import pytest
@@ -106,6 +107,18 @@ def test_random_tori_vs_dense(orc, size):
             assert np.all((K == 2)[dead & n8(nxt)])
             assert c[0, 0] == nxt.sum() and c[0, 1] == want_cand.sum()
             assert c[0, 2] == births.sum() and c[0, 3] == (alive & ~nxt).sum()
+            # candidates without an alive neighbour are deleted; the cells
+            # empty after that (and after the births) that touch a birth
+            # get one new Candidate each
+            deleted = cand & (n == 0)
+            empty3 = ~alive & ~(cand & (n >= 1))
+            created = empty3 & n8(births)
+            assert c[0, 4] == created.sum() and c[0, 5] == deleted.sum()
+            # allocator operations: a birth and a death each delete one
+            # object and create one; creations and deletions one each
+            news = births.sum() + (alive & ~nxt).sum() + created.sum()
+            frees = births.sum() + (alive & ~nxt).sum() + deleted.sum()
+            assert c[0, 6] == news + frees
             alive, cand = nxt, K == 2
 
 

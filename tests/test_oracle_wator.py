@@ -1,6 +1,7 @@
 """Pins of the Wa-Tor oracle (thesis Sec. 7.6).
 
 Bookkeeping identities, hand-checkable histories (lone fish, lone shark,
+the fish phase before the shark phase, a breeding shark,
 shark next to a fish, full grid of fish) and an exhaustive check that a
 contested cell goes to the requester on the lowest cell index.
 """
@@ -133,3 +134,35 @@ def test_deterministic(orc):
     s = orc.wator_run(48, 48, 7, m[0], m[1], m[2], 25, t0=15)
     for x, y in zip(r1[:3], s[:3]):
         assert np.array_equal(x, y)
+
+
+def test_fish_phase_precedes_shark_phase(orc):
+    """A 3x1 torus leaves every agent one choice, so the draws do not matter:
+    the fish at 0 moves to the empty cell 2 in the fish phase, then the shark
+    at 1 hunts it there (Sec. 7.6: the fish phase runs before the shark
+    phase, a shark prefers a neighbouring fish and is fed on eating)."""
+    k = np.array([1, 2, 0], np.int8)
+    a = np.zeros(3, np.int16)
+    e = np.array([0, 3, 0], np.int16)
+    k2, a2, e2, c = orc.wator_run(3, 1, 11, k, a, e, 1)
+    assert k2.tolist() == [0, 0, 2]
+    assert e2[2] == 3 and a2[2] == 1
+    fish, sharks, fb, eaten, sb, starved, fmoves, smoves = c[0]
+    assert (fish, sharks, fb, eaten, sb, starved, fmoves, smoves) == (0, 1, 0, 1, 0, 0, 1, 1)
+
+
+def test_ripe_shark_leaves_a_fed_newborn(orc):
+    """A lone shark one step short of breeding age moves and breeds: the
+    newborn on the old cell starts with age 0 and a full energy reserve, the
+    parent's age is reset and its energy has dropped by one."""
+    W = H = 8
+    k, a, e = empty(W, H)
+    s = 3 * W + 3
+    k[s], a[s], e[s] = 2, 11, 3
+    k2, a2, e2, c = orc.wator_run(W, H, 2, k, a, e, 1)
+    sharks = np.flatnonzero(k2 == 2)
+    assert sharks.size == 2 and s in sharks and c[0, 4] == 1
+    assert e2[s] == 3 and a2[s] == 0
+    (p,) = [x for x in sharks if x != s]
+    assert e2[p] == 2 and a2[p] == 0
+    assert abs(p % W - s % W) + abs(p // W - s // W) == 1
