@@ -8,8 +8,9 @@ an extension of Life, Sec. 7.8).
   cell with a neighbour count outside `survive` starts blocking, a blocking
   cell advances and frees its cell after `block` generations, a dead cell
   with a count in `born` becomes alive) on random tori, for short and for
-  the thesis' 255-generation blocking; and every dead, unblocked cell with
-  an alive neighbour holds a Candidate.
+  the thesis' 255-generation blocking; every dead, unblocked cell with
+  an alive neighbour holds a Candidate; every counter follows from the
+  state arrays before and after the generation.
 * Worked cases of the Burst rule: a lone cell survives (0 is in the
   survive set); two touching cells die at once, block for exactly 255
   generations, become Candidates in the 256th and are deleted in the 257th.
@@ -86,10 +87,23 @@ def test_equals_textbook_generations_automaton(orc, block):
         k, st, bl = objects_from_states(s)
         ref = s
         for t in range(1, 3 * block + 12):
+            prev, kprev, n = ref, k.reshape(H, W), count8(ref == 1)
             ref = textbook_step(ref, S, B, block)
-            k, st, bl, _ = orc.gen_run(W, H, k, st, bl, 1, (mask(S), mask(B), block))
+            k, st, bl, c = orc.gen_run(W, H, k, st, bl, 1, (mask(S), mask(B), block))
             got = states_from_objects(k, bl, (H, W))
             assert np.array_equal(got, ref), (block, trial, t)
+            # counters from the two state arrays: populations, births,
+            # deaths, expiries, and the Candidates deleted (no alive
+            # neighbour) and created (on cells empty after that, next to a
+            # birth)
+            births = (prev == 0) & (ref == 1)
+            deleted = (kprev == 2) & (n == 0)
+            empty3 = (kprev == 0) | deleted
+            nb8 = count8(births) >= 1
+            want = [(ref == 1).sum(), (ref >= 2).sum(), (k == 2).sum(), births.sum(),
+                    ((prev == 1) & (ref != 1)).sum(), (prev == block + 1).sum(),
+                    (empty3 & nb8 & ~births).sum(), deleted.sum()]
+            assert c[0].tolist() == [int(x) for x in want], (block, trial, t)
             # every dead unblocked cell with an alive neighbour is a Candidate
             need = (ref == 0) & (count8(ref == 1) >= 1)
             assert np.all(k.reshape(H, W)[need] == 2)

@@ -8,8 +8,11 @@
 * Worked cases on a two-into-one junction: a traffic light's green index and
   timer follow floor(t / P) mod n and t mod P; a red street's front car
   never enters; a yield controller lets the priority street through while it
-  has waiting cars; a smart light turns green at once for the only street
-  with a waiting car.
+  has waiting cars; a smart light turns green at once (timer restarted)
+  for the only street with a waiting car and keeps its phase when both
+  wait; "waiting" means within the lookahead window and routed into the
+  guarded street in this step; the switch and lost-claim counters; a
+  controller of a street with one entry does nothing.
 """
 import numpy as np
 import pytest
@@ -110,3 +113,97 @@ def test_smart_light_turns_green_for_the_only_waiting_street(orc):
     plain = np.array([-1, -1, 0], np.int8)
     v2, green, _, _ = orc.nasch_ctrl_run(g, 3, v, 1, plain, phase_len=50)
     assert green[2] == 0 and cars_on(g, v2, 2) == 0  # a plain light keeps B red
+
+
+def smart_light(orc, g, v, **kw):
+    """One step of the junction with a smart light (phase 50) on O."""
+    return orc.nasch_ctrl_run(g, 3, v, 1, np.array([-1, -1, 1], np.int8), phase_len=50, **kw)
+
+
+def test_lookahead_window(orc):
+    """A car waits when it is within `lookahead` (5) cells of the end of its
+    street: the cell 5 before the last is outside the window."""
+    g = junction()
+    for p, waits in ((14, False), (15, True)):
+        v = np.full(g["num_cells"], -1, np.int8)
+        v[20 + p] = 0  # street B only; the smart light starts green on A
+        _, green, timer, _ = smart_light(orc, g, v)
+        assert (green[2], timer[2]) == ((1, 0) if waits else (0, 1)), p
+
+
+def test_smart_light_keeps_its_phase_when_both_streets_wait(orc):
+    g = junction()
+    v = np.full(g["num_cells"], -1, np.int8)
+    v[19] = v[39] = 0
+    _, green, timer, cnt = smart_light(orc, g, v)
+    assert (green[2], timer[2]) == (0, 1) and cnt[0, 5] == 0
+
+
+def test_smart_light_restarts_its_timer_on_a_switch(orc):
+    g = junction()
+    v = np.full(g["num_cells"], -1, np.int8)
+    v[39] = 0
+    _, green, timer, cnt = smart_light(orc, g, v, timer=np.array([0, 0, 3], np.int16))
+    assert (green[2], timer[2]) == (1, 0) and cnt[0, 5] == 1
+
+
+@pytest.mark.parametrize("P", [2, 5])
+def test_switch_counter_counts_phase_changes(orc, P):
+    g = junction()
+    v0 = np.full(g["num_cells"], -1, np.int8)
+    _, _, _, cnt = orc.nasch_ctrl_run(g, 3, v0, 4 * P, np.array([-1, -1, 0], np.int8), phase_len=P)
+    assert cnt[:, 5].tolist() == [int(t % P == 0) for t in range(1, 4 * P + 1)]
+
+
+def test_lost_claim_is_counted_without_controllers(orc):
+    """Two cars enter the same street in one step: the one on the lower cell
+    index wins, the other stops at the end of its own street."""
+    g = junction()
+    v = np.full(g["num_cells"], -1, np.int8)
+    v[19], v[37] = 4, 4
+    v1, _, _, cnt = orc.nasch_ctrl_run(g, 3, v, 1, np.full(3, -1, np.int8))
+    assert cnt[0, 4] == 1 and v1[39] == 2 and v1[44] == 5
+
+
+def test_controller_on_a_street_with_one_entry_does_nothing(orc):
+    """Street A leads into street O and nothing else does: whatever the
+    controller on O, its state never changes and A's cars pass freely."""
+    g = dict(num_streets=2, street_start=np.array([0, 20], np.int32), street_len=np.array([20, 60], np.int32),
+             out_deg=np.array([1, 0], np.int32), out_street=np.array([1, -1, -1, -1, -1, -1], np.int32),
+             is_source=np.zeros(2, np.uint8), num_cells=80, v_max=5, brake_threshold=0,
+             sources_enabled=0, sinks_enabled=1)
+    v = np.full(80, -1, np.int8)
+    v[15:20] = 3
+    free, _ = orc.nasch_run(g, 3, v, 7)
+    for kind in (0, 1, 2):
+        v1, green, timer, cnt = orc.nasch_ctrl_run(g, 3, v, 7, np.array([-1, kind], np.int8), phase_len=3)
+        assert green[1] == 0 and timer[1] == 0 and cnt[:, 5].sum() == 0
+        assert np.array_equal(v1, free)
+
+
+def test_waiting_follows_this_steps_route(orc):
+    """Street A turns into O or X (a random route per step), B only into O;
+    a smart light guards O and starts green on A.  A car at the end of A
+    waits for O only when this step's route of A leads there: when A's car
+    turns into X, B is the only street waiting for O and gets green at once."""
+    lens = np.array([20, 20, 60, 40], np.int32)
+    start = np.array([0, 20, 40, 100], np.int32)
+    out = np.full(12, -1, np.int32)
+    out[0:2] = [2, 3]
+    out[3] = 2
+    g = dict(num_streets=4, street_start=start, street_len=lens, out_deg=np.array([2, 1, 0, 0], np.int32),
+             out_street=out, is_source=np.zeros(4, np.uint8), num_cells=140, v_max=5,
+             brake_threshold=0, sources_enabled=0, sinks_enabled=1)
+    kind = np.array([-1, -1, 1, -1], np.int8)
+    seen = set()
+    for seed in range(1, 17):
+        v = np.full(140, -1, np.int8)
+        v[19] = v[39] = 0
+        v1, green, timer, _ = orc.nasch_ctrl_run(g, seed, v, 1, kind, phase_len=50)
+        to_x = bool(v1[100] >= 0)
+        seen.add(to_x)
+        if to_x:
+            assert (green[2], timer[2]) == (1, 0) and v1[40] == 1 and v1[39] < 0
+        else:
+            assert (green[2], timer[2]) == (0, 1) and v1[40] == 1 and v1[39] == 0
+    assert seen == {False, True}
