@@ -2,8 +2,9 @@
 
 Momentum conservation, the softened two-body circular orbit and its O(dt^2)
 phase error, O(dt^2) energy drift, merge bookkeeping (mass and momentum
-conserved, midpoint position, lowest receiver wins, a merge into a body that
-is itself merged is skipped), FP32 against FP64, and the adjoint against
+conserved, midpoint position and mass-weighted velocity in every component,
+lowest receiver wins, equal masses ordered by id, a merge into a body that
+is itself merged is skipped), the two-body acceleration closed form, FP32 against FP64, and the adjoint against
 central finite differences (both the pair kernel and the whole 50-step run).
 """
 import numpy as np
@@ -112,6 +113,55 @@ def test_merge_conserves_mass_and_momentum(orc):
     live = out["live"] == 1
     assert (~live).sum() == k.sum()
     assert abs(out["m"][live].astype(np.float64).sum() - m0) / m0 < 1e-5
+    # merges alone (G = 0: no forces) keep the momentum vector
+    out, k = orc.nbody_run_f32(st, 20, G=0.0, merge_r=2e-2)
+    assert k.sum() > 0
+    live = out["live"] == 1
+    m = st["m"].astype(np.float64)
+    for c in ("vx", "vy", "vz"):
+        P0 = float((m * st[c]).sum())
+        P1 = float((out["m"][live].astype(np.float64) * out[c][live]).sum())
+        scale = float((m * np.abs(st[c])).sum())
+        assert abs(P1 - P0) / scale < 1e-5, c
+
+
+def test_merge_of_an_off_axis_pair(orc):
+    """Position (midpoint) and velocity (mass-weighted) of a merge in all
+    three components, with dt = 0 so nothing moves before the merge."""
+    st = _bodies([(0.5, 0.4, 0.3, 1.0, -2.0, 4.0, 3.0), (0.501, 0.402, 0.297, -1.0, 2.0, 0.5, 1.0)])
+    out, k = orc.nbody_run_f32(st, 1, G=0.0, dt=0.0, merge_r=5e-3)
+    assert k[0] == 1 and list(out["live"]) == [1, 0] and out["m"][0] == 4.0
+    want_x = [(0.5 + 0.501) / 2, (0.4 + 0.402) / 2, (0.3 + 0.297) / 2]
+    want_v = [(3.0 - 1.0) / 4, (-6.0 + 2.0) / 4, (12.0 + 0.5) / 4]
+    for c, w in zip(("x", "y", "z"), want_x):
+        assert abs(out[c][0] - w) < 1e-6, c
+    for c, w in zip(("vx", "vy", "vz"), want_v):
+        assert abs(out[c][0] - w) < 1e-6, c
+
+
+def test_equal_masses_merge_into_the_higher_id(orc):
+    """"Lighter" orders bodies by (mass, id): of two equal masses within the
+    threshold, the one with the lower id is merged into the other."""
+    st = _bodies([(0.5, 0.5, 0.5, 0, 0, 0, 2.0), (0.502, 0.5, 0.5, 0, 0, 0, 2.0)])
+    out, k = orc.nbody_run_f32(st, 1, G=0.0, dt=0.0, merge_r=5e-3)
+    assert k[0] == 1 and list(out["live"]) == [0, 1] and out["m"][1] == 4.0
+
+
+def test_two_body_acceleration_closed_form(orc):
+    """a = G m d / (d^2 + eps^2)^(3/2) towards the other body, along each
+    axis, for G != 1, in FP32 and FP64."""
+    G, eps, d, m2 = 0.7, 1e-2, 0.25, 3.0
+    want = G * m2 * d / (d * d + eps * eps) ** 1.5
+    for axis in range(3):
+        p = np.zeros((2, 3))
+        p[1, axis] = d
+        st = _bodies([(*p[0], 0, 0, 0, 1.0), (*p[1], 0, 0, 0, m2)])
+        a32 = np.stack(orc.nbody_accel_f32(st, G=G, eps=eps), 1)
+        a64 = orc.nbody_accel_f64(p, np.array([1.0, m2]), G=G, eps=eps)
+        for a, tol in ((a32, 1e-6), (a64, 1e-13)):
+            assert abs(a[0, axis] - want) / want < tol
+            assert abs(a[1, axis] + G * 1.0 * d / (d * d + eps * eps) ** 1.5) / want < tol
+            assert np.all(np.delete(a[0], axis) == 0) and np.all(np.delete(a[1], axis) == 0)
 
 
 def test_pair_adjoint_vs_fd(orc):
