@@ -2,11 +2,16 @@
 
 * Never opening a tree node by the width criterion (theta = 0) gives the
   direct all-pairs sum, checked against an FP64 direct sum.
-* The tree is the region quad tree: worked node counts and depths; the
-  accelerations do not depend on the insertion order (bitwise).
+* The tree is the region quad tree of half-open squares: worked node
+  counts and depths; the accelerations do not depend on the insertion
+  order (bitwise); a body always opens the tree nodes that contain it.
+* Visit and node counters: N (nodes - 1 + N) visits at theta = 0 and a
+  worked three-body count.
 * The error against the direct sum falls with theta; two bodies
   attract with equal and opposite accelerations times their masses.
-* A body leaving the unit square is reflected with its velocity negated.
+* The body update is semi-implicit Euler (two-body step for G != 1); a body
+  leaving the unit square at any wall is reflected with its velocity
+  negated, and one landing on 1 is clamped below it.
 """
 import numpy as np
 import pytest
@@ -84,3 +89,77 @@ def test_wall_reflection(orc):
     out, _ = orc.bh_run(st, 1, dt=0.01)
     assert out["vx"][0] == -1.0 and abs(out["x"][0] - (2.0 - 1.005)) < 1e-6
     assert out["vy"][0] == -0.5 and abs(out["y"][0] - 0.495) < 1e-6
+
+
+def test_squares_are_half_open(orc):
+    """A body on a midline belongs to the upper quadrant ([p, p + w) squares):
+    bodies at x = 0.5 and x = 0.4 (or y) already sit in different quadrants
+    of the root, and the same holds one level down."""
+    f = lambda *v: np.array(v, np.float32)  # noqa: E731
+    assert orc.bh_build(f(0.5, 0.4), f(0.1, 0.1)) == (1, 0)
+    assert orc.bh_build(f(0.1, 0.1), f(0.5, 0.4)) == (1, 0)
+    # (0.5, 0.5) and (0.75, 0.5) share the root's quadrant 3; in its tree
+    # node [0.5, 1)^2 the one on the midline x = 0.75 goes to quadrant 1
+    assert orc.bh_build(f(0.5, 0.75), f(0.5, 0.5)) == (2, 1)
+
+
+def test_a_body_inside_a_tree_node_always_opens_it(orc):
+    """With a huge theta only the body's own ancestors are opened: bodies 0
+    and 1 share the tree node [0, 0.5)^2 and see each other and body 2
+    exactly; body 2 sees that tree node as one body of mass 2 at its centre
+    of gravity.  Visits: 4 + 4 + 2 (tree node, two bodies, body 2; tree
+    node, body 2 itself)."""
+    x = np.array([0.05, 0.45, 0.9], np.float32)
+    y = np.array([0.05, 0.45, 0.9], np.float32)
+    m = np.array([1.0, 1.0, 1.0], np.float32)
+    eps = 1e-2
+    ax, ay = orc.bh_accel(x, y, m, eps=eps, theta=10.0)
+    rx, ry = direct(x, y, m, eps)
+    assert np.allclose(ax[:2], rx[:2], rtol=1e-6) and np.allclose(ay[:2], ry[:2], rtol=1e-6)
+    d = np.array([0.25 - 0.9, 0.25 - 0.9])
+    s2 = d @ d + eps * eps
+    want = 2.0 * d / (s2 * np.sqrt(s2))
+    assert np.allclose([ax[2], ay[2]], want, rtol=1e-5)
+    _, cnt = orc.bh_run(dict(x=x, y=y, vx=np.zeros(3, np.float32), vy=np.zeros(3, np.float32), m=m),
+                        1, theta=10.0)
+    assert cnt[0].tolist() == [2, 10]
+
+
+def test_theta_zero_visits_every_child_of_every_tree_node(orc):
+    """At theta = 0 every body opens every tree node, so one step visits
+    N (nodes - 1 + N) non-empty child slots; the node count is the region
+    quad tree's."""
+    st = inputs.bh_initial(500, 2)
+    nodes, _ = orc.bh_build(st["x"], st["y"])
+    _, cnt = orc.bh_run(st, 1, theta=0.0)
+    assert cnt[0].tolist() == [nodes, 500 * (nodes - 1 + 500)]
+
+
+def test_body_update_is_semi_implicit_euler(orc):
+    """v += G a dt, then x += v dt with the new velocity, for G != 1: two
+    bodies at rest pulled towards each other by the softened pair force."""
+    G, eps, dt = 0.5, 1e-2, 1e-3
+    st = dict(x=np.array([0.3, 0.7], np.float32), y=np.array([0.5, 0.5], np.float32),
+              vx=np.zeros(2, np.float32), vy=np.zeros(2, np.float32), m=np.array([1.0, 2.0], np.float32))
+    out, _ = orc.bh_run(st, 1, G=G, eps=eps, dt=dt)
+    d = 0.4
+    for b, (other_m, sign) in enumerate(((2.0, 1), (1.0, -1))):
+        v = sign * G * other_m * d / (d * d + eps * eps) ** 1.5 * dt
+        assert abs(out["vx"][b] - v) < 1e-5 * abs(v)
+        assert abs(out["x"][b] - (st["x"][b] + v * dt)) < 5e-8
+        assert out["vy"][b] == 0 and out["y"][b] == 0.5
+
+
+def test_low_walls_and_the_upper_clamp(orc):
+    """A body crossing x = 0 (or y = 0) is reflected with its velocity
+    negated; one that lands exactly on 1 is reflected onto 1 and clamped to
+    the largest float below 1."""
+    st = dict(x=np.array([0.004], np.float32), y=np.array([0.003], np.float32),
+              vx=np.array([-1.0], np.float32), vy=np.array([-0.5], np.float32), m=np.array([1.0], np.float32))
+    out, _ = orc.bh_run(st, 1, dt=0.01)
+    assert out["vx"][0] == 1.0 and abs(out["x"][0] - 0.006) < 1e-7
+    assert out["vy"][0] == 0.5 and abs(out["y"][0] - 0.002) < 1e-7
+    st = dict(x=np.array([0.5], np.float32), y=np.array([0.25], np.float32),
+              vx=np.array([0.5], np.float32), vy=np.array([0.0], np.float32), m=np.array([1.0], np.float32))
+    out, _ = orc.bh_run(st, 1, dt=1.0)
+    assert out["x"][0] == np.float32(1 - 2.0 ** -24) and out["vx"][0] == -0.5
