@@ -14,23 +14,29 @@ leg may import this package.  It never imports the CUDA library and the CUDA
 library never imports it; both consume the same seeded inputs from
 ``paper_1908_05845_gb300.inputs``.
 
-Pins (tests/test_oracle_*.py): Philox agreement with the input generator's
-separately written implementation on a million draws (parity unpinned
-against the published generator: its known-answer vectors are not
-available here); Life blinker /
-glider / block, all 512 3x3 neighbourhoods and dense B3/S23 on random tori,
-the candidate-set closed form; Wa-Tor bookkeeping, lone fish / lone shark
-histories, full grid without sharks; NaSch free-flow closed form, car
-conservation on a ring with p = 0, evenly spaced flow; n-body momentum
-conservation, two-body circular orbit, energy drift O(dt^2), merge mass
-conservation; adjoint against central finite differences and the pair
-kernel against finite differences of the acceleration; generation rules
-against dense reference automata; traffic-light phases and yield
-priorities; Barnes-Hut against direct summation at theta 0 and the region
-tree's node count; spring mesh against one-spring and oscillator closed
+Pins (tests/test_oracle_*.py): Philox against Triton's implementation of
+the same generator (every output word) and the input generator's separately
+written numpy one (a million draws); Life blinker / glider / block, all 512
+3x3 neighbourhoods and dense B3/S23 on random tori, the candidate set and
+every counter from the dense boards; Wa-Tor bookkeeping, lone fish / lone
+shark / breeding shark histories, the fish phase before the shark phase, a
+full grid without sharks, the lowest-index grant; NaSch free-flow closed
+form, car conservation on a ring, evenly spaced flow, braking statistics,
+the entry claim and its loser, the sink rule; n-body momentum conservation
+(also through merges), two-body circular orbit and acceleration closed
+forms, energy drift O(dt^2), merge rules in every component; adjoint
+against central finite differences and the pair kernel against finite
+differences of the acceleration; generation rules and counters against a
+textbook Generations automaton; traffic-light phases, smart lights, yield
+priorities, the lookahead window, route-dependent waiting and the
+controller counters; Barnes-Hut against direct summation at theta 0, the
+region tree's node counts, half-open squares, the visit count, the body
+update and the walls; spring mesh against one-spring and oscillator closed
 forms, momentum and energy conservation and connected components; BFS
 against Manhattan distances and scipy shortest paths.  Parity of every
-function here is pinned by at least one of those.
+function here is pinned by at least one of those, and each pin set was
+checked by planting mistakes in a copy of this oracle: every planted
+mistake that changes an output fails a pin.
 """
 from __future__ import annotations
 
