@@ -68,3 +68,33 @@ def test_clustered_bodies_contended_insertion(orc):
     for k in ("x", "y", "vx", "vy"):
         assert np.array_equal(got[k], want[k]), k
     assert nodes == orc.bh_build(want["x"], want["y"])[0]
+
+
+def test_midlines_walls_and_a_large_theta(orc):
+    """Boundary cases, bit-exact against the oracle: bodies on the exact
+    midlines of squares at several depths (half-open squares); a theta so
+    large that only a body's own ancestors are opened; bodies that cross
+    the low walls; one that lands exactly on 1 and is clamped below it."""
+    g = np.array([0.5, 0.25, 0.75, 0.375, 0.625, 0.125, 0.875], np.float32)
+    xs, ys = np.meshgrid(g, g)
+    rng = np.random.default_rng(3)
+    st = dict(x=xs.reshape(-1), y=ys.reshape(-1), vx=(rng.standard_normal(49) * 1e-3).astype(np.float32),
+              vy=(rng.standard_normal(49) * 1e-3).astype(np.float32), m=np.ones(49, np.float32))
+    three = dict(x=np.array([0.05, 0.45, 0.9], np.float32), y=np.array([0.05, 0.45, 0.9], np.float32),
+                 vx=np.zeros(3, np.float32), vy=np.zeros(3, np.float32), m=np.ones(3, np.float32))
+    walls = dict(x=np.array([0.004, 0.6], np.float32), y=np.array([0.003, 0.7], np.float32),
+                 vx=np.array([-1.0, 0.2], np.float32), vy=np.array([-0.5, 0.1], np.float32),
+                 m=np.ones(2, np.float32))
+    land = dict(x=np.array([0.5], np.float32), y=np.array([0.25], np.float32), vx=np.array([0.5], np.float32),
+                vy=np.zeros(1, np.float32), m=np.ones(1, np.float32))
+    for state, p, T in ((st, P, 8), (st, dict(P, theta=10.0), 8), (three, dict(P, theta=10.0), 5),
+                        (walls, dict(P, dt=1e-2), 3), (land, dict(P, dt=1.0), 2)):
+        sim = BarnesHut(state, **p)
+        sim.step(T)
+        got, nodes = sim.read()
+        assert sim.heap.check() == 0
+        sim.close()
+        want, _ = orc.bh_run(state, T, **p)
+        for k in ("x", "y", "vx", "vy"):
+            assert np.array_equal(got[k], want[k]), (k, len(state["x"]), p)
+        assert nodes == orc.bh_build(want["x"], want["y"])[0]

@@ -104,3 +104,69 @@ def test_controllers_small_graphs_many_seeds(orc):
         want, wg, wt, _ = orc.nasch_ctrl_run(g, seed, v, 50, kind, phase_len=3, lookahead=4)
         assert np.array_equal(got, want), seed
         assert np.array_equal(green, wg) and np.array_equal(timer, wt), seed
+
+
+def junction():
+    """Streets 0 (A) and 1 (B), 20 cells each, lead into street 2 (O, 60
+    cells), a sink."""
+    out = np.full(9, -1, np.int32)
+    out[0] = out[3] = 2
+    return dict(num_streets=3, street_start=np.array([0, 20, 40], np.int32),
+                street_len=np.array([20, 20, 60], np.int32), out_deg=np.array([1, 1, 0], np.int32),
+                out_street=out, is_source=np.zeros(3, np.uint8), num_cells=100, v_max=5,
+                brake_threshold=0, sources_enabled=0, sinks_enabled=1)
+
+
+def fork():
+    """Street A turns into O or X (a random route per step), B only into O;
+    O and X are sinks."""
+    out = np.full(12, -1, np.int32)
+    out[0:2] = [2, 3]
+    out[3] = 2
+    return dict(num_streets=4, street_start=np.array([0, 20, 40, 100], np.int32),
+                street_len=np.array([20, 20, 60, 40], np.int32), out_deg=np.array([2, 1, 0, 0], np.int32),
+                out_street=out, is_source=np.zeros(4, np.uint8), num_cells=140, v_max=5,
+                brake_threshold=0, sources_enabled=0, sinks_enabled=1)
+
+
+def single_entry():
+    """Street A leads into street O and nothing else does."""
+    return dict(num_streets=2, street_start=np.array([0, 20], np.int32), street_len=np.array([20, 60], np.int32),
+                out_deg=np.array([1, 0], np.int32), out_street=np.array([1, -1, -1, -1, -1, -1], np.int32),
+                is_source=np.zeros(2, np.uint8), num_cells=80, v_max=5, brake_threshold=0,
+                sources_enabled=0, sinks_enabled=1)
+
+
+def cars(n, cells, v=0):
+    a = np.full(n, -1, np.int8)
+    a[list(cells)] = v
+    return a
+
+
+def test_controller_worked_cases(orc):
+    """The controllers' degenerate and boundary cases, each bit-exact
+    against the oracle (velocities, green index and timer): a car just
+    outside and just inside the lookahead window, both streets waiting at a
+    smart light, a lost claim without controllers, a controller on a street
+    with one entry (each kind), a red street's queue under a plain light, a
+    yield controller, and route-dependent waiting on a fork for 16 seeds."""
+    J, NONE = junction(), np.full(3, -1, np.int8)
+    smart, light, yld = (np.array([-1, -1, k], np.int8) for k in (1, 0, 2))
+    cases = [(J, 3, cars(100, [34]), smart, 50, 1), (J, 3, cars(100, [35]), smart, 50, 1),
+             (J, 3, cars(100, [19, 39]), smart, 50, 1), (J, 3, cars(100, [19, 37], 4), NONE, 8, 1),
+             (J, 3, cars(100, range(10, 20)), light, 4, 24),
+             (J, 3, cars(100, list(range(0, 20)) + list(range(35, 40))), yld, 8, 10)]
+    cases += [(single_entry(), 3, cars(80, range(15, 20), 3), np.array([-1, k], np.int8), 3, 7) for k in (0, 1, 2)]
+    cases += [(fork(), seed, cars(140, [19, 39]), np.array([-1, -1, 1, -1], np.int8), 50, 1) for seed in range(1, 17)]
+    for n, (g, seed, v, kind, P, T) in enumerate(cases):
+        sim = Traffic(g, seed, v)
+        sim.set_controllers(kind, phase_len=P, lookahead=5)
+        sim.step(T)
+        got = sim.read()
+        green, timer = sim.controller_state()
+        assert sim.heap.check() == 0
+        sim.close()
+        want, wg, wt, _ = orc.nasch_ctrl_run(g, seed, v, T, kind, phase_len=P, lookahead=5)
+        assert np.array_equal(got, want), n
+        guarded = kind >= 0
+        assert np.array_equal(green[guarded], wg[guarded]) and np.array_equal(timer[guarded], wt[guarded]), n
