@@ -251,6 +251,7 @@ def run_gpu(args, ws, rank, local):
     F = int((k0 == 1).sum())
     S = int((k0 == 2).sum())
     enum0, alloc0, free0 = sim.heap.counters()
+    blocks0 = sim.heap.alloc_counters()["enumerated_blocks"]
     clocks = ClockSampler(local)
     if ws > 1:
         torch.distributed.barrier()
@@ -273,6 +274,7 @@ def run_gpu(args, ws, rank, local):
     if ws > 1:
         torch.distributed.barrier()
     enum1, alloc1, free1 = sim.heap.counters()
+    blocks1 = sim.heap.alloc_counters()["enumerated_blocks"]
     sim.sync()
     objects = enum1 - enum0
     assert objects == int(objs_phase.sum()), (objects, objs_phase.sum())
@@ -309,6 +311,16 @@ def run_gpu(args, ws, rank, local):
                 # the same against the nominal HBM3e bandwidth (7.9 TB/s)
                 "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS}
 
+    # the whole step: every do-all's objects x its bytes per object, a
+    # 16-byte bitmap read-modify-write per device new or delete, and 24
+    # bytes (bitmap word read, entry written) per enumerated block
+    step_bytes = (sum(BYTES_PER_OBJECT.get(PHASES[p], 0) * objs_phase[p] for p in range(8))
+                  + 16 * allocfree + 24 * (blocks1 - blocks0))
+    step_achieved = step_bytes / t_local / 1e9
+    step_roofline = {"bound": "hbm", "achieved": step_achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": step_achieved / hbm_peak, "bytes_per_step": step_bytes / args.steps,
+                     "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": step_achieved / NOMINAL_HBM_GBS}
+
     cpu = None
     e2e = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -332,6 +344,7 @@ def run_gpu(args, ws, rank, local):
                        "l2": "flushed (256 MiB write) before every timed step"},
             "alloc_free_per_s": allocfree_all / t_max,
             "roofline": roofline,
+            "step_roofline": step_roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
