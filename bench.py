@@ -154,6 +154,22 @@ def reduce_over_ranks(t_local: float, objects: int, allocfree: int, device):
     return float(v.item()), int(o[0].item()), int(o[1].item())
 
 
+def host_info() -> dict:
+    """The host the CPU legs ran on: logical CPUs, architecture and the
+    processor's model name (from lscpu, when it is there)."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip().lower() == "model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "model": model}
+
+
 def replica_seed(rank: int) -> int:
     """Seed of rank `rank`'s independent replica."""
     return SEED + rank
@@ -205,7 +221,7 @@ def run_reference(args, ws, rank):
         "vs_baseline": None, "dtype": "int32/int16", "data": "synthetic (seeded Philox)",
         "config": {"workload": "wator_2048x2048", "W": W_SIDE, "H": W_SIDE, "seed": SEED,
                    "steps_in_config": CONFIG_STEPS, "instances": 1},
-        "cpu_baseline": {"value": value, "unit": "object-updates/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "object-updates/s", "cores": 1, "kind": "oracle", "host": host_info(),
                          "sample": "Wa-Tor 2048x2048 steps 1..%d from the seeded initial state, "
                                    "single-threaded C oracle" % args.steps},
         "e2e": {"value": value, "unit": "object-updates/s", "h2d_bytes_per_step": 0,
@@ -325,7 +341,7 @@ def run_gpu(args, ws, rank, local):
     e2e = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         upd, dt, _ = oracle_sample(args.cpu_steps)
-        cpu = {"value": upd / dt, "unit": "object-updates/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": upd / dt, "unit": "object-updates/s", "cores": 1, "kind": "oracle", "host": host_info(),
                "sample": "Wa-Tor 2048x2048 steps 1..%d (single-threaded C oracle, %.1f s)"
                          % (args.cpu_steps, dt)}
     if rank == 0 and not args.no_e2e:
@@ -613,7 +629,7 @@ def run_generation(args):
             "compaction_speedup": p["ms_per_generation"] / c["ms_per_generation"],
             # every object is visited by two of the four do-alls per generation
             "cpu_baseline": {"value": 2.0 * float(np.sum(cnt[:, :3])) / cpu_s, "unit": "object-updates/s",
-                             "cores": 1, "kind": "oracle",
+                             "cores": 1, "kind": "oracle", "host": host_info(),
                              "sample": "all %d generations (%.1f s)" % (T, cpu_s)}}
     print(json.dumps(line), flush=True)
     return 0 if (p["bit_exact"] and c["bit_exact"]) else 1
@@ -667,7 +683,7 @@ def run_bh(args):
                       "tree_levels_per_step": (l1 - l0) / args.steps, "tree_nodes_end": nodes,
                       "parity_10_steps_bit_exact": bool(exact),
                       "cpu_baseline": {"value": N * 10 / cpu_s, "unit": "body-steps/s", "cores": 1,
-                                       "kind": "oracle", "sample": "10 steps (%.1f s)" % cpu_s}}), flush=True)
+                                       "kind": "oracle", "host": host_info(), "sample": "10 steps (%.1f s)" % cpu_s}}), flush=True)
     return 0 if exact else 1
 
 
@@ -713,7 +729,7 @@ def run_bfs(args):
                       "config": {"workload": "bfs_road_grid_%dx%d" % (side, side), "vertices": side * side,
                                  "directed_edges": edges, "check_every": args.bfs_check},
                       "bit_exact": bool(np.array_equal(d, want) and lv == wl),
-                      "cpu_baseline": {"value": edges / cpu_s, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                      "cpu_baseline": {"value": edges / cpu_s, "unit": "edges/s", "cores": 1, "kind": "oracle", "host": host_info(),
                                        "sample": "one full search (%.3f s)" % cpu_s}}), flush=True)
     return 0 if np.array_equal(d, want) else 1
 
@@ -803,7 +819,7 @@ def run_structure(args):
         # compute step plus one node visit per BFS level
         n_obj = len(g["kind"]) + len(g["p1"])
         ou = 3 * (2 * 40 * n_obj) + int(oc[:, 4].sum()) * len(g["kind"])
-        cpu = {"value": ou / cpu_s, "unit": "object-updates/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": ou / cpu_s, "unit": "object-updates/s", "cores": 1, "kind": "oracle", "host": host_info(),
                "sample": "3 iterations (%.1f s)" % cpu_s}
     p, c = out["plain"], out["compact_every_50"]
     print(json.dumps({"metric": "object-updates/s", "value": p["object_updates_per_s"], "unit": "object-updates/s",
