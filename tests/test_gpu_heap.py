@@ -221,3 +221,30 @@ def test_bounded_wait_runs_out_and_context_stays_usable():
     h.parallel_do(A, "test.add_i32", smmo.AddI32Args(0, 5))
     (got,) = h.gather(A, h.enumerate_live(A), ["v"])
     assert np.array_equal(np.sort(got.cpu().numpy()), np.arange(640) + 5)
+
+
+def test_calls_on_a_class_without_objects():
+    """Degenerate calls on a class with no objects are no-ops: creating
+    zero objects, a do-all, an enumeration and a gather, a compaction (no
+    candidates: no pass); the class works normally afterwards."""
+    h, A, B, C = make()
+    h.bulk_new(B, 100, [torch.arange(100, dtype=torch.int32, device="cuda"), None])
+    hd, first = h.bulk_new(A, 0, None, want_handles=True)
+    assert hd.numel() == 0 and first == -1
+    h.parallel_do(A, "test.add_i32", smmo.AddI32Args(0, 5))
+    hd = h.enumerate_live(A)
+    assert hd.numel() == 0
+    (v,) = h.gather(A, hd, ["v"])
+    assert v.numel() == 0
+    cs = h.compact(A, 1, 0)
+    assert cs["passes"] == 0 and cs["objects_moved"] == 0 and cs["blocks_freed"] == 0
+    h.sync()
+    assert h.check() == 0
+    st = h.stats()
+    assert st["live_objects"][A] == 0 and st["live_objects"][B] == 100
+    h.bulk_new(A, 70, [torch.arange(70, dtype=torch.int32, device="cuda"), None])
+    h.parallel_do(A, "test.add_i32", smmo.AddI32Args(0, 5))
+    h.sync()
+    _, (vv,) = values(h, A, ["v"])
+    assert np.array_equal(np.sort(vv), np.arange(5, 75))
+    assert h.check() == 0
