@@ -234,9 +234,11 @@ int smmo_enumerate_live(smmo_heap* heap, int class_id, int include_subclasses,
                         int64_t* out_count, void* stream);
 
 /* Copies field columns of n objects into dense arrays: dst[k][i] = column
- * `columns[k]` of object handles[i].  Column indices count inner-array
- * columns (see bulk_new).  handles/dst are device pointers; `columns` and
- * `dst` arrays are host arrays of length ncol.  Asynchronous. */
+ * `columns[k]` of object handles[i], read from the SOA columns of the
+ * objects' blocks (block structure, Sec. 5.2.1).  Column indices count
+ * inner-array columns (see bulk_new).  handles/dst are device pointers;
+ * `columns` and `dst` arrays are host arrays of length ncol.
+ * Asynchronous. */
 int smmo_gather_fields(smmo_heap* heap, int class_id, const smmo_handle* handles,
                        int64_t n, const int* columns, int ncol,
                        void* const* dst, void* stream);
@@ -256,9 +258,9 @@ int smmo_compact(smmo_heap* heap, int class_id, int defrag_factor,
                  int64_t k1, smmo_compact_stats* out, void* stream);
 
 /* Rewrites n caller-held handles (device array) to where the last
- * smmo_compact moved their objects (following its forwarding slots, as the
- * rewrite of the heap's own HANDLE columns does; handles of objects that
- * did not move are unchanged).  Valid until the next allocation: returns
+ * smmo_compact moved their objects (following its forwarding slots,
+ * Sec. 6.3.4, as the rewrite of the heap's own HANDLE columns does,
+ * Sec. 6.3.5; handles of objects that did not move are unchanged).  Valid until the next allocation: returns
  * SMMO_E_UNSUPPORTED once a device new or bulk_new has run since that
  * compaction (the freed source blocks may hold new objects).  Synchronises
  * `stream`. */
@@ -315,7 +317,9 @@ int smmo_heap_last_device_error(smmo_heap* heap, int* code, uint64_t* detail, vo
 
 /* Synchronises `stream` and returns the first device error recorded since
  * the last sync (then clears it).  *detail (host, nullable) receives the
- * error's detail word (e.g. the offending handle). */
+ * error's detail word (e.g. the offending handle).  Device retry loops are
+ * bounded and record SMMO_E_CONTENTION / SMMO_E_DEVICE_OOM here where the
+ * thesis' allocation retries without bound (Alg. 5.1). */
 int smmo_heap_sync(smmo_heap* heap, void* stream, uint64_t* detail);
 
 /* Device pointer to the start of a block's data segment and the column
