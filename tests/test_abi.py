@@ -87,3 +87,27 @@ def test_entry_points_reject_null_objects(libsmmo):
     assert libsmmo.smmo_measure_fp32_peak(0, ctypes.byref(d), None) == -1
     assert libsmmo.smmo_measure_mufu_peak(1, None, None) == -1
     assert libsmmo.smmo_selftest_barrier_timeout(None, 16, None) == -1
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """Without libsmmo.so the binding raises; there is no CPU fallback."""
+    from paper_1908_05845_gb300 import smmo
+    monkeypatch.setattr(smmo, "LIB_PATH", os.path.join(ROOT, "no_such_dir", "libsmmo.so"))
+    monkeypatch.setattr(smmo, "_lib", None)
+    with pytest.raises(smmo.SmmoError):
+        smmo.lib()
+
+
+def test_the_package_never_uses_the_oracle():
+    """Nothing in the product package imports, loads or runs the oracle."""
+    pkg = os.path.join(ROOT, "paper_1908_05845_gb300")
+    bad = []
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath or "__pycache__" in dirpath:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                if re.search(r"^\s*(import oracle|from oracle)|liboracle|oracle\.h|orc_", src, flags=re.M):
+                    bad.append(f)
+    assert not bad, bad
