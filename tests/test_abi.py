@@ -111,3 +111,18 @@ def test_the_package_never_uses_the_oracle():
                 if re.search(r"^\s*(import oracle|from oracle)|liboracle|oracle\.h|orc_", src, flags=re.M):
                     bad.append(f)
     assert not bad, bad
+
+
+def test_the_oracle_shares_no_code_with_the_package():
+    """The oracle includes only its own header and the C library, and its
+    wrapper imports nothing from the product package."""
+    od = os.path.join(ROOT, "oracle")
+    for f in os.listdir(od):
+        p = os.path.join(od, f)
+        if f.endswith((".c", ".h")):
+            incs = re.findall(r'^\s*#\s*include\s*[<"]([^>"]+)[>"]', open(p).read(), flags=re.M)
+            assert all(i == "oracle.h" or "/" not in i and i.endswith(".h") and not i.startswith("smmo") for i in incs), (f, incs)
+            assert "oracle.h" in incs or f == "oracle.h", f
+        elif f.endswith(".py"):
+            assert not re.search(r"^\s*(import|from)\s+paper_1908_05845_gb300|libsmmo", open(p).read(),
+                                 flags=re.M), f
