@@ -23,3 +23,21 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_profile_commands_run_committed_files():
+    """Every ncu command in profiles/ keeps the GPU clocks as they are
+    (--clock-control none) and runs bench.py with options it still has."""
+    import re
+    bench = open(os.path.join(ROOT, "bench.py")).read()
+    pdir = os.path.join(ROOT, "profiles")
+    for f in sorted(os.listdir(pdir)):
+        text = open(os.path.join(pdir, f)).read().replace("\\\n", " ").replace('\\"', "'")
+        cmds = re.findall(r"(?m)^\s*(ncu\s+--.*)$", text) + re.findall(r'"command":\s*"(ncu [^"]*)"', text)
+        assert cmds, f
+        for c in cmds:
+            assert "--clock-control none" in c, (f, c)
+            tail = c.split("python bench.py", 1)
+            if len(tail) == 2:
+                for opt in re.findall(r"(--[a-z][a-z0-9-]*)", tail[1]):
+                    assert '"%s"' % opt in bench, (f, opt)
