@@ -47,7 +47,12 @@ def test_street_graph_and_cars(orc):
     assert g["num_streets"] == S and L.min() >= 100 and L.max() <= 500
     assert within(g["num_cells"], S * 300, np.sqrt(S * (401 ** 2 - 1) / 12))
     assert np.array_equal(g["street_start"], np.concatenate([[0], np.cumsum(L)[:-1]]))
+    s_ids = np.arange(S, dtype=np.uint32)
+    assert np.array_equal(L, 100 + orc.draw(1, inputs.TAG_LEN, 0, s_ids) % 401)
     deg = g["out_deg"]
+    want_deg = 1 + orc.draw(1, inputs.TAG_OUTDEG, 0, s_ids) % 3
+    want_deg[64:128] = 0
+    assert np.array_equal(deg, want_deg)
     assert (g["is_source"][:64] == 1).all() and (g["is_source"][64:] == 0).all()
     assert (deg[64:128] == 0).all() and set(np.unique(np.delete(deg, np.arange(64, 128)))) == {1, 2, 3}
     out = g["out_street"].reshape(S, 3)
