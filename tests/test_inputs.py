@@ -109,3 +109,26 @@ def test_compaction_recipe():
     dead, a_ref, b_ref = inputs.compact_synthetic(n, 1)
     assert within(dead.sum(), 0.6 * n, np.sqrt(0.24 * n))
     assert a_ref.min() >= 0 and a_ref.max() < n and b_ref.min() >= 0 and b_ref.max() < n
+
+
+def test_road_grid_recipe(orc):
+    """Grid edge e (2 v to the right of v, 2 v + 1 below it) is kept iff its
+    draw is below floor(0.71 2^32); the CSR lists both directions with
+    neighbours in increasing id."""
+    side = 64
+    rp, col = inputs.road_grid(side, 3)
+    n = side * side
+    v = np.arange(n)
+    thr = (71 << 32) // 100
+    right = (v % side + 1 < side) & (orc.draw(3, inputs.TAG_EDGE, 0, (2 * v).astype(np.uint32)) < thr)
+    down = (v // side + 1 < side) & (orc.draw(3, inputs.TAG_EDGE, 0, (2 * v + 1).astype(np.uint32)) < thr)
+    want = [[] for _ in range(n)]
+    for u in np.flatnonzero(right):
+        want[u].append(u + 1)
+        want[u + 1].append(u)
+    for u in np.flatnonzero(down):
+        want[u].append(u + side)
+        want[u + side].append(u)
+    assert rp[0] == 0 and rp[-1] == len(col)
+    for u in range(n):
+        assert col[rp[u]:rp[u + 1]].tolist() == sorted(want[u]), u
