@@ -76,9 +76,13 @@ def test_controller_kinds(orc):
     assert set(np.unique(kind[indeg >= 2])) == {0, 1, 2}
 
 
-def test_nbody_recipe():
+def test_nbody_recipe(orc):
     N = 65536
     st = inputs.nbody_initial(N, 1)
+    i = np.arange(N, dtype=np.uint32)
+    for k, c in enumerate(("x", "y", "z")):
+        want = ((orc.draw(1, inputs.TAG_NBODY, k, i).astype(np.float64) + 0.5) / 2.0 ** 32).astype(np.float32)
+        assert np.array_equal(st[c], want), c
     for c in ("x", "y", "z"):
         p = st[c].astype(np.float64)
         assert p.min() > 0 and p.max() < 1
