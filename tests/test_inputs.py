@@ -136,3 +136,38 @@ def test_road_grid_recipe(orc):
     assert rp[0] == 0 and rp[-1] == len(col)
     for u in range(n):
         assert col[rp[u]:rp[u + 1]].tolist() == sorted(want[u]), u
+
+
+def test_mesh_draws(orc):
+    """The spring mesh's random decisions, re-derived from the oracle's
+    Philox: node jitter (+-0.15 on both axes), kept candidate links
+    (probability 0.9, candidate e = 2 v right / 2 v + 1 up), stiffness
+    0.5 + U and break limit 0.005 + 0.045 U, x10 at anchor and pull nodes."""
+    rows, cols, seed = 12, 20, 4
+    g = inputs.structure_mesh(rows, cols, seed)
+    N = rows * cols
+    v = np.arange(N)
+
+    def u(step, idx):
+        return orc.draw(seed, inputs.TAG_MESH, step, np.asarray(idx, np.uint32)).astype(np.float64) / 2.0 ** 32
+
+    assert np.array_equal(g["x"], (v % cols + (u(0, v) - 0.5) * 0.3).astype(np.float32))
+    assert np.array_equal(g["y"], (v // cols + (u(1, v) - 0.5) * 0.3).astype(np.float32))
+    p1, p2 = g["p1"].astype(np.int64), g["p2"].astype(np.int64)
+    e = 2 * p1 + (p2 == p1 + cols)
+    keep = (9 << 32) // 10
+    drawn = orc.draw(seed, inputs.TAG_MESH, 4, e.astype(np.uint32)) < keep
+    # a link is kept by its draw, or as the only link of a node that kept none
+    lonely = ~drawn
+    assert all(g["nspr"][p1[j]] == 1 or g["nspr"][p2[j]] == 1 for j in np.flatnonzero(lonely))
+    # every existing candidate whose draw keeps it is in the mesh
+    kept = set(e.tolist())
+    for a in range(N):
+        r, c = divmod(a, cols)
+        for ee, ok in ((2 * a, c + 1 < cols), (2 * a + 1, r + 1 < rows and (r + c) % 2 == 0)):
+            if ok and orc.draw(seed, inputs.TAG_MESH, 4, np.array([ee], np.uint32))[0] < keep:
+                assert ee in kept, ee
+    assert np.array_equal(g["k"], (0.5 + u(2, e)).astype(np.float32))
+    f = 0.005 + 0.045 * u(3, e)
+    clamp = (g["kind"][p1] != 2) | (g["kind"][p2] != 2)
+    assert np.array_equal(g["fmax"], np.where(clamp, f * 10.0, f).astype(np.float32))
