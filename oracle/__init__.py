@@ -1,13 +1,15 @@
 """CPU oracle for the SMMO hot path -- TEST INFRASTRUCTURE ONLY.
 
-A plain, slow, single-threaded array-of-structs restatement (in C, see the
+A plain, slow, array-of-structs restatement (in C, see the
 ``*.c`` files beside this one) of the thesis' SMMO workloads: object-based
 Game of Life and the generational automaton (Sec. 7.8), Wa-Tor (Sec. 7.6),
 Nagel-Schreckenberg traffic with and without traffic controllers
 (Sec. 7.5), n-body with collision merge (Sec. 7.1/7.2) and the n-body
 adjoint, Barnes-Hut (Sec. 7.3), the spring mesh "structure" (Sec. 7.4) and
 frontier BFS (Sec. 4.3).  It has its own Philox4x32-10 (Salmon et al.,
-SC'11).
+SC'11).  Everything runs on one thread except the n-body receiver loops,
+which OpenMP may spread over cores (each receiver keeps its partner order,
+so results do not depend on the thread count; ``set_threads``).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
 leg may import this package.  It never imports the CUDA library and the CUDA
@@ -56,7 +58,8 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction, strict IEEE)."""
+    """Compile the oracle with gcc (no FMA contraction, strict IEEE; OpenMP
+    for the n-body receiver loops only)."""
     srcs = [os.path.join(_HERE, s) for s in _SOURCES]
     deps = srcs + [os.path.join(_HERE, "oracle.h")]
     if (not force and os.path.exists(_LIB_PATH)
@@ -65,7 +68,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", "-o", tmp] + srcs + ["-lm"]
+           "-fno-fast-math", "-fopenmp", "-o", tmp] + srcs + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -81,6 +84,12 @@ def _load():
 
 def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def set_threads(n: int) -> int:
+    """Threads for the n-body receiver loops (n <= 0: OpenMP's default, all
+    cores); returns the count now in use.  Results do not depend on it."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 # ------------------------------------------------------------------ Philox
@@ -162,6 +171,20 @@ def wator_run(W, H, seed, kind, age, energy, T, t0=0, inst=0, fish_breed=4,
     if rc != 0:
         raise ValueError("orc_wator_run: bad arguments")
     return kind, age, energy, cnt[:T]
+
+
+def batched_instance_run(job):
+    """One instance of a batched heap run alone, for a process pool (a
+    top-level function, so a spawned worker can unpickle it).  job = (index,
+    kind 0 Life / 1 Wa-Tor, side, seed, k, a, e, s, T); returns (index,
+    kind, age, energy, state) per cell after T steps, with the arrays of the
+    kind that does not have them zero."""
+    i, kind, side, seed, k, a, e, s, T = job
+    if kind == 0:
+        wk, ws, _ = gol_run(side, side, np.asarray(k).astype(np.uint8), s, T)
+        return i, wk.astype(np.int8), np.zeros_like(a), np.zeros_like(e), ws
+    wk, wa, we, _ = wator_run(side, side, seed, k, a, e, T, inst=i)
+    return i, wk, wa, we, np.zeros_like(s)
 
 
 # ------------------------------------------------------ Nagel-Schreckenberg

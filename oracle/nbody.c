@@ -40,12 +40,31 @@
 #include <string.h>
 #include "oracle.h"
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads for the receiver loops below (n <= 0: the OpenMP default).
+ * Returns the number now in use (1 without OpenMP). */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 /* ---------------------------------------------------------------- FP32 */
 int orc_nbody_accel_f32(int N, float G, float eps, const float* x,
                         const float* y, const float* z, const float* m,
                         const uint8_t* live, float* ax, float* ay, float* az) {
   if (N < 0) return -1;
   const float eps2 = eps * eps;
+  /* receivers are independent; each sums its j in increasing order, so the
+   * result does not depend on the number of threads */
+#pragma omp parallel for schedule(dynamic, 64)
   for (int i = 0; i < N; ++i) {
     float sx = 0.0f, sy = 0.0f, sz = 0.0f;
     if (live[i]) {
@@ -81,7 +100,8 @@ static int64_t merge_pass(int N, float R, float* x, float* y, float* z,
   const float R2 = R * R;
   for (int i = 0; i < N; ++i) { pick[i] = -1; target[i] = -1; }
   /* prepare merge: receiver b scans bodies in id order, stops at the first
-   * lighter body within the threshold */
+   * lighter body within the threshold (receivers are independent) */
+#pragma omp parallel for schedule(dynamic, 64)
   for (int b = 0; b < N; ++b) {
     if (!live[b]) continue;
     for (int j = 0; j < N; ++j) {
@@ -208,6 +228,7 @@ int orc_nbody_accel_f64(int N, double G, double eps, const double* pos,
                         const double* m, double* acc) {
   if (N < 0) return -1;
   const double e2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 64)
   for (int i = 0; i < N; ++i) {
     double s[3] = {0, 0, 0};
     for (int j = 0; j < N; ++j) {
@@ -263,6 +284,7 @@ int orc_nbody_pair_adjoint_f64(int N, double G, double eps, const double* pos,
                                const double* m, const double* mu, double* g) {
   if (N < 0) return -1;
   const double e2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 64)
   for (int k = 0; k < N; ++k) {
     double acc[3] = {0, 0, 0};
     for (int j = 0; j < N; ++j) {

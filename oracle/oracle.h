@@ -1,8 +1,8 @@
 /*
  * oracle.h -- CPU oracle for the SMMO hot path (TEST INFRASTRUCTURE ONLY).
  *
- * This is a plain, slow, single-threaded array-of-structs restatement of the
- * four SMMO workloads of the thesis (Springer, "Memory-Efficient
+ * This is a plain, slow, array-of-structs restatement of the
+ * SMMO workloads of the thesis (Springer, "Memory-Efficient
  * Object-Oriented Programming on GPUs", Ch. 7) plus its own Philox4x32-10.
  * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may
  * load it.  It shares no code, header or constant generator with the CUDA
@@ -10,6 +10,11 @@
  * in common are the seeded input arrays built by
  * paper_1908_05845_gb300/inputs.py, which contain none of the method's
  * arithmetic.
+ *
+ * Everything runs on one thread except the n-body receiver loops (FP32
+ * forces and merge scan, FP64 forces and pair adjoint), which OpenMP may
+ * spread over several: each receiver keeps its own partner order, so the
+ * results do not depend on the thread count (orc_set_threads).
  *
  * Every entry point returns 0 on success and a negative value on bad
  * arguments.  All arrays are caller-owned host memory.
@@ -146,6 +151,9 @@ typedef struct {
 int orc_nbody_run_f32(int N, const orc_nbody_params_f32* p, float* x, float* y,
                       float* z, float* vx, float* vy, float* vz, float* m,
                       uint8_t* live, int T, int64_t* counters);
+/* Threads for the n-body receiver loops (n <= 0: OpenMP's default);
+ * returns the count now in use (1 when built without OpenMP). */
+int orc_set_threads(int n);
 /* Accelerations only (one force evaluation), FP32, same order as the run. */
 int orc_nbody_accel_f32(int N, float G, float eps, const float* x,
                         const float* y, const float* z, const float* m,

@@ -244,3 +244,25 @@ def test_f32_trajectory_sweep_agrees_with_f64_adjoint_on_short_horizon(orc):
         g32, L32 = orc.nbody_adjoint_f32traj(st, T)
         assert abs(L32 - L64) / L64 < 1e-5
         assert np.linalg.norm(g32 - g64) / np.linalg.norm(g64) < tol
+
+
+def test_thread_count_does_not_change_any_result(orc):
+    """The receiver loops may run on several threads (each receiver keeps
+    its partner order): 1 and 8 threads give bit-identical FP32 runs with
+    merges, FP64 forces and FP64 pair-adjoint terms."""
+    st = inputs.nbody_initial(1500, 2)
+    pos, vel, m = as64(st)
+    mu = np.random.default_rng(1).normal(size=pos.shape)
+    outs = []
+    try:
+        for th in (1, 8):
+            orc.set_threads(th)
+            run, k = orc.nbody_run_f32(st, 6, merge_r=3e-2)
+            outs.append((run, k, orc.nbody_accel_f64(pos, m), orc.nbody_pair_adjoint_f64(pos, m, mu)))
+    finally:
+        orc.set_threads(0)
+    (r1, k1, a1, g1), (r8, k8, a8, g8) = outs
+    assert k1.sum() > 0 and np.array_equal(k1, k8)
+    for key in ("x", "y", "z", "vx", "vy", "vz", "m", "live"):
+        assert np.array_equal(r1[key], r8[key]), key
+    assert np.array_equal(a1, a8) and np.array_equal(g1, g8)
