@@ -417,19 +417,17 @@ def _events(stream):
 
 def batched_init(seed, n):
     from paper_1908_05845_gb300 import inputs
-    from paper_1908_05845_gb300.workloads import LIFE
-    kinds, sides = inputs.batched_instances(seed, n)
-    ks, ags, ens, sts = [], [], [], []
-    for i, (kd, sd) in enumerate(zip(kinds, sides)):
-        if kd == LIFE:
-            k, s = inputs.gol_initial(sd, sd, seed, inst=i)
-            a = np.zeros(sd * sd, np.int16)
-            e = np.zeros(sd * sd, np.int16)
-        else:
-            k, a, e = inputs.wator_initial(sd, sd, seed, inst=i)
-            s = np.zeros(sd * sd, np.uint8)
-        ks.append(k.astype(np.int8)); ags.append(a); ens.append(e); sts.append(s)
-    return kinds, sides, (np.concatenate(ks), np.concatenate(ags), np.concatenate(ens), np.concatenate(sts))
+    return inputs.batched_initial(seed, n)
+
+
+def batched_parity_sample(kinds, sides, k_want=16):
+    """Instances whose end state the batched bench compares with the
+    oracle: the 8 largest and the rest spread evenly over the sizes."""
+    order = np.argsort(-sides.astype(np.int64), kind="stable")
+    big = [int(i) for i in order[:8]]
+    rest = order[8:]
+    spread = [int(rest[j]) for j in np.linspace(0, len(rest) - 1, max(0, k_want - 8)).round().astype(int)] if len(rest) else []
+    return sorted(set(big + spread))
 
 
 def run_batched(args):
@@ -477,9 +475,9 @@ def run_batched(args):
             sl = slice(offs[i], offs[i + 1])
             worlds.append(World([kinds[i]], [sides[i]], [sides[i]], SEED, *(x[sl] for x in init),
                                 config=smmo.default_config(**cfg),
-                                heap_bytes=heap_bytes_for(int(sides[i]) ** 2), stream=stream))
-        # instance ids: every per-instance world draws with instance 0; the
-        # batched one with the instance index, so only timing is compared
+                                heap_bytes=heap_bytes_for(int(sides[i]) ** 2), stream=stream, inst_ids=[i]))
+        # every per-instance world draws with its instance's number, so both
+        # arms simulate the same instances
         for x in worlds:
             x.step(args.warmup)
         e0 = sum(x.heap.counters()[0] for x in worlds)
@@ -508,20 +506,26 @@ def run_batched(args):
         res["per_instance_graphs"] = objs_g / t_g
         for x in worlds:
             x.close()
-    # parity of a sample of instances against the oracle
+    # parity of a sample of instances against the oracle (a spawned pool:
+    # the CUDA context exists already)
+    import multiprocessing as mp
     import oracle
     from paper_1908_05845_gb300.workloads import LIFE
     checked = []
-    for i in [int(j) for j in np.argsort(sides)[:3]]:
+    jobs = []
+    for i in batched_parity_sample(kinds, sides):
         sl = slice(offs[i], offs[i + 1])
-        sd = int(sides[i])
-        if kinds[i] == LIFE:
-            wk, ws, _ = oracle.gol_run(sd, sd, init[0][sl].astype(np.uint8), init[3][sl], steps_done)
-            ok = np.array_equal(k_gpu[sl].astype(np.uint8), wk) and np.array_equal(s_gpu[sl], ws)
-        else:
-            wk, wa, we, _ = oracle.wator_run(sd, sd, SEED, init[0][sl], init[1][sl], init[2][sl], steps_done, inst=i)
-            ok = np.array_equal(k_gpu[sl], wk) and np.array_equal(a_gpu[sl], wa) and np.array_equal(e_gpu[sl], we)
-        checked.append({"instance": i, "side": sd, "kind": "life" if kinds[i] == LIFE else "wator", "bit_exact": bool(ok)})
+        jobs.append((i, int(kinds[i]), int(sides[i]), SEED, *(x[sl] for x in init), steps_done))
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        for i, wk, wa, we, ws in pool.imap_unordered(oracle.batched_instance_run, jobs):
+            sl = slice(offs[i], offs[i + 1])
+            if kinds[i] == LIFE:
+                ok = np.array_equal(k_gpu[sl], wk) and np.array_equal(s_gpu[sl], ws)
+            else:
+                ok = np.array_equal(k_gpu[sl], wk) and np.array_equal(a_gpu[sl], wa) and np.array_equal(e_gpu[sl], we)
+            checked.append({"instance": i, "side": int(sides[i]), "kind": "life" if kinds[i] == LIFE else "wator",
+                            "bit_exact": bool(ok)})
+    checked.sort(key=lambda r: -r["side"])
     line = {"metric": "object-updates/s", "value": res["batched"], "unit": "object-updates/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_b / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/int16",

@@ -65,7 +65,11 @@ typedef uint32_t smmo_handle;
 enum {
   SMMO_I8 = 1, SMMO_U8 = 2, SMMO_I16 = 3, SMMO_U16 = 4, SMMO_I32 = 5,
   SMMO_U32 = 6, SMMO_F32 = 7, SMMO_I64 = 8, SMMO_U64 = 9, SMMO_F64 = 10,
-  SMMO_HANDLE = 11 /* a smmo_handle (4 bytes) */
+  SMMO_HANDLE = 11, /* a smmo_handle (4 bytes) */
+  /* uint32 index of the object's instance in the heap's instance table
+   * (smmo_batch_define); bulk_new records SMMO_E_BOUNDS for an index
+   * outside the table */
+  SMMO_INSTANCE = 12
 };
 
 #define SMMO_MAX_CLASSES 16
@@ -107,6 +111,12 @@ typedef struct {
    * floor(N_T n / (n + 1)) objects.  Warp caches refill from candidates
    * first.  Default 1 (at most half full). */
   int32_t defrag_factor;
+  /* Fan-out of the hierarchical bitmaps (Sec. 5.3.1): bits per container,
+   * 32 or 64 (default 64).  A container of 32 is half of a 64-bit word, so
+   * level 0 is stored the same way for both; with 32 every level above
+   * has one bit per 32 bits below it (one more level for large heaps, a
+   * lookup descends a narrower word). */
+  int32_t bitmap_fanout;
 } smmo_heap_config;
 
 /* Fills `cfg` with the defaults above. */
@@ -174,19 +184,54 @@ int smmo_class_info(smmo_heap* heap, int class_id, int* nfields,
 int smmo_heap_freeze(smmo_heap* heap);
 
 /* Methods are compiled into the library and looked up by name, e.g.
- * "test.add_i32", "wator.fish_prepare" (see the workload sections). */
-int smmo_method_lookup(const char* name, int* method_id);
+ * "test.add_i32", "wator.fish_prepare" (see the workload sections); the
+ * thesis' methods are members of the classes (Sec. 5.1.1), here they are
+ * kernels that take the class as an argument.  heap may be NULL (the id
+ * is the same for every heap); with a heap whose geometry is fixed, a
+ * method that needs a batch (the test.batch_* methods) is rejected
+ * (SMMO_E_UNSUPPORTED) when the heap has no instance table. */
+int smmo_method_lookup(smmo_heap* heap, const char* name, int* method_id);
+
+/* ----------------------------------------------------------- batches
+ * A batch is a set of independent problem instances whose objects share
+ * one heap: one parallel_do of a class runs the method on the objects of
+ * every instance in a single launch (the thesis' parallel_do, Sec. 5.2.7,
+ * over all objects of a class, whatever instance they belong to).  The
+ * instance table is owned by the heap and lives in its buffer; an object
+ * names its instance in a SMMO_INSTANCE field, and a method reads the
+ * instance's row through the heap (device code: smmo::instance_of).
+ * Instances that own a range of a global numbering (the cells of the
+ * cellular worlds) can also be found from an index in their range. */
+typedef struct {
+  int32_t kind;      /* caller-defined kind (the worlds: SMMO_WORLD_*)     */
+  uint32_t id;       /* the instance's number in its random counters       */
+  uint32_t W, H;     /* grid extent (0 when the instance has no grid)      */
+  uint64_t base;     /* first index of its range of a global numbering     */
+  uint64_t count;    /* length of that range (0: none)                     */
+  int64_t param[2];  /* caller-defined parameters                          */
+} smmo_instance_desc;
+/* Gives the heap its instance table: n_inst (1 .. 2^20) rows, copied (host
+ * array `inst`).  Ranges [base, base + count) must ascend and not overlap,
+ * and end below 2^32.  Must precede the first bulk_new / freeze (else
+ * SMMO_E_FROZEN); once per heap.  The table is carved from the heap
+ * buffer when the geometry is fixed. */
+int smmo_batch_define(smmo_heap* heap, const smmo_instance_desc* inst, int n_inst);
+/* Instances in the heap's table (0: none) into *n_inst (host). */
+int smmo_batch_count(smmo_heap* heap, int* n_inst);
 
 /* Host-launched creation of n objects of a concrete class (the thesis'
  * parallel_new, Sec. 5.1.1).  field_src[k] is a device array of n elements
  * for SOA column k (columns are the fields in order, an inner array of
  * `count` elements contributing `count` columns).  Objects fill whole free
  * blocks in ascending block order; out_handles (device, nullable) receives
- * their handles.  out_first_block (host, nullable) receives the first
- * block index when the blocks used are consecutive, else -1 (objects i
- * then sit at block first + i / N_T, slot i % N_T).  Synchronises
- * `stream`.  SMMO_E_OOM if the heap has fewer than ceil(n / N_T) free
- * blocks. */
+ * their handles.  Asynchronous on `stream` (capturable) unless
+ * out_first_block is given: then it synchronises `stream` and writes the
+ * first block index when the blocks used are consecutive, else -1 (objects
+ * i then sit at block first + i / N_T, slot i % N_T).  Fixing the geometry
+ * (the first bulk_new of a heap) also synchronises.  SMMO_E_OOM at once if
+ * ceil(n / N_T) exceeds the heap's block count; if fewer blocks are free
+ * when the kernels run, nothing is created and SMMO_E_OOM is recorded in
+ * the device error word (smmo_heap_sync; synchronous calls return it). */
 int smmo_bulk_new(smmo_heap* heap, int class_id, int64_t n,
                   const void* const* field_src, smmo_handle* out_handles,
                   int64_t* out_first_block, void* stream);
@@ -351,8 +396,11 @@ typedef struct {
 } smmo_wator_params;
 
 /* Registers the classes in a fresh heap (no class registered yet, else
- * SMMO_E_FROZEN) and creates the instances.  kind/W/H: host arrays of
- * n_inst entries (W, H >= 3).  Per-cell initial state: device arrays over
+ * SMMO_E_FROZEN), gives the heap its instance table (smmo_batch_define:
+ * instance i has kind[i], W[i] x H[i] cells starting at the sum of the
+ * sizes before it, and draws with instance number i) and creates the
+ * instances.  kind/W/H: host arrays of n_inst entries (W, H >= 3).
+ * Per-cell initial state: device arrays over
  * the concatenation of all instances' cells in instance order, row-major
  * (cell = y * W + x): init_kind (Life: 0 empty, 1 Alive, 2 Candidate;
  * Wa-Tor: 0 empty, 1 Fish, 2 Shark), init_age (Wa-Tor: age; Life: the
@@ -360,7 +408,7 @@ typedef struct {
  * init_energy (Wa-Tor, nullable = 0), init_state (Life is_new flag,
  * nullable = 0).  params may be NULL.  Life-kind instances start with the
  * Life rule (see smmo_world_set_life_rule).  Synchronises `stream`.  The
- * world allocates two small instance tables with cudaMalloc, freed by
+ * world allocates its 4-byte step counter with cudaMalloc, freed by
  * smmo_world_destroy. */
 int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind,
                       const uint32_t* W, const uint32_t* H, uint64_t seed,
@@ -368,6 +416,16 @@ int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind,
                       const int16_t* init_age, const int16_t* init_energy,
                       const uint8_t* init_state, void* stream,
                       smmo_world** out);
+/* As smmo_world_create with the instance table given as rows (host array
+ * of n_inst): kind, id (the instance number of its draws, any value, so
+ * one instance of a larger batch can be run alone with its own draws), W
+ * and H are used; base and count must be the running sum of the sizes
+ * and W x H (else SMMO_E_INVALID_ARG); param is ignored. */
+int smmo_world_create_batch(smmo_heap* heap, const smmo_instance_desc* inst, int n_inst,
+                            uint64_t seed, const smmo_wator_params* params,
+                            const int8_t* init_kind, const int16_t* init_age,
+                            const int16_t* init_energy, const uint8_t* init_state,
+                            void* stream, smmo_world** out);
 /* Advances every instance by nsteps steps.  Asynchronous (host loop of
  * parallel_do launches; capturable in a CUDA graph). */
 int smmo_world_step(smmo_world* w, int nsteps, void* stream);

@@ -319,13 +319,12 @@ __global__ void __launch_bounds__(256) k_rewrite(HeapView h, uint32_t u_cls, Rew
 // Level l of a hierarchical bitmap as the OR of the containers below (the
 // restore of defrag[c] after a compaction used its level 0 as scratch).
 __global__ void k_rebuild_level(HeapView h, int k, uint32_t l) {
-  const unsigned long long* lo = bm_level(h, k, l - 1);
   unsigned long long* hi = bm_level(h, k, l);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < h.level_words[l]; i += gridDim.x * blockDim.x) {
     unsigned long long v = 0;
-    for (uint32_t j = 0; j < 64; ++j) {
-      const uint64_t q = (uint64_t)i * 64 + j;
-      if (q < h.level_words[l - 1] && lo[q]) v |= 1ull << j;
+    for (uint32_t j = 0; j < 64; ++j) {  // bit q of level l: container q of level l - 1
+      const uint32_t q = i * 64 + j;
+      if (q < h.level_bits[l] && bm_container(h, k, l - 1, q)) v |= 1ull << j;
     }
     hi[i] = v;
   }

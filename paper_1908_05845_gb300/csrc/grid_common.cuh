@@ -30,16 +30,6 @@ __device__ __forceinline__ uint32_t philox_draw(uint64_t seed, uint32_t tag, uin
 // Random-stream tags of the step draws.
 enum : uint32_t { TAG_FISH = 1, TAG_SHARK = 2, TAG_ROUTE = 5, TAG_BRAKE = 6 };
 
-// One simulation instance of a (batched) heap: its cells occupy the global
-// cell range [cell_base, cell_base + W*H) of the dense Cell objects.
-struct Inst {
-  uint32_t cell_base;
-  uint32_t W;
-  uint32_t H;
-  uint32_t id;    // instance number used in the random counter
-  uint64_t wdiv;  // div_magic(W)
-};
-
 // Division by the invariant width W as a multiply-high (Granlund and
 // Montgomery, PLDI 1994): with M = floor((2^64 - 1) / W) + 1 the product
 // lc M / 2^64 exceeds lc / W by less than lc / 2^64 < 1 / W for lc < 2^32,
@@ -53,14 +43,12 @@ __device__ __forceinline__ void cell_xy(const Inst* in, uint32_t lc, uint32_t* x
   *x = lc - q * in->W;
 }
 
-// Instance owning global cell g (instances sorted by cell_base).
-__device__ __forceinline__ const Inst* find_inst(const Inst* tab, uint32_t n, uint32_t g) {
-  uint32_t lo = 0, hi = n;  // invariant: tab[lo].cell_base <= g
-  while (hi - lo > 1) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (__ldg(&tab[mid].cell_base) <= g) lo = mid; else hi = mid;
-  }
-  return tab + lo;
+// Instance owning global cell g: the heap's instance-table row whose cell
+// range holds g (one simulation instance of a batched heap; its cells
+// occupy the global range [cell_base, cell_base + W*H) of the dense Cell
+// objects).
+__device__ __forceinline__ const Inst* find_inst(const HeapView& h, uint32_t g) {
+  return instance_at(h.inst, h.n_inst, g);
 }
 
 // The Cell objects are created by one bulk_new into consecutive blocks of

@@ -21,7 +21,7 @@ int esize(int t) {
   switch (t) {
     case SMMO_I8: case SMMO_U8: return 1;
     case SMMO_I16: case SMMO_U16: return 2;
-    case SMMO_I32: case SMMO_U32: case SMMO_F32: case SMMO_HANDLE: return 4;
+    case SMMO_I32: case SMMO_U32: case SMMO_F32: case SMMO_HANDLE: case SMMO_INSTANCE: return 4;
     case SMMO_I64: case SMMO_U64: case SMMO_F64: return 8;
     default: return 0;
   }
@@ -69,6 +69,9 @@ __global__ void __launch_bounds__(256) k_enumerate(HeapView h, int c) {
   const unsigned long long* L0 = bm_level(h, bm_alloc(h, c), 0);
   const unsigned long long* L1 = h.nlevels > 1 ? bm_level(h, bm_alloc(h, c), 1) : nullptr;
   const uint32_t nw = h.level_words[0];
+  // level-1 bits of the containers of one level-0 word (1 or 2 of them)
+  const uint32_t per_word = 6 - h.bm_shift;
+  const unsigned long long l1mask = (1ull << (1u << per_word)) - 1;
   const unsigned long long capmask = h.cls[c].capmask;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -78,7 +81,10 @@ __global__ void __launch_bounds__(256) k_enumerate(HeapView h, int c) {
   for (uint32_t r = 0; r < rounds; ++r) {
     const uint32_t w = r * nwarps + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     unsigned long long word = 0;
-    if (w < nw && (!L1 || ((L1[w >> 6] >> (w & 63)) & 1))) word = L0[w];
+    if (w < nw) {
+      const uint32_t c0 = w << per_word;  // first container of word w
+      if (!L1 || ((L1[c0 >> 6] >> (c0 & 63)) & l1mask)) word = L0[w];
+    }
     if (lane == 0) wcnt[warp] = (uint32_t)__popcll(word);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -155,6 +161,10 @@ __global__ void __launch_bounds__(1024) k_find_free(HeapView h, uint32_t want, u
 // in order (block j holds objects j*cap .. j*cap+cap-1).
 __global__ void k_bulk_claim(HeapView h, uint32_t c, const uint32_t* list, uint32_t nb,
                              uint64_t n, uint32_t cap, unsigned long long capmask) {
+  if (h.st->aux[0] < nb) {  // k_find_free found too few free blocks
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_error(h, SMMO_E_OOM, nb);
+    return;
+  }
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += gridDim.x * blockDim.x) {
     const uint32_t bid = list[j];
     if (!bm_try_clear(h, bm_free(), bid)) { set_error(h, SMMO_E_CONTENTION, bid); continue; }
@@ -184,9 +194,10 @@ __device__ __forceinline__ void copy_elem(void* dst, const void* src, uint32_t s
 }
 
 __global__ void k_bulk_copy(HeapView h, uint32_t c, const uint32_t* list, uint64_t n,
-                            ColSrc src, uint32_t ncols, uint32_t* out_handles) {
+                            ColSrc src, uint32_t ncols, uint32_t* out_handles, uint32_t nb) {
   const ClassLayout& L = h.cls[c];
   const uint32_t cap = L.cap;
+  if (h.st->aux[0] < nb) return;  // too few free blocks: k_bulk_claim recorded OOM
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t bid = list[i / cap];
@@ -198,6 +209,10 @@ __global__ void k_bulk_copy(HeapView h, uint32_t c, const uint32_t* list, uint64
         copy_elem(blk + L.col_off[k] + (size_t)slot * sz, (const uint8_t*)src.p[k] + i * sz, sz);
     }
     if (out_handles) out_handles[i] = (bid << 6) | slot;
+    if (L.inst_col >= 0) {  // an instance index must name a row of the table
+      const uint32_t k = *reinterpret_cast<const uint32_t*>(blk + L.col_off[L.inst_col] + (size_t)slot * 4);
+      if (k >= h.n_inst) set_error(h, SMMO_E_BOUNDS, ((unsigned long long)k << 32) | ((bid << 6) | slot));
+    }
   }
 }
 
@@ -279,14 +294,19 @@ __global__ void __launch_bounds__(256) k_stats(HeapView h) {
 __global__ void k_check_levels(HeapView h, int k) {
   unsigned long long bad = 0;
   for (uint32_t l = 1; l < h.nlevels; ++l) {
-    const unsigned long long* lo = bm_level(h, k, l - 1);
     const unsigned long long* hi = bm_level(h, k, l);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < h.level_words[l - 1];
+    // bit i of level l for every container i of level l - 1
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < h.level_bits[l];
          i += gridDim.x * blockDim.x) {
-      const bool want = lo[i] != 0;
+      const bool want = bm_container(h, k, l - 1, i) != 0;
       const bool have = (hi[i >> 6] >> (i & 63)) & 1;
       if (want != have) ++bad;
     }
+    // bits past the last container stay clear
+    const uint32_t top = h.level_words[l] * 64;
+    for (uint32_t i = h.level_bits[l] + blockIdx.x * blockDim.x + threadIdx.x; i < top;
+         i += gridDim.x * blockDim.x)
+      if ((hi[i >> 6] >> (i & 63)) & 1) ++bad;
   }
   if (bad) atomicAdd(&h.st->aux[2], bad);
 }
@@ -421,6 +441,7 @@ int freeze(smmo_heap* h, cudaStream_t s) {
     if (!ci.abstract && cap < 2) return SMMO_E_UNSUPPORTED;
     L.cap = (uint32_t)cap;
     L.ncols = (uint32_t)ci.ncols;
+    L.inst_col = -1;
     L.capmask = cap >= 64 ? kAll : ((1ull << cap) - 1);
     L.dlimit = (uint32_t)((uint64_t)cap * (uint64_t)h->cfg.defrag_factor / (uint64_t)(h->cfg.defrag_factor + 1));
     size_t off = 0;
@@ -428,6 +449,7 @@ int freeze(smmo_heap* h, cudaStream_t s) {
     for (auto& f : ci.fields)
       for (int k = 0; k < f.count; ++k) {
         off = align_up(off, 16);
+        if (f.elem_type == SMMO_INSTANCE && L.inst_col < 0) L.inst_col = col;
         L.col_off[col] = (uint32_t)off;
         L.col_size[col] = (uint32_t)esize(f.elem_type);
         off += (size_t)cap * esize(f.elem_type);
@@ -440,26 +462,33 @@ int freeze(smmo_heap* h, cudaStream_t s) {
   const size_t fixed = align_up(sizeof(DeviceState), 256) +
                        align_up(sizeof(ClassLayout) * SMMO_MAX_CLASSES, 256) + 8 * 256;
   if (h->buf_bytes <= fixed) return SMMO_E_OOM;
-  auto bm_geom = [](uint64_t M, uint32_t* lw, uint32_t* lo, uint32_t* nl) {
+  // levels of F-bit containers (F = bitmap fan-out): level 0 has M bits,
+  // level l + 1 one bit per container of level l, up to a level that is a
+  // single container; each level is stored in whole 64-bit words
+  const uint32_t fshift = h->cfg.bitmap_fanout == 32 ? 5u : 6u;
+  auto bm_geom = [fshift](uint64_t M, uint32_t* lw, uint32_t* lo, uint32_t* lb, uint32_t* nl) {
     uint64_t bits = M, off = 0;
     int l = 0;
-    do {
+    for (;;) {
       const uint64_t w = (bits + 63) / 64;
       lw[l] = (uint32_t)w;
       lo[l] = (uint32_t)off;
+      lb[l] = (uint32_t)bits;
       off += w;
-      bits = w;
       ++l;
-    } while (bits > 1 && l < SMMO_MAX_LEVELS);
+      if (bits <= (1ull << fshift) || l == SMMO_MAX_LEVELS) break;
+      bits = (bits + (1ull << fshift) - 1) >> fshift;
+    }
     *nl = (uint32_t)l;
-    return (uint64_t)align_up(off, 32);
+    return bits <= (1ull << fshift) ? (uint64_t)align_up(off, 32) : 0ull;  // 0: too many levels
   };
+  const size_t inst_bytes = h->batch.size() * sizeof(Inst);
   auto need_bytes = [&](uint64_t M) {
-    uint32_t lw[SMMO_MAX_LEVELS], lo[SMMO_MAX_LEVELS], nl;
-    const uint64_t bw = bm_geom(M, lw, lo, &nl);
+    uint32_t lw[SMMO_MAX_LEVELS], lo[SMMO_MAX_LEVELS], lb[SMMO_MAX_LEVELS], nl;
+    const uint64_t bw = bm_geom(M, lw, lo, lb, &nl);
     return fixed + align_up(M * 8, 256) + align_up(M * 4, 256) + align_up(rscratch_bytes(M), 256) +
            align_up(M * 4 + 1024, 256) + align_up((M + 63) / 64 * 8, 256) + align_up(bw * 8 * nbm, 256) +
-           M * block_bytes;
+           align_up(inst_bytes, 256) + M * block_bytes;
   };
   uint64_t M = h->buf_bytes / (block_bytes + 40);
   M = std::min<uint64_t>(M, (1ull << 26) - 1);
@@ -467,8 +496,9 @@ int freeze(smmo_heap* h, cudaStream_t s) {
   if (M < 2) return SMMO_E_OOM;
   HeapView& v = h->view;
   memset(&v, 0, sizeof(v));
-  uint32_t lw[SMMO_MAX_LEVELS], lo[SMMO_MAX_LEVELS], nl;
-  const uint64_t bw = bm_geom(M, lw, lo, &nl);
+  uint32_t lw[SMMO_MAX_LEVELS], lo[SMMO_MAX_LEVELS], lb[SMMO_MAX_LEVELS], nl;
+  const uint64_t bw = bm_geom(M, lw, lo, lb, &nl);
+  if (bw == 0) return SMMO_E_UNSUPPORTED;
   uint8_t* p = h->buf;
   auto take = [&](size_t bytes) { uint8_t* r = p; p += align_up(bytes, 256); return r; };
   v.st = (DeviceState*)take(sizeof(DeviceState));
@@ -481,12 +511,16 @@ int freeze(smmo_heap* h, cudaStream_t s) {
   h->d_scratch = (uint32_t*)take(M * 4 + 1024);
   h->d_moved = (unsigned long long*)take((M + 63) / 64 * 8);
   v.bitmaps = (unsigned long long*)take(bw * 8 * nbm);
+  h->d_inst = h->batch.empty() ? nullptr : (Inst*)take(inst_bytes);
+  v.inst = h->d_inst;
+  v.n_inst = (uint32_t)h->batch.size();
   v.data = p;
   v.block_bytes = (uint32_t)block_bytes;
   v.num_blocks = (uint32_t)M;
   v.bm_words = (uint32_t)bw;
   v.nlevels = nl;
-  for (uint32_t l = 0; l < nl; ++l) { v.level_words[l] = lw[l]; v.level_off[l] = lo[l]; }
+  v.bm_shift = fshift;
+  for (uint32_t l = 0; l < nl; ++l) { v.level_words[l] = lw[l]; v.level_off[l] = lo[l]; v.level_bits[l] = lb[l]; }
   v.num_classes = nc;
   v.lookup_retries = h->cfg.lookup_retries;
   v.alloc_retries = h->cfg.alloc_retries;
@@ -501,12 +535,24 @@ int freeze(smmo_heap* h, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaMemsetAsync(v.alloc_bm, 0xFF, M * 8, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(v.block_type, 0xFF, M * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(v.bitmaps, 0, bw * 8 * nbm, s);
+  std::vector<Inst> itab(h->batch.size());
+  for (size_t i = 0; i < h->batch.size(); ++i) {
+    const smmo_instance_desc& d = h->batch[i];
+    Inst& r = itab[i];
+    memset(&r, 0, sizeof(r));
+    r.cell_base = (uint32_t)d.base;
+    r.W = d.W; r.H = d.H; r.id = d.id;
+    r.wdiv = d.W ? ~0ull / d.W + 1 : 0ull;
+    r.count = (uint32_t)d.count;
+    r.kind = d.kind;
+    r.param[0] = d.param[0]; r.param[1] = d.param[1];
+  }
+  if (e == cudaSuccess && !itab.empty())
+    e = cudaMemcpyAsync(h->d_inst, itab.data(), inst_bytes, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_status(e);
-  uint64_t bits = M;
-  for (uint32_t l = 0; l < nl; ++l) {
+  for (uint32_t l = 0; l < nl; ++l) {  // the free bitmap: every block free
     const uint32_t grid = std::min<uint32_t>((lw[l] + 255) / 256, 4096);
-    k_fill_bitmap<<<std::max(grid, 1u), 256, 0, s>>>(v.bitmaps + lo[l], lw[l], bits);
-    bits = lw[l];
+    k_fill_bitmap<<<std::max(grid, 1u), 256, 0, s>>>(v.bitmaps + lo[l], lw[l], lb[l]);
   }
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_status(e);
@@ -573,6 +619,7 @@ void smmo_heap_config_default(smmo_heap_config* c) {
   c->ctas_per_sm = 8;
   c->debug_checks = 0;
   c->defrag_factor = 1;
+  c->bitmap_fanout = 64;
 }
 
 int smmo_heap_create(const smmo_heap_config* cfg, void* dev_buf, size_t buf_bytes, void* stream,
@@ -584,7 +631,7 @@ int smmo_heap_create(const smmo_heap_config* cfg, void* dev_buf, size_t buf_byte
   if (cfg) c = *cfg;
   if (c.threads_per_cta <= 0 || c.threads_per_cta % 64 || c.threads_per_cta > 512 ||
       c.ctas_per_sm <= 0 || c.lookup_retries < 1 || c.alloc_retries < 1 || c.bitmap_spins < 1 ||
-      c.defrag_factor < 1 || c.defrag_factor > 63)
+      c.defrag_factor < 1 || c.defrag_factor > 63 || (c.bitmap_fanout != 32 && c.bitmap_fanout != 64))
     return SMMO_E_INVALID_ARG;
   smmo_heap* h = new smmo_heap();
   h->cfg = c;
@@ -669,15 +716,43 @@ int smmo_class_layout(smmo_heap* h, int c, uint32_t* col_off, int* ncols, uint32
   return SMMO_OK;
 }
 
-int smmo_method_lookup(const char* name, int* method_id) {
+int smmo_method_lookup(smmo_heap* h, const char* name, int* method_id) {
   if (!name || !method_id) return SMMO_E_INVALID_ARG;
   int base = 0;
   for (const Table& t : kTables) {
     for (int i = 0; i < *t.n; ++i)
-      if (strcmp(t.e[i].name, name) == 0) { *method_id = base + i; return SMMO_OK; }
+      if (strcmp(t.e[i].name, name) == 0) {
+        // a batch method reads the instance table, which this heap lacks
+        if (h && h->frozen && h->batch.empty() && strncmp(name, "test.batch_", 11) == 0)
+          return SMMO_E_UNSUPPORTED;
+        *method_id = base + i;
+        return SMMO_OK;
+      }
     base += *t.n;
   }
   return SMMO_E_INVALID_ARG;
+}
+
+int smmo_batch_define(smmo_heap* h, const smmo_instance_desc* inst, int n_inst) {
+  if (!h || !inst || n_inst < 1 || n_inst > (1 << 20)) return SMMO_E_INVALID_ARG;
+  if (h->frozen) return SMMO_E_FROZEN;
+  if (!h->batch.empty()) return SMMO_E_UNSUPPORTED;  // once per heap
+  uint64_t end = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    const smmo_instance_desc& d = inst[i];
+    if (d.count > 0) {
+      if (d.base < end || d.base + d.count > (1ull << 32) || d.base + d.count < d.base) return SMMO_E_INVALID_ARG;
+      end = d.base + d.count;
+    }
+  }
+  h->batch.assign(inst, inst + n_inst);
+  return SMMO_OK;
+}
+
+int smmo_batch_count(smmo_heap* h, int* n_inst) {
+  if (!h || !n_inst) return SMMO_E_INVALID_ARG;
+  *n_inst = (int)h->batch.size();
+  return SMMO_OK;
 }
 
 int smmo_bulk_new(smmo_heap* h, int c, int64_t n, const void* const* field_src,
@@ -695,27 +770,32 @@ int smmo_bulk_new(smmo_heap* h, int c, int64_t n, const void* const* field_src,
   const uint64_t nb64 = ((uint64_t)n + cap - 1) / cap;
   if (nb64 > h->view.num_blocks) return SMMO_E_OOM;
   const uint32_t nb = (uint32_t)nb64;
+  // k_find_free leaves the number of blocks it found in aux[0]; the claim
+  // and copy kernels do nothing (the claim records SMMO_E_OOM) when it is
+  // short, so no host round trip is needed
   unsigned long long* found_d = &h->view.st->aux[0];
   k_find_free<<<1, 1024, 0, s>>>(h->view, nb, h->d_scratch, found_d);
-  unsigned long long found = 0;
-  cudaError_t e = cudaMemcpyAsync(&found, found_d, sizeof(found), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return smmo::cuda_status(e);
-  if (found < nb) return SMMO_E_OOM;
-  uint32_t first = 0, last = 0;
-  e = cudaMemcpyAsync(&first, h->d_scratch, 4, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&last, h->d_scratch + nb - 1, 4, cudaMemcpyDeviceToHost, s);
   const uint32_t g1 = std::min<uint32_t>((nb + 255) / 256, 8192);
   k_bulk_claim<<<std::max(g1, 1u), 256, 0, s>>>(h->view, c, h->d_scratch, nb, (uint64_t)n, cap, ci.layout.capmask);
   ColSrc src;
   memset(&src, 0, sizeof(src));
   for (int k = 0; k < ci.ncols; ++k) src.p[k] = field_src ? field_src[k] : nullptr;
   const uint64_t g2 = std::min<uint64_t>(((uint64_t)n + 255) / 256, 65535);
-  k_bulk_copy<<<(unsigned)std::max<uint64_t>(g2, 1), 256, 0, s>>>(h->view, c, h->d_scratch, (uint64_t)n, src, ci.ncols, out_handles);
-  if (e == cudaSuccess) e = cudaGetLastError();
+  k_bulk_copy<<<(unsigned)std::max<uint64_t>(g2, 1), 256, 0, s>>>(h->view, c, h->d_scratch, (uint64_t)n, src, ci.ncols,
+                                                                  out_handles, nb);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return smmo::cuda_status(e);
+  if (!out_first_block) return SMMO_OK;
+  // synchronous form: the first and last block used, and an OOM now
+  unsigned long long found = 0;
+  uint32_t first = 0, last = 0;
+  e = cudaMemcpyAsync(&found, found_d, sizeof(found), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&first, h->d_scratch, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&last, h->d_scratch + nb - 1, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return smmo::cuda_status(e);
-  if (out_first_block && last - first == nb - 1) *out_first_block = first;
+  if (found < nb) return SMMO_E_OOM;
+  if (last - first == nb - 1) *out_first_block = first;
   return SMMO_OK;
 }
 

@@ -38,6 +38,8 @@ struct smmo_heap {
   uint32_t compact_passes = 0;
   int64_t compact_news = -1, compact_bulks = -1;
   int64_t bulk_calls = 0;                  // bulk_new calls that created objects
+  std::vector<smmo_instance_desc> batch;   // instance table (smmo_batch_define)
+  smmo::Inst* d_inst = nullptr;            // its device copy, inside buf
 };
 
 namespace smmo {

@@ -47,7 +47,7 @@ struct ClassLayout {
   uint32_t ncols;
   unsigned long long capmask;         // low N_T bits set
   uint32_t dlimit;                    // defrag candidate iff fill <= dlimit
-  uint32_t pad;
+  int32_t inst_col;                   // column of the SMMO_INSTANCE field (-1: none)
   uint32_t col_off[SMMO_MAX_COLS];    // byte offset of each SOA column
   uint32_t col_size[SMMO_MAX_COLS];   // element size of each column
 };
@@ -65,6 +65,21 @@ struct DeviceState {
   unsigned long long stat_free_blocks;
   unsigned long long pad2;
   unsigned long long ctr[SMMO_NSHARD][SMMO_NCTR];
+};
+
+// One row of a heap's instance table (smmo_batch_define): a problem
+// instance whose objects share the heap with the other instances'.  The
+// instances that own a range of a global numbering (the cells of the
+// cellular worlds) are sorted by it, so an index finds its instance.
+struct Inst {
+  uint32_t cell_base;  // first index of the instance's range
+  uint32_t W;
+  uint32_t H;
+  uint32_t id;         // instance number in the random counters
+  uint64_t wdiv;       // floor((2^64 - 1) / W) + 1 (division by W), 0 if W = 0
+  uint32_t count;      // length of the range
+  int32_t kind;
+  long long param[2];
 };
 
 // An enumerated block: its index, its class and the snapshot of its
@@ -85,12 +100,16 @@ struct HeapView {
   const ClassLayout* cls;             // per-class layouts (device)
   REntry* R;                          // enumeration scratch
   uint32_t* rcnt;                     // its entry count (the heap's, or a saved snapshot's)
+  const Inst* inst;                   // instance table (null: no batch)
+  uint32_t n_inst;
   uint32_t block_bytes;
   uint32_t num_blocks;
   uint32_t bm_words;                  // words of one hierarchical bitmap
   uint32_t nlevels;
+  uint32_t bm_shift;                  // log2 of the bitmap fan-out (5 or 6)
   uint32_t level_off[SMMO_MAX_LEVELS];
   uint32_t level_words[SMMO_MAX_LEVELS];
+  uint32_t level_bits[SMMO_MAX_LEVELS];
   int32_t num_classes;
   int32_t lookup_retries;
   int32_t alloc_retries;
@@ -153,6 +172,15 @@ __device__ __forceinline__ int nth_set_bit64(unsigned long long b, uint32_t n) {
 }
 
 // ---------------------------------------------------- hierarchical bitmaps
+// Every level is a dense bit array in 64-bit words; a container is F =
+// 2^bm_shift consecutive bits (F = 64: one word; F = 32: half a word), and
+// bit i of level l + 1 says whether container i of level l has a set bit
+// (Sec. 5.3.1).  So level 0 holds one bit per block whatever F is.
+// Container mask of bit `pos` inside its storage word.
+__device__ __forceinline__ unsigned long long bm_cmask(const HeapView& h, uint32_t pos) {
+  return h.bm_shift == 6 ? kAll : (0xFFFFFFFFull << (pos & 32));
+}
+
 // Blocking set/clear of bit `pos` at level l >= 1 (higher levels are always
 // changed with the blocking form, Sec. 5.3.1 "set and clear with atomic
 // operations"), then propagation upwards while a container changes between
@@ -171,8 +199,9 @@ static __device__ __forceinline__ void bm_propagate(const HeapView& h, int k, in
     }
     if (!done) { set_error(h, SMMO_E_CONTENTION, ((unsigned long long)k << 32) | pos); return; }
     // continue only on set-first / clear-last of this container
-    if (set ? (prev != 0) : (prev != m)) return;
-    pos >>= 6;
+    const unsigned long long cm = bm_cmask(h, pos);
+    if (set ? ((prev & cm) != 0) : ((prev & cm) != m)) return;
+    pos >>= h.bm_shift;
   }
 }
 
@@ -183,7 +212,7 @@ __device__ __forceinline__ bool bm_try_set(const HeapView& h, int k, uint32_t po
   const unsigned long long m = 1ull << (pos & 63);
   const unsigned long long prev = atomicOr(w, m);
   if (prev & m) return false;
-  if (prev == 0 && h.nlevels > 1) bm_propagate(h, k, 1, pos >> 6, true);
+  if ((prev & bm_cmask(h, pos)) == 0 && h.nlevels > 1) bm_propagate(h, k, 1, pos >> h.bm_shift, true);
   return true;
 }
 
@@ -192,7 +221,7 @@ __device__ __forceinline__ bool bm_try_clear(const HeapView& h, int k, uint32_t 
   const unsigned long long m = 1ull << (pos & 63);
   const unsigned long long prev = atomicAnd(w, ~m);
   if (!(prev & m)) return false;
-  if (prev == m && h.nlevels > 1) bm_propagate(h, k, 1, pos >> 6, false);
+  if ((prev & bm_cmask(h, pos)) == m && h.nlevels > 1) bm_propagate(h, k, 1, pos >> h.bm_shift, false);
   return true;
 }
 
@@ -217,6 +246,13 @@ __device__ __forceinline__ bool bm_get(const HeapView& h, int k, uint32_t pos) {
   return (ld_cg(bm_level(h, k, 0) + (pos >> 6)) >> (pos & 63)) & 1;
 }
 
+// The bits of container `idx` of level l (right-aligned).
+__device__ __forceinline__ unsigned long long bm_container(const HeapView& h, int k, int l, uint32_t idx) {
+  const uint32_t first = idx << h.bm_shift;
+  const unsigned long long w = ld_cg(bm_level(h, k, l) + (first >> 6));
+  return h.bm_shift == 6 ? w : (w >> (first & 32)) & 0xFFFFFFFFull;
+}
+
 // Top-down search for any set bit (Alg. 5.4 try_find_set).  Against
 // contention (the purpose of the bitmap rotation of Sec. 5.3.2) each level
 // picks a seed-dependent set bit uniformly among the set bits of the
@@ -224,12 +260,12 @@ __device__ __forceinline__ bool bm_get(const HeapView& h, int k, uint32_t pos) {
 // after a gap, so when the set bits are clustered most threads would land on
 // the same container.  Returns -1 (FAIL) on an empty or inconsistent path.
 __device__ __forceinline__ int bm_try_find_set(const HeapView& h, int k, uint32_t seed) {
-  uint32_t idx = 0;
+  uint32_t idx = 0;  // container index at the current level (one at the top)
   for (int l = (int)h.nlevels - 1; l >= 0; --l) {
-    const unsigned long long w = ld_cg(bm_level(h, k, l) + idx);
+    const unsigned long long w = bm_container(h, k, l, idx);
     if (w == 0) return -1;
     const uint32_t pick = mix32(seed + 0x9E3779B9u * (uint32_t)(l + 1)) % (uint32_t)__popcll(w);
-    idx = idx * 64 + (uint32_t)nth_set_bit64(w, pick);
+    idx = (idx << h.bm_shift) + (uint32_t)nth_set_bit64(w, pick);
   }
   return idx < h.num_blocks ? (int)idx : -1;
 }
@@ -261,6 +297,28 @@ __device__ __forceinline__ T* field_ptr(const HeapView& h, uint32_t col_off, uin
 
 __device__ __forceinline__ uint32_t type_of(const HeapView& h, uint32_t handle) {
   return __ldcg(h.block_type + (handle >> 6));
+}
+
+// ----------------------------------------------------------- instances
+// The instance-table row of object `self` of class c, named by the class's
+// SMMO_INSTANCE field (null if the class has none or the index is out of
+// the table).
+__device__ __forceinline__ const Inst* instance_of(const HeapView& h, uint32_t c, uint32_t self) {
+  const int col = __ldg(&h.cls[c].inst_col);
+  if (col < 0) return nullptr;
+  const uint32_t i = *field_ptr<uint32_t>(h, __ldg(&h.cls[c].col_off[col]), self);
+  return i < h.n_inst ? h.inst + i : nullptr;
+}
+
+// The row whose range [cell_base, cell_base + count) holds global index g
+// (rows sorted by cell_base; g must lie in some range).
+__device__ __forceinline__ const Inst* instance_at(const Inst* tab, uint32_t n, uint32_t g) {
+  uint32_t lo = 0, hi = n;  // invariant: tab[lo].cell_base <= g
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(&tab[mid].cell_base) <= g) lo = mid; else hi = mid;
+  }
+  return tab + lo;
 }
 
 // ------------------------------------------------------------- deallocation

@@ -84,6 +84,23 @@ struct ValueI32 {
   }
 };
 
+// Batch method: an object of a class with a SMMO_INSTANCE field updates its
+// int32 column col from the row of its instance, v = v * param[0] +
+// param[1] + kind (64-bit arithmetic, low 32 bits kept), and adds the
+// instance's id to column col_id (one launch over every instance).
+struct BatchAffine {
+  struct Args { uint32_t col; uint32_t col_id; };
+  __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
+    const Inst* in = instance_of(h, c, self);
+    if (!in) { set_error(h, SMMO_E_BOUNDS, self); return; }
+    int32_t* v = field_ptr<int32_t>(h, __ldg(&h.cls[c].col_off[a.col]), self);
+    const long long r = (long long)*v * __ldg(&in->param[0]) + __ldg(&in->param[1]) + __ldg(&in->kind);
+    *v = (int32_t)(uint32_t)(unsigned long long)r;
+    int32_t* idc = field_ptr<int32_t>(h, __ldg(&h.cls[c].col_off[a.col_id]), self);
+    *idc += (int32_t)__ldg(&in->id);
+  }
+};
+
 }  // namespace
 
 const smmo::MethodEntry g_methods_test[] = {
@@ -94,6 +111,7 @@ const smmo::MethodEntry g_methods_test[] = {
     SMMO_METHOD("test.replace", Replace),
     SMMO_METHOD("test.set_ref_from", SetRefFrom),
     SMMO_METHOD_REDUCE("test.value_i32", ValueI32),
+    SMMO_METHOD("test.batch_affine", BatchAffine),
 };
 const int g_methods_test_n = sizeof(g_methods_test) / sizeof(g_methods_test[0]);
 

@@ -38,9 +38,6 @@ using namespace smmo;
 namespace {
 
 struct WorldArgs {
-  const Inst* winst;
-  const Inst* linst;
-  uint32_t nwinst, nlinst;
   CellRef cells;
   uint32_t occ_off, req_off;
   uint32_t fish, shark, alive, cand;
@@ -94,7 +91,7 @@ struct FishPrepare {
     const uint32_t g = *fld<int32_t>(h, self, a.f_cell);
     int16_t* agep = fld<int16_t>(h, self, a.f_age);
     *agep = (int16_t)(*agep + 1);
-    const Inst* in = find_inst(a.winst, a.nwinst, g);
+    const Inst* in = find_inst(h, g);
     const uint32_t lc = g - in->cell_base, W = in->W, H = in->H;
     uint32_t x, y;
     cell_xy(in, lc, &x, &y);
@@ -153,7 +150,7 @@ struct SharkPrepare {
     *enp = en;
     uint32_t tgt = g;
     if (en != 0) {
-      const Inst* in = find_inst(a.winst, a.nwinst, g);
+      const Inst* in = find_inst(h, g);
       const uint32_t lc = g - in->cell_base, W = in->W, H = in->H;
       uint32_t x, y;
       cell_xy(in, lc, &x, &y);
@@ -245,7 +242,7 @@ struct CandPrepare {
   using Args = WorldArgs;
   __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
     const uint32_t g = *fld<int32_t>(h, self, a.c_cell);
-    const Inst* in = find_inst(a.linst, a.nlinst, g);
+    const Inst* in = find_inst(h, g);
     const uint32_t lc = g - in->cell_base;
     uint32_t x, y;
     cell_xy(in, lc, &x, &y);
@@ -264,7 +261,7 @@ struct AlivePrepare {
       *fld<uint8_t>(h, self, a.a_action) = blocked >= a.block ? ACT_EXPIRE : ACT_AGE;
       return;
     }
-    const Inst* in = find_inst(a.linst, a.nlinst, g);
+    const Inst* in = find_inst(h, g);
     const uint32_t lc = g - in->cell_base;
     uint32_t x, y;
     cell_xy(in, lc, &x, &y);
@@ -301,7 +298,7 @@ struct AliveUpdate {
     if (*fld<uint8_t>(h, self, a.a_isnew)) {
       // create Candidates on empty surrounding cells; the creator of an empty
       // cell e is the first new Alive of e's neighbourhood in scan order
-      const Inst* in = find_inst(a.linst, a.nlinst, g);
+      const Inst* in = find_inst(h, g);
       const uint32_t lc = g - in->cell_base, W = in->W, H = in->H;
       uint32_t x, y;
       cell_xy(in, lc, &x, &y);
@@ -458,9 +455,7 @@ struct smmo_world {
   uint64_t total_cells = 0;
   int cls_cell = -1, cls_wagent = -1, cls_fish = -1, cls_shark = -1;
   int cls_lagent = -1, cls_alive = -1, cls_cand = -1;
-  Inst* d_winst = nullptr;
-  Inst* d_linst = nullptr;
-  uint32_t nw = 0, nl = 0;
+  uint32_t nw = 0, nl = 0;  // Wa-Tor and Life instances
   uint32_t t = 0;  // steps done
   uint32_t* d_t = nullptr;  // device step counter
   cudaGraphExec_t graph = nullptr;
@@ -532,37 +527,40 @@ int world_steps(smmo_world* w, int nsteps, cudaStream_t s, PhaseTimer* pt) {
 
 extern "C" {
 
-int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32_t* W,
-                      const uint32_t* H, uint64_t seed, const smmo_wator_params* params,
-                      const int8_t* init_kind, const int16_t* init_age, const int16_t* init_energy,
-                      const uint8_t* init_state, void* stream, smmo_world** out) {
-  if (!heap || n_inst < 1 || !kind || !W || !H || !init_kind || !out) return SMMO_E_INVALID_ARG;
+int smmo_world_create_batch(smmo_heap* heap, const smmo_instance_desc* inst, int n_inst, uint64_t seed,
+                            const smmo_wator_params* params, const int8_t* init_kind, const int16_t* init_age,
+                            const int16_t* init_energy, const uint8_t* init_state, void* stream,
+                            smmo_world** out) {
+  if (!heap || n_inst < 1 || !inst || !init_kind || !out) return SMMO_E_INVALID_ARG;
   if (!heap->classes.empty() || heap->frozen) return SMMO_E_FROZEN;
   cudaStream_t s = (cudaStream_t)stream;
+  uint64_t total = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    const smmo_instance_desc& d = inst[i];
+    if ((d.kind != SMMO_WORLD_LIFE && d.kind != SMMO_WORLD_WATOR) || d.W < 3 || d.H < 3) return SMMO_E_INVALID_ARG;
+    if (d.base != total || d.count != (uint64_t)d.W * d.H) return SMMO_E_INVALID_ARG;
+    total += d.count;
+    if (total >= (1ull << 31)) return SMMO_E_INVALID_ARG;
+  }
+  int st = smmo_batch_define(heap, inst, n_inst);  // the heap owns the instance table
+  if (st) return st;
   smmo_world* w = new smmo_world();
   w->heap = heap;
   w->n_inst = n_inst;
   w->p.fish_breed = 4; w->p.shark_breed = 12; w->p.starve = 3; w->p.breed_strict = 0;
   if (params) w->p = *params;
-  std::vector<Inst> wi, li;
   for (int i = 0; i < n_inst; ++i) {
-    if ((kind[i] != SMMO_WORLD_LIFE && kind[i] != SMMO_WORLD_WATOR) || W[i] < 3 || H[i] < 3) {
-      delete w;
-      return SMMO_E_INVALID_ARG;
-    }
-    w->kind.push_back(kind[i]);
-    w->W.push_back(W[i]);
-    w->H.push_back(H[i]);
-    w->base.push_back((uint32_t)w->total_cells);
-    Inst in{(uint32_t)w->total_cells, W[i], H[i], (uint32_t)i, div_magic(W[i])};
-    (kind[i] == SMMO_WORLD_WATOR ? wi : li).push_back(in);
-    w->total_cells += (uint64_t)W[i] * H[i];
+    w->kind.push_back(inst[i].kind);
+    w->W.push_back(inst[i].W);
+    w->H.push_back(inst[i].H);
+    w->base.push_back((uint32_t)inst[i].base);
+    (inst[i].kind == SMMO_WORLD_WATOR ? w->nw : w->nl) += 1;
   }
-  if (w->total_cells >= (1ull << 31)) { delete w; return SMMO_E_INVALID_ARG; }
+  w->total_cells = total;
   // classes
   smmo_field_desc cell_f[2] = {{"occ", SMMO_HANDLE, 1, -1}, {"req", SMMO_U64, 1, -1}};
-  int st = smmo_class_register(heap, "Cell", cell_f, 2, -1, 0, &w->cls_cell);
-  if (!st && !wi.empty()) {
+  st = smmo_class_register(heap, "Cell", cell_f, 2, -1, 0, &w->cls_cell);
+  if (!st && w->nw) {
     smmo_field_desc ag[2] = {{"cell", SMMO_I32, 1, -1}, {"target", SMMO_I32, 1, -1}};
     smmo_field_desc fi[1] = {{"age", SMMO_I16, 1, -1}};
     smmo_field_desc sh[2] = {{"age", SMMO_I16, 1, -1}, {"energy", SMMO_I16, 1, -1}};
@@ -570,7 +568,7 @@ int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32
     if (!st) st = smmo_class_register(heap, "Fish", fi, 1, w->cls_wagent, 0, &w->cls_fish);
     if (!st) st = smmo_class_register(heap, "Shark", sh, 2, w->cls_wagent, 0, &w->cls_shark);
   }
-  if (!st && !li.empty()) {
+  if (!st && w->nl) {
     smmo_field_desc ag[2] = {{"cell", SMMO_I32, 1, -1}, {"action", SMMO_U8, 1, -1}};
     smmo_field_desc al[2] = {{"is_new", SMMO_U8, 1, -1}, {"blocked", SMMO_U16, 1, -1}};
     st = smmo_class_register(heap, "LAgent", ag, 2, -1, 1, &w->cls_lagent);
@@ -582,17 +580,9 @@ int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32
   if (!st && heap->classes[w->cls_cell].layout.cap != 64 && heap->classes[w->cls_cell].layout.cap != 32)
     st = SMMO_E_UNSUPPORTED;  // dense cell addressing needs N = 32 or 64
   if (st) { delete w; return st; }
-  // instance tables (device memory inside the heap's scratch tail is not
-  // reserved for this, so use a dedicated allocation owned by the world)
-  w->nw = (uint32_t)wi.size();
-  w->nl = (uint32_t)li.size();
-  cudaError_t e = cudaSuccess;
-  e = cudaMalloc(&w->d_t, sizeof(uint32_t));
+  // the step counter (the instance table is the heap's)
+  cudaError_t e = cudaMalloc(&w->d_t, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemsetAsync(w->d_t, 0, sizeof(uint32_t), s);
-  if (e == cudaSuccess && w->nw) e = cudaMalloc(&w->d_winst, sizeof(Inst) * w->nw);
-  if (e == cudaSuccess && w->nl) e = cudaMalloc(&w->d_linst, sizeof(Inst) * w->nl);
-  if (e == cudaSuccess && w->nw) e = cudaMemcpyAsync(w->d_winst, wi.data(), sizeof(Inst) * w->nw, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && w->nl) e = cudaMemcpyAsync(w->d_linst, li.data(), sizeof(Inst) * w->nl, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) { smmo_world_destroy(w); return cuda_status(e); }
   // cells: occ = null, req = all ones
   const uint64_t N = w->total_cells;
@@ -613,7 +603,6 @@ int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32
   // argument block
   WorldArgs& a = w->args;
   memset(&a, 0, sizeof(a));
-  a.winst = w->d_winst; a.linst = w->d_linst; a.nwinst = w->nw; a.nlinst = w->nl;
   a.cells.data = heap->view.data;
   a.cells.block_bytes = heap->view.block_bytes;
   a.cells.b0 = (uint32_t)first;
@@ -706,6 +695,27 @@ int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32
   if (st) { smmo_world_destroy(w); return st; }
   *out = w;
   return SMMO_OK;
+}
+
+int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind, const uint32_t* W,
+                      const uint32_t* H, uint64_t seed, const smmo_wator_params* params,
+                      const int8_t* init_kind, const int16_t* init_age, const int16_t* init_energy,
+                      const uint8_t* init_state, void* stream, smmo_world** out) {
+  if (!heap || n_inst < 1 || !kind || !W || !H) return SMMO_E_INVALID_ARG;
+  std::vector<smmo_instance_desc> d(n_inst);
+  uint64_t base = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    memset(&d[i], 0, sizeof(d[i]));
+    d[i].kind = kind[i];
+    d[i].id = (uint32_t)i;
+    d[i].W = W[i];
+    d[i].H = H[i];
+    d[i].base = base;
+    d[i].count = (uint64_t)W[i] * H[i];
+    base += d[i].count;
+  }
+  return smmo_world_create_batch(heap, d.data(), n_inst, seed, params, init_kind, init_age, init_energy,
+                                 init_state, stream, out);
 }
 
 int smmo_world_step(smmo_world* w, int nsteps, void* stream) {
@@ -916,8 +926,6 @@ int smmo_world_destroy(smmo_world* w) {
   if (!w) return SMMO_E_INVALID_ARG;
   if (w->graph) cudaGraphExecDestroy(w->graph);
   if (w->d_t) cudaFree(w->d_t);
-  if (w->d_winst) cudaFree(w->d_winst);
-  if (w->d_linst) cudaFree(w->d_linst);
   delete w;
   return SMMO_OK;
 }

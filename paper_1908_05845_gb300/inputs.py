@@ -233,6 +233,25 @@ def batched_instances(seed: int, n: int = 256, side_min: int = 64, ratio: float 
     return kind, side
 
 
+def batched_initial(seed: int, n: int = 256, **kw):
+    """The batched heap's instances (kinds and sides from batched_instances)
+    and their initial states, instance i drawn with instance id i, as
+    concatenated per-cell arrays (kind i8, age i16, energy i16, state u8)."""
+    kinds, sides = batched_instances(seed, n, **kw)
+    ks, ags, ens, sts = [], [], [], []
+    for i, (kd, sd) in enumerate(zip(kinds, sides)):
+        sd = int(sd)
+        if kd == LIFE:
+            k, s = gol_initial(sd, sd, seed, inst=i)
+            a = np.zeros(sd * sd, np.int16)
+            e = np.zeros(sd * sd, np.int16)
+        else:
+            k, a, e = wator_initial(sd, sd, seed, inst=i)
+            s = np.zeros(sd * sd, np.uint8)
+        ks.append(k.astype(np.int8)); ags.append(a); ens.append(e); sts.append(s)
+    return kinds, sides, (np.concatenate(ks), np.concatenate(ags), np.concatenate(ens), np.concatenate(sts))
+
+
 # -------------------------------------------------------------- compaction
 def compact_synthetic(n: int, seed: int, kill=(3, 5)):
     """(kill mask of the first class, its references into the second class,

@@ -20,7 +20,7 @@ _lock = threading.Lock()
 _lib = None
 
 NULL = 0xFFFFFFFF
-I8, U8, I16, U16, I32, U32, F32, I64, U64, F64, HANDLE = range(1, 12)
+I8, U8, I16, U16, I32, U32, F32, I64, U64, F64, HANDLE, INSTANCE = range(1, 13)
 _TORCH = {I8: torch.int8, U8: torch.uint8, I16: torch.int16, U16: torch.int16, I32: torch.int32,
           U32: torch.int32, F32: torch.float32, I64: torch.int64, U64: torch.int64,
           F64: torch.float64, HANDLE: torch.int32}
@@ -73,7 +73,15 @@ class HeapConfig(ctypes.Structure):
     _fields_ = [("block_data_bytes", ctypes.c_uint32), ("lookup_retries", ctypes.c_int32),
                 ("alloc_retries", ctypes.c_int32), ("bitmap_spins", ctypes.c_int32),
                 ("threads_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("debug_checks", ctypes.c_int32), ("defrag_factor", ctypes.c_int32)]
+                ("debug_checks", ctypes.c_int32), ("defrag_factor", ctypes.c_int32),
+                ("bitmap_fanout", ctypes.c_int32)]
+
+
+class InstanceDesc(ctypes.Structure):
+    """One row of a heap's instance table (smmo_instance_desc)."""
+    _fields_ = [("kind", ctypes.c_int32), ("id", ctypes.c_uint32), ("W", ctypes.c_uint32),
+                ("H", ctypes.c_uint32), ("base", ctypes.c_uint64), ("count", ctypes.c_uint64),
+                ("param", ctypes.c_int64 * 2)]
 
 
 class HeapStats(ctypes.Structure):
@@ -106,10 +114,16 @@ def default_config(**kw) -> HeapConfig:
 _method_ids = {}
 
 
-def method_id(name: str) -> int:
+def method_id(name: str, heap=None) -> int:
+    """Id of a compiled-in method; with a heap, the library also checks
+    that the heap can run it (a batch method needs an instance table)."""
+    if heap is not None:
+        mid = ctypes.c_int()
+        check(lib().smmo_method_lookup(heap.handle, name.encode(), ctypes.byref(mid)), "method_lookup " + name)
+        return mid.value
     if name not in _method_ids:
         mid = ctypes.c_int()
-        check(lib().smmo_method_lookup(name.encode(), ctypes.byref(mid)), "method_lookup " + name)
+        check(lib().smmo_method_lookup(None, name.encode(), ctypes.byref(mid)), "method_lookup " + name)
         _method_ids[name] = mid.value
     return _method_ids[name]
 
@@ -199,8 +213,12 @@ class Heap:
         return dict(col_off=list(off[:n.value]), block_bytes=bb.value, data_base=base.value)
 
     # ---------------------------------------------------------- objects
-    def bulk_new(self, cls: int, n: int, columns=None, want_handles: bool = False):
-        """columns: list (one per SOA column) of device tensors or None."""
+    def bulk_new(self, cls: int, n: int, columns=None, want_handles: bool = False, asynchronous: bool = False):
+        """columns: list (one per SOA column) of device tensors or None.
+        Returns (handles or None, first block or -1).  asynchronous=True
+        only enqueues the kernels (the first block is then not read back,
+        -1; a shortage of free blocks shows up in sync()); the column
+        tensors are kept alive for the heap's stream with record_stream."""
         cols = self.columns(cls)
         src = (ctypes.c_void_p * max(1, len(cols)))()
         keep = []
@@ -213,14 +231,38 @@ class Heap:
                     keep.append(t)
                     src[k] = t.data_ptr()
         out = torch.empty(max(1, n), dtype=torch.int32, device=self.buf.device) if want_handles else None
-        first = ctypes.c_int64()
+        first = ctypes.c_int64(-1)
         check(lib().smmo_bulk_new(self._h, cls, ctypes.c_int64(n), src,
-                                  _ptr(out) if out is not None else None, ctypes.byref(first),
+                                  _ptr(out) if out is not None else None,
+                                  None if asynchronous else ctypes.byref(first),
                                   _stream(self.stream)), "bulk_new")
+        if asynchronous:
+            st = self.stream if self.stream is not None else torch.cuda.current_stream()
+            for t in keep:
+                t.record_stream(st)
         return (out[:n] if out is not None else None), first.value
 
+    def batch_define(self, rows) -> None:
+        """Instance table (smmo_batch_define): rows of dicts with keys kind,
+        id, W, H, base, count, param (all optional, default 0)."""
+        arr = (InstanceDesc * len(rows))()
+        for i, r in enumerate(rows):
+            p = list(r.get("param", (0, 0))) + [0, 0]
+            arr[i] = InstanceDesc(int(r.get("kind", 0)), int(r.get("id", i)), int(r.get("W", 0)),
+                                  int(r.get("H", 0)), int(r.get("base", 0)), int(r.get("count", 0)),
+                                  (ctypes.c_int64 * 2)(int(p[0]), int(p[1])))
+        check(lib().smmo_batch_define(self._h, arr, len(rows)), "batch_define")
+
+    def _mid(self, method) -> int:
+        if not isinstance(method, str):
+            return int(method)
+        mids = self.__dict__.setdefault("_mids", {})
+        if method not in mids:
+            mids[method] = method_id(method, self)
+        return mids[method]
+
     def parallel_do(self, cls: int, method, args=None):
-        mid = method_id(method) if isinstance(method, str) else int(method)
+        mid = self._mid(method)
         if args is None:
             ap, n = None, 0
         else:
@@ -341,6 +383,10 @@ class Heap:
 
 
 # ------------------------------------------------------ method argument blocks
+class BatchAffineArgs(ctypes.Structure):
+    _fields_ = [("col", ctypes.c_uint32), ("col_id", ctypes.c_uint32)]
+
+
 class AddI32Args(ctypes.Structure):
     _fields_ = [("col", ctypes.c_uint32), ("value", ctypes.c_int32)]
 

@@ -32,7 +32,9 @@ class World:
     def __init__(self, kinds, widths, heights, seed: int, init_kind, init_age=None,
                  init_energy=None, init_state=None, params: WatorParams | None = None,
                  heap_bytes: int | None = None, config: smmo.HeapConfig | None = None,
-                 stream=None):
+                 stream=None, inst_ids=None):
+        """inst_ids: the instance numbers of the draws (default 0..n-1), so
+        that one instance of a larger batch can be run alone."""
         n = len(kinds)
         self.kinds = [int(k) for k in kinds]
         self.W = [int(w) for w in widths]
@@ -55,16 +57,20 @@ class World:
         s = dt(init_state, torch.uint8)
         self.heap = smmo.Heap(heap_bytes or heap_bytes_for(self.total), config, stream=stream)
         self._w = ctypes.c_void_p()
-        ka = (ctypes.c_int * n)(*self.kinds)
-        wa = (ctypes.c_uint32 * n)(*self.W)
-        ha = (ctypes.c_uint32 * n)(*self.H)
+        ids = list(range(n)) if inst_ids is None else [int(i) for i in inst_ids]
+        rows = (smmo.InstanceDesc * n)()
+        base = 0
+        for i in range(n):
+            rows[i] = smmo.InstanceDesc(self.kinds[i], ids[i], self.W[i], self.H[i], base, self.sizes[i],
+                                        (ctypes.c_int64 * 2)(0, 0))
+            base += self.sizes[i]
         p = ctypes.byref(params) if params is not None else None
 
         def ptr(t):
             return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
-        smmo.check(smmo.lib().smmo_world_create(
-            self.heap.handle, n, ka, wa, ha, ctypes.c_uint64(seed), p, ptr(k), ptr(a), ptr(e),
+        smmo.check(smmo.lib().smmo_world_create_batch(
+            self.heap.handle, rows, n, ctypes.c_uint64(seed), p, ptr(k), ptr(a), ptr(e),
             ptr(s), smmo._stream(stream), ctypes.byref(self._w)), "world_create")
         ids = (ctypes.c_int * 7)()
         smmo.check(smmo.lib().smmo_world_info(self._w, None, ids, None), "world_info")

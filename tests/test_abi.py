@@ -27,7 +27,8 @@ def libsmmo():
 def test_header_declares_calls():
     names = declared()
     for n in ("smmo_heap_create", "smmo_class_register", "smmo_bulk_new", "smmo_parallel_do",
-              "smmo_enumerate_live", "smmo_compact"):
+              "smmo_enumerate_live", "smmo_compact", "smmo_method_lookup", "smmo_batch_define",
+              "smmo_batch_count", "smmo_world_create_batch"):
         assert n in names
 
 
@@ -44,8 +45,9 @@ def test_status_strings(libsmmo):
 
 def test_method_table(libsmmo):
     mid = ctypes.c_int()
-    assert libsmmo.smmo_method_lookup(b"test.add_i32", ctypes.byref(mid)) == 0
-    assert libsmmo.smmo_method_lookup(b"no.such.method", ctypes.byref(mid)) == -1
+    assert libsmmo.smmo_method_lookup(None, b"test.add_i32", ctypes.byref(mid)) == 0
+    assert libsmmo.smmo_method_lookup(None, b"no.such.method", ctypes.byref(mid)) == -1
+    assert libsmmo.smmo_method_lookup(None, b"test.batch_affine", ctypes.byref(mid)) == 0
 
 
 def test_create_rejects_bad_args(libsmmo):
@@ -63,7 +65,7 @@ def test_every_workload_method_is_registered(libsmmo):
     for name in (b"wator.fish_update", b"gol.candidate_prepare", b"bh.body_insert",
                  b"bfs.vertex_visit", b"structure.spring_compute_force", b"structure.node_visit",
                  b"structure.spring_delete", b"test.value_i32"):
-        assert libsmmo.smmo_method_lookup(name, ctypes.byref(mid)) == 0, name
+        assert libsmmo.smmo_method_lookup(None, name, ctypes.byref(mid)) == 0, name
 
 
 def test_entry_points_reject_null_objects(libsmmo):
@@ -126,3 +128,24 @@ def test_the_oracle_shares_no_code_with_the_package():
         elif f.endswith(".py"):
             assert not re.search(r"^\s*(import|from)\s+paper_1908_05845_gb300|libsmmo", open(p).read(),
                                  flags=re.M), f
+
+
+def test_header_method_lookup_takes_a_heap():
+    """The method table lookup names the heap it will run on (the scope
+    table's signature), and bulk_new's contract is asynchronous."""
+    src = open(os.path.join(ROOT, "include", "smmo.h")).read()
+    assert re.search(r"int smmo_method_lookup\(smmo_heap\* heap, const char\* name, int\* method_id\);", src)
+    i = src.index("int smmo_bulk_new(")
+    assert "Asynchronous on `stream`" in src[src.rindex("/*", 0, i):i]
+
+
+def test_batch_define_checks_its_arguments(libsmmo):
+    """Host-side checks of smmo_batch_define (before any CUDA call)."""
+    class Desc(ctypes.Structure):
+        _fields_ = [("kind", ctypes.c_int32), ("id", ctypes.c_uint32), ("W", ctypes.c_uint32),
+                    ("H", ctypes.c_uint32), ("base", ctypes.c_uint64), ("count", ctypes.c_uint64),
+                    ("param", ctypes.c_int64 * 2)]
+    rows = (Desc * 2)()
+    assert libsmmo.smmo_batch_define(None, rows, 2) == -1
+    n = ctypes.c_int()
+    assert libsmmo.smmo_batch_count(None, ctypes.byref(n)) == -1

@@ -78,8 +78,9 @@ def test_device_new_coalesced_and_counts():
     assert h.check() == 0
 
 
-def test_replace_alloc_and_free_in_one_kernel():
-    h, A, B, C = make()
+@pytest.mark.parametrize("fanout", [64, 32])
+def test_replace_alloc_and_free_in_one_kernel(fanout):
+    h, A, B, C = make(bitmap_fanout=fanout)
     n = 30_000
     h.bulk_new(A, n, [torch.arange(n, dtype=torch.int32, device="cuda"), None])
     for _ in range(3):
@@ -97,8 +98,9 @@ def test_replace_alloc_and_free_in_one_kernel():
     assert st["free_blocks"] + st["blocks"][A] == st["num_blocks"]
 
 
-def test_churn_against_host_model():
-    h, A, B, C = make()
+@pytest.mark.parametrize("fanout", [64, 32])
+def test_churn_against_host_model(fanout):
+    h, A, B, C = make(bitmap_fanout=fanout)
     rng = np.random.default_rng(0)
     n = 8192
     h.bulk_new(A, n, [torch.arange(n, dtype=torch.int32, device="cuda"), None])
