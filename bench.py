@@ -267,7 +267,8 @@ def run_gpu(args, ws, rank, local):
     F = int((k0 == 1).sum())
     S = int((k0 == 2).sum())
     enum0, alloc0, free0 = sim.heap.counters()
-    blocks0 = sim.heap.alloc_counters()["enumerated_blocks"]
+    ac0 = sim.heap.alloc_counters()
+    blocks0 = ac0["enumerated_blocks"]
     clocks = ClockSampler(local)
     if ws > 1:
         torch.distributed.barrier()
@@ -290,7 +291,8 @@ def run_gpu(args, ws, rank, local):
     if ws > 1:
         torch.distributed.barrier()
     enum1, alloc1, free1 = sim.heap.counters()
-    blocks1 = sim.heap.alloc_counters()["enumerated_blocks"]
+    ac1 = sim.heap.alloc_counters()
+    blocks1 = ac1["enumerated_blocks"]
     sim.sync()
     objects = enum1 - enum0
     assert objects == int(objs_phase.sum()), (objects, objs_phase.sum())
@@ -365,6 +367,9 @@ def run_gpu(args, ws, rank, local):
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
+            # allocator events per step (warp-cache refills, blocks taken
+            # from the free bitmap, reservations that found a full block...)
+            "alloc_events_per_step": {k: (ac1[k] - ac0[k]) / args.steps for k in ac1},
             "phase_ms_per_step": {PHASES[p]: {"enumerate": phase_ms[2 * p] / args.steps,
                                               "method": phase_ms[2 * p + 1] / args.steps}
                                   for p in range(4, 8)},

@@ -90,7 +90,7 @@ typedef struct {
 typedef struct {
   /* Bytes of a block's data segment.  0 = 64 * size of the smallest
    * registered class (Sec. 5.2.2, block capacity
-   * N_T = floor(64 size(T_s) / size(T))). Rounded up to 128. */
+   * N_T = floor(64 size(T_s) / size(T))). Rounded up to 64. */
   uint32_t block_data_bytes;
   /* Active-block lookups tried before a new block is initialised
    * (Sec. 5.3.2, "lookup retry").  Default 5. */
@@ -399,7 +399,8 @@ typedef struct {
  * SMMO_E_FROZEN), gives the heap its instance table (smmo_batch_define:
  * instance i has kind[i], W[i] x H[i] cells starting at the sum of the
  * sizes before it, and draws with instance number i) and creates the
- * instances.  kind/W/H: host arrays of n_inst entries (W, H >= 3).
+ * instances.  kind/W/H: host arrays of n_inst entries (W, H >= 3; at most
+ * 2^30 cells in all).
  * Per-cell initial state: device arrays over
  * the concatenation of all instances' cells in instance order, row-major
  * (cell = y * W + x): init_kind (Life: 0 empty, 1 Alive, 2 Candidate;

@@ -1,7 +1,7 @@
 """Autotuner for the heap's launch and layout parameters.
 
-Searches block capacity (through the block data segment size: 384 bytes
-gives the cellular classes N_T = 32, 768 bytes N_T = 64), threads per CTA and
+Searches block capacity (through the block data segment size: 320 bytes
+gives the cells N_T = 32, 640 bytes N_T = 64), threads per CTA and
 CTAs per SM of the persistent do-all grid over their full grid, then the
 fan-out of the hierarchical bitmaps (32 or 64 bits per container) at the
 best of those, by timing a few steps of a world built from a sample of the
@@ -25,7 +25,7 @@ from . import smmo
 from .workloads import World, heap_bytes_for
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune_cache.json")
-SPACE = {"block_data_bytes": (384, 768), "threads_per_cta": (128, 256, 512), "ctas_per_sm": (4, 8, 16)}
+SPACE = {"block_data_bytes": (320, 640), "threads_per_cta": (128, 256, 512), "ctas_per_sm": (4, 8, 16)}
 # searched one at a time at the best point of SPACE
 FANOUT = {"bitmap_fanout": (64, 32)}
 _PKG = os.path.dirname(os.path.abspath(__file__))

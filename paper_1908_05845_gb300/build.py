@@ -34,6 +34,8 @@ def nvcc() -> str:
 def _flags(src: str, extra=()):
     f = [nvcc(), "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC, "--expt-relaxed-constexpr"]
+    # extra compiler options (e.g. -DSMMO_DOALL_MIN_CTAS=2) from the environment
+    f += os.environ.get("SMMO_NVCC_FLAGS", "").split()
     if os.path.basename(src) in STRICT_FP:
         f += ["--fmad=false", "-prec-div=true", "-prec-sqrt=true", "-ftz=false"]
     return f + list(extra)

@@ -426,7 +426,7 @@ int freeze(smmo_heap* h, cudaStream_t s) {
   }
   if (min_size == (1 << 30)) return SMMO_E_UNSUPPORTED;
   uint32_t data_bytes = h->cfg.block_data_bytes ? h->cfg.block_data_bytes : 64u * (uint32_t)min_size;
-  data_bytes = (uint32_t)align_up(data_bytes, 128);
+  data_bytes = (uint32_t)align_up(data_bytes, 64);
   // capacity N_T: the largest N <= 64 whose 16-byte-aligned SOA columns fit
   for (auto& ci : h->classes) {
     ClassLayout& L = ci.layout;

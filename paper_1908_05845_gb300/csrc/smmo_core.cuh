@@ -23,6 +23,11 @@
 #include "smmo.h"
 
 #define SMMO_MAX_COLS 32
+// CTAs of 512 threads per SM that the do-all kernels are compiled for (the
+// register cap: 65536 / (512 x this)); 3 gives 40 registers.
+#ifndef SMMO_DOALL_MIN_CTAS
+#define SMMO_DOALL_MIN_CTAS 3
+#endif
 #define SMMO_MAX_LEVELS 6
 #define SMMO_NSHARD 32
 #define SMMO_CTR_SLOW 0
@@ -498,6 +503,11 @@ struct WarpAllocCache {
   int lock;
 };
 static __shared__ WarpAllocCache g_wcache[32];
+struct WarpNewBcast {  // warp_new: the cache's slots, broadcast by the leader
+  unsigned long long bits;
+  uint32_t bid;
+};
+static __shared__ WarpNewBcast g_wnew[32];
 
 __device__ __forceinline__ void alloc_cache_init() {
   const uint32_t lane = threadIdx.x & 31;
@@ -604,6 +614,180 @@ __device__ __forceinline__ uint32_t smmo_new(const HeapView& h, uint32_t c) {
   return result;
 }
 
+// ------------------------------------------------ warp-parallel allocation
+// new for a converged warp that needs `need` (1..32) objects of class c at
+// once (the deferred creations below): lane i < need receives a handle.
+// The warp's cache is used first; the rest is reserved in the blocks of
+// class c around the warp's hint (the 64 blocks of the hint's level-0
+// bitmap word) with one block per lane and every reservation in flight at
+// the same time: one round of loads (allocation bitmaps and type ids),
+// one round of atomicOr reservations, one round of type re-checks (a block
+// re-initialised to another class in between is rolled back, Alg. 5.1),
+// then the block-state changes of the blocks that became full or left the
+// candidates (as reserve_in).  A leader-at-a-time refill (smmo_new) serves
+// what is still missing, e.g. when every nearby block is full.
+__device__ __forceinline__ uint32_t warp_new(const HeapView& h, uint32_t c, uint32_t need) {
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  WarpAllocCache& wc = g_wcache[w];
+  uint32_t result = kNull;
+  // (1) the warp's cache (the warp is converged: no lane group of it is
+  // inside smmo_new, so the leader may touch the cache without the lock)
+  if (lane == 0) {
+    unsigned long long avail = wc.bits[c], take = 0;
+    for (uint32_t i = 0; i < need && avail; ++i) {
+      const unsigned long long low = avail & (0ull - avail);
+      take |= low;
+      avail ^= low;
+    }
+    wc.bits[c] = avail;
+    g_wnew[w].bits = take;
+    g_wnew[w].bid = wc.bid[c];
+    if (take) count(h, SMMO_CTR_ALLOC(c), __popcll(take));
+  }
+  __syncwarp();
+  const unsigned long long take = g_wnew[w].bits;
+  uint32_t got_n = (uint32_t)__popcll(take);
+  if (lane < got_n) result = (g_wnew[w].bid << 6) | (uint32_t)nth_set_bit64(take, lane);
+  __syncwarp();
+  // (2) the blocks of class c among the 64 around the hint, one per lane
+  const uint32_t hint = wc.hint;
+  if (got_n < need && hint < h.num_blocks) {
+    const uint32_t rem = need - got_n;
+    const uint32_t base = hint & ~63u;
+    uint32_t bid = kNull;
+    unsigned long long freeb = 0;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const uint32_t b = base + half * 32 + lane;
+      const bool ok = b < h.num_blocks && __ldcg(h.block_type + b) == c;
+      const unsigned long long f = ok ? ~ld_cg(h.alloc_bm + b) : 0ull;
+      if (bid == kNull && f) { bid = b; freeb = f; }
+    }
+    // the lowest free slots, in lane order, until rem are covered
+    const uint32_t nf = (uint32_t)__popcll(freeb);
+    uint32_t incl = nf;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= (uint32_t)o) incl += v;
+    }
+    const uint32_t excl = incl - nf;
+    unsigned long long pick = 0;
+    if (excl < rem) {
+      unsigned long long f = freeb;
+      for (uint32_t i = excl; i < rem && f; ++i) {
+        const unsigned long long low = f & (0ull - f);
+        pick |= low;
+        f ^= low;
+      }
+    }
+    unsigned long long got = 0;
+    if (pick) {
+      const unsigned long long before = atomicOr(h.alloc_bm + bid, pick);
+      got = pick & ~before;
+      if (got) {
+        const uint32_t t = atomicAdd(h.block_type + bid, 0u);
+        if (t < (uint32_t)h.num_classes) {
+          const unsigned long long tcap = __ldg(&h.cls[t].capmask);
+          const uint32_t dlim = __ldg(&h.cls[t].dlimit);
+          const uint32_t fb = __popcll(before & tcap), fa = fb + __popcll(got);
+          if ((before | got) == kAll) bm_clear(h, bm_active(h, t), bid);   // filled it
+          if (fb <= dlim && fa > dlim) bm_clear(h, bm_defrag(h, t), bid);  // no candidate now
+        }
+        if (t != c) {  // re-initialised to another class meanwhile: roll back
+          dealloc_bits(h, bid, t, got);
+          got = 0;
+        } else {
+          count(h, SMMO_CTR_ALLOC(c), __popcll(got));
+        }
+      }
+    }
+    // concatenate the lanes' reserved slots; lane got_n + j takes number j
+    const uint32_t ng = (uint32_t)__popcll(got);
+    uint32_t gi = ng;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, gi, o);
+      if (lane >= (uint32_t)o) gi += v;
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, gi, 31);
+    const uint32_t want = lane - got_n;  // wraps for lanes already served
+    uint32_t src = 0;  // first lane whose inclusive count exceeds want
+#pragma unroll
+    for (uint32_t step = 16; step; step >>= 1) {
+      const uint32_t v = __shfl_sync(0xFFFFFFFFu, gi, src + step - 1);
+      if (v <= want) src += step;
+    }
+    src &= 31;
+    const uint32_t sb = __shfl_sync(0xFFFFFFFFu, bid, src);
+    const unsigned long long sg = __shfl_sync(0xFFFFFFFFu, got, src);
+    const uint32_t sexcl = __shfl_sync(0xFFFFFFFFu, gi, src) - (uint32_t)__popcll(sg);
+    if (lane >= got_n && lane < need && want < total) result = (sb << 6) | (uint32_t)nth_set_bit64(sg, want - sexcl);
+    got_n += total;
+  }
+  // (3) what is still missing, one leader at a time
+  if (got_n < need && lane >= got_n && lane < need) result = smmo_new(h, c);
+  __syncwarp();
+  return lane < need ? result : kNull;
+}
+
+// ------------------------------------------------------- deferred creation
+// A method that creates objects may defer them: defer_new(payload) appends
+// a word to its warp's list in shared memory, and the do-all creates the
+// objects between rounds, 32 at a time with the whole warp (one
+// warp-aggregated new, Alg. 5.6, for 32 objects), passing each new object
+// and its payload to M::create.  The objects exist before the do-all ends,
+// as with a new inside the method, but the method itself carries no
+// allocator code, and the allocation is not split into the few lanes of a
+// round that create.  A method opts in by defining kDeferMax (the most
+// defer_new calls one run makes), child_class(args) and create(h, args,
+// child, payload); child is kNull if the heap is exhausted (the error is
+// recorded).
+template <class M, class = void>
+struct defers { static constexpr uint32_t max = 0; };
+template <class M>
+struct defers<M, decltype((void)M::kDeferMax)> { static constexpr uint32_t max = M::kDeferMax; };
+
+
+struct DeferList {
+  uint32_t n;
+  uint32_t item[32 + 32 * 2];  // < 32 left over + one round of at most 2 per lane
+};
+static __shared__ DeferList g_defer[16];
+
+__device__ __forceinline__ void defer_new(uint32_t payload) {
+  DeferList& d = g_defer[threadIdx.x >> 5];
+  const uint32_t at = atomicAdd(&d.n, 1u);
+  d.item[at] = payload;
+}
+
+// Creates the deferred objects of the calling (converged) warp in rounds of
+// 32 while 32 or more wait; with all = true also the rest (fewer than 32,
+// with part of the warp).
+template <class M>
+__device__ __forceinline__ void defer_flush(const HeapView& h, const typename M::Args& args, bool all) {
+  DeferList& d = g_defer[threadIdx.x >> 5];
+  const uint32_t lane = threadIdx.x & 31;
+  __syncwarp();
+  uint32_t n = d.n;
+  while (n >= 32) {
+    n -= 32;
+    const uint32_t p = d.item[n + lane];
+    const uint32_t child = warp_new(h, M::child_class(args), 32);
+    M::create(h, args, child, p);
+    __syncwarp();
+  }
+  if (all && n) {
+    const uint32_t p = lane < n ? d.item[lane] : 0u;
+    const uint32_t child = warp_new(h, M::child_class(args), n);
+    if (lane < n) M::create(h, args, child, p);
+    n = 0;
+  }
+  __syncwarp();
+  if (lane == 0) d.n = n;
+  __syncwarp();
+}
+
 // ---------------------------------------------------------------- do-all
 // Persistent do-all over the enumerated blocks (Sec. 5.2.7): the slots of
 // one block are handled by consecutive threads (one warp per 32 slots, a
@@ -616,17 +800,21 @@ __device__ __forceinline__ uint32_t smmo_new(const HeapView& h, uint32_t c) {
 // classes (the concrete subclasses of one class, enumerated one after the
 // other into one snapshot): every unit takes its block's class from the
 // enumeration entry and passes it to the method, and every block counts as
-// two units.
-template <class M, bool POLY = false>
-__global__ void __launch_bounds__(512, 3) do_all_kernel(HeapView h, uint32_t c,
-                                                     typename M::Args args) {
+// two units.  A method that defers its creations (defer_new) has them made
+// after each unit once 32 are listed, and the rest at the end.
+//
+// (Packing the live slots of several blocks into full warps through a
+// shared-memory queue was measured and dropped: the rounds then span two
+// blocks' columns and cost more sectors and instructions than the idle
+// lanes of partly full units, which these latency-bound kernels hide.)
+template <class M, bool POLY, class F, class G>
+__device__ __forceinline__ void for_each_unit(const HeapView& h, uint32_t c, F&& f, G&& after_unit) {
   const uint32_t n = __ldcg(h.rcnt);
   const uint32_t cap = POLY ? 64u : __ldg(&h.cls[c].cap);
   const uint32_t halves = cap > 32 ? 2u : 1u;
   const uint32_t units = n * halves;
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  alloc_cache_init();
   uint32_t visited = 0;
   const uint32_t per = (units + nwarps - 1) / nwarps;
   const uint32_t ub = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * per;
@@ -636,10 +824,29 @@ __global__ void __launch_bounds__(512, 3) do_all_kernel(HeapView h, uint32_t c,
     const REntry e = h.R[halves == 2 ? (u >> 1) : u];
     g_wcache[threadIdx.x >> 5].hint = e.block;
     if (lane == 0) visited += __popcll(halves == 2 ? (e.bits >> ((u & 1) * 32)) & 0xFFFFFFFFull : e.bits);
-    if ((e.bits >> slot) & 1) M::run(h, args, POLY ? e.cls : c, (e.block << 6) | slot);
+    if ((e.bits >> slot) & 1) f(POLY ? e.cls : c, (e.block << 6) | slot);
     __syncwarp();  // reconverge: lane groups never run different iterations
+    after_unit();
   }
   if (lane == 0 && visited) count(h, SMMO_CTR_VISIT, visited);
+}
+
+template <class M, bool POLY = false>
+__global__ void __launch_bounds__(512, SMMO_DOALL_MIN_CTAS) do_all_kernel(HeapView h, uint32_t c,
+                                                                          typename M::Args args) {
+  alloc_cache_init();
+  constexpr bool kDefer = defers<M>::max > 0;
+  static_assert(defers<M>::max <= 2, "defer list holds two per lane and unit");
+  if (kDefer && (threadIdx.x & 31) == 0) g_defer[threadIdx.x >> 5].n = 0;
+  __syncwarp();
+  for_each_unit<M, POLY>(
+      h, c, [&](uint32_t cls, uint32_t self) { M::run(h, args, cls, self); },
+      [&]() {
+        if constexpr (kDefer) {
+          if (g_defer[threadIdx.x >> 5].n >= 32) defer_flush<M>(h, args, false);
+        }
+      });
+  if constexpr (kDefer) defer_flush<M>(h, args, true);
   alloc_cache_flush(h);
 }
 
@@ -671,30 +878,15 @@ __device__ __forceinline__ long long reduce2(int op, long long x, long long y) {
 }
 
 template <class M, bool POLY = false>
-__global__ void __launch_bounds__(512, 3) do_all_reduce_kernel(HeapView h, uint32_t c, typename M::Args args,
-                                                               int op, long long* out) {
+__global__ void __launch_bounds__(512, SMMO_DOALL_MIN_CTAS) do_all_reduce_kernel(HeapView h, uint32_t c,
+                                                                                 typename M::Args args, int op,
+                                                                                 long long* out) {
   __shared__ long long part[16];
-  const uint32_t n = __ldcg(h.rcnt);
-  const uint32_t cap = POLY ? 64u : __ldg(&h.cls[c].cap);
-  const uint32_t halves = cap > 32 ? 2u : 1u;
-  const uint32_t units = n * halves;
   const uint32_t lane = threadIdx.x & 31;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   alloc_cache_init();
-  uint32_t visited = 0;
   long long acc = reduce_identity(op);
-  const uint32_t per = (units + nwarps - 1) / nwarps;
-  const uint32_t ub = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * per;
-  const uint32_t ue = ub + per < units ? ub + per : units;
-  for (uint32_t u = ub; u < ue; ++u) {
-    const uint32_t slot = (halves == 2 ? (u & 1) * 32 : 0) + lane;
-    const REntry e = h.R[halves == 2 ? (u >> 1) : u];
-    g_wcache[threadIdx.x >> 5].hint = e.block;
-    if (lane == 0) visited += __popcll(halves == 2 ? (e.bits >> ((u & 1) * 32)) & 0xFFFFFFFFull : e.bits);
-    if ((e.bits >> slot) & 1) acc = reduce2(op, acc, M::run(h, args, POLY ? e.cls : c, (e.block << 6) | slot));
-    __syncwarp();
-  }
-  if (lane == 0 && visited) count(h, SMMO_CTR_VISIT, visited);
+  for_each_unit<M, POLY>(
+      h, c, [&](uint32_t cls, uint32_t self) { acc = reduce2(op, acc, M::run(h, args, cls, self)); }, [] {});
   alloc_cache_flush(h);
 #pragma unroll
   for (int o = 16; o; o >>= 1) acc = reduce2(op, acc, __shfl_xor_sync(0xFFFFFFFFu, acc, o));

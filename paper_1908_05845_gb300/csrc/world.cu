@@ -39,7 +39,7 @@ namespace {
 
 struct WorldArgs {
   CellRef cells;
-  uint32_t occ_off, req_off;
+  uint32_t occ_off, req_off, kind_off;
   uint32_t fish, shark, alive, cand;
   uint32_t f_cell, f_target, f_age;
   uint32_t s_cell, s_target, s_age, s_energy;
@@ -65,24 +65,91 @@ __device__ __forceinline__ T* fld(const HeapView& h, uint32_t self, uint32_t off
 }
 
 // ================================================================ Wa-Tor
-// One phase = prepare (choose a neighbour, post a request) + update (move if
+// A cell holds its occupant's handle, a 32-bit request word and a one-byte
+// kind that only the Life instances use (see the Life section).  One phase
+// = prepare (choose a neighbour, post a request) + update (move if
 // granted).  The thesis' Cell::prepare / Cell::decide passes are folded into
-// the request word of the target cell: an agent on cell s posts
-// key = ((0xFFFFFFFF - phase) << 32) | s with atomicMin; the smallest key of
-// the current phase wins (lowest source cell), keys of older phases are
-// larger and never win, so no pass over all cells is needed to reset them.
-__device__ __forceinline__ unsigned long long req_key(uint32_t t, uint32_t phase, uint32_t src) {
-  return ((unsigned long long)(0xFFFFFFFFu - (2u * t + phase)) << 32) | src;
+// the request word of the target cell: the movers into a cell are among its
+// four neighbours, so the lowest source cell is the requester of lowest rank
+// among them (rank = how many of the target's neighbours have a smaller cell
+// index); a requester posts key = ((2^30 - 1 - epoch) << 2) | rank with
+// atomicMin, epoch = 2 t + phase.  The smallest key of the current phase
+// wins, keys of older phases are larger and never win, so no pass over all
+// cells resets them (2^29 steps).  The prepare keeps target | rank << 30 in
+// the agent's target field (cells are below 2^30), so the update finds
+// both without recomputing.  (A kind byte per cell for the Wa-Tor
+// neighbour tests, replacing the handle and type-id loads, was measured:
+// the prepares gained less than the two extra byte stores per mover cost
+// the updates.)
+enum : uint8_t { K_EMPTY = 0, K_ALIVE = 1, K_CAND = 2, K_BLOCK = 3 };
+constexpr uint32_t kCellMask = 0x3FFFFFFFu;
+
+__device__ __forceinline__ uint32_t req_key(uint32_t t, uint32_t phase, uint32_t rank) {
+  return ((0x3FFFFFFFu - (2u * t + phase)) << 2) | rank;
 }
 
-// The (r mod k)-th of the k directions set in mask (in direction order 0..3),
-// as the neighbour cell nb[d]; every index is a constant, so nb stays in
-// registers.
-__device__ __forceinline__ uint32_t pick_dir(const uint32_t (&nb)[4], uint32_t mask, uint32_t r) {
+// Rank (0..3) of the neighbour in direction e of cell (tx, ty) among its
+// four neighbours by cell index, on a W x H torus (W, H >= 3).  Cell index
+// = row W + column, so neighbours order by row first: the row above
+// (ty - 1), the cell's own row (the horizontal pair) and the row below
+// (ty + 1), taken mod H.  Inside the torus that is up, pair, down; on the
+// first row (up wraps to the last row) pair, down, up; on the last row
+// (down wraps to row 0) down, up, pair.  Within the pair left comes before
+// right except on the first and last columns, where one of them wraps.
+__device__ __forceinline__ uint32_t nb_rank(uint32_t tx, uint32_t ty, uint32_t W, uint32_t H, int e) {
+  const bool top = ty == 0, bottom = ty + 1 == H;
+  if (e == 0) return top ? 3u : bottom ? 1u : 0u;  // up
+  if (e == 2) return top ? 2u : bottom ? 0u : 3u;  // down
+  const uint32_t pair = top ? 0u : bottom ? 2u : 1u;
+  const bool hwrap = tx == 0 || tx + 1 == W;
+  return pair + ((e == 3) == hwrap ? 1u : 0u);     // left (3) or right (1)
+}
+
+// (x, y) of the neighbour in direction d of local cell (x, y).
+__device__ __forceinline__ void nb_xy(uint32_t x, uint32_t y, uint32_t W, uint32_t H, int d, uint32_t* nx,
+                                      uint32_t* ny) {
+  *nx = x; *ny = y;
+  if (d == 0) *ny = y == 0 ? H - 1 : y - 1;
+  else if (d == 1) *nx = x + 1 == W ? 0 : x + 1;
+  else if (d == 2) *ny = y + 1 == H ? 0 : y + 1;
+  else *nx = x == 0 ? W - 1 : x - 1;
+}
+
+// The (r mod k)-th of the k directions set in mask (in direction order 0..3).
+__device__ __forceinline__ int pick_dir(uint32_t mask, uint32_t r) {
   uint32_t k = r % (uint32_t)__popc(mask);
   while (k--) mask &= mask - 1;
-  const int d = __ffs(mask) - 1;
-  return d == 0 ? nb[0] : d == 1 ? nb[1] : d == 2 ? nb[2] : nb[3];
+  return __ffs(mask) - 1;
+}
+
+// Posts the request of the agent on local cell (x, y) of `in` to move in
+// direction d; returns target | rank << 30 for the agent's target field.
+__device__ __forceinline__ uint32_t post_request(const WorldArgs& a, const Inst* in, uint32_t x, uint32_t y,
+                                                 int d, uint32_t t) {
+  uint32_t tx, ty;
+  nb_xy(x, y, in->W, in->H, d, &tx, &ty);
+  const uint32_t rank = nb_rank(tx, ty, in->W, in->H, (d + 2) & 3);  // we are its neighbour d + 2
+  const uint32_t tgt = in->cell_base + ty * in->W + tx;
+  atomicMin(a.cells.col<uint32_t>(tgt, a.req_off), req_key(t, a.phase, rank));
+  return tgt | (rank << 30);
+}
+
+// Whether the request recorded in target field value tv (see post_request)
+// won.
+__device__ __forceinline__ bool won_request(const WorldArgs& a, uint32_t tv) {
+  return *a.cells.col<uint32_t>(tv & kCellMask, a.req_off) == req_key(*a.tp, a.phase, tv >> 30);
+}
+
+// Occupant of a Wa-Tor cell (the Wa-Tor methods test neighbours through
+// the handle; their cells' kind bytes stay K_EMPTY).
+__device__ __forceinline__ void set_occ(const WorldArgs& a, uint32_t g, uint32_t handle) {
+  *a.cells.col<uint32_t>(g, a.occ_off) = handle;
+}
+
+// Occupant of a Life cell and its kind byte.
+__device__ __forceinline__ void set_cell(const WorldArgs& a, uint32_t g, uint32_t handle, uint8_t kind) {
+  *a.cells.col<uint32_t>(g, a.occ_off) = handle;
+  *a.cells.col<uint8_t>(g, a.kind_off) = kind;
 }
 
 struct FishPrepare {
@@ -95,47 +162,52 @@ struct FishPrepare {
     const uint32_t lc = g - in->cell_base, W = in->W, H = in->H;
     uint32_t x, y;
     cell_xy(in, lc, &x, &y);
-    uint32_t nb[4], empty = 0;
+    uint32_t empty = 0;
 #pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      nb[d] = in->cell_base + torus_nb4(x, y, W, H, d);
-      if (*a.cells.col<uint32_t>(nb[d], a.occ_off) == kNull) empty |= 1u << d;
-    }
+    for (int d = 0; d < 4; ++d)
+      if (*a.cells.col<uint32_t>(in->cell_base + torus_nb4(x, y, W, H, d), a.occ_off) == kNull) empty |= 1u << d;
     uint32_t tgt = g;
     if (empty) {
       const uint32_t t = *a.tp;
       const uint32_t r = philox_draw(a.seed, TAG_FISH, t, lc, in->id);
-      tgt = pick_dir(nb, empty, r);
-      atomicMin(a.cells.col<unsigned long long>(tgt, a.req_off), req_key(t, a.phase, g));
+      tgt = post_request(a, in, x, y, pick_dir(empty, r), t);
     }
     *fld<int32_t>(h, self, a.f_target) = (int32_t)tgt;
   }
 };
 
+// Moves a fish whose request won; a ripe mover leaves a newborn fish on its
+// old cell (created after the round, see defer_new), every other mover
+// leaves it empty.
 struct FishUpdate {
   using Args = WorldArgs;
+  static constexpr uint32_t kDeferMax = 1;
+  __device__ static uint32_t child_class(const Args& a) { return a.fish; }
+  __device__ static void create(const HeapView& h, const Args& a, uint32_t child, uint32_t g) {
+    if (child != kNull) {
+      *fld<int32_t>(h, child, a.f_cell) = (int32_t)g;
+      *fld<int32_t>(h, child, a.f_target) = (int32_t)g;
+      *fld<int16_t>(h, child, a.f_age) = 0;
+    }
+    set_occ(a, g, child);
+  }
   __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
     int32_t* cellp = fld<int32_t>(h, self, a.f_cell);
     const uint32_t g = *cellp;
-    const uint32_t tgt = *fld<int32_t>(h, self, a.f_target);
-    if (tgt == g) return;
-    if (*a.cells.col<unsigned long long>(tgt, a.req_off) != req_key(*a.tp, a.phase, g)) return;
-    *a.cells.col<uint32_t>(tgt, a.occ_off) = self;
+    const uint32_t tv = *fld<int32_t>(h, self, a.f_target);
+    const uint32_t tgt = tv & kCellMask;
+    if (tgt == g || !won_request(a, tv)) return;
+    set_occ(a, tgt, self);
     *cellp = (int32_t)tgt;
     int16_t* agep = fld<int16_t>(h, self, a.f_age);
     const int age = *agep;
     const bool ripe = a.breed_strict ? age > a.fish_breed : age >= a.fish_breed;
-    uint32_t child = kNull;
     if (ripe) {
       *agep = 0;
-      child = smmo_new(h, a.fish);
-      if (child != kNull) {
-        *fld<int32_t>(h, child, a.f_cell) = (int32_t)g;
-        *fld<int32_t>(h, child, a.f_target) = (int32_t)g;
-        *fld<int16_t>(h, child, a.f_age) = 0;
-      }
+      defer_new(g);
+    } else {
+      set_occ(a, g, kNull);
     }
-    *a.cells.col<uint32_t>(g, a.occ_off) = child;
   }
 };
 
@@ -154,62 +226,67 @@ struct SharkPrepare {
       const uint32_t lc = g - in->cell_base, W = in->W, H = in->H;
       uint32_t x, y;
       cell_xy(in, lc, &x, &y);
-      uint32_t nb[4], fish = 0, empty = 0;
+      uint32_t fish = 0, empty = 0;
 #pragma unroll
       for (int d = 0; d < 4; ++d) {
-        nb[d] = in->cell_base + torus_nb4(x, y, W, H, d);
-        const uint32_t o = *a.cells.col<uint32_t>(nb[d], a.occ_off);
+        const uint32_t o = *a.cells.col<uint32_t>(in->cell_base + torus_nb4(x, y, W, H, d), a.occ_off);
         if (o == kNull) empty |= 1u << d;
         else if (type_of(h, o) == a.fish) fish |= 1u << d;
       }
       if (fish | empty) {
         const uint32_t t = *a.tp;
         const uint32_t r = philox_draw(a.seed, TAG_SHARK, t, lc, in->id);
-        tgt = pick_dir(nb, fish ? fish : empty, r);
-        atomicMin(a.cells.col<unsigned long long>(tgt, a.req_off), req_key(t, a.phase, g));
+        tgt = post_request(a, in, x, y, pick_dir(fish ? fish : empty, r), t);
       }
     }
     *fld<int32_t>(h, self, a.s_target) = (int32_t)tgt;
   }
 };
 
+// A starved shark leaves its cell and deletes itself; a mover eats the fish
+// on its target (deleting an object of another class) and, when ripe,
+// leaves a newborn shark on its old cell (deferred, as for fish).
 struct SharkUpdate {
   using Args = WorldArgs;
+  static constexpr uint32_t kDeferMax = 1;
+  __device__ static uint32_t child_class(const Args& a) { return a.shark; }
+  __device__ static void create(const HeapView& h, const Args& a, uint32_t child, uint32_t g) {
+    if (child != kNull) {
+      *fld<int32_t>(h, child, a.s_cell) = (int32_t)g;
+      *fld<int32_t>(h, child, a.s_target) = (int32_t)g;
+      *fld<int16_t>(h, child, a.s_age) = 0;
+      *fld<int16_t>(h, child, a.s_energy) = (int16_t)a.starve;
+    }
+    set_occ(a, g, child);
+  }
   __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
     int32_t* cellp = fld<int32_t>(h, self, a.s_cell);
     const uint32_t g = *cellp;
     int16_t* enp = fld<int16_t>(h, self, a.s_energy);
+    const uint32_t tv = *fld<int32_t>(h, self, a.s_target);
+    int16_t* agep = fld<int16_t>(h, self, a.s_age);
+    const int age = *agep;
     if (*enp == 0) {  // starved: leave the cell and delete itself (last statement)
-      *a.cells.col<uint32_t>(g, a.occ_off) = kNull;
+      set_occ(a, g, kNull);
       smmo_delete(h, self);
       return;
     }
-    const uint32_t tgt = *fld<int32_t>(h, self, a.s_target);
-    if (tgt == g) return;
-    if (*a.cells.col<unsigned long long>(tgt, a.req_off) != req_key(*a.tp, a.phase, g)) return;
-    uint32_t* tocc = a.cells.col<uint32_t>(tgt, a.occ_off);
-    const uint32_t prey = *tocc;
+    const uint32_t tgt = tv & kCellMask;
+    if (tgt == g || !won_request(a, tv)) return;
+    const uint32_t prey = *a.cells.col<uint32_t>(tgt, a.occ_off);
     if (prey != kNull) {  // eat the fish (deleting an object of another class)
       smmo_delete(h, prey);
       *enp = (int16_t)a.starve;
     }
-    *tocc = self;
+    set_occ(a, tgt, self);
     *cellp = (int32_t)tgt;
-    int16_t* agep = fld<int16_t>(h, self, a.s_age);
-    const int age = *agep;
     const bool ripe = a.breed_strict ? age > a.shark_breed : age >= a.shark_breed;
-    uint32_t child = kNull;
     if (ripe) {
       *agep = 0;
-      child = smmo_new(h, a.shark);
-      if (child != kNull) {
-        *fld<int32_t>(h, child, a.s_cell) = (int32_t)g;
-        *fld<int32_t>(h, child, a.s_target) = (int32_t)g;
-        *fld<int16_t>(h, child, a.s_age) = 0;
-        *fld<int16_t>(h, child, a.s_energy) = (int16_t)a.starve;
-      }
+      defer_new(g);
+    } else {
+      set_occ(a, g, kNull);
     }
-    *a.cells.col<uint32_t>(g, a.occ_off) = child;
   }
 };
 
@@ -223,17 +300,21 @@ __device__ __forceinline__ uint32_t torus8(uint32_t x, uint32_t y, int dx, int d
   return ny * W + nx;
 }
 
-__device__ __forceinline__ int alive_neighbours(const HeapView& h, const WorldArgs& a,
-                                                const Inst* in, uint32_t x, uint32_t y) {
+// Kind byte of a Life cell (see the Wa-Tor section): an Alive born in this
+// generation's candidate update is K_NEW until the alive prepare of the
+// next generation clears its is_new; a dead Alive that blocks its cell is
+// K_BLOCK.  Alive neighbours are those of kind K_ALIVE or K_NEW.
+enum : uint8_t { K_NEW = 4 };
+
+__device__ __forceinline__ int alive_neighbours(const WorldArgs& a, const Inst* in, uint32_t x, uint32_t y) {
   int n = 0;
 #pragma unroll
   for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
     for (int dx = -1; dx <= 1; ++dx) {
       if (!dx && !dy) continue;
-      const uint32_t o = *a.cells.col<uint32_t>(in->cell_base + torus8(x, y, dx, dy, in->W, in->H), a.occ_off);
-      if (o != kNull && type_of(h, o) == a.alive && (a.block == 0 || *fld<uint16_t>(h, o, a.a_blocked) == 0))
-        ++n;
+      const uint8_t k = *a.cells.col<uint8_t>(in->cell_base + torus8(x, y, dx, dy, in->W, in->H), a.kind_off);
+      n += (k == K_ALIVE) | (k == K_NEW);
     }
   return n;
 }
@@ -246,7 +327,7 @@ struct CandPrepare {
     const uint32_t lc = g - in->cell_base;
     uint32_t x, y;
     cell_xy(in, lc, &x, &y);
-    const int n = alive_neighbours(h, a, in, x, y);
+    const int n = alive_neighbours(a, in, x, y);
     *fld<uint8_t>(h, self, a.c_action) = ((a.born >> n) & 1) ? ACT_BORN : (n == 0 ? ACT_DELETE : ACT_KEEP);
   }
 };
@@ -255,7 +336,11 @@ struct AlivePrepare {
   using Args = WorldArgs;
   __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
     const uint32_t g = *fld<int32_t>(h, self, a.a_cell);
-    *fld<uint8_t>(h, self, a.a_isnew) = 0;
+    uint8_t* isnew = fld<uint8_t>(h, self, a.a_isnew);
+    if (*isnew) {  // K_NEW -> K_ALIVE; concurrent neighbour counts see either
+      *isnew = 0;
+      *a.cells.col<uint8_t>(g, a.kind_off) = K_ALIVE;
+    }
     const uint32_t blocked = a.block ? *fld<uint16_t>(h, self, a.a_blocked) : 0u;
     if (blocked) {  // dead and blocking its cell
       *fld<uint8_t>(h, self, a.a_action) = blocked >= a.block ? ACT_EXPIRE : ACT_AGE;
@@ -265,28 +350,33 @@ struct AlivePrepare {
     const uint32_t lc = g - in->cell_base;
     uint32_t x, y;
     cell_xy(in, lc, &x, &y);
-    const int n = alive_neighbours(h, a, in, x, y);
+    const int n = alive_neighbours(a, in, x, y);
     *fld<uint8_t>(h, self, a.a_action) = ((a.survive >> n) & 1) ? ACT_KEEP : ACT_DIE;
   }
 };
 
+// A candidate that is born is replaced by a new Alive (created after the
+// round, see defer_new: nothing else in this do-all reads its cell); one
+// without alive neighbours leaves its cell empty.
 struct CandUpdate {
   using Args = WorldArgs;
+  static constexpr uint32_t kDeferMax = 1;
+  __device__ static uint32_t child_class(const Args& a) { return a.alive; }
+  __device__ static void create(const HeapView& h, const Args& a, uint32_t child, uint32_t g) {
+    if (child != kNull) {
+      *fld<int32_t>(h, child, a.a_cell) = (int32_t)g;
+      *fld<uint8_t>(h, child, a.a_action) = ACT_KEEP;
+      *fld<uint8_t>(h, child, a.a_isnew) = 1;
+      *fld<uint16_t>(h, child, a.a_blocked) = 0;
+    }
+    set_cell(a, g, child, child != kNull ? K_NEW : K_EMPTY);
+  }
   __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
     const uint8_t act = *fld<uint8_t>(h, self, a.c_action);
     if (act == ACT_KEEP) return;
     const uint32_t g = *fld<int32_t>(h, self, a.c_cell);
-    uint32_t repl = kNull;
-    if (act == ACT_BORN) {
-      repl = smmo_new(h, a.alive);
-      if (repl != kNull) {
-        *fld<int32_t>(h, repl, a.a_cell) = (int32_t)g;
-        *fld<uint8_t>(h, repl, a.a_action) = ACT_KEEP;
-        *fld<uint8_t>(h, repl, a.a_isnew) = 1;
-        *fld<uint16_t>(h, repl, a.a_blocked) = 0;
-      }
-    }
-    *a.cells.col<uint32_t>(g, a.occ_off) = repl;
+    if (act == ACT_BORN) defer_new(g);
+    else set_cell(a, g, kNull, K_EMPTY);
     smmo_delete(h, self);
   }
 };
@@ -297,7 +387,9 @@ struct AliveUpdate {
     const uint32_t g = *fld<int32_t>(h, self, a.a_cell);
     if (*fld<uint8_t>(h, self, a.a_isnew)) {
       // create Candidates on empty surrounding cells; the creator of an empty
-      // cell e is the first new Alive of e's neighbourhood in scan order
+      // cell e is the first new Alive of e's neighbourhood in scan order.
+      // Kinds read here: K_NEW never changes during this do-all, and only
+      // the creator of e writes e, so what the others read does not matter.
       const Inst* in = find_inst(h, g);
       const uint32_t lc = g - in->cell_base, W = in->W, H = in->H;
       uint32_t x, y;
@@ -306,33 +398,32 @@ struct AliveUpdate {
         for (int dy = -1; dy <= 1; ++dy) {
           const uint32_t el = torus8(x, y, dx, dy, W, H);
           const uint32_t e = in->cell_base + el;
-          uint32_t* eocc = a.cells.col<uint32_t>(e, a.occ_off);
-          if (*(volatile uint32_t*)eocc != kNull) continue;
+          if (*a.cells.col<uint8_t>(e, a.kind_off) != K_EMPTY) continue;
           uint32_t ex, ey;
           cell_xy(in, el, &ex, &ey);
           uint32_t first = kNull;
           for (int ddx = -1; ddx <= 1 && first == kNull; ++ddx)
             for (int ddy = -1; ddy <= 1; ++ddy) {
-              const uint32_t o = *(volatile uint32_t*)a.cells.col<uint32_t>(
-                  in->cell_base + torus8(ex, ey, ddx, ddy, W, H), a.occ_off);
-              if (o != kNull && type_of(h, o) == a.alive && *fld<uint8_t>(h, o, a.a_isnew)) {
+              const uint32_t o = in->cell_base + torus8(ex, ey, ddx, ddy, W, H);
+              if (*a.cells.col<uint8_t>(o, a.kind_off) == K_NEW) {
                 first = o;
                 break;
               }
             }
-          if (first == self) {
+          if (first == g) {
             const uint32_t cnd = smmo_new(h, a.cand);
             if (cnd != kNull) {
               *fld<int32_t>(h, cnd, a.c_cell) = (int32_t)e;
               *fld<uint8_t>(h, cnd, a.c_action) = ACT_KEEP;
             }
-            *eocc = cnd;
+            set_cell(a, e, cnd, cnd != kNull ? K_CAND : K_EMPTY);
           }
         }
     } else {
       const uint8_t act = *fld<uint8_t>(h, self, a.a_action);
       if (act == ACT_DIE && a.block) {
         *fld<uint16_t>(h, self, a.a_blocked) = 1;  // dead: blocks its cell
+        *a.cells.col<uint8_t>(g, a.kind_off) = K_BLOCK;
       } else if (act == ACT_AGE) {
         uint16_t* b = fld<uint16_t>(h, self, a.a_blocked);
         *b = (uint16_t)(*b + 1);
@@ -342,7 +433,7 @@ struct AliveUpdate {
           *fld<int32_t>(h, cnd, a.c_cell) = (int32_t)g;
           *fld<uint8_t>(h, cnd, a.c_action) = ACT_KEEP;
         }
-        *a.cells.col<uint32_t>(g, a.occ_off) = cnd;
+        set_cell(a, g, cnd, cnd != kNull ? K_CAND : K_EMPTY);
         smmo_delete(h, self);
       }
     }
@@ -410,25 +501,40 @@ struct ExportBits {
   }
 };
 
-// Initial back-references: every agent writes its handle into its cell.
+// Kind byte of the cell of agent `self` of class c.
+__device__ __forceinline__ uint8_t kind_code(const HeapView& h, const WorldArgs& a, uint32_t c, uint32_t self) {
+  if (c == a.fish || c == a.shark) return K_EMPTY;  // Wa-Tor keeps no kind bytes
+  if (c == a.cand) return K_CAND;
+  if (*fld<uint16_t>(h, self, a.a_blocked)) return K_BLOCK;
+  return *fld<uint8_t>(h, self, a.a_isnew) ? K_NEW : K_ALIVE;
+}
+
+// Initial back-references: every agent writes its handle and kind into its
+// cell.
 struct Link {
   using Args = WorldArgs;
   __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
     uint32_t off = c == a.fish ? a.f_cell : c == a.shark ? a.s_cell : c == a.alive ? a.a_cell : a.c_cell;
-    *a.cells.col<uint32_t>(*fld<int32_t>(h, self, off), a.occ_off) = self;
+    set_cell(a, *fld<int32_t>(h, self, off), self, kind_code(h, a, c, self));
   }
 };
 
-// Occupied cells whose agent does not live on them count as errors.
+// Occupied cells whose agent does not live on them, and cells whose kind
+// byte disagrees with their occupant, count as errors.
 struct CheckCells {
   using Args = WorldArgs;
   __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
     const uint32_t g = a.cells.cell_of(self);
     const uint32_t o = *a.cells.col<uint32_t>(g, a.occ_off);
-    if (o == kNull) return;
+    const uint8_t k = *a.cells.col<uint8_t>(g, a.kind_off);
+    if (o == kNull) {
+      if (k != K_EMPTY) atomicAdd(a.errors, 1ull);
+      return;
+    }
     const uint32_t t = type_of(h, o);
+    if (t >= (uint32_t)h.num_classes) { atomicAdd(a.errors, 1ull); return; }
     uint32_t off = t == a.fish ? a.f_cell : t == a.shark ? a.s_cell : t == a.alive ? a.a_cell : a.c_cell;
-    if (t >= (uint32_t)h.num_classes || (uint32_t)*fld<int32_t>(h, o, off) != g) atomicAdd(a.errors, 1ull);
+    if ((uint32_t)*fld<int32_t>(h, o, off) != g || k != kind_code(h, a, t, o)) atomicAdd(a.errors, 1ull);
   }
 };
 
@@ -540,7 +646,7 @@ int smmo_world_create_batch(smmo_heap* heap, const smmo_instance_desc* inst, int
     if ((d.kind != SMMO_WORLD_LIFE && d.kind != SMMO_WORLD_WATOR) || d.W < 3 || d.H < 3) return SMMO_E_INVALID_ARG;
     if (d.base != total || d.count != (uint64_t)d.W * d.H) return SMMO_E_INVALID_ARG;
     total += d.count;
-    if (total >= (1ull << 31)) return SMMO_E_INVALID_ARG;
+    if (total > kCellMask + 1ull) return SMMO_E_INVALID_ARG;  // cells below 2^30
   }
   int st = smmo_batch_define(heap, inst, n_inst);  // the heap owns the instance table
   if (st) return st;
@@ -558,8 +664,8 @@ int smmo_world_create_batch(smmo_heap* heap, const smmo_instance_desc* inst, int
   }
   w->total_cells = total;
   // classes
-  smmo_field_desc cell_f[2] = {{"occ", SMMO_HANDLE, 1, -1}, {"req", SMMO_U64, 1, -1}};
-  st = smmo_class_register(heap, "Cell", cell_f, 2, -1, 0, &w->cls_cell);
+  smmo_field_desc cell_f[3] = {{"occ", SMMO_HANDLE, 1, -1}, {"req", SMMO_U32, 1, -1}, {"kind", SMMO_U8, 1, -1}};
+  st = smmo_class_register(heap, "Cell", cell_f, 3, -1, 0, &w->cls_cell);
   if (!st && w->nw) {
     smmo_field_desc ag[2] = {{"cell", SMMO_I32, 1, -1}, {"target", SMMO_I32, 1, -1}};
     smmo_field_desc fi[1] = {{"age", SMMO_I16, 1, -1}};
@@ -575,7 +681,8 @@ int smmo_world_create_batch(smmo_heap* heap, const smmo_instance_desc* inst, int
     if (!st) st = smmo_class_register(heap, "Alive", al, 2, w->cls_lagent, 0, &w->cls_alive);
     if (!st) st = smmo_class_register(heap, "Candidate", nullptr, 0, w->cls_lagent, 0, &w->cls_cand);
   }
-  if (heap->cfg.block_data_bytes == 0) heap->cfg.block_data_bytes = 768;  // every class gets N_T = 64
+  // 768 bytes: Cell (9 bytes), Fish, Shark and the Life agents get N_T = 64
+  if (heap->cfg.block_data_bytes == 0) heap->cfg.block_data_bytes = 768;
   if (!st) st = freeze(heap, s);
   if (!st && heap->classes[w->cls_cell].layout.cap != 64 && heap->classes[w->cls_cell].layout.cap != 32)
     st = SMMO_E_UNSUPPORTED;  // dense cell addressing needs N = 32 or 64
@@ -584,20 +691,20 @@ int smmo_world_create_batch(smmo_heap* heap, const smmo_instance_desc* inst, int
   cudaError_t e = cudaMalloc(&w->d_t, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemsetAsync(w->d_t, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) { smmo_world_destroy(w); return cuda_status(e); }
-  // cells: occ = null, req = all ones
+  // cells: occ = null, req = all ones (above every key), kind = empty
   const uint64_t N = w->total_cells;
-  uint32_t* occ0 = nullptr;
-  unsigned long long* req0 = nullptr;
-  e = cudaMallocAsync(&occ0, N * 4, s);
-  if (e == cudaSuccess) e = cudaMallocAsync(&req0, N * 8, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(occ0, 0xFF, N * 4, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(req0, 0xFF, N * 8, s);
+  uint32_t* ones = nullptr;
+  uint8_t* zeros = nullptr;
+  e = cudaMallocAsync(&ones, N * 4, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&zeros, N, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ones, 0xFF, N * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(zeros, 0, N, s);
   if (e != cudaSuccess) { smmo_world_destroy(w); return cuda_status(e); }
-  const void* csrc[2] = {occ0, req0};
+  const void* csrc[3] = {ones, ones, zeros};
   int64_t first = -1;
   st = smmo_bulk_new(heap, w->cls_cell, (int64_t)N, csrc, nullptr, &first, stream);
-  cudaFreeAsync(occ0, s);
-  cudaFreeAsync(req0, s);
+  cudaFreeAsync(ones, s);
+  cudaFreeAsync(zeros, s);
   if (!st && first < 0) st = SMMO_E_OOM;  // cells must be contiguous
   if (st) { smmo_world_destroy(w); return st; }
   // argument block
@@ -611,6 +718,7 @@ int smmo_world_create_batch(smmo_heap* heap, const smmo_instance_desc* inst, int
   const ClassLayout& CL = heap->classes[w->cls_cell].layout;
   a.occ_off = CL.col_off[0];
   a.req_off = CL.col_off[1];
+  a.kind_off = CL.col_off[2];
   a.fish = a.shark = a.alive = a.cand = kNull;
   if (w->nw) {
     const ClassLayout& F = heap->classes[w->cls_fish].layout;

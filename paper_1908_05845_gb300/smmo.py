@@ -23,7 +23,7 @@ NULL = 0xFFFFFFFF
 I8, U8, I16, U16, I32, U32, F32, I64, U64, F64, HANDLE, INSTANCE = range(1, 13)
 _TORCH = {I8: torch.int8, U8: torch.uint8, I16: torch.int16, U16: torch.int16, I32: torch.int32,
           U32: torch.int32, F32: torch.float32, I64: torch.int64, U64: torch.int64,
-          F64: torch.float64, HANDLE: torch.int32}
+          F64: torch.float64, HANDLE: torch.int32, INSTANCE: torch.int32}
 MAX_CLASSES = 16
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "heap has too few free blocks",

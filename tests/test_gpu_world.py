@@ -166,11 +166,11 @@ def test_results_identical_for_every_tuning_choice(orc):
         ks.append(kk.astype(np.int8)); ags.append(aa); ens.append(ee); sts.append(s)
     init = [np.concatenate(x) for x in (ks, ags, ens, sts)]
     outs = []
-    for cfg in ({"block_data_bytes": 384, "threads_per_cta": 128, "ctas_per_sm": 4},
-                {"block_data_bytes": 768, "threads_per_cta": 512, "ctas_per_sm": 16},
-                {"block_data_bytes": 768, "threads_per_cta": 256, "ctas_per_sm": 8},
-                {"block_data_bytes": 768, "threads_per_cta": 256, "ctas_per_sm": 8, "bitmap_fanout": 32},
-                {"block_data_bytes": 384, "threads_per_cta": 512, "ctas_per_sm": 4, "bitmap_fanout": 32}):
+    for cfg in ({"block_data_bytes": 320, "threads_per_cta": 128, "ctas_per_sm": 4},
+                {"block_data_bytes": 640, "threads_per_cta": 512, "ctas_per_sm": 16},
+                {"block_data_bytes": 640, "threads_per_cta": 256, "ctas_per_sm": 8},
+                {"block_data_bytes": 640, "threads_per_cta": 256, "ctas_per_sm": 8, "bitmap_fanout": 32},
+                {"block_data_bytes": 320, "threads_per_cta": 512, "ctas_per_sm": 4, "bitmap_fanout": 32}):
         w = World(kinds, sides, sides, seed, *init, config=smmo.default_config(**cfg))
         w.step(20)
         outs.append(w.export())
