@@ -341,14 +341,28 @@ def run_gpu(args, ws, rank, local):
 
     cpu = None
     e2e = None
+    parity = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        upd, dt, _ = oracle_sample(args.cpu_steps)
+        # the oracle runs the timed steps themselves when they are few
+        # enough (then the timed run's end state is compared with it)
+        csteps = args.steps if args.steps <= 100 else args.cpu_steps
+        upd, dt, want = oracle_sample(csteps)
         cpu = {"value": upd / dt, "unit": "object-updates/s", "cores": 1, "kind": "oracle", "host": host_info(),
                "sample": "Wa-Tor 2048x2048 steps 1..%d (single-threaded C oracle, %.1f s)"
-                         % (args.cpu_steps, dt)}
+                         % (csteps, dt)}
+        if csteps == args.steps and seed == SEED:
+            got = sim.read()
+            parity = {"value": bool(all(np.array_equal(g, w) for g, w in zip(got, want))),
+                      "steps": args.steps,
+                      "compared": "kind, age and energy of all %d cells after the timed steps, against the "
+                                  "oracle's run of the same steps" % (W_SIDE * W_SIDE)}
     if rank == 0 and not args.no_e2e:
         e2e = run_e2e(args, seed, hb)
     sim.close()
+    secondary = {}
+    if rank == 0 and ws == 1 and not args.no_secondary:
+        secondary["batched_speedup_vs_per_instance"] = secondary_batched(args)
+        secondary["adjoint_over_forward"] = secondary_adjoint(args)
 
     if rank == 0:
         line = {
@@ -373,12 +387,103 @@ def run_gpu(args, ws, rank, local):
             "phase_ms_per_step": {PHASES[p]: {"enumerate": phase_ms[2 * p] / args.steps,
                                               "method": phase_ms[2 * p + 1] / args.steps}
                                   for p in range(4, 8)},
+            "parity_bit_exact": parity,
         }
+        line.update(secondary)
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def secondary_batched(args, n_inst: int = 64, steps: int = 10, warm: int = 3):
+    """Batched heap against one launch sequence per instance, on the first
+    n_inst instances of the batched recipe (sides 64..1021, log-uniform),
+    default heap configuration: device ms per step of one captured graph
+    over all instances, and of every instance stepped on a heap of its
+    own (same instance numbers, so both simulate the same thing)."""
+    import torch
+    from paper_1908_05845_gb300 import inputs
+    from paper_1908_05845_gb300.workloads import World, heap_bytes_for
+    kinds, sides, init = inputs.batched_initial(SEED, n_inst)
+    offs = np.concatenate([[0], np.cumsum(sides.astype(np.int64) ** 2)])
+    total = int(offs[-1])
+    stream = torch.cuda.Stream()
+    clocks = ClockSampler(torch.cuda.current_device())
+    with torch.cuda.stream(stream):
+        w = World(kinds, sides, sides, SEED, *init, heap_bytes=heap_bytes_for(total), stream=stream)
+        w.step(warm)
+        w.capture(1)
+        e0 = w.heap.counters()[0]
+        a, b = _events(stream)
+        torch.cuda.synchronize()
+        clocks.start()
+        a.record(stream)
+        for _ in range(steps):
+            w.replay()
+        b.record(stream)
+        b.synchronize()
+        t_b = a.elapsed_time(b)
+        objs_b = w.heap.counters()[0] - e0
+        w.sync()
+        w.close()
+        worlds = [World([kinds[i]], [sides[i]], [sides[i]], SEED, *(x[offs[i]:offs[i + 1]] for x in init),
+                        heap_bytes=heap_bytes_for(int(sides[i]) ** 2), stream=stream, inst_ids=[i])
+                  for i in range(n_inst)]
+        for x in worlds:
+            x.step(warm)
+        e0 = sum(x.heap.counters()[0] for x in worlds)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(steps):
+            for x in worlds:
+                x.step(1)
+        b.record(stream)
+        b.synchronize()
+        t_p = a.elapsed_time(b)
+        clk = clocks.stop()
+        objs_p = sum(x.heap.counters()[0] for x in worlds) - e0
+        for x in worlds:
+            x.close()
+    return {"value": (objs_b / t_b) / (objs_p / t_p), "instances": n_inst, "cells": total, "steps": steps,
+            "batched_ms_per_step": t_b / steps, "per_instance_ms_per_step": t_p / steps,
+            "batched_object_updates_per_s": objs_b / t_b * 1e3,
+            "per_instance_object_updates_per_s": objs_p / t_p * 1e3,
+            "objects_equal": bool(objs_b == objs_p), "config": "default heap configuration (not tuned)",
+            "clocks": clk}
+
+
+def secondary_adjoint(args, n: int = 65536, steps: int = 50, ckpt: int = 10):
+    """Cost of the n-body adjoint against its forward run (no merging,
+    65,536 bodies, 50 steps, checkpoints every 10): device time of the
+    checkpointed forward and of the reverse sweep (which recomputes each
+    segment), per step."""
+    import torch
+    from paper_1908_05845_gb300 import inputs
+    from paper_1908_05845_gb300.nbody import NBody
+    st = inputs.nbody_initial(n, SEED)
+    stream = torch.cuda.Stream()
+    clocks = ClockSampler(torch.cuda.current_device())
+    with torch.cuda.stream(stream):
+        w = NBody(st, merge=False, stream=stream)
+        a, b = _events(stream)
+        torch.cuda.synchronize()
+        clocks.start()
+        a.record(stream)
+        w.forward_ckpt(steps, ckpt)
+        b.record(stream)
+        b.synchronize()
+        t_f = a.elapsed_time(b)
+        a.record(stream)
+        w.backward()
+        b.record(stream)
+        b.synchronize()
+        t_b = a.elapsed_time(b)
+        clk = clocks.stop()
+        w.close()
+    return {"value": t_b / t_f, "bodies": n, "steps": steps, "checkpoint_every": ckpt,
+            "forward_ms_per_step": t_f / steps, "backward_ms_per_step": t_b / steps, "clocks": clk}
 
 
 def run_e2e(args, seed, hb):
@@ -678,6 +783,21 @@ def run_bh(args):
         chk.step(10)
         got, _ = chk.read()
         chk.close()
+    # independent repetitions of the timed run: the device error word of
+    # each (a bounded wait that gave up records its site in the detail)
+    repeats = []
+    for r in range(args.bh_repeat):
+        with torch.cuda.stream(stream):
+            code, detail = 0, 0
+            try:
+                rs = BarnesHut(st, stream=stream, **P)
+                rs.step(args.warmup + args.steps)
+                code, detail = rs.heap.sync(raise_on_error=False)
+            except Exception as ex:  # a step that reported an error
+                code, detail = rs.heap.sync(raise_on_error=False)
+                code = code or getattr(ex, "status", -99)
+            rs.close()
+        repeats.append({"run": r, "status": int(code), "detail": hex(int(detail))})
     t0 = time.time()
     want, _ = oracle.bh_run(st, 10, **P)
     cpu_s = time.time() - t0
@@ -691,6 +811,8 @@ def run_bh(args):
                       "tree_node_deletes_per_step": (f1 - f0) / args.steps,
                       "tree_levels_per_step": (l1 - l0) / args.steps, "tree_nodes_end": nodes,
                       "parity_10_steps_bit_exact": bool(exact),
+                      "repeated_runs": {"runs": len(repeats), "steps_each": args.warmup + args.steps,
+                                        "errors": [x for x in repeats if x["status"]]},
                       "cpu_baseline": {"value": N * 10 / cpu_s, "unit": "body-steps/s", "cores": 1,
                                        "kind": "oracle", "host": host_info(), "sample": "10 steps (%.1f s)" % cpu_s}}), flush=True)
     return 0 if exact else 1
@@ -1098,23 +1220,53 @@ def run_alloc(args):
     """Raw allocation throughput (the thesis' Linux-scalability experiment,
     Sec. 5.6.4): 16,384 threads each allocate n objects of a 64-byte class
     inside one do-all, then every object deletes itself in a second do-all.
-    Reported: allocations/s and frees/s for each n, heap size chosen so the
-    largest n fills it."""
+    One heap serves every n; its block count is the smallest that holds the
+    spawners plus 16,384 x n_max objects in full blocks (heap sized for 100 %
+    at n_max = 1024: 1 GiB of object data).  Reported per n: allocations/s
+    and frees/s (best of --reps), objects created, and the heap utilisation
+    they reach (bytes of live objects over the bytes of the blocks the
+    objects may use); at n_max, allocations that find no room leave the
+    device error SMMO_E_DEVICE_OOM, and the utilisation says how far the
+    allocator got."""
     import torch
     from paper_1908_05845_gb300 import smmo
     threads = 16384
-    rows = []
-    for n in [int(x) for x in args.alloc_n.split(",")]:
-        nbytes = int(threads * n * 64 * 1.3) + (64 << 20)
-        # blocks sized for 64 objects of the 64-byte class (the spawning
-        # class is smaller and would otherwise set the block size, Sec. 5.2.2)
-        h = smmo.Heap(nbytes, smmo.default_config(block_data_bytes=64 * 64))
+    ns = [int(x) for x in args.alloc_n.split(",")]
+    n_max = max(ns)
+    cfg = smmo.default_config(block_data_bytes=64 * 64)  # 64 objects of 64 bytes per block
+
+    def make(nbytes):
+        h = smmo.Heap(nbytes, cfg)
         D = h.register("Spawner", [("v", smmo.I32)])
         O = h.register("Obj", [("w", smmo.I32, 16)])
-        h.bulk_new(D, threads, [torch.arange(threads, dtype=torch.int32, device="cuda")])
-        a, b = _events(None)
-        st = torch.cuda.current_stream()
+        h.freeze()
+        return h, D, O
+
+    # smallest buffer whose block count holds the spawners and n_max objects per thread
+    spawner_blocks = -(-threads // 64)
+    want = spawner_blocks + threads * n_max // 64
+    lo, hi = want * 4096, want * 4400 + (64 << 20)
+    while hi - lo > 4096:
+        mid = (lo + hi) // 2 // 256 * 256
+        h, _, _ = make(mid)
+        m = h.stats()["num_blocks"]
+        h.close()
+        del h
+        if m >= want:
+            hi = mid
+        else:
+            lo = mid
+    h, D, O = make(hi)
+    M = h.stats()["num_blocks"]
+    h.bulk_new(D, threads, [torch.arange(threads, dtype=torch.int32, device="cuda")])
+    obj_capacity = (M - spawner_blocks) * 64
+    a, b = _events(None)
+    st = torch.cuda.current_stream()
+    rows = []
+    for n in ns:
         best_a = best_f = None
+        live = 0
+        oom = False
         for rep in range(args.reps):
             torch.cuda.synchronize()
             a.record(st)
@@ -1122,20 +1274,31 @@ def run_alloc(args):
             b.record(st)
             b.synchronize()
             ta = a.elapsed_time(b) / 1e3
+            code, _ = h.sync(raise_on_error=False)
+            oom = oom or code == -3  # SMMO_E_DEVICE_OOM
+            live = h.stats()["live_objects"][O]
             a.record(st)
             h.parallel_do(O, "test.free_self_if", smmo.FreeSelfIfArgs(0, 0, 0))
             b.record(st)
             b.synchronize()
             tf = a.elapsed_time(b) / 1e3
+            h.sync()
             best_a = ta if best_a is None else min(best_a, ta)
             best_f = tf if best_f is None else min(best_f, tf)
-        h.sync()
         stt = h.stats()
-        rows.append({"n": n, "allocs_per_s": threads * n / best_a, "frees_per_s": threads * n / best_f,
-                     "alloc_ms": 1e3 * best_a, "free_ms": 1e3 * best_f, "live_after": stt["live_objects"][O],
-                     "free_blocks_after": stt["free_blocks"], "num_blocks": stt["num_blocks"]})
-        h.close()
-    print(json.dumps({"metric": "allocations/s", "workload": "alloc_16384_threads_64B", "rows": rows}), flush=True)
+        rows.append({"n": n, "allocs_per_s": live / best_a, "frees_per_s": live / best_f,
+                     "alloc_plus_free_per_s": 2 * live / (best_a + best_f),
+                     "alloc_ms": 1e3 * best_a, "free_ms": 1e3 * best_f, "objects": live,
+                     "requested": threads * n, "utilisation": live / obj_capacity, "device_oom": oom,
+                     "live_after_free": stt["live_objects"][O], "free_blocks_after": stt["free_blocks"]})
+    h.close()
+    print(json.dumps({"metric": "allocations/s", "workload": "alloc_16384_threads_64B",
+                      "heap": {"num_blocks": M, "object_blocks": M - spawner_blocks,
+                               "object_bytes": obj_capacity * 64,
+                               "sized_for": "100 %% at n = %d" % n_max},
+                      "thesis_context": "Sec. 5.6.4 (TITAN Xp, 1 GiB heap): utilisation DynaSOAr 96.9 %, "
+                                        "BitmapAlloc 98.4 %, Halloc and mallocMC at most 49.8 %",
+                      "rows": rows}), flush=True)
     return 0
 
 
@@ -1201,6 +1364,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the batched-vs-per-instance and adjoint-over-forward measurements")
     ap.add_argument("--workload", default="wator",
                     choices=["wator", "batched", "gol", "generation", "nasch", "nbody", "bh", "bfs", "alloc",
                              "compact", "structure", "wator_compact", "nbody_compact"])
@@ -1209,9 +1374,11 @@ def main():
     ap.add_argument("--struct-cols", type=int, default=8192)
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--bh-bodies", type=int, default=65536)
+    ap.add_argument("--bh-repeat", type=int, default=0,
+                    help="extra independent Barnes-Hut runs whose device error words are reported")
     ap.add_argument("--gen-steps", type=int, default=500)
     ap.add_argument("--compact-objects", type=int, default=32_768_000)
-    ap.add_argument("--alloc-n", default="1,4,16,64,256")
+    ap.add_argument("--alloc-n", default="1,4,16,64,256,1024")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--retune", action="store_true")

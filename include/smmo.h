@@ -362,7 +362,14 @@ int smmo_heap_last_device_error(smmo_heap* heap, int* code, uint64_t* detail, vo
 
 /* Synchronises `stream` and returns the first device error recorded since
  * the last sync (then clears it).  *detail (host, nullable) receives the
- * error's detail word (e.g. the offending handle).  Device retry loops are
+ * error's detail word (e.g. the offending handle).  For SMMO_E_CONTENTION,
+ * bits 48..55 name the loop that gave up: 1 propagation of a hierarchical
+ * bitmap bit (bits 32..47 the bitmap, 0..31 the position), 2 / 3 a blocking
+ * bitmap set / clear (same fields), 4 the block-state updates of a
+ * deallocation (bits 32..47 the pending active, allocated, free and
+ * candidate changes, 4 bits each, two's complement; bits 0..31 the block),
+ * 5 the warp allocation cache's lock, 6 the rounds of a device new (bits
+ * 0..31 the class); 0 a workload's own site (see its section).  Device retry loops are
  * bounded and record SMMO_E_CONTENTION / SMMO_E_DEVICE_OOM here where the
  * thesis' allocation retries without bound (Alg. 5.1). */
 int smmo_heap_sync(smmo_heap* heap, void* stream, uint64_t* detail);
@@ -483,7 +490,10 @@ int smmo_world_step_profiled(smmo_world* w, int nsteps, double* phase_ms,
  *     is held by every GPU that loads the library until the process exits.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept for the life of the
+ *     process: after a cudaDeviceReset of that device (which ends the
+ *     context the array lives in) this entry point must not be called
+ *     again.
  *   - Every call uses the same array and clears it at its start.  Calls
  *     whose work overlaps on the GPU (other streams, other host threads on
  *     the same device) race on it and must be serialised by the caller. */

@@ -142,6 +142,10 @@ __device__ __forceinline__ unsigned long long ld_cg(const unsigned long long* p)
   return __ldcg(p);
 }
 
+// Site of a SMMO_E_CONTENTION, in bits 48..55 of its detail word.
+constexpr unsigned long long kSitePropagate = 1ull << 48, kSiteSet = 2ull << 48, kSiteClear = 3ull << 48,
+                             kSiteDealloc = 4ull << 48, kSiteCacheLock = 5ull << 48, kSiteRounds = 6ull << 48;
+
 __device__ __forceinline__ void set_error(const HeapView& h, int code,
                                           unsigned long long detail) {
   if (atomicCAS(&h.st->err, 0, code) == 0) h.st->err_detail = detail;
@@ -202,7 +206,7 @@ static __device__ __forceinline__ void bm_propagate(const HeapView& h, int k, in
       if (set ? !(prev & m) : (prev & m)) { done = true; break; }
       __nanosleep(32);
     }
-    if (!done) { set_error(h, SMMO_E_CONTENTION, ((unsigned long long)k << 32) | pos); return; }
+    if (!done) { set_error(h, SMMO_E_CONTENTION, kSitePropagate | ((unsigned long long)k << 32) | pos); return; }
     // continue only on set-first / clear-last of this container
     const unsigned long long cm = bm_cmask(h, pos);
     if (set ? ((prev & cm) != 0) : ((prev & cm) != m)) return;
@@ -236,7 +240,7 @@ __device__ __forceinline__ void bm_set(const HeapView& h, int k, uint32_t pos) {
     if (bm_try_set(h, k, pos)) return;
     __nanosleep(32);
   }
-  set_error(h, SMMO_E_CONTENTION, ((unsigned long long)k << 32) | pos);
+  set_error(h, SMMO_E_CONTENTION, kSiteSet | ((unsigned long long)k << 32) | pos);
 }
 
 __device__ __forceinline__ void bm_clear(const HeapView& h, int k, uint32_t pos) {
@@ -244,7 +248,7 @@ __device__ __forceinline__ void bm_clear(const HeapView& h, int k, uint32_t pos)
     if (bm_try_clear(h, k, pos)) return;
     __nanosleep(32);
   }
-  set_error(h, SMMO_E_CONTENTION, ((unsigned long long)k << 32) | pos);
+  set_error(h, SMMO_E_CONTENTION, kSiteClear | ((unsigned long long)k << 32) | pos);
 }
 
 __device__ __forceinline__ bool bm_get(const HeapView& h, int k, uint32_t pos) {
@@ -368,7 +372,9 @@ static __device__ __forceinline__ void dealloc_bits(const HeapView& h, uint32_t 
     if (fre > 0 && act == 0 && alc == 0 && dfr == 0 && bm_try_set(h, bm_free(), bid)) --fre;
     if (act | alc | fre | dfr) __nanosleep(32);
   }
-  if (act | alc | fre | dfr) set_error(h, SMMO_E_CONTENTION, bid);
+  if (act | alc | fre | dfr)  // pending block-state changes left: act, alc, fre, dfr in bits 32..47
+    set_error(h, SMMO_E_CONTENTION, kSiteDealloc | ((unsigned long long)((act & 15) | (alc & 15) << 4 |
+                                                                          (fre & 15) << 8 | (dfr & 15) << 12) << 32) | bid);
 }
 
 // destroy(ptr) for a single object (Alg. 5.2 / 5.12).
@@ -544,7 +550,7 @@ __device__ __forceinline__ unsigned long long cache_take(const HeapView& h, uint
   WarpAllocCache& wc = g_wcache[threadIdx.x >> 5];
   int spins = 0;
   while (atomicCAS(&wc.lock, 0, 1) != 0) {
-    if (++spins > h.bitmap_spins) { set_error(h, SMMO_E_CONTENTION, c); *bid = 0; return 0; }
+    if (++spins > h.bitmap_spins) { set_error(h, SMMO_E_CONTENTION, kSiteCacheLock | c); *bid = 0; return 0; }
     __nanosleep(8);
   }
   __threadfence_block();
@@ -610,7 +616,7 @@ __device__ __forceinline__ uint32_t smmo_new(const HeapView& h, uint32_t c) {
       if (slot >= 0) result = (bid << 6) | (uint32_t)slot;
     }
   }
-  if (round == h.alloc_retries && result == kNull) set_error(h, SMMO_E_CONTENTION, c);
+  if (round == h.alloc_retries && result == kNull) set_error(h, SMMO_E_CONTENTION, kSiteRounds | c);
   return result;
 }
 
