@@ -1180,35 +1180,40 @@ def run_nbody(args):
         w.close()
     # ALU roofline of the force pass (no-merge forward with checkpoints,
     # which is the force kernel plus an O(N) drift): 19 FP32 operations per
-    # pair (3 sub, 7 mul, 7 add, 1 sqrt, 1 div, each counted once; the
-    # fixed evaluation order forbids contraction into FMA) against one FP32
-    # operation per lane per clock: SMs x 128 lanes x max SM clock
+    # pair (3 sub, 3 fused multiply-adds for |r|^2 + eps^2, 1 mul, 1 sqrt,
+    # 1 div, 1 mul for the weight, 3 fused multiply-adds for the sum; a
+    # fused multiply-add counts as two) against the measured fused
+    # multiply-add rate of this GPU (two operations per lane and clock)
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     mhz = (load_peaks() or {}).get("sm_max_mhz", 2070.0)
-    derived_tops = props.multi_processor_count * 128 * mhz * 1e6 / 1e12
-    # the measured FP32 add/multiply rate of this GPU (library microbenchmark)
+    derived_tflops = props.multi_processor_count * 128 * 2 * mhz * 1e6 / 1e12
+    fma = ctypes.c_double()
+    smmo.check(smmo.lib().smmo_measure_fma_peak(8192, ctypes.byref(fma), smmo._stream(None)), "fma_peak")
+    peak_tflops = fma.value / 1e12
     ops = ctypes.c_double()
     smmo.check(smmo.lib().smmo_measure_fp32_peak(8192, ctypes.byref(ops), smmo._stream(None)), "fp32_peak")
-    peak_tops = ops.value / 1e12
     mufu = ctypes.c_double()
     smmo.check(smmo.lib().smmo_measure_mufu_peak(4096, ctypes.byref(mufu), smmo._stream(None)), "mufu_peak")
     fwd_pairs_per_s = float(N) * N * 50 / t_f
-    ach_tops = fwd_pairs_per_s * 19 / 1e12
+    ach_tflops = fwd_pairs_per_s * 19 / 1e12
     print(json.dumps({"metric": "pair-interactions/s", "value": pairs / t, "unit": "pairs/s",
                       "ms_per_step": 1e3 * t / args.steps, "steps": args.steps, "merges": merges,
                       "live_after": live, "adjoint_backward_over_forward": t_b / t_f,
                       "forward_ckpt_ms_per_step": 1e3 * t_f / 50, "backward_ms_per_step": 1e3 * t_b / 50,
                       "dtype": "f32",
-                      "roofline": {"bound": "alu", "achieved": ach_tops, "peak": peak_tops, "unit": "TFLOP/s",
-                                   "frac": ach_tops / peak_tops, "traffic": None, "kernel": "k_force",
-                                   "peak_source": "measured: FP32 multiply-then-add chains on every SM "
-                                                  "(smmo_measure_fp32_peak)",
-                                   "peak_derived": derived_tops,
+                      "roofline": {"bound": "alu", "achieved": ach_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                                   "frac": ach_tflops / peak_tflops, "traffic": None, "kernel": "k_force",
+                                   "flops_per_pair": 19,
+                                   "peak_source": "measured: FP32 fused multiply-add chains on every SM "
+                                                  "(smmo_measure_fma_peak, two operations each)",
+                                   "peak_derived": derived_tflops,
+                                   # the FP32 instruction rate (one multiply or add per lane and clock)
+                                   "fp32_instr_peak_per_s": ops.value,
                                    # the two hardware approximations per pair against the
                                    # special-function pipe's measured rate
                                    "mufu_peak_per_s": mufu.value,
                                    "mufu_frac": fwd_pairs_per_s * 2 / mufu.value if mufu.value else None,
-                                   "peak_derived_source": "%d SMs x 128 FP32 lanes x %.0f MHz"
+                                   "peak_derived_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz"
                                                           % (props.multi_processor_count, mhz)},
                       "config": {"workload": "nbody_65536_merge",
                                  "note": "force O(N^2), merge search on a uniform grid"}}),

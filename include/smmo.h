@@ -572,7 +572,9 @@ int smmo_traffic_destroy(smmo_traffic* w);
  * class Body {x, y, z, vx, vy, vz, m, id, lx, ly, lz, lvx, lvy, lvz}
  * (the last six: adjoint state).  A step is drift-kick-drift: x += v dt/2,
  * a = G sum_j m_j r_ij / (|r_ij|^2 + eps^2)^{3/2} summed over body ids in
- * increasing order with a fixed FP32 evaluation order and IEEE division and
+ * increasing order with a fixed FP32 evaluation order (|r|^2 + eps^2 and the
+ * sum as fused multiply-adds: s2 = fma(dz, dz, fma(dy, dy, fma(dx, dx,
+ * eps^2))), a = fma(m_j / (s2 sqrt(s2)), r, a)) and IEEE division and
  * square root, v += a dt, x += v dt/2; then, if merge != 0, a receiver takes
  * the first lighter body ((m, id) lexicographic) within merge_r in id order,
  * a body picked by several receivers goes to the lowest receiver id, and it
@@ -740,13 +742,17 @@ int smmo_structure_export(smmo_structure* w, const smmo_structure_out* out, void
 int smmo_structure_info(smmo_structure* w, int* class_ids, int64_t* counters, void* stream);
 int smmo_structure_destroy(smmo_structure* w);
 
-/* FP32 add/multiply throughput of this GPU (the peak of the n-body
- * force's roofline, whose fixed evaluation order uses no FMA): every SM
- * full of threads running eight independent multiply-then-add chains for
- * `iters` (1..2^20) iterations, timed with CUDA events.  *ops_per_s (host)
- * = FP32 operations (one per multiply, one per add) per second.
- * Synchronises `stream`. */
+/* FP32 add/multiply throughput of this GPU: every SM full of threads
+ * running eight independent multiply-then-add chains (separate
+ * instructions) for `iters` (1..2^20) iterations, timed with CUDA events.
+ * *ops_per_s (host) = FP32 operations (one per multiply, one per add) per
+ * second, i.e. FP32 instructions per second.  Synchronises `stream`. */
 int smmo_measure_fp32_peak(int iters, double* ops_per_s, void* stream);
+/* The same with fused multiply-add chains (the peak of the n-body force's
+ * roofline, whose fixed evaluation order uses fused multiply-adds):
+ * *flops_per_s (host) = floating-point operations per second, two per
+ * fused multiply-add.  Synchronises `stream`. */
+int smmo_measure_fma_peak(int iters, double* flops_per_s, void* stream);
 /* Special-function (reciprocal square root) throughput, measured the same
  * way with eight independent chains of the hardware approximation per
  * thread: *ops_per_s (host) = approximations per second.  The force kernel

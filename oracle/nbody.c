@@ -20,11 +20,14 @@
  * picked by several receivers goes to the lowest receiver id, and a merge
  * into a body that is itself being merged is skipped (as printed).
  *
- * The FP32 path fixes the evaluation order of every operation and must be
- * compiled with -ffp-contract=off (no fused multiply-add):
- *   dx = xj - xi (same for y, z); s2 = ((dx*dx + dy*dy) + dz*dz) + eps*eps;
- *   inv = 1 / (s2 * sqrt(s2)); f = mj * inv; a += f * d (per component);
- *   a = G * a.
+ * The FP32 path fixes the evaluation order of every operation, with the
+ * fused multiply-adds written out (fmaf, one rounding each) and every other
+ * product and sum rounded on its own (compiled with -ffp-contract=off, so
+ * the compiler fuses nothing else):
+ *   dx = xj - xi (same for y, z);
+ *   s2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps*eps)));
+ *   inv = 1 / (s2 * sqrt(s2)); f = mj * inv;
+ *   a = fmaf(f, d, a) per component, j in increasing id; a = G * a.
  *
  * The adjoint (no-merge variant, loss L = 1/2 sum_i m_i |v_i(T)|^2) is the
  * reverse of one drift-kick-drift step with
@@ -73,15 +76,14 @@ int orc_nbody_accel_f32(int N, float G, float eps, const float* x,
         float dx = x[j] - x[i];
         float dy = y[j] - y[i];
         float dz = z[j] - z[i];
-        float s2 = dx * dx;
-        s2 = s2 + dy * dy;
-        s2 = s2 + dz * dz;
-        s2 = s2 + eps2;
+        float s2 = fmaf(dx, dx, eps2);
+        s2 = fmaf(dy, dy, s2);
+        s2 = fmaf(dz, dz, s2);
         float inv = 1.0f / (s2 * sqrtf(s2));
         float f = m[j] * inv;
-        sx = sx + f * dx;
-        sy = sy + f * dy;
-        sz = sz + f * dz;
+        sx = fmaf(f, dx, sx);
+        sy = fmaf(f, dy, sy);
+        sz = fmaf(f, dz, sz);
       }
     }
     ax[i] = G * sx; ay[i] = G * sy; az[i] = G * sz;
@@ -200,15 +202,14 @@ int orc_nbody_step_sample_f32(int N, float G, float eps, float dt, const float* 
       float dx = x1[j] - x1[i];
       float dy = y1[j] - y1[i];
       float dz = z1[j] - z1[i];
-      float s2 = dx * dx;
-      s2 = s2 + dy * dy;
-      s2 = s2 + dz * dz;
-      s2 = s2 + eps2;
+      float s2 = fmaf(dx, dx, eps2);
+      s2 = fmaf(dy, dy, s2);
+      s2 = fmaf(dz, dz, s2);
       float inv = 1.0f / (s2 * sqrtf(s2));
       float f = m[j] * inv;
-      sx = sx + f * dx;
-      sy = sy + f * dy;
-      sz = sz + f * dz;
+      sx = fmaf(f, dx, sx);
+      sy = fmaf(f, dy, sy);
+      sz = fmaf(f, dz, sz);
     }
     float ax = G * sx, ay = G * sy, az = G * sz;
     float nvx = vx[i] + ax * dt, nvy = vy[i] + ay * dt, nvz = vz[i] + az * dt;

@@ -17,8 +17,8 @@
 // then deletes itself).
 //
 // FP32 arithmetic uses explicit round-to-nearest intrinsics in the order
-//   s2 = ((dx*dx + dy*dy) + dz*dz) + eps^2; inv = 1/(s2*sqrt(s2));
-//   f = m_j*inv; a += f*d;
+//   s2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps^2))); inv = 1/(s2*sqrt(s2));
+//   f = m_j*inv; a = fma(f, d, a);
 // with IEEE division and square root, so results equal a sequential FP32
 // evaluation in the same order bit for bit.  The self pair and freed ids
 // (mass 0 in the staging array) add exactly +0 and need no branch.
@@ -109,55 +109,60 @@ struct Stage {
 // functions equal the IEEE-rounded ones.
 constexpr unsigned kCoordMaxBits = 0x48800000u;  // 2^18
 
-// One pair term m_j inv (x_j - x_i), inv = 1 / (s2 sqrt(s2)), in the fixed
-// evaluation order.
+// One pair's weight f = m_j inv, inv = 1 / (s2 sqrt(s2)), in the fixed
+// evaluation order: s2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps^2))),
+// one rounding per fused multiply-add, every other operation rounded on
+// its own.
 template <bool FAST>
-__device__ __forceinline__ void pair_term(const float4 p, float xi, float yi, float zi, float eps2, float& tx,
-                                          float& ty, float& tz) {
-  const float dx = fs(p.x, xi), dy = fs(p.y, yi), dz = fs(p.z, zi);
-  float s2 = fm(dx, dx);
-  s2 = fa(s2, fm(dy, dy));
-  s2 = fa(s2, fm(dz, dz));
-  s2 = fa(s2, eps2);
+__device__ __forceinline__ float pair_f(float mj, float dx, float dy, float dz, float eps2) {
+  float s2 = __fmaf_rn(dx, dx, eps2);
+  s2 = __fmaf_rn(dy, dy, s2);
+  s2 = __fmaf_rn(dz, dz, s2);
   const float inv = FAST ? rcp_rn_fast(fm(s2, sqrt_rn_fast(s2))) : __fdiv_rn(1.0f, fm(s2, __fsqrt_rn(s2)));
-  const float f = fm(p.w, inv);
-  tx = fm(f, dx);
-  ty = fm(f, dy);
-  tz = fm(f, dz);
+  return fm(mj, inv);
 }
 
-// Terms computed per round before they are added: one body per thread
-// leaves few warps per SM (65,536 threads), so the independent work of a
-// round has to hide the latency of the square-root and reciprocal chains
-// (32 terms: 128 registers, 2 CTAs per SM, 3.8 ms per forward step against
-// 6.2 with a plain unrolled loop).
-constexpr int kForceTerms = 32;
+// Pairs whose weights are computed per round before they are accumulated:
+// one body per thread leaves few warps per SM (65,536 threads), so the
+// independent work of a round has to hide the latency of the square-root
+// and reciprocal chains (each term keeps f and the three differences).
+#ifndef SMMO_NBODY_TERMS
+#define SMMO_NBODY_TERMS 16
+#endif
+constexpr int kForceTerms = SMMO_NBODY_TERMS;
 
 // Sum of the pair terms of one tile into (ax, ay, az), j in increasing
-// order: the terms of kForceTerms consecutive j are computed first (they
-// are independent), then added in order, so the result is that of the plain
-// loop bit for bit.
+// order: the weights of kForceTerms consecutive j are computed first (they
+// are independent), then a = fma(f, d, a) in order, so the result is that
+// of the plain loop bit for bit.
 template <bool FAST>
 __device__ __forceinline__ void force_tile(const float4* tile, uint32_t cnt, float xi, float yi, float zi,
                                            float eps2, float& ax, float& ay, float& az) {
   uint32_t k = 0;
   for (; k + kForceTerms <= cnt; k += kForceTerms) {
-    float tx[kForceTerms], ty[kForceTerms], tz[kForceTerms];
-#pragma unroll
-    for (int u = 0; u < kForceTerms; ++u) pair_term<FAST>(tile[k + u], xi, yi, zi, eps2, tx[u], ty[u], tz[u]);
+    float f[kForceTerms], dx[kForceTerms], dy[kForceTerms], dz[kForceTerms];
 #pragma unroll
     for (int u = 0; u < kForceTerms; ++u) {
-      ax = fa(ax, tx[u]);
-      ay = fa(ay, ty[u]);
-      az = fa(az, tz[u]);
+      const float4 p = tile[k + u];
+      dx[u] = fs(p.x, xi);
+      dy[u] = fs(p.y, yi);
+      dz[u] = fs(p.z, zi);
+      f[u] = pair_f<FAST>(p.w, dx[u], dy[u], dz[u], eps2);
+    }
+#pragma unroll
+    for (int u = 0; u < kForceTerms; ++u) {
+      ax = __fmaf_rn(f[u], dx[u], ax);
+      ay = __fmaf_rn(f[u], dy[u], ay);
+      az = __fmaf_rn(f[u], dz[u], az);
     }
   }
   for (; k < cnt; ++k) {
-    float tx, ty, tz;
-    pair_term<FAST>(tile[k], xi, yi, zi, eps2, tx, ty, tz);
-    ax = fa(ax, tx);
-    ay = fa(ay, ty);
-    az = fa(az, tz);
+    const float4 p = tile[k];
+    const float dx = fs(p.x, xi), dy = fs(p.y, yi), dz = fs(p.z, zi);
+    const float f = pair_f<FAST>(p.w, dx, dy, dz, eps2);
+    ax = __fmaf_rn(f, dx, ax);
+    ay = __fmaf_rn(f, dy, ay);
+    az = __fmaf_rn(f, dz, az);
   }
 }
 
@@ -917,6 +922,22 @@ __global__ void __launch_bounds__(256) k_fp32_peak(float* out, int iters) {
   for (int k = 0; k < 8; ++k) s += x[k];
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
+// FP32 fused multiply-add throughput: the same chains as one fused
+// multiply-add each (two floating-point operations per instruction).
+__global__ void __launch_bounds__(256) k_fma_peak(float* out, int iters) {
+  float x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = 1.0f + (float)(threadIdx.x + k) * 1e-3f;
+  const float m = 0.999999f, c = 1e-6f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = __fmaf_rn(x[k], m, c);
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
 // Special-function throughput: eight independent chains per thread of the
 // hardware reciprocal square root (x -> rsqrt(x) stays near 1).
 __global__ void __launch_bounds__(256) k_mufu_peak(float* out, int iters) {
@@ -1001,6 +1022,11 @@ int smmo_selftest_fp32_rn(uint32_t lo_bits, uint32_t hi_bits, uint64_t* out4, vo
 int smmo_measure_fp32_peak(int iters, double* ops_per_s, void* stream) {
   if (!ops_per_s || iters < 1 || iters > (1 << 20)) return SMMO_E_INVALID_ARG;
   return time_peak(k_fp32_peak, iters, 16.0, ops_per_s, (cudaStream_t)stream);
+}
+
+int smmo_measure_fma_peak(int iters, double* flops_per_s, void* stream) {
+  if (!flops_per_s || iters < 1 || iters > (1 << 20)) return SMMO_E_INVALID_ARG;
+  return time_peak(k_fma_peak, iters, 16.0, flops_per_s, (cudaStream_t)stream);  // 8 chains x 2 flops
 }
 
 int smmo_measure_mufu_peak(int iters, double* ops_per_s, void* stream) {

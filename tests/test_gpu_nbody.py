@@ -156,6 +156,19 @@ def test_measured_fp32_peak_is_near_the_unit_count():
     assert 0.5 * nominal < ops.value < 1.05 * nominal, (ops.value, nominal)
 
 
+def test_measured_fma_peak_is_near_twice_the_unit_count():
+    """The fused multiply-add microbenchmark behind the force kernel's
+    roofline (two operations per fused multiply-add) measures between half
+    and all of SMs x 128 lanes x 2 x the maximum SM clock."""
+    import ctypes
+    from paper_1908_05845_gb300 import smmo
+    flops = ctypes.c_double()
+    assert smmo.lib().smmo_measure_fma_peak(4096, ctypes.byref(flops), None) == 0
+    props = torch.cuda.get_device_properties(0)
+    nominal = props.multi_processor_count * 128 * 2 * 2.07e9
+    assert 0.5 * nominal < flops.value < 1.05 * nominal, (flops.value, nominal)
+
+
 def test_measured_special_function_peak_is_below_the_fp32_rate():
     """The special-function pipe (one reciprocal square root per lane and
     instruction) is a fraction of the FP32 rate: between 1 T/s and half of

@@ -75,7 +75,7 @@ MUTANTS = [
     ('C12', 'nasch_ctrl', 'nasch_ctrl.c', 'if (kind < 0 || n < 2) continue;', 'if (kind < 0 || n < 1) continue;'),  # single-incoming street controlled
     ('C13', 'nasch_ctrl', 'nasch_ctrl.c', 'const int o = route_of(g, seed, t, s);\n      if (o < 0) continue;', 'const int o = route_of(g, seed, t + 1, s);\n      if (o < 0) continue;'),  # controller reads next step route
     ('B1', 'nbody', 'nbody.c', '        float dx = x[j] - x[i];', '        float dx = x[i] - x[j];'),  # force sign x
-    ('B2', 'nbody', 'nbody.c', '        s2 = s2 + eps2;\n        float inv', '        float inv'),  # no softening f32
+    ('B2', 'nbody', 'nbody.c', '        float s2 = fmaf(dx, dx, eps2);', '        float s2 = dx * dx;'),  # no softening f32
     ('B3', 'nbody', 'nbody.c', '      z[i] = z[i] + vz[i] * h;\n    }\n    int64_t merges', '    }\n    int64_t merges'),  # z second drift dropped
     ('B4', 'nbody', 'nbody.c', 'return ma < mb || (ma == mb && ia < ib);', 'return ma < mb || (ma == mb && ia > ib);'),  # tie order
     ('B5', 'nbody', 'nbody.c', 'y[t] = (y[j] + y[t]) / 2.0f;', 'y[t] = y[t];'),  # merge y position
