@@ -48,13 +48,21 @@ BYTES_PER_OBJECT = {
     "shark_prepare": 4 + 4 + 4 + 4 + 4 * 4 + 4 * 4 + 16,  # cell, age, energy r/w, target, occ, types, req
     "shark_update": 4 + 2 + 4 + 8 + 4 + 4 + 4 + 2 + 4,
 }
+# a species' prepare and update fused into one launch (the phased Wa-Tor
+# step kernels) move the bytes of both
+BYTES_PER_OBJECT["fish_step"] = BYTES_PER_OBJECT["fish_prepare"] + BYTES_PER_OBJECT["fish_update"]
+BYTES_PER_OBJECT["shark_step"] = BYTES_PER_OBJECT["shark_prepare"] + BYTES_PER_OBJECT["shark_update"]
 PHASES = ["life_cand_prepare", "life_alive_prepare", "life_cand_update", "life_alive_update",
           "fish_prepare", "fish_update", "shark_prepare", "shark_update"]
+# phase names when each species runs as one fused launch (phases 5 and 7 empty)
+PHASES_FUSED = PHASES[:4] + ["fish_step", "", "shark_step", ""]
+STEP_KERNELS = {"four_do_alls": 0, "phased1": 1, "phased2": 2, "four_do_alls_queued": 4, "phased2_queued": 6}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "wator_2048_fish_update_traffic.txt")  # JSON
 # Sources of the Wa-Tor do-all kernels: the allocator and do-all core, the
 # cellular helpers, and the Wa-Tor section of world.cu (between its Wa-Tor
 # and Life banners), so that changes elsewhere keep a traffic capture valid.
-KERNEL_SOURCES = ["paper_1908_05845_gb300/csrc/smmo_core.cuh", "paper_1908_05845_gb300/csrc/grid_common.cuh"]
+KERNEL_SOURCES = ["paper_1908_05845_gb300/csrc/smmo_core.cuh", "paper_1908_05845_gb300/csrc/grid_common.cuh",
+                  "paper_1908_05845_gb300/csrc/phased.cuh", "paper_1908_05845_gb300/csrc/levels.cuh"]
 WATOR_SECTION = ("paper_1908_05845_gb300/csrc/world.cu",
                  "// ================================================================ Wa-Tor",
                  "// ================================================================ Life")
@@ -251,13 +259,15 @@ def run_gpu(args, ws, rank, local):
     hb = heap_bytes_for(W_SIDE * W_SIDE, 1.0)
     stream = torch.cuda.current_stream()
     # warm-up on its own world (same seed)
-    warm = WaTor(W_SIDE, W_SIDE, seed, k0, a0, e0, heap_bytes=hb)
+    mode = STEP_KERNELS[args.step_kernels]
+    fused = (mode & 3) != 0
+    warm = WaTor(W_SIDE, W_SIDE, seed, k0, a0, e0, heap_bytes=hb, step_kernels=mode)
     if args.warmup:
         warm.step_profiled(args.warmup)
     warm.sync()
     warm.close()
     del warm
-    sim = WaTor(W_SIDE, W_SIDE, seed, k0, a0, e0, heap_bytes=hb)
+    sim = WaTor(W_SIDE, W_SIDE, seed, k0, a0, e0, heap_bytes=hb, step_kernels=mode)
     fish_cls, shark_cls = sim.class_ids["Fish"], sim.class_ids["Shark"]
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     phase_ms = np.zeros(16)
@@ -304,9 +314,10 @@ def run_gpu(args, ws, rank, local):
     value = objects_all / t_max
 
     # roofline of the dominant kernel
+    names = PHASES_FUSED if fused else PHASES
     meth = phase_ms[1::2]
     dom = int(np.argmax(meth))
-    name = PHASES[dom]
+    name = names[dom]
     peaks = load_peaks()
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     bytes_dom = BYTES_PER_OBJECT.get(name, 0) * objs_phase[dom]
@@ -332,7 +343,7 @@ def run_gpu(args, ws, rank, local):
     # the whole step: every do-all's objects x its bytes per object, a
     # 16-byte bitmap read-modify-write per device new or delete, and 24
     # bytes (bitmap word read, entry written) per enumerated block
-    step_bytes = (sum(BYTES_PER_OBJECT.get(PHASES[p], 0) * objs_phase[p] for p in range(8))
+    step_bytes = (sum(BYTES_PER_OBJECT.get(names[p], 0) * objs_phase[p] for p in range(8))
                   + 16 * allocfree + 24 * (blocks1 - blocks0))
     step_achieved = step_bytes / t_local / 1e9
     step_roofline = {"bound": "hbm", "achieved": step_achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -359,6 +370,9 @@ def run_gpu(args, ws, rank, local):
     if rank == 0 and not args.no_e2e:
         e2e = run_e2e(args, seed, hb)
     sim.close()
+    compared = None
+    if rank == 0 and ws == 1 and not args.no_secondary:
+        compared = compare_step_kernels(args, seed, hb, (k0, a0, e0), flush)
     secondary = {}
     if rank == 0 and ws == 1 and not args.no_secondary:
         secondary["batched_speedup_vs_per_instance"] = secondary_batched(args)
@@ -384,9 +398,11 @@ def run_gpu(args, ws, rank, local):
             # allocator events per step (warp-cache refills, blocks taken
             # from the free bitmap, reservations that found a full block...)
             "alloc_events_per_step": {k: (ac1[k] - ac0[k]) / args.steps for k in ac1},
-            "phase_ms_per_step": {PHASES[p]: {"enumerate": phase_ms[2 * p] / args.steps,
-                                              "method": phase_ms[2 * p + 1] / args.steps}
-                                  for p in range(4, 8)},
+            "phase_ms_per_step": {names[p]: {"enumerate": phase_ms[2 * p] / args.steps,
+                                             "method": phase_ms[2 * p + 1] / args.steps}
+                                  for p in range(4, 8) if names[p]},
+            "step_kernels": args.step_kernels,
+            "step_kernels_compared": compared,
             "parity_bit_exact": parity,
         }
         line.update(secondary)
@@ -395,6 +411,36 @@ def run_gpu(args, ws, rank, local):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def compare_step_kernels(args, seed, hb, init, flush, steps: int = 20):
+    """ms per step of the same Wa-Tor run (seeded start, L2 flushed before
+    every step, CUDA events around each step) in each step-kernel mode: the
+    four do-alls, each species' prepare and update fused into one launch
+    with one or two units per warp round, and either with the creations
+    queued for a launch of their own."""
+    import torch
+    from paper_1908_05845_gb300.workloads import WaTor
+    out = {}
+    steps = min(steps, args.steps)
+    for name, mode in STEP_KERNELS.items():
+        w = WaTor(W_SIDE, W_SIDE, seed, *init, heap_bytes=hb, step_kernels=mode)
+        total = 0.0
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            flush.zero_()
+            _, sm, _ = w.step_profiled(1)
+            total += sm
+        got = w.read() if seed == SEED else None
+        w.sync()
+        w.close()
+        out[name] = {"ms_per_step": total / steps, "steps": steps}
+        if got is not None:
+            out[name]["state"] = got
+    # the modes must agree cell for cell
+    states = [v.pop("state") for v in out.values() if "state" in v]
+    same = all(all(np.array_equal(a, b) for a, b in zip(states[0], st)) for st in states[1:])
+    return {"modes": out, "identical_results": bool(same) if states else None}
 
 
 def secondary_batched(args, n_inst: int = 64, steps: int = 10, warm: int = 3):
@@ -1378,6 +1424,8 @@ def main():
     ap.add_argument("--struct-iters", type=int, default=100)
     ap.add_argument("--struct-cols", type=int, default=8192)
     ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--step-kernels", default="four_do_alls", choices=sorted(STEP_KERNELS),
+                    help="how a Wa-Tor iteration is launched (smmo_world_set_step_kernels)")
     ap.add_argument("--bh-bodies", type=int, default=65536)
     ap.add_argument("--bh-repeat", type=int, default=0,
                     help="extra independent Barnes-Hut runs whose device error words are reported")

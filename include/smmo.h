@@ -407,7 +407,7 @@ typedef struct {
  * instance i has kind[i], W[i] x H[i] cells starting at the sum of the
  * sizes before it, and draws with instance number i) and creates the
  * instances.  kind/W/H: host arrays of n_inst entries (W, H >= 3; at most
- * 2^30 cells in all).
+ * 2^30 - 2 cells in all).
  * Per-cell initial state: device arrays over
  * the concatenation of all instances' cells in instance order, row-major
  * (cell = y * W + x): init_kind (Life: 0 empty, 1 Alive, 2 Candidate;
@@ -417,7 +417,9 @@ typedef struct {
  * nullable = 0).  params may be NULL.  Life-kind instances start with the
  * Life rule (see smmo_world_set_life_rule).  Synchronises `stream`.  The
  * world allocates its 4-byte step counter with cudaMalloc, freed by
- * smmo_world_destroy. */
+ * smmo_world_destroy (with 1 KiB of grid-barrier words behind it), and,
+ * when there are Wa-Tor instances, a creation queue of 4.125 bytes per cell
+ * plus 132 bytes per warp slot of the GPU (also cudaMalloc). */
 int smmo_world_create(smmo_heap* heap, int n_inst, const int* kind,
                       const uint32_t* W, const uint32_t* H, uint64_t seed,
                       const smmo_wator_params* params, const int8_t* init_kind,
@@ -448,6 +450,25 @@ int smmo_world_step(smmo_world* w, int nsteps, void* stream);
  * Candidate without alive neighbour is deleted), block <= 65535.  Takes
  * effect at the next step; drops a captured graph. */
 int smmo_world_set_life_rule(smmo_world* w, uint32_t survive, uint32_t born, uint32_t block);
+/* How a Wa-Tor iteration (Sec. 7.6: every agent of a species posts its
+ * move request, then every agent reads the requests and moves) is
+ * launched; the results are the same in every mode.
+ *   SMMO_WATOR_FOUR_DO_ALLS (the default): parallel_do(Fish, prepare), parallel_do(Fish,
+ *     update), then the same for Shark: four do-all launches, the request
+ *     word passed through the agent's target field.
+ *   SMMO_WATOR_PHASED1 / SMMO_WATOR_PHASED2: each species'
+ *     prepare and update in one cooperative launch over one snapshot, the
+ *     phases separated by a grid barrier, the request word kept in shared
+ *     memory between them; 1 or 2 units of 32 slots per warp round.
+ *   | SMMO_WATOR_QUEUED_CREATION (with any of the above): the newborns of
+ *     an update are written to a queue (payload and placement hint) instead
+ *     of being allocated inside the update, and one more launch after it
+ *     creates them, a full warp per 32.
+ * Any other value: SMMO_E_INVALID_ARG.  Takes effect at the next step;
+ * drops a captured graph. */
+enum { SMMO_WATOR_FOUR_DO_ALLS = 0, SMMO_WATOR_PHASED1 = 1, SMMO_WATOR_PHASED2 = 2,
+       SMMO_WATOR_QUEUED_CREATION = 4 };
+int smmo_world_set_step_kernels(smmo_world* w, int mode);
 /* Writes the live objects into per-cell device arrays (same indexing as
  * the initial state; kind, age, energy, state as above, age of an Alive =
  * its blocked count; empty cells 0) and
@@ -467,7 +488,9 @@ int smmo_world_replay(smmo_world* w, void* stream);
  * to phase_ms (host, 16 doubles, accumulated): index 2*p is the
  * enumeration and 2*p+1 the method kernel of phase p = Life candidate
  * prepare, alive prepare, candidate update, alive update, fish prepare,
- * fish update, shark prepare, shark update.  step_ms (host, nullable)
+ * fish update, shark prepare, shark update (in the fused modes of
+ * smmo_world_set_step_kernels the fish and shark prepare phases p = 4 and 6
+ * hold the fused launch, and p = 5 and 7 stay 0).  step_ms (host, nullable)
  * accumulates the device time from the first to the last launch of each
  * step; launches (host, nullable) is increased by the number of kernels
  * launched.  Synchronises `stream` once, after the last step. */

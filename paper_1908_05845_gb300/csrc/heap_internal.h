@@ -129,6 +129,24 @@ int launch_do_all(smmo_heap* h, int cls, const void* args, cudaStream_t s) {
 }
 #define SMMO_METHOD(name, M) {name, sizeof(typename M::Args), &launch_do_all<M>, nullptr}
 
+// Creates the objects that do_all<M> (M::kQueued) left in its queue.
+template <class M>
+int launch_create_queued(smmo_heap* h, int, const void* args, cudaStream_t s) {
+  const typename M::Args* a = static_cast<const typename M::Args*>(args);
+  static int occ_threads = 0, occ_blocks = 0;
+  if (occ_threads != h->cfg.threads_per_cta) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, smmo::create_queued_kernel<M>, h->cfg.threads_per_cta, 0) !=
+            cudaSuccess || nb < 1)
+      nb = 1;
+    occ_blocks = nb;
+    occ_threads = h->cfg.threads_per_cta;
+  }
+  const int per_sm = occ_blocks < h->cfg.ctas_per_sm ? occ_blocks : h->cfg.ctas_per_sm;
+  smmo::create_queued_kernel<M><<<h->num_sms * per_sm, h->cfg.threads_per_cta, 0, s>>>(h->view, *a);
+  return smmo::cuda_status(cudaGetLastError());
+}
+
 template <class M, bool POLY = false>
 int launch_do_all_reduce_view(smmo_heap* h, int cls, const void* args, int op, long long* out, cudaStream_t s,
                               const smmo::HeapView* v) {

@@ -508,12 +508,12 @@ struct WarpAllocCache {
   uint32_t hint;
   int lock;
 };
-static __shared__ WarpAllocCache g_wcache[32];
+static __shared__ WarpAllocCache g_wcache[16];  // do-all CTAs have at most 16 warps
 struct WarpNewBcast {  // warp_new: the cache's slots, broadcast by the leader
   unsigned long long bits;
   uint32_t bid;
 };
-static __shared__ WarpNewBcast g_wnew[32];
+static __shared__ WarpNewBcast g_wnew[16];
 
 __device__ __forceinline__ void alloc_cache_init() {
   const uint32_t lane = threadIdx.x & 31;
@@ -771,7 +771,7 @@ __device__ __forceinline__ void defer_new(uint32_t payload) {
 // 32 while 32 or more wait; with all = true also the rest (fewer than 32,
 // with part of the warp).
 template <class M>
-__device__ __forceinline__ void defer_flush(const HeapView& h, const typename M::Args& args, bool all) {
+__device__ __forceinline__ void defer_flush_alloc(const HeapView& h, const typename M::Args& args, bool all) {
   DeferList& d = g_defer[threadIdx.x >> 5];
   const uint32_t lane = threadIdx.x & 31;
   __syncwarp();
@@ -794,6 +794,79 @@ __device__ __forceinline__ void defer_flush(const HeapView& h, const typename M:
   __syncwarp();
 }
 
+// Deferred creation through a queue in global memory (a method with
+// kQueued = true and queue(args)): instead of allocating inside the do-all,
+// the warp writes its deferred payloads in chunks of 32, each with the
+// block it was working on as the placement hint, and a later launch
+// (create_queued_kernel) creates them, one full warp per chunk.  The do-all
+// then carries no allocator code at all.  A chunk's unused tail holds kNull
+// (payloads are never kNull).
+struct DeferQueue {
+  uint32_t* item;   // payloads, chunks of 32
+  uint32_t* hint;   // per chunk: the placement hint
+  uint32_t* count;  // entries written (a multiple of 32); zeroed before the do-all
+  uint32_t cap;     // capacity in entries (a multiple of 32)
+};
+template <class M, class = void>
+struct queued { static constexpr bool value = false; };
+template <class M>
+struct queued<M, decltype((void)M::kQueued)> { static constexpr bool value = M::kQueued; };
+
+template <class M>
+__device__ __forceinline__ void defer_flush_queue(const HeapView& h, const typename M::Args& args, bool all) {
+  DeferList& d = g_defer[threadIdx.x >> 5];
+  const uint32_t lane = threadIdx.x & 31;
+  __syncwarp();
+  const DeferQueue q = M::queue(args);
+  const uint32_t hint = g_wcache[threadIdx.x >> 5].hint;
+  uint32_t n = d.n;
+  while (n >= 32 || (all && n)) {
+    const uint32_t take = n >= 32 ? 32u : n;
+    n -= take;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(q.count, 32u);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (base + 32 <= q.cap) {
+      q.item[base + lane] = lane < take ? d.item[n + lane] : kNull;
+      if (lane == 0) q.hint[base >> 5] = hint;
+    } else if (lane == 0) {
+      set_error(h, SMMO_E_DEVICE_OOM, M::child_class(args));  // queue full: creations lost
+    }
+    __syncwarp();
+  }
+  if (lane == 0) d.n = n;
+  __syncwarp();
+}
+
+template <class M>
+__device__ __forceinline__ void defer_flush(const HeapView& h, const typename M::Args& args, bool all) {
+  if constexpr (queued<M>::value) defer_flush_queue<M>(h, args, all);
+  else defer_flush_alloc<M>(h, args, all);
+}
+
+// Creates the queued objects of method M: chunk k goes to warp k mod
+// (warps of the grid); the warp takes its chunk's hint and creates the
+// chunk's objects with one warp-parallel new.
+template <class M>
+__global__ void __launch_bounds__(512, SMMO_DOALL_MIN_CTAS) create_queued_kernel(HeapView h, typename M::Args args) {
+  alloc_cache_init();
+  const DeferQueue q = M::queue(args);
+  const uint32_t total = __ldcg(q.count);
+  const uint32_t chunks = (total < q.cap ? total : q.cap) >> 5;
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t ch = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < chunks; ch += nwarps) {
+    const uint32_t p = q.item[ch * 32 + lane];
+    const uint32_t need = (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, p != kNull));
+    if (lane == 0) g_wcache[w].hint = q.hint[ch];
+    __syncwarp();
+    const uint32_t child = warp_new(h, M::child_class(args), need);
+    if (lane < need) M::create(h, args, child, p);
+    __syncwarp();
+  }
+  alloc_cache_flush(h);
+}
+
 // ---------------------------------------------------------------- do-all
 // Persistent do-all over the enumerated blocks (Sec. 5.2.7): the slots of
 // one block are handled by consecutive threads (one warp per 32 slots, a
@@ -813,6 +886,35 @@ __device__ __forceinline__ void defer_flush(const HeapView& h, const typename M:
 // shared-memory queue was measured and dropped: the rounds then span two
 // blocks' columns and cost more sectors and instructions than the idle
 // lanes of partly full units, which these latency-bound kernels hide.)
+// The enumeration entries of 32 consecutive units (at most 17 entries for
+// blocks of 64 slots), one per lane, so that a unit's block and bitmap come
+// from a shuffle instead of a load at the head of its chain of dependent
+// loads.
+struct UnitEntries {
+  uint32_t e0;     // entry index held by lane 0
+  uint32_t block;  // this lane's entry
+  uint32_t cls;
+  uint32_t lo, hi;
+  __device__ __forceinline__ void load(const HeapView& h, uint32_t u0, uint32_t uend, uint32_t halves) {
+    const uint32_t lane = threadIdx.x & 31;
+    e0 = halves == 2 ? (u0 >> 1) : u0;
+    const uint32_t elast = halves == 2 ? ((uend - 1) >> 1) : uend - 1;
+    block = kNull; cls = 0; lo = hi = 0;
+    if (e0 + lane <= elast) {
+      const uint4 raw = __ldcg(reinterpret_cast<const uint4*>(h.R + e0 + lane));
+      block = raw.x; cls = raw.y; lo = raw.z; hi = raw.w;
+    }
+  }
+  // block, class and the unit's 32 slot bits of unit u (warp-converged)
+  __device__ __forceinline__ void unit(uint32_t u, uint32_t halves, uint32_t* blk, uint32_t* c, uint32_t* bits32) const {
+    const uint32_t src = (halves == 2 ? (u >> 1) : u) - e0;
+    *blk = __shfl_sync(0xFFFFFFFFu, block, src);
+    *c = __shfl_sync(0xFFFFFFFFu, cls, src);
+    const uint32_t l = __shfl_sync(0xFFFFFFFFu, lo, src), hh = __shfl_sync(0xFFFFFFFFu, hi, src);
+    *bits32 = (halves == 2 && (u & 1)) ? hh : l;
+  }
+};
+
 template <class M, bool POLY, class F, class G>
 __device__ __forceinline__ void for_each_unit(const HeapView& h, uint32_t c, F&& f, G&& after_unit) {
   const uint32_t n = __ldcg(h.rcnt);
@@ -825,14 +927,20 @@ __device__ __forceinline__ void for_each_unit(const HeapView& h, uint32_t c, F&&
   const uint32_t per = (units + nwarps - 1) / nwarps;
   const uint32_t ub = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * per;
   const uint32_t ue = ub + per < units ? ub + per : units;
-  for (uint32_t u = ub; u < ue; ++u) {
-    const uint32_t slot = (halves == 2 ? (u & 1) * 32 : 0) + lane;
-    const REntry e = h.R[halves == 2 ? (u >> 1) : u];
-    g_wcache[threadIdx.x >> 5].hint = e.block;
-    if (lane == 0) visited += __popcll(halves == 2 ? (e.bits >> ((u & 1) * 32)) & 0xFFFFFFFFull : e.bits);
-    if ((e.bits >> slot) & 1) f(POLY ? e.cls : c, (e.block << 6) | slot);
-    __syncwarp();  // reconverge: lane groups never run different iterations
-    after_unit();
+  for (uint32_t u0 = ub; u0 < ue; u0 += 32) {
+    const uint32_t uend = u0 + 32 < ue ? u0 + 32 : ue;
+    UnitEntries ents;
+    ents.load(h, u0, uend, halves);
+    for (uint32_t u = u0; u < uend; ++u) {
+      uint32_t blk, ecls, bits32;
+      ents.unit(u, halves, &blk, &ecls, &bits32);
+      const uint32_t slot = (halves == 2 ? (u & 1) * 32 : 0) + lane;
+      g_wcache[threadIdx.x >> 5].hint = blk;
+      if (lane == 0) visited += __popc(bits32);
+      if ((bits32 >> lane) & 1) f(POLY ? ecls : c, (blk << 6) | slot);
+      __syncwarp();  // reconverge: lane groups never run different iterations
+      after_unit();
+    }
   }
   if (lane == 0 && visited) count(h, SMMO_CTR_VISIT, visited);
 }

@@ -30,6 +30,7 @@
 
 #include "grid_common.cuh"
 #include "heap_internal.h"
+#include "phased.cuh"
 #include "smmo.h"
 #include "smmo_core.cuh"
 
@@ -57,6 +58,8 @@ struct WorldArgs {
   uint32_t* out_count;
   unsigned long long* errors;
   uint32_t* seen;  // one bit per cell (allocation-free export only)
+  unsigned long long* ctl;  // grid-barrier words of a two-phase launch (zeroed per step)
+  DeferQueue fq, sq;        // queued creations of fish and sharks (one buffer, two counters)
 };
 
 template <class T>
@@ -117,9 +120,20 @@ __device__ __forceinline__ void nb_xy(uint32_t x, uint32_t y, uint32_t W, uint32
 
 // The (r mod k)-th of the k directions set in mask (in direction order 0..3).
 __device__ __forceinline__ int pick_dir(uint32_t mask, uint32_t r) {
-  uint32_t k = r % (uint32_t)__popc(mask);
+  const uint32_t n = (uint32_t)__popc(mask);
+  uint32_t k = n == 3 ? r % 3u : r & (n - 1);  // n is 1, 2, 3 or 4
   while (k--) mask &= mask - 1;
   return __ffs(mask) - 1;
+}
+
+// The direction an agent on local cell lc of `in` takes among the set bits
+// of mask (non-empty): the (draw mod k)-th of the k choices.  With a single
+// choice the draw cannot change the result and is not computed (the draws
+// are counter-based, so skipping one affects no other).
+__device__ __forceinline__ int choose_dir(const WorldArgs& a, const Inst* in, uint32_t tag, uint32_t t,
+                                          uint32_t lc, uint32_t mask) {
+  if ((mask & (mask - 1)) == 0) return __ffs(mask) - 1;
+  return pick_dir(mask, philox_draw(a.seed, tag, t, lc, in->id));
 }
 
 // Posts the request of the agent on local cell (x, y) of `in` to move in
@@ -169,8 +183,7 @@ struct FishPrepare {
     uint32_t tgt = g;
     if (empty) {
       const uint32_t t = *a.tp;
-      const uint32_t r = philox_draw(a.seed, TAG_FISH, t, lc, in->id);
-      tgt = post_request(a, in, x, y, pick_dir(empty, r), t);
+      tgt = post_request(a, in, x, y, choose_dir(a, in, TAG_FISH, t, lc, empty), t);
     }
     *fld<int32_t>(h, self, a.f_target) = (int32_t)tgt;
   }
@@ -235,8 +248,7 @@ struct SharkPrepare {
       }
       if (fish | empty) {
         const uint32_t t = *a.tp;
-        const uint32_t r = philox_draw(a.seed, TAG_SHARK, t, lc, in->id);
-        tgt = post_request(a, in, x, y, pick_dir(fish ? fish : empty, r), t);
+        tgt = post_request(a, in, x, y, choose_dir(a, in, TAG_SHARK, t, lc, fish ? fish : empty), t);
       }
     }
     *fld<int32_t>(h, self, a.s_target) = (int32_t)tgt;
@@ -288,6 +300,184 @@ struct SharkUpdate {
       set_occ(a, g, kNull);
     }
   }
+};
+
+// ------------------------------------------------- Wa-Tor in two phases
+// The same fish and shark rules as the four do-alls above, for the fused
+// launch of phased.cuh: the prepare phase returns the request word
+// (target | rank << 30) as the carry instead of storing it in the agent's
+// target field, kIdle for an agent that posts no request, and for a shark
+// kStarve when it starves; the update phase runs only for those.  The
+// carries are distinct from every request word because cells stay below
+// 2^30 - 2 (smmo_world_create_batch).
+constexpr uint32_t kIdleWord = 0xFFFFFFFFu, kStarveWord = 0xFFFFFFFEu;
+
+struct FishPhased {
+  using Args = WorldArgs;
+  static constexpr uint32_t kIdle = kIdleWord;
+  static constexpr uint32_t kDeferMax = 1;
+  struct P {
+    uint32_t g, x, y, occ[4];
+    int32_t age;
+    const Inst* in;
+  };
+  struct U {
+    uint32_t g, req;
+    int32_t age;
+  };
+  __device__ static uint32_t child_class(const Args& a) { return a.fish; }
+  __device__ static void create(const HeapView& h, const Args& a, uint32_t child, uint32_t g) {
+    FishUpdate::create(h, a, child, g);
+  }
+  __device__ static void load1(const HeapView& h, const Args& a, uint32_t, uint32_t self, P& p) {
+    p.g = *fld<int32_t>(h, self, a.f_cell);
+    p.age = *fld<int16_t>(h, self, a.f_age);
+  }
+  __device__ static void load2(const HeapView& h, const Args& a, uint32_t, uint32_t, P& p) {
+    p.in = find_inst(h, p.g);
+    cell_xy(p.in, p.g - p.in->cell_base, &p.x, &p.y);
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+      p.occ[d] = *a.cells.col<uint32_t>(p.in->cell_base + torus_nb4(p.x, p.y, p.in->W, p.in->H, d), a.occ_off);
+  }
+  __device__ static uint32_t prepare(const HeapView& h, const Args& a, uint32_t, uint32_t self, P& p) {
+    *fld<int16_t>(h, self, a.f_age) = (int16_t)(p.age + 1);
+    uint32_t empty = 0;
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+      if (p.occ[d] == kNull) empty |= 1u << d;
+    if (!empty) return kIdle;
+    const uint32_t t = *a.tp;
+    return post_request(a, p.in, p.x, p.y, choose_dir(a, p.in, TAG_FISH, t, p.g - p.in->cell_base, empty), t);
+  }
+  __device__ static void spill(const HeapView& h, const Args& a, uint32_t, uint32_t self, uint32_t w) {
+    *fld<int32_t>(h, self, a.f_target) = (int32_t)w;
+  }
+  __device__ static uint32_t unspill(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+    return (uint32_t)*fld<int32_t>(h, self, a.f_target);
+  }
+  __device__ static void uload(const HeapView& h, const Args& a, uint32_t, uint32_t self, uint32_t w, U& q) {
+    q.req = __ldcg(a.cells.col<uint32_t>(w & kCellMask, a.req_off));
+    q.g = *fld<int32_t>(h, self, a.f_cell);
+    q.age = *fld<int16_t>(h, self, a.f_age);
+  }
+  __device__ static void update(const HeapView& h, const Args& a, uint32_t, uint32_t self, uint32_t w, U& q) {
+    if (q.req != req_key(*a.tp, a.phase, w >> 30)) return;  // another fish won the target
+    const uint32_t tgt = w & kCellMask;
+    set_occ(a, tgt, self);
+    *fld<int32_t>(h, self, a.f_cell) = (int32_t)tgt;
+    const bool ripe = a.breed_strict ? q.age > a.fish_breed : q.age >= a.fish_breed;
+    if (ripe) {
+      *fld<int16_t>(h, self, a.f_age) = 0;
+      defer_new(q.g);
+    } else {
+      set_occ(a, q.g, kNull);
+    }
+  }
+};
+
+struct SharkPhased {
+  using Args = WorldArgs;
+  static constexpr uint32_t kIdle = kIdleWord;
+  static constexpr uint32_t kDeferMax = 1;
+  struct P {
+    uint32_t g, x, y, occ[4];
+    int32_t age, energy;
+    const Inst* in;
+  };
+  struct U {
+    uint32_t g, req, prey;
+    int32_t age;
+  };
+  __device__ static uint32_t child_class(const Args& a) { return a.shark; }
+  __device__ static void create(const HeapView& h, const Args& a, uint32_t child, uint32_t g) {
+    SharkUpdate::create(h, a, child, g);
+  }
+  __device__ static void load1(const HeapView& h, const Args& a, uint32_t, uint32_t self, P& p) {
+    p.g = *fld<int32_t>(h, self, a.s_cell);
+    p.age = *fld<int16_t>(h, self, a.s_age);
+    p.energy = *fld<int16_t>(h, self, a.s_energy);
+  }
+  __device__ static void load2(const HeapView& h, const Args& a, uint32_t, uint32_t, P& p) {
+    p.in = find_inst(h, p.g);
+    cell_xy(p.in, p.g - p.in->cell_base, &p.x, &p.y);
+    if (p.energy == 1) return;  // starves in this step: no neighbour is looked at
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+      p.occ[d] = *a.cells.col<uint32_t>(p.in->cell_base + torus_nb4(p.x, p.y, p.in->W, p.in->H, d), a.occ_off);
+  }
+  __device__ static uint32_t prepare(const HeapView& h, const Args& a, uint32_t, uint32_t self, P& p) {
+    *fld<int16_t>(h, self, a.s_age) = (int16_t)(p.age + 1);
+    const int16_t en = (int16_t)(p.energy - 1);
+    *fld<int16_t>(h, self, a.s_energy) = en;
+    if (en == 0) return kStarveWord;
+    uint32_t fish = 0, empty = 0;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      if (p.occ[d] == kNull) empty |= 1u << d;
+      else if (type_of(h, p.occ[d]) == a.fish) fish |= 1u << d;
+    }
+    if (!(fish | empty)) return kIdle;
+    const uint32_t t = *a.tp;
+    return post_request(a, p.in, p.x, p.y,
+                        choose_dir(a, p.in, TAG_SHARK, t, p.g - p.in->cell_base, fish ? fish : empty), t);
+  }
+  __device__ static void spill(const HeapView& h, const Args& a, uint32_t, uint32_t self, uint32_t w) {
+    *fld<int32_t>(h, self, a.s_target) = (int32_t)w;
+  }
+  __device__ static uint32_t unspill(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+    return (uint32_t)*fld<int32_t>(h, self, a.s_target);
+  }
+  __device__ static void uload(const HeapView& h, const Args& a, uint32_t, uint32_t self, uint32_t w, U& q) {
+    q.g = *fld<int32_t>(h, self, a.s_cell);
+    if (w == kStarveWord) return;
+    const uint32_t tgt = w & kCellMask;
+    q.req = __ldcg(a.cells.col<uint32_t>(tgt, a.req_off));
+    // only the winner of the target writes its occupant in this phase
+    q.prey = __ldcg(a.cells.col<uint32_t>(tgt, a.occ_off));
+    q.age = *fld<int16_t>(h, self, a.s_age);
+  }
+  __device__ static void update(const HeapView& h, const Args& a, uint32_t, uint32_t self, uint32_t w, U& q) {
+    if (w == kStarveWord) {  // starved: leave the cell and delete itself
+      set_occ(a, q.g, kNull);
+      smmo_delete(h, self);
+      return;
+    }
+    if (q.req != req_key(*a.tp, a.phase, w >> 30)) return;  // another shark won the target
+    const uint32_t tgt = w & kCellMask;
+    if (q.prey != kNull) {  // eat the fish (deleting an object of another class)
+      smmo_delete(h, q.prey);
+      *fld<int16_t>(h, self, a.s_energy) = (int16_t)a.starve;
+    }
+    set_occ(a, tgt, self);
+    *fld<int32_t>(h, self, a.s_cell) = (int32_t)tgt;
+    const bool ripe = a.breed_strict ? q.age > a.shark_breed : q.age >= a.shark_breed;
+    if (ripe) {
+      *fld<int16_t>(h, self, a.s_age) = 0;
+      defer_new(q.g);
+    } else {
+      set_occ(a, q.g, kNull);
+    }
+  }
+};
+
+// The same methods with their creations queued (smmo_core.cuh, DeferQueue)
+// and made by a separate launch after the update.
+struct FishUpdateQ : FishUpdate {
+  static constexpr bool kQueued = true;
+  __device__ static DeferQueue queue(const Args& a) { return a.fq; }
+};
+struct SharkUpdateQ : SharkUpdate {
+  static constexpr bool kQueued = true;
+  __device__ static DeferQueue queue(const Args& a) { return a.sq; }
+};
+struct FishPhasedQ : FishPhased {
+  static constexpr bool kQueued = true;
+  __device__ static DeferQueue queue(const Args& a) { return a.fq; }
+};
+struct SharkPhasedQ : SharkPhased {
+  static constexpr bool kQueued = true;
+  __device__ static DeferQueue queue(const Args& a) { return a.sq; }
 };
 
 // ================================================================ Life
@@ -563,7 +753,9 @@ struct smmo_world {
   int cls_lagent = -1, cls_alive = -1, cls_cand = -1;
   uint32_t nw = 0, nl = 0;  // Wa-Tor and Life instances
   uint32_t t = 0;  // steps done
-  uint32_t* d_t = nullptr;  // device step counter
+  uint32_t* d_t = nullptr;  // device step counter, followed by the barrier words of the fused phases
+  int step_kernels = SMMO_WATOR_FOUR_DO_ALLS;  // how a Wa-Tor iteration is launched
+  uint32_t* d_queue = nullptr;  // queued creations: items, then one hint per 32 items
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
   WorldArgs args{};
@@ -577,6 +769,35 @@ struct PhaseTimer {
   std::vector<int> phase;
   int64_t launches = 0;
 };
+
+// Opens a step: t <- t + 1, and clears the grid-barrier words of the
+// step's two fused Wa-Tor launches (2 x kBarrierWords, behind t) and the
+// two creation-queue counters (one more word behind them).
+__global__ void k_world_step_begin(uint32_t* t, unsigned long long* ctl) {
+  if (threadIdx.x == 0) *t += 1;
+  for (int i = threadIdx.x; i < 2 * kBarrierWords + 1; i += blockDim.x) ctl[i] = 0ull;
+}
+
+unsigned long long* world_ctl(const smmo_world* w) {
+  return reinterpret_cast<unsigned long long*>(reinterpret_cast<uint8_t*>(w->d_t) + 256);
+}
+
+// The fused fish or shark phase (phased.cuh) with K units per round; the
+// barrier words come with the arguments.  The register budget: 48 warps
+// per SM (40 registers) for one unit per round, 40 warps (48 registers)
+// for two.
+#ifndef SMMO_PHASED_WARPS1
+#define SMMO_PHASED_WARPS1 48
+#endif
+#ifndef SMMO_PHASED_WARPS2
+#define SMMO_PHASED_WARPS2 40
+#endif
+template <class M, int K>
+int launch_wator_phased(smmo_heap* h, int cls, const void* args, cudaStream_t s) {
+  constexpr int kMinb = (K == 1 ? SMMO_PHASED_WARPS1 : SMMO_PHASED_WARPS2) / (kPhasedThreads / 32);
+  const WorldArgs* a = static_cast<const WorldArgs*>(args);
+  return launch_phased<M, K, (kMinb > 0 ? kMinb : 1)>(h, cls, *a, a->ctl, s);
+}
 
 // reuse = the previous do-all enumerated the same concrete class and did
 // not create or delete objects of it, so its snapshot is still exact
@@ -608,7 +829,7 @@ int world_steps(smmo_world* w, int nsteps, cudaStream_t s, PhaseTimer* pt) {
   WorldArgs a = w->args;
   for (int k = 0; k < nsteps; ++k) {
     ++w->t;
-    k_step_begin<<<1, 1, 0, s>>>(w->d_t);
+    k_world_step_begin<<<1, 128, 0, s>>>(w->d_t, world_ctl(w));
     if (pt) pt->launches += 1;
     int st = cuda_status(cudaGetLastError());
     if (w->nl) {  // one Life generation (Sec. 7.8, four do-alls)
@@ -617,13 +838,32 @@ int world_steps(smmo_world* w, int nsteps, cudaStream_t s, PhaseTimer* pt) {
       if (!st) st = pdo(w, w->cls_cand, &launch_do_all<CandUpdate>, a, s, pt, 2);
       if (!st) st = pdo(w, w->cls_alive, &launch_do_all<AliveUpdate>, a, s, pt, 3);
     }
-    if (!st && w->nw) {  // one Wa-Tor iteration (Sec. 7.6): fish phase, shark phase
+    const int kern = w->step_kernels & 3;
+    const bool q = (w->step_kernels & SMMO_WATOR_QUEUED_CREATION) != 0;
+    if (!st && w->nw && kern != SMMO_WATOR_FOUR_DO_ALLS) {
+      // one Wa-Tor iteration, each phase (prepare + update) in one launch
+      const bool k2 = kern == SMMO_WATOR_PHASED2;
+      a.phase = 0;
+      a.ctl = world_ctl(w);
+      method_launch_fn ff = q ? (k2 ? &launch_wator_phased<FishPhasedQ, 2> : &launch_wator_phased<FishPhasedQ, 1>)
+                              : (k2 ? &launch_wator_phased<FishPhased, 2> : &launch_wator_phased<FishPhased, 1>);
+      method_launch_fn sf = q ? (k2 ? &launch_wator_phased<SharkPhasedQ, 2> : &launch_wator_phased<SharkPhasedQ, 1>)
+                              : (k2 ? &launch_wator_phased<SharkPhased, 2> : &launch_wator_phased<SharkPhased, 1>);
+      st = pdo(w, w->cls_fish, ff, a, s, pt, 4);
+      if (!st && q) st = pdo(w, w->cls_fish, &launch_create_queued<FishPhasedQ>, a, s, pt, 4, true);
+      a.phase = 1;
+      a.ctl = world_ctl(w) + kBarrierWords;
+      if (!st) st = pdo(w, w->cls_shark, sf, a, s, pt, 6);
+      if (!st && q) st = pdo(w, w->cls_shark, &launch_create_queued<SharkPhasedQ>, a, s, pt, 6, true);
+    } else if (!st && w->nw) {  // one Wa-Tor iteration (Sec. 7.6): fish phase, shark phase
       a.phase = 0;
       st = pdo(w, w->cls_fish, &launch_do_all<FishPrepare>, a, s, pt, 4);
-      if (!st) st = pdo(w, w->cls_fish, &launch_do_all<FishUpdate>, a, s, pt, 5, true);
+      if (!st) st = pdo(w, w->cls_fish, q ? &launch_do_all<FishUpdateQ> : &launch_do_all<FishUpdate>, a, s, pt, 5, true);
+      if (!st && q) st = pdo(w, w->cls_fish, &launch_create_queued<FishUpdateQ>, a, s, pt, 5, true);
       a.phase = 1;
       if (!st) st = pdo(w, w->cls_shark, &launch_do_all<SharkPrepare>, a, s, pt, 6);
-      if (!st) st = pdo(w, w->cls_shark, &launch_do_all<SharkUpdate>, a, s, pt, 7, true);
+      if (!st) st = pdo(w, w->cls_shark, q ? &launch_do_all<SharkUpdateQ> : &launch_do_all<SharkUpdate>, a, s, pt, 7, true);
+      if (!st && q) st = pdo(w, w->cls_shark, &launch_create_queued<SharkUpdateQ>, a, s, pt, 7, true);
     }
     if (st) return st;
   }
@@ -646,7 +886,7 @@ int smmo_world_create_batch(smmo_heap* heap, const smmo_instance_desc* inst, int
     if ((d.kind != SMMO_WORLD_LIFE && d.kind != SMMO_WORLD_WATOR) || d.W < 3 || d.H < 3) return SMMO_E_INVALID_ARG;
     if (d.base != total || d.count != (uint64_t)d.W * d.H) return SMMO_E_INVALID_ARG;
     total += d.count;
-    if (total > kCellMask + 1ull) return SMMO_E_INVALID_ARG;  // cells below 2^30
+    if (total > kCellMask - 1ull) return SMMO_E_INVALID_ARG;  // cells below 2^30 - 2
   }
   int st = smmo_batch_define(heap, inst, n_inst);  // the heap owns the instance table
   if (st) return st;
@@ -688,8 +928,16 @@ int smmo_world_create_batch(smmo_heap* heap, const smmo_instance_desc* inst, int
     st = SMMO_E_UNSUPPORTED;  // dense cell addressing needs N = 32 or 64
   if (st) { delete w; return st; }
   // the step counter (the instance table is the heap's)
-  cudaError_t e = cudaMalloc(&w->d_t, sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMemsetAsync(w->d_t, 0, sizeof(uint32_t), s);
+  const size_t tbytes = 256 + (2 * kBarrierWords + 1) * sizeof(unsigned long long);
+  cudaError_t e = cudaMalloc(&w->d_t, tbytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w->d_t, 0, tbytes, s);
+  // creation queue of the Wa-Tor updates: at most one creation per agent
+  // (agents <= cells), plus a partly filled chunk per warp of the grid
+  uint32_t qcap = 0;
+  if (e == cudaSuccess && w->nw) {
+    qcap = (uint32_t)(((total + 32ull * (uint64_t)heap->num_sms * 64ull) + 31ull) & ~31ull);
+    e = cudaMalloc(&w->d_queue, (size_t)qcap * 4 + (size_t)(qcap / 32) * 4);
+  }
   if (e != cudaSuccess) { smmo_world_destroy(w); return cuda_status(e); }
   // cells: occ = null, req = all ones (above every key), kind = empty
   const uint64_t N = w->total_cells;
@@ -734,6 +982,15 @@ int smmo_world_create_batch(smmo_heap* heap, const smmo_instance_desc* inst, int
     a.a_cell = A.col_off[0]; a.a_action = A.col_off[1]; a.a_isnew = A.col_off[2];
     a.a_blocked = A.col_off[3];
     a.c_cell = C.col_off[0]; a.c_action = C.col_off[1];
+  }
+  if (w->d_queue) {
+    uint32_t* qcnt = reinterpret_cast<uint32_t*>(world_ctl(w) + 2 * kBarrierWords);
+    a.fq.item = w->d_queue;
+    a.fq.hint = w->d_queue + qcap;
+    a.fq.cap = qcap;
+    a.fq.count = qcnt;
+    a.sq = a.fq;
+    a.sq.count = qcnt + 1;
   }
   a.seed = seed;
   a.survive = (1u << 2) | (1u << 3);  // Life until smmo_world_set_life_rule
@@ -838,6 +1095,13 @@ int smmo_world_set_life_rule(smmo_world* w, uint32_t survive, uint32_t born, uin
   w->args.born = born;
   w->args.block = block;
   if (w->graph) { cudaGraphExecDestroy(w->graph); w->graph = nullptr; }  // captured with the old rule
+  return SMMO_OK;
+}
+
+int smmo_world_set_step_kernels(smmo_world* w, int mode) {
+  if (!w || mode < 0 || (mode & ~(3 | SMMO_WATOR_QUEUED_CREATION)) || (mode & 3) == 3) return SMMO_E_INVALID_ARG;
+  w->step_kernels = mode;
+  if (w->graph) { cudaGraphExecDestroy(w->graph); w->graph = nullptr; }  // captured with the old kernels
   return SMMO_OK;
 }
 
@@ -1034,6 +1298,7 @@ int smmo_world_destroy(smmo_world* w) {
   if (!w) return SMMO_E_INVALID_ARG;
   if (w->graph) cudaGraphExecDestroy(w->graph);
   if (w->d_t) cudaFree(w->d_t);
+  if (w->d_queue) cudaFree(w->d_queue);
   delete w;
   return SMMO_OK;
 }

@@ -12,6 +12,9 @@ import torch
 from . import smmo
 
 LIFE, WATOR = 0, 1
+# how a Wa-Tor iteration is launched (smmo_world_set_step_kernels)
+FOUR_DO_ALLS, PHASED1, PHASED2 = 0, 1, 2
+QUEUED = 4  # or-ed with one of the above: creations queued and made by a launch of their own
 
 
 class WatorParams(ctypes.Structure):
@@ -32,9 +35,10 @@ class World:
     def __init__(self, kinds, widths, heights, seed: int, init_kind, init_age=None,
                  init_energy=None, init_state=None, params: WatorParams | None = None,
                  heap_bytes: int | None = None, config: smmo.HeapConfig | None = None,
-                 stream=None, inst_ids=None):
+                 stream=None, inst_ids=None, step_kernels: int | None = None):
         """inst_ids: the instance numbers of the draws (default 0..n-1), so
-        that one instance of a larger batch can be run alone."""
+        that one instance of a larger batch can be run alone.  step_kernels:
+        FOUR_DO_ALLS, PHASED1 or PHASED2 (the library's default when None)."""
         n = len(kinds)
         self.kinds = [int(k) for k in kinds]
         self.W = [int(w) for w in widths]
@@ -76,6 +80,13 @@ class World:
         smmo.check(smmo.lib().smmo_world_info(self._w, None, ids, None), "world_info")
         names = ["Cell", "WAgent", "Fish", "Shark", "LAgent", "Alive", "Candidate"]
         self.class_ids = dict(zip(names, list(ids)))
+        if step_kernels is not None:
+            self.set_step_kernels(step_kernels)
+
+    def set_step_kernels(self, mode: int):
+        """FOUR_DO_ALLS, PHASED1 or PHASED2, optionally | QUEUED (see
+        smmo_world_set_step_kernels)."""
+        smmo.check(smmo.lib().smmo_world_set_step_kernels(self._w, int(mode)), "world_set_step_kernels")
 
     def step(self, n: int = 1):
         smmo.check(smmo.lib().smmo_world_step(self._w, n, smmo._stream(self.stream)), "world_step")
