@@ -56,7 +56,8 @@ PHASES = ["life_cand_prepare", "life_alive_prepare", "life_cand_update", "life_a
           "fish_prepare", "fish_update", "shark_prepare", "shark_update"]
 # phase names when each species runs as one fused launch (phases 5 and 7 empty)
 PHASES_FUSED = PHASES[:4] + ["fish_step", "", "shark_step", ""]
-STEP_KERNELS = {"four_do_alls": 0, "phased1": 1, "phased2": 2, "four_do_alls_queued": 4, "phased2_queued": 6}
+STEP_KERNELS = {"four_do_alls": 0, "phased1": 1, "phased2": 2, "four_do_alls_queued": 4, "phased2_queued": 6,
+                "four_do_alls_marked": 8, "four_do_alls_marked_queued": 12}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "wator_2048_fish_update_traffic.txt")  # JSON
 # Sources of the Wa-Tor do-all kernels: the allocator and do-all core, the
 # cellular helpers, and the Wa-Tor section of world.cu (between its Wa-Tor

@@ -464,10 +464,14 @@ int smmo_world_set_life_rule(smmo_world* w, uint32_t survive, uint32_t born, uin
  *     an update are written to a queue (payload and placement hint) instead
  *     of being allocated inside the update, and one more launch after it
  *     creates them, a full warp per 32.
+ *   | SMMO_WATOR_MARKED_UPDATE (with SMMO_WATOR_FOUR_DO_ALLS only): the
+ *     prepare do-all marks, per 32 slots, the agents that posted a request
+ *     (or starve), and the update do-all runs its method only on those; it
+ *     still walks and counts every agent.
  * Any other value: SMMO_E_INVALID_ARG.  Takes effect at the next step;
  * drops a captured graph. */
 enum { SMMO_WATOR_FOUR_DO_ALLS = 0, SMMO_WATOR_PHASED1 = 1, SMMO_WATOR_PHASED2 = 2,
-       SMMO_WATOR_QUEUED_CREATION = 4 };
+       SMMO_WATOR_QUEUED_CREATION = 4, SMMO_WATOR_MARKED_UPDATE = 8 };
 int smmo_world_set_step_kernels(smmo_world* w, int mode);
 /* Writes the live objects into per-cell device arrays (same indexing as
  * the initial state; kind, age, energy, state as above, age of an Alive =

@@ -458,7 +458,7 @@ int freeze(smmo_heap* h, cudaStream_t s) {
   }
   const size_t block_bytes = data_bytes;
   const int nbm = 1 + 3 * nc;
-  // carve: state | layouts | alloc_bm | block_type | R | scratch | bitmaps | data
+  // carve: state | layouts | alloc_bm | block_type | R | scratch | moved | bitmaps | unit marks | instances | data
   const size_t fixed = align_up(sizeof(DeviceState), 256) +
                        align_up(sizeof(ClassLayout) * SMMO_MAX_CLASSES, 256) + 8 * 256;
   if (h->buf_bytes <= fixed) return SMMO_E_OOM;
@@ -488,9 +488,10 @@ int freeze(smmo_heap* h, cudaStream_t s) {
     const uint64_t bw = bm_geom(M, lw, lo, lb, &nl);
     return fixed + align_up(M * 8, 256) + align_up(M * 4, 256) + align_up(rscratch_bytes(M), 256) +
            align_up(M * 4 + 1024, 256) + align_up((M + 63) / 64 * 8, 256) + align_up(bw * 8 * nbm, 256) +
+           align_up(M * 8, 256) +
            align_up(inst_bytes, 256) + M * block_bytes;
   };
-  uint64_t M = h->buf_bytes / (block_bytes + 40);
+  uint64_t M = h->buf_bytes / (block_bytes + 48);
   M = std::min<uint64_t>(M, (1ull << 26) - 1);
   while (M > 0 && need_bytes(M) > h->buf_bytes) M -= std::max<uint64_t>(1, M / 1000);
   if (M < 2) return SMMO_E_OOM;
@@ -511,6 +512,7 @@ int freeze(smmo_heap* h, cudaStream_t s) {
   h->d_scratch = (uint32_t*)take(M * 4 + 1024);
   h->d_moved = (unsigned long long*)take((M + 63) / 64 * 8);
   v.bitmaps = (unsigned long long*)take(bw * 8 * nbm);
+  v.umark = (uint32_t*)take(M * 8);  // two 32-slot units per block
   h->d_inst = h->batch.empty() ? nullptr : (Inst*)take(inst_bytes);
   v.inst = h->d_inst;
   v.n_inst = (uint32_t)h->batch.size();

@@ -105,6 +105,7 @@ struct HeapView {
   const ClassLayout* cls;             // per-class layouts (device)
   REntry* R;                          // enumeration scratch
   uint32_t* rcnt;                     // its entry count (the heap's, or a saved snapshot's)
+  uint32_t* umark;                    // per unit of R: slots marked by a marking do-all
   const Inst* inst;                   // instance table (null: no batch)
   uint32_t n_inst;
   uint32_t block_bytes;
@@ -161,15 +162,9 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
   return x;
 }
 
-// Position of the n-th (0-based) set bit of b (Alg. 5.9 "nth_set_bit":
-// clear the n lowest set bits, then find-first-set).  -1 if b has <= n bits.
-__device__ __forceinline__ int nth_set_bit(unsigned long long b, int n) {
-  for (int i = 0; i < n; ++i) b &= b - 1;
-  return b ? __ffsll((long long)b) - 1 : -1;
-}
-
-// Position of set bit number n (0-based, n < popcount(b)) of b, by binary
-// search on population counts of halves.
+// Position of set bit number n (0-based, n < popcount(b)) of b (the
+// nth_set_bit of Alg. 5.9, which clears the n lowest set bits one at a
+// time; here a binary search on population counts of halves).
 __device__ __forceinline__ int nth_set_bit64(unsigned long long b, uint32_t n) {
   int pos = 0;
 #pragma unroll
@@ -178,6 +173,14 @@ __device__ __forceinline__ int nth_set_bit64(unsigned long long b, uint32_t n) {
     if (n >= c) { n -= c; b >>= w; pos += w; }
   }
   return pos;
+}
+
+// The k lowest set bits of b (all of them if b has at most k): a mask up
+// to the position of set bit number k, found by the binary search above,
+// instead of clearing the lowest set bit k times.
+__device__ __forceinline__ unsigned long long lowest_set_bits(unsigned long long b, uint32_t k) {
+  if ((uint32_t)__popcll(b) <= k) return b;
+  return b & ((1ull << nth_set_bit64(b, k)) - 1);
 }
 
 // ---------------------------------------------------- hierarchical bitmaps
@@ -403,14 +406,9 @@ static __device__ __forceinline__ unsigned long long reserve_in(const HeapView& 
                                                              int n) {
   for (int s = 0; s < h.bitmap_spins; ++s) {
     const unsigned long long cur = ld_cg(h.alloc_bm + bid);
-    unsigned long long freeb = ~cur;
+    const unsigned long long freeb = ~cur;
     if (freeb == 0) { count(h, SMMO_CTR_RESERVE_FAIL, 1); return 0; }  // full or invalidated
-    unsigned long long pick = 0;
-    for (int i = 0; i < n && freeb; ++i) {
-      const unsigned long long low = freeb & (0ull - freeb);
-      pick |= low;
-      freeb ^= low;
-    }
+    const unsigned long long pick = lowest_set_bits(freeb, (uint32_t)n);
     const unsigned long long before = atomicOr(h.alloc_bm + bid, pick);
     const unsigned long long got = pick & ~before;
     if (!got) continue;
@@ -560,17 +558,9 @@ __device__ __forceinline__ unsigned long long cache_take(const HeapView& h, uint
     avail = cache_refill(h, c, seed, &b);
     wc.bid[c] = b;
   }
-  unsigned long long take = avail;
-  if (__popcll(avail) > n) {  // keep the highest bits, hand out the n lowest
-    take = 0;
-    for (int i = 0; i < n; ++i) {
-      const unsigned long long low = avail & (0ull - avail);
-      take |= low;
-      avail ^= low;
-    }
-  } else {
-    avail = 0;
-  }
+  // keep the highest bits, hand out the n lowest
+  const unsigned long long take = lowest_set_bits(avail, (uint32_t)n);
+  avail ^= take;
   wc.bits[c] = b == kNull ? 0ull : avail;
   __threadfence_block();
   atomicExch(&wc.lock, 0);
@@ -612,7 +602,7 @@ __device__ __forceinline__ uint32_t smmo_new(const HeapView& h, uint32_t c) {
     }
     if (result == kNull) {
       const int rank = __popc(need & ((1u << lane) - 1));
-      const int slot = nth_set_bit(got, rank);
+      const int slot = rank < __popcll(got) ? nth_set_bit64(got, (uint32_t)rank) : -1;
       if (slot >= 0) result = (bid << 6) | (uint32_t)slot;
     }
   }
@@ -625,8 +615,9 @@ __device__ __forceinline__ uint32_t smmo_new(const HeapView& h, uint32_t c) {
 // once (the deferred creations below): lane i < need receives a handle.
 // The warp's cache is used first; the rest is reserved in the blocks of
 // class c around the warp's hint (the 64 blocks of the hint's level-0
-// bitmap word) with one block per lane and every reservation in flight at
-// the same time: one round of loads (allocation bitmaps and type ids),
+// bitmap word, then those of the neighbouring words, 32 per round while
+// slots are missing) with one block per lane and every reservation of a
+// round in flight at the same time: one round of loads (allocation bitmaps and type ids),
 // one round of atomicOr reservations, one round of type re-checks (a block
 // re-initialised to another class in between is rolled back, Alg. 5.1),
 // then the block-state changes of the blocks that became full or left the
@@ -639,13 +630,8 @@ __device__ __forceinline__ uint32_t warp_new(const HeapView& h, uint32_t c, uint
   // (1) the warp's cache (the warp is converged: no lane group of it is
   // inside smmo_new, so the leader may touch the cache without the lock)
   if (lane == 0) {
-    unsigned long long avail = wc.bits[c], take = 0;
-    for (uint32_t i = 0; i < need && avail; ++i) {
-      const unsigned long long low = avail & (0ull - avail);
-      take |= low;
-      avail ^= low;
-    }
-    wc.bits[c] = avail;
+    const unsigned long long avail = wc.bits[c], take = lowest_set_bits(avail, need);
+    wc.bits[c] = avail ^ take;
     g_wnew[w].bits = take;
     g_wnew[w].bid = wc.bid[c];
     if (take) count(h, SMMO_CTR_ALLOC(c), __popcll(take));
@@ -655,81 +641,74 @@ __device__ __forceinline__ uint32_t warp_new(const HeapView& h, uint32_t c, uint
   uint32_t got_n = (uint32_t)__popcll(take);
   if (lane < got_n) result = (g_wnew[w].bid << 6) | (uint32_t)nth_set_bit64(take, lane);
   __syncwarp();
-  // (2) the blocks of class c among the 64 around the hint, one per lane
+  // (2) blocks of class c near the hint, 32 per round (one per lane): the
+  // two halves of the hint's level-0 bitmap word, then of the word after
+  // it and of the word before it, while slots are missing
   const uint32_t hint = wc.hint;
-  if (got_n < need && hint < h.num_blocks) {
-    const uint32_t rem = need - got_n;
-    const uint32_t base = hint & ~63u;
-    uint32_t bid = kNull;
-    unsigned long long freeb = 0;
+  if (hint < h.num_blocks) {
+    const int32_t w0 = (int32_t)(hint >> 6);
+    for (int r = 0; r < 6 && got_n < need; ++r) {
+      const int32_t wd = w0 + (r < 2 ? 0 : (r < 4 ? 1 : -1));
+      if (wd < 0) continue;
+      const uint32_t cand = (uint32_t)wd * 64u + (uint32_t)(r & 1) * 32u + lane;
+      const uint32_t rem = need - got_n;
+      const bool ok = cand < h.num_blocks && __ldcg(h.block_type + cand) == c;
+      const unsigned long long freeb = ok ? ~ld_cg(h.alloc_bm + cand) : 0ull;
+      const uint32_t bid = freeb ? cand : kNull;
+      // the lowest free slots, in lane order, until rem are covered
+      const uint32_t nf = (uint32_t)__popcll(freeb);
+      uint32_t incl = nf;
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const uint32_t b = base + half * 32 + lane;
-      const bool ok = b < h.num_blocks && __ldcg(h.block_type + b) == c;
-      const unsigned long long f = ok ? ~ld_cg(h.alloc_bm + b) : 0ull;
-      if (bid == kNull && f) { bid = b; freeb = f; }
-    }
-    // the lowest free slots, in lane order, until rem are covered
-    const uint32_t nf = (uint32_t)__popcll(freeb);
-    uint32_t incl = nf;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (lane >= (uint32_t)o) incl += v;
-    }
-    const uint32_t excl = incl - nf;
-    unsigned long long pick = 0;
-    if (excl < rem) {
-      unsigned long long f = freeb;
-      for (uint32_t i = excl; i < rem && f; ++i) {
-        const unsigned long long low = f & (0ull - f);
-        pick |= low;
-        f ^= low;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= (uint32_t)o) incl += v;
       }
-    }
-    unsigned long long got = 0;
-    if (pick) {
-      const unsigned long long before = atomicOr(h.alloc_bm + bid, pick);
-      got = pick & ~before;
-      if (got) {
-        const uint32_t t = atomicAdd(h.block_type + bid, 0u);
-        if (t < (uint32_t)h.num_classes) {
-          const unsigned long long tcap = __ldg(&h.cls[t].capmask);
-          const uint32_t dlim = __ldg(&h.cls[t].dlimit);
-          const uint32_t fb = __popcll(before & tcap), fa = fb + __popcll(got);
-          if ((before | got) == kAll) bm_clear(h, bm_active(h, t), bid);   // filled it
-          if (fb <= dlim && fa > dlim) bm_clear(h, bm_defrag(h, t), bid);  // no candidate now
-        }
-        if (t != c) {  // re-initialised to another class meanwhile: roll back
-          dealloc_bits(h, bid, t, got);
-          got = 0;
-        } else {
-          count(h, SMMO_CTR_ALLOC(c), __popcll(got));
+      const uint32_t excl = incl - nf;
+      const unsigned long long pick = excl < rem ? lowest_set_bits(freeb, rem - excl) : 0ull;
+      unsigned long long got = 0;
+      if (pick) {
+        const unsigned long long before = atomicOr(h.alloc_bm + bid, pick);
+        got = pick & ~before;
+        if (got) {
+          const uint32_t t = atomicAdd(h.block_type + bid, 0u);
+          if (t < (uint32_t)h.num_classes) {
+            const unsigned long long tcap = __ldg(&h.cls[t].capmask);
+            const uint32_t dlim = __ldg(&h.cls[t].dlimit);
+            const uint32_t fb = __popcll(before & tcap), fa = fb + __popcll(got);
+            if ((before | got) == kAll) bm_clear(h, bm_active(h, t), bid);   // filled it
+            if (fb <= dlim && fa > dlim) bm_clear(h, bm_defrag(h, t), bid);  // no candidate now
+          }
+          if (t != c) {  // re-initialised to another class meanwhile: roll back
+            dealloc_bits(h, bid, t, got);
+            got = 0;
+          } else {
+            count(h, SMMO_CTR_ALLOC(c), __popcll(got));
+          }
         }
       }
-    }
-    // concatenate the lanes' reserved slots; lane got_n + j takes number j
-    const uint32_t ng = (uint32_t)__popcll(got);
-    uint32_t gi = ng;
+      // concatenate the lanes' reserved slots; lane got_n + j takes number j
+      const uint32_t ng = (uint32_t)__popcll(got);
+      uint32_t gi = ng;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, gi, o);
-      if (lane >= (uint32_t)o) gi += v;
-    }
-    const uint32_t total = __shfl_sync(0xFFFFFFFFu, gi, 31);
-    const uint32_t want = lane - got_n;  // wraps for lanes already served
-    uint32_t src = 0;  // first lane whose inclusive count exceeds want
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, gi, o);
+        if (lane >= (uint32_t)o) gi += v;
+      }
+      const uint32_t total = __shfl_sync(0xFFFFFFFFu, gi, 31);
+      const uint32_t want = lane - got_n;  // wraps for lanes already served
+      uint32_t src = 0;  // first lane whose inclusive count exceeds want
 #pragma unroll
-    for (uint32_t step = 16; step; step >>= 1) {
-      const uint32_t v = __shfl_sync(0xFFFFFFFFu, gi, src + step - 1);
-      if (v <= want) src += step;
+      for (uint32_t step = 16; step; step >>= 1) {
+        const uint32_t v = __shfl_sync(0xFFFFFFFFu, gi, src + step - 1);
+        if (v <= want) src += step;
+      }
+      src &= 31;
+      const uint32_t sb = __shfl_sync(0xFFFFFFFFu, bid, src);
+      const unsigned long long sg = __shfl_sync(0xFFFFFFFFu, got, src);
+      const uint32_t sexcl = __shfl_sync(0xFFFFFFFFu, gi, src) - (uint32_t)__popcll(sg);
+      if (lane >= got_n && lane < need && want < total) result = (sb << 6) | (uint32_t)nth_set_bit64(sg, want - sexcl);
+      got_n += total;
     }
-    src &= 31;
-    const uint32_t sb = __shfl_sync(0xFFFFFFFFu, bid, src);
-    const unsigned long long sg = __shfl_sync(0xFFFFFFFFu, got, src);
-    const uint32_t sexcl = __shfl_sync(0xFFFFFFFFu, gi, src) - (uint32_t)__popcll(sg);
-    if (lane >= got_n && lane < need && want < total) result = (sb << 6) | (uint32_t)nth_set_bit64(sg, want - sexcl);
-    got_n += total;
   }
   // (3) what is still missing, one leader at a time
   if (got_n < need && lane >= got_n && lane < need) result = smmo_new(h, c);
@@ -915,30 +894,91 @@ struct UnitEntries {
   }
 };
 
+// Marking and filtered do-alls.  A marking method (M::kMarks) returns from
+// run whether the object has work in the do-all that follows over the same
+// snapshot; the do-all stores the ballot of those slots per unit in
+// h.umark.  A filtered method (M::kFiltered) is run only on the marked slots
+// of each unit: the do-all still walks every unit and counts every object of
+// the snapshot, but an object whose method would return at once (the
+// marking do-all already knew that) costs no load, and the marked slots of
+// consecutive units are packed into full warps, so 32 of them issue their
+// loads together instead of unit after unit.  The pair behaves as the
+// unfiltered pair as long as nothing re-enumerates the class in between.
+template <class M, class = void>
+struct marks { static constexpr bool value = false; };
+template <class M>
+struct marks<M, decltype((void)M::kMarks)> { static constexpr bool value = M::kMarks; };
+template <class M, class = void>
+struct filtered { static constexpr bool value = false; };
+template <class M>
+struct filtered<M, decltype((void)M::kFiltered)> { static constexpr bool value = M::kFiltered; };
+
+// Marked slots of a filtered do-all, collected per warp until 32 can run
+// at once (one per lane).
+static __shared__ uint32_t g_pack[16][64];
+
 template <class M, bool POLY, class F, class G>
 __device__ __forceinline__ void for_each_unit(const HeapView& h, uint32_t c, F&& f, G&& after_unit) {
+  constexpr bool kMark = marks<M>::value, kFilter = filtered<M>::value;
+  static_assert(!(kFilter && POLY), "a filtered do-all runs over one class");
   const uint32_t n = __ldcg(h.rcnt);
   const uint32_t cap = POLY ? 64u : __ldg(&h.cls[c].cap);
   const uint32_t halves = cap > 32 ? 2u : 1u;
   const uint32_t units = n * halves;
-  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   uint32_t visited = 0;
   const uint32_t per = (units + nwarps - 1) / nwarps;
   const uint32_t ub = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * per;
   const uint32_t ue = ub + per < units ? ub + per : units;
+  uint32_t np = 0;  // filtered: marked slots waiting in g_pack[w] (warp-uniform)
   for (uint32_t u0 = ub; u0 < ue; u0 += 32) {
     const uint32_t uend = u0 + 32 < ue ? u0 + 32 : ue;
     UnitEntries ents;
     ents.load(h, u0, uend, halves);
+    uint32_t umk = 0;
+    if constexpr (kFilter) umk = u0 + lane < uend ? __ldcg(h.umark + u0 + lane) : 0u;
     for (uint32_t u = u0; u < uend; ++u) {
       uint32_t blk, ecls, bits32;
       ents.unit(u, halves, &blk, &ecls, &bits32);
       const uint32_t slot = (halves == 2 ? (u & 1) * 32 : 0) + lane;
-      g_wcache[threadIdx.x >> 5].hint = blk;
       if (lane == 0) visited += __popc(bits32);
-      if ((bits32 >> lane) & 1) f(POLY ? ecls : c, (blk << 6) | slot);
-      __syncwarp();  // reconverge: lane groups never run different iterations
+      if constexpr (kFilter) {
+        // the marked slots of the unit join the warp's list; every full 32
+        // of them run together, one per lane
+        const uint32_t run_bits = bits32 & __shfl_sync(0xFFFFFFFFu, umk, u - u0);
+        if (run_bits == 0) continue;
+        if ((run_bits >> lane) & 1) g_pack[w][np + __popc(run_bits & ((1u << lane) - 1))] = (blk << 6) | slot;
+        np += __popc(run_bits);
+        __syncwarp();
+        if (np < 32) continue;
+        np -= 32;
+        const uint32_t self = g_pack[w][np + lane];
+        __syncwarp();
+        g_wcache[w].hint = self >> 6;
+        f(c, self);
+        __syncwarp();
+        after_unit();
+      } else {
+        g_wcache[w].hint = blk;
+        bool mk = false;
+        if ((bits32 >> lane) & 1) mk = f(POLY ? ecls : c, (blk << 6) | slot);
+        __syncwarp();  // reconverge: lane groups never run different iterations
+        if constexpr (kMark) {
+          const uint32_t m = __ballot_sync(0xFFFFFFFFu, mk);
+          if (lane == 0) h.umark[u] = m;
+        }
+        after_unit();
+      }
+    }
+  }
+  if constexpr (kFilter) {
+    if (np) {
+      const uint32_t self = lane < np ? g_pack[w][lane] : kNull;
+      __syncwarp();
+      g_wcache[w].hint = __shfl_sync(0xFFFFFFFFu, self, 0) >> 6;
+      if (lane < np) f(c, self);
+      __syncwarp();
       after_unit();
     }
   }
@@ -954,7 +994,15 @@ __global__ void __launch_bounds__(512, SMMO_DOALL_MIN_CTAS) do_all_kernel(HeapVi
   if (kDefer && (threadIdx.x & 31) == 0) g_defer[threadIdx.x >> 5].n = 0;
   __syncwarp();
   for_each_unit<M, POLY>(
-      h, c, [&](uint32_t cls, uint32_t self) { M::run(h, args, cls, self); },
+      h, c,
+      [&](uint32_t cls, uint32_t self) -> bool {
+        if constexpr (marks<M>::value) {
+          return M::run(h, args, cls, self);
+        } else {
+          M::run(h, args, cls, self);
+          return false;
+        }
+      },
       [&]() {
         if constexpr (kDefer) {
           if (g_defer[threadIdx.x >> 5].n >= 32) defer_flush<M>(h, args, false);
@@ -1000,7 +1048,12 @@ __global__ void __launch_bounds__(512, SMMO_DOALL_MIN_CTAS) do_all_reduce_kernel
   alloc_cache_init();
   long long acc = reduce_identity(op);
   for_each_unit<M, POLY>(
-      h, c, [&](uint32_t cls, uint32_t self) { acc = reduce2(op, acc, M::run(h, args, cls, self)); }, [] {});
+      h, c,
+      [&](uint32_t cls, uint32_t self) -> bool {
+        acc = reduce2(op, acc, M::run(h, args, cls, self));
+        return false;
+      },
+      [] {});
   alloc_cache_flush(h);
 #pragma unroll
   for (int o = 16; o; o >>= 1) acc = reduce2(op, acc, __shfl_xor_sync(0xFFFFFFFFu, acc, o));

@@ -166,9 +166,11 @@ __device__ __forceinline__ void set_cell(const WorldArgs& a, uint32_t g, uint32_
   *a.cells.col<uint8_t>(g, a.kind_off) = kind;
 }
 
+// The prepares return whether the agent has anything to do in the update
+// (a posted request, or a starving shark), for the marking do-all below.
 struct FishPrepare {
   using Args = WorldArgs;
-  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+  __device__ static bool run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
     const uint32_t g = *fld<int32_t>(h, self, a.f_cell);
     int16_t* agep = fld<int16_t>(h, self, a.f_age);
     *agep = (int16_t)(*agep + 1);
@@ -186,6 +188,7 @@ struct FishPrepare {
       tgt = post_request(a, in, x, y, choose_dir(a, in, TAG_FISH, t, lc, empty), t);
     }
     *fld<int32_t>(h, self, a.f_target) = (int32_t)tgt;
+    return tgt != g;
   }
 };
 
@@ -226,7 +229,7 @@ struct FishUpdate {
 
 struct SharkPrepare {
   using Args = WorldArgs;
-  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
+  __device__ static bool run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
     const uint32_t g = *fld<int32_t>(h, self, a.s_cell);
     int16_t* agep = fld<int16_t>(h, self, a.s_age);
     int16_t* enp = fld<int16_t>(h, self, a.s_energy);
@@ -252,6 +255,7 @@ struct SharkPrepare {
       }
     }
     *fld<int32_t>(h, self, a.s_target) = (int32_t)tgt;
+    return en == 0 || tgt != g;
   }
 };
 
@@ -471,6 +475,15 @@ struct SharkUpdateQ : SharkUpdate {
   static constexpr bool kQueued = true;
   __device__ static DeferQueue queue(const Args& a) { return a.sq; }
 };
+// Marking prepares and filtered updates (smmo_core.cuh): the update runs
+// only on the agents whose prepare posted a request (or starved); the rest
+// would return at once.
+struct FishPrepareM : FishPrepare { static constexpr bool kMarks = true; };
+struct SharkPrepareM : SharkPrepare { static constexpr bool kMarks = true; };
+struct FishUpdateF : FishUpdate { static constexpr bool kFiltered = true; };
+struct SharkUpdateF : SharkUpdate { static constexpr bool kFiltered = true; };
+struct FishUpdateQF : FishUpdateQ { static constexpr bool kFiltered = true; };
+struct SharkUpdateQF : SharkUpdateQ { static constexpr bool kFiltered = true; };
 struct FishPhasedQ : FishPhased {
   static constexpr bool kQueued = true;
   __device__ static DeferQueue queue(const Args& a) { return a.fq; }
@@ -856,13 +869,20 @@ int world_steps(smmo_world* w, int nsteps, cudaStream_t s, PhaseTimer* pt) {
       if (!st) st = pdo(w, w->cls_shark, sf, a, s, pt, 6);
       if (!st && q) st = pdo(w, w->cls_shark, &launch_create_queued<SharkPhasedQ>, a, s, pt, 6, true);
     } else if (!st && w->nw) {  // one Wa-Tor iteration (Sec. 7.6): fish phase, shark phase
+      const bool mk = (w->step_kernels & SMMO_WATOR_MARKED_UPDATE) != 0;
+      method_launch_fn fp = mk ? &launch_do_all<FishPrepareM> : &launch_do_all<FishPrepare>;
+      method_launch_fn sp = mk ? &launch_do_all<SharkPrepareM> : &launch_do_all<SharkPrepare>;
+      method_launch_fn fu = q ? (mk ? &launch_do_all<FishUpdateQF> : &launch_do_all<FishUpdateQ>)
+                              : (mk ? &launch_do_all<FishUpdateF> : &launch_do_all<FishUpdate>);
+      method_launch_fn su = q ? (mk ? &launch_do_all<SharkUpdateQF> : &launch_do_all<SharkUpdateQ>)
+                              : (mk ? &launch_do_all<SharkUpdateF> : &launch_do_all<SharkUpdate>);
       a.phase = 0;
-      st = pdo(w, w->cls_fish, &launch_do_all<FishPrepare>, a, s, pt, 4);
-      if (!st) st = pdo(w, w->cls_fish, q ? &launch_do_all<FishUpdateQ> : &launch_do_all<FishUpdate>, a, s, pt, 5, true);
+      st = pdo(w, w->cls_fish, fp, a, s, pt, 4);
+      if (!st) st = pdo(w, w->cls_fish, fu, a, s, pt, 5, true);
       if (!st && q) st = pdo(w, w->cls_fish, &launch_create_queued<FishUpdateQ>, a, s, pt, 5, true);
       a.phase = 1;
-      if (!st) st = pdo(w, w->cls_shark, &launch_do_all<SharkPrepare>, a, s, pt, 6);
-      if (!st) st = pdo(w, w->cls_shark, q ? &launch_do_all<SharkUpdateQ> : &launch_do_all<SharkUpdate>, a, s, pt, 7, true);
+      if (!st) st = pdo(w, w->cls_shark, sp, a, s, pt, 6);
+      if (!st) st = pdo(w, w->cls_shark, su, a, s, pt, 7, true);
       if (!st && q) st = pdo(w, w->cls_shark, &launch_create_queued<SharkUpdateQ>, a, s, pt, 7, true);
     }
     if (st) return st;
@@ -1099,7 +1119,9 @@ int smmo_world_set_life_rule(smmo_world* w, uint32_t survive, uint32_t born, uin
 }
 
 int smmo_world_set_step_kernels(smmo_world* w, int mode) {
-  if (!w || mode < 0 || (mode & ~(3 | SMMO_WATOR_QUEUED_CREATION)) || (mode & 3) == 3) return SMMO_E_INVALID_ARG;
+  if (!w || mode < 0 || (mode & ~(3 | SMMO_WATOR_QUEUED_CREATION | SMMO_WATOR_MARKED_UPDATE)) || (mode & 3) == 3 ||
+      ((mode & SMMO_WATOR_MARKED_UPDATE) && (mode & 3)))
+    return SMMO_E_INVALID_ARG;
   w->step_kernels = mode;
   if (w->graph) { cudaGraphExecDestroy(w->graph); w->graph = nullptr; }  // captured with the old kernels
   return SMMO_OK;

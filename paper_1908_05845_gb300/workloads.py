@@ -15,6 +15,7 @@ LIFE, WATOR = 0, 1
 # how a Wa-Tor iteration is launched (smmo_world_set_step_kernels)
 FOUR_DO_ALLS, PHASED1, PHASED2 = 0, 1, 2
 QUEUED = 4  # or-ed with one of the above: creations queued and made by a launch of their own
+MARKED = 8  # or-ed with FOUR_DO_ALLS: the update runs only on the agents its prepare marked
 
 
 class WatorParams(ctypes.Structure):
@@ -84,8 +85,8 @@ class World:
             self.set_step_kernels(step_kernels)
 
     def set_step_kernels(self, mode: int):
-        """FOUR_DO_ALLS, PHASED1 or PHASED2, optionally | QUEUED (see
-        smmo_world_set_step_kernels)."""
+        """FOUR_DO_ALLS, PHASED1 or PHASED2, optionally | QUEUED, and
+        FOUR_DO_ALLS optionally | MARKED (see smmo_world_set_step_kernels)."""
         smmo.check(smmo.lib().smmo_world_set_step_kernels(self._w, int(mode)), "world_set_step_kernels")
 
     def step(self, n: int = 1):

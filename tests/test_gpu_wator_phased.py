@@ -1,8 +1,9 @@
-"""Wa-Tor with each species' prepare and update in one cooperative launch
-(grid barrier between the phases, request words kept in shared memory):
-bit-exact against the oracle in every launch mode, including warps whose
-units do not all fit the shared carry and spill it to the agents' target
-field, graph replay, and batched worlds mixing Life and Wa-Tor instances."""
+"""Wa-Tor in every step-kernel mode (four do-alls; each species' prepare and
+update in one cooperative launch with the request words kept in shared
+memory; creations queued for a launch of their own; updates run only on
+the agents their prepare marked): bit-exact against the oracle, including
+warps whose units do not all fit the shared carry, mode switches between
+steps, graph replay, and batched worlds mixing Life and Wa-Tor instances."""
 import numpy as np
 import pytest
 
@@ -10,10 +11,11 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_1908_05845_gb300 import inputs, smmo  # noqa: E402
-from paper_1908_05845_gb300.workloads import (FOUR_DO_ALLS, LIFE, PHASED1, PHASED2, QUEUED, WATOR,  # noqa: E402
-                                              WaTor, World)
+from paper_1908_05845_gb300.workloads import (FOUR_DO_ALLS, LIFE, MARKED, PHASED1, PHASED2, QUEUED,  # noqa: E402
+                                              WATOR, WaTor, World)
 
-MODES = [FOUR_DO_ALLS, PHASED1, PHASED2, FOUR_DO_ALLS | QUEUED, PHASED1 | QUEUED, PHASED2 | QUEUED]
+MODES = [FOUR_DO_ALLS, PHASED1, PHASED2, FOUR_DO_ALLS | QUEUED, PHASED1 | QUEUED, PHASED2 | QUEUED,
+         FOUR_DO_ALLS | MARKED, FOUR_DO_ALLS | MARKED | QUEUED]
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -81,6 +83,8 @@ def test_modes_switch_between_steps_and_graph_replay(orc):
         sim.step(4)
         sim.set_step_kernels(FOUR_DO_ALLS | QUEUED)
         sim.step(2)
+        sim.set_step_kernels(FOUR_DO_ALLS | MARKED)
+        sim.step(3)
         sim.set_step_kernels(PHASED2)
         sim.step(2)
         sim.capture(3)
@@ -89,7 +93,7 @@ def test_modes_switch_between_steps_and_graph_replay(orc):
         got = sim.read()
         sim.sync()
         sim.close()
-    want = orc.wator_run(W, H, seed, k, a, e, 3 + 4 + 2 + 2 + 12)
+    want = orc.wator_run(W, H, seed, k, a, e, 3 + 4 + 2 + 3 + 2 + 12)
     for g, w in zip(got, want[:3]):
         assert np.array_equal(g, w)
 
@@ -97,13 +101,14 @@ def test_modes_switch_between_steps_and_graph_replay(orc):
 def test_unknown_mode_is_rejected():
     k, a, e = inputs.wator_initial(16, 16, 1)
     sim = WaTor(16, 16, 1, k, a, e)
-    for bad in (3, 7, 8, -1):
+    for bad in (3, 7, 9, 10, 16, -1):
         with pytest.raises(smmo.SmmoError):
             sim.set_step_kernels(bad)
     sim.close()
 
 
-@pytest.mark.parametrize("mode", [FOUR_DO_ALLS, PHASED2, FOUR_DO_ALLS | QUEUED, PHASED2 | QUEUED])
+@pytest.mark.parametrize("mode", [FOUR_DO_ALLS, PHASED2, FOUR_DO_ALLS | QUEUED, PHASED2 | QUEUED,
+                                  FOUR_DO_ALLS | MARKED])
 def test_batched_life_and_wator_in_every_mode(orc, mode):
     seed = 3
     kinds, sides, init = inputs.batched_initial(seed, 24, side_min=16, ratio=10.0)
