@@ -856,7 +856,7 @@ def run_bh(args):
                       "object_updates_per_s": (e1 - e0) / t,
                       "tree_node_news_per_step": (a1 - a0) / args.steps,
                       "tree_node_deletes_per_step": (f1 - f0) / args.steps,
-                      "tree_levels_per_step": (l1 - l0) / args.steps, "tree_nodes_end": nodes,
+                      "tree_traversals_per_step": (l1 - l0) / args.steps, "tree_nodes_end": nodes,
                       "parity_10_steps_bit_exact": bool(exact),
                       "repeated_runs": {"runs": len(repeats), "steps_each": args.warmup + args.steps,
                                         "errors": [x for x in repeats if x["status"]]},

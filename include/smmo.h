@@ -666,13 +666,16 @@ typedef struct smmo_bh smmo_bh;
  * `stream`. */
 int smmo_bh_create(smmo_heap* heap, int64_t n, const float* const* cols,
                    const smmo_bh_params* p, void* stream, smmo_bh** out);
-/* nsteps steps; each step reads back one flag per 8 tree levels. */
+/* nsteps steps; asynchronous (no host round trip: each bottom-up traversal
+ * is one count of pending children and one do-all whose threads walk up the
+ * tree, each node processed by the thread that finishes its last tree-node
+ * child).  Capturable in a CUDA graph. */
 int smmo_bh_step(smmo_bh* w, int nsteps, void* stream);
 /* out5: device, 5 x n floats (x, y, vx, vy, m by id); *tree_nodes (host,
  * nullable) = live TreeNodes.  Synchronises `stream`. */
 int smmo_bh_export(smmo_bh* w, float* out5, int64_t* tree_nodes, void* stream);
 /* class ids [NodeBase, BodyNode, TreeNode] (host array of 3, nullable) and
- * tree levels processed so far (nullable). */
+ * bottom-up traversals run so far, two per step (nullable). */
 int smmo_bh_info(smmo_bh* w, int* class_ids, int64_t* levels);
 int smmo_bh_destroy(smmo_bh* w);
 

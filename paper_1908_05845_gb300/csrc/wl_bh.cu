@@ -6,9 +6,10 @@
 // A tree node covers the square [p1x, p1x + w) x [p1y, p1y + w) of the unit
 // square and splits it into quadrants (x >= mid_x) + 2 (y >= mid_y); a
 // child slot holds null, a BodyNode or a TreeNode.  One step:
-//   summaries   bottom-up frontier traversal over TreeNodes (a node joins
-//               the frontier once all its TreeNode children are done):
-//               mass and centre of gravity from the children in child order;
+//   summaries   bottom-up traversal over TreeNodes (a node is processed
+//               once all its TreeNode children are done; walks up the tree,
+//               see TreePending): mass and centre of gravity from the
+//               children in child order;
 //   force       per body, preorder depth-first traversal from the root with
 //               an explicit stack: a tree node is opened if the body lies in
 //               its square or w^2 >= theta^2 d^2, else its summary acts;
@@ -91,85 +92,120 @@ __device__ __forceinline__ void pair_acc(float xi, float yi, float xj, float yj,
 }
 
 // ---------------------------------------------------------------- traversal
-struct TreeInitFrontier {
+// Bottom-up traversals (summaries, collapse) as walks up the tree instead of
+// one launch per level: TreePending stores per tree node the number of its
+// children that are tree nodes (in the frontier byte) and marks the nodes
+// without any (done = 2) as the starts; the walk do-all processes each start
+// node, then counts down its parent's pending children, and the thread that
+// brings a parent to zero processes the parent and goes on up.  A node is
+// therefore processed once, after all its tree-node children, exactly as in
+// a level-by-level frontier traversal (Sec. 7.3), and computes the same
+// values from its children in child order.  Values written by other threads
+// in the same launch are read through L2, after the fence that follows the
+// count-down.  The walks wait for nobody.
+struct TreePending {
   using Args = BHArgs;
   __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
-    uint8_t front = 1;
+    uint8_t pending = 0;
     for (int i = 0; i < 4; ++i) {
       const uint32_t ch = *F<uint32_t>(h, c, self, T_CH + i);
-      if (ch != kNull && type_of(h, ch) == a.tree_cls) front = 0;
+      if (ch != kNull && type_of(h, ch) == a.tree_cls) ++pending;
     }
-    *F<uint8_t>(h, c, self, T_FRONT) = front;
-    *F<uint8_t>(h, c, self, T_DONE) = 0;
+    *F<uint8_t>(h, c, self, T_FRONT) = pending;
+    *F<uint8_t>(h, c, self, T_DONE) = pending == 0 ? 2 : 0;
   }
 };
 
-struct TreeAdvance {
+// Counts down the pending tree-node children of p (its frontier byte, with
+// an atomic on the byte's 32-bit word: the column starts on a 64-byte
+// boundary, and a count never goes below 0, so no borrow reaches the
+// neighbouring bytes); true for the thread that brings it to 0.
+__device__ __forceinline__ bool last_child_done(const HeapView& h, uint32_t T, uint32_t p) {
+  uint8_t* b = F<uint8_t>(h, T, p, T_FRONT);
+  unsigned int* word = reinterpret_cast<unsigned int*>(reinterpret_cast<uintptr_t>(b) & ~uintptr_t(3));
+  const uint32_t shift = (uint32_t)(reinterpret_cast<uintptr_t>(b) & 3) * 8u;
+  __threadfence();  // this node's results before the count-down
+  const uint32_t old = atomicSub(word, 1u << shift);
+  if (((old >> shift) & 0xFFu) != 1u) return false;
+  __threadfence();  // the other children's results before the parent's reads
+  return true;
+}
+
+// Mass and centre of gravity of tree node `self` from its children.
+__device__ __forceinline__ void summarize(const HeapView& h, uint32_t T, uint32_t self) {
+  float ms = 0.0f, sx = 0.0f, sy = 0.0f;
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t ch = Lcg<uint32_t>(h, T, self, T_CH + i);
+    if (ch == kNull) continue;
+    const uint32_t t = type_of(h, ch);
+    const float cm = Lcg<float>(h, t, ch, C_M), cx = Lcg<float>(h, t, ch, C_PX), cy = Lcg<float>(h, t, ch, C_PY);
+    ms = fa(ms, cm);
+    sx = fa(sx, fm(cm, cx));
+    sy = fa(sy, fm(cm, cy));
+  }
+  *F<float>(h, T, self, C_M) = ms;
+  *F<float>(h, T, self, C_PX) = ms > 0.0f ? __fdiv_rn(sx, ms) : 0.0f;
+  *F<float>(h, T, self, C_PY) = ms > 0.0f ? __fdiv_rn(sy, ms) : 0.0f;
+  *F<uint8_t>(h, T, self, T_DONE) = 1;
+}
+
+struct TreeSummaryWalk {
   using Args = BHArgs;
   __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
-    uint8_t front = 0;
-    if (!*F<uint8_t>(h, c, self, T_DONE)) {
-      front = 1;
-      for (int i = 0; i < 4; ++i) {
-        const uint32_t ch = *F<uint32_t>(h, c, self, T_CH + i);
-        if (ch != kNull && type_of(h, ch) == a.tree_cls && !*F<uint8_t>(h, a.tree_cls, ch, T_DONE)) front = 0;
-      }
+    if (*F<uint8_t>(h, c, self, T_DONE) != 2) return;  // not a start of a walk
+    uint32_t node = self;
+    for (int depth = 0; depth <= kMaxDepth + 1; ++depth) {
+      summarize(h, c, node);
+      const uint32_t p = Lcg<uint32_t>(h, c, node, C_PARENT);
+      if (p == kNull || !last_child_done(h, c, p)) return;
+      node = p;
     }
-    *F<uint8_t>(h, c, self, T_FRONT) = front;
+    set_error(h, SMMO_E_BOUNDS, kTagDepth | self);  // deeper than any tree the insertion builds
   }
 };
 
-struct TreeSummary {
-  using Args = BHArgs;
-  __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
-    if (!*F<uint8_t>(h, c, self, T_FRONT)) return;
-    float ms = 0.0f, sx = 0.0f, sy = 0.0f;
-    for (int i = 0; i < 4; ++i) {
-      const uint32_t ch = *F<uint32_t>(h, c, self, T_CH + i);
-      if (ch == kNull) continue;
-      const uint32_t t = type_of(h, ch);
-      const float cm = *F<float>(h, t, ch, C_M), cx = *F<float>(h, t, ch, C_PX), cy = *F<float>(h, t, ch, C_PY);
-      ms = fa(ms, cm);
-      sx = fa(sx, fm(cm, cx));
-      sy = fa(sy, fm(cm, cy));
-    }
-    *F<float>(h, c, self, C_M) = ms;
-    *F<float>(h, c, self, C_PX) = ms > 0.0f ? __fdiv_rn(sx, ms) : 0.0f;
-    *F<float>(h, c, self, C_PY) = ms > 0.0f ? __fdiv_rn(sy, ms) : 0.0f;
-    *F<uint8_t>(h, c, self, T_DONE) = 1;
-    *F<uint8_t>(h, c, self, T_FRONT) = 0;
+// Collapse of tree node `self` (all its tree-node children collapsed): a
+// node without children is unlinked and deleted, one whose only child is a
+// body is replaced by that body; returns its parent (kNull for the root).
+__device__ __forceinline__ uint32_t collapse_node(const HeapView& h, const BHArgs& a, uint32_t T, uint32_t self) {
+  int n = 0;
+  uint32_t single = kNull;
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t ch = Lcg<uint32_t>(h, T, self, T_CH + i);
+    if (ch != kNull) { ++n; single = ch; }
   }
-};
+  const uint32_t parent = Lcg<uint32_t>(h, T, self, C_PARENT);
+  if (parent != kNull) {
+    const int idx = Lcg<int8_t>(h, T, self, C_CIDX);
+    uint32_t* slot = F<uint32_t>(h, T, parent, T_CH + idx);
+    if (n == 0) {  // empty: unlink and delete
+      *slot = kNull;
+      smmo_delete(h, self);
+      return parent;
+    }
+    if (n == 1 && type_of(h, single) == a.body_cls) {  // single body: it takes our slot
+      *F<uint32_t>(h, a.body_cls, single, C_PARENT) = parent;
+      *F<int8_t>(h, a.body_cls, single, C_CIDX) = (int8_t)idx;
+      *slot = single;
+      smmo_delete(h, self);
+      return parent;
+    }
+  }
+  *F<uint8_t>(h, T, self, T_DONE) = 1;
+  return parent;
+}
 
-struct TreeCollapse {
+struct TreeCollapseWalk {
   using Args = BHArgs;
   __device__ static void run(const HeapView& h, const Args& a, uint32_t c, uint32_t self) {
-    if (!*F<uint8_t>(h, c, self, T_FRONT)) return;
-    *F<uint8_t>(h, c, self, T_FRONT) = 0;
-    int n = 0;
-    uint32_t single = kNull;
-    for (int i = 0; i < 4; ++i) {
-      const uint32_t ch = *F<uint32_t>(h, c, self, T_CH + i);
-      if (ch != kNull) { ++n; single = ch; }
+    if (*F<uint8_t>(h, c, self, T_DONE) != 2) return;  // not a start of a walk
+    uint32_t node = self;
+    for (int depth = 0; depth <= kMaxDepth + 1; ++depth) {
+      const uint32_t p = collapse_node(h, a, c, node);
+      if (p == kNull || !last_child_done(h, c, p)) return;
+      node = p;
     }
-    const uint32_t parent = *F<uint32_t>(h, c, self, C_PARENT);
-    if (parent != kNull) {
-      const int idx = *F<int8_t>(h, c, self, C_CIDX);
-      uint32_t* slot = F<uint32_t>(h, c, parent, T_CH + idx);
-      if (n == 0) {  // empty: unlink and delete
-        *slot = kNull;
-        smmo_delete(h, self);
-        return;
-      }
-      if (n == 1 && type_of(h, single) == a.body_cls) {  // single body: it takes our slot
-        *F<uint32_t>(h, a.body_cls, single, C_PARENT) = parent;
-        *F<int8_t>(h, a.body_cls, single, C_CIDX) = (int8_t)idx;
-        *slot = single;
-        smmo_delete(h, self);
-        return;
-      }
-    }
-    *F<uint8_t>(h, c, self, T_DONE) = 1;
+    set_error(h, SMMO_E_BOUNDS, kTagDepth | self);
   }
 };
 
@@ -356,8 +392,8 @@ struct BodyExport {
 }  // namespace
 
 const smmo::MethodEntry g_methods_bh[] = {
-    SMMO_METHOD("bh.tree_init_frontier", TreeInitFrontier), SMMO_METHOD("bh.tree_advance", TreeAdvance),
-    SMMO_METHOD("bh.tree_summary", TreeSummary), SMMO_METHOD("bh.tree_collapse", TreeCollapse),
+    SMMO_METHOD("bh.tree_pending", TreePending), SMMO_METHOD("bh.tree_summary", TreeSummaryWalk),
+    SMMO_METHOD("bh.tree_collapse", TreeCollapseWalk),
     SMMO_METHOD("bh.body_force", BodyForce), SMMO_METHOD("bh.body_update", BodyUpdate),
     SMMO_METHOD("bh.body_remove", BodyRemove), SMMO_METHOD("bh.body_insert", BodyInsert),
     SMMO_METHOD("bh.body_export", BodyExport)};
@@ -367,9 +403,8 @@ struct smmo_bh {
   smmo_heap* heap = nullptr;
   int cls_base = -1, cls_body = -1, cls_tree = -1;
   uint32_t n0 = 0;
-  uint8_t* d_root_done = nullptr;  // the root's done flag inside the heap
   BHArgs args{};
-  int64_t levels = 0;  // traversal levels run (statistics)
+  int64_t levels = 0;  // bottom-up traversals run (statistics)
 };
 
 namespace {
@@ -379,27 +414,16 @@ int pdo(smmo_bh* w, int cls, method_launch_fn fn, const BHArgs& a, cudaStream_t 
   return st;
 }
 
-// Bottom-up traversal: init, then groups of 8 (process, advance) levels
-// until the root is done (extra levels after that change nothing).  With
-// `fixed` (the process step creates and deletes no tree node, as for the
-// summaries) one enumeration serves the whole traversal.
-int bottom_up(smmo_bh* w, method_launch_fn process, cudaStream_t s, bool fixed) {
+// Bottom-up traversal: the pending counts, then one walk do-all over the
+// same snapshot (the count creates and deletes nothing; the walk of the
+// collapse deletes tree nodes, which it never visits again).  Two launches
+// and one enumeration, no host round trip.
+int bottom_up(smmo_bh* w, method_launch_fn walk, cudaStream_t s) {
   const BHArgs& a = w->args;
-  int st = pdo(w, w->cls_tree, &launch_do_all<TreeInitFrontier>, a, s);
-  for (int group = 0; group < 64 && !st; ++group) {
-    for (int k = 0; k < 8 && !st; ++k) {
-      st = pdo(w, w->cls_tree, process, a, s, fixed);
-      if (!st) st = pdo(w, w->cls_tree, &launch_do_all<TreeAdvance>, a, s, fixed);
-      ++w->levels;
-    }
-    if (st) break;
-    uint8_t done = 0;
-    cudaError_t e = cudaMemcpyAsync(&done, w->d_root_done, 1, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (done) return SMMO_OK;
-  }
-  return st ? st : SMMO_E_TIMEOUT;
+  int st = pdo(w, w->cls_tree, &launch_do_all<TreePending>, a, s);
+  if (!st) st = pdo(w, w->cls_tree, walk, a, s, true);
+  if (!st) ++w->levels;
+  return st;
 }
 }  // namespace
 
@@ -465,10 +489,6 @@ int smmo_bh_create(smmo_heap* heap, int64_t n, const float* const* cols, const s
   if (e != cudaSuccess) st = cuda_status(e);
   if (st) { smmo_bh_destroy(w); return st; }
   a.root = root;
-  {
-    const ClassLayout& T = heap->classes[w->cls_tree].layout;
-    w->d_root_done = heap->view.data + (size_t)(root >> 6) * heap->view.block_bytes + T.col_off[T_DONE] + (root & 63);
-  }
   // bodies: parent null, fields from the caller's columns, id = index
   std::vector<void*> bd(10, nullptr);
   e = cudaSuccess;
@@ -502,14 +522,14 @@ int smmo_bh_step(smmo_bh* w, int nsteps, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const BHArgs& a = w->args;
   for (int k = 0; k < nsteps; ++k) {
-    int st = bottom_up(w, &launch_do_all<TreeSummary>, s, true);
+    int st = bottom_up(w, &launch_do_all<TreeSummaryWalk>, s);
     // no body is created or deleted in a step: one enumeration of the
     // bodies serves the four body do-alls
     if (!st) st = pdo(w, w->cls_body, &launch_do_all<BodyForce>, a, s);
     if (!st) st = pdo(w, w->cls_body, &launch_do_all<BodyUpdate>, a, s, true);
     if (!st) st = pdo(w, w->cls_body, &launch_do_all<BodyRemove>, a, s, true);
     if (!st) st = pdo(w, w->cls_body, &launch_do_all<BodyInsert>, a, s, true);
-    if (!st) st = bottom_up(w, &launch_do_all<TreeCollapse>, s, false);
+    if (!st) st = bottom_up(w, &launch_do_all<TreeCollapseWalk>, s);
     if (st) return st;
   }
   return SMMO_OK;

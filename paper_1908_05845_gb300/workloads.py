@@ -378,6 +378,7 @@ class BarnesHut:
         return dict(zip(("x", "y", "vx", "vy", "m"), o)), tn.value
 
     def levels(self) -> int:
+        """Bottom-up tree traversals run so far (two per step)."""
         lv = ctypes.c_int64()
         smmo.check(smmo.lib().smmo_bh_info(self._w, None, ctypes.byref(lv)), "bh_info")
         return lv.value
