@@ -889,6 +889,132 @@ int world_steps(smmo_world* w, int nsteps, cudaStream_t s, PhaseTimer* pt) {
   }
   return SMMO_OK;
 }
+// ----------------------------------------------------------- world creation
+// The agents of the initial state, gathered on the device: a class code per
+// cell (0 none, 1 Fish, 2 Shark, 3 Alive, 4 Candidate, from the kind of the
+// cell's instance and init_kind), counted per chunk of kGatherChunk cells,
+// scanned, and scattered in ascending cell order into the SOA columns of
+// each class, so that bulk creation places the objects exactly as a host
+// loop over the cells would.
+constexpr uint32_t kGatherChunk = 1024;  // 256 threads x 4 cells
+
+__device__ __forceinline__ int agent_code(const Inst* tab, uint32_t n_inst, const int8_t* kind, uint64_t g) {
+  const int k = kind[g];
+  if (k != 1 && k != 2) return 0;
+  return instance_at(tab, n_inst, (uint32_t)g)->kind == SMMO_WORLD_WATOR ? k : 2 + k;
+}
+
+__global__ void __launch_bounds__(256) k_agent_count(const Inst* tab, uint32_t n_inst, const int8_t* kind, uint64_t N,
+                                                     uint32_t* counts, uint32_t nchunks) {
+  __shared__ uint32_t c[4];
+  if (threadIdx.x < 4) c[threadIdx.x] = 0u;
+  __syncthreads();
+  const uint64_t base = (uint64_t)blockIdx.x * kGatherChunk;
+  for (int r = 0; r < 4; ++r) {
+    const uint64_t g = base + (uint64_t)r * 256u + threadIdx.x;
+    if (g < N) {
+      const int code = agent_code(tab, n_inst, kind, g);
+      if (code) atomicAdd(&c[code - 1], 1u);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) counts[(size_t)threadIdx.x * nchunks + blockIdx.x] = c[threadIdx.x];
+}
+
+// Exclusive scan of each code's chunk counts in place (one CTA); totals in tot.
+__global__ void __launch_bounds__(1024) k_agent_scan(uint32_t* counts, uint32_t nchunks, uint32_t* tot) {
+  __shared__ uint32_t sc[1024];
+  for (int code = 0; code < 4; ++code) {
+    uint32_t* cc = counts + (size_t)code * nchunks;
+    uint32_t run = 0;
+    for (uint32_t b0 = 0; b0 < nchunks; b0 += 1024) {
+      const uint32_t i = b0 + threadIdx.x;
+      const uint32_t v = i < nchunks ? cc[i] : 0u;
+      sc[threadIdx.x] = v;
+      __syncthreads();
+      for (uint32_t o = 1; o < 1024; o <<= 1) {
+        const uint32_t x = threadIdx.x >= o ? sc[threadIdx.x - o] : 0u;
+        __syncthreads();
+        sc[threadIdx.x] += x;
+        __syncthreads();
+      }
+      if (i < nchunks) cc[i] = run + sc[threadIdx.x] - v;
+      run += sc[1023];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) tot[code] = run;
+    __syncthreads();
+  }
+}
+
+struct AgentCols {
+  int32_t* cell[4];    // Fish, Shark, Alive, Candidate
+  int32_t* target[2];  // Fish, Shark
+  int16_t* age[2];     // Fish, Shark
+  int16_t* energy;     // Shark
+  uint8_t* act[2];     // Alive, Candidate
+  uint8_t* isnew;      // Alive
+  uint16_t* blocked;   // Alive
+};
+
+__global__ void __launch_bounds__(256) k_agent_scatter(const Inst* tab, uint32_t n_inst, const int8_t* kind,
+                                                       const int16_t* age, const int16_t* energy,
+                                                       const uint8_t* state, uint64_t N, const uint32_t* offs,
+                                                       uint32_t nchunks, AgentCols c) {
+  __shared__ uint32_t wsum[4][8], run[4];
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x < 4) run[threadIdx.x] = offs[(size_t)threadIdx.x * nchunks + blockIdx.x];
+  __syncthreads();
+  const uint64_t base = (uint64_t)blockIdx.x * kGatherChunk;
+  for (int r = 0; r < 4; ++r) {
+    const uint64_t g = base + (uint64_t)r * 256u + threadIdx.x;
+    const int code = g < N ? agent_code(tab, n_inst, kind, g) : 0;
+    uint32_t rank = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, code == k + 1);
+      if (code == k + 1) rank = __popc(m & ((1u << lane) - 1));
+      if (lane == 0) wsum[k][w] = __popc(m);
+    }
+    __syncthreads();
+    if (code) {
+      const int k = code - 1;
+      uint32_t pos = run[k] + rank;
+      for (uint32_t v = 0; v < w; ++v) pos += wsum[k][v];
+      const int16_t a0 = age ? age[g] : (int16_t)0;
+      c.cell[k][pos] = (int32_t)g;
+      if (k < 2) {
+        c.target[k][pos] = (int32_t)g;
+        c.age[k][pos] = a0;
+        if (k == 1) c.energy[pos] = energy ? energy[g] : (int16_t)0;
+      } else {
+        c.act[k - 2][pos] = 0;
+        if (k == 2) {
+          c.isnew[pos] = state ? state[g] : (uint8_t)0;
+          c.blocked[pos] = (uint16_t)a0;
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+      uint32_t t = 0;
+      for (int v = 0; v < 8; ++v) t += wsum[threadIdx.x][v];
+      run[threadIdx.x] += t;
+    }
+    __syncthreads();
+  }
+}
+
+// Agents with more than one agent on their cell: sum of (count - 1) over the
+// cells (the allocating export's duplicate count), warp-aggregated.
+__global__ void k_count_extra(const uint32_t* cnt, uint64_t N, unsigned long long* err) {
+  unsigned long long extra = 0;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N; g += (uint64_t)gridDim.x * blockDim.x)
+    if (cnt[g] > 1u) extra += cnt[g] - 1u;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) extra += __shfl_xor_sync(0xFFFFFFFFu, extra, o);
+  if ((threadIdx.x & 31) == 0 && extra) atomicAdd(err, extra);
+}
 }  // namespace
 
 extern "C" {
@@ -1018,62 +1144,58 @@ int smmo_world_create_batch(smmo_heap* heap, const smmo_instance_desc* inst, int
   a.block = 0;
   a.fish_breed = w->p.fish_breed; a.shark_breed = w->p.shark_breed; a.starve = w->p.starve;
   a.breed_strict = w->p.breed_strict;
-  // agents: gather the per-kind cell lists on the host (setup only)
-  std::vector<int8_t> hk(N);
-  std::vector<int16_t> ha(N, 0), he(N, 0);
-  std::vector<uint8_t> hs(N, 0);
-  e = cudaMemcpyAsync(hk.data(), init_kind, N, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && init_age) e = cudaMemcpyAsync(ha.data(), init_age, N * 2, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && init_energy) e = cudaMemcpyAsync(he.data(), init_energy, N * 2, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && init_state) e = cudaMemcpyAsync(hs.data(), init_state, N, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) { smmo_world_destroy(w); return cuda_status(e); }
-  struct Pop {
-    std::vector<int32_t> cell, target;
-    std::vector<int16_t> age, energy;
-    std::vector<uint8_t> act, isnew;
-    std::vector<uint16_t> blocked;
-  };
-  Pop fish, shark, alive, cand;
-  for (int i = 0; i < n_inst; ++i) {
-    const uint64_t b = w->base[i], n = (uint64_t)w->W[i] * w->H[i];
-    for (uint64_t g = b; g < b + n; ++g) {
-      const int k = hk[g];
-      if (k == 0) continue;
-      if (w->kind[i] == SMMO_WORLD_WATOR) {
-        Pop& P = k == 1 ? fish : shark;
-        P.cell.push_back((int32_t)g); P.target.push_back((int32_t)g);
-        P.age.push_back(ha[g]); P.energy.push_back(he[g]);
-      } else {
-        Pop& P = k == 1 ? alive : cand;
-        P.cell.push_back((int32_t)g); P.act.push_back(0); P.isnew.push_back(k == 1 ? hs[g] : 0);
-        P.blocked.push_back(k == 1 ? (uint16_t)ha[g] : 0);
-      }
-    }
+  // agents: gathered per class on the device in ascending cell order (see
+  // k_agent_scatter), then created by one bulk creation per class
+  const uint32_t nchunks = (uint32_t)((N + kGatherChunk - 1) / kGatherChunk);
+  uint32_t* counts = nullptr;
+  uint32_t tot[4] = {0, 0, 0, 0};
+  e = cudaMallocAsync(&counts, ((size_t)4 * nchunks + 4) * sizeof(uint32_t), s);
+  if (e == cudaSuccess) {
+    k_agent_count<<<nchunks, 256, 0, s>>>(heap->d_inst, (uint32_t)n_inst, init_kind, N, counts, nchunks);
+    k_agent_scan<<<1, 1024, 0, s>>>(counts, nchunks, counts + (size_t)4 * nchunks);
+    e = cudaGetLastError();
   }
-  auto upload = [&](int cls, std::vector<const void*> cols_h, std::vector<size_t> esz, size_t n) -> int {
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(tot, counts + (size_t)4 * nchunks, sizeof(tot), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  AgentCols cols;
+  memset(&cols, 0, sizeof(cols));
+  std::vector<void*> tmp;
+  auto col = [&](size_t bytes) -> void* {
+    void* q = nullptr;
+    if (e == cudaSuccess && bytes) e = cudaMallocAsync(&q, bytes, s);
+    if (q) tmp.push_back(q);
+    return q;
+  };
+  for (int k = 0; k < 4; ++k) cols.cell[k] = (int32_t*)col((size_t)tot[k] * 4);
+  for (int k = 0; k < 2; ++k) {
+    cols.target[k] = (int32_t*)col((size_t)tot[k] * 4);
+    cols.age[k] = (int16_t*)col((size_t)tot[k] * 2);
+    cols.act[k] = (uint8_t*)col((size_t)tot[2 + k]);
+  }
+  cols.energy = (int16_t*)col((size_t)tot[1] * 2);
+  cols.isnew = (uint8_t*)col((size_t)tot[2]);
+  cols.blocked = (uint16_t*)col((size_t)tot[2] * 2);
+  if (e == cudaSuccess) {
+    k_agent_scatter<<<nchunks, 256, 0, s>>>(heap->d_inst, (uint32_t)n_inst, init_kind, init_age, init_energy,
+                                            init_state, N, counts, nchunks, cols);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) st = cuda_status(e);
+  auto create = [&](int cls, std::vector<const void*> src, uint32_t n) -> int {
     if (n == 0) return SMMO_OK;
-    std::vector<void*> d(cols_h.size(), nullptr);
-    cudaError_t ee = cudaSuccess;
-    for (size_t k = 0; k < cols_h.size() && ee == cudaSuccess; ++k) {
-      ee = cudaMallocAsync(&d[k], n * esz[k], s);
-      if (ee == cudaSuccess) ee = cudaMemcpyAsync(d[k], cols_h[k], n * esz[k], cudaMemcpyHostToDevice, s);
-    }
-    int r = ee == cudaSuccess ? smmo_bulk_new(heap, cls, (int64_t)n, (const void* const*)d.data(), nullptr, nullptr, stream)
-                              : cuda_status(ee);
-    for (void* p : d) if (p) cudaFreeAsync(p, s);
-    return r;
+    return smmo_bulk_new(heap, cls, (int64_t)n, src.data(), nullptr, nullptr, stream);
   };
   if (!st && w->nw) {
-    st = upload(w->cls_fish, {fish.cell.data(), fish.target.data(), fish.age.data()}, {4, 4, 2}, fish.cell.size());
-    if (!st) st = upload(w->cls_shark, {shark.cell.data(), shark.target.data(), shark.age.data(), shark.energy.data()},
-                         {4, 4, 2, 2}, shark.cell.size());
+    st = create(w->cls_fish, {cols.cell[0], cols.target[0], cols.age[0]}, tot[0]);
+    if (!st) st = create(w->cls_shark, {cols.cell[1], cols.target[1], cols.age[1], cols.energy}, tot[1]);
   }
   if (!st && w->nl) {
-    st = upload(w->cls_alive, {alive.cell.data(), alive.act.data(), alive.isnew.data(), alive.blocked.data()},
-                {4, 1, 1, 2}, alive.cell.size());
-    if (!st) st = upload(w->cls_cand, {cand.cell.data(), cand.act.data()}, {4, 1}, cand.cell.size());
+    st = create(w->cls_alive, {cols.cell[2], cols.act[0], cols.isnew, cols.blocked}, tot[2]);
+    if (!st) st = create(w->cls_cand, {cols.cell[3], cols.act[1]}, tot[3]);
   }
+  for (void* q : tmp) cudaFreeAsync(q, s);
+  if (counts) cudaFreeAsync(counts, s);
   if (!st && w->nw) st = pdo(w, w->cls_wagent, &launch_do_all<Link>, a, s);
   if (!st && w->nl) st = pdo(w, w->cls_lagent, &launch_do_all<Link>, a, s);
   if (!st) { e = cudaStreamSynchronize(s); if (e != cudaSuccess) st = cuda_status(e); }
@@ -1215,11 +1337,11 @@ int smmo_world_export(smmo_world* w, int8_t* kind, int16_t* age, int16_t* energy
   if (w->nw) st = pdo(w, w->cls_wagent, &launch_do_all<Export>, a, s);
   if (!st && w->nl) st = pdo(w, w->cls_lagent, &launch_do_all<Export>, a, s);
   if (!st) st = pdo(w, w->cls_cell, &launch_do_all<CheckCells>, a, s);
-  // cells holding two agents
-  std::vector<uint32_t> hc(N);
+  // agents beyond the first on a cell, counted on the device
   unsigned long long herr = 0;
   if (!st) {
-    e = cudaMemcpyAsync(hc.data(), cnt, N * 4, cudaMemcpyDeviceToHost, s);
+    k_count_extra<<<w->heap->num_sms * 8, 256, 0, s>>>(cnt, N, err);
+    e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) st = cuda_status(e);
@@ -1227,7 +1349,6 @@ int smmo_world_export(smmo_world* w, int8_t* kind, int16_t* age, int16_t* energy
   cudaFreeAsync(cnt, s);
   cudaFreeAsync(err, s);
   if (st) return st;
-  for (uint64_t g = 0; g < N; ++g) if (hc[g] > 1) herr += hc[g] - 1;
   if (errors) *errors = (int64_t)herr;
   return SMMO_OK;
 }
