@@ -28,6 +28,15 @@
 #ifndef SMMO_DOALL_MIN_CTAS
 #define SMMO_DOALL_MIN_CTAS 3
 #endif
+// warp_new: the first nearby round that may end the search when its 32
+// blocks have no free slot, and the number of missing slots from which the
+// warp takes a fresh block instead of refilling one leader at a time
+#ifndef SMMO_NEAR_STOP_FROM
+#define SMMO_NEAR_STOP_FROM 2
+#endif
+#ifndef SMMO_FRESH_MIN
+#define SMMO_FRESH_MIN 16
+#endif
 #define SMMO_MAX_LEVELS 6
 #define SMMO_NSHARD 32
 #define SMMO_CTR_SLOW 0
@@ -429,6 +438,20 @@ static __device__ __forceinline__ unsigned long long reserve_in(const HeapView& 
   return 0;
 }
 
+// A block from the free bitmap, initialised for class c and full for the
+// caller (initialize_block, Alg. 5.10: no slot is open to others until the
+// caller frees what it does not use).  -1 if no block is free.
+static __device__ __forceinline__ int take_fresh_block(const HeapView& h, uint32_t c, uint32_t seed) {
+  const int fb = bm_clear_any(h, bm_free(), seed ^ 0x5bd1e995u);
+  if (fb < 0) return -1;
+  atomicExch(h.block_type + fb, c);
+  __threadfence();
+  atomicExch(h.alloc_bm + fb, kAll);
+  bm_set(h, bm_alloc(h, c), (uint32_t)fb);
+  count(h, SMMO_CTR_SLOW, 1);
+  return fb;
+}
+
 // Finds room for a warp's cache: (0) near the hint (the block whose objects
 // the warp is running a method on): the hint block itself if it is of class
 // c and has a free slot, else a defragmentation candidate among the 64
@@ -466,13 +489,8 @@ static __device__ __forceinline__ unsigned long long refill_reserve(const HeapVi
     if (got) { *bid_out = (uint32_t)b; return got; }
   }
   count(h, SMMO_CTR_LOOKUP_MISS, 1);
-  const int fb = bm_clear_any(h, bm_free(), seed ^ 0x5bd1e995u);
+  const int fb = take_fresh_block(h, c, seed);
   if (fb >= 0) {
-    atomicExch(h.block_type + fb, c);
-    __threadfence();
-    atomicExch(h.alloc_bm + fb, kAll);
-    bm_set(h, bm_alloc(h, c), (uint32_t)fb);
-    count(h, SMMO_CTR_SLOW, 1);
     *bid_out = (uint32_t)fb;
     return __ldg(&h.cls[c].capmask);
   }
@@ -621,8 +639,10 @@ __device__ __forceinline__ uint32_t smmo_new(const HeapView& h, uint32_t c) {
 // one round of atomicOr reservations, one round of type re-checks (a block
 // re-initialised to another class in between is rolled back, Alg. 5.1),
 // then the block-state changes of the blocks that became full or left the
-// candidates (as reserve_in).  A leader-at-a-time refill (smmo_new) serves
-// what is still missing, e.g. when every nearby block is full.
+// candidates (as reserve_in).  After the hint's own word, a round whose 32
+// blocks have no free slot ends the search; if SMMO_FRESH_MIN or more slots
+// are still missing the warp takes a fresh block (its surplus goes to the
+// warp's cache), and a leader-at-a-time refill (smmo_new) serves the rest.
 __device__ __forceinline__ uint32_t warp_new(const HeapView& h, uint32_t c, uint32_t need) {
   const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   WarpAllocCache& wc = g_wcache[w];
@@ -655,6 +675,7 @@ __device__ __forceinline__ uint32_t warp_new(const HeapView& h, uint32_t c, uint
       const bool ok = cand < h.num_blocks && __ldcg(h.block_type + cand) == c;
       const unsigned long long freeb = ok ? ~ld_cg(h.alloc_bm + cand) : 0ull;
       const uint32_t bid = freeb ? cand : kNull;
+      if (r >= SMMO_NEAR_STOP_FROM && __ballot_sync(0xFFFFFFFFu, freeb != 0ull) == 0u) break;  // full around: stop
       // the lowest free slots, in lane order, until rem are covered
       const uint32_t nf = (uint32_t)__popcll(freeb);
       uint32_t incl = nf;
@@ -710,7 +731,28 @@ __device__ __forceinline__ uint32_t warp_new(const HeapView& h, uint32_t c, uint
       got_n += total;
     }
   }
-  // (3) what is still missing, one leader at a time
+  // (3) SMMO_FRESH_MIN or more still missing (a full neighbourhood, as in a
+  // birth wave): one fresh block for the warp, the surplus kept in its cache
+  // (the cache is empty here: step (1) found fewer slots than needed)
+  if (need - got_n >= SMMO_FRESH_MIN) {
+    int fb = -1;
+    if (lane == 0) fb = take_fresh_block(h, c, mix32(((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 0x9E3779B9u + got_n));
+    fb = __shfl_sync(0xFFFFFFFFu, fb, 0);
+    if (fb >= 0) {
+      const unsigned long long capm = __ldg(&h.cls[c].capmask);
+      const unsigned long long mine = lowest_set_bits(capm, need - got_n);
+      const uint32_t k = (uint32_t)__popcll(mine);
+      if (lane >= got_n && lane - got_n < k) result = ((uint32_t)fb << 6) | (uint32_t)nth_set_bit64(mine, lane - got_n);
+      if (lane == 0) {
+        wc.bits[c] = capm & ~mine;
+        wc.bid[c] = (uint32_t)fb;
+        count(h, SMMO_CTR_ALLOC(c), k);
+      }
+      got_n += k;
+    }
+    __syncwarp();
+  }
+  // (4) what is still missing, one leader at a time
   if (got_n < need && lane >= got_n && lane < need) result = smmo_new(h, c);
   __syncwarp();
   return lane < need ? result : kNull;
