@@ -598,11 +598,11 @@ def run_batched(args):
     n_inst = args.instances
     kinds, sides, init = batched_init(SEED, n_inst)
     total = int(np.sum(sides.astype(np.int64) ** 2))
-    sample = np.arange(0, n_inst, 8)
-    sk, ss = kinds[sample], sides[sample]
     offs = np.concatenate([[0], np.cumsum(sides.astype(np.int64) ** 2)])
-    samp_init = tuple(np.concatenate([x[offs[i]:offs[i + 1]] for i in sample]) for x in init)
-    cfg, _ = autotune.tune("batched_life_wator", sk, ss, SEED, samp_init, use_cache=not args.retune)
+    # tuned on the full set of instances (a sample of them ranked the
+    # launch shapes differently from the full world)
+    cfg, _ = autotune.tune("batched_life_wator_%d" % n_inst, kinds, sides, SEED, init, steps=10, warm=3,
+                           use_cache=not args.retune)
     stream = torch.cuda.Stream()
     res = {}
     with torch.cuda.stream(stream):

@@ -4,8 +4,9 @@ Searches block capacity (through the block data segment size: 320 bytes
 gives the cells N_T = 32, 640 bytes N_T = 64), threads per CTA and
 CTAs per SM of the persistent do-all grid over their full grid, then the
 fan-out of the hierarchical bitmaps (32 or 64 bits per container) at the
-best of those, by timing a few steps of a world built from a sample of the
-instances with CUDA events.  Results are cached in a JSON file keyed by GPU
+best of those, by timing a few steps of a world built from the given
+instances (the bench passes all of them) with CUDA events.  Results are
+cached in a JSON file keyed by GPU
 name, workload and a hash of the library's sources (a rebuilt library is
 tuned again).  Every choice computes the same result (tested), so tuning
 never changes what the simulation does.
@@ -74,7 +75,7 @@ def time_world(cfg: dict, kinds, sides, seed, init, steps: int = 8, warm: int = 
 
 
 def tune(workload: str, kinds, sides, seed, init, space=SPACE, steps: int = 8, use_cache=True,
-         extra=FANOUT):
+         extra=FANOUT, warm: int = 2):
     """Best heap config (dict) for the given instance sample: the grid of
     `space`, then each parameter of `extra` in turn at the best point."""
     cache = _load()
@@ -84,7 +85,7 @@ def tune(workload: str, kinds, sides, seed, init, space=SPACE, steps: int = 8, u
     best, best_ms, table = None, None, []
     for vals in itertools.product(*space.values()):
         cfg = dict(zip(space.keys(), vals))
-        ms = time_world(cfg, kinds, sides, seed, init, steps)
+        ms = time_world(cfg, kinds, sides, seed, init, steps, warm)
         table.append((cfg, ms))
         if best_ms is None or ms < best_ms:
             best, best_ms = cfg, ms
@@ -95,7 +96,7 @@ def tune(workload: str, kinds, sides, seed, init, space=SPACE, steps: int = 8, u
             if v == choices[0]:  # the default, already timed as `best`
                 best = cfg
                 continue
-            ms = time_world(cfg, kinds, sides, seed, init, steps)
+            ms = time_world(cfg, kinds, sides, seed, init, steps, warm)
             table.append((cfg, ms))
             if ms < best_ms:
                 best, best_ms = cfg, ms

@@ -591,36 +591,47 @@ struct AliveUpdate {
     if (*fld<uint8_t>(h, self, a.a_isnew)) {
       // create Candidates on empty surrounding cells; the creator of an empty
       // cell e is the first new Alive of e's neighbourhood in scan order.
-      // Kinds read here: K_NEW never changes during this do-all, and only
-      // the creator of e writes e, so what the others read does not matter.
+      // The kinds of the 5 x 5 window around g are read once (bit 5 a + b
+      // for offset (a - 2, b - 2), so increasing bit numbers are the scan
+      // order, dx outer, dy inner) and every decision is taken from them:
+      // K_NEW never changes during this do-all, a cell turns neither empty
+      // nor new in it, and only the creator of e writes e, so a kind read
+      // earlier gives the same decisions as one read at the time.  The first
+      // new Alive around e is the lowest set bit of the new-Alive bits under
+      // e's 3 x 3 mask; W, H >= 3, so of the offsets -2..2 only (0, 0) (bit
+      // 12) is g itself.
       const Inst* in = find_inst(h, g);
       const uint32_t lc = g - in->cell_base, W = in->W, H = in->H;
       uint32_t x, y;
       cell_xy(in, lc, &x, &y);
+      uint32_t isnew = 0, isempty = 0;
+#pragma unroll
+      for (int ia = 0; ia < 5; ++ia) {
+        const int xv = (int)x + ia - 2;
+        const uint32_t col = (uint32_t)(xv < 0 ? xv + (int)W : (xv >= (int)W ? xv - (int)W : xv));
+#pragma unroll
+        for (int ib = 0; ib < 5; ++ib) {
+          const int yv = (int)y + ib - 2;
+          const uint32_t row = (uint32_t)(yv < 0 ? yv + (int)H : (yv >= (int)H ? yv - (int)H : yv));
+          const uint8_t k = *a.cells.col<uint8_t>(in->cell_base + row * W + col, a.kind_off);
+          isnew |= (uint32_t)(k == K_NEW) << (5 * ia + ib);
+          isempty |= (uint32_t)(k == K_EMPTY) << (5 * ia + ib);
+        }
+      }
+      constexpr uint32_t kBlock3 = 0x7u | (0x7u << 5) | (0x7u << 10);  // 3 x 3 at offset (-2, -2)
       for (int dx = -1; dx <= 1; ++dx)
         for (int dy = -1; dy <= 1; ++dy) {
-          const uint32_t el = torus8(x, y, dx, dy, W, H);
-          const uint32_t e = in->cell_base + el;
-          if (*a.cells.col<uint8_t>(e, a.kind_off) != K_EMPTY) continue;
-          uint32_t ex, ey;
-          cell_xy(in, el, &ex, &ey);
-          uint32_t first = kNull;
-          for (int ddx = -1; ddx <= 1 && first == kNull; ++ddx)
-            for (int ddy = -1; ddy <= 1; ++ddy) {
-              const uint32_t o = in->cell_base + torus8(ex, ey, ddx, ddy, W, H);
-              if (*a.cells.col<uint8_t>(o, a.kind_off) == K_NEW) {
-                first = o;
-                break;
-              }
-            }
-          if (first == g) {
-            const uint32_t cnd = smmo_new(h, a.cand);
-            if (cnd != kNull) {
-              *fld<int32_t>(h, cnd, a.c_cell) = (int32_t)e;
-              *fld<uint8_t>(h, cnd, a.c_action) = ACT_KEEP;
-            }
-            set_cell(a, e, cnd, cnd != kNull ? K_CAND : K_EMPTY);
+          const uint32_t eb = 5 * (dx + 2) + dy + 2;
+          if (!((isempty >> eb) & 1u)) continue;
+          const uint32_t around = isnew & (kBlock3 << (eb - 6));
+          if ((uint32_t)(__ffs(around) - 1) != 12u) continue;  // another new Alive comes first
+          const uint32_t e = in->cell_base + torus8(x, y, dx, dy, W, H);
+          const uint32_t cnd = smmo_new(h, a.cand);
+          if (cnd != kNull) {
+            *fld<int32_t>(h, cnd, a.c_cell) = (int32_t)e;
+            *fld<uint8_t>(h, cnd, a.c_action) = ACT_KEEP;
           }
+          set_cell(a, e, cnd, cnd != kNull ? K_CAND : K_EMPTY);
         }
     } else {
       const uint8_t act = *fld<uint8_t>(h, self, a.a_action);
