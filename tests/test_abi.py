@@ -149,3 +149,37 @@ def test_batch_define_checks_its_arguments(libsmmo):
     assert libsmmo.smmo_batch_define(None, rows, 2) == -1
     n = ctypes.c_int()
     assert libsmmo.smmo_batch_count(None, ctypes.byref(n)) == -1
+
+
+def test_step_kernel_modes_agree_with_the_header(libsmmo):
+    """The Wa-Tor step-kernel mode values of include/smmo.h, the Python
+    binding and bench.py's names are the same numbers, and the host rejects
+    a null world before any CUDA call."""
+    src = open(os.path.join(ROOT, "include", "smmo.h")).read()
+    hdr = {k: int(v) for k, v in re.findall(r"(SMMO_WATOR_\w+)\s*=\s*(\d+)", src)}
+    from paper_1908_05845_gb300 import workloads as wl
+    assert hdr == {"SMMO_WATOR_FOUR_DO_ALLS": wl.FOUR_DO_ALLS, "SMMO_WATOR_PHASED1": wl.PHASED1,
+                   "SMMO_WATOR_PHASED2": wl.PHASED2, "SMMO_WATOR_QUEUED_CREATION": wl.QUEUED,
+                   "SMMO_WATOR_MARKED_UPDATE": wl.MARKED}
+    import bench
+    assert bench.STEP_KERNELS["four_do_alls"] == wl.FOUR_DO_ALLS
+    assert bench.STEP_KERNELS["phased2_queued"] == wl.PHASED2 | wl.QUEUED
+    assert bench.STEP_KERNELS["four_do_alls_marked_queued"] == wl.FOUR_DO_ALLS | wl.MARKED | wl.QUEUED
+    # every mode the bench compares is one the library accepts (checked on a GPU);
+    # here: no fused mode is combined with the marked update
+    for mode in bench.STEP_KERNELS.values():
+        assert not (mode & wl.MARKED and mode & 3)
+    assert libsmmo.smmo_world_set_step_kernels(None, 0) == -1
+
+
+def test_fused_phase_bytes_are_the_sum_of_the_pair():
+    """A fused species launch is charged the bytes of its prepare and its
+    update, and the whole-step byte count is the same in either form."""
+    import bench
+    b = bench.BYTES_PER_OBJECT
+    assert b["fish_step"] == b["fish_prepare"] + b["fish_update"]
+    assert b["shark_step"] == b["shark_prepare"] + b["shark_update"]
+    objs = [0, 0, 0, 0, 7.0, 7.0, 3.0, 3.0]
+    four = sum(b.get(bench.PHASES[p], 0) * objs[p] for p in range(8))
+    fused = sum(b.get(bench.PHASES_FUSED[p], 0) * objs[p] for p in range(8) if bench.PHASES_FUSED[p])
+    assert four == fused
