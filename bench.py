@@ -59,23 +59,20 @@ PHASES_FUSED = PHASES[:4] + ["fish_step", "", "shark_step", ""]
 STEP_KERNELS = {"four_do_alls": 0, "phased1": 1, "phased2": 2, "four_do_alls_queued": 4, "phased2_queued": 6,
                 "four_do_alls_marked": 8, "four_do_alls_marked_queued": 12}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "wator_2048_fish_update_traffic.txt")  # JSON
-# Sources of the Wa-Tor do-all kernels: the allocator and do-all core, the
-# cellular helpers, and the Wa-Tor section of world.cu (between its Wa-Tor
-# and Life banners), so that changes elsewhere keep a traffic capture valid.
+# Sources of the Wa-Tor kernels: the allocator and do-all core, the
+# cellular helpers, the fused phases, and the Wa-Tor methods and their
+# variants (world_wator.cuh, world_modes.cu, world_phased.cu), so that
+# changes elsewhere keep a traffic capture valid.
 KERNEL_SOURCES = ["paper_1908_05845_gb300/csrc/smmo_core.cuh", "paper_1908_05845_gb300/csrc/grid_common.cuh",
-                  "paper_1908_05845_gb300/csrc/phased.cuh", "paper_1908_05845_gb300/csrc/levels.cuh"]
-WATOR_SECTION = ("paper_1908_05845_gb300/csrc/world.cu",
-                 "// ================================================================ Wa-Tor",
-                 "// ================================================================ Life")
+                  "paper_1908_05845_gb300/csrc/phased.cuh", "paper_1908_05845_gb300/csrc/levels.cuh",
+                  "paper_1908_05845_gb300/csrc/world_wator.cuh", "paper_1908_05845_gb300/csrc/world_modes.cu",
+                  "paper_1908_05845_gb300/csrc/world_phased.cu"]
 
 
 def kernel_hash(read=lambda f: open(os.path.join(ROOT, f), "rb").read()) -> str:
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         h.update(read(f))
-    src = read(WATOR_SECTION[0]).decode()
-    a, b = src.index(WATOR_SECTION[1]), src.index(WATOR_SECTION[2])
-    h.update(src[a:b].encode())
     return h.hexdigest()[:16]
 
 

@@ -28,470 +28,9 @@
 #include <mutex>
 #include <vector>
 
-#include "grid_common.cuh"
-#include "heap_internal.h"
-#include "phased.cuh"
-#include "smmo.h"
-#include "smmo_core.cuh"
-
-using namespace smmo;
+#include "world_wator.cuh"
 
 namespace {
-
-struct WorldArgs {
-  CellRef cells;
-  uint32_t occ_off, req_off, kind_off;
-  uint32_t fish, shark, alive, cand;
-  uint32_t f_cell, f_target, f_age;
-  uint32_t s_cell, s_target, s_age, s_energy;
-  uint32_t a_cell, a_action, a_isnew, a_blocked;
-  uint32_t c_cell, c_action;
-  uint32_t survive, born, block;  // rule of the Life-kind instances
-  uint64_t seed;
-  const uint32_t* tp;  // device step counter (1-based during a step)
-  uint32_t phase;      // 0 fish, 1 shark
-  int32_t fish_breed, shark_breed, starve, breed_strict;
-  int8_t* out_kind;
-  int16_t* out_age;
-  int16_t* out_energy;
-  uint8_t* out_state;
-  uint32_t* out_count;
-  unsigned long long* errors;
-  uint32_t* seen;  // one bit per cell (allocation-free export only)
-  unsigned long long* ctl;  // grid-barrier words of a two-phase launch (zeroed per step)
-  DeferQueue fq, sq;        // queued creations of fish and sharks (one buffer, two counters)
-};
-
-template <class T>
-__device__ __forceinline__ T* fld(const HeapView& h, uint32_t self, uint32_t off) {
-  return field_ptr<T>(h, off, self);
-}
-
-// ================================================================ Wa-Tor
-// A cell holds its occupant's handle, a 32-bit request word and a one-byte
-// kind that only the Life instances use (see the Life section).  One phase
-// = prepare (choose a neighbour, post a request) + update (move if
-// granted).  The thesis' Cell::prepare / Cell::decide passes are folded into
-// the request word of the target cell: the movers into a cell are among its
-// four neighbours, so the lowest source cell is the requester of lowest rank
-// among them (rank = how many of the target's neighbours have a smaller cell
-// index); a requester posts key = ((2^30 - 1 - epoch) << 2) | rank with
-// atomicMin, epoch = 2 t + phase.  The smallest key of the current phase
-// wins, keys of older phases are larger and never win, so no pass over all
-// cells resets them (2^29 steps).  The prepare keeps target | rank << 30 in
-// the agent's target field (cells are below 2^30), so the update finds
-// both without recomputing.  (A kind byte per cell for the Wa-Tor
-// neighbour tests, replacing the handle and type-id loads, was measured:
-// the prepares gained less than the two extra byte stores per mover cost
-// the updates.)
-enum : uint8_t { K_EMPTY = 0, K_ALIVE = 1, K_CAND = 2, K_BLOCK = 3 };
-constexpr uint32_t kCellMask = 0x3FFFFFFFu;
-
-__device__ __forceinline__ uint32_t req_key(uint32_t t, uint32_t phase, uint32_t rank) {
-  return ((0x3FFFFFFFu - (2u * t + phase)) << 2) | rank;
-}
-
-// Rank (0..3) of the neighbour in direction e of cell (tx, ty) among its
-// four neighbours by cell index, on a W x H torus (W, H >= 3).  Cell index
-// = row W + column, so neighbours order by row first: the row above
-// (ty - 1), the cell's own row (the horizontal pair) and the row below
-// (ty + 1), taken mod H.  Inside the torus that is up, pair, down; on the
-// first row (up wraps to the last row) pair, down, up; on the last row
-// (down wraps to row 0) down, up, pair.  Within the pair left comes before
-// right except on the first and last columns, where one of them wraps.
-__device__ __forceinline__ uint32_t nb_rank(uint32_t tx, uint32_t ty, uint32_t W, uint32_t H, int e) {
-  const bool top = ty == 0, bottom = ty + 1 == H;
-  if (e == 0) return top ? 3u : bottom ? 1u : 0u;  // up
-  if (e == 2) return top ? 2u : bottom ? 0u : 3u;  // down
-  const uint32_t pair = top ? 0u : bottom ? 2u : 1u;
-  const bool hwrap = tx == 0 || tx + 1 == W;
-  return pair + ((e == 3) == hwrap ? 1u : 0u);     // left (3) or right (1)
-}
-
-// (x, y) of the neighbour in direction d of local cell (x, y).
-__device__ __forceinline__ void nb_xy(uint32_t x, uint32_t y, uint32_t W, uint32_t H, int d, uint32_t* nx,
-                                      uint32_t* ny) {
-  *nx = x; *ny = y;
-  if (d == 0) *ny = y == 0 ? H - 1 : y - 1;
-  else if (d == 1) *nx = x + 1 == W ? 0 : x + 1;
-  else if (d == 2) *ny = y + 1 == H ? 0 : y + 1;
-  else *nx = x == 0 ? W - 1 : x - 1;
-}
-
-// The (r mod k)-th of the k directions set in mask (in direction order 0..3).
-__device__ __forceinline__ int pick_dir(uint32_t mask, uint32_t r) {
-  const uint32_t n = (uint32_t)__popc(mask);
-  uint32_t k = n == 3 ? r % 3u : r & (n - 1);  // n is 1, 2, 3 or 4
-  while (k--) mask &= mask - 1;
-  return __ffs(mask) - 1;
-}
-
-// The direction an agent on local cell lc of `in` takes among the set bits
-// of mask (non-empty): the (draw mod k)-th of the k choices.  With a single
-// choice the draw cannot change the result and is not computed (the draws
-// are counter-based, so skipping one affects no other).
-__device__ __forceinline__ int choose_dir(const WorldArgs& a, const Inst* in, uint32_t tag, uint32_t t,
-                                          uint32_t lc, uint32_t mask) {
-  if ((mask & (mask - 1)) == 0) return __ffs(mask) - 1;
-  return pick_dir(mask, philox_draw(a.seed, tag, t, lc, in->id));
-}
-
-// Posts the request of the agent on local cell (x, y) of `in` to move in
-// direction d; returns target | rank << 30 for the agent's target field.
-__device__ __forceinline__ uint32_t post_request(const WorldArgs& a, const Inst* in, uint32_t x, uint32_t y,
-                                                 int d, uint32_t t) {
-  uint32_t tx, ty;
-  nb_xy(x, y, in->W, in->H, d, &tx, &ty);
-  const uint32_t rank = nb_rank(tx, ty, in->W, in->H, (d + 2) & 3);  // we are its neighbour d + 2
-  const uint32_t tgt = in->cell_base + ty * in->W + tx;
-  atomicMin(a.cells.col<uint32_t>(tgt, a.req_off), req_key(t, a.phase, rank));
-  return tgt | (rank << 30);
-}
-
-// Whether the request recorded in target field value tv (see post_request)
-// won.
-__device__ __forceinline__ bool won_request(const WorldArgs& a, uint32_t tv) {
-  return *a.cells.col<uint32_t>(tv & kCellMask, a.req_off) == req_key(*a.tp, a.phase, tv >> 30);
-}
-
-// Occupant of a Wa-Tor cell (the Wa-Tor methods test neighbours through
-// the handle; their cells' kind bytes stay K_EMPTY).
-__device__ __forceinline__ void set_occ(const WorldArgs& a, uint32_t g, uint32_t handle) {
-  *a.cells.col<uint32_t>(g, a.occ_off) = handle;
-}
-
-// Occupant of a Life cell and its kind byte.
-__device__ __forceinline__ void set_cell(const WorldArgs& a, uint32_t g, uint32_t handle, uint8_t kind) {
-  *a.cells.col<uint32_t>(g, a.occ_off) = handle;
-  *a.cells.col<uint8_t>(g, a.kind_off) = kind;
-}
-
-// The prepares return whether the agent has anything to do in the update
-// (a posted request, or a starving shark), for the marking do-all below.
-struct FishPrepare {
-  using Args = WorldArgs;
-  __device__ static bool run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
-    const uint32_t g = *fld<int32_t>(h, self, a.f_cell);
-    int16_t* agep = fld<int16_t>(h, self, a.f_age);
-    *agep = (int16_t)(*agep + 1);
-    const Inst* in = find_inst(h, g);
-    const uint32_t lc = g - in->cell_base, W = in->W, H = in->H;
-    uint32_t x, y;
-    cell_xy(in, lc, &x, &y);
-    uint32_t empty = 0;
-#pragma unroll
-    for (int d = 0; d < 4; ++d)
-      if (*a.cells.col<uint32_t>(in->cell_base + torus_nb4(x, y, W, H, d), a.occ_off) == kNull) empty |= 1u << d;
-    uint32_t tgt = g;
-    if (empty) {
-      const uint32_t t = *a.tp;
-      tgt = post_request(a, in, x, y, choose_dir(a, in, TAG_FISH, t, lc, empty), t);
-    }
-    *fld<int32_t>(h, self, a.f_target) = (int32_t)tgt;
-    return tgt != g;
-  }
-};
-
-// Moves a fish whose request won; a ripe mover leaves a newborn fish on its
-// old cell (created after the round, see defer_new), every other mover
-// leaves it empty.
-struct FishUpdate {
-  using Args = WorldArgs;
-  static constexpr uint32_t kDeferMax = 1;
-  __device__ static uint32_t child_class(const Args& a) { return a.fish; }
-  __device__ static void create(const HeapView& h, const Args& a, uint32_t child, uint32_t g) {
-    if (child != kNull) {
-      *fld<int32_t>(h, child, a.f_cell) = (int32_t)g;
-      *fld<int32_t>(h, child, a.f_target) = (int32_t)g;
-      *fld<int16_t>(h, child, a.f_age) = 0;
-    }
-    set_occ(a, g, child);
-  }
-  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
-    int32_t* cellp = fld<int32_t>(h, self, a.f_cell);
-    const uint32_t g = *cellp;
-    const uint32_t tv = *fld<int32_t>(h, self, a.f_target);
-    const uint32_t tgt = tv & kCellMask;
-    if (tgt == g || !won_request(a, tv)) return;
-    set_occ(a, tgt, self);
-    *cellp = (int32_t)tgt;
-    int16_t* agep = fld<int16_t>(h, self, a.f_age);
-    const int age = *agep;
-    const bool ripe = a.breed_strict ? age > a.fish_breed : age >= a.fish_breed;
-    if (ripe) {
-      *agep = 0;
-      defer_new(g);
-    } else {
-      set_occ(a, g, kNull);
-    }
-  }
-};
-
-struct SharkPrepare {
-  using Args = WorldArgs;
-  __device__ static bool run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
-    const uint32_t g = *fld<int32_t>(h, self, a.s_cell);
-    int16_t* agep = fld<int16_t>(h, self, a.s_age);
-    int16_t* enp = fld<int16_t>(h, self, a.s_energy);
-    *agep = (int16_t)(*agep + 1);
-    const int16_t en = (int16_t)(*enp - 1);
-    *enp = en;
-    uint32_t tgt = g;
-    if (en != 0) {
-      const Inst* in = find_inst(h, g);
-      const uint32_t lc = g - in->cell_base, W = in->W, H = in->H;
-      uint32_t x, y;
-      cell_xy(in, lc, &x, &y);
-      uint32_t fish = 0, empty = 0;
-#pragma unroll
-      for (int d = 0; d < 4; ++d) {
-        const uint32_t o = *a.cells.col<uint32_t>(in->cell_base + torus_nb4(x, y, W, H, d), a.occ_off);
-        if (o == kNull) empty |= 1u << d;
-        else if (type_of(h, o) == a.fish) fish |= 1u << d;
-      }
-      if (fish | empty) {
-        const uint32_t t = *a.tp;
-        tgt = post_request(a, in, x, y, choose_dir(a, in, TAG_SHARK, t, lc, fish ? fish : empty), t);
-      }
-    }
-    *fld<int32_t>(h, self, a.s_target) = (int32_t)tgt;
-    return en == 0 || tgt != g;
-  }
-};
-
-// A starved shark leaves its cell and deletes itself; a mover eats the fish
-// on its target (deleting an object of another class) and, when ripe,
-// leaves a newborn shark on its old cell (deferred, as for fish).
-struct SharkUpdate {
-  using Args = WorldArgs;
-  static constexpr uint32_t kDeferMax = 1;
-  __device__ static uint32_t child_class(const Args& a) { return a.shark; }
-  __device__ static void create(const HeapView& h, const Args& a, uint32_t child, uint32_t g) {
-    if (child != kNull) {
-      *fld<int32_t>(h, child, a.s_cell) = (int32_t)g;
-      *fld<int32_t>(h, child, a.s_target) = (int32_t)g;
-      *fld<int16_t>(h, child, a.s_age) = 0;
-      *fld<int16_t>(h, child, a.s_energy) = (int16_t)a.starve;
-    }
-    set_occ(a, g, child);
-  }
-  __device__ static void run(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
-    int32_t* cellp = fld<int32_t>(h, self, a.s_cell);
-    const uint32_t g = *cellp;
-    int16_t* enp = fld<int16_t>(h, self, a.s_energy);
-    const uint32_t tv = *fld<int32_t>(h, self, a.s_target);
-    int16_t* agep = fld<int16_t>(h, self, a.s_age);
-    const int age = *agep;
-    if (*enp == 0) {  // starved: leave the cell and delete itself (last statement)
-      set_occ(a, g, kNull);
-      smmo_delete(h, self);
-      return;
-    }
-    const uint32_t tgt = tv & kCellMask;
-    if (tgt == g || !won_request(a, tv)) return;
-    const uint32_t prey = *a.cells.col<uint32_t>(tgt, a.occ_off);
-    if (prey != kNull) {  // eat the fish (deleting an object of another class)
-      smmo_delete(h, prey);
-      *enp = (int16_t)a.starve;
-    }
-    set_occ(a, tgt, self);
-    *cellp = (int32_t)tgt;
-    const bool ripe = a.breed_strict ? age > a.shark_breed : age >= a.shark_breed;
-    if (ripe) {
-      *agep = 0;
-      defer_new(g);
-    } else {
-      set_occ(a, g, kNull);
-    }
-  }
-};
-
-// ------------------------------------------------- Wa-Tor in two phases
-// The same fish and shark rules as the four do-alls above, for the fused
-// launch of phased.cuh: the prepare phase returns the request word
-// (target | rank << 30) as the carry instead of storing it in the agent's
-// target field, kIdle for an agent that posts no request, and for a shark
-// kStarve when it starves; the update phase runs only for those.  The
-// carries are distinct from every request word because cells stay below
-// 2^30 - 2 (smmo_world_create_batch).
-constexpr uint32_t kIdleWord = 0xFFFFFFFFu, kStarveWord = 0xFFFFFFFEu;
-
-struct FishPhased {
-  using Args = WorldArgs;
-  static constexpr uint32_t kIdle = kIdleWord;
-  static constexpr uint32_t kDeferMax = 1;
-  struct P {
-    uint32_t g, x, y, occ[4];
-    int32_t age;
-    const Inst* in;
-  };
-  struct U {
-    uint32_t g, req;
-    int32_t age;
-  };
-  __device__ static uint32_t child_class(const Args& a) { return a.fish; }
-  __device__ static void create(const HeapView& h, const Args& a, uint32_t child, uint32_t g) {
-    FishUpdate::create(h, a, child, g);
-  }
-  __device__ static void load1(const HeapView& h, const Args& a, uint32_t, uint32_t self, P& p) {
-    p.g = *fld<int32_t>(h, self, a.f_cell);
-    p.age = *fld<int16_t>(h, self, a.f_age);
-  }
-  __device__ static void load2(const HeapView& h, const Args& a, uint32_t, uint32_t, P& p) {
-    p.in = find_inst(h, p.g);
-    cell_xy(p.in, p.g - p.in->cell_base, &p.x, &p.y);
-#pragma unroll
-    for (int d = 0; d < 4; ++d)
-      p.occ[d] = *a.cells.col<uint32_t>(p.in->cell_base + torus_nb4(p.x, p.y, p.in->W, p.in->H, d), a.occ_off);
-  }
-  __device__ static uint32_t prepare(const HeapView& h, const Args& a, uint32_t, uint32_t self, P& p) {
-    *fld<int16_t>(h, self, a.f_age) = (int16_t)(p.age + 1);
-    uint32_t empty = 0;
-#pragma unroll
-    for (int d = 0; d < 4; ++d)
-      if (p.occ[d] == kNull) empty |= 1u << d;
-    if (!empty) return kIdle;
-    const uint32_t t = *a.tp;
-    return post_request(a, p.in, p.x, p.y, choose_dir(a, p.in, TAG_FISH, t, p.g - p.in->cell_base, empty), t);
-  }
-  __device__ static void spill(const HeapView& h, const Args& a, uint32_t, uint32_t self, uint32_t w) {
-    *fld<int32_t>(h, self, a.f_target) = (int32_t)w;
-  }
-  __device__ static uint32_t unspill(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
-    return (uint32_t)*fld<int32_t>(h, self, a.f_target);
-  }
-  __device__ static void uload(const HeapView& h, const Args& a, uint32_t, uint32_t self, uint32_t w, U& q) {
-    q.req = __ldcg(a.cells.col<uint32_t>(w & kCellMask, a.req_off));
-    q.g = *fld<int32_t>(h, self, a.f_cell);
-    q.age = *fld<int16_t>(h, self, a.f_age);
-  }
-  __device__ static void update(const HeapView& h, const Args& a, uint32_t, uint32_t self, uint32_t w, U& q) {
-    if (q.req != req_key(*a.tp, a.phase, w >> 30)) return;  // another fish won the target
-    const uint32_t tgt = w & kCellMask;
-    set_occ(a, tgt, self);
-    *fld<int32_t>(h, self, a.f_cell) = (int32_t)tgt;
-    const bool ripe = a.breed_strict ? q.age > a.fish_breed : q.age >= a.fish_breed;
-    if (ripe) {
-      *fld<int16_t>(h, self, a.f_age) = 0;
-      defer_new(q.g);
-    } else {
-      set_occ(a, q.g, kNull);
-    }
-  }
-};
-
-struct SharkPhased {
-  using Args = WorldArgs;
-  static constexpr uint32_t kIdle = kIdleWord;
-  static constexpr uint32_t kDeferMax = 1;
-  struct P {
-    uint32_t g, x, y, occ[4];
-    int32_t age, energy;
-    const Inst* in;
-  };
-  struct U {
-    uint32_t g, req, prey;
-    int32_t age;
-  };
-  __device__ static uint32_t child_class(const Args& a) { return a.shark; }
-  __device__ static void create(const HeapView& h, const Args& a, uint32_t child, uint32_t g) {
-    SharkUpdate::create(h, a, child, g);
-  }
-  __device__ static void load1(const HeapView& h, const Args& a, uint32_t, uint32_t self, P& p) {
-    p.g = *fld<int32_t>(h, self, a.s_cell);
-    p.age = *fld<int16_t>(h, self, a.s_age);
-    p.energy = *fld<int16_t>(h, self, a.s_energy);
-  }
-  __device__ static void load2(const HeapView& h, const Args& a, uint32_t, uint32_t, P& p) {
-    p.in = find_inst(h, p.g);
-    cell_xy(p.in, p.g - p.in->cell_base, &p.x, &p.y);
-    if (p.energy == 1) return;  // starves in this step: no neighbour is looked at
-#pragma unroll
-    for (int d = 0; d < 4; ++d)
-      p.occ[d] = *a.cells.col<uint32_t>(p.in->cell_base + torus_nb4(p.x, p.y, p.in->W, p.in->H, d), a.occ_off);
-  }
-  __device__ static uint32_t prepare(const HeapView& h, const Args& a, uint32_t, uint32_t self, P& p) {
-    *fld<int16_t>(h, self, a.s_age) = (int16_t)(p.age + 1);
-    const int16_t en = (int16_t)(p.energy - 1);
-    *fld<int16_t>(h, self, a.s_energy) = en;
-    if (en == 0) return kStarveWord;
-    uint32_t fish = 0, empty = 0;
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      if (p.occ[d] == kNull) empty |= 1u << d;
-      else if (type_of(h, p.occ[d]) == a.fish) fish |= 1u << d;
-    }
-    if (!(fish | empty)) return kIdle;
-    const uint32_t t = *a.tp;
-    return post_request(a, p.in, p.x, p.y,
-                        choose_dir(a, p.in, TAG_SHARK, t, p.g - p.in->cell_base, fish ? fish : empty), t);
-  }
-  __device__ static void spill(const HeapView& h, const Args& a, uint32_t, uint32_t self, uint32_t w) {
-    *fld<int32_t>(h, self, a.s_target) = (int32_t)w;
-  }
-  __device__ static uint32_t unspill(const HeapView& h, const Args& a, uint32_t, uint32_t self) {
-    return (uint32_t)*fld<int32_t>(h, self, a.s_target);
-  }
-  __device__ static void uload(const HeapView& h, const Args& a, uint32_t, uint32_t self, uint32_t w, U& q) {
-    q.g = *fld<int32_t>(h, self, a.s_cell);
-    if (w == kStarveWord) return;
-    const uint32_t tgt = w & kCellMask;
-    q.req = __ldcg(a.cells.col<uint32_t>(tgt, a.req_off));
-    // only the winner of the target writes its occupant in this phase
-    q.prey = __ldcg(a.cells.col<uint32_t>(tgt, a.occ_off));
-    q.age = *fld<int16_t>(h, self, a.s_age);
-  }
-  __device__ static void update(const HeapView& h, const Args& a, uint32_t, uint32_t self, uint32_t w, U& q) {
-    if (w == kStarveWord) {  // starved: leave the cell and delete itself
-      set_occ(a, q.g, kNull);
-      smmo_delete(h, self);
-      return;
-    }
-    if (q.req != req_key(*a.tp, a.phase, w >> 30)) return;  // another shark won the target
-    const uint32_t tgt = w & kCellMask;
-    if (q.prey != kNull) {  // eat the fish (deleting an object of another class)
-      smmo_delete(h, q.prey);
-      *fld<int16_t>(h, self, a.s_energy) = (int16_t)a.starve;
-    }
-    set_occ(a, tgt, self);
-    *fld<int32_t>(h, self, a.s_cell) = (int32_t)tgt;
-    const bool ripe = a.breed_strict ? q.age > a.shark_breed : q.age >= a.shark_breed;
-    if (ripe) {
-      *fld<int16_t>(h, self, a.s_age) = 0;
-      defer_new(q.g);
-    } else {
-      set_occ(a, q.g, kNull);
-    }
-  }
-};
-
-// The same methods with their creations queued (smmo_core.cuh, DeferQueue)
-// and made by a separate launch after the update.
-struct FishUpdateQ : FishUpdate {
-  static constexpr bool kQueued = true;
-  __device__ static DeferQueue queue(const Args& a) { return a.fq; }
-};
-struct SharkUpdateQ : SharkUpdate {
-  static constexpr bool kQueued = true;
-  __device__ static DeferQueue queue(const Args& a) { return a.sq; }
-};
-// Marking prepares and filtered updates (smmo_core.cuh): the update runs
-// only on the agents whose prepare posted a request (or starved); the rest
-// would return at once.
-struct FishPrepareM : FishPrepare { static constexpr bool kMarks = true; };
-struct SharkPrepareM : SharkPrepare { static constexpr bool kMarks = true; };
-struct FishUpdateF : FishUpdate { static constexpr bool kFiltered = true; };
-struct SharkUpdateF : SharkUpdate { static constexpr bool kFiltered = true; };
-struct FishUpdateQF : FishUpdateQ { static constexpr bool kFiltered = true; };
-struct SharkUpdateQF : SharkUpdateQ { static constexpr bool kFiltered = true; };
-struct FishPhasedQ : FishPhased {
-  static constexpr bool kQueued = true;
-  __device__ static DeferQueue queue(const Args& a) { return a.fq; }
-};
-struct SharkPhasedQ : SharkPhased {
-  static constexpr bool kQueued = true;
-  __device__ static DeferQueue queue(const Args& a) { return a.sq; }
-};
 
 // ================================================================ Life
 enum : uint8_t { ACT_KEEP = 0, ACT_BORN = 1, ACT_DELETE = 2, ACT_DIE = 3, ACT_AGE = 4, ACT_EXPIRE = 5 };
@@ -806,23 +345,6 @@ unsigned long long* world_ctl(const smmo_world* w) {
   return reinterpret_cast<unsigned long long*>(reinterpret_cast<uint8_t*>(w->d_t) + 256);
 }
 
-// The fused fish or shark phase (phased.cuh) with K units per round; the
-// barrier words come with the arguments.  The register budget: 48 warps
-// per SM (40 registers) for one unit per round, 40 warps (48 registers)
-// for two.
-#ifndef SMMO_PHASED_WARPS1
-#define SMMO_PHASED_WARPS1 48
-#endif
-#ifndef SMMO_PHASED_WARPS2
-#define SMMO_PHASED_WARPS2 40
-#endif
-template <class M, int K>
-int launch_wator_phased(smmo_heap* h, int cls, const void* args, cudaStream_t s) {
-  constexpr int kMinb = (K == 1 ? SMMO_PHASED_WARPS1 : SMMO_PHASED_WARPS2) / (kPhasedThreads / 32);
-  const WorldArgs* a = static_cast<const WorldArgs*>(args);
-  return launch_phased<M, K, (kMinb > 0 ? kMinb : 1)>(h, cls, *a, a->ctl, s);
-}
-
 // reuse = the previous do-all enumerated the same concrete class and did
 // not create or delete objects of it, so its snapshot is still exact
 int pdo(smmo_world* w, int cls, method_launch_fn fn, const WorldArgs& a, cudaStream_t s,
@@ -862,39 +384,37 @@ int world_steps(smmo_world* w, int nsteps, cudaStream_t s, PhaseTimer* pt) {
       if (!st) st = pdo(w, w->cls_cand, &launch_do_all<CandUpdate>, a, s, pt, 2);
       if (!st) st = pdo(w, w->cls_alive, &launch_do_all<AliveUpdate>, a, s, pt, 3);
     }
-    const int kern = w->step_kernels & 3;
-    const bool q = (w->step_kernels & SMMO_WATOR_QUEUED_CREATION) != 0;
-    if (!st && w->nw && kern != SMMO_WATOR_FOUR_DO_ALLS) {
+    const int mode = w->step_kernels;
+    if (!st && w->nw && (mode & 3) != SMMO_WATOR_FOUR_DO_ALLS) {
       // one Wa-Tor iteration, each phase (prepare + update) in one launch
-      const bool k2 = kern == SMMO_WATOR_PHASED2;
+      // (world_modes.cu), the creations after it when they are queued
+      method_launch_fn fc = wator_mode_launcher(kWFishCreate, mode), sc = wator_mode_launcher(kWSharkCreate, mode);
       a.phase = 0;
       a.ctl = world_ctl(w);
-      method_launch_fn ff = q ? (k2 ? &launch_wator_phased<FishPhasedQ, 2> : &launch_wator_phased<FishPhasedQ, 1>)
-                              : (k2 ? &launch_wator_phased<FishPhased, 2> : &launch_wator_phased<FishPhased, 1>);
-      method_launch_fn sf = q ? (k2 ? &launch_wator_phased<SharkPhasedQ, 2> : &launch_wator_phased<SharkPhasedQ, 1>)
-                              : (k2 ? &launch_wator_phased<SharkPhased, 2> : &launch_wator_phased<SharkPhased, 1>);
-      st = pdo(w, w->cls_fish, ff, a, s, pt, 4);
-      if (!st && q) st = pdo(w, w->cls_fish, &launch_create_queued<FishPhasedQ>, a, s, pt, 4, true);
+      st = pdo(w, w->cls_fish, wator_mode_launcher(kWFishPrepare, mode), a, s, pt, 4);
+      if (!st && fc) st = pdo(w, w->cls_fish, fc, a, s, pt, 4, true);
       a.phase = 1;
       a.ctl = world_ctl(w) + kBarrierWords;
-      if (!st) st = pdo(w, w->cls_shark, sf, a, s, pt, 6);
-      if (!st && q) st = pdo(w, w->cls_shark, &launch_create_queued<SharkPhasedQ>, a, s, pt, 6, true);
+      if (!st) st = pdo(w, w->cls_shark, wator_mode_launcher(kWSharkPrepare, mode), a, s, pt, 6);
+      if (!st && sc) st = pdo(w, w->cls_shark, sc, a, s, pt, 6, true);
     } else if (!st && w->nw) {  // one Wa-Tor iteration (Sec. 7.6): fish phase, shark phase
-      const bool mk = (w->step_kernels & SMMO_WATOR_MARKED_UPDATE) != 0;
-      method_launch_fn fp = mk ? &launch_do_all<FishPrepareM> : &launch_do_all<FishPrepare>;
-      method_launch_fn sp = mk ? &launch_do_all<SharkPrepareM> : &launch_do_all<SharkPrepare>;
-      method_launch_fn fu = q ? (mk ? &launch_do_all<FishUpdateQF> : &launch_do_all<FishUpdateQ>)
-                              : (mk ? &launch_do_all<FishUpdateF> : &launch_do_all<FishUpdate>);
-      method_launch_fn su = q ? (mk ? &launch_do_all<SharkUpdateQF> : &launch_do_all<SharkUpdateQ>)
-                              : (mk ? &launch_do_all<SharkUpdateF> : &launch_do_all<SharkUpdate>);
+      // the four plain do-alls here; marked, filtered and queued variants
+      // from world_modes.cu
+      method_launch_fn fp = wator_mode_launcher(kWFishPrepare, mode), sp = wator_mode_launcher(kWSharkPrepare, mode);
+      method_launch_fn fu = wator_mode_launcher(kWFishUpdate, mode), su = wator_mode_launcher(kWSharkUpdate, mode);
+      method_launch_fn fc = wator_mode_launcher(kWFishCreate, mode), sc = wator_mode_launcher(kWSharkCreate, mode);
+      if (!fp) fp = &launch_do_all<FishPrepare>;
+      if (!sp) sp = &launch_do_all<SharkPrepare>;
+      if (!fu) fu = &launch_do_all<FishUpdate>;
+      if (!su) su = &launch_do_all<SharkUpdate>;
       a.phase = 0;
       st = pdo(w, w->cls_fish, fp, a, s, pt, 4);
       if (!st) st = pdo(w, w->cls_fish, fu, a, s, pt, 5, true);
-      if (!st && q) st = pdo(w, w->cls_fish, &launch_create_queued<FishUpdateQ>, a, s, pt, 5, true);
+      if (!st && fc) st = pdo(w, w->cls_fish, fc, a, s, pt, 5, true);
       a.phase = 1;
       if (!st) st = pdo(w, w->cls_shark, sp, a, s, pt, 6);
       if (!st) st = pdo(w, w->cls_shark, su, a, s, pt, 7, true);
-      if (!st && q) st = pdo(w, w->cls_shark, &launch_create_queued<SharkUpdateQ>, a, s, pt, 7, true);
+      if (!st && sc) st = pdo(w, w->cls_shark, sc, a, s, pt, 7, true);
     }
     if (st) return st;
   }
