@@ -4,11 +4,14 @@
 // independent instances ("batched heap": all instances' objects share the
 // heap and every step runs one parallel_do per class over all of them).
 //
-// Classes: Cell {occ: handle of the agent on the cell, req: u64 request
-// word}; WAgent (abstract) {cell, target} with Fish {age} and Shark {age,
-// energy}; LAgent (abstract) {cell, action} with Alive {is_new, blocked}
-// and Candidate {}.  Cells are created once by bulk_new in global cell order
-// and addressed densely; agents hold their global cell index.
+// Classes: Cell {occ: handle of the agent on the cell, req: u32 request
+// word, kind: u8}; WAgent (abstract) {cell, target} with Fish {age} and
+// Shark {age, energy}; LAgent (abstract) {cell, action} with Alive {is_new,
+// blocked} and Candidate {}.  Cells are created once by bulk_new in global
+// cell order and addressed densely; agents hold their global cell index.
+// The Wa-Tor methods are in world_wator.cuh (the four plain do-alls, here)
+// and world_modes.cu / world_phased.cu (the other step kernels); this file
+// holds the Life methods, the exports and the world API.
 //
 // The Life-kind instances follow one rule: an alive object survives iff bit
 // n of `survive` is set (n = alive, i.e. not blocking, Alive objects among
